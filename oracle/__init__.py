@@ -1,0 +1,329 @@
+"""FP64 CPU oracle of the LEEA hot path -- test infrastructure.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It wraps ``leea_oracle.c`` (plain C, double
+precision, single-threaded) through ctypes and numpy; it never imports the
+CUDA package, and the CUDA package never imports it.
+
+Every function takes and returns numpy arrays in the oracle's own layout:
+populations are ``float64[pop, c]`` in the logical gene order of Section 3.2
+(per layer: W row-major out x in, then b).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "leea_oracle.c")
+_HDR = os.path.join(_HERE, "leea_oracle.h")
+_OUT = os.path.join(_HERE, "_build", "libleea_oracle.so")
+
+TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
+ELITE, CROSSOVER, MUTATION = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: same results on x86 and Arm)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
+        tmp = _OUT + f".tmp{os.getpid()}"
+        subprocess.check_call([
+            "gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+            "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+@dataclass
+class Params:
+    """Operator parameters; defaults are the paper's (Section 4, hyperparameter block)."""
+    xo_op: int = 0          # 0 uniform, 1 arithmetic crossover
+    xo_gene_p: float = 0.5  # P(gene from parent 2) in uniform crossover
+    sel_op: int = 0         # 0 truncation, 1 tournament
+    rho: float = 0.5        # truncation proportion
+    tour_k: int = 3         # tournament size
+    n_elite: int = -1       # -1 => round(p_e * pop)
+    p_e: float = 0.05
+    p_c: float = 0.5
+    sigma: float = 0.001
+    mut_rate: float = 1.0   # 1.0 mutates every gene, as in the paper
+    alpha: float = 1.0      # 1.0 disables inheritance
+    init: int = 0           # 0 N(0, 1/fan_in), 1 Glorot-uniform
+    precision: int = 0      # 0 FP32, 1 BF16 shadow, 2 FP8 shadow
+
+
+class _CParams(ctypes.Structure):
+    _fields_ = [
+        ("xo_op", ctypes.c_int32), ("xo_gene_p", ctypes.c_float),
+        ("sel_op", ctypes.c_int32), ("rho", ctypes.c_float),
+        ("tour_k", ctypes.c_int32), ("n_elite", ctypes.c_int32),
+        ("p_e", ctypes.c_float), ("p_c", ctypes.c_float),
+        ("sigma", ctypes.c_float), ("mut_rate", ctypes.c_float),
+        ("alpha", ctypes.c_float), ("init", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+def _cparams(p: Params) -> _CParams:
+    return _CParams(**{f.name: getattr(p, f.name) for f in fields(Params)})
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        P = ctypes.POINTER
+        i32, u32, u64, i64, dbl = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_double
+        vp = ctypes.c_void_p
+        L.leea_cpu_philox.argtypes = [P(u32), P(u32), P(u32)]
+        L.leea_cpu_philox.restype = None
+        L.leea_cpu_draw.argtypes = [u64, u32, u32, u32, u32]
+        L.leea_cpu_draw.restype = u32
+        L.leea_cpu_u01.argtypes = [u32]
+        L.leea_cpu_u01.restype = dbl
+        L.leea_cpu_normal.argtypes = [u64, u32, u32, u32, u32]
+        L.leea_cpu_normal.restype = dbl
+        L.leea_cpu_index.argtypes = [u32, u32]
+        L.leea_cpu_index.restype = u32
+        L.leea_cpu_threshold.argtypes = [dbl]
+        L.leea_cpu_threshold.restype = u64
+        L.leea_cpu_num_params.argtypes = [vp, i32]
+        L.leea_cpu_num_params.restype = i64
+        L.leea_cpu_counts.argtypes = [i32, P(_CParams), P(i32), P(i32), P(i32), P(i32)]
+        L.leea_cpu_init.argtypes = [i32, vp, i32, i32, u64, vp]
+        L.leea_cpu_evaluate.argtypes = [i32, vp, i32, vp, vp, vp, i32, vp, vp, vp]
+        L.leea_cpu_rank.argtypes = [i32, vp, vp]
+        L.leea_cpu_select.argtypes = [i32, P(_CParams), vp, vp, u64, u32, vp, vp, vp, vp]
+        L.leea_cpu_breed.argtypes = [i32, vp, i32, P(_CParams), u64, u32, vp, vp, vp, vp, i32, i32, vp]
+        L.leea_cpu_inherit.argtypes = [i32, dbl, vp, vp, i32, vp]
+        L.leea_cpu_create.argtypes = [i32, vp, i32, P(_CParams), u64, P(vp)]
+        L.leea_cpu_generation.argtypes = [vp, vp, vp, i32]
+        L.leea_cpu_fitness.argtypes = [vp, vp, vp, vp]
+        L.leea_cpu_best_params.argtypes = [vp, vp, i64]
+        L.leea_cpu_get_population.argtypes = [vp, vp]
+        L.leea_cpu_set_population.argtypes = [vp, vp]
+        L.leea_cpu_set_fitness.argtypes = [vp, vp]
+        L.leea_cpu_set_generation.argtypes = [vp, u32, i32]
+        L.leea_cpu_get_selection.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.leea_cpu_generation_index.argtypes = [vp]
+        L.leea_cpu_generation_index.restype = u32
+        L.leea_cpu_destroy.argtypes = [vp]
+        L.leea_cpu_destroy.restype = None
+        for name in ("leea_cpu_counts", "leea_cpu_init", "leea_cpu_evaluate", "leea_cpu_rank",
+                     "leea_cpu_select", "leea_cpu_breed", "leea_cpu_inherit", "leea_cpu_create",
+                     "leea_cpu_generation", "leea_cpu_fitness", "leea_cpu_best_params",
+                     "leea_cpu_get_population", "leea_cpu_set_population", "leea_cpu_set_fitness",
+                     "leea_cpu_set_generation", "leea_cpu_get_selection"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str) -> None:
+    if rc != 0:
+        raise OracleError(f"{what} failed with status {rc}")
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dims(dims) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+# ---- random streams -------------------------------------------------------
+def philox(ctr, key) -> np.ndarray:
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().leea_cpu_philox(c, k, o)
+    return np.array(list(o), dtype=np.uint32)
+
+
+def draw(seed: int, tag: int, gen: int, ent: int, n: int) -> int:
+    return int(lib().leea_cpu_draw(seed, tag, gen, ent, n))
+
+
+def u01(u: int) -> float:
+    return float(lib().leea_cpu_u01(u))
+
+
+def normal(seed: int, tag: int, gen: int, ent: int, i: int) -> float:
+    return float(lib().leea_cpu_normal(seed, tag, gen, ent, i))
+
+
+def index(u: int, m: int) -> int:
+    return int(lib().leea_cpu_index(u, m))
+
+
+def threshold(q: float) -> int:
+    return int(lib().leea_cpu_threshold(float(q)))
+
+
+# ---- layout ---------------------------------------------------------------
+def num_params(dims) -> int:
+    d = _dims(dims)
+    return int(lib().leea_cpu_num_params(_ptr(d), len(d)))
+
+
+def counts(pop: int, prm: Params) -> tuple[int, int, int, int]:
+    e, c, m, pl = (ctypes.c_int32() for _ in range(4))
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_counts(pop, ctypes.byref(cp), ctypes.byref(e), ctypes.byref(c),
+                                 ctypes.byref(m), ctypes.byref(pl)), "counts")
+    return e.value, c.value, m.value, pl.value
+
+
+# ---- steps ----------------------------------------------------------------
+def init(pop: int, dims, init_kind: int, seed: int) -> np.ndarray:
+    d = _dims(dims)
+    out = np.empty((pop, num_params(d)), dtype=np.float64)
+    _check(lib().leea_cpu_init(pop, _ptr(d), len(d), init_kind, seed, _ptr(out)), "init")
+    return out
+
+
+def evaluate(popv, dims, x, y, want_logits: bool = False):
+    """Returns (f[pop], correct[pop]) or (f, correct, logits[pop, batch, d_out])."""
+    d = _dims(dims)
+    pv = _f64(popv)
+    pop = pv.shape[0]
+    xv = _f64(x).reshape(-1, int(d[0]))
+    yv = _i32(y)
+    batch = xv.shape[0]
+    f = np.empty(pop, dtype=np.float64)
+    cor = np.empty(pop, dtype=np.int32)
+    logits = np.empty((pop, batch, int(d[-1])), dtype=np.float64) if want_logits else None
+    _check(lib().leea_cpu_evaluate(pop, _ptr(d), len(d), _ptr(pv), _ptr(xv), _ptr(yv), batch,
+                                   _ptr(f), _ptr(cor), _ptr(logits)), "evaluate")
+    return (f, cor, logits) if want_logits else (f, cor)
+
+
+def rank(f_adj) -> np.ndarray:
+    f = _f64(f_adj)
+    order = np.empty(f.shape[0], dtype=np.int32)
+    _check(lib().leea_cpu_rank(f.shape[0], _ptr(f), _ptr(order)), "rank")
+    return order
+
+
+def select(prm: Params, f_adj, order, seed: int, gen: int):
+    """Returns (par1, par2, kind, f_inh)."""
+    f = _f64(f_adj)
+    o = _i32(order)
+    pop = f.shape[0]
+    par1, par2, kind = (np.empty(pop, dtype=np.int32) for _ in range(3))
+    f_inh = np.empty(pop, dtype=np.float64)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_select(pop, ctypes.byref(cp), _ptr(f), _ptr(o), seed, gen,
+                                 _ptr(par1), _ptr(par2), _ptr(kind), _ptr(f_inh)), "select")
+    return par1, par2, kind, f_inh
+
+
+def breed(prm: Params, dims, seed: int, gen: int, parents, par1, par2, kind,
+          j0: int = 0, j1: int | None = None) -> np.ndarray:
+    d = _dims(dims)
+    pv = _f64(parents)
+    pop = pv.shape[0]
+    j1 = pop if j1 is None else j1
+    out = np.empty((j1 - j0, pv.shape[1]), dtype=np.float64)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_breed(pop, _ptr(d), len(d), ctypes.byref(cp), seed, gen, _ptr(pv),
+                                _ptr(_i32(par1)), _ptr(_i32(par2)), _ptr(_i32(kind)),
+                                j0, j1, _ptr(out)), "breed")
+    return out
+
+
+def inherit(alpha: float, f_inh, f, first: bool) -> np.ndarray:
+    fv = _f64(f)
+    fi = None if f_inh is None else _f64(f_inh)
+    out = np.empty_like(fv)
+    _check(lib().leea_cpu_inherit(fv.shape[0], float(alpha), _ptr(fi), _ptr(fv), int(first),
+                                  _ptr(out)), "inherit")
+    return out
+
+
+# ---- Algorithm 1 as a state object ---------------------------------------------
+class State:
+    """The oracle's LEEA run (the leea_cpu_* state ABI)."""
+
+    def __init__(self, pop: int, dims, prm: Params, seed: int):
+        self.pop = pop
+        self.dims = _dims(dims)
+        self.c = num_params(self.dims)
+        self._cp = _cparams(prm)
+        h = ctypes.c_void_p()
+        _check(lib().leea_cpu_create(pop, _ptr(self.dims), len(self.dims), ctypes.byref(self._cp),
+                                     seed, ctypes.byref(h)), "create")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.leea_cpu_destroy(h)
+            self._h = None
+
+    def generation(self, x, y) -> None:
+        xv = _f64(x).reshape(-1, int(self.dims[0]))
+        yv = _i32(y)
+        _check(lib().leea_cpu_generation(self._h, _ptr(xv), _ptr(yv), xv.shape[0]), "generation")
+
+    def fitness(self):
+        f_adj = np.empty(self.pop, dtype=np.float64)
+        f_raw = np.empty(self.pop, dtype=np.float64)
+        cor = np.empty(self.pop, dtype=np.int32)
+        _check(lib().leea_cpu_fitness(self._h, _ptr(f_adj), _ptr(f_raw), _ptr(cor)), "fitness")
+        return f_adj, f_raw, cor
+
+    def best_params(self) -> np.ndarray:
+        out = np.empty(self.c, dtype=np.float64)
+        _check(lib().leea_cpu_best_params(self._h, _ptr(out), self.c), "best_params")
+        return out
+
+    def population(self) -> np.ndarray:
+        out = np.empty((self.pop, self.c), dtype=np.float64)
+        _check(lib().leea_cpu_get_population(self._h, _ptr(out)), "get_population")
+        return out
+
+    def set_population(self, popv) -> None:
+        pv = _f64(popv)
+        assert pv.shape == (self.pop, self.c)
+        _check(lib().leea_cpu_set_population(self._h, _ptr(pv)), "set_population")
+
+    def set_fitness(self, f_adj) -> None:
+        _check(lib().leea_cpu_set_fitness(self._h, _ptr(_f64(f_adj))), "set_fitness")
+
+    def set_generation(self, gen: int, evaluated: bool) -> None:
+        _check(lib().leea_cpu_set_generation(self._h, gen, int(evaluated)), "set_generation")
+
+    @property
+    def gen(self) -> int:
+        return int(lib().leea_cpu_generation_index(self._h))
+
+    def selection(self):
+        """Returns (order, par1, par2, kind, f_inh) of the last breed."""
+        arrs = [np.empty(self.pop, dtype=np.int32) for _ in range(4)]
+        f_inh = np.empty(self.pop, dtype=np.float64)
+        _check(lib().leea_cpu_get_selection(self._h, *[_ptr(a) for a in arrs], _ptr(f_inh)),
+               "get_selection")
+        return (*arrs, f_inh)

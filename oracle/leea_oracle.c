@@ -1,0 +1,552 @@
+/*
+ * leea_oracle.c -- FP64 CPU oracle of the LEEA hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY (see leea_oracle.h).  Plain, slow and written to
+ * be checked against the paper by eye: every loop follows the definition it
+ * cites, in the order the paper gives, with no blocking or fusion.
+ */
+#include "leea_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 bit     */
+/* multiplies, xor with the other counter words and the round key, and a    */
+/* Weyl-sequence bump of the key between rounds.                             */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void leea_cpu_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        uint64_t prod0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(prod1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)prod1;
+        uint32_t y2 = (uint32_t)(prod0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)prod0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static void stream_block(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
+                         uint32_t block, uint32_t out[4])
+{
+    uint32_t key[2] = { (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) };
+    uint32_t ctr[4] = { block, ent, gen, tag };
+    leea_cpu_philox(ctr, key, out);
+}
+
+/* Scalar draw n of the stream (tag, generation, entity). */
+uint32_t leea_cpu_draw(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t n)
+{
+    uint32_t w[4];
+    stream_block(seed, tag, gen, ent, n >> 2, w);
+    return w[n & 3u];
+}
+
+/* Open-interval uniform from the top 23 bits: (2k + 1) / 2^24, k = u >> 9.
+ * Exact in both float and double; never 0, never 1. */
+double leea_cpu_u01(uint32_t u)
+{
+    return (double)((u >> 9) * 2u + 1u) * (1.0 / 16777216.0);
+}
+
+/* Standard normal for gene i by the Box-Muller transform: the block i >> 2
+ * carries two pairs (words 0,1 and 2,3); the first word of a pair gives the
+ * radius, the second the angle; even genes take the cosine, odd the sine. */
+double leea_cpu_normal(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t i)
+{
+    uint32_t w[4];
+    stream_block(seed, tag, gen, ent, i >> 2, w);
+    uint32_t pair = (i & 3u) >> 1;
+    double u1 = leea_cpu_u01(w[2 * pair]);
+    double u2 = leea_cpu_u01(w[2 * pair + 1]);
+    double r = sqrt(-2.0 * log(u1));
+    const double two_pi = 6.283185307179586476925286766559;
+    return (i & 1u) ? r * sin(two_pi * u2) : r * cos(two_pi * u2);
+}
+
+/* Uniform index in [0, m): floor(u * m / 2^32), multiply-shift without
+ * rejection. */
+uint32_t leea_cpu_index(uint32_t u, uint32_t m)
+{
+    return (uint32_t)(((uint64_t)u * (uint64_t)m) >> 32);
+}
+
+/* A draw u "hits" with probability q iff u < threshold(q). */
+uint64_t leea_cpu_threshold(double q)
+{
+    if (!(q > 0.0)) return 0;
+    if (q >= 1.0) return (uint64_t)1 << 32;
+    return (uint64_t)floor(q * 4294967296.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Layout and operator counts                                               */
+/* ------------------------------------------------------------------------ */
+
+/* c = sum over layers of (out * in + out)  (Section 3.2, theta in R^c). */
+int64_t leea_cpu_num_params(const int32_t* dims, int32_t n_dims)
+{
+    if (!dims || n_dims < 2) return -1;
+    int64_t c = 0;
+    for (int l = 0; l + 1 < n_dims; l++) {
+        if (dims[l] <= 0 || dims[l + 1] <= 0) return -1;
+        c += (int64_t)dims[l + 1] * dims[l] + dims[l + 1];
+    }
+    return c;
+}
+
+/* Offspring counts of Algorithm 1: p_E*lambda elites, p_C*lambda crossover
+ * children, the remaining p_M*lambda mutation children; parents come from the
+ * top rho*lambda (Section 3.1).  Rounding: n_E and n_C by round(), n_M takes
+ * the rest, the pool is max(1, floor(rho*lambda)). */
+int leea_cpu_counts(int32_t pop, const leea_cpu_params* prm, int32_t* n_e,
+                    int32_t* n_c, int32_t* n_m, int32_t* pool)
+{
+    if (pop <= 0 || !prm) return LEEA_CPU_EINVAL;
+    int32_t e = prm->n_elite >= 0 ? prm->n_elite
+                                  : (int32_t)round((double)prm->p_e * (double)pop);
+    if (e > pop) e = pop;
+    if (e < 0) e = 0;
+    int32_t cc = (int32_t)round((double)prm->p_c * (double)pop);
+    if (cc > pop - e) cc = pop - e;
+    if (cc < 0) cc = 0;
+    int32_t pl = (int32_t)floor((double)prm->rho * (double)pop);
+    if (pl < 1) pl = 1;
+    if (pl > pop) pl = pop;
+    if (n_e) *n_e = e;
+    if (n_c) *n_c = cc;
+    if (n_m) *n_m = pop - e - cc;
+    if (pool) *pool = pl;
+    return LEEA_CPU_OK;
+}
+
+static int valid_params(const leea_cpu_params* prm)
+{
+    if (!prm) return 0;
+    if (prm->xo_op != 0 && prm->xo_op != 1) return 0;
+    if (prm->sel_op != 0 && prm->sel_op != 1) return 0;
+    if (!(prm->xo_gene_p >= 0.0f && prm->xo_gene_p <= 1.0f)) return 0;
+    if (!(prm->rho > 0.0f && prm->rho <= 1.0f)) return 0;
+    if (prm->sel_op == 1 && prm->tour_k < 1) return 0;
+    if (!(prm->p_e >= 0.0f && prm->p_e <= 1.0f)) return 0;
+    if (!(prm->p_c >= 0.0f && prm->p_c <= 1.0f)) return 0;
+    if (!(prm->sigma >= 0.0f) || isinf(prm->sigma)) return 0;
+    if (!(prm->mut_rate >= 0.0f && prm->mut_rate <= 1.0f)) return 0;
+    if (!(prm->alpha >= 0.0f && prm->alpha <= 1.0f)) return 0;
+    if (prm->init != 0 && prm->init != 1) return 0;
+    if (prm->precision < 0 || prm->precision > 2) return 0;
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initialisation (Section 4.1: Glorot-uniform; the alternative N(0,1/fan_in)) */
+/* ------------------------------------------------------------------------ */
+int leea_cpu_init(int32_t pop, const int32_t* dims, int32_t n_dims, int32_t init,
+                  uint64_t seed, double* pop_out)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || pop <= 0 || !pop_out || (init != 0 && init != 1)) return LEEA_CPU_EINVAL;
+    for (int32_t p = 0; p < pop; p++) {
+        double* theta = pop_out + (int64_t)p * c;
+        int64_t i = 0;
+        for (int l = 0; l + 1 < n_dims; l++) {
+            int32_t fan_in = dims[l], fan_out = dims[l + 1];
+            int64_t nw = (int64_t)fan_out * fan_in;
+            for (int64_t k = 0; k < nw; k++, i++) {
+                if (init == 0) {
+                    double z = leea_cpu_normal(seed, LEEA_CPU_TAG_INIT, 0, (uint32_t)p, (uint32_t)i);
+                    theta[i] = z * sqrt(1.0 / (double)fan_in);
+                } else {
+                    double a = sqrt(6.0 / (double)(fan_in + fan_out));
+                    double u = leea_cpu_u01(leea_cpu_draw(seed, LEEA_CPU_TAG_INIT, 0, (uint32_t)p, (uint32_t)i));
+                    theta[i] = a * (2.0 * u - 1.0);
+                }
+            }
+            for (int32_t k = 0; k < fan_out; k++, i++) theta[i] = 0.0; /* biases */
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Fitness (Eq. 1): negative mean cross-entropy of the softmax output over   */
+/* the batch; hidden layers use ReLU (Section 4.1).  Also counts correct    */
+/* argmax predictions, ties to the lowest class.                            */
+/* ------------------------------------------------------------------------ */
+int leea_cpu_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
+                      const double* popv, const double* x, const int32_t* y,
+                      int32_t batch, double* f_out, int32_t* correct_out,
+                      double* logits_out)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || pop <= 0 || batch <= 0 || !popv || !x || !y || !f_out) return LEEA_CPU_EINVAL;
+    int32_t d_out = dims[n_dims - 1];
+    for (int32_t b = 0; b < batch; b++)
+        if (y[b] < 0 || y[b] >= d_out) return LEEA_CPU_EINVAL;
+    int32_t widest = 0;
+    for (int l = 0; l < n_dims; l++) if (dims[l] > widest) widest = dims[l];
+    double* a = (double*)malloc(sizeof(double) * (size_t)widest);
+    double* z = (double*)malloc(sizeof(double) * (size_t)widest);
+    if (!a || !z) { free(a); free(z); return LEEA_CPU_ENOMEM; }
+
+    for (int32_t p = 0; p < pop; p++) {
+        const double* theta = popv + (int64_t)p * c;
+        double loss_sum = 0.0;
+        int32_t correct = 0;
+        for (int32_t b = 0; b < batch; b++) {
+            for (int32_t k = 0; k < dims[0]; k++) a[k] = x[(int64_t)b * dims[0] + k];
+            const double* w = theta;
+            for (int l = 0; l + 1 < n_dims; l++) {
+                int32_t n_in = dims[l], n_out = dims[l + 1];
+                const double* bias = w + (int64_t)n_out * n_in;
+                for (int32_t o = 0; o < n_out; o++) {
+                    double acc = 0.0;
+                    for (int32_t k = 0; k < n_in; k++) acc += w[(int64_t)o * n_in + k] * a[k];
+                    acc += bias[o];
+                    int last = (l + 2 == n_dims);
+                    z[o] = (!last && acc < 0.0) ? 0.0 : acc; /* ReLU on hidden layers */
+                }
+                memcpy(a, z, sizeof(double) * (size_t)n_out);
+                w = bias + n_out;
+            }
+            /* a[0..d_out) are the logits.  Cross-entropy against the one-hot
+             * label: log(sum_j exp(z_j)) - z_y, with the maximum subtracted. */
+            double zmax = a[0];
+            int32_t arg = 0;
+            for (int32_t j = 1; j < d_out; j++)
+                if (a[j] > zmax) { zmax = a[j]; arg = j; }
+            double s = 0.0;
+            for (int32_t j = 0; j < d_out; j++) s += exp(a[j] - zmax);
+            double loss = log(s) + zmax - a[y[b]];
+            loss_sum += loss;
+            if (arg == y[b]) correct++;
+            if (logits_out)
+                memcpy(logits_out + ((int64_t)p * batch + b) * d_out, a, sizeof(double) * (size_t)d_out);
+        }
+        f_out[p] = -loss_sum / (double)batch;
+        if (correct_out) correct_out[p] = correct;
+    }
+    free(a);
+    free(z);
+    return LEEA_CPU_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sort by fitness, descending (Algorithm 1).  NaN ranks as -infinity; ties  */
+/* go to the lower index (a stable sort).                                   */
+/* ------------------------------------------------------------------------ */
+typedef struct { double f; int32_t idx; } rank_item;
+
+static int rank_cmp(const void* pa, const void* pb)
+{
+    const rank_item* a = (const rank_item*)pa;
+    const rank_item* b = (const rank_item*)pb;
+    double fa = isnan(a->f) ? -INFINITY : a->f;
+    double fb = isnan(b->f) ? -INFINITY : b->f;
+    if (fa > fb) return -1;
+    if (fa < fb) return 1;
+    return (a->idx < b->idx) ? -1 : (a->idx > b->idx);
+}
+
+int leea_cpu_rank(int32_t pop, const double* f_adj, int32_t* order)
+{
+    if (pop <= 0 || !f_adj || !order) return LEEA_CPU_EINVAL;
+    rank_item* items = (rank_item*)malloc(sizeof(rank_item) * (size_t)pop);
+    if (!items) return LEEA_CPU_ENOMEM;
+    for (int32_t i = 0; i < pop; i++) { items[i].f = f_adj[i]; items[i].idx = i; }
+    qsort(items, (size_t)pop, sizeof(rank_item), rank_cmp);
+    for (int32_t r = 0; r < pop; r++) order[r] = items[r].idx;
+    free(items);
+    return LEEA_CPU_OK;
+}
+
+/* Does individual a beat individual b? Higher fitness wins, NaN counts as
+ * -infinity, equal fitness goes to the lower index. */
+static int beats(const double* f_adj, int32_t a, int32_t b)
+{
+    rank_item ia = { f_adj[a], a }, ib = { f_adj[b], b };
+    return rank_cmp(&ia, &ib) < 0;
+}
+
+/* One parent for child j, from draws [first, first + k) of its SEL stream.
+ * Truncation (Section 3.1): uniform over the top `pool` of the ranking.
+ * Tournament: best of k uniform draws (with replacement) over everybody. */
+static int32_t pick_parent(int32_t pop, const leea_cpu_params* prm, const double* f_adj,
+                           const int32_t* order, int32_t pool, uint64_t seed, uint32_t gen,
+                           uint32_t j, uint32_t first)
+{
+    if (prm->sel_op == 0) {
+        uint32_t u = leea_cpu_draw(seed, LEEA_CPU_TAG_SEL, gen, j, first);
+        return order[leea_cpu_index(u, (uint32_t)pool)];
+    }
+    int32_t best = -1;
+    for (int32_t t = 0; t < prm->tour_k; t++) {
+        uint32_t u = leea_cpu_draw(seed, LEEA_CPU_TAG_SEL, gen, j, first + (uint32_t)t);
+        int32_t cand = (int32_t)leea_cpu_index(u, (uint32_t)pop);
+        if (best < 0 || beats(f_adj, cand, best)) best = cand;
+    }
+    return best;
+}
+
+/* Elites, crossover pairs and mutation parents of Algorithm 1, in that child
+ * order, and the inherited fitness of each child (Section 3.1):
+ * f_inh = (f1 + f2) / 2 after crossover, f3 after mutation; an elite keeps
+ * its own adjusted fitness. */
+int leea_cpu_select(int32_t pop, const leea_cpu_params* prm, const double* f_adj,
+                    const int32_t* order, uint64_t seed, uint32_t gen,
+                    int32_t* par1, int32_t* par2, int32_t* kind, double* f_inh)
+{
+    if (pop <= 0 || !valid_params(prm) || !f_adj || !order || !par1 || !par2 || !kind || !f_inh)
+        return LEEA_CPU_EINVAL;
+    int32_t n_e, n_c, n_m, pool;
+    leea_cpu_counts(pop, prm, &n_e, &n_c, &n_m, &pool);
+    uint32_t k_draws = (prm->sel_op == 0) ? 1u : (uint32_t)prm->tour_k;
+    for (int32_t j = 0; j < pop; j++) {
+        if (j < n_e) {
+            kind[j] = LEEA_CPU_ELITE;
+            par1[j] = par2[j] = order[j];
+            f_inh[j] = f_adj[order[j]];
+        } else if (j < n_e + n_c) {
+            kind[j] = LEEA_CPU_CROSSOVER;
+            par1[j] = pick_parent(pop, prm, f_adj, order, pool, seed, gen, (uint32_t)j, 0);
+            par2[j] = pick_parent(pop, prm, f_adj, order, pool, seed, gen, (uint32_t)j, k_draws);
+            f_inh[j] = 0.5 * (f_adj[par1[j]] + f_adj[par2[j]]);
+        } else {
+            kind[j] = LEEA_CPU_MUTATION;
+            par1[j] = pick_parent(pop, prm, f_adj, order, pool, seed, gen, (uint32_t)j, 0);
+            par2[j] = par1[j];
+            f_inh[j] = f_adj[par1[j]];
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Crossover and mutation (Section 3.2), children j0 <= j < j1.              */
+/*   uniform:     gene i from parent 2 iff its XO draw hits xo_gene_p        */
+/*   arithmetic:  (theta_1 + theta_2) / 2                                    */
+/*   mutation:    theta_1 + sigma * N(0,1) on genes whose MUTMASK draw hits  */
+/*                mut_rate (every gene when mut_rate = 1)                    */
+/*   elite:       unchanged copy                                             */
+/* ------------------------------------------------------------------------ */
+int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
+                   const leea_cpu_params* prm, uint64_t seed, uint32_t gen,
+                   const double* parents, const int32_t* par1, const int32_t* par2,
+                   const int32_t* kind, int32_t j0, int32_t j1, double* children)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || pop <= 0 || !valid_params(prm) || !parents || !par1 || !par2 || !kind ||
+        !children || j0 < 0 || j1 > pop || j0 > j1)
+        return LEEA_CPU_EINVAL;
+    uint64_t thr_xo = leea_cpu_threshold((double)prm->xo_gene_p);
+    uint64_t thr_mut = leea_cpu_threshold((double)prm->mut_rate);
+    double sigma = (double)prm->sigma;
+    for (int32_t j = j0; j < j1; j++) {
+        if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
+        const double* a = parents + (int64_t)par1[j] * c;
+        const double* b = parents + (int64_t)par2[j] * c;
+        double* out = children + (int64_t)(j - j0) * c;
+        for (int64_t i = 0; i < c; i++) {
+            double v;
+            if (kind[j] == LEEA_CPU_ELITE) {
+                v = a[i];
+            } else if (kind[j] == LEEA_CPU_CROSSOVER) {
+                if (prm->xo_op == 0) {
+                    uint32_t u = leea_cpu_draw(seed, LEEA_CPU_TAG_XO, gen, (uint32_t)j, (uint32_t)i);
+                    v = ((uint64_t)u < thr_xo) ? b[i] : a[i];
+                } else {
+                    v = 0.5 * (a[i] + b[i]);
+                }
+            } else if (kind[j] == LEEA_CPU_MUTATION) {
+                uint32_t u = leea_cpu_draw(seed, LEEA_CPU_TAG_MUTMASK, gen, (uint32_t)j, (uint32_t)i);
+                if ((uint64_t)u < thr_mut)
+                    v = a[i] + sigma * leea_cpu_normal(seed, LEEA_CPU_TAG_NORMAL, gen, (uint32_t)j, (uint32_t)i);
+                else
+                    v = a[i];
+            } else {
+                return LEEA_CPU_EINVAL;
+            }
+            out[i] = v;
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
+/* Fitness inheritance (Section 3.1): f_adj = (1 - alpha) f_inh + alpha f.
+ * The first evaluation has nothing to inherit: f_adj = f. */
+int leea_cpu_inherit(int32_t pop, double alpha, const double* f_inh, const double* f,
+                     int32_t first, double* f_adj)
+{
+    if (pop <= 0 || !f || !f_adj || (!first && !f_inh)) return LEEA_CPU_EINVAL;
+    for (int32_t p = 0; p < pop; p++)
+        f_adj[p] = first ? f[p] : (1.0 - alpha) * f_inh[p] + alpha * f[p];
+    return LEEA_CPU_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 1 as a state object.  The first generation call evaluates the  */
+/* freshly initialised population; every later call sorts, selects, breeds  */
+/* with generation counter g = 1, 2, ... and evaluates the new population.  */
+/* ------------------------------------------------------------------------ */
+struct leea_cpu_state {
+    int32_t pop, n_dims;
+    int32_t dims[16];
+    int64_t c;
+    leea_cpu_params prm;
+    uint64_t seed;
+    uint32_t gen;
+    int32_t evaluated;
+    double *cur, *next;
+    double *f_adj, *f_raw, *f_inh;
+    int32_t *correct, *order, *par1, *par2, *kind;
+};
+
+void leea_cpu_destroy(leea_cpu_state* s)
+{
+    if (!s) return;
+    free(s->cur); free(s->next);
+    free(s->f_adj); free(s->f_raw); free(s->f_inh);
+    free(s->correct); free(s->order); free(s->par1); free(s->par2); free(s->kind);
+    free(s);
+}
+
+int leea_cpu_create(int32_t pop, const int32_t* dims, int32_t n_dims,
+                    const leea_cpu_params* prm, uint64_t seed, leea_cpu_state** out)
+{
+    if (!out) return LEEA_CPU_EINVAL;
+    *out = NULL;
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || n_dims > 16 || pop <= 0 || !valid_params(prm)) return LEEA_CPU_EINVAL;
+    leea_cpu_state* s = (leea_cpu_state*)calloc(1, sizeof(*s));
+    if (!s) return LEEA_CPU_ENOMEM;
+    s->pop = pop; s->n_dims = n_dims; s->c = c; s->prm = *prm; s->seed = seed;
+    memcpy(s->dims, dims, sizeof(int32_t) * (size_t)n_dims);
+    size_t np = (size_t)pop;
+    s->cur = (double*)malloc(sizeof(double) * np * (size_t)c);
+    s->next = (double*)malloc(sizeof(double) * np * (size_t)c);
+    s->f_adj = (double*)calloc(np, sizeof(double));
+    s->f_raw = (double*)calloc(np, sizeof(double));
+    s->f_inh = (double*)calloc(np, sizeof(double));
+    s->correct = (int32_t*)calloc(np, sizeof(int32_t));
+    s->order = (int32_t*)calloc(np, sizeof(int32_t));
+    s->par1 = (int32_t*)calloc(np, sizeof(int32_t));
+    s->par2 = (int32_t*)calloc(np, sizeof(int32_t));
+    s->kind = (int32_t*)calloc(np, sizeof(int32_t));
+    if (!s->cur || !s->next || !s->f_adj || !s->f_raw || !s->f_inh || !s->correct ||
+        !s->order || !s->par1 || !s->par2 || !s->kind) {
+        leea_cpu_destroy(s);
+        return LEEA_CPU_ENOMEM;
+    }
+    leea_cpu_init(pop, dims, n_dims, prm->init, seed, s->cur);
+    *out = s;
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_generation(leea_cpu_state* s, const double* x, const int32_t* y, int32_t batch)
+{
+    if (!s || !x || !y || batch <= 0) return LEEA_CPU_EINVAL;
+    int rc;
+    int first = !s->evaluated;
+    if (!first) {
+        uint32_t g = s->gen + 1;
+        rc = leea_cpu_rank(s->pop, s->f_adj, s->order);
+        if (rc) return rc;
+        rc = leea_cpu_select(s->pop, &s->prm, s->f_adj, s->order, s->seed, g,
+                             s->par1, s->par2, s->kind, s->f_inh);
+        if (rc) return rc;
+        rc = leea_cpu_breed(s->pop, s->dims, s->n_dims, &s->prm, s->seed, g, s->cur,
+                            s->par1, s->par2, s->kind, 0, s->pop, s->next);
+        if (rc) return rc;
+        double* t = s->cur; s->cur = s->next; s->next = t;
+        s->gen = g;
+    }
+    rc = leea_cpu_evaluate(s->pop, s->dims, s->n_dims, s->cur, x, y, batch,
+                           s->f_raw, s->correct, NULL);
+    if (rc) return rc;
+    rc = leea_cpu_inherit(s->pop, (double)s->prm.alpha, s->f_inh, s->f_raw, first, s->f_adj);
+    if (rc) return rc;
+    s->evaluated = 1;
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_fitness(const leea_cpu_state* s, double* f_adj, double* f_raw, int32_t* correct)
+{
+    if (!s) return LEEA_CPU_EINVAL;
+    if (!s->evaluated) return LEEA_CPU_ESTATE;
+    size_t np = (size_t)s->pop;
+    if (f_adj) memcpy(f_adj, s->f_adj, sizeof(double) * np);
+    if (f_raw) memcpy(f_raw, s->f_raw, sizeof(double) * np);
+    if (correct) memcpy(correct, s->correct, sizeof(int32_t) * np);
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_best_params(const leea_cpu_state* s, double* out, int64_t c)
+{
+    if (!s || !out || c != s->c) return LEEA_CPU_EINVAL;
+    if (!s->evaluated) return LEEA_CPU_ESTATE;
+    int32_t best = 0;
+    for (int32_t p = 1; p < s->pop; p++)
+        if (beats(s->f_adj, p, best)) best = p;
+    memcpy(out, s->cur + (int64_t)best * s->c, sizeof(double) * (size_t)s->c);
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_get_population(const leea_cpu_state* s, double* out)
+{
+    if (!s || !out) return LEEA_CPU_EINVAL;
+    memcpy(out, s->cur, sizeof(double) * (size_t)s->pop * (size_t)s->c);
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_set_population(leea_cpu_state* s, const double* in)
+{
+    if (!s || !in) return LEEA_CPU_EINVAL;
+    memcpy(s->cur, in, sizeof(double) * (size_t)s->pop * (size_t)s->c);
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_set_fitness(leea_cpu_state* s, const double* f_adj)
+{
+    if (!s || !f_adj) return LEEA_CPU_EINVAL;
+    memcpy(s->f_adj, f_adj, sizeof(double) * (size_t)s->pop);
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_set_generation(leea_cpu_state* s, uint32_t gen, int32_t evaluated)
+{
+    if (!s) return LEEA_CPU_EINVAL;
+    s->gen = gen;
+    s->evaluated = evaluated ? 1 : 0;
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_get_selection(const leea_cpu_state* s, int32_t* order, int32_t* par1,
+                           int32_t* par2, int32_t* kind, double* f_inh)
+{
+    if (!s) return LEEA_CPU_EINVAL;
+    size_t np = (size_t)s->pop;
+    if (order) memcpy(order, s->order, sizeof(int32_t) * np);
+    if (par1) memcpy(par1, s->par1, sizeof(int32_t) * np);
+    if (par2) memcpy(par2, s->par2, sizeof(int32_t) * np);
+    if (kind) memcpy(kind, s->kind, sizeof(int32_t) * np);
+    if (f_inh) memcpy(f_inh, s->f_inh, sizeof(double) * np);
+    return LEEA_CPU_OK;
+}
+
+uint32_t leea_cpu_generation_index(const leea_cpu_state* s)
+{
+    return s ? s->gen : 0;
+}

@@ -1,0 +1,118 @@
+/*
+ * leea_oracle.h -- FP64 CPU oracle of the LEEA hot path (Prellberg & Kramer,
+ * "Limited Evaluation Evolutionary Optimization of Large Neural Networks").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or helper with the CUDA library; the two meet only through
+ * seeded inputs and the published definitions they both restate.
+ *
+ * Everything here is plain, slow, single-threaded C in double precision.
+ * Each function names the passage of the paper it follows.
+ *
+ * Population layout on this side: pop[p * c + i], with the logical gene order
+ * of a fully connected net dims[0]-dims[1]-...-dims[n-1]: for each layer l,
+ * first W_l (dims[l+1] rows x dims[l] columns, row-major) then b_l.
+ * (Section 3.2: the direct encoding theta in R^c.)
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
+ * the 64-bit seed, with the counter (n >> 2, entity, generation, tag); scalar
+ * draw n of a stream is word (n & 3) of that block.
+ */
+#ifndef LEEA_ORACLE_H
+#define LEEA_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LEEA_CPU_OK = 0,
+    LEEA_CPU_EINVAL = 1,
+    LEEA_CPU_ENOMEM = 2,
+    LEEA_CPU_ESTATE = 4
+};
+
+/* Philox stream tags (counter word 3). */
+enum {
+    LEEA_CPU_TAG_INIT = 1,    /* entity = individual, n = gene              */
+    LEEA_CPU_TAG_SEL = 2,     /* entity = child, n = draw index             */
+    LEEA_CPU_TAG_XO = 3,      /* entity = child, n = gene                   */
+    LEEA_CPU_TAG_MUTMASK = 4, /* entity = child, n = gene                   */
+    LEEA_CPU_TAG_NORMAL = 5   /* entity = child, n = gene                   */
+};
+
+/* How a child of the next generation is made (Algorithm 1). */
+enum { LEEA_CPU_ELITE = 0, LEEA_CPU_CROSSOVER = 1, LEEA_CPU_MUTATION = 2 };
+
+/* Operator parameters.  Same meaning as the CUDA library's leea_params, but a
+ * separate declaration: the oracle includes nothing from the product. */
+typedef struct {
+    int32_t xo_op;     /* 0 uniform, 1 arithmetic crossover (Section 3.2)      */
+    float xo_gene_p;   /* P(gene taken from parent 2), uniform crossover       */
+    int32_t sel_op;    /* 0 truncation (Section 3.1), 1 tournament             */
+    float rho;         /* truncation proportion                                */
+    int32_t tour_k;    /* tournament size                                      */
+    int32_t n_elite;   /* >= 0 explicit count; -1 => round(p_e * pop)          */
+    float p_e;         /* elite proportion                                     */
+    float p_c;         /* crossover proportion; mutation takes the rest        */
+    float sigma;       /* mutation strength (constant control)                 */
+    float mut_rate;    /* per-gene mutation probability (1 = every gene)       */
+    float alpha;       /* inheritance weight on the fresh evaluation           */
+    int32_t init;      /* 0 N(0, 1/fan_in), 1 Glorot-uniform (Section 4.1)     */
+    int32_t precision; /* 0 FP32, 1 BF16 shadow, 2 FP8-e4m3 shadow             */
+} leea_cpu_params;
+
+/* ---- random number streams ------------------------------------------- */
+void leea_cpu_philox(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+uint32_t leea_cpu_draw(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t n);
+double leea_cpu_u01(uint32_t u);
+double leea_cpu_normal(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t i);
+uint32_t leea_cpu_index(uint32_t u, uint32_t m);
+uint64_t leea_cpu_threshold(double q);
+
+/* ---- layout and operator counts ----------------------------------------- */
+int64_t leea_cpu_num_params(const int32_t* dims, int32_t n_dims);
+int leea_cpu_counts(int32_t pop, const leea_cpu_params* prm, int32_t* n_e,
+                    int32_t* n_c, int32_t* n_m, int32_t* pool);
+
+/* ---- the steps of one generation (Algorithm 1) --------------------------- */
+int leea_cpu_init(int32_t pop, const int32_t* dims, int32_t n_dims, int32_t init,
+                  uint64_t seed, double* pop_out);
+int leea_cpu_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
+                      const double* popv, const double* x, const int32_t* y,
+                      int32_t batch, double* f_out, int32_t* correct_out,
+                      double* logits_out);
+int leea_cpu_rank(int32_t pop, const double* f_adj, int32_t* order);
+int leea_cpu_select(int32_t pop, const leea_cpu_params* prm, const double* f_adj,
+                    const int32_t* order, uint64_t seed, uint32_t gen,
+                    int32_t* par1, int32_t* par2, int32_t* kind, double* f_inh);
+int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
+                   const leea_cpu_params* prm, uint64_t seed, uint32_t gen,
+                   const double* parents, const int32_t* par1, const int32_t* par2,
+                   const int32_t* kind, int32_t j0, int32_t j1, double* children);
+int leea_cpu_inherit(int32_t pop, double alpha, const double* f_inh, const double* f,
+                     int32_t first, double* f_adj);
+
+/* ---- the whole algorithm as a state object -------------------------------- */
+typedef struct leea_cpu_state leea_cpu_state;
+int leea_cpu_create(int32_t pop, const int32_t* dims, int32_t n_dims,
+                    const leea_cpu_params* prm, uint64_t seed, leea_cpu_state** out);
+int leea_cpu_generation(leea_cpu_state* s, const double* x, const int32_t* y, int32_t batch);
+int leea_cpu_fitness(const leea_cpu_state* s, double* f_adj, double* f_raw, int32_t* correct);
+int leea_cpu_best_params(const leea_cpu_state* s, double* out, int64_t c);
+int leea_cpu_get_population(const leea_cpu_state* s, double* out);
+int leea_cpu_set_population(leea_cpu_state* s, const double* in);
+int leea_cpu_set_fitness(leea_cpu_state* s, const double* f_adj);
+int leea_cpu_set_generation(leea_cpu_state* s, uint32_t gen, int32_t evaluated);
+int leea_cpu_get_selection(const leea_cpu_state* s, int32_t* order, int32_t* par1,
+                           int32_t* par2, int32_t* kind, double* f_inh);
+uint32_t leea_cpu_generation_index(const leea_cpu_state* s);
+void leea_cpu_destroy(leea_cpu_state* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEEA_ORACLE_H */
