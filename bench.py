@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Throughput of the LEEA hot path on GB300: generations/s (and network-samples/s)
+of P = 1000 nets 784-112-10 (89,050 parameters) on batches of 100 synthetic
+MNIST-shaped images, FP32, with the roofline fraction of the dominant kernel.
+
+One step = one generation of Algorithm 1 through the C ABI (rank, select,
+breed, evaluate).  The population (2 x 356 MB) is larger than L2, so no flush
+is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 (under torch.distributed.run) runs N independent replicas, one per GPU
+(the generation's selection needs every parent, so a run does not shard);
+the value is all replicas' generations over the slowest replica's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "generations/sec and network·samples/sec at P=1000, 89k MLP; % of roofline"
+POP, DIMS, BATCH = 1000, [784, 112, 10], 100
+PARAMS = dict(xo_op=0, xo_gene_p=0.5, sel_op=0, rho=0.5, n_elite=1, p_c=0.5, sigma=0.005, mut_rate=0.1,
+              alpha=1.0, init=0)
+WORKLOAD = ("P=1000 MLPs 784-112-10 (89,050 params, FP32), batch 100 synthetic 28x28 images; uniform crossover "
+            "p_C=0.5, truncation rho=0.5, elitism 1, mutation sigma=0.005 on 10% of genes, alpha=1")
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
+STAGES = ("rank", "select", "breed", "evaluate")
+
+# DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum), valid only while the kernel source is unchanged.
+TRAFFIC = {}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), float(m.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL)), "measured"
+    except Exception:
+        return 6800.0, SM_MAX_MHZ_NOMINAL, "fallback"
+
+
+def _src_sha(name: str) -> str:
+    p = os.path.join(ROOT, "paper_1806_09819_gb300", "csrc", name)
+    with open(p, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# --------------------------------------------------------------------------------
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world: int, use_cuda: bool):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend="nccl" if use_cuda else "gloo")
+    return dist
+
+
+def max_over_ranks(value: float, dist, device=None) -> float:
+    """Max of a host float over all ranks (identity without a process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(dist, device=None):
+    if dist is None:
+        return
+    import torch
+    t = torch.zeros(1, device=device)
+    dist.all_reduce(t)
+
+
+# --------------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0:
+            time.sleep(0.02)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def mark(self):
+        return len(self.lines)
+
+    def stop(self, since: int = 0):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [l.split(",") for l in self.lines[max(0, since - 1):] if l.count(",") >= 6]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                smax.append(float(r[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _gpu_id_for(dev: int) -> str | None:
+    try:
+        import torch
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        return uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# --------------------------------------------------------------------------------
+def oracle_step_sample(parents64, f_adj64, x64, y, n_children: int, gen: int, seed: int = 0) -> float:
+    """Rank + select all P children, then breed and evaluate `n_children` of
+    them (strided over elite, crossover and mutation children); returns the
+    CPU seconds taken."""
+    import numpy as np
+    import oracle
+    prm = oracle.Params(**PARAMS)
+    t0 = time.perf_counter()
+    order = oracle.rank(f_adj64)
+    p1, p2, kind, f_inh = oracle.select(prm, f_adj64, order, seed, gen)
+    rows = np.linspace(0, POP - 1, n_children).round().astype(int)
+    kids = np.concatenate([oracle.breed(prm, DIMS, seed, gen, parents64, p1, p2, kind, j0=int(j), j1=int(j) + 1)
+                           for j in rows])
+    f, _ = oracle.evaluate(kids, DIMS, x64, y)
+    oracle.inherit(float(prm.alpha), f_inh[rows], f, first=False)
+    return time.perf_counter() - t0
+
+
+def oracle_inputs(parents=None, f_adj=None):
+    import numpy as np
+    import oracle
+    from paper_1806_09819_gb300 import synthetic
+    oracle.build()
+    c = oracle.num_params(DIMS)
+    if parents is None:
+        parents = synthetic.random_population(POP, c, seed=1, scale=0.05)
+    if f_adj is None:
+        f_adj = np.random.default_rng(2).normal(-2.3, 0.05, size=POP).astype(np.float32)
+    x, y = synthetic.make_split(BATCH, seed=4)
+    return parents.astype(np.float64), f_adj.astype(np.float64), x.astype(np.float64), y
+
+
+def cpu_baseline(parents=None, f_adj=None, n_children: int = 1000):
+    args = oracle_inputs(parents, f_adj)
+    secs = oracle_step_sample(*args, n_children=n_children, gen=1)
+    gen_per_s = (n_children / POP) / secs
+    return {"value": gen_per_s, "unit": "generations/s", "cores": 1, "kind": "oracle",
+            "sample": f"one generation's rank+select over all {POP} nets, breed+evaluate of {n_children} of the "
+                      f"{POP} children (strided), batch {BATCH}; value = ({n_children}/{POP}) / seconds",
+            "seconds": secs, "network_samples_per_sec": gen_per_s * POP * BATCH}
+
+
+# --------------------------------------------------------------------------------
+# arms
+# --------------------------------------------------------------------------------
+def run_reference(args, rank: int, world: int):
+    """The oracle as the reference arm: each step a bounded sample of one generation."""
+    if rank != 0:
+        return
+    inputs = oracle_inputs()
+    per_step_budget = 60.0 / max(1, args.steps + args.warmup)
+    probe = oracle_step_sample(*inputs, n_children=2, gen=1) / 2.0
+    n_children = int(max(1, min(POP, round(per_step_budget / max(probe, 1e-6)))))
+    for w in range(args.warmup):
+        oracle_step_sample(*inputs, n_children=n_children, gen=2 + w)
+    total = 0.0
+    for k in range(args.steps):
+        total += oracle_step_sample(*inputs, n_children=n_children, gen=100 + k)
+    gen_per_s = args.steps * (n_children / POP) / total
+    sample = (f"per step: rank+select of {POP} nets, breed+evaluate of {n_children} of {POP} children, "
+              f"batch {BATCH}; value = steps*({n_children}/{POP}) / seconds")
+    line = {"impl": "reference", "metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * POP / n_children * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "host CPU run"},
+            "cpu_baseline": {"value": gen_per_s, "unit": "generations/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": gen_per_s, "unit": "generations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "network_samples_per_sec": gen_per_s * POP * BATCH}
+    print(json.dumps(line), flush=True)
+
+
+def run_native(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+    from paper_1806_09819_gb300 import build as B
+    from paper_1806_09819_gb300 import leea, synthetic
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = dist_init(world, True)
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(dist, dev)
+    B.build()
+    leea.load_library()
+
+    steps, warmup = args.steps, args.warmup
+    (xtr, ytr), _ = synthetic.dataset(n_train=60000, n_test=1)
+    n_batches = warmup + 1 + steps
+    idx = synthetic.batch_indices(len(ytr), BATCH, n_batches, seed=synthetic.BATCH_SEED + rank)
+    xs = torch.from_numpy(xtr[idx]).to(dev)       # [n_batches, B, 784], resident in HBM
+    ys = torch.from_numpy(ytr[idx]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    st = leea.LeeaState(POP, DIMS, leea.Params(**PARAMS), seed=1000 + rank, stream=stream)
+    for k in range(warmup + 1):  # the first call evaluates the initial population
+        st.leea_generation(xs[k], ys[k])
+    torch.cuda.synchronize(dev)
+    st.leea_profile_enable(True)
+    st.leea_profile_read()
+
+    clocks = ClockSampler(_gpu_id_for(local_rank))
+    clocks.start()
+    # ---- timed region: K generations, inputs resident in HBM ----
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    mark = clocks.mark()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(steps):
+        st.leea_generation(xs[warmup + 1 + k], ys[warmup + 1 + k])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist, dev)
+    clk = clocks.stop(mark)
+    ms = ev0.elapsed_time(ev1)
+    prof = st.leea_profile_read()
+    st.leea_profile_enable(False)
+    ms_max = max_over_ranks(ms, dist, dev)
+    gen_per_s = world * steps / (ms_max / 1000.0)
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e_steps = max(10, min(steps, 1000))
+    sel = idx[np.arange(e2e_steps) % n_batches]
+    xh = torch.from_numpy(xtr[sel]).pin_memory()
+    yh = torch.from_numpy(ytr[sel]).pin_memory()
+    f_host = None
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        st.leea_generation_host(xh[k], yh[k])
+        f_host = st.leea_fitness()                    # device->host read of the step's result
+    t_e2e = time.perf_counter() - t0
+    barrier(dist, dev)
+    t_e2e = max_over_ranks(t_e2e, dist, dev)
+    e2e = {"value": world * e2e_steps / t_e2e, "unit": "generations/s",
+           "h2d_bytes_per_step": int(xh[0].numel() * 4 + yh[0].numel() * 4),
+           "d2h_bytes_per_step": int(f_host.nbytes), "steps": e2e_steps}
+
+    # ---- roofline of the dominant kernel ----
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    n_e, n_c, n_m, _ = leea.leea_counts(POP, leea.Params(**PARAMS))
+    c = leea.leea_num_params(DIMS)
+    d0, h, d_out = DIMS
+    work = {
+        "breed": ("hbm", 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) / 1e9, "GB/s", hbm_peak),
+        "evaluate": ("alu", 2.0 * POP * BATCH * (d0 * h + h * d_out) / 1e12, "TFLOP/s",
+                     SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12),
+        "rank": ("latency", None, None, None),
+        "select": ("latency", None, None, None),
+    }
+    kernels = {}
+    for name in STAGES:
+        tot_ms, launches = prof[name]
+        per = tot_ms / max(1, launches)
+        bound, units, unit, peak = work[name]
+        entry = {"launches": launches, "ms_per_launch": per, "share": tot_ms / max(1e-12, sum(v[0] for v in prof.values()))}
+        if units is not None:
+            ach = units / (per / 1000.0)
+            entry.update({"bound": bound, "achieved": ach, "unit": unit, "peak": peak, "frac": ach / peak})
+        kernels[name] = entry
+    dom = max(("breed", "evaluate"), key=lambda n: prof[n][0])
+    kd = kernels[dom]
+    src = {"breed": "leea_breed.cu", "evaluate": "leea_eval_simt.cu"}[dom]
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == _src_sha(src) else None
+    roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
+                "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
+                "peak_source": f"{peak_src} ({'HBM copy' if kd['unit'] == 'GB/s' else 'FP32 FFMA: 152 SM x 128 lanes x 2 x max SM clock'})"}
+
+    line = {"metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps,
+            "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (2 population buffers of 356 MB), no flush"},
+            "network_samples_per_sec": gen_per_s * POP * BATCH,
+            "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())), "roofline": roofline,
+            "kernels": kernels, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pop_now = st.leea_get_population()
+        f_now = st.leea_fitness()
+        line["cpu_baseline"] = cpu_baseline(pop_now, f_now, n_children=args.cpu_children)
+    st.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-children", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local_rank = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_native(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

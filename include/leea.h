@@ -1,0 +1,273 @@
+/*
+ * leea.h -- C ABI of the GB300 (sm_103a) LEEA library.
+ *
+ * The limited-evaluation evolutionary algorithm of Prellberg & Kramer,
+ * "Limited Evaluation Evolutionary Optimization of Large Neural Networks"
+ * (Algorithm 1, Sections 3.1-3.3): a population of `pop` directly encoded
+ * fully connected nets is evaluated on one shared minibatch, then ranked,
+ * selected, crossed over and mutated into the next generation, all on the GPU.
+ *
+ * Conventions for every entry point
+ *  - Plain C types only.  Pointers named *_dev are CUDA device pointers, *_host
+ *    are host pointers.  `stream` is a cudaStream_t passed as void* (NULL means
+ *    the legacy default stream).
+ *  - Every call returns a leea_status and never aborts; on failure
+ *    leea_last_error() returns a message (thread-local, valid until the next
+ *    failing call on the same thread).  Argument errors are reported before
+ *    any work is enqueued.
+ *  - Calls that take a stream only ENQUEUE work on it and return; inputs must
+ *    stay valid and outputs untouched until the stream has reached the end of
+ *    that work.  Calls that return host data synchronise the stream first.
+ *  - Caller-owned buffers stay caller-owned; the library never frees them.
+ *
+ * Net and population layout (Section 3.2, direct encoding theta in R^c)
+ *  - dims = {d_0, d_1, ..., d_L}: layer l maps d_l inputs to d_{l+1} outputs;
+ *    every layer but the last is followed by ReLU, the last by softmax
+ *    (Section 4.1).  The evaluation kernels take L = 2 (d_0-h-d_out, d_out <=
+ *    32); initialisation and breeding take any 1 <= L <= 15.
+ *  - Genes of one individual in logical order: for each layer, W_l as d_{l+1}
+ *    rows of d_l floats (row-major, out x in), then b_l (d_{l+1} floats).
+ *    c = sum_l (d_{l+1} d_l + d_{l+1}).
+ *  - On the device an individual occupies c_pad = round_up(c, 32) floats so
+ *    that each one starts 128-byte aligned: individual p starts at
+ *    pop_dev + p * c_pad; genes c..c_pad-1 are zero.  Host copies made by
+ *    leea_get_population / leea_best_params use the unpadded logical layout.
+ *  - Minibatch: x is float[batch][d_0] row-major, y is int32[batch] with
+ *    labels in [0, d_out).  A label outside that range makes the fitness of
+ *    every individual NaN for that batch.
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with key
+ * (seed & 0xffffffff, seed >> 32) and counter (n >> 2, entity, generation, tag);
+ * draw n of a stream is word n & 3 of that block.  Because the generator is
+ * counter-based, a run is reproducible from (seed, generation) alone.
+ */
+#ifndef LEEA_H
+#define LEEA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The library is built with hidden visibility; everything declared here is
+ * exported. */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
+typedef enum {
+    LEEA_OK = 0,
+    LEEA_EINVAL = 1,   /* invalid argument                                   */
+    LEEA_ENOMEM = 2,   /* device or host allocation failed                   */
+    LEEA_ECUDA = 3,    /* a CUDA call or kernel launch failed                */
+    LEEA_ESTATE = 4,   /* call not valid in the object's current state       */
+    LEEA_ETIMEOUT = 5  /* a bounded device wait gave up                      */
+} leea_status;
+
+/* Philox stream tags (counter word 3). */
+enum {
+    LEEA_TAG_INIT = 1,     /* entity = individual, n = gene index           */
+    LEEA_TAG_SEL = 2,      /* entity = child, n = selection draw            */
+    LEEA_TAG_XO = 3,       /* entity = child, n = gene index                */
+    LEEA_TAG_MUTMASK = 4,  /* entity = child, n = gene index                */
+    LEEA_TAG_NORMAL = 5    /* entity = child, n = gene index                */
+};
+
+/* How child j of the next generation is made (Algorithm 1). */
+enum { LEEA_KIND_ELITE = 0, LEEA_KIND_CROSSOVER = 1, LEEA_KIND_MUTATION = 2 };
+
+/* Operator parameters.  Defaults (leea_default_params) are the paper's
+ * hyperparameter block of Section 4. */
+typedef struct {
+    int32_t xo_op;      /* 0 uniform crossover, 1 arithmetic (Section 3.2)    */
+    float xo_gene_p;    /* uniform crossover: P(gene from parent 2); 0.5      */
+    int32_t sel_op;     /* 0 truncation (Section 3.1), 1 tournament           */
+    float rho;          /* truncation proportion rho in (0, 1]; 0.5           */
+    int32_t tour_k;     /* tournament size (>= 1); 3                          */
+    int32_t n_elite;    /* elite count; -1 => round(p_e * pop)                */
+    float p_e;          /* elite proportion p_E; 0.05                         */
+    float p_c;          /* crossover proportion p_C; 0.5; mutation the rest   */
+    float sigma;        /* mutation strength sigma (constant); 0.001          */
+    float mut_rate;     /* per-gene mutation probability; 1 = every gene      */
+    float alpha;        /* inheritance weight alpha on the new fitness; 1     */
+    int32_t init;       /* 0 N(0, 1/fan_in), 1 Glorot-uniform (Section 4.1)   */
+    int32_t precision;  /* 0 FP32 (only value accepted by this version)       */
+} leea_params;
+
+/* Fills *out with the paper's defaults (Section 4). */
+leea_status leea_default_params(leea_params* out);
+
+/* ---------------------------------------------------------------------- */
+/* Layout and operator counts                                              */
+/* ---------------------------------------------------------------------- */
+
+/* c, the number of genes of one individual (Section 3.2); -1 if dims invalid. */
+int64_t leea_num_params(const int32_t* dims, int32_t n_dims);
+
+/* c_pad = round_up(c, 32), the device stride between individuals; -1 if invalid. */
+int64_t leea_padded_params(const int32_t* dims, int32_t n_dims);
+
+/* Offspring counts of Algorithm 1: n_elite = n_elite param or round(p_E pop),
+ * n_crossover = round(p_C pop) (clipped to pop - n_elite), n_mutation = the
+ * rest; pool = max(1, floor(rho pop)), the truncation pool (Section 3.1).
+ * Any output pointer may be NULL. */
+leea_status leea_counts(int32_t pop, const leea_params* p, int32_t* n_elite,
+                        int32_t* n_crossover, int32_t* n_mutation, int32_t* pool);
+
+/* ---------------------------------------------------------------------- */
+/* Step entry points on caller-owned device buffers (stream-ordered)        */
+/* ---------------------------------------------------------------------- */
+
+/* Random initial population (Algorithm 1, first line; Section 4.1).
+ * init 0: W ~ N(0, 1/d_l) by Box-Muller on the INIT stream; init 1:
+ * Glorot-uniform W ~ U(-a, a), a = sqrt(6 / (d_l + d_{l+1})).  Biases and the
+ * padding are zero.  pop_dev: float[pop][c_pad], written. */
+leea_status leea_init_population(int32_t pop, const int32_t* dims, int32_t n_dims,
+                                 int32_t init, uint64_t seed, float* pop_dev,
+                                 void* stream);
+
+/* Sort by fitness, descending (Algorithm 1).  order_dev[r] = index of the
+ * r-th best individual; NaN ranks as -infinity, equal fitness goes to the
+ * lower index.  f_adj_dev: float[pop] (read); order_dev: int32[pop] (written). */
+leea_status leea_rank(int32_t pop, const float* f_adj_dev, int32_t* order_dev,
+                      void* stream);
+
+/* Parent selection and inherited fitness (Algorithm 1; Section 3.1).
+ * Children 0..n_elite-1 are the elites order[j]; the next n_crossover
+ * children get two parents, the rest one.  Truncation: each parent is
+ * order[floor(u * pool / 2^32)] with u draw 0 (parent 1) or 1 (parent 2) of
+ * the SEL stream of (gen, child).  Tournament: the best of tour_k draws
+ * (indices floor(u * pop / 2^32), draws 0..k-1 for parent 1, k..2k-1 for
+ * parent 2), ties to the lower index.  f_inh = (f1 + f2)/2 after crossover,
+ * f3 after mutation, the elite's own f_adj for an elite.
+ * Inputs f_adj_dev float[pop], order_dev int32[pop]; outputs par1_dev,
+ * par2_dev, kind_dev int32[pop] and f_inh_dev float[pop]. */
+leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_dev,
+                        const int32_t* order_dev, uint64_t seed, uint32_t gen,
+                        int32_t* par1_dev, int32_t* par2_dev, int32_t* kind_dev,
+                        float* f_inh_dev, void* stream);
+
+/* Crossover and mutation (Section 3.2) into a separate children buffer.
+ * For child j and gene i: elite -> copy of parent 1; uniform crossover ->
+ * parent 2's gene iff XO draw i < floor(xo_gene_p 2^32), else parent 1's;
+ * arithmetic crossover -> (a + b) / 2; mutation -> a + sigma z_i on genes whose
+ * MUTMASK draw i < floor(mut_rate 2^32) (all genes when mut_rate = 1), with z_i
+ * the Box-Muller normal of the NORMAL stream.  parents_dev and children_dev
+ * are float[pop][c_pad] and must not overlap. */
+leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
+                       const leea_params* p, uint64_t seed, uint32_t gen,
+                       const float* parents_dev, const int32_t* par1_dev,
+                       const int32_t* par2_dev, const int32_t* kind_dev,
+                       float* children_dev, void* stream);
+
+/* Fitness of every individual on one minibatch (Eq. 1) and inheritance
+ * (Section 3.1).  f = -(1/batch) sum_b CE(softmax(z_b), y_b) computed in FP32
+ * with the maximum subtracted; correct = #{b : argmax z_b = y_b} (ties to the
+ * lowest class); f_adj = (1 - alpha) f_inh + alpha f, or f_adj = f when
+ * f_inh_dev is NULL (the first evaluation).  Reductions have a fixed order,
+ * so identical individuals get bitwise identical results.
+ * n_dims must be 3 (d_0-h-d_out with d_out <= 32).  f_adj_dev and
+ * correct_dev may be NULL; f_raw_dev may not. */
+leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
+                          const float* pop_dev, const float* x_dev, const int32_t* y_dev,
+                          int32_t batch, float alpha, const float* f_inh_dev,
+                          float* f_raw_dev, float* f_adj_dev, int32_t* correct_dev,
+                          void* stream);
+
+/* Diagnostic: words n0 .. n0+count-1 of the Philox stream (tag, gen, ent),
+ * written to out_dev (uint32[count]).  Lets a caller check the generator. */
+leea_status leea_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
+                             uint32_t n0, int64_t count, uint32_t* out_dev, void* stream);
+
+/* Diagnostic: the Box-Muller normals z_i, i = n0 .. n0+count-1, of stream
+ * (tag, gen, ent) as used by mutation and initialisation (float[count]). */
+leea_status leea_normal_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
+                             uint32_t n0, int64_t count, float* out_dev, void* stream);
+
+/* ---------------------------------------------------------------------- */
+/* Algorithm 1 as a library-owned state object                             */
+/* ---------------------------------------------------------------------- */
+
+typedef struct leea_state leea_state;
+
+/* Allocates two population buffers of pop x c_pad floats plus per-individual
+ * arrays on the current device, and enqueues the initialisation on `stream`,
+ * which every later call of this object uses.  *out receives the object. */
+leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims,
+                        const leea_params* p, uint64_t seed, void* stream,
+                        leea_state** out);
+
+/* One generation of Algorithm 1 on the minibatch (x_dev, y_dev).  The first
+ * call only evaluates the initial population (f_adj = f).  Every later call
+ * increments the generation counter g, sorts by f_adj, selects, breeds into
+ * the other buffer with the streams of generation g, swaps the buffers and
+ * evaluates the new population with inheritance.  Enqueue only. */
+leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_dev,
+                            int32_t batch);
+
+/* leea_generation with the minibatch in HOST memory: copies it to a
+ * library-owned staging buffer on the object's stream, then runs the
+ * generation.  Host buffers may be reused once the call returns. */
+leea_status leea_generation_host(leea_state* s, const float* x_host,
+                                 const int32_t* y_host, int32_t batch);
+
+/* Adjusted fitness f_adj (float[pop]) and, if correct_host is not NULL, the
+ * correct-prediction counts of the last evaluation.  Synchronises. */
+leea_status leea_fitness(leea_state* s, float* f_adj_host, int32_t* correct_host);
+
+/* Raw fitness f of the last evaluation, before inheritance.  Synchronises. */
+leea_status leea_raw_fitness(leea_state* s, float* f_raw_host);
+
+/* Genes (float[c], logical layout) of the individual with the highest f_adj
+ * (ties to the lower index, NaN as -infinity).  Synchronises. */
+leea_status leea_best_params(leea_state* s, float* out_host, int64_t c);
+
+/* Whole current population, float[pop][c] logical layout.  Synchronises. */
+leea_status leea_get_population(leea_state* s, float* out_host);
+
+/* Replaces the current population (float[pop][c] logical layout). */
+leea_status leea_set_population(leea_state* s, const float* in_host);
+
+/* Replaces the adjusted fitness vector (float[pop]). */
+leea_status leea_set_fitness(leea_state* s, const float* f_adj_host);
+
+/* Sets the generation counter and whether the population counts as evaluated
+ * (checkpoint resume and lock-step testing). */
+leea_status leea_set_generation(leea_state* s, uint32_t gen, int32_t evaluated);
+
+/* Ranking and selection of the last breed: order, par1, par2, kind int32[pop]
+ * and f_inh float[pop]; any pointer may be NULL.  Synchronises. */
+leea_status leea_get_selection(leea_state* s, int32_t* order, int32_t* par1,
+                               int32_t* par2, int32_t* kind, float* f_inh);
+
+/* Generation counter g (0 before the first breed). */
+uint32_t leea_generation_index(const leea_state* s);
+
+/* c of the object's nets, or -1 for NULL. */
+int64_t leea_state_num_params(const leea_state* s);
+
+/* Per-stage timing with CUDA events recorded on the object's stream around
+ * each kernel of leea_generation.  Stages: 0 rank, 1 select, 2 breed,
+ * 3 evaluate. */
+#define LEEA_NUM_STAGES 4
+leea_status leea_profile_enable(leea_state* s, int32_t enable);
+
+/* Synchronises, then returns per stage the summed kernel time in ms and the
+ * number of launches since the last read, and resets both. */
+leea_status leea_profile_read(leea_state* s, double* ms_out, int64_t* launches_out);
+
+/* Thread-local message of the last failure on this thread ("" if none). */
+const char* leea_last_error(void);
+
+/* Frees the object and its device memory (synchronises its stream first). */
+void leea_destroy(leea_state* s);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEEA_H */

@@ -1,0 +1,710 @@
+// leea_capi.cu -- the C ABI declared in include/leea.h: argument checking,
+// layout arithmetic, the step entry points and the state object that strings
+// them together in the order of Algorithm 1.
+#include "leea.h"
+#include "leea_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace leea;
+
+namespace {
+
+thread_local char g_error[1024] = "";
+
+leea_status fail(leea_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_error, sizeof(g_error), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+leea_status cuda_fail(cudaError_t err, const char* what)
+{
+    if (err == cudaErrorMemoryAllocation)
+        return fail(LEEA_ENOMEM, "%s: %s", what, cudaGetErrorString(err));
+    return fail(LEEA_ECUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+#define LEEA_CUDA_TRY(expr, what)                         \
+    do {                                                  \
+        cudaError_t err_ = (expr);                        \
+        if (err_ != cudaSuccess) return cuda_fail(err_, what); \
+    } while (0)
+
+// Offsets of Section 3.2's direct encoding, plus the initialisation scale of
+// each weight matrix (Section 4.1).
+bool make_layout(const int32_t* dims, int32_t n_dims, int32_t init, NetLayout* net)
+{
+    if (!dims || n_dims < 2 || n_dims > kMaxLayers + 1) return false;
+    std::memset(net, 0, sizeof(*net));
+    net->n_layers = n_dims - 1;
+    int64_t off = 0;
+    for (int l = 0; l < n_dims; ++l) {
+        if (dims[l] <= 0 || dims[l] > (1 << 20)) return false;
+        net->dims[l] = dims[l];
+    }
+    for (int l = 0; l + 1 < n_dims; ++l) {
+        const int64_t fan_in = dims[l], fan_out = dims[l + 1];
+        net->w_off[l] = off;
+        off += fan_in * fan_out;
+        net->b_off[l] = off;
+        off += fan_out;
+        net->init_scale[l] = init == 1 ? static_cast<float>(std::sqrt(6.0 / static_cast<double>(fan_in + fan_out)))
+                                       : static_cast<float>(std::sqrt(1.0 / static_cast<double>(fan_in)));
+    }
+    net->c = off;
+    net->c_pad = (off + 31) / 32 * 32;
+    return off < (int64_t{1} << 32);  // gene indices feed 32-bit Philox counters
+}
+
+uint64_t threshold(double q)
+{
+    if (!(q > 0.0)) return 0;
+    if (q >= 1.0) return uint64_t{1} << 32;
+    return static_cast<uint64_t>(std::floor(q * 4294967296.0));
+}
+
+leea_status check_params(const leea_params* p)
+{
+    if (!p) return fail(LEEA_EINVAL, "params is NULL");
+    if (p->xo_op != 0 && p->xo_op != 1) return fail(LEEA_EINVAL, "xo_op must be 0 or 1");
+    if (p->sel_op != 0 && p->sel_op != 1) return fail(LEEA_EINVAL, "sel_op must be 0 or 1");
+    if (!(p->xo_gene_p >= 0.0f && p->xo_gene_p <= 1.0f)) return fail(LEEA_EINVAL, "xo_gene_p not in [0,1]");
+    if (!(p->rho > 0.0f && p->rho <= 1.0f)) return fail(LEEA_EINVAL, "rho not in (0,1]");
+    if (p->sel_op == 1 && p->tour_k < 1) return fail(LEEA_EINVAL, "tour_k must be >= 1");
+    if (!(p->p_e >= 0.0f && p->p_e <= 1.0f)) return fail(LEEA_EINVAL, "p_e not in [0,1]");
+    if (!(p->p_c >= 0.0f && p->p_c <= 1.0f)) return fail(LEEA_EINVAL, "p_c not in [0,1]");
+    if (!(p->sigma >= 0.0f) || std::isinf(p->sigma)) return fail(LEEA_EINVAL, "sigma must be finite and >= 0");
+    if (!(p->mut_rate >= 0.0f && p->mut_rate <= 1.0f)) return fail(LEEA_EINVAL, "mut_rate not in [0,1]");
+    if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
+    if (p->init != 0 && p->init != 1) return fail(LEEA_EINVAL, "init must be 0 or 1");
+    if (p->precision != 0) return fail(LEEA_EINVAL, "precision must be 0 (FP32)");
+    return LEEA_OK;
+}
+
+// Same rounding rules as the paper's proportions demand (Algorithm 1): round()
+// for elites and crossover children, the rest mutate; pool = max(1, floor(rho pop)).
+void counts_of(int32_t pop, const leea_params* p, int32_t* ne, int32_t* nc, int32_t* nm, int32_t* pool)
+{
+    int32_t e = p->n_elite >= 0 ? p->n_elite
+                                : static_cast<int32_t>(std::round(static_cast<double>(p->p_e) * pop));
+    e = e > pop ? pop : (e < 0 ? 0 : e);
+    int32_t c = static_cast<int32_t>(std::round(static_cast<double>(p->p_c) * pop));
+    c = c > pop - e ? pop - e : (c < 0 ? 0 : c);
+    int32_t pl = static_cast<int32_t>(std::floor(static_cast<double>(p->rho) * pop));
+    pl = pl < 1 ? 1 : (pl > pop ? pop : pl);
+    *ne = e;
+    *nc = c;
+    *nm = pop - e - c;
+    *pool = pl;
+}
+
+constexpr int32_t kMaxPop = 1 << 24;
+
+leea_status check_pop(int32_t pop)
+{
+    if (pop <= 0 || pop > kMaxPop) return fail(LEEA_EINVAL, "pop must be in [1, %d]", kMaxPop);
+    return LEEA_OK;
+}
+
+leea_status check_eval_shape(const NetLayout& net, int32_t batch)
+{
+    if (net.n_layers != 2) return fail(LEEA_EINVAL, "evaluation supports n_dims == 3 (d_0-h-d_out)");
+    if (net.dims[2] > 32) return fail(LEEA_EINVAL, "evaluation supports d_out <= 32");
+    if (batch <= 0) return fail(LEEA_EINVAL, "batch must be >= 1");
+    return LEEA_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+// Plain functions
+// ------------------------------------------------------------------------
+extern "C" {
+
+const char* leea_last_error(void) { return g_error; }
+
+leea_status leea_default_params(leea_params* out)
+{
+    if (!out) return fail(LEEA_EINVAL, "out is NULL");
+    out->xo_op = 0;
+    out->xo_gene_p = 0.5f;
+    out->sel_op = 0;
+    out->rho = 0.5f;
+    out->tour_k = 3;
+    out->n_elite = -1;
+    out->p_e = 0.05f;
+    out->p_c = 0.5f;
+    out->sigma = 0.001f;
+    out->mut_rate = 1.0f;
+    out->alpha = 1.0f;
+    out->init = 0;
+    out->precision = 0;
+    return LEEA_OK;
+}
+
+int64_t leea_num_params(const int32_t* dims, int32_t n_dims)
+{
+    NetLayout net;
+    return make_layout(dims, n_dims, 0, &net) ? net.c : -1;
+}
+
+int64_t leea_padded_params(const int32_t* dims, int32_t n_dims)
+{
+    NetLayout net;
+    return make_layout(dims, n_dims, 0, &net) ? net.c_pad : -1;
+}
+
+leea_status leea_counts(int32_t pop, const leea_params* p, int32_t* n_elite, int32_t* n_crossover,
+                        int32_t* n_mutation, int32_t* pool)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if ((st = check_params(p))) return st;
+    int32_t ne, nc, nm, pl;
+    counts_of(pop, p, &ne, &nc, &nm, &pl);
+    if (n_elite) *n_elite = ne;
+    if (n_crossover) *n_crossover = nc;
+    if (n_mutation) *n_mutation = nm;
+    if (pool) *pool = pl;
+    return LEEA_OK;
+}
+
+// ------------------------------------------------------------------------
+// Step entry points
+// ------------------------------------------------------------------------
+leea_status leea_init_population(int32_t pop, const int32_t* dims, int32_t n_dims, int32_t init,
+                                 uint64_t seed, float* pop_dev, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if (init != 0 && init != 1) return fail(LEEA_EINVAL, "init must be 0 or 1");
+    NetLayout net;
+    if (!make_layout(dims, n_dims, init, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if (!pop_dev) return fail(LEEA_EINVAL, "pop_dev is NULL");
+    LEEA_CUDA_TRY(launch_init(net, pop, init, seed, pop_dev, static_cast<cudaStream_t>(stream)), "init kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_rank(int32_t pop, const float* f_adj_dev, int32_t* order_dev, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if (!f_adj_dev || !order_dev) return fail(LEEA_EINVAL, "NULL device pointer");
+    LEEA_CUDA_TRY(launch_rank(pop, f_adj_dev, order_dev, static_cast<cudaStream_t>(stream)), "rank kernel");
+    return LEEA_OK;
+}
+
+static SelectArgs select_args(int32_t pop, const leea_params* p, uint64_t seed, uint32_t gen)
+{
+    SelectArgs a{};
+    int32_t ne, nc, nm, pl;
+    counts_of(pop, p, &ne, &nc, &nm, &pl);
+    a.pop = pop;
+    a.n_elite = ne;
+    a.n_cross = nc;
+    a.pool = pl;
+    a.sel_op = p->sel_op;
+    a.tour_k = p->tour_k;
+    a.seed = seed;
+    a.gen = gen;
+    return a;
+}
+
+leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_dev,
+                        const int32_t* order_dev, uint64_t seed, uint32_t gen, int32_t* par1_dev,
+                        int32_t* par2_dev, int32_t* kind_dev, float* f_inh_dev, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if ((st = check_params(p))) return st;
+    if (!f_adj_dev || !order_dev || !par1_dev || !par2_dev || !kind_dev || !f_inh_dev)
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    const SelectArgs a = select_args(pop, p, seed, gen);
+    LEEA_CUDA_TRY(launch_select(a, f_adj_dev, order_dev, par1_dev, par2_dev, kind_dev, f_inh_dev,
+                                static_cast<cudaStream_t>(stream)),
+                  "select kernel");
+    return LEEA_OK;
+}
+
+static BreedArgs breed_args(int32_t pop, const NetLayout& net, const leea_params* p, uint64_t seed,
+                            uint32_t gen)
+{
+    BreedArgs a{};
+    a.pop = pop;
+    a.c = net.c;
+    a.c_pad = net.c_pad;
+    a.xo_op = p->xo_op;
+    a.thr_xo = threshold(static_cast<double>(p->xo_gene_p));
+    a.thr_mut = threshold(static_cast<double>(p->mut_rate));
+    a.sigma = p->sigma;
+    a.seed = seed;
+    a.gen = gen;
+    return a;
+}
+
+leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                       uint64_t seed, uint32_t gen, const float* parents_dev, const int32_t* par1_dev,
+                       const int32_t* par2_dev, const int32_t* kind_dev, float* children_dev,
+                       void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if ((st = check_params(p))) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, p->init, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if (!parents_dev || !par1_dev || !par2_dev || !kind_dev || !children_dev)
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    const size_t bytes = sizeof(float) * static_cast<size_t>(pop) * static_cast<size_t>(net.c_pad);
+    const char* pa = reinterpret_cast<const char*>(parents_dev);
+    const char* ch = reinterpret_cast<const char*>(children_dev);
+    if (pa < ch + bytes && ch < pa + bytes) return fail(LEEA_EINVAL, "parents and children overlap");
+    if ((reinterpret_cast<uintptr_t>(parents_dev) | reinterpret_cast<uintptr_t>(children_dev)) & 15u)
+        return fail(LEEA_EINVAL, "population buffers must be 16-byte aligned");
+    const BreedArgs a = breed_args(pop, net, p, seed, gen);
+    LEEA_CUDA_TRY(launch_breed(a, parents_dev, par1_dev, par2_dev, kind_dev, children_dev,
+                               static_cast<cudaStream_t>(stream)),
+                  "breed kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims, const float* pop_dev,
+                          const float* x_dev, const int32_t* y_dev, int32_t batch, float alpha,
+                          const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
+                          int32_t* correct_dev, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if ((st = check_eval_shape(net, batch))) return st;
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
+    if (!pop_dev || !x_dev || !y_dev || !f_raw_dev) return fail(LEEA_EINVAL, "NULL device pointer");
+    LEEA_CUDA_TRY(launch_eval_simt(net, pop, pop_dev, x_dev, y_dev, batch, alpha, f_inh_dev, f_raw_dev,
+                                   f_adj_dev, correct_dev, static_cast<cudaStream_t>(stream)),
+                  "evaluate kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t n0,
+                             int64_t count, uint32_t* out_dev, void* stream)
+{
+    if (count < 0 || !out_dev) return fail(LEEA_EINVAL, "bad count or NULL output");
+    if (count == 0) return LEEA_OK;
+    LEEA_CUDA_TRY(launch_philox_fill(seed, tag, gen, ent, n0, count, out_dev, static_cast<cudaStream_t>(stream)),
+                  "philox fill kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_normal_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t n0,
+                             int64_t count, float* out_dev, void* stream)
+{
+    if (count < 0 || !out_dev) return fail(LEEA_EINVAL, "bad count or NULL output");
+    if (count == 0) return LEEA_OK;
+    LEEA_CUDA_TRY(launch_normal_fill(seed, tag, gen, ent, n0, count, out_dev, static_cast<cudaStream_t>(stream)),
+                  "normal fill kernel");
+    return LEEA_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------
+// State object
+// ------------------------------------------------------------------------
+namespace {
+
+constexpr int kProfRing = 4096;
+
+struct ProfileRing {
+    cudaEvent_t ev[LEEA_NUM_STAGES][2][kProfRing];
+    int n[LEEA_NUM_STAGES] = { 0, 0, 0, 0 };
+    double ms[LEEA_NUM_STAGES] = { 0, 0, 0, 0 };
+    int64_t launches[LEEA_NUM_STAGES] = { 0, 0, 0, 0 };
+    bool created = false;
+};
+
+}  // namespace
+
+struct leea_state {
+    int32_t pop;
+    NetLayout net;
+    leea_params prm;
+    uint64_t seed;
+    cudaStream_t stream;
+    uint32_t gen;
+    bool evaluated;
+    int cur;
+    float* popbuf[2];
+    float *f_adj, *f_raw, *f_inh;
+    int32_t *correct, *order, *par1, *par2, *kind;
+    float* x_stage;
+    int32_t* y_stage;
+    int64_t stage_cap;  // samples the staging buffers hold
+    bool profiling;
+    ProfileRing* prof;
+};
+
+namespace {
+
+void free_state(leea_state* s)
+{
+    if (!s) return;
+    cudaFree(s->popbuf[0]);
+    cudaFree(s->popbuf[1]);
+    cudaFree(s->f_adj);
+    cudaFree(s->f_raw);
+    cudaFree(s->f_inh);
+    cudaFree(s->correct);
+    cudaFree(s->order);
+    cudaFree(s->par1);
+    cudaFree(s->par2);
+    cudaFree(s->kind);
+    cudaFree(s->x_stage);
+    cudaFree(s->y_stage);
+    if (s->prof) {
+        if (s->prof->created)
+            for (int st = 0; st < LEEA_NUM_STAGES; ++st)
+                for (int e = 0; e < 2; ++e)
+                    for (int k = 0; k < kProfRing; ++k) cudaEventDestroy(s->prof->ev[st][e][k]);
+        delete s->prof;
+    }
+    delete s;
+}
+
+// Folds the recorded event pairs of every stage into the running sums.
+leea_status prof_fold(leea_state* s)
+{
+    ProfileRing* pr = s->prof;
+    if (!pr) return LEEA_OK;
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "profile sync");
+    for (int st = 0; st < LEEA_NUM_STAGES; ++st) {
+        for (int k = 0; k < pr->n[st]; ++k) {
+            float ms = 0.0f;
+            LEEA_CUDA_TRY(cudaEventElapsedTime(&ms, pr->ev[st][0][k], pr->ev[st][1][k]), "profile elapsed");
+            pr->ms[st] += ms;
+        }
+        pr->launches[st] += pr->n[st];
+        pr->n[st] = 0;
+    }
+    return LEEA_OK;
+}
+
+struct StageScope {
+    leea_state* s;
+    int stage;
+    bool on;
+    StageScope(leea_state* st, int stage_) : s(st), stage(stage_), on(st->profiling && st->prof)
+    {
+        if (!on) return;
+        if (s->prof->n[stage] == kProfRing) prof_fold(s);
+        cudaEventRecord(s->prof->ev[stage][0][s->prof->n[stage]], s->stream);
+    }
+    void done()
+    {
+        if (!on) return;
+        cudaEventRecord(s->prof->ev[stage][1][s->prof->n[stage]], s->stream);
+        s->prof->n[stage]++;
+        on = false;
+    }
+};
+
+leea_status check_state(leea_state* s)
+{
+    if (!s) return fail(LEEA_EINVAL, "state is NULL");
+    return LEEA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                        uint64_t seed, void* stream, leea_state** out)
+{
+    if (!out) return fail(LEEA_EINVAL, "out is NULL");
+    *out = nullptr;
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if ((st = check_params(p))) return st;
+    leea_state* s = new (std::nothrow) leea_state();
+    if (!s) return fail(LEEA_ENOMEM, "host allocation failed");
+    if (!make_layout(dims, n_dims, p->init, &s->net)) {
+        delete s;
+        return fail(LEEA_EINVAL, "invalid dims");
+    }
+    if (s->net.n_layers != 2 || s->net.dims[2] > 32) {
+        delete s;
+        return fail(LEEA_EINVAL, "the state object evaluates d_0-h-d_out nets (n_dims == 3, d_out <= 32)");
+    }
+    s->pop = pop;
+    s->prm = *p;
+    s->seed = seed;
+    s->stream = static_cast<cudaStream_t>(stream);
+    const size_t np = static_cast<size_t>(pop);
+    const size_t pop_bytes = sizeof(float) * np * static_cast<size_t>(s->net.c_pad);
+    cudaError_t err = cudaSuccess;
+    for (int b = 0; b < 2 && err == cudaSuccess; ++b) err = cudaMalloc(&s->popbuf[b], pop_bytes);
+    if (err == cudaSuccess) err = cudaMalloc(&s->f_adj, sizeof(float) * np);
+    if (err == cudaSuccess) err = cudaMalloc(&s->f_raw, sizeof(float) * np);
+    if (err == cudaSuccess) err = cudaMalloc(&s->f_inh, sizeof(float) * np);
+    if (err == cudaSuccess) err = cudaMalloc(&s->correct, sizeof(int32_t) * np);
+    if (err == cudaSuccess) err = cudaMalloc(&s->order, sizeof(int32_t) * np);
+    if (err == cudaSuccess) err = cudaMalloc(&s->par1, sizeof(int32_t) * np);
+    if (err == cudaSuccess) err = cudaMalloc(&s->par2, sizeof(int32_t) * np);
+    if (err == cudaSuccess) err = cudaMalloc(&s->kind, sizeof(int32_t) * np);
+    if (err != cudaSuccess) {
+        free_state(s);
+        return cuda_fail(err, "leea_create allocation");
+    }
+    err = cudaMemsetAsync(s->popbuf[1], 0, pop_bytes, s->stream);
+    if (err == cudaSuccess) err = launch_init(s->net, pop, p->init, seed, s->popbuf[0], s->stream);
+    if (err != cudaSuccess) {
+        free_state(s);
+        return cuda_fail(err, "leea_create init");
+    }
+    *out = s;
+    return LEEA_OK;
+}
+
+leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_dev, int32_t batch)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if ((st = check_eval_shape(s->net, batch))) return st;
+    if (!x_dev || !y_dev) return fail(LEEA_EINVAL, "NULL minibatch pointer");
+    const bool first = !s->evaluated;
+    if (!first) {
+        const uint32_t g = s->gen + 1;
+        {
+            StageScope sc(s, 0);
+            LEEA_CUDA_TRY(launch_rank(s->pop, s->f_adj, s->order, s->stream), "rank kernel");
+            sc.done();
+        }
+        {
+            StageScope sc(s, 1);
+            const SelectArgs a = select_args(s->pop, &s->prm, s->seed, g);
+            LEEA_CUDA_TRY(launch_select(a, s->f_adj, s->order, s->par1, s->par2, s->kind, s->f_inh, s->stream),
+                          "select kernel");
+            sc.done();
+        }
+        {
+            StageScope sc(s, 2);
+            const BreedArgs a = breed_args(s->pop, s->net, &s->prm, s->seed, g);
+            LEEA_CUDA_TRY(launch_breed(a, s->popbuf[s->cur], s->par1, s->par2, s->kind, s->popbuf[s->cur ^ 1],
+                                       s->stream),
+                          "breed kernel");
+            sc.done();
+        }
+        s->cur ^= 1;
+        s->gen = g;
+    }
+    {
+        StageScope sc(s, 3);
+        LEEA_CUDA_TRY(launch_eval_simt(s->net, s->pop, s->popbuf[s->cur], x_dev, y_dev, batch, s->prm.alpha,
+                                       first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct, s->stream),
+                      "evaluate kernel");
+        sc.done();
+    }
+    s->evaluated = true;
+    return LEEA_OK;
+}
+
+leea_status leea_generation_host(leea_state* s, const float* x_host, const int32_t* y_host, int32_t batch)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if ((st = check_eval_shape(s->net, batch))) return st;
+    if (!x_host || !y_host) return fail(LEEA_EINVAL, "NULL minibatch pointer");
+    if (batch > s->stage_cap) {
+        LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "staging sync");
+        cudaFree(s->x_stage);
+        cudaFree(s->y_stage);
+        s->x_stage = nullptr;
+        s->y_stage = nullptr;
+        s->stage_cap = 0;
+        LEEA_CUDA_TRY(cudaMalloc(&s->x_stage, sizeof(float) * static_cast<size_t>(batch) * s->net.dims[0]),
+                      "staging allocation");
+        LEEA_CUDA_TRY(cudaMalloc(&s->y_stage, sizeof(int32_t) * static_cast<size_t>(batch)), "staging allocation");
+        s->stage_cap = batch;
+    }
+    LEEA_CUDA_TRY(cudaMemcpyAsync(s->x_stage, x_host, sizeof(float) * static_cast<size_t>(batch) * s->net.dims[0],
+                                  cudaMemcpyHostToDevice, s->stream),
+                  "minibatch copy");
+    LEEA_CUDA_TRY(cudaMemcpyAsync(s->y_stage, y_host, sizeof(int32_t) * static_cast<size_t>(batch),
+                                  cudaMemcpyHostToDevice, s->stream),
+                  "label copy");
+    return leea_generation(s, s->x_stage, s->y_stage, batch);
+}
+
+static leea_status copy_out(leea_state* s, void* dst, const void* src, size_t bytes, const char* what)
+{
+    LEEA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream), what);
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), what);
+    return LEEA_OK;
+}
+
+leea_status leea_fitness(leea_state* s, float* f_adj_host, int32_t* correct_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!s->evaluated) return fail(LEEA_ESTATE, "no generation has been evaluated yet");
+    if (!f_adj_host) return fail(LEEA_EINVAL, "f_adj_host is NULL");
+    LEEA_CUDA_TRY(cudaMemcpyAsync(f_adj_host, s->f_adj, sizeof(float) * s->pop, cudaMemcpyDeviceToHost, s->stream),
+                  "fitness copy");
+    if (correct_host)
+        LEEA_CUDA_TRY(cudaMemcpyAsync(correct_host, s->correct, sizeof(int32_t) * s->pop, cudaMemcpyDeviceToHost,
+                                      s->stream),
+                      "correct copy");
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "fitness sync");
+    return LEEA_OK;
+}
+
+leea_status leea_raw_fitness(leea_state* s, float* f_raw_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!s->evaluated) return fail(LEEA_ESTATE, "no generation has been evaluated yet");
+    if (!f_raw_host) return fail(LEEA_EINVAL, "f_raw_host is NULL");
+    return copy_out(s, f_raw_host, s->f_raw, sizeof(float) * s->pop, "raw fitness copy");
+}
+
+static bool beats(float a, int32_t ia, float b, int32_t ib)
+{
+    const float fa = std::isnan(a) ? -INFINITY : a, fb = std::isnan(b) ? -INFINITY : b;
+    return fa > fb || (fa == fb && ia < ib);
+}
+
+leea_status leea_best_params(leea_state* s, float* out_host, int64_t c)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!s->evaluated) return fail(LEEA_ESTATE, "no generation has been evaluated yet");
+    if (!out_host || c != s->net.c) return fail(LEEA_EINVAL, "out_host NULL or c != %lld", (long long)s->net.c);
+    std::vector<float> f(static_cast<size_t>(s->pop));
+    if ((st = copy_out(s, f.data(), s->f_adj, sizeof(float) * s->pop, "fitness copy"))) return st;
+    int32_t best = 0;
+    for (int32_t p = 1; p < s->pop; ++p)
+        if (beats(f[p], p, f[best], best)) best = p;
+    return copy_out(s, out_host, s->popbuf[s->cur] + static_cast<int64_t>(best) * s->net.c_pad,
+                    sizeof(float) * static_cast<size_t>(c), "best params copy");
+}
+
+leea_status leea_get_population(leea_state* s, float* out_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!out_host) return fail(LEEA_EINVAL, "out_host is NULL");
+    LEEA_CUDA_TRY(cudaMemcpy2DAsync(out_host, sizeof(float) * s->net.c, s->popbuf[s->cur],
+                                    sizeof(float) * s->net.c_pad, sizeof(float) * s->net.c, s->pop,
+                                    cudaMemcpyDeviceToHost, s->stream),
+                  "population copy");
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "population sync");
+    return LEEA_OK;
+}
+
+leea_status leea_set_population(leea_state* s, const float* in_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!in_host) return fail(LEEA_EINVAL, "in_host is NULL");
+    LEEA_CUDA_TRY(cudaMemcpy2DAsync(s->popbuf[s->cur], sizeof(float) * s->net.c_pad, in_host,
+                                    sizeof(float) * s->net.c, sizeof(float) * s->net.c, s->pop,
+                                    cudaMemcpyHostToDevice, s->stream),
+                  "population copy");
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "population sync");
+    return LEEA_OK;
+}
+
+leea_status leea_set_fitness(leea_state* s, const float* f_adj_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!f_adj_host) return fail(LEEA_EINVAL, "f_adj_host is NULL");
+    LEEA_CUDA_TRY(cudaMemcpyAsync(s->f_adj, f_adj_host, sizeof(float) * s->pop, cudaMemcpyHostToDevice, s->stream),
+                  "fitness copy");
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "fitness sync");
+    return LEEA_OK;
+}
+
+leea_status leea_set_generation(leea_state* s, uint32_t gen, int32_t evaluated)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    s->gen = gen;
+    s->evaluated = evaluated != 0;
+    return LEEA_OK;
+}
+
+leea_status leea_get_selection(leea_state* s, int32_t* order, int32_t* par1, int32_t* par2, int32_t* kind,
+                               float* f_inh)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    const size_t ni = sizeof(int32_t) * s->pop;
+    struct { void* dst; const void* src; size_t n; } copies[] = {
+        { order, s->order, ni }, { par1, s->par1, ni }, { par2, s->par2, ni },
+        { kind, s->kind, ni }, { f_inh, s->f_inh, sizeof(float) * s->pop } };
+    for (auto& c : copies)
+        if (c.dst)
+            LEEA_CUDA_TRY(cudaMemcpyAsync(c.dst, c.src, c.n, cudaMemcpyDeviceToHost, s->stream), "selection copy");
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "selection sync");
+    return LEEA_OK;
+}
+
+uint32_t leea_generation_index(const leea_state* s) { return s ? s->gen : 0u; }
+
+int64_t leea_state_num_params(const leea_state* s) { return s ? s->net.c : -1; }
+
+leea_status leea_profile_enable(leea_state* s, int32_t enable)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (enable && !s->prof) {
+        s->prof = new (std::nothrow) ProfileRing();
+        if (!s->prof) return fail(LEEA_ENOMEM, "profile ring allocation");
+        for (int stg = 0; stg < LEEA_NUM_STAGES; ++stg)
+            for (int e = 0; e < 2; ++e)
+                for (int k = 0; k < kProfRing; ++k)
+                    LEEA_CUDA_TRY(cudaEventCreate(&s->prof->ev[stg][e][k]), "event create");
+        s->prof->created = true;
+    }
+    s->profiling = enable != 0;
+    return LEEA_OK;
+}
+
+leea_status leea_profile_read(leea_state* s, double* ms_out, int64_t* launches_out)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!ms_out || !launches_out) return fail(LEEA_EINVAL, "NULL output");
+    if (!s->prof) {
+        for (int k = 0; k < LEEA_NUM_STAGES; ++k) { ms_out[k] = 0.0; launches_out[k] = 0; }
+        return LEEA_OK;
+    }
+    if ((st = prof_fold(s))) return st;
+    for (int k = 0; k < LEEA_NUM_STAGES; ++k) {
+        ms_out[k] = s->prof->ms[k];
+        launches_out[k] = s->prof->launches[k];
+        s->prof->ms[k] = 0.0;
+        s->prof->launches[k] = 0;
+    }
+    return LEEA_OK;
+}
+
+void leea_destroy(leea_state* s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->stream);
+    free_state(s);
+}
+
+}  // extern "C"

@@ -1,0 +1,60 @@
+// leea_internal.h -- launch interface between the C ABI (leea_capi.cu) and the
+// kernels.  Host-only declarations; every launcher enqueues on `stream` and
+// returns the launch error (cudaSuccess when the launch was accepted).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace leea {
+
+constexpr int kMaxLayers = 15;
+
+// Per-layer offsets of a net, computed on the host (logical gene order of
+// Section 3.2: W_l rows out x in, then b_l).
+struct NetLayout {
+    int32_t n_layers;                  // L = n_dims - 1
+    int32_t dims[kMaxLayers + 1];
+    int64_t w_off[kMaxLayers];         // first gene of W_l
+    int64_t b_off[kMaxLayers];         // first gene of b_l
+    float init_scale[kMaxLayers];      // N(0,1/fan_in): 1/sqrt(d_l); Glorot: a
+    int64_t c;                         // genes
+    int64_t c_pad;                     // device stride, multiple of 32
+};
+
+struct SelectArgs {
+    int32_t pop, n_elite, n_cross, pool;
+    int32_t sel_op, tour_k;
+    uint64_t seed;
+    uint32_t gen;
+};
+
+struct BreedArgs {
+    int32_t pop;
+    int64_t c, c_pad;
+    int32_t xo_op;
+    uint64_t thr_xo, thr_mut;
+    float sigma;
+    uint64_t seed;
+    uint32_t gen;
+};
+
+cudaError_t launch_init(const NetLayout& net, int32_t pop, int32_t init, uint64_t seed,
+                        float* pop_dev, cudaStream_t stream);
+cudaError_t launch_rank(int32_t pop, const float* f_adj, int32_t* order, cudaStream_t stream);
+cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t* order,
+                          int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh,
+                          cudaStream_t stream);
+cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t* par1,
+                         const int32_t* par2, const int32_t* kind, float* children,
+                         cudaStream_t stream);
+// Evaluation of d_0-h-d_out nets (one hidden layer), SIMT FP32.
+cudaError_t launch_eval_simt(const NetLayout& net, int32_t pop, const float* pop_dev,
+                             const float* x, const int32_t* y, int32_t batch, float alpha,
+                             const float* f_inh, float* f_raw, float* f_adj, int32_t* correct,
+                             cudaStream_t stream);
+cudaError_t launch_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
+                               uint32_t n0, int64_t count, uint32_t* out, cudaStream_t stream);
+cudaError_t launch_normal_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
+                               uint32_t n0, int64_t count, float* out, cudaStream_t stream);
+
+}  // namespace leea

@@ -1,0 +1,124 @@
+// leea_select.cu -- sort by fitness and parent selection (Algorithm 1;
+// Section 3.1: elites, truncation selection from the top rho*lambda, fitness
+// inheritance values) plus the tournament alternative.
+#include "leea_internal.h"
+#include "philox.cuh"
+
+namespace leea {
+
+constexpr uint32_t kTagSel = 2;
+constexpr int32_t kKindElite = 0, kKindCross = 1, kKindMut = 2;
+
+// A 64-bit key whose ascending order is: fitness descending (NaN as -inf,
+// -0 as +0), then index ascending.  Comparing keys is exact, so the order is
+// the same total order any correct sort of the same FP32 vector produces.
+__device__ __forceinline__ uint64_t rank_key(float f, int32_t idx)
+{
+    uint32_t b = __float_as_uint(f);
+    if (f != f) b = 0xFF800000u;       // NaN -> -inf
+    if (b == 0x80000000u) b = 0u;      // -0 -> +0
+    const uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // grows with f
+    return (static_cast<uint64_t>(~asc) << 32) | static_cast<uint32_t>(idx);
+}
+
+// Rank by counting: the rank of i is the number of keys below its own.  Each
+// thread owns one individual and scans every key through a shared tile; at
+// the population sizes of the method (<= a few 10^4) this is a handful of
+// microseconds and needs no scratch memory.
+constexpr int kRankTile = 2048;
+
+__global__ void __launch_bounds__(256) rank_kernel(int32_t pop, const float* __restrict__ f_adj,
+                                                   int32_t* __restrict__ order)
+{
+    __shared__ uint64_t tile[kRankTile];
+    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t mine = i < pop ? rank_key(f_adj[i], i) : ~0ull;
+    int32_t r = 0;
+    for (int32_t base = 0; base < pop; base += kRankTile) {
+        const int32_t n = pop - base < kRankTile ? pop - base : kRankTile;
+        __syncthreads();
+        for (int32_t t = threadIdx.x; t < n; t += blockDim.x) tile[t] = rank_key(f_adj[base + t], base + t);
+        __syncthreads();
+#pragma unroll 8
+        for (int32_t t = 0; t < n; ++t) r += tile[t] < mine ? 1 : 0;
+    }
+    if (i < pop) order[r] = i;
+}
+
+cudaError_t launch_rank(int32_t pop, const float* f_adj, int32_t* order, cudaStream_t stream)
+{
+    rank_kernel<<<(pop + 255) / 256, 256, 0, stream>>>(pop, f_adj, order);
+    return cudaGetLastError();
+}
+
+// Draw n of child j's SEL stream, caching the current Philox block.
+struct SelStream {
+    uint64_t seed;
+    uint32_t gen, ent, blk;
+    uint4 w;
+    __device__ SelStream(uint64_t s, uint32_t g, uint32_t e) : seed(s), gen(g), ent(e), blk(0xFFFFFFFFu) {}
+    __device__ uint32_t draw(uint32_t n)
+    {
+        if ((n >> 2) != blk) {
+            blk = n >> 2;
+            w = stream_block(seed, kTagSel, gen, ent, blk);
+        }
+        return word_of(w, n & 3u);
+    }
+};
+
+__device__ __forceinline__ int32_t pick_parent(const SelectArgs& a, const float* f_adj,
+                                               const int32_t* order, SelStream& st, uint32_t first)
+{
+    if (a.sel_op == 0)
+        return order[index_of(st.draw(first), static_cast<uint32_t>(a.pool))];
+    int32_t best = -1;
+    uint64_t best_key = 0;
+    for (int32_t t = 0; t < a.tour_k; ++t) {
+        const int32_t cand = static_cast<int32_t>(index_of(st.draw(first + t), static_cast<uint32_t>(a.pop)));
+        const uint64_t k = rank_key(f_adj[cand], cand);
+        if (best < 0 || k < best_key) { best = cand; best_key = k; }
+    }
+    return best;
+}
+
+__global__ void __launch_bounds__(256) select_kernel(SelectArgs a, const float* __restrict__ f_adj,
+                                                     const int32_t* __restrict__ order,
+                                                     int32_t* __restrict__ par1, int32_t* __restrict__ par2,
+                                                     int32_t* __restrict__ kind, float* __restrict__ f_inh)
+{
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.pop) return;
+    SelStream st(a.seed, a.gen, static_cast<uint32_t>(j));
+    int32_t k, p1, p2;
+    float fi;
+    if (j < a.n_elite) {
+        k = kKindElite;
+        p1 = p2 = order[j];
+        fi = f_adj[p1];
+    } else if (j < a.n_elite + a.n_cross) {
+        k = kKindCross;
+        const uint32_t draws = a.sel_op == 0 ? 1u : static_cast<uint32_t>(a.tour_k);
+        p1 = pick_parent(a, f_adj, order, st, 0u);
+        p2 = pick_parent(a, f_adj, order, st, draws);
+        fi = 0.5f * (f_adj[p1] + f_adj[p2]);
+    } else {
+        k = kKindMut;
+        p1 = p2 = pick_parent(a, f_adj, order, st, 0u);
+        fi = f_adj[p1];
+    }
+    kind[j] = k;
+    par1[j] = p1;
+    par2[j] = p2;
+    f_inh[j] = fi;
+}
+
+cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t* order,
+                          int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh,
+                          cudaStream_t stream)
+{
+    select_kernel<<<(a.pop + 255) / 256, 256, 0, stream>>>(a, f_adj, order, par1, par2, kind, f_inh);
+    return cudaGetLastError();
+}
+
+}  // namespace leea

@@ -1,0 +1,323 @@
+"""Thin ctypes binding of the C ABI in ``include/leea.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libleea.so``.  Device buffers are torch CUDA tensors (torch is used
+for device memory and streams); each function passes their data pointers and
+the current torch stream straight through.  If the library cannot be loaded
+the functions raise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, fields
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libleea.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = range(6)
+TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
+KIND_ELITE, KIND_CROSSOVER, KIND_MUTATION = 0, 1, 2
+NUM_STAGES = 4
+STAGES = ("rank", "select", "breed", "evaluate")
+
+
+class LeeaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"LEEA status {status}: {msg}")
+        self.status = status
+
+
+class leea_params(ctypes.Structure):
+    _fields_ = [
+        ("xo_op", ctypes.c_int32), ("xo_gene_p", ctypes.c_float),
+        ("sel_op", ctypes.c_int32), ("rho", ctypes.c_float),
+        ("tour_k", ctypes.c_int32), ("n_elite", ctypes.c_int32),
+        ("p_e", ctypes.c_float), ("p_c", ctypes.c_float),
+        ("sigma", ctypes.c_float), ("mut_rate", ctypes.c_float),
+        ("alpha", ctypes.c_float), ("init", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+@dataclass
+class Params:
+    """Operator parameters (fields of ``leea_params``); defaults are the paper's."""
+    xo_op: int = 0
+    xo_gene_p: float = 0.5
+    sel_op: int = 0
+    rho: float = 0.5
+    tour_k: int = 3
+    n_elite: int = -1
+    p_e: float = 0.05
+    p_c: float = 0.5
+    sigma: float = 0.001
+    mut_rate: float = 1.0
+    alpha: float = 1.0
+    init: int = 0
+    precision: int = 0
+
+    def c_struct(self) -> leea_params:
+        return leea_params(**{f.name: getattr(self, f.name) for f in fields(Params)})
+
+
+_lib = None
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Loads ``libleea.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"LEEA CUDA library not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    i32, u32, u64, i64, f32 = ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64, ctypes.c_float
+    vp = ctypes.c_void_p
+    P = ctypes.POINTER
+    sig = {
+        "leea_default_params": [P(leea_params)],
+        "leea_num_params": ([vp, i32], i64),
+        "leea_padded_params": ([vp, i32], i64),
+        "leea_counts": [i32, P(leea_params), P(i32), P(i32), P(i32), P(i32)],
+        "leea_init_population": [i32, vp, i32, i32, u64, vp, vp],
+        "leea_rank": [i32, vp, vp, vp],
+        "leea_select": [i32, P(leea_params), vp, vp, u64, u32, vp, vp, vp, vp, vp],
+        "leea_breed": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp],
+        "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, vp],
+        "leea_philox_fill": [u64, u32, u32, u32, u32, i64, vp, vp],
+        "leea_normal_fill": [u64, u32, u32, u32, u32, i64, vp, vp],
+        "leea_create": [i32, vp, i32, P(leea_params), u64, vp, P(vp)],
+        "leea_generation": [vp, vp, vp, i32],
+        "leea_generation_host": [vp, vp, vp, i32],
+        "leea_fitness": [vp, vp, vp],
+        "leea_raw_fitness": [vp, vp],
+        "leea_best_params": [vp, vp, i64],
+        "leea_get_population": [vp, vp],
+        "leea_set_population": [vp, vp],
+        "leea_set_fitness": [vp, vp],
+        "leea_set_generation": [vp, u32, i32],
+        "leea_get_selection": [vp, vp, vp, vp, vp, vp],
+        "leea_generation_index": ([vp], u32),
+        "leea_state_num_params": ([vp], i64),
+        "leea_profile_enable": [vp, i32],
+        "leea_profile_read": [vp, vp, vp],
+        "leea_last_error": ([], ctypes.c_char_p),
+        "leea_destroy": ([vp], None),
+    }
+    for name, spec in sig.items():
+        fn = getattr(L, name)
+        if isinstance(spec, tuple):
+            fn.argtypes, fn.restype = spec
+        else:
+            fn.argtypes, fn.restype = spec, ctypes.c_int
+    _lib = L
+    return L
+
+
+def exported_symbols() -> list[str]:
+    """Names of the entry points the binding expects the library to export."""
+    return ["leea_default_params", "leea_num_params", "leea_padded_params", "leea_counts",
+            "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_evaluate",
+            "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
+            "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
+            "leea_get_population", "leea_set_population", "leea_set_fitness", "leea_set_generation",
+            "leea_get_selection", "leea_generation_index", "leea_state_num_params",
+            "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy"]
+
+
+def _check(rc: int) -> None:
+    if rc != OK:
+        msg = load_library().leea_last_error()
+        raise LeeaError(rc, msg.decode() if msg else "")
+
+
+def _dims(dims) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(dims, dtype=np.int32))
+
+
+def _dptr(t) -> int | None:
+    """Device pointer of a torch CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _hp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ---- plain functions ------------------------------------------------------------
+def leea_default_params() -> Params:
+    s = leea_params()
+    _check(load_library().leea_default_params(ctypes.byref(s)))
+    return Params(**{f.name: getattr(s, f.name) for f in fields(Params)})
+
+
+def leea_num_params(dims) -> int:
+    d = _dims(dims)
+    return int(load_library().leea_num_params(_hp(d), len(d)))
+
+
+def leea_padded_params(dims) -> int:
+    d = _dims(dims)
+    return int(load_library().leea_padded_params(_hp(d), len(d)))
+
+
+def leea_counts(pop: int, prm: Params) -> tuple[int, int, int, int]:
+    vals = [ctypes.c_int32() for _ in range(4)]
+    cp = prm.c_struct()
+    _check(load_library().leea_counts(pop, ctypes.byref(cp), *[ctypes.byref(v) for v in vals]))
+    return tuple(v.value for v in vals)
+
+
+# ---- step entry points (torch CUDA tensors) ------------------------------------------
+def leea_init_population(pop: int, dims, init: int, seed: int, pop_dev, stream=None) -> None:
+    d = _dims(dims)
+    _check(load_library().leea_init_population(pop, _hp(d), len(d), init, seed, _dptr(pop_dev), _stream(stream)))
+
+
+def leea_rank(pop: int, f_adj_dev, order_dev, stream=None) -> None:
+    _check(load_library().leea_rank(pop, _dptr(f_adj_dev), _dptr(order_dev), _stream(stream)))
+
+
+def leea_select(pop: int, prm: Params, f_adj_dev, order_dev, seed: int, gen: int,
+                par1_dev, par2_dev, kind_dev, f_inh_dev, stream=None) -> None:
+    cp = prm.c_struct()
+    _check(load_library().leea_select(pop, ctypes.byref(cp), _dptr(f_adj_dev), _dptr(order_dev), seed, gen,
+                                      _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev), _dptr(f_inh_dev),
+                                      _stream(stream)))
+
+
+def leea_breed(pop: int, dims, prm: Params, seed: int, gen: int, parents_dev, par1_dev, par2_dev,
+               kind_dev, children_dev, stream=None) -> None:
+    d = _dims(dims)
+    cp = prm.c_struct()
+    _check(load_library().leea_breed(pop, _hp(d), len(d), ctypes.byref(cp), seed, gen, _dptr(parents_dev),
+                                     _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev), _dptr(children_dev),
+                                     _stream(stream)))
+
+
+def leea_evaluate(pop: int, dims, pop_dev, x_dev, y_dev, batch: int, alpha: float, f_inh_dev,
+                  f_raw_dev, f_adj_dev=None, correct_dev=None, stream=None) -> None:
+    d = _dims(dims)
+    _check(load_library().leea_evaluate(pop, _hp(d), len(d), _dptr(pop_dev), _dptr(x_dev), _dptr(y_dev), batch,
+                                        float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev), _dptr(f_adj_dev),
+                                        _dptr(correct_dev), _stream(stream)))
+
+
+def leea_philox_fill(seed: int, tag: int, gen: int, ent: int, n0: int, count: int, out_dev, stream=None) -> None:
+    _check(load_library().leea_philox_fill(seed, tag, gen, ent, n0, count, _dptr(out_dev), _stream(stream)))
+
+
+def leea_normal_fill(seed: int, tag: int, gen: int, ent: int, n0: int, count: int, out_dev, stream=None) -> None:
+    _check(load_library().leea_normal_fill(seed, tag, gen, ent, n0, count, _dptr(out_dev), _stream(stream)))
+
+
+# ---- the state object --------------------------------------------------------------
+class LeeaState:
+    """Algorithm 1 as a library-owned object (``leea_create`` ... ``leea_destroy``)."""
+
+    def __init__(self, pop: int, dims, prm: Params, seed: int, stream=None):
+        self.lib = load_library()
+        self.pop = pop
+        self.dims = _dims(dims)
+        self._cp = prm.c_struct()
+        h = ctypes.c_void_p()
+        _check(self.lib.leea_create(pop, _hp(self.dims), len(self.dims), ctypes.byref(self._cp), seed,
+                                    _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.c = int(self.lib.leea_state_num_params(h))
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            self.lib.leea_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def leea_generation(self, x_dev, y_dev) -> None:
+        _check(self.lib.leea_generation(self._h, _dptr(x_dev), _dptr(y_dev), int(y_dev.shape[0])))
+
+    def leea_generation_host(self, x_host, y_host) -> None:
+        """x_host / y_host: CPU torch tensors (ideally pinned) or numpy arrays."""
+        xp = x_host.data_ptr() if hasattr(x_host, "data_ptr") else x_host.ctypes.data
+        yp = y_host.data_ptr() if hasattr(y_host, "data_ptr") else y_host.ctypes.data
+        _check(self.lib.leea_generation_host(self._h, xp, yp, int(y_host.shape[0])))
+
+    def leea_fitness(self, with_correct: bool = False):
+        f = np.empty(self.pop, dtype=np.float32)
+        cor = np.empty(self.pop, dtype=np.int32) if with_correct else None
+        _check(self.lib.leea_fitness(self._h, _hp(f), None if cor is None else _hp(cor)))
+        return (f, cor) if with_correct else f
+
+    def leea_raw_fitness(self) -> np.ndarray:
+        f = np.empty(self.pop, dtype=np.float32)
+        _check(self.lib.leea_raw_fitness(self._h, _hp(f)))
+        return f
+
+    def leea_best_params(self) -> np.ndarray:
+        out = np.empty(self.c, dtype=np.float32)
+        _check(self.lib.leea_best_params(self._h, _hp(out), self.c))
+        return out
+
+    def leea_get_population(self) -> np.ndarray:
+        out = np.empty((self.pop, self.c), dtype=np.float32)
+        _check(self.lib.leea_get_population(self._h, _hp(out)))
+        return out
+
+    def leea_set_population(self, popv) -> None:
+        a = np.ascontiguousarray(np.asarray(popv, dtype=np.float32))
+        assert a.shape == (self.pop, self.c)
+        _check(self.lib.leea_set_population(self._h, _hp(a)))
+
+    def leea_set_fitness(self, f_adj) -> None:
+        a = np.ascontiguousarray(np.asarray(f_adj, dtype=np.float32))
+        _check(self.lib.leea_set_fitness(self._h, _hp(a)))
+
+    def leea_set_generation(self, gen: int, evaluated: bool) -> None:
+        _check(self.lib.leea_set_generation(self._h, gen, int(evaluated)))
+
+    def leea_get_selection(self):
+        """(order, par1, par2, kind, f_inh) of the last breed."""
+        ints = [np.empty(self.pop, dtype=np.int32) for _ in range(4)]
+        f_inh = np.empty(self.pop, dtype=np.float32)
+        _check(self.lib.leea_get_selection(self._h, *[_hp(a) for a in ints], _hp(f_inh)))
+        return (*ints, f_inh)
+
+    @property
+    def gen(self) -> int:
+        return int(self.lib.leea_generation_index(self._h))
+
+    def leea_profile_enable(self, on: bool = True) -> None:
+        _check(self.lib.leea_profile_enable(self._h, int(on)))
+
+    def leea_profile_read(self):
+        """{stage: (ms_total, launches)} since the last read."""
+        ms = np.zeros(NUM_STAGES, dtype=np.float64)
+        n = np.zeros(NUM_STAGES, dtype=np.int64)
+        _check(self.lib.leea_profile_read(self._h, _hp(ms), _hp(n)))
+        return {STAGES[k]: (float(ms[k]), int(n[k])) for k in range(NUM_STAGES)}

@@ -1,0 +1,102 @@
+"""The CUDA library builds for sm_103a, loads, exports every entry point that
+include/leea.h declares, and its host-only logic (layout, operator counts,
+argument checking) agrees with the oracle.  No compute call is made."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1806_09819_gb300 import build as B
+from paper_1806_09819_gb300 import leea
+
+HEADER = os.path.join(B.INCLUDE, "leea.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return leea.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(leea_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_what_the_binding_binds():
+    assert declared_functions() == sorted(leea.exported_symbols())
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    # and nothing else under the leea_ prefix is required by the binding
+    import subprocess
+    out = subprocess.run(["nm", "-D", "--defined-only", B.LIB], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (leea_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_default_params_are_the_papers(lib, oracle_mod):
+    d = leea.leea_default_params()
+    o = oracle_mod.Params()
+    for f in ("xo_op", "sel_op", "tour_k", "n_elite", "init", "precision"):
+        assert getattr(d, f) == getattr(o, f)
+    for f in ("xo_gene_p", "rho", "p_e", "p_c", "sigma", "mut_rate", "alpha"):
+        assert np.float32(getattr(d, f)) == np.float32(getattr(o, f))
+
+
+@pytest.mark.parametrize("dims", [[784, 112, 10], [784, 32, 10], [2, 2, 2], [196, 256, 128, 64, 10], [3, 1]])
+def test_layout_matches_oracle(lib, oracle_mod, dims):
+    c = leea.leea_num_params(dims)
+    assert c == oracle_mod.num_params(dims)
+    cp = leea.leea_padded_params(dims)
+    assert cp % 32 == 0 and c <= cp < c + 32
+
+
+def test_invalid_dims(lib):
+    assert leea.leea_num_params([784]) == -1
+    assert leea.leea_num_params([784, 0, 10]) == -1
+
+
+def test_counts_match_oracle(lib, oracle_mod):
+    rng = np.random.default_rng(0)
+    for _ in range(300):
+        pop = int(rng.integers(1, 5000))
+        kw = dict(p_e=float(rng.uniform(0, 0.3)), p_c=float(rng.uniform(0, 1)), rho=float(rng.uniform(0.01, 1)),
+                  n_elite=int(rng.choice([-1, 0, 1, 3])))
+        assert leea.leea_counts(pop, leea.Params(**kw)) == oracle_mod.counts(pop, oracle_mod.Params(**kw))
+
+
+def test_argument_errors_are_reported_before_any_work(lib):
+    with pytest.raises(leea.LeeaError) as e:
+        leea.leea_counts(0, leea.Params())
+    assert e.value.status == leea.EINVAL and "pop" in str(e.value)
+    with pytest.raises(leea.LeeaError) as e:
+        leea.leea_counts(10, leea.Params(rho=0.0))
+    assert "rho" in str(e.value)
+    # leea_create validates before touching the device.
+    d = np.array([784, 112, 10], dtype=np.int32)
+    h = ctypes.c_void_p()
+    bad = leea.Params(sigma=-1.0).c_struct()
+    rc = lib.leea_create(10, d.ctypes.data_as(ctypes.c_void_p), 3, ctypes.byref(bad), 1, None, ctypes.byref(h))
+    assert rc == leea.EINVAL and h.value is None
+    assert b"sigma" in lib.leea_last_error()
+    d4 = np.array([196, 256, 128, 64, 10], dtype=np.int32)
+    good = leea.Params().c_struct()
+    rc = lib.leea_create(10, d4.ctypes.data_as(ctypes.c_void_p), 5, ctypes.byref(good), 1, None, ctypes.byref(h))
+    assert rc == leea.EINVAL
+
+
+def test_oracle_and_library_share_no_code():
+    # The two sides are separate translation units with separate headers.
+    csrc = B.CSRC
+    for f in os.listdir(csrc):
+        text = open(os.path.join(csrc, f)).read()
+        assert "leea_oracle" not in text and "oracle/" not in text
+    here = os.path.dirname(os.path.abspath(__file__))
+    otext = open(os.path.join(here, "..", "oracle", "leea_oracle.c")).read()
+    assert "philox.cuh" not in otext and "leea.h\"" not in otext
