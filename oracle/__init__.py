@@ -13,6 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 from dataclasses import dataclass, fields
 
@@ -31,12 +32,20 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (portable flags: same results on x86 and Arm)."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
+    stamp_path = os.path.join(os.path.dirname(_OUT), "STAMP")
+    try:
+        with open(stamp_path) as fh:
+            same_host = fh.read() == platform.machine()
+    except OSError:
+        same_host = False
+    if force or not same_host or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < newest:
         tmp = _OUT + f".tmp{os.getpid()}"
         subprocess.check_call([
             "gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
             "-Wall", "-Wextra", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _OUT)
+        with open(stamp_path, "w") as fh:
+            fh.write(platform.machine())
     return _OUT
 
 

@@ -10,6 +10,7 @@ from __future__ import annotations
 import concurrent.futures
 import glob
 import os
+import platform
 import shutil
 import subprocess
 
@@ -48,9 +49,20 @@ def _stale(target: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _stamp() -> str:
+    return f"{platform.machine()} {nvcc()}"
+
+
 def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
     """Compile every CUDA source and link ``libleea.so``; returns its path."""
     os.makedirs(OUT_DIR, exist_ok=True)
+    stamp_path = os.path.join(OUT_DIR, "STAMP")
+    try:
+        with open(stamp_path) as fh:
+            same_host = fh.read() == _stamp()
+    except OSError:
+        same_host = False
+    force = force or not same_host  # objects built on another machine are never reused
     headers = _headers()
     srcs = _sources()
     flags = NVCC_FLAGS + (extra_flags or [])
@@ -80,6 +92,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             print(res.stdout, res.stderr)
             raise RuntimeError("linking libleea.so failed")
         os.replace(tmp, LIB)
+    with open(stamp_path, "w") as fh:
+        fh.write(_stamp())
     return LIB
 
 

@@ -31,11 +31,20 @@ __global__ void __launch_bounds__(kBreedThreads) breed_kernel(BreedArgs a, int32
     const int32_t j = blockIdx.x / chunks;
     const int32_t chunk = blockIdx.x - j * chunks;
     const int32_t kd = kind[j];
-    const float4* A = reinterpret_cast<const float4*>(parents + static_cast<int64_t>(par1[j]) * a.c_pad);
-    const float4* B = reinterpret_cast<const float4*>(parents + static_cast<int64_t>(par2[j]) * a.c_pad);
+    const int32_t i1 = par1[j], i2 = par2[j];
     float4* O = reinterpret_cast<float4*>(children + static_cast<int64_t>(j) * a.c_pad);
     const int64_t nq = a.c_pad >> 2;
     const int64_t q0 = static_cast<int64_t>(chunk) * (kBreedThreads * kBreedUnroll) + threadIdx.x;
+    if (i1 < 0 || i1 >= a.pop || i2 < 0 || i2 >= a.pop) {
+        // A parent index outside the population: the child becomes NaN (its
+        // fitness then ranks last) instead of reading out of bounds.
+        const float nan = __int_as_float(0x7FC00000);
+        for (int u = 0; u < kBreedUnroll; ++u)
+            if (q0 + u * kBreedThreads < nq) O[q0 + u * kBreedThreads] = make_float4(nan, nan, nan, nan);
+        return;
+    }
+    const float4* A = reinterpret_cast<const float4*>(parents + static_cast<int64_t>(i1) * a.c_pad);
+    const float4* B = reinterpret_cast<const float4*>(parents + static_cast<int64_t>(i2) * a.c_pad);
 
     float4 va[kBreedUnroll], vb[kBreedUnroll];
 #pragma unroll
