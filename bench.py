@@ -258,7 +258,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
     ys = torch.from_numpy(ytr[idx]).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    st = leea.LeeaState(POP, DIMS, leea.Params(**PARAMS), seed=1000 + rank, stream=stream)
+    st = leea.LeeaState(POP, DIMS, leea.Params(**PARAMS, eval_path=args.eval_path), seed=1000 + rank, stream=stream)
     for k in range(warmup + 1):  # the first call evaluates the initial population
         st.leea_generation(xs[k], ys[k])
     torch.cuda.synchronize(dev)
@@ -309,10 +309,14 @@ def run_native(args, rank: int, world: int, local_rank: int):
     n_e, n_c, n_m, _ = leea.leea_counts(POP, leea.Params(**PARAMS))
     c = leea.leea_num_params(DIMS)
     d0, h, d_out = DIMS
+    tensor_eval = args.eval_path != leea.EVAL_SIMT
     work = {
         "breed": ("hbm", 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) / 1e9, "GB/s", hbm_peak),
-        "evaluate": ("alu", 2.0 * POP * BATCH * (d0 * h + h * d_out) / 1e12, "TFLOP/s",
-                     SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12),
+        # tensor-core path: the per-individual weight stream (X stays in L2);
+        # CUDA-core path: FP32 FFMA work
+        "evaluate": (("hbm", 4.0 * c * POP / 1e9, "GB/s", hbm_peak) if tensor_eval else
+                     ("alu", 2.0 * POP * BATCH * (d0 * h + h * d_out) / 1e12, "TFLOP/s",
+                      SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12)),
         "rank": ("latency", None, None, None),
         "select": ("latency", None, None, None),
     }
@@ -328,17 +332,21 @@ def run_native(args, rank: int, world: int, local_rank: int):
         kernels[name] = entry
     dom = max(("breed", "evaluate"), key=lambda n: prof[n][0])
     kd = kernels[dom]
-    src = {"breed": "leea_breed.cu", "evaluate": "leea_eval_simt.cu"}[dom]
+    src = {"breed": "leea_breed.cu", "evaluate": "leea_eval_tc.cu" if tensor_eval else "leea_eval_simt.cu"}[dom]
     tr = TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == _src_sha(src) else None
     roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
                 "peak_source": f"{peak_src} ({'HBM copy' if kd['unit'] == 'GB/s' else 'FP32 FFMA: 152 SM x 128 lanes x 2 x max SM clock'})"}
+    if tensor_eval:
+        kernels["evaluate"]["tensor_tflops_3xtf32"] = (3 * 2.0 * POP * 128 * 800 * h / 1e12) / (
+            prof["evaluate"][0] / max(1, prof["evaluate"][1]) / 1000.0)
 
     line = {"metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps,
             "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "eval_kernel": "tcgen05 3xTF32" if tensor_eval else "CUDA-core FP32 FFMA",
                        "l2": "inputs larger than L2 (2 population buffers of 356 MB), no flush"},
             "network_samples_per_sec": gen_per_s * POP * BATCH,
             "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())), "roofline": roofline,
@@ -362,6 +370,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-children", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--eval-path", type=int, default=0, help="0 auto (tensor cores), 1 CUDA-core FP32, 2 tensor")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -93,7 +93,16 @@ typedef struct {
     float alpha;        /* inheritance weight alpha on the new fitness; 1     */
     int32_t init;       /* 0 N(0, 1/fan_in), 1 Glorot-uniform (Section 4.1)   */
     int32_t precision;  /* 0 FP32 (only value accepted by this version)       */
+    int32_t eval_path;  /* LEEA_EVAL_AUTO / _SIMT / _TENSOR, see below        */
 } leea_params;
+
+/* Evaluation kernels.  AUTO takes the tensor-core kernel when the shape
+ * allows it (d_0 % 4 == 0, h % 16 == 0, h <= 256, d_out <= 16, 16-byte aligned
+ * buffers) and the CUDA-core kernel otherwise.  SIMT: exact FP32 FFMA on the
+ * CUDA cores.  TENSOR: tcgen05 tensor cores with a three-term TF32 split
+ * (X_hi W_hi + X_hi W_lo + X_lo W_hi, FP32 accumulation), which is within
+ * ~1e-6 relative of FP32; LEEA_EINVAL if the shape does not allow it. */
+enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2 };
 
 /* Fills *out with the paper's defaults (Section 4). */
 leea_status leea_default_params(leea_params* out);
@@ -168,12 +177,19 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
  * f_inh_dev is NULL (the first evaluation).  Reductions have a fixed order,
  * so identical individuals get bitwise identical results.
  * n_dims must be 3 (d_0-h-d_out with d_out <= 32).  f_adj_dev and
- * correct_dev may be NULL; f_raw_dev may not. */
+ * correct_dev may be NULL; f_raw_dev may not.  eval_path: LEEA_EVAL_*. */
 leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
                           const float* pop_dev, const float* x_dev, const int32_t* y_dev,
                           int32_t batch, float alpha, const float* f_inh_dev,
                           float* f_raw_dev, float* f_adj_dev, int32_t* correct_dev,
-                          void* stream);
+                          int32_t eval_path, void* stream);
+
+/* Synchronises `stream`, then reads and clears this device's status word.
+ * Returns LEEA_ETIMEOUT if a kernel's bounded wait gave up since the last
+ * check (its outputs are then invalid), LEEA_OK otherwise.  flags_out, if
+ * not NULL, receives the raw bits.  The state object's synchronising calls
+ * (leea_fitness, leea_best_params, ...) perform the same check. */
+leea_status leea_device_status(void* stream, uint32_t* flags_out);
 
 /* Diagnostic: words n0 .. n0+count-1 of the Philox stream (tag, gen, ent),
  * written to out_dev (uint32[count]).  Lets a caller check the generator. */

@@ -88,6 +88,8 @@ leea_status check_params(const leea_params* p)
     if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
     if (p->init != 0 && p->init != 1) return fail(LEEA_EINVAL, "init must be 0 or 1");
     if (p->precision != 0) return fail(LEEA_EINVAL, "precision must be 0 (FP32)");
+    if (p->eval_path < LEEA_EVAL_AUTO || p->eval_path > LEEA_EVAL_TENSOR)
+        return fail(LEEA_EINVAL, "eval_path must be LEEA_EVAL_AUTO, _SIMT or _TENSOR");
     return LEEA_OK;
 }
 
@@ -109,6 +111,66 @@ void counts_of(int32_t pop, const leea_params* p, int32_t* ne, int32_t* nc, int3
 }
 
 constexpr int32_t kMaxPop = 1 << 24;
+
+// Status word written by kernels whose waits are bounded (one per device).
+__device__ unsigned int g_device_status = 0;
+
+// Device address of g_device_status on the current device (looked up once per
+// device, with that device current).
+unsigned int* device_status_ptr()
+{
+    static unsigned int* cache[64] = { nullptr };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    if (!cache[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+        cache[dev] = static_cast<unsigned int*>(p);
+    }
+    return cache[dev];
+}
+
+// Synchronises `stream`, reads and clears the status word.
+leea_status check_device_status(cudaStream_t stream, uint32_t* flags_out)
+{
+    cudaError_t err = cudaStreamSynchronize(stream);
+    if (err != cudaSuccess) return cuda_fail(err, "stream synchronise");
+    unsigned int* p = device_status_ptr();
+    if (!p) return fail(LEEA_ECUDA, "device status word unavailable");
+    unsigned int v = 0;
+    err = cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return cuda_fail(err, "status read");
+    if (v) {
+        const unsigned int zero = 0;
+        err = cudaMemcpy(p, &zero, sizeof(zero), cudaMemcpyHostToDevice);
+        if (err != cudaSuccess) return cuda_fail(err, "status clear");
+    }
+    if (flags_out) *flags_out = v;
+    if (v & kStatusEvalTimeout)
+        return fail(LEEA_ETIMEOUT, "a tensor-core evaluation wait timed out; its fitness values are invalid");
+    return LEEA_OK;
+}
+
+// Runs the evaluation kernel that `path` selects (LEEA_EVAL_*).
+leea_status dispatch_eval(const NetLayout& net, int32_t pop, const float* pop_dev, const float* x,
+                          const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                          float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream)
+{
+    const bool tc_ok = eval_tc_supported(net, batch, pop_dev, x);
+    if (path == LEEA_EVAL_TENSOR && !tc_ok)
+        return fail(LEEA_EINVAL, "tensor-core evaluation needs d_0 %% 4 == 0, h %% 16 == 0, h <= 256, "
+                                 "d_out <= 16 and 16-byte aligned population and x");
+    cudaError_t err;
+    if (tc_ok && path != LEEA_EVAL_SIMT) {
+        unsigned int* status = device_status_ptr();
+        if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+        err = launch_eval_tc(net, pop, pop_dev, x, y, batch, alpha, f_inh, f_raw, f_adj, correct, status, stream);
+    } else {
+        err = launch_eval_simt(net, pop, pop_dev, x, y, batch, alpha, f_inh, f_raw, f_adj, correct, stream);
+    }
+    if (err != cudaSuccess) return cuda_fail(err, "evaluate kernel");
+    return LEEA_OK;
+}
 
 leea_status check_pop(int32_t pop)
 {
@@ -149,6 +211,7 @@ leea_status leea_default_params(leea_params* out)
     out->alpha = 1.0f;
     out->init = 0;
     out->precision = 0;
+    out->eval_path = LEEA_EVAL_AUTO;
     return LEEA_OK;
 }
 
@@ -280,7 +343,7 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims, const l
 leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims, const float* pop_dev,
                           const float* x_dev, const int32_t* y_dev, int32_t batch, float alpha,
                           const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
-                          int32_t* correct_dev, void* stream)
+                          int32_t* correct_dev, int32_t eval_path, void* stream)
 {
     leea_status st = check_pop(pop);
     if (st) return st;
@@ -289,10 +352,14 @@ leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims, cons
     if ((st = check_eval_shape(net, batch))) return st;
     if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
     if (!pop_dev || !x_dev || !y_dev || !f_raw_dev) return fail(LEEA_EINVAL, "NULL device pointer");
-    LEEA_CUDA_TRY(launch_eval_simt(net, pop, pop_dev, x_dev, y_dev, batch, alpha, f_inh_dev, f_raw_dev,
-                                   f_adj_dev, correct_dev, static_cast<cudaStream_t>(stream)),
-                  "evaluate kernel");
-    return LEEA_OK;
+    if (eval_path < LEEA_EVAL_AUTO || eval_path > LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "bad eval_path");
+    return dispatch_eval(net, pop, pop_dev, x_dev, y_dev, batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev,
+                         correct_dev, eval_path, static_cast<cudaStream_t>(stream));
+}
+
+leea_status leea_device_status(void* stream, uint32_t* flags_out)
+{
+    return check_device_status(static_cast<cudaStream_t>(stream), flags_out);
 }
 
 leea_status leea_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t n0,
@@ -509,10 +576,11 @@ leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_
     }
     {
         StageScope sc(s, 3);
-        LEEA_CUDA_TRY(launch_eval_simt(s->net, s->pop, s->popbuf[s->cur], x_dev, y_dev, batch, s->prm.alpha,
-                                       first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct, s->stream),
-                      "evaluate kernel");
+        st = dispatch_eval(s->net, s->pop, s->popbuf[s->cur], x_dev, y_dev, batch, s->prm.alpha,
+                           first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct, s->prm.eval_path,
+                           s->stream);
         sc.done();
+        if (st) return st;
     }
     s->evaluated = true;
     return LEEA_OK;
@@ -548,8 +616,7 @@ leea_status leea_generation_host(leea_state* s, const float* x_host, const int32
 static leea_status copy_out(leea_state* s, void* dst, const void* src, size_t bytes, const char* what)
 {
     LEEA_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s->stream), what);
-    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), what);
-    return LEEA_OK;
+    return check_device_status(s->stream, nullptr);
 }
 
 leea_status leea_fitness(leea_state* s, float* f_adj_host, int32_t* correct_host)
@@ -564,8 +631,7 @@ leea_status leea_fitness(leea_state* s, float* f_adj_host, int32_t* correct_host
         LEEA_CUDA_TRY(cudaMemcpyAsync(correct_host, s->correct, sizeof(int32_t) * s->pop, cudaMemcpyDeviceToHost,
                                       s->stream),
                       "correct copy");
-    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "fitness sync");
-    return LEEA_OK;
+    return check_device_status(s->stream, nullptr);
 }
 
 leea_status leea_raw_fitness(leea_state* s, float* f_raw_host)

@@ -9,6 +9,9 @@ namespace leea {
 
 constexpr int kMaxLayers = 15;
 
+// Bits of the device status word (set by kernels, read and cleared by the host).
+constexpr unsigned int kStatusEvalTimeout = 1u;  // a bounded mbarrier wait of the tensor-core eval gave up
+
 // Per-layer offsets of a net, computed on the host (logical gene order of
 // Section 3.2: W_l rows out x in, then b_l).
 struct NetLayout {
@@ -52,6 +55,12 @@ cudaError_t launch_eval_simt(const NetLayout& net, int32_t pop, const float* pop
                              const float* x, const int32_t* y, int32_t batch, float alpha,
                              const float* f_inh, float* f_raw, float* f_adj, int32_t* correct,
                              cudaStream_t stream);
+// Evaluation on the tcgen05 tensor cores (3xTF32), d_0-h-d_out with d_0 % 4 == 0,
+// h % 16 == 0, h <= 256, d_out <= 16 and 16-byte aligned population and x.
+bool eval_tc_supported(const NetLayout& net, int32_t batch, const float* pop_dev, const float* x);
+cudaError_t launch_eval_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const float* x,
+                           const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                           float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream);
 cudaError_t launch_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
                                uint32_t n0, int64_t count, uint32_t* out, cudaStream_t stream);
 cudaError_t launch_normal_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,

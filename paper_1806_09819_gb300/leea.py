@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "_build", "libleea.so")
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = range(6)
 TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
 KIND_ELITE, KIND_CROSSOVER, KIND_MUTATION = 0, 1, 2
+EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR = 0, 1, 2
 NUM_STAGES = 4
 STAGES = ("rank", "select", "breed", "evaluate")
 
@@ -38,7 +39,7 @@ class leea_params(ctypes.Structure):
         ("p_e", ctypes.c_float), ("p_c", ctypes.c_float),
         ("sigma", ctypes.c_float), ("mut_rate", ctypes.c_float),
         ("alpha", ctypes.c_float), ("init", ctypes.c_int32),
-        ("precision", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("eval_path", ctypes.c_int32),
     ]
 
 
@@ -58,6 +59,7 @@ class Params:
     alpha: float = 1.0
     init: int = 0
     precision: int = 0
+    eval_path: int = 0  # EVAL_AUTO, EVAL_SIMT or EVAL_TENSOR
 
     def c_struct(self) -> leea_params:
         return leea_params(**{f.name: getattr(self, f.name) for f in fields(Params)})
@@ -87,7 +89,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_rank": [i32, vp, vp, vp],
         "leea_select": [i32, P(leea_params), vp, vp, u64, u32, vp, vp, vp, vp, vp],
         "leea_breed": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp],
-        "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, vp],
+        "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, i32, vp],
+        "leea_device_status": [vp, P(u32)],
         "leea_philox_fill": [u64, u32, u32, u32, u32, i64, vp, vp],
         "leea_normal_fill": [u64, u32, u32, u32, u32, i64, vp, vp],
         "leea_create": [i32, vp, i32, P(leea_params), u64, vp, P(vp)],
@@ -122,6 +125,7 @@ def exported_symbols() -> list[str]:
     """Names of the entry points the binding expects the library to export."""
     return ["leea_default_params", "leea_num_params", "leea_padded_params", "leea_counts",
             "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_evaluate",
+            "leea_device_status",
             "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
             "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
             "leea_get_population", "leea_set_population", "leea_set_fitness", "leea_set_generation",
@@ -212,11 +216,18 @@ def leea_breed(pop: int, dims, prm: Params, seed: int, gen: int, parents_dev, pa
 
 
 def leea_evaluate(pop: int, dims, pop_dev, x_dev, y_dev, batch: int, alpha: float, f_inh_dev,
-                  f_raw_dev, f_adj_dev=None, correct_dev=None, stream=None) -> None:
+                  f_raw_dev, f_adj_dev=None, correct_dev=None, eval_path: int = EVAL_AUTO, stream=None) -> None:
     d = _dims(dims)
     _check(load_library().leea_evaluate(pop, _hp(d), len(d), _dptr(pop_dev), _dptr(x_dev), _dptr(y_dev), batch,
                                         float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev), _dptr(f_adj_dev),
-                                        _dptr(correct_dev), _stream(stream)))
+                                        _dptr(correct_dev), int(eval_path), _stream(stream)))
+
+
+def leea_device_status(stream=None) -> int:
+    """Synchronises, reads and clears the device status word; raises on a timeout flag."""
+    flags = ctypes.c_uint32()
+    _check(load_library().leea_device_status(_stream(stream), ctypes.byref(flags)))
+    return flags.value
 
 
 def leea_philox_fill(seed: int, tag: int, gen: int, ent: int, n0: int, count: int, out_dev, stream=None) -> None:

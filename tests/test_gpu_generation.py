@@ -44,7 +44,7 @@ def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=11, gen0=3, sample=No
     f_adj, cor = st.leea_fitness(with_correct=True)
     f_raw = st.leea_raw_fitness()
 
-    o_prm = oracle_mod.Params(**prm)
+    o_prm = oracle_mod.Params(**{k: v for k, v in prm.items() if k != "eval_path"})
     f0d = f0.astype(np.float64)
     o_order = oracle_mod.rank(f0d)
     np.testing.assert_array_equal(order, o_order)
@@ -68,8 +68,10 @@ def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=11, gen0=3, sample=No
     st.close()
 
 
-def test_lockstep_small_config(gpu, oracle_mod):
-    _lockstep(gpu, oracle_mod, CONFIG_SMALL["dims"], CONFIG_SMALL["pop"], CONFIG_SMALL["batch"], CONFIG_SMALL["prm"])
+@pytest.mark.parametrize("path", [1, 2])
+def test_lockstep_small_config(gpu, oracle_mod, path):
+    prm = dict(CONFIG_SMALL["prm"], eval_path=path)
+    _lockstep(gpu, oracle_mod, CONFIG_SMALL["dims"], CONFIG_SMALL["pop"], CONFIG_SMALL["batch"], prm)
 
 
 @pytest.mark.parametrize("prm", [dict(sigma=0.5), dict(sel_op=1, tour_k=2, xo_op=1, alpha=0.5),
@@ -78,12 +80,13 @@ def test_lockstep_2_2_2(gpu, oracle_mod, prm):
     _lockstep(gpu, oracle_mod, [2, 2, 2], 4, 8, prm)
 
 
-def test_lockstep_full_size_sampled(gpu, oracle_mod):
+@pytest.mark.parametrize("path", [1, 2])
+def test_lockstep_full_size_sampled(gpu, oracle_mod, path):
     # Full workload; the oracle recomputes a sample of children (the elite,
     # crossover and mutation children, first and last) one by one.
     sample = np.array([0, 1, 2, 250, 499, 500, 501, 502, 777, 998, 999])
-    _lockstep(gpu, oracle_mod, CONFIG_FULL["dims"], CONFIG_FULL["pop"], CONFIG_FULL["batch"], CONFIG_FULL["prm"],
-              sample=sample)
+    prm = dict(CONFIG_FULL["prm"], eval_path=path)
+    _lockstep(gpu, oracle_mod, CONFIG_FULL["dims"], CONFIG_FULL["pop"], CONFIG_FULL["batch"], prm, sample=sample)
 
 
 def test_first_generation_evaluates_the_initial_population(gpu, oracle_mod):

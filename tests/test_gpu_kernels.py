@@ -172,11 +172,27 @@ EVAL_CASES = [
     ([2, 2, 2], 4, 8), ([784, 32, 10], 32, 16), ([784, 112, 10], 64, 100), ([784, 37, 10], 5, 19),
     ([5, 3, 4], 6, 1), ([784, 200, 10], 3, 129), ([784, 112, 10], 4, 512), ([784, 16, 10], 7, 33),
     ([100, 300, 32], 3, 70), ([784, 256, 10], 2, 256),
+    # shapes for the tensor-core kernel: ragged sample tiles, K < 32, P > SM count, d_out = 16
+    ([784, 48, 10], 3, 128), ([784, 112, 10], 2, 129), ([16, 16, 2], 5, 7), ([784, 128, 16], 4, 77),
+    ([784, 112, 10], 400, 100), ([784, 112, 10], 1, 1), ([36, 64, 10], 9, 300),
 ]
 
 
-@pytest.mark.parametrize("dims,pop,batch", EVAL_CASES, ids=lambda v: str(v))
-def test_evaluate_matches_oracle(gpu, oracle_mod, dims, pop, batch):
+def _tc_shape(dims):
+    return len(dims) == 3 and dims[0] % 4 == 0 and dims[1] % 16 == 0 and dims[1] <= 256 and dims[2] <= 16
+
+
+def _eval_params():
+    out = []
+    for dims, pop, batch in EVAL_CASES:
+        out.append(pytest.param(dims, pop, batch, 1, id=f"simt-{dims}-{pop}-{batch}"))
+        if _tc_shape(dims):
+            out.append(pytest.param(dims, pop, batch, 2, id=f"tensor-{dims}-{pop}-{batch}"))
+    return out
+
+
+@pytest.mark.parametrize("dims,pop,batch,path", _eval_params())
+def test_evaluate_matches_oracle(gpu, oracle_mod, dims, pop, batch, path):
     torch = _torch()
     c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
     popv = synthetic.random_population(pop, c, seed=c + batch, scale=0.15)
@@ -193,8 +209,8 @@ def test_evaluate_matches_oracle(gpu, oracle_mod, dims, pop, batch):
     f_raw = torch.empty(pop, dtype=torch.float32, device="cuda")
     f_adj = torch.empty_like(f_raw)
     cor = torch.empty(pop, dtype=torch.int32, device="cuda")
-    gpu.leea_evaluate(pop, dims, pd, xd, yd, batch, alpha, fi_d, f_raw, f_adj, cor)
-    torch.cuda.synchronize()
+    gpu.leea_evaluate(pop, dims, pd, xd, yd, batch, alpha, fi_d, f_raw, f_adj, cor, eval_path=path)
+    assert gpu.leea_device_status() == 0
     f_ref, cor_ref, logits = oracle_mod.evaluate(popv.astype(np.float64), dims, x.astype(np.float64), y,
                                                  want_logits=True)
     assert_fitness_close(f_raw.cpu().numpy(), f_ref)
@@ -202,12 +218,26 @@ def test_evaluate_matches_oracle(gpu, oracle_mod, dims, pop, batch):
     adj_ref = oracle_mod.inherit(float(np.float32(alpha)), f_inh.astype(np.float64), f_ref, first=False)
     assert_fitness_close(f_adj.cpu().numpy(), adj_ref, "f_adj")
     # First evaluation (no f_inh): f_adj = f exactly.
-    gpu.leea_evaluate(pop, dims, pd, xd, yd, batch, alpha, None, f_raw, f_adj, cor)
+    gpu.leea_evaluate(pop, dims, pd, xd, yd, batch, alpha, None, f_raw, f_adj, cor, eval_path=path)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(f_adj.cpu().numpy(), f_raw.cpu().numpy())
 
 
-def test_evaluate_zero_weights_and_clones(gpu, oracle_mod):
+def test_tensor_path_rejects_unsupported_shapes(gpu):
+    torch = _torch()
+    dims = [784, 37, 10]
+    cp = gpu.leea_padded_params(dims)
+    pd = torch.zeros((2, cp), dtype=torch.float32, device="cuda")
+    x = torch.zeros((4, 784), dtype=torch.float32, device="cuda")
+    y = torch.zeros(4, dtype=torch.int32, device="cuda")
+    f = torch.empty(2, dtype=torch.float32, device="cuda")
+    with pytest.raises(gpu.LeeaError) as e:
+        gpu.leea_evaluate(2, dims, pd, x, y, 4, 1.0, None, f, eval_path=gpu.EVAL_TENSOR)
+    assert e.value.status == gpu.EINVAL
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_evaluate_zero_weights_and_clones(gpu, oracle_mod, path):
     torch = _torch()
     dims, pop, batch = [784, 112, 10], 6, 100
     c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
@@ -218,12 +248,29 @@ def test_evaluate_zero_weights_and_clones(gpu, oracle_mod):
     f_raw = torch.empty(pop, dtype=torch.float32, device="cuda")
     cor = torch.empty(pop, dtype=torch.int32, device="cuda")
     gpu.leea_evaluate(pop, dims, pd, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), batch, 1.0, None,
-                      f_raw, None, cor)
+                      f_raw, None, cor, eval_path=path)
     torch.cuda.synchronize()
     f = f_raw.cpu().numpy()
     assert np.all(np.abs(f[:3] + np.log(10.0)) < 1e-6)
     assert (cor.cpu().numpy()[:3] == (y == 0).sum()).all()
     assert f[3] == f[4] == f[5]  # bitwise: fixed reduction order
+
+
+def test_tensor_and_simt_paths_agree_at_full_size(gpu):
+    torch = _torch()
+    dims, pop, batch = [784, 112, 10], 1000, 100
+    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    pd = torch.empty((pop, cp), dtype=torch.float32, device="cuda")
+    gpu.leea_init_population(pop, dims, 0, 99, pd)
+    x, y = synthetic.make_split(batch, seed=8)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    out = {}
+    for path in (1, 2):
+        f = torch.empty(pop, dtype=torch.float32, device="cuda")
+        gpu.leea_evaluate(pop, dims, pd, xd, yd, batch, 1.0, None, f, eval_path=path)
+        out[path] = f.cpu().numpy()
+    assert gpu.leea_device_status() == 0
+    assert_fitness_close(out[2], out[1].astype(np.float64), "tensor vs simt")
 
 
 def test_evaluate_bad_label_gives_nan_and_errors(gpu):
