@@ -252,15 +252,24 @@ def run_native(args, rank: int, world: int, local_rank: int):
 
     steps, warmup = args.steps, args.warmup
     (xtr, ytr), _ = synthetic.dataset(n_train=60000, n_test=1)
+    u8 = args.input == "u8"
+    if u8:  # the images as their 8-bit levels k (x = k / 255), as MNIST stores them
+        xtr = synthetic.to_levels(xtr)
     n_batches = warmup + 1 + steps
     idx = synthetic.batch_indices(len(ytr), BATCH, n_batches, seed=synthetic.BATCH_SEED + rank)
     xs = torch.from_numpy(xtr[idx]).to(dev)       # [n_batches, B, 784], resident in HBM
     ys = torch.from_numpy(ytr[idx]).to(dev)
     stream = torch.cuda.current_stream(dev)
 
+    def gen(st, k):
+        if u8:
+            st.leea_generation_u8(xs[k], ys[k], 255.0)
+        else:
+            st.leea_generation(xs[k], ys[k])
+
     st = leea.LeeaState(POP, DIMS, leea.Params(**PARAMS, eval_path=args.eval_path), seed=1000 + rank, stream=stream)
     for k in range(warmup + 1):  # the first call evaluates the initial population
-        st.leea_generation(xs[k], ys[k])
+        gen(st, k)
     torch.cuda.synchronize(dev)
     st.leea_profile_enable(True)
     st.leea_profile_read()
@@ -274,7 +283,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for k in range(steps):
-        st.leea_generation(xs[warmup + 1 + k], ys[warmup + 1 + k])
+        gen(st, warmup + 1 + k)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(dist, dev)
@@ -295,13 +304,16 @@ def run_native(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for k in range(e2e_steps):
-        st.leea_generation_host(xh[k], yh[k])
+        if u8:
+            st.leea_generation_u8_host(xh[k], yh[k], 255.0)
+        else:
+            st.leea_generation_host(xh[k], yh[k])
         f_host = st.leea_fitness()                    # device->host read of the step's result
     t_e2e = time.perf_counter() - t0
     barrier(dist, dev)
     t_e2e = max_over_ranks(t_e2e, dist, dev)
     e2e = {"value": world * e2e_steps / t_e2e, "unit": "generations/s",
-           "h2d_bytes_per_step": int(xh[0].numel() * 4 + yh[0].numel() * 4),
+           "h2d_bytes_per_step": int(xh[0].numel() * xh.element_size() + yh[0].numel() * 4),
            "d2h_bytes_per_step": int(f_host.nbytes), "steps": e2e_steps}
 
     # ---- roofline of the dominant kernel ----
@@ -332,21 +344,25 @@ def run_native(args, rank: int, world: int, local_rank: int):
         kernels[name] = entry
     dom = max(("breed", "evaluate"), key=lambda n: prof[n][0])
     kd = kernels[dom]
-    src = {"breed": "leea_breed.cu", "evaluate": "leea_eval_tc.cu" if tensor_eval else "leea_eval_simt.cu"}[dom]
+    src = {"breed": "leea_breed.cu",
+           "evaluate": ("leea_eval_u8.cu" if u8 else "leea_eval_tc.cu") if tensor_eval else "leea_eval_simt.cu"}[dom]
     tr = TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == _src_sha(src) else None
     roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
                 "peak_source": f"{peak_src} ({'HBM copy' if kd['unit'] == 'GB/s' else 'FP32 FFMA: 152 SM x 128 lanes x 2 x max SM clock'})"}
-    if tensor_eval:
-        kernels["evaluate"]["tensor_tflops_3xtf32"] = (3 * 2.0 * POP * 128 * 800 * h / 1e12) / (
+    if tensor_eval:  # tensor-core work actually issued (3 passes, M padded to 128, K to the MMA step)
+        k_pad = 784 if u8 else 800
+        kernels["evaluate"]["tensor_tflops_issued"] = (3 * 2.0 * POP * 128 * k_pad * h / 1e12) / (
             prof["evaluate"][0] / max(1, prof["evaluate"][1]) / 1000.0)
 
     line = {"metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps,
             "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "eval_kernel": "tcgen05 3xTF32" if tensor_eval else "CUDA-core FP32 FFMA",
+                       "input": "uint8 levels k, x = k/255" if u8 else "float32 x",
+                       "eval_kernel": (("tcgen05 BF16 exact pieces, batch in TMEM" if u8 else "tcgen05 3xTF32")
+                                       if tensor_eval else "CUDA-core FP32 FFMA"),
                        "l2": "inputs larger than L2 (2 population buffers of 356 MB), no flush"},
             "network_samples_per_sec": gen_per_s * POP * BATCH,
             "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())), "roofline": roofline,
@@ -371,6 +387,8 @@ def main():
     ap.add_argument("--cpu-children", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eval-path", type=int, default=0, help="0 auto (tensor cores), 1 CUDA-core FP32, 2 tensor")
+    ap.add_argument("--input", choices=["u8", "f32"], default="u8",
+                    help="minibatch as 8-bit levels (x = k/255, the images' own encoding) or as float32")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

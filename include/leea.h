@@ -184,6 +184,21 @@ leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
                           float* f_raw_dev, float* f_adj_dev, int32_t* correct_dev,
                           int32_t eval_path, void* stream);
 
+/* leea_evaluate for minibatches of 8-bit levels: x_u8_dev is uint8[batch][d_0]
+ * and the input value is x = k / x_div (x_div = 255 for images stored as
+ * bytes, as MNIST's are).  The tensor-core path needs batch <= 128,
+ * d_0 % 4 == 0, h % 16 == 0, h + round_up(8 ceil(d_0 / 16), 16) <= 512 and
+ * d_out <= 16.  It forms layer 1 from exact products: the levels are exact
+ * in BF16 and each weight is split exactly into three BF16 pieces, so only
+ * the tensor core's FP32 accumulation rounds.  Otherwise, or with
+ * LEEA_EVAL_SIMT, the CUDA-core kernel computes x = k / x_div in FP32.
+ * x_div must be finite and > 0. */
+leea_status leea_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims,
+                             const float* pop_dev, const uint8_t* x_u8_dev, float x_div,
+                             const int32_t* y_dev, int32_t batch, float alpha,
+                             const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
+                             int32_t* correct_dev, int32_t eval_path, void* stream);
+
 /* Synchronises `stream`, then reads and clears this device's status word.
  * Returns LEEA_ETIMEOUT if a kernel's bounded wait gave up since the last
  * check (its outputs are then invalid), LEEA_OK otherwise.  flags_out, if
@@ -224,9 +239,18 @@ leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_
 
 /* leea_generation with the minibatch in HOST memory: copies it to a
  * library-owned staging buffer on the object's stream, then runs the
- * generation.  Host buffers may be reused once the call returns. */
+ * generation.  Pageable host buffers are copied before the call returns;
+ * pinned (page-locked) ones are read asynchronously and must stay unchanged
+ * until the stream has reached the copy. */
 leea_status leea_generation_host(leea_state* s, const float* x_host,
                                  const int32_t* y_host, int32_t batch);
+
+/* leea_generation / leea_generation_host for minibatches of 8-bit levels
+ * (x = k / x_div, see leea_evaluate_u8). */
+leea_status leea_generation_u8(leea_state* s, const uint8_t* x_u8_dev, float x_div,
+                               const int32_t* y_dev, int32_t batch);
+leea_status leea_generation_u8_host(leea_state* s, const uint8_t* x_u8_host, float x_div,
+                                    const int32_t* y_host, int32_t batch);
 
 /* Adjusted fitness f_adj (float[pop]) and, if correct_host is not NULL, the
  * correct-prediction counts of the last evaluation.  Synchronises. */

@@ -148,6 +148,8 @@ leea_status check_device_status(cudaStream_t stream, uint32_t* flags_out)
     if (flags_out) *flags_out = v;
     if (v & kStatusEvalTimeout)
         return fail(LEEA_ETIMEOUT, "a tensor-core evaluation wait timed out; its fitness values are invalid");
+    if (v & kStatusBreedTimeout)
+        return fail(LEEA_ETIMEOUT, "a breed kernel wait timed out; the children are invalid");
     return LEEA_OK;
 }
 
@@ -167,6 +169,31 @@ leea_status dispatch_eval(const NetLayout& net, int32_t pop, const float* pop_de
         err = launch_eval_tc(net, pop, pop_dev, x, y, batch, alpha, f_inh, f_raw, f_adj, correct, status, stream);
     } else {
         err = launch_eval_simt(net, pop, pop_dev, x, y, batch, alpha, f_inh, f_raw, f_adj, correct, stream);
+    }
+    if (err != cudaSuccess) return cuda_fail(err, "evaluate kernel");
+    return LEEA_OK;
+}
+
+// The same for 8-bit inputs x = k / x_div.
+leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
+                             const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                             float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream)
+{
+    if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
+    const bool tc_ok = eval_u8_tc_supported(net, batch, pop_dev);
+    if (path == LEEA_EVAL_TENSOR && !tc_ok)
+        return fail(LEEA_EINVAL, "tensor-core evaluation of 8-bit inputs needs batch <= 128, d_0 %% 4 == 0, "
+                                 "h %% 16 == 0, h + round_up(8 ceil(d_0/16), 16) <= 512, d_out <= 16 and a "
+                                 "16-byte aligned population");
+    cudaError_t err;
+    if (tc_ok && path != LEEA_EVAL_SIMT) {
+        unsigned int* status = device_status_ptr();
+        if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+        err = launch_eval_u8_tc(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct, status,
+                                stream);
+    } else {
+        err = launch_eval_simt_u8(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
+                                  stream);
     }
     if (err != cudaSuccess) return cuda_fail(err, "evaluate kernel");
     return LEEA_OK;
@@ -334,7 +361,9 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims, const l
     if ((reinterpret_cast<uintptr_t>(parents_dev) | reinterpret_cast<uintptr_t>(children_dev)) & 15u)
         return fail(LEEA_EINVAL, "population buffers must be 16-byte aligned");
     const BreedArgs a = breed_args(pop, net, p, seed, gen);
-    LEEA_CUDA_TRY(launch_breed(a, parents_dev, par1_dev, par2_dev, kind_dev, children_dev,
+    unsigned int* status = device_status_ptr();
+    if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+    LEEA_CUDA_TRY(launch_breed(a, parents_dev, par1_dev, par2_dev, kind_dev, children_dev, status,
                                static_cast<cudaStream_t>(stream)),
                   "breed kernel");
     return LEEA_OK;
@@ -355,6 +384,23 @@ leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims, cons
     if (eval_path < LEEA_EVAL_AUTO || eval_path > LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "bad eval_path");
     return dispatch_eval(net, pop, pop_dev, x_dev, y_dev, batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev,
                          correct_dev, eval_path, static_cast<cudaStream_t>(stream));
+}
+
+leea_status leea_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims, const float* pop_dev,
+                             const uint8_t* x_u8_dev, float x_div, const int32_t* y_dev, int32_t batch, float alpha,
+                             const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev, int32_t* correct_dev,
+                             int32_t eval_path, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if ((st = check_eval_shape(net, batch))) return st;
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
+    if (!pop_dev || !x_u8_dev || !y_dev || !f_raw_dev) return fail(LEEA_EINVAL, "NULL device pointer");
+    if (eval_path < LEEA_EVAL_AUTO || eval_path > LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "bad eval_path");
+    return dispatch_eval_u8(net, pop, pop_dev, x_u8_dev, x_div, y_dev, batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev,
+                            correct_dev, eval_path, static_cast<cudaStream_t>(stream));
 }
 
 leea_status leea_device_status(void* stream, uint32_t* flags_out)
@@ -413,9 +459,10 @@ struct leea_state {
     float* popbuf[2];
     float *f_adj, *f_raw, *f_inh;
     int32_t *correct, *order, *par1, *par2, *kind;
-    float* x_stage;
+    void* x_stage;      // minibatch staging for the host entry points (float or uint8 rows)
     int32_t* y_stage;
-    int64_t stage_cap;  // samples the staging buffers hold
+    size_t x_stage_bytes;
+    int64_t y_stage_cap;
     bool profiling;
     ProfileRing* prof;
 };
@@ -542,12 +589,14 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
     return LEEA_OK;
 }
 
-leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_dev, int32_t batch)
+static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, float x_div, const int32_t* y_dev,
+                                  int32_t batch)
 {
     leea_status st = check_state(s);
     if (st) return st;
     if ((st = check_eval_shape(s->net, batch))) return st;
     if (!x_dev || !y_dev) return fail(LEEA_EINVAL, "NULL minibatch pointer");
+    if (u8 && (!(x_div > 0.0f) || std::isinf(x_div))) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
     const bool first = !s->evaluated;
     if (!first) {
         const uint32_t g = s->gen + 1;
@@ -566,8 +615,10 @@ leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_
         {
             StageScope sc(s, 2);
             const BreedArgs a = breed_args(s->pop, s->net, &s->prm, s->seed, g);
+            unsigned int* status = device_status_ptr();
+            if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
             LEEA_CUDA_TRY(launch_breed(a, s->popbuf[s->cur], s->par1, s->par2, s->kind, s->popbuf[s->cur ^ 1],
-                                       s->stream),
+                                       status, s->stream),
                           "breed kernel");
             sc.done();
         }
@@ -576,14 +627,68 @@ leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_
     }
     {
         StageScope sc(s, 3);
-        st = dispatch_eval(s->net, s->pop, s->popbuf[s->cur], x_dev, y_dev, batch, s->prm.alpha,
-                           first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct, s->prm.eval_path,
-                           s->stream);
+        if (u8)
+            st = dispatch_eval_u8(s->net, s->pop, s->popbuf[s->cur], static_cast<const uint8_t*>(x_dev), x_div, y_dev,
+                                  batch, s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,
+                                  s->prm.eval_path, s->stream);
+        else
+            st = dispatch_eval(s->net, s->pop, s->popbuf[s->cur], static_cast<const float*>(x_dev), y_dev, batch,
+                               s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,
+                               s->prm.eval_path, s->stream);
         sc.done();
         if (st) return st;
     }
     s->evaluated = true;
     return LEEA_OK;
+}
+
+// Copies a host minibatch into the object's staging buffers (grown on demand).
+static leea_status stage_batch(leea_state* s, const void* x_host, size_t x_bytes, const int32_t* y_host, int32_t batch)
+{
+    if (x_bytes > s->x_stage_bytes || batch > s->y_stage_cap) {
+        LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "staging sync");
+        if (x_bytes > s->x_stage_bytes) {
+            cudaFree(s->x_stage);
+            s->x_stage = nullptr;
+            s->x_stage_bytes = 0;
+            LEEA_CUDA_TRY(cudaMalloc(&s->x_stage, x_bytes), "staging allocation");
+            s->x_stage_bytes = x_bytes;
+        }
+        if (batch > s->y_stage_cap) {
+            cudaFree(s->y_stage);
+            s->y_stage = nullptr;
+            s->y_stage_cap = 0;
+            LEEA_CUDA_TRY(cudaMalloc(&s->y_stage, sizeof(int32_t) * static_cast<size_t>(batch)), "staging allocation");
+            s->y_stage_cap = batch;
+        }
+    }
+    LEEA_CUDA_TRY(cudaMemcpyAsync(s->x_stage, x_host, x_bytes, cudaMemcpyHostToDevice, s->stream), "minibatch copy");
+    LEEA_CUDA_TRY(cudaMemcpyAsync(s->y_stage, y_host, sizeof(int32_t) * static_cast<size_t>(batch),
+                                  cudaMemcpyHostToDevice, s->stream),
+                  "label copy");
+    return LEEA_OK;
+}
+
+leea_status leea_generation(leea_state* s, const float* x_dev, const int32_t* y_dev, int32_t batch)
+{
+    return run_generation(s, x_dev, false, 1.0f, y_dev, batch);
+}
+
+leea_status leea_generation_u8(leea_state* s, const uint8_t* x_u8_dev, float x_div, const int32_t* y_dev,
+                               int32_t batch)
+{
+    return run_generation(s, x_u8_dev, true, x_div, y_dev, batch);
+}
+
+leea_status leea_generation_u8_host(leea_state* s, const uint8_t* x_u8_host, float x_div, const int32_t* y_host,
+                                    int32_t batch)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if ((st = check_eval_shape(s->net, batch))) return st;
+    if (!x_u8_host || !y_host) return fail(LEEA_EINVAL, "NULL minibatch pointer");
+    if ((st = stage_batch(s, x_u8_host, static_cast<size_t>(batch) * s->net.dims[0], y_host, batch))) return st;
+    return run_generation(s, s->x_stage, true, x_div, s->y_stage, batch);
 }
 
 leea_status leea_generation_host(leea_state* s, const float* x_host, const int32_t* y_host, int32_t batch)
@@ -592,25 +697,9 @@ leea_status leea_generation_host(leea_state* s, const float* x_host, const int32
     if (st) return st;
     if ((st = check_eval_shape(s->net, batch))) return st;
     if (!x_host || !y_host) return fail(LEEA_EINVAL, "NULL minibatch pointer");
-    if (batch > s->stage_cap) {
-        LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "staging sync");
-        cudaFree(s->x_stage);
-        cudaFree(s->y_stage);
-        s->x_stage = nullptr;
-        s->y_stage = nullptr;
-        s->stage_cap = 0;
-        LEEA_CUDA_TRY(cudaMalloc(&s->x_stage, sizeof(float) * static_cast<size_t>(batch) * s->net.dims[0]),
-                      "staging allocation");
-        LEEA_CUDA_TRY(cudaMalloc(&s->y_stage, sizeof(int32_t) * static_cast<size_t>(batch)), "staging allocation");
-        s->stage_cap = batch;
-    }
-    LEEA_CUDA_TRY(cudaMemcpyAsync(s->x_stage, x_host, sizeof(float) * static_cast<size_t>(batch) * s->net.dims[0],
-                                  cudaMemcpyHostToDevice, s->stream),
-                  "minibatch copy");
-    LEEA_CUDA_TRY(cudaMemcpyAsync(s->y_stage, y_host, sizeof(int32_t) * static_cast<size_t>(batch),
-                                  cudaMemcpyHostToDevice, s->stream),
-                  "label copy");
-    return leea_generation(s, s->x_stage, s->y_stage, batch);
+    if ((st = stage_batch(s, x_host, sizeof(float) * static_cast<size_t>(batch) * s->net.dims[0], y_host, batch)))
+        return st;
+    return run_generation(s, s->x_stage, false, 1.0f, s->y_stage, batch);
 }
 
 static leea_status copy_out(leea_state* s, void* dst, const void* src, size_t bytes, const char* what)

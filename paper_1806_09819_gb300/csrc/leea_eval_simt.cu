@@ -22,7 +22,11 @@ struct EvalSimtArgs {
     int32_t d_in, h, d_out, batch;
     int64_t c_pad;
     float alpha;
+    float x_div;  // 8-bit inputs: x = k / x_div
 };
+
+__device__ __forceinline__ float input_value(float v, float) { return v; }
+__device__ __forceinline__ float input_value(uint8_t k, float div) { return static_cast<float>(k) / div; }
 
 template <int TM, int TN>
 struct SimtTile {
@@ -38,9 +42,9 @@ struct SimtTile {
     }
 };
 
-template <int TM, int TN>
+template <int TM, int TN, typename XT>
 __global__ void __launch_bounds__(kEvalThreads, 2)
-eval_simt_kernel(EvalSimtArgs e, const float* __restrict__ popv, const float* __restrict__ x,
+eval_simt_kernel(EvalSimtArgs e, const float* __restrict__ popv, const XT* __restrict__ x,
                  const int32_t* __restrict__ y, const float* __restrict__ f_inh,
                  float* __restrict__ f_raw, float* __restrict__ f_adj, int32_t* __restrict__ correct)
 {
@@ -96,7 +100,7 @@ eval_simt_kernel(EvalSimtArgs e, const float* __restrict__ popv, const float* __
                     const int idx = tid + u * kEvalThreads;  // < BN * kBK
                     const int n = idx / kBK, k = idx % kBK;
                     const int gn = b0 + n, gk = k0 + k;
-                    rb[u] = (gn < Bt && gk < K) ? x[static_cast<int64_t>(gn) * K + gk] : 0.0f;
+                    rb[u] = (gn < Bt && gk < K) ? input_value(x[static_cast<int64_t>(gn) * K + gk], e.x_div) : 0.0f;
                 }
             };
             auto store_tile = [&](int buf) {
@@ -224,18 +228,18 @@ eval_simt_kernel(EvalSimtArgs e, const float* __restrict__ popv, const float* __
     }
 }
 
-template <int TM, int TN>
-static cudaError_t launch_simt_t(const EvalSimtArgs& e, int32_t pop, const float* popv, const float* x,
+template <int TM, int TN, typename XT>
+static cudaError_t launch_simt_t(const EvalSimtArgs& e, int32_t pop, const float* popv, const XT* x,
                                  const int32_t* y, const float* f_inh, float* f_raw, float* f_adj,
                                  int32_t* correct, cudaStream_t stream)
 {
     const size_t smem = SimtTile<TM, TN>::smem_bytes(e.d_out);
-    cudaError_t err = cudaFuncSetAttribute(eval_simt_kernel<TM, TN>,
+    cudaError_t err = cudaFuncSetAttribute(eval_simt_kernel<TM, TN, XT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    eval_simt_kernel<TM, TN><<<pop, kEvalThreads, smem, stream>>>(e, popv, x, y, f_inh, f_raw, f_adj,
-                                                                   correct);
+    eval_simt_kernel<TM, TN, XT><<<pop, kEvalThreads, smem, stream>>>(e, popv, x, y, f_inh, f_raw, f_adj,
+                                                                       correct);
     return cudaGetLastError();
 }
 
@@ -244,22 +248,39 @@ static int pick_micro(int extent)
     return extent <= 32 ? 2 : extent <= 64 ? 4 : 8;
 }
 
-cudaError_t launch_eval_simt(const NetLayout& net, int32_t pop, const float* pop_dev,
-                             const float* x, const int32_t* y, int32_t batch, float alpha,
-                             const float* f_inh, float* f_raw, float* f_adj, int32_t* correct,
-                             cudaStream_t stream)
+template <typename XT>
+static cudaError_t launch_simt_any(const NetLayout& net, int32_t pop, const float* pop_dev, const XT* x,
+                                   float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                                   float* f_raw, float* f_adj, int32_t* correct, cudaStream_t stream)
 {
     if (net.n_layers != 2 || net.dims[2] > kMaxOut) return cudaErrorInvalidValue;
-    EvalSimtArgs e{ net.dims[0], net.dims[1], net.dims[2], batch, net.c_pad, alpha };
+    EvalSimtArgs e{ net.dims[0], net.dims[1], net.dims[2], batch, net.c_pad, alpha, x_div };
     const int tm = pick_micro(e.h), tn = pick_micro(batch);
 #define LEEA_SIMT_CASE(A, B)                                                                      \
     if (tm == A && tn == B)                                                                       \
-        return launch_simt_t<A, B>(e, pop, pop_dev, x, y, f_inh, f_raw, f_adj, correct, stream);
+        return launch_simt_t<A, B, XT>(e, pop, pop_dev, x, y, f_inh, f_raw, f_adj, correct, stream);
     LEEA_SIMT_CASE(2, 2) LEEA_SIMT_CASE(2, 4) LEEA_SIMT_CASE(2, 8)
     LEEA_SIMT_CASE(4, 2) LEEA_SIMT_CASE(4, 4) LEEA_SIMT_CASE(4, 8)
     LEEA_SIMT_CASE(8, 2) LEEA_SIMT_CASE(8, 4) LEEA_SIMT_CASE(8, 8)
 #undef LEEA_SIMT_CASE
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_eval_simt(const NetLayout& net, int32_t pop, const float* pop_dev,
+                             const float* x, const int32_t* y, int32_t batch, float alpha,
+                             const float* f_inh, float* f_raw, float* f_adj, int32_t* correct,
+                             cudaStream_t stream)
+{
+    return launch_simt_any<float>(net, pop, pop_dev, x, 1.0f, y, batch, alpha, f_inh, f_raw, f_adj, correct,
+                                  stream);
+}
+
+cudaError_t launch_eval_simt_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
+                                float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                                float* f_raw, float* f_adj, int32_t* correct, cudaStream_t stream)
+{
+    return launch_simt_any<uint8_t>(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
+                                    stream);
 }
 
 }  // namespace leea

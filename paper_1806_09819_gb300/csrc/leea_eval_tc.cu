@@ -134,7 +134,7 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant
         // ------------------------------------------------------------ TMA producer
         if (lane == 0) {
             uint32_t stage = 0, phase = 0;
-            uint32_t issued[8] = { 0, 0, 0, 0, 0, 0, 0, 0 };
+            uint32_t issued_mask = 0, parity_mask = 0;  // per stage: issued at all / parity of the last issue
             bool ok = true;
             for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
                 for (int mt = 0; ok && mt < a.m_tiles; ++mt) {
@@ -148,7 +148,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant
                         ptx::mbar_arrive_expect_tx(&s.full[stage], kXTileBytes + s.w_bytes);
                         ptx::tma_load_2d(st, &tmap_x, &s.full[stage], kc * kKChunk, mt * kMTile);
                         ptx::tma_load_3d(st + 2 * kXTileBytes, &tmap_w, &s.full[stage], kc * kKChunk, 0, p);
-                        issued[stage]++;
+                        issued_mask |= 1u << stage;
+                        parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
                         if (++stage == static_cast<uint32_t>(a.stages)) { stage = 0; phase ^= 1u; }
                     }
                 }
@@ -156,8 +157,8 @@ eval_tc_kernel(const __grid_constant__ CUtensorMap tmap_x, const __grid_constant
             if (!ok) {  // let every copy already in flight land before the CTA exits
                 volatile int never = 0;
                 for (int i = 0; i < a.stages; ++i)
-                    if (issued[i])
-                        ptx::mbar_wait_bounded(&s.full[i], (issued[i] - 1u) & 1u, &never, kDrainLimitNs);
+                    if (issued_mask & (1u << i))
+                        ptx::mbar_wait_bounded(&s.full[i], (parity_mask >> i) & 1u, &never, kDrainLimitNs);
             }
         }
     } else if (warp == 1) {

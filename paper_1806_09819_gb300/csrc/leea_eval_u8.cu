@@ -1,0 +1,459 @@
+// leea_eval_u8.cu -- fitness of every individual (Eq. 1; Section 3.3) for
+// minibatches of 8-bit image levels, x = k / x_div with k in [0, 255] (MNIST's
+// encoding), on the tcgen05 tensor cores with FP32-class accuracy.
+//
+// The integers k are exact in BF16, and every FP32 weight is split exactly into
+// three BF16 pieces w = w1 + w2 + w3 (8 significant bits each).  So
+// D = K W1_p^T = sum_i K w_i is formed from exact products, and only the FP32
+// accumulation in the tensor core rounds.  The epilogue scales by 1 / x_div.
+//
+// The batch (<= 128 samples) is written once per CTA into tensor memory as
+// the MMA's A operand (lane = sample, two BF16 per column), so shared memory
+// only carries the weight pieces: per 64-wide K stage, 3 x h rows of 128
+// bytes in the 128-byte swizzled K-major layout.
+//
+// Warp roles (persistent CTA, one per SM, individuals strided by gridDim.x):
+//   warp 0      TMEM allocation and the single MMA-issuing thread
+//   warps 1-8   weight loaders: prefetch the next individual's W1 into L2,
+//               load FP32 W1 with 128-bit loads, split into BF16 pieces and
+//               store them swizzled into the stage ring
+//   warps 9-12  write the batch into TMEM once; then the epilogue (bias,
+//               ReLU, layer 2 with W2 staged transposed in shared memory,
+//               softmax cross-entropy, fixed-order batch sum, inheritance)
+// Every mbarrier wait is bounded in time; on expiry the kernel sets
+// kStatusEvalTimeout, drains its MMAs and exits.
+#include <cuda_bf16.h>
+
+#include "leea_internal.h"
+#include "tc_ptx.cuh"
+
+namespace leea {
+
+namespace {
+
+constexpr int kLoaderWarps = 8;
+constexpr int kU8Threads = 32 * (1 + kLoaderWarps + 4);
+constexpr int kKStage = 64;        // K elements per stage: one 128-byte BF16 row
+constexpr int kU8Stages = 4;
+constexpr int kMaxOutU8 = 16;
+constexpr int kRowBatch = 8;       // 16-row groups a loader thread holds in registers at once
+constexpr uint32_t kTmemCols = 512;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint64_t kDrainLimitNs = 200000000ull;
+
+struct EvalU8Args {
+    int32_t pop, k, h, d_out, dpad, batch, k_stages, k16;
+    int64_t c_pad;
+    float inv_div, alpha;
+    uint32_t a_col;  // first TMEM column of the A operand (the accumulator uses 0 .. h-1)
+    const float* popv;
+    const uint8_t* x;
+    const int32_t* y;
+    const float* f_inh;
+    float* f_raw;
+    float* f_adj;
+    int32_t* correct;
+    unsigned int* status;
+};
+
+struct U8Smem {
+    uint8_t* ring;        // kU8Stages x 3 pieces x h x 128 B
+    uint32_t piece_bytes;
+    float* w2t;           // [h][dpad]
+    float* b1;            // [h]
+    float* b2;            // [16]
+    uint64_t *full, *empty, *acc_full, *acc_empty, *a_ready, *drain;
+    uint32_t* tmem_holder;
+    volatile int* abort_flag;
+    int* ep_go;
+    float* red_loss;
+    int32_t* red_ok;
+};
+
+__device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
+{
+    U8Smem s;
+    s.ring = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
+    s.piece_bytes = static_cast<uint32_t>(a.h) * 128u;
+    uint8_t* p = s.ring + kU8Stages * 3u * s.piece_bytes;
+    s.w2t = reinterpret_cast<float*>(p);
+    p += sizeof(float) * a.h * a.dpad;
+    s.b1 = reinterpret_cast<float*>(p);
+    p += sizeof(float) * a.h;
+    s.b2 = reinterpret_cast<float*>(p);
+    p += sizeof(float) * 16;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(p);
+    s.full = bars;
+    s.empty = bars + kU8Stages;
+    s.acc_full = bars + 2 * kU8Stages;
+    s.acc_empty = s.acc_full + 1;
+    s.a_ready = s.acc_full + 2;
+    s.drain = s.acc_full + 3;
+    uint32_t* w = reinterpret_cast<uint32_t*>(s.acc_full + 4);
+    s.tmem_holder = w;
+    s.abort_flag = reinterpret_cast<volatile int*>(w + 1);
+    s.ep_go = reinterpret_cast<int*>(w + 2);
+    s.red_loss = reinterpret_cast<float*>(w + 4);
+    s.red_ok = reinterpret_cast<int32_t*>(w + 8);
+    return s;
+}
+
+size_t u8_smem_bytes(int32_t h, int32_t dpad)
+{
+    return 1024 + static_cast<size_t>(kU8Stages) * 3 * h * 128 + sizeof(float) * (h * dpad + h + 16) +
+           8 * (2 * kU8Stages + 4) + 64;
+}
+
+__device__ __forceinline__ void raise_abort(const U8Smem& s, const EvalU8Args& a)
+{
+    *s.abort_flag = 1;
+    atomicOr(a.status, kStatusEvalTimeout);
+}
+
+__device__ __forceinline__ uint32_t bf16_bits(float v)
+{
+    return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
+}
+
+// Exact three-way split of an FP32 value into BF16 pieces (rounding to
+// nearest at each step; the remainders are exact in FP32).
+__device__ __forceinline__ void split3(float w, uint32_t& p1, uint32_t& p2, uint32_t& p3)
+{
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(w);
+    const float r1 = w - __bfloat162float(h1);
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(h2);
+    p1 = __bfloat16_as_ushort(h1);
+    p2 = __bfloat16_as_ushort(h2);
+    p3 = bf16_bits(r2);
+}
+
+__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
+                 : "memory");
+}
+
+__global__ void __launch_bounds__(kU8Threads, 1) eval_u8_kernel(const EvalU8Args a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const U8Smem s = carve(smem_raw, a);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kU8Stages; ++i) {
+            ptx::mbar_init(&s.full[i], kLoaderWarps);
+            ptx::mbar_init(&s.empty[i], 1);
+        }
+        ptx::mbar_init(s.acc_full, 1);
+        ptx::mbar_init(s.acc_empty, 128);
+        ptx::mbar_init(s.a_ready, 128);
+        ptx::mbar_init(s.drain, 1);
+        *s.abort_flag = 0;
+        *s.ep_go = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) ptx::tmem_alloc(s.tmem_holder, kTmemCols);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *s.tmem_holder;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = ptx::idesc_bf16(128, static_cast<uint32_t>(a.h));
+            bool ok = ptx::mbar_wait_bounded(s.a_ready, 0u, s.abort_flag, kWaitLimitNs);
+            if (!ok) raise_abort(s, a);
+            ptx::tc_fence_after();
+            uint32_t stage = 0, phase = 0, acc_phase = 0;
+            const uint32_t ring = ptx::smem_u32(s.ring);
+            for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+                if (!ptx::mbar_wait_bounded(s.acc_empty, acc_phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+                    raise_abort(s, a);
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                for (int kc = 0; kc < a.k_stages; ++kc) {
+                    if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kWaitLimitNs)) {
+                        raise_abort(s, a);
+                        ok = false;
+                        break;
+                    }
+                    ptx::tc_fence_after();
+                    const uint32_t sb = ring + stage * 3u * s.piece_bytes;
+#pragma unroll
+                    for (int kk = 0; kk < kKStage / 16; ++kk) {
+                        const int kg = kc * kKStage + kk * 16;
+                        if (kg >= a.k16) break;
+                        const uint32_t a_tmem = tmem_base + a.a_col + static_cast<uint32_t>(kg >> 1);
+#pragma unroll
+                        for (int piece = 0; piece < 3; ++piece) {
+                            const uint64_t bd = ptx::smem_desc_sw128(sb + piece * s.piece_bytes + kk * 32u);
+                            ptx::mma_f16_tmem_a(tmem_base, a_tmem, bd, idesc, (kc | kk | piece) != 0 ? 1u : 0u);
+                        }
+                    }
+                    ptx::mma_commit(&s.empty[stage]);
+                    if (++stage == kU8Stages) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                ptx::mma_commit(s.acc_full);
+                acc_phase ^= 1u;
+            }
+            ptx::mma_commit(s.drain);
+            volatile int never = 0;
+            ptx::mbar_wait_bounded(s.drain, 0u, &never, ok ? kWaitLimitNs : kDrainLimitNs);
+        }
+    } else if (warp <= kLoaderWarps) {
+        // ------------------------------------------------------------ weight loaders
+        const int lt = threadIdx.x - 32;
+        const int row0 = lt >> 4, c4 = lt & 15;  // 16 threads cover one row's 64 K-elements
+        const int groups = a.h >> 4;
+        uint32_t stage = 0, phase = 0;
+        bool ok = true;
+        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+            const float* w1 = a.popv + static_cast<int64_t>(p) * a.c_pad;
+            if (lt == 0) {
+                const int pn = p + gridDim.x;  // stream the next individual's weights into L2
+                if (pn < a.pop)
+                    prefetch_l2(a.popv + static_cast<int64_t>(pn) * a.c_pad,
+                                static_cast<uint32_t>(a.c_pad * 4 < 0x7FFFFFF0 ? a.c_pad * 4 : 0x7FFFFFF0) & ~15u);
+            }
+            for (int kc = 0; kc < a.k_stages; ++kc) {
+                const int k = kc * kKStage + 4 * c4;
+                uint8_t* sb = s.ring + stage * 3u * s.piece_bytes;
+                for (int g0 = 0; g0 < groups; g0 += kRowBatch) {
+                    float4 v[kRowBatch];
+#pragma unroll
+                    for (int u = 0; u < kRowBatch; ++u) {
+                        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (g0 + u < groups && k < a.k)
+                            v[u] = __ldg(reinterpret_cast<const float4*>(
+                                w1 + static_cast<int64_t>(row0 + 16 * (g0 + u)) * a.k + k));
+                    }
+                    if (g0 == 0 &&
+                        !ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+                        raise_abort(s, a);
+                        ok = false;
+                        break;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kRowBatch; ++u) {
+                        if (g0 + u < groups) {
+                            const int r = row0 + 16 * (g0 + u);
+                            uint32_t q0[3], q1[3], q2[3], q3[3];
+                            split3(v[u].x, q0[0], q0[1], q0[2]);
+                            split3(v[u].y, q1[0], q1[1], q1[2]);
+                            split3(v[u].z, q2[0], q2[1], q2[2]);
+                            split3(v[u].w, q3[0], q3[1], q3[2]);
+                            const uint32_t off = static_cast<uint32_t>(r) * 128u +
+                                                 ((static_cast<uint32_t>(c4 >> 1) ^ static_cast<uint32_t>(r & 7)) << 4) +
+                                                 (static_cast<uint32_t>(c4 & 1) << 3);
+#pragma unroll
+                            for (int piece = 0; piece < 3; ++piece) {
+                                const uint2 pk =
+                                    make_uint2(q0[piece] | (q1[piece] << 16), q2[piece] | (q3[piece] << 16));
+                                *reinterpret_cast<uint2*>(sb + piece * s.piece_bytes + off) = pk;
+                            }
+                        }
+                    }
+                }
+                if (!ok) break;
+                ptx::fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&s.full[stage]);
+                if (++stage == kU8Stages) { stage = 0; phase ^= 1u; }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ batch into TMEM, then epilogue
+        const int et = threadIdx.x - 32 * (1 + kLoaderWarps);
+        const int q = warp & 3;  // TMEM lane quarter of this warp
+        const int row = q * 32 + lane;
+        const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
+        {
+            // Row `row` of the batch as BF16 pairs (k even in the low half).
+            const uint8_t* xr = a.x + static_cast<int64_t>(row) * a.k;
+            const bool live = row < a.batch;
+            for (int c0 = 0; c0 < a.k16 / 2; c0 += 16) {
+                uint32_t cols[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int k0 = 2 * (c0 + i);
+                    const uint32_t lo = (live && k0 < a.k) ? static_cast<uint32_t>(xr[k0]) : 0u;
+                    const uint32_t hi = (live && k0 + 1 < a.k) ? static_cast<uint32_t>(xr[k0 + 1]) : 0u;
+                    cols[i] = (__float_as_uint(static_cast<float>(lo)) >> 16) |
+                              (__float_as_uint(static_cast<float>(hi)) & 0xFFFF0000u);
+                }
+                ptx::tmem_st16(tmem_base + lane_addr + a.a_col + static_cast<uint32_t>(c0), cols);
+            }
+            ptx::tmem_st_wait();
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(s.a_ready);
+        }
+
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+            // Stage b1, W2 (transposed, rows padded to dpad) and b2 of individual p.
+            const float* src = a.popv + static_cast<int64_t>(p) * a.c_pad + static_cast<int64_t>(a.h) * a.k;
+            for (int i = et; i < a.h; i += 128) s.b1[i] = src[i];
+            for (int i = et; i < a.d_out * a.h; i += 128) {
+                const int o = i / a.h, col = i - o * a.h;
+                s.w2t[col * a.dpad + o] = src[a.h + i];
+            }
+            for (int i = et; i < a.h * (a.dpad - a.d_out); i += 128) {
+                const int pad = a.dpad - a.d_out;
+                s.w2t[(i / pad) * a.dpad + a.d_out + i % pad] = 0.0f;
+            }
+            if (et < 16) s.b2[et] = et < a.d_out ? src[a.h + a.d_out * a.h + et] : 0.0f;
+            if (et == 0) {
+                const bool got = ptx::mbar_wait_bounded(s.acc_full, acc_phase, s.abort_flag, kWaitLimitNs);
+                if (!got) raise_abort(s, a);
+                *s.ep_go = got ? 1 : 0;
+            }
+            ptx::named_barrier_sync(1, 128);  // A: accumulator ready (or abort); parameters staged
+            if (!*s.ep_go) { ok = false; break; }
+            ptx::tc_fence_after();
+
+            float logit[kMaxOutU8];
+#pragma unroll
+            for (int o = 0; o < kMaxOutU8; ++o) logit[o] = 0.0f;
+            for (int c = 0; c < a.h; c += 16) {
+                float v[16];
+                ptx::tmem_ld16(tmem_base + lane_addr + static_cast<uint32_t>(c), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = c + j;
+                    const float hv = fmaxf(fmaf(v[j], a.inv_div, s.b1[col]), 0.0f);
+                    const float4* wr = reinterpret_cast<const float4*>(s.w2t + col * a.dpad);
+#pragma unroll
+                    for (int o4 = 0; o4 < kMaxOutU8 / 4; ++o4) {
+                        if (4 * o4 < a.d_out) {
+                            const float4 w = wr[o4];
+                            logit[4 * o4 + 0] = fmaf(w.x, hv, logit[4 * o4 + 0]);
+                            logit[4 * o4 + 1] = fmaf(w.y, hv, logit[4 * o4 + 1]);
+                            logit[4 * o4 + 2] = fmaf(w.z, hv, logit[4 * o4 + 2]);
+                            logit[4 * o4 + 3] = fmaf(w.w, hv, logit[4 * o4 + 3]);
+                        }
+                    }
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(s.acc_empty);
+            acc_phase ^= 1u;
+
+            float loss = 0.0f;
+            int32_t good = 0;
+            if (row < a.batch) {
+                float zmax = logit[0] + s.b2[0];
+                int arg = 0;
+#pragma unroll
+                for (int o = 1; o < kMaxOutU8; ++o) {
+                    if (o < a.d_out) {
+                        const float z = logit[o] + s.b2[o];
+                        if (z > zmax) { zmax = z; arg = o; }
+                    }
+                }
+                float se = 0.0f;
+#pragma unroll
+                for (int o = 0; o < kMaxOutU8; ++o)
+                    if (o < a.d_out) se += expf(logit[o] + s.b2[o] - zmax);
+                const int32_t lbl = a.y[row];
+                if (lbl >= 0 && lbl < a.d_out) {
+                    float zl = 0.0f;
+#pragma unroll
+                    for (int o = 0; o < kMaxOutU8; ++o)
+                        if (o == lbl) zl = logit[o] + s.b2[o];
+                    loss = logf(se) + zmax - zl;
+                    good = (arg == lbl) ? 1 : 0;
+                } else {
+                    loss = __int_as_float(0x7FC00000);
+                }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
+                good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
+            }
+            if (lane == 0) {
+                s.red_loss[q] = loss;
+                s.red_ok[q] = good;
+            }
+            ptx::named_barrier_sync(1, 128);  // B: quarter sums written; staged parameters no longer read
+            if (et == 0) {
+                const float total = ((s.red_loss[0] + s.red_loss[1]) + s.red_loss[2]) + s.red_loss[3];
+                const int32_t n_ok = s.red_ok[0] + s.red_ok[1] + s.red_ok[2] + s.red_ok[3];
+                const float f = -(total / static_cast<float>(a.batch));
+                a.f_raw[p] = f;
+                if (a.f_adj) a.f_adj[p] = a.f_inh ? (1.0f - a.alpha) * a.f_inh[p] + a.alpha * f : f;
+                if (a.correct) a.correct[p] = n_ok;
+            }
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+}  // namespace
+
+bool eval_u8_tc_supported(const NetLayout& net, int32_t batch, const float* pop_dev)
+{
+    if (net.n_layers != 2) return false;
+    const int32_t k = net.dims[0], h = net.dims[1], d_out = net.dims[2];
+    if (k % 4 != 0 || h % 16 != 0 || h > 256 || d_out > kMaxOutU8 || batch < 1 || batch > 128) return false;
+    const int32_t k16 = (k + 15) / 16 * 16;
+    const int32_t a_cols = (k16 / 2 + 15) / 16 * 16;
+    if (h + a_cols > static_cast<int32_t>(kTmemCols)) return false;
+    if (reinterpret_cast<uintptr_t>(pop_dev) & 15u) return false;
+    const int32_t dpad = (d_out + 3) / 4 * 4;
+    return u8_smem_bytes(h, dpad) <= 227u * 1024u;
+}
+
+cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
+                              float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                              float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
+                              cudaStream_t stream)
+{
+    EvalU8Args a{};
+    a.pop = pop;
+    a.k = net.dims[0];
+    a.h = net.dims[1];
+    a.d_out = net.dims[2];
+    a.dpad = (a.d_out + 3) / 4 * 4;
+    a.batch = batch;
+    a.k16 = (a.k + 15) / 16 * 16;
+    a.k_stages = (a.k + kKStage - 1) / kKStage;
+    a.c_pad = net.c_pad;
+    a.inv_div = static_cast<float>(1.0 / static_cast<double>(x_div));
+    a.alpha = alpha;
+    a.a_col = static_cast<uint32_t>(a.h);
+    a.popv = pop_dev;
+    a.x = x;
+    a.y = y;
+    a.f_inh = f_inh;
+    a.f_raw = f_raw;
+    a.f_adj = f_adj;
+    a.correct = correct;
+    a.status = status;
+    const size_t smem = u8_smem_bytes(a.h, a.dpad);
+    int dev = 0, sms = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err != cudaSuccess) return err;
+    err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(eval_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    const int grid = pop < sms ? pop : sms;
+    eval_u8_kernel<<<grid, kU8Threads, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace leea

@@ -10,7 +10,8 @@ namespace leea {
 constexpr int kMaxLayers = 15;
 
 // Bits of the device status word (set by kernels, read and cleared by the host).
-constexpr unsigned int kStatusEvalTimeout = 1u;  // a bounded mbarrier wait of the tensor-core eval gave up
+constexpr unsigned int kStatusEvalTimeout = 1u;   // a bounded mbarrier wait of the tensor-core eval gave up
+constexpr unsigned int kStatusBreedTimeout = 2u;  // a bounded mbarrier wait of the breed kernel gave up
 
 // Per-layer offsets of a net, computed on the host (logical gene order of
 // Section 3.2: W_l rows out x in, then b_l).
@@ -49,7 +50,7 @@ cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t
                           cudaStream_t stream);
 cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t* par1,
                          const int32_t* par2, const int32_t* kind, float* children,
-                         cudaStream_t stream);
+                         unsigned int* status, cudaStream_t stream);
 // Evaluation of d_0-h-d_out nets (one hidden layer), SIMT FP32.
 cudaError_t launch_eval_simt(const NetLayout& net, int32_t pop, const float* pop_dev,
                              const float* x, const int32_t* y, int32_t batch, float alpha,
@@ -61,6 +62,17 @@ bool eval_tc_supported(const NetLayout& net, int32_t batch, const float* pop_dev
 cudaError_t launch_eval_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const float* x,
                            const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
                            float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream);
+// 8-bit inputs x = k / x_div: CUDA-core FP32 evaluation of any shape, and the
+// tensor-core evaluation (batch in TMEM, exact BF16 pieces) for batch <= 128,
+// d_0 % 4 == 0, h % 16 == 0, h + d_0/2 (rounded) <= 512 TMEM columns, d_out <= 16.
+cudaError_t launch_eval_simt_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
+                                float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                                float* f_raw, float* f_adj, int32_t* correct, cudaStream_t stream);
+bool eval_u8_tc_supported(const NetLayout& net, int32_t batch, const float* pop_dev);
+cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
+                              float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                              float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
+                              cudaStream_t stream);
 cudaError_t launch_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
                                uint32_t n0, int64_t count, uint32_t* out, cudaStream_t stream);
 cudaError_t launch_normal_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,

@@ -91,6 +91,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_breed": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp],
         "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, i32, vp],
         "leea_device_status": [vp, P(u32)],
+        "leea_evaluate_u8": [i32, vp, i32, vp, vp, f32, vp, i32, f32, vp, vp, vp, vp, i32, vp],
+        "leea_generation_u8": [vp, vp, f32, vp, i32],
+        "leea_generation_u8_host": [vp, vp, f32, vp, i32],
         "leea_philox_fill": [u64, u32, u32, u32, u32, i64, vp, vp],
         "leea_normal_fill": [u64, u32, u32, u32, u32, i64, vp, vp],
         "leea_create": [i32, vp, i32, P(leea_params), u64, vp, P(vp)],
@@ -125,7 +128,7 @@ def exported_symbols() -> list[str]:
     """Names of the entry points the binding expects the library to export."""
     return ["leea_default_params", "leea_num_params", "leea_padded_params", "leea_counts",
             "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_evaluate",
-            "leea_device_status",
+            "leea_device_status", "leea_evaluate_u8", "leea_generation_u8", "leea_generation_u8_host",
             "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
             "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
             "leea_get_population", "leea_set_population", "leea_set_fitness", "leea_set_generation",
@@ -223,6 +226,14 @@ def leea_evaluate(pop: int, dims, pop_dev, x_dev, y_dev, batch: int, alpha: floa
                                         _dptr(correct_dev), int(eval_path), _stream(stream)))
 
 
+def leea_evaluate_u8(pop: int, dims, pop_dev, x_u8_dev, x_div: float, y_dev, batch: int, alpha: float, f_inh_dev,
+                     f_raw_dev, f_adj_dev=None, correct_dev=None, eval_path: int = EVAL_AUTO, stream=None) -> None:
+    d = _dims(dims)
+    _check(load_library().leea_evaluate_u8(pop, _hp(d), len(d), _dptr(pop_dev), _dptr(x_u8_dev), float(x_div),
+                                           _dptr(y_dev), batch, float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev),
+                                           _dptr(f_adj_dev), _dptr(correct_dev), int(eval_path), _stream(stream)))
+
+
 def leea_device_status(stream=None) -> int:
     """Synchronises, reads and clears the device status word; raises on a timeout flag."""
     flags = ctypes.c_uint32()
@@ -272,6 +283,14 @@ class LeeaState:
 
     def leea_generation(self, x_dev, y_dev) -> None:
         _check(self.lib.leea_generation(self._h, _dptr(x_dev), _dptr(y_dev), int(y_dev.shape[0])))
+
+    def leea_generation_u8(self, x_u8_dev, y_dev, x_div: float = 255.0) -> None:
+        _check(self.lib.leea_generation_u8(self._h, _dptr(x_u8_dev), float(x_div), _dptr(y_dev), int(y_dev.shape[0])))
+
+    def leea_generation_u8_host(self, x_u8_host, y_host, x_div: float = 255.0) -> None:
+        xp = x_u8_host.data_ptr() if hasattr(x_u8_host, "data_ptr") else x_u8_host.ctypes.data
+        yp = y_host.data_ptr() if hasattr(y_host, "data_ptr") else y_host.ctypes.data
+        _check(self.lib.leea_generation_u8_host(self._h, xp, float(x_div), yp, int(y_host.shape[0])))
 
     def leea_generation_host(self, x_host, y_host) -> None:
         """x_host / y_host: CPU torch tensors (ideally pinned) or numpy arrays."""

@@ -50,6 +50,13 @@ def make_split(n: int, seed: int, tmpl: np.ndarray | None = None, noise: float =
     return x.astype(np.float32), y
 
 
+def to_levels(x: np.ndarray) -> np.ndarray:
+    """The 8-bit levels k of images x = k / 255 (uint8, same shape)."""
+    k = np.rint(np.asarray(x, dtype=np.float64) * 255.0)
+    assert np.all((k >= 0) & (k <= 255)) and np.all(np.float32(k / 255.0) == np.asarray(x, dtype=np.float32))
+    return k.astype(np.uint8)
+
+
 def dataset(n_train: int = 60000, n_test: int = 10000, seed: int = DATA_SEED):
     """((x_train, y_train), (x_test, y_test)) of the synthetic stand-in."""
     tmpl = templates(seed)

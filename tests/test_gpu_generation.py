@@ -23,8 +23,9 @@ def _dev_batch(x, y):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda(), torch.from_numpy(np.ascontiguousarray(y)).cuda()
 
 
-def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=11, gen0=3, sample=None):
-    """One generation from a common state; returns nothing, asserts parity."""
+def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=11, gen0=3, sample=None, u8=False):
+    """One generation from a common state; returns nothing, asserts parity.
+    With u8=True the minibatch goes in as 8-bit levels k (x = k / 255)."""
     c = gpu.leea_num_params(dims)
     st = gpu.LeeaState(pop, dims, gpu.Params(**prm), seed)
     pop0 = synthetic.random_population(pop, c, seed=seed + 1, scale=0.1)
@@ -37,7 +38,12 @@ def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=11, gen0=3, sample=No
         x, y = synthetic.make_split(batch, seed=seed + 2)
     else:
         x, y = synthetic.tiny_problem(dims[0], dims[-1], batch, seed=seed + 2)
-    st.leea_generation(*_dev_batch(x, y))
+    if u8:
+        xl, yd = _dev_batch(synthetic.to_levels(x), y)
+        st.leea_generation_u8(xl, yd, 255.0)
+        x = synthetic.to_levels(x).astype(np.float64) / 255.0
+    else:
+        st.leea_generation(*_dev_batch(x, y))
     assert st.gen == gen0 + 1
     order, par1, par2, kind, f_inh = st.leea_get_selection()
     kids = st.leea_get_population()
@@ -78,6 +84,20 @@ def test_lockstep_small_config(gpu, oracle_mod, path):
                                  dict(n_elite=4, p_c=0.0, sigma=0.1)])
 def test_lockstep_2_2_2(gpu, oracle_mod, prm):
     _lockstep(gpu, oracle_mod, [2, 2, 2], 4, 8, prm)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_lockstep_full_size_sampled_u8(gpu, oracle_mod, path):
+    sample = np.array([0, 1, 2, 250, 499, 500, 501, 502, 777, 998, 999])
+    prm = dict(CONFIG_FULL["prm"], eval_path=path)
+    _lockstep(gpu, oracle_mod, CONFIG_FULL["dims"], CONFIG_FULL["pop"], CONFIG_FULL["batch"], prm, sample=sample,
+              u8=True)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_lockstep_small_config_u8(gpu, oracle_mod, path):
+    prm = dict(CONFIG_SMALL["prm"], eval_path=path)
+    _lockstep(gpu, oracle_mod, CONFIG_SMALL["dims"], CONFIG_SMALL["pop"], CONFIG_SMALL["batch"], prm, u8=True)
 
 
 @pytest.mark.parametrize("path", [1, 2])
@@ -148,6 +168,21 @@ def test_host_entry_point_matches_device_entry_point(gpu):
         x, y = synthetic.make_split(batch, seed=100 + g)
         a.leea_generation(*_dev_batch(x, y))
         b.leea_generation_host(torch.from_numpy(x).pin_memory(), torch.from_numpy(y).pin_memory())
+    np.testing.assert_array_equal(a.leea_fitness(), b.leea_fitness())
+    np.testing.assert_array_equal(a.leea_get_population(), b.leea_get_population())
+
+
+def test_u8_host_entry_point_matches_device_entry_point(gpu):
+    import torch
+    dims, pop, batch = [784, 112, 10], 64, 100
+    prm = gpu.Params(n_elite=1, sigma=0.005, mut_rate=0.1)
+    a = gpu.LeeaState(pop, dims, prm, 5)
+    b = gpu.LeeaState(pop, dims, prm, 5)
+    for g in range(3):
+        x, y = synthetic.make_split(batch, seed=200 + g)
+        k = synthetic.to_levels(x)
+        a.leea_generation_u8(*_dev_batch(k, y))
+        b.leea_generation_u8_host(torch.from_numpy(k).pin_memory(), torch.from_numpy(y).pin_memory())
     np.testing.assert_array_equal(a.leea_fitness(), b.leea_fitness())
     np.testing.assert_array_equal(a.leea_get_population(), b.leea_get_population())
 

@@ -288,3 +288,103 @@ def test_evaluate_bad_label_gives_nan_and_errors(gpu):
         gpu.leea_evaluate(2, dims, pd, x, y, 0, 1.0, None, f_raw)
     with pytest.raises(gpu.LeeaError):
         gpu.leea_evaluate(2, [4, 3, 3, 2], pd, x, y, 3, 1.0, None, f_raw)
+
+
+# ---- evaluation of 8-bit inputs (x = k / 255) ------------------------------------------------
+U8_CASES = [
+    ([784, 112, 10], 64, 100), ([784, 32, 10], 32, 16), ([784, 112, 10], 3, 128), ([784, 16, 10], 5, 1),
+    ([36, 64, 10], 9, 33), ([784, 48, 16], 4, 77), ([784, 112, 10], 400, 100), ([784, 112, 10], 3, 129),
+    ([784, 37, 10], 3, 20), ([12, 256, 10], 3, 50),
+]
+
+
+def _u8_tc_shape(dims, batch):
+    k, h, d_out = dims
+    a_cols = ((((k + 15) // 16) * 8 + 15) // 16) * 16
+    return k % 4 == 0 and h % 16 == 0 and h <= 256 and d_out <= 16 and batch <= 128 and h + a_cols <= 512
+
+
+def _u8_params():
+    out = []
+    for dims, pop, batch in U8_CASES:
+        out.append(pytest.param(dims, pop, batch, 1, id=f"simt-{dims}-{pop}-{batch}"))
+        if _u8_tc_shape(dims, batch):
+            out.append(pytest.param(dims, pop, batch, 2, id=f"tensor-{dims}-{pop}-{batch}"))
+    return out
+
+
+@pytest.mark.parametrize("dims,pop,batch,path", _u8_params())
+def test_evaluate_u8_matches_oracle(gpu, oracle_mod, dims, pop, batch, path):
+    torch = _torch()
+    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    popv = synthetic.random_population(pop, c, seed=c + 7 * batch, scale=0.15)
+    rng = np.random.default_rng(batch)
+    levels = rng.integers(0, 256, size=(batch, dims[0])).astype(np.uint8)
+    y = rng.integers(0, dims[-1], size=batch).astype(np.int32)
+    f_inh = rng.normal(-2.3, 0.1, size=pop).astype(np.float32)
+    pd = to_device_pop(popv, cp)
+    xd, yd = torch.from_numpy(levels).cuda(), torch.from_numpy(y).cuda()
+    f_raw = torch.empty(pop, dtype=torch.float32, device="cuda")
+    f_adj = torch.empty_like(f_raw)
+    cor = torch.empty(pop, dtype=torch.int32, device="cuda")
+    gpu.leea_evaluate_u8(pop, dims, pd, xd, 255.0, yd, batch, 0.3, torch.from_numpy(f_inh).cuda(), f_raw, f_adj, cor,
+                         eval_path=path)
+    assert gpu.leea_device_status() == 0
+    x64 = levels.astype(np.float64) / 255.0
+    f_ref, cor_ref, logits = oracle_mod.evaluate(popv.astype(np.float64), dims, x64, y, want_logits=True)
+    assert_fitness_close(f_raw.cpu().numpy(), f_ref)
+    assert_correct_close(cor.cpu().numpy(), cor_ref, logits)
+    adj_ref = oracle_mod.inherit(float(np.float32(0.3)), f_inh.astype(np.float64), f_ref, first=False)
+    assert_fitness_close(f_adj.cpu().numpy(), adj_ref, "f_adj")
+
+
+def test_evaluate_u8_tensor_rejects_large_batches(gpu):
+    torch = _torch()
+    dims = [784, 112, 10]
+    cp = gpu.leea_padded_params(dims)
+    pd = torch.zeros((2, cp), dtype=torch.float32, device="cuda")
+    x = torch.zeros((129, 784), dtype=torch.uint8, device="cuda")
+    y = torch.zeros(129, dtype=torch.int32, device="cuda")
+    f = torch.empty(2, dtype=torch.float32, device="cuda")
+    with pytest.raises(gpu.LeeaError):
+        gpu.leea_evaluate_u8(2, dims, pd, x, 255.0, y, 129, 1.0, None, f, eval_path=gpu.EVAL_TENSOR)
+    with pytest.raises(gpu.LeeaError):
+        gpu.leea_evaluate_u8(2, dims, pd, x, 0.0, y, 129, 1.0, None, f)
+
+
+def test_evaluate_u8_clones_and_zero_weights(gpu):
+    torch = _torch()
+    dims, pop, batch = [784, 112, 10], 7, 100
+    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    x, y = synthetic.make_split(batch, seed=4)
+    popv = np.zeros((pop, c), dtype=np.float32)
+    popv[3:] = synthetic.random_population(1, c, seed=5)
+    pd = to_device_pop(popv, cp)
+    f_raw = torch.empty(pop, dtype=torch.float32, device="cuda")
+    cor = torch.empty(pop, dtype=torch.int32, device="cuda")
+    gpu.leea_evaluate_u8(pop, dims, pd, torch.from_numpy(synthetic.to_levels(x)).cuda(), 255.0,
+                         torch.from_numpy(y).cuda(), batch, 1.0, None, f_raw, None, cor, eval_path=gpu.EVAL_TENSOR)
+    assert gpu.leea_device_status() == 0
+    f = f_raw.cpu().numpy()
+    assert np.all(np.abs(f[:3] + np.log(10.0)) < 1e-6)
+    assert (cor.cpu().numpy()[:3] == (y == 0).sum()).all()
+    assert f[3] == f[4] == f[5] == f[6]
+
+
+def test_u8_and_float_inputs_agree(gpu):
+    # The same images as float x = k/255 and as levels k: both paths within
+    # the fitness tolerance of each other at the full workload size.
+    torch = _torch()
+    dims, pop, batch = [784, 112, 10], 1000, 100
+    cp = gpu.leea_padded_params(dims)
+    pd = torch.empty((pop, cp), dtype=torch.float32, device="cuda")
+    gpu.leea_init_population(pop, dims, 0, 17, pd)
+    x, y = synthetic.make_split(batch, seed=9)
+    yd = torch.from_numpy(y).cuda()
+    f_float = torch.empty(pop, dtype=torch.float32, device="cuda")
+    f_u8 = torch.empty(pop, dtype=torch.float32, device="cuda")
+    gpu.leea_evaluate(pop, dims, pd, torch.from_numpy(x).cuda(), yd, batch, 1.0, None, f_float, eval_path=1)
+    gpu.leea_evaluate_u8(pop, dims, pd, torch.from_numpy(synthetic.to_levels(x)).cuda(), 255.0, yd, batch, 1.0, None,
+                         f_u8, eval_path=2)
+    assert gpu.leea_device_status() == 0
+    assert_fitness_close(f_u8.cpu().numpy(), f_float.cpu().numpy().astype(np.float64), "u8 vs float")
