@@ -35,7 +35,7 @@ PARAMS = dict(xo_op=0, xo_gene_p=0.5, sel_op=0, rho=0.5, n_elite=1, p_c=0.5, sig
 WORKLOAD = ("P=1000 MLPs 784-112-10 (89,050 params, FP32), batch 100 synthetic 28x28 images; uniform crossover "
             "p_C=0.5, truncation rho=0.5, elitism 1, mutation sigma=0.005 on 10% of genes, alpha=1")
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
-STAGES = ("rank", "select", "breed", "evaluate")
+STAGES = ("select", "breed", "evaluate")
 
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
@@ -329,7 +329,6 @@ def run_native(args, rank: int, world: int, local_rank: int):
         "evaluate": (("hbm", 4.0 * c * POP / 1e9, "GB/s", hbm_peak) if tensor_eval else
                      ("alu", 2.0 * POP * BATCH * (d0 * h + h * d_out) / 1e12, "TFLOP/s",
                       SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12)),
-        "rank": ("latency", None, None, None),
         "select": ("latency", None, None, None),
     }
     kernels = {}

@@ -187,8 +187,8 @@ leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
 /* leea_evaluate for minibatches of 8-bit levels: x_u8_dev is uint8[batch][d_0]
  * and the input value is x = k / x_div (x_div = 255 for images stored as
  * bytes, as MNIST's are).  The tensor-core path needs batch <= 128,
- * d_0 % 4 == 0, h % 16 == 0, h + round_up(8 ceil(d_0 / 16), 16) <= 512 and
- * d_out <= 16.  It forms layer 1 from exact products: the levels are exact
+ * d_0 % 4 == 0, h % 16 == 0, h <= 128, h + round_up(8 ceil(d_0 / 16), 16) <= 512
+ * and d_out <= 16.  It forms layer 1 from exact products: the levels are exact
  * in BF16 and each weight is split exactly into three BF16 pieces, so only
  * the tensor core's FP32 accumulation rounds.  Otherwise, or with
  * LEEA_EVAL_SIMT, the CUDA-core kernel computes x = k / x_div in FP32.
@@ -288,9 +288,9 @@ uint32_t leea_generation_index(const leea_state* s);
 int64_t leea_state_num_params(const leea_state* s);
 
 /* Per-stage timing with CUDA events recorded on the object's stream around
- * each kernel of leea_generation.  Stages: 0 rank, 1 select, 2 breed,
- * 3 evaluate. */
-#define LEEA_NUM_STAGES 4
+ * each kernel of leea_generation.  Stages: 0 ranking + selection (one fused
+ * launch for pop <= 4096), 1 breeding, 2 evaluation. */
+#define LEEA_NUM_STAGES 3
 leea_status leea_profile_enable(leea_state* s, int32_t enable);
 
 /* Synchronises, then returns per stage the summed kernel time in ms and the

@@ -10,10 +10,16 @@
 //                        cp.async.bulk, tracked by transaction-count mbarriers;
 //   warps 1-16           take a stage, compute the child chunk and write it
 //                        with 128-bit stores, then release the stage.
-// A consumer thread owns blocks of four consecutive genes, which is exactly
-// one Philox block of each per-gene stream.  Normals are only generated for
-// blocks in which some gene is masked for mutation.  Every mbarrier wait is
-// bounded in time; on expiry the kernel sets kStatusBreedTimeout and exits.
+// Work items walk the children alternately from the front (elites, crossover
+// children) and the back (mutation children), so every SM mixes the
+// HBM-heavier crossover items with the arithmetic-heavier mutation items.
+// A consumer thread owns blocks of four consecutive genes (two per chunk),
+// which is exactly one Philox block of each per-gene stream.  In mutation
+// children only the Box-Muller pairs that hold a masked gene are generated,
+// and a warp first gathers them into a dense job list (ballot-free prefix
+// scan over the lanes) so that normals are computed by consecutive lanes
+// instead of by whichever lane happens to own a masked gene.  Every mbarrier
+// wait is bounded in time; on expiry the kernel sets kStatusBreedTimeout.
 #include "leea_internal.h"
 #include "philox.cuh"
 #include "tc_ptx.cuh"
@@ -88,51 +94,131 @@ __device__ __forceinline__ void raise_abort(volatile int* abort_flag, unsigned i
     atomicOr(status, kStatusBreedTimeout);
 }
 
-// The four child genes of block q (genes 4q .. 4q+3).
-__device__ __forceinline__ float4 breed_block(const BreedArgs& a, int32_t kind, uint32_t j, uint32_t q, float4 va,
-                                              float4 vb)
+constexpr int kBlocksPerLane = 2;  // 4096-gene chunk = 1024 blocks = 512 consumers x 2
+static_assert(kChunk / 4 == kBlocksPerLane * 32 * kConsumerWarps, "consumers must tile a chunk exactly");
+
+// Zero the padding genes (>= c) of block q.
+__device__ __forceinline__ float4 clear_padding(float4 v, uint32_t q, int64_t c)
 {
-    float v[4] = { va.x, va.y, va.z, va.w };
+    const int64_t i0 = 4 * static_cast<int64_t>(q);
+    if (i0 + 3 >= c) {
+        if (i0 + 0 >= c) v.x = 0.0f;
+        if (i0 + 1 >= c) v.y = 0.0f;
+        if (i0 + 2 >= c) v.z = 0.0f;
+        if (i0 + 3 >= c) v.w = 0.0f;
+    }
+    return v;
+}
+
+// Elite copy, uniform or arithmetic crossover of block q.
+__device__ __forceinline__ float4 cross_block(const BreedArgs& a, const PhiloxKeys& key, int32_t kind, uint32_t j,
+                                              uint32_t q, float4 va, float4 vb)
+{
     if (kind == 1) {
-        const float w2[4] = { vb.x, vb.y, vb.z, vb.w };
         if (a.xo_op == 0) {
-            const uint4 r = stream_block(a.seed, kTagXo, a.gen, j, q);
-            const uint32_t rw[4] = { r.x, r.y, r.z, r.w };
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = hits(rw[k], a.thr_xo) ? w2[k] : v[k];
+            const uint4 r = philox_keyed(make_uint4(q, j, a.gen, kTagXo), key);
+            va.x = hits(r.x, a.thr_xo) ? vb.x : va.x;
+            va.y = hits(r.y, a.thr_xo) ? vb.y : va.y;
+            va.z = hits(r.z, a.thr_xo) ? vb.z : va.z;
+            va.w = hits(r.w, a.thr_xo) ? vb.w : va.w;
         } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) v[k] = 0.5f * (v[k] + w2[k]);
-        }
-    } else if (kind == 2) {
-        const uint4 r = stream_block(a.seed, kTagMutMask, a.gen, j, q);
-        const bool m0 = hits(r.x, a.thr_mut), m1 = hits(r.y, a.thr_mut);
-        const bool m2 = hits(r.z, a.thr_mut), m3 = hits(r.w, a.thr_mut);
-        if (m0 | m1 | m2 | m3) {
-            const uint4 n = stream_block(a.seed, kTagNormal, a.gen, j, q);
-            if (m0 | m1) {
-                const float2 z = box_muller(n.x, n.y);
-                if (m0) v[0] = fmaf(a.sigma, z.x, v[0]);
-                if (m1) v[1] = fmaf(a.sigma, z.y, v[1]);
-            }
-            if (m2 | m3) {
-                const float2 z = box_muller(n.z, n.w);
-                if (m2) v[2] = fmaf(a.sigma, z.x, v[2]);
-                if (m3) v[3] = fmaf(a.sigma, z.y, v[3]);
-            }
+            va = make_float4(0.5f * (va.x + vb.x), 0.5f * (va.y + vb.y), 0.5f * (va.z + vb.z), 0.5f * (va.w + vb.w));
         }
     } else if (kind == kKindInvalid) {
         const float nan = __int_as_float(0x7FC00000);
-        v[0] = v[1] = v[2] = v[3] = nan;
+        va = make_float4(nan, nan, nan, nan);
     }
-    // Genes past c are padding and stay zero whatever the operator.
-    const int64_t i0 = 4 * static_cast<int64_t>(q);
-    if (i0 + 3 >= a.c) {
+    return va;
+}
+
+// Mutation of this lane's kBlocksPerLane blocks q[g] (valid where live[g]).
+// Slot s = 2 g + pair names the Box-Muller pair (genes 4q + 2 pair, +1).
+__device__ __forceinline__ void mutate_blocks(const BreedArgs& a, const PhiloxKeys& key, uint32_t j,
+                                              const uint32_t (&q)[kBlocksPerLane], const bool (&live)[kBlocksPerLane],
+                                              float4 (&v)[kBlocksPerLane], int lane)
+{
+    constexpr int kSlots = 2 * kBlocksPerLane;
+    uint32_t hit[kBlocksPerLane];  // 4 bits: which genes of the block mutate
+    uint32_t need = 0;             // kSlots bits: which pairs need normals
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (i0 + k >= a.c) v[k] = 0.0f;
+    for (int g = 0; g < kBlocksPerLane; ++g) {
+        hit[g] = 0;
+        if (live[g]) {
+            const uint4 r = philox_keyed(make_uint4(q[g], j, a.gen, kTagMutMask), key);
+            hit[g] = (hits(r.x, a.thr_mut) ? 1u : 0u) | (hits(r.y, a.thr_mut) ? 2u : 0u) |
+                     (hits(r.z, a.thr_mut) ? 4u : 0u) | (hits(r.w, a.thr_mut) ? 8u : 0u);
+        }
+        need |= ((hit[g] & 3u) ? 1u : 0u) << (2 * g);
+        need |= ((hit[g] & 12u) ? 1u : 0u) << (2 * g + 1);
     }
-    return make_float4(v[0], v[1], v[2], v[3]);
+    // Exclusive prefix of the per-lane job counts: jobs are numbered by lane,
+    // then by slot.
+    const uint32_t cnt = __popc(need);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, off);
+        if (lane >= off) incl += o;
+    }
+    const uint32_t excl = incl - cnt;
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+
+    float2 z[kSlots];
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) z[sl] = make_float2(0.f, 0.f);
+    for (uint32_t base = 0; base < total; base += 32) {
+        const uint32_t job = base + static_cast<uint32_t>(lane);
+        // Owner lane o: the last lane whose exclusive prefix is <= job.
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = o + step;
+            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, cand & 31);
+            if (cand < 32 && e <= job) o = cand;
+        }
+        const uint32_t mo = __shfl_sync(0xFFFFFFFFu, need, o);
+        const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, o);
+        float2 zz = make_float2(0.f, 0.f);
+        if (job < total) {
+            // The (job - eo)-th set slot of the owner.
+            uint32_t nth = job - eo, slot = 0, mm = mo;
+#pragma unroll
+            for (int sl = 0; sl < kSlots; ++sl) {
+                if (mm & 1u) {
+                    if (nth == 0) { slot = sl; break; }
+                    --nth;
+                }
+                mm >>= 1;
+            }
+            // Lanes of a warp own consecutive blocks (q[g] - lane is the same
+            // for every lane): shift this lane's block g to the owner's.
+            uint32_t qg = q[0];
+#pragma unroll
+            for (int g = 1; g < kBlocksPerLane; ++g)
+                if (static_cast<uint32_t>(g) == (slot >> 1)) qg = q[g];
+            const uint32_t qb = qg - static_cast<uint32_t>(lane) + static_cast<uint32_t>(o);
+            const uint4 n = philox_keyed(make_uint4(qb, j, a.gen, kTagNormal), key);
+            zz = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
+        }
+        // Every lane fetches the normals of its own slots numbered in this pass.
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const uint32_t id = excl + __popc(need & ((1u << sl) - 1u));
+            const bool mine = ((need >> sl) & 1u) && id >= base && id < base + 32;
+            const int src = mine ? static_cast<int>(id - base) : lane;
+            const float zx = __shfl_sync(0xFFFFFFFFu, zz.x, src);
+            const float zy = __shfl_sync(0xFFFFFFFFu, zz.y, src);
+            if (mine) z[sl] = make_float2(zx, zy);
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < kBlocksPerLane; ++g) {
+        const float2 z0 = z[2 * g], z1 = z[2 * g + 1];
+        if (hit[g] & 1u) v[g].x = fmaf(a.sigma, z0.x, v[g].x);
+        if (hit[g] & 2u) v[g].y = fmaf(a.sigma, z0.y, v[g].y);
+        if (hit[g] & 4u) v[g].z = fmaf(a.sigma, z1.x, v[g].z);
+        if (hit[g] & 8u) v[g].w = fmaf(a.sigma, z1.y, v[g].w);
+    }
 }
 
 __global__ void __launch_bounds__(kBreedThreads, 1)
@@ -167,8 +253,9 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
                     ok = false;
                     break;
                 }
-                const int32_t j = static_cast<int32_t>(it / chunks_per_child);
-                const int32_t ck = static_cast<int32_t>(it - static_cast<int64_t>(j) * chunks_per_child);
+                const int32_t ci = static_cast<int32_t>(it / chunks_per_child);
+                const int32_t ck = static_cast<int32_t>(it - static_cast<int64_t>(ci) * chunks_per_child);
+                const int32_t j = (ci & 1) ? a.pop - 1 - (ci >> 1) : (ci >> 1);
                 if (j != cur_j) {
                     cur_j = j;
                     cur_kind = kind[j];
@@ -204,6 +291,7 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
     } else {
         // ------------------------------------------------------------ consumers
         const int ct = threadIdx.x - 32;
+        const PhiloxKeys key = philox_keys(a.seed);
         uint32_t stage = 0, phase = 0;
         for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
             if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kWaitLimitNs)) {
@@ -216,11 +304,33 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
             float4* O = reinterpret_cast<float4*>(children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
             const int nq = m.len >> 2;
             const uint32_t q0 = static_cast<uint32_t>(m.g0) >> 2;
-#pragma unroll 2
-            for (int t = ct; t < nq; t += 32 * kConsumerWarps) {
-                const float4 va = (m.kind >= 0) ? A[t] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float4 vb = (m.kind == 1) ? B[t] : va;
-                O[t] = breed_block(a, m.kind, static_cast<uint32_t>(m.j), q0 + static_cast<uint32_t>(t), va, vb);
+            const uint32_t j = static_cast<uint32_t>(m.j);
+            uint32_t q[kBlocksPerLane];
+            bool live[kBlocksPerLane];
+            float4 v[kBlocksPerLane];
+#pragma unroll
+            for (int g = 0; g < kBlocksPerLane; ++g) {
+                const int t = ct + g * 32 * kConsumerWarps;
+                live[g] = t < nq;
+                q[g] = q0 + static_cast<uint32_t>(t);
+                v[g] = (live[g] && m.kind >= 0) ? A[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            if (m.kind == 2) {
+                mutate_blocks(a, key, j, q, live, v, lane);
+            } else {
+#pragma unroll
+                for (int g = 0; g < kBlocksPerLane; ++g) {
+                    const int t = ct + g * 32 * kConsumerWarps;
+                    if (live[g]) {
+                        const float4 vb = (m.kind == 1) ? B[t] : v[g];
+                        v[g] = cross_block(a, key, m.kind, j, q[g], v[g], vb);
+                    }
+                }
+            }
+#pragma unroll
+            for (int g = 0; g < kBlocksPerLane; ++g) {
+                const int t = ct + g * 32 * kConsumerWarps;
+                if (live[g]) O[t] = clear_padding(v[g], q[g], a.c);
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&s.empty[stage]);

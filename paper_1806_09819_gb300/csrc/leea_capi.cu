@@ -183,7 +183,7 @@ leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop
     const bool tc_ok = eval_u8_tc_supported(net, batch, pop_dev);
     if (path == LEEA_EVAL_TENSOR && !tc_ok)
         return fail(LEEA_EINVAL, "tensor-core evaluation of 8-bit inputs needs batch <= 128, d_0 %% 4 == 0, "
-                                 "h %% 16 == 0, h + round_up(8 ceil(d_0/16), 16) <= 512, d_out <= 16 and a "
+                                 "h %% 16 == 0, h <= 128, h + round_up(8 ceil(d_0/16), 16) <= 512, d_out <= 16 and a "
                                  "16-byte aligned population");
     cudaError_t err;
     if (tc_ok && path != LEEA_EVAL_SIMT) {
@@ -439,9 +439,9 @@ constexpr int kProfRing = 4096;
 
 struct ProfileRing {
     cudaEvent_t ev[LEEA_NUM_STAGES][2][kProfRing];
-    int n[LEEA_NUM_STAGES] = { 0, 0, 0, 0 };
-    double ms[LEEA_NUM_STAGES] = { 0, 0, 0, 0 };
-    int64_t launches[LEEA_NUM_STAGES] = { 0, 0, 0, 0 };
+    int n[LEEA_NUM_STAGES] = {};
+    double ms[LEEA_NUM_STAGES] = {};
+    int64_t launches[LEEA_NUM_STAGES] = {};
     bool created = false;
 };
 
@@ -602,18 +602,13 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         const uint32_t g = s->gen + 1;
         {
             StageScope sc(s, 0);
-            LEEA_CUDA_TRY(launch_rank(s->pop, s->f_adj, s->order, s->stream), "rank kernel");
+            const SelectArgs a = select_args(s->pop, &s->prm, s->seed, g);
+            LEEA_CUDA_TRY(launch_rank_select(a, s->f_adj, s->order, s->par1, s->par2, s->kind, s->f_inh, s->stream),
+                          "rank/select kernel");
             sc.done();
         }
         {
             StageScope sc(s, 1);
-            const SelectArgs a = select_args(s->pop, &s->prm, s->seed, g);
-            LEEA_CUDA_TRY(launch_select(a, s->f_adj, s->order, s->par1, s->par2, s->kind, s->f_inh, s->stream),
-                          "select kernel");
-            sc.done();
-        }
-        {
-            StageScope sc(s, 2);
             const BreedArgs a = breed_args(s->pop, s->net, &s->prm, s->seed, g);
             unsigned int* status = device_status_ptr();
             if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
@@ -626,7 +621,7 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         s->gen = g;
     }
     {
-        StageScope sc(s, 3);
+        StageScope sc(s, 2);
         if (u8)
             st = dispatch_eval_u8(s->net, s->pop, s->popbuf[s->cur], static_cast<const uint8_t*>(x_dev), x_div, y_dev,
                                   batch, s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,

@@ -14,14 +14,15 @@
 //
 // Warp roles (persistent CTA, one per SM, individuals strided by gridDim.x):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
-//   warps 1-8   weight loaders: prefetch the next individual's W1 into L2,
-//               load FP32 W1 with 128-bit loads, split into BF16 pieces and
-//               store them swizzled into the stage ring
-//   warps 9-12  write the batch into TMEM once; then the epilogue (bias,
+//   warp 1      TMA producer: FP32 W1 tiles (h rows x 64 K) into a raw ring
+//   warps 2-9   converters: split each raw tile into three BF16 pieces and
+//               store them swizzled into the piece ring the MMAs read
+//   warps 10-13 write the batch into TMEM once; then the epilogue (bias,
 //               ReLU, layer 2 with W2 staged transposed in shared memory,
 //               softmax cross-entropy, fixed-order batch sum, inheritance)
 // Every mbarrier wait is bounded in time; on expiry the kernel sets
 // kStatusEvalTimeout, drains its MMAs and exits.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "leea_internal.h"
@@ -31,10 +32,13 @@ namespace leea {
 
 namespace {
 
-constexpr int kLoaderWarps = 8;
-constexpr int kU8Threads = 32 * (1 + kLoaderWarps + 4);
+constexpr int kLoaderWarps = 8;    // converter warps
+constexpr int kFirstLoaderWarp = 2;
+constexpr int kFirstEpilogueWarp = kFirstLoaderWarp + kLoaderWarps;
+constexpr int kU8Threads = 32 * (kFirstEpilogueWarp + 4);
 constexpr int kKStage = 64;        // K elements per stage: one 128-byte BF16 row
-constexpr int kU8Stages = 4;
+constexpr int kPieceStages = 2;    // BF16 piece ring
+constexpr int kMaxRawStages = 4;   // FP32 raw ring (TMA)
 constexpr int kMaxOutU8 = 16;
 constexpr int kRowBatch = 8;       // 16-row groups a loader thread holds in registers at once
 constexpr uint32_t kTmemCols = 512;
@@ -42,7 +46,7 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr uint64_t kDrainLimitNs = 200000000ull;
 
 struct EvalU8Args {
-    int32_t pop, k, h, d_out, dpad, batch, k_stages, k16;
+    int32_t pop, k, h, d_out, dpad, batch, k_stages, k16, raw_stages;
     int64_t c_pad;
     float inv_div, alpha;
     uint32_t a_col;  // first TMEM column of the A operand (the accumulator uses 0 .. h-1)
@@ -57,12 +61,13 @@ struct EvalU8Args {
 };
 
 struct U8Smem {
-    uint8_t* ring;        // kU8Stages x 3 pieces x h x 128 B
-    uint32_t piece_bytes;
+    uint8_t* ring;        // kPieceStages x 3 pieces x h x 128 B (1024-aligned)
+    uint8_t* raw;         // raw_stages x h x 256 B (FP32 rows of 64 K-elements)
+    uint32_t piece_bytes, raw_bytes;
     float* w2t;           // [h][dpad]
     float* b1;            // [h]
     float* b2;            // [16]
-    uint64_t *full, *empty, *acc_full, *acc_empty, *a_ready, *drain;
+    uint64_t *full, *empty, *raw_full, *raw_empty, *acc_full, *acc_empty, *a_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
@@ -75,7 +80,9 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     U8Smem s;
     s.ring = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
     s.piece_bytes = static_cast<uint32_t>(a.h) * 128u;
-    uint8_t* p = s.ring + kU8Stages * 3u * s.piece_bytes;
+    s.raw_bytes = static_cast<uint32_t>(a.h) * 256u;
+    s.raw = s.ring + kPieceStages * 3u * s.piece_bytes;
+    uint8_t* p = s.raw + a.raw_stages * s.raw_bytes;
     s.w2t = reinterpret_cast<float*>(p);
     p += sizeof(float) * a.h * a.dpad;
     s.b1 = reinterpret_cast<float*>(p);
@@ -84,8 +91,10 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     p += sizeof(float) * 16;
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.full = bars;
-    s.empty = bars + kU8Stages;
-    s.acc_full = bars + 2 * kU8Stages;
+    s.empty = bars + kPieceStages;
+    s.raw_full = bars + 2 * kPieceStages;
+    s.raw_empty = s.raw_full + a.raw_stages;
+    s.acc_full = s.raw_empty + a.raw_stages;
     s.acc_empty = s.acc_full + 1;
     s.a_ready = s.acc_full + 2;
     s.drain = s.acc_full + 3;
@@ -98,10 +107,18 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     return s;
 }
 
-size_t u8_smem_bytes(int32_t h, int32_t dpad)
+size_t u8_smem_bytes(int32_t h, int32_t dpad, int32_t raw_stages)
 {
-    return 1024 + static_cast<size_t>(kU8Stages) * 3 * h * 128 + sizeof(float) * (h * dpad + h + 16) +
-           8 * (2 * kU8Stages + 4) + 64;
+    return 1024 + static_cast<size_t>(kPieceStages) * 3 * h * 128 + static_cast<size_t>(raw_stages) * h * 256 +
+           sizeof(float) * (h * dpad + h + 16) + 8 * (2 * kPieceStages + 2 * raw_stages + 4) + 64;
+}
+
+// Deepest raw ring (2..4 stages) that fits in 227 KB of shared memory; 0 if none.
+int32_t u8_raw_stages(int32_t h, int32_t dpad)
+{
+    for (int32_t st = kMaxRawStages; st >= 2; --st)
+        if (u8_smem_bytes(h, dpad, st) <= 227u * 1024u) return st;
+    return 0;
 }
 
 __device__ __forceinline__ void raise_abort(const U8Smem& s, const EvalU8Args& a)
@@ -128,23 +145,23 @@ __device__ __forceinline__ void split3(float w, uint32_t& p1, uint32_t& p2, uint
     p3 = bf16_bits(r2);
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(src)), "r"(bytes)
-                 : "memory");
-}
-
-__global__ void __launch_bounds__(kU8Threads, 1) eval_u8_kernel(const EvalU8Args a)
+__global__ void __launch_bounds__(kU8Threads, 1)
+eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
 {
     extern __shared__ uint8_t smem_raw[];
     const U8Smem s = carve(smem_raw, a);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kU8Stages; ++i) {
+        for (int i = 0; i < kPieceStages; ++i) {
             ptx::mbar_init(&s.full[i], kLoaderWarps);
             ptx::mbar_init(&s.empty[i], 1);
         }
+        for (int i = 0; i < a.raw_stages; ++i) {
+            ptx::mbar_init(&s.raw_full[i], 1);
+            ptx::mbar_init(&s.raw_empty[i], kLoaderWarps);
+        }
+        ptx::tma_prefetch_map(&tmap_w);
         ptx::mbar_init(s.acc_full, 1);
         ptx::mbar_init(s.acc_empty, 128);
         ptx::mbar_init(s.a_ready, 128);
@@ -195,7 +212,7 @@ __global__ void __launch_bounds__(kU8Threads, 1) eval_u8_kernel(const EvalU8Args
                         }
                     }
                     ptx::mma_commit(&s.empty[stage]);
-                    if (++stage == kU8Stages) { stage = 0; phase ^= 1u; }
+                    if (++stage == kPieceStages) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
                 ptx::mma_commit(s.acc_full);
@@ -205,70 +222,91 @@ __global__ void __launch_bounds__(kU8Threads, 1) eval_u8_kernel(const EvalU8Args
             volatile int never = 0;
             ptx::mbar_wait_bounded(s.drain, 0u, &never, ok ? kWaitLimitNs : kDrainLimitNs);
         }
-    } else if (warp <= kLoaderWarps) {
-        // ------------------------------------------------------------ weight loaders
-        const int lt = threadIdx.x - 32;
-        const int row0 = lt >> 4, c4 = lt & 15;  // 16 threads cover one row's 64 K-elements
-        const int groups = a.h >> 4;
-        uint32_t stage = 0, phase = 0;
-        bool ok = true;
-        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
-            const float* w1 = a.popv + static_cast<int64_t>(p) * a.c_pad;
-            if (lt == 0) {
-                const int pn = p + gridDim.x;  // stream the next individual's weights into L2
-                if (pn < a.pop)
-                    prefetch_l2(a.popv + static_cast<int64_t>(pn) * a.c_pad,
-                                static_cast<uint32_t>(a.c_pad * 4 < 0x7FFFFFF0 ? a.c_pad * 4 : 0x7FFFFFF0) & ~15u);
-            }
-            for (int kc = 0; kc < a.k_stages; ++kc) {
-                const int k = kc * kKStage + 4 * c4;
-                uint8_t* sb = s.ring + stage * 3u * s.piece_bytes;
-                for (int g0 = 0; g0 < groups; g0 += kRowBatch) {
-                    float4 v[kRowBatch];
-#pragma unroll
-                    for (int u = 0; u < kRowBatch; ++u) {
-                        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                        if (g0 + u < groups && k < a.k)
-                            v[u] = __ldg(reinterpret_cast<const float4*>(
-                                w1 + static_cast<int64_t>(row0 + 16 * (g0 + u)) * a.k + k));
-                    }
-                    if (g0 == 0 &&
-                        !ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ TMA producer (raw FP32 tiles)
+        if (lane == 0) {
+            uint32_t stage = 0, phase = 0;
+            uint32_t issued_mask = 0, parity_mask = 0;
+            bool ok = true;
+            for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+                for (int kc = 0; kc < a.k_stages; ++kc) {
+                    if (!ptx::mbar_wait_bounded(&s.raw_empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
                         raise_abort(s, a);
                         ok = false;
                         break;
                     }
+                    ptx::mbar_arrive_expect_tx(&s.raw_full[stage], s.raw_bytes);
+                    ptx::tma_load_3d(s.raw + stage * s.raw_bytes, &tmap_w, &s.raw_full[stage], kc * kKStage, 0, p);
+                    issued_mask |= 1u << stage;
+                    parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
+                    if (++stage == static_cast<uint32_t>(a.raw_stages)) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (!ok) {  // let copies in flight land before the CTA exits
+                volatile int never = 0;
+                for (int i = 0; i < a.raw_stages; ++i)
+                    if (issued_mask & (1u << i))
+                        ptx::mbar_wait_bounded(&s.raw_full[i], (parity_mask >> i) & 1u, &never, kDrainLimitNs);
+            }
+        }
+    } else if (warp < kFirstEpilogueWarp) {
+        // ------------------------------------------------------------ converters
+        // Thread (row0, c4) converts K-elements 4 c4 .. 4 c4 + 3 of rows row0 + 16 u.
+        const int lt = threadIdx.x - 32 * kFirstLoaderWarp;
+        const int row0 = lt >> 4, c4 = lt & 15;
+        const int groups = a.h >> 4;
+        uint32_t rstage = 0, rphase = 0, stage = 0, phase = 0;
+        bool ok = true;
+        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+            for (int kc = 0; kc < a.k_stages; ++kc) {
+                if (!ptx::mbar_wait_bounded(&s.raw_full[rstage], rphase, s.abort_flag, kWaitLimitNs)) {
+                    raise_abort(s, a);
+                    ok = false;
+                    break;
+                }
+                const uint8_t* rb = s.raw + rstage * s.raw_bytes;
+                float4 v[kRowBatch];
 #pragma unroll
-                    for (int u = 0; u < kRowBatch; ++u) {
-                        if (g0 + u < groups) {
-                            const int r = row0 + 16 * (g0 + u);
-                            uint32_t q0[3], q1[3], q2[3], q3[3];
-                            split3(v[u].x, q0[0], q0[1], q0[2]);
-                            split3(v[u].y, q1[0], q1[1], q1[2]);
-                            split3(v[u].z, q2[0], q2[1], q2[2]);
-                            split3(v[u].w, q3[0], q3[1], q3[2]);
-                            const uint32_t off = static_cast<uint32_t>(r) * 128u +
-                                                 ((static_cast<uint32_t>(c4 >> 1) ^ static_cast<uint32_t>(r & 7)) << 4) +
-                                                 (static_cast<uint32_t>(c4 & 1) << 3);
+                for (int u = 0; u < kRowBatch; ++u)
+                    v[u] = u < groups ? *reinterpret_cast<const float4*>(rb + (row0 + 16 * u) * 256 + c4 * 16)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                __syncwarp();
+                if (lane == 0) ptx::mbar_arrive(&s.raw_empty[rstage]);
+                if (++rstage == static_cast<uint32_t>(a.raw_stages)) { rstage = 0; rphase ^= 1u; }
+                if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+                    raise_abort(s, a);
+                    ok = false;
+                    break;
+                }
+                uint8_t* sb = s.ring + stage * 3u * s.piece_bytes;
 #pragma unroll
-                            for (int piece = 0; piece < 3; ++piece) {
-                                const uint2 pk =
-                                    make_uint2(q0[piece] | (q1[piece] << 16), q2[piece] | (q3[piece] << 16));
-                                *reinterpret_cast<uint2*>(sb + piece * s.piece_bytes + off) = pk;
-                            }
+                for (int u = 0; u < kRowBatch; ++u) {
+                    if (u < groups) {
+                        const int r = row0 + 16 * u;
+                        uint32_t q0[3], q1[3], q2[3], q3[3];
+                        split3(v[u].x, q0[0], q0[1], q0[2]);
+                        split3(v[u].y, q1[0], q1[1], q1[2]);
+                        split3(v[u].z, q2[0], q2[1], q2[2]);
+                        split3(v[u].w, q3[0], q3[1], q3[2]);
+                        const uint32_t off = static_cast<uint32_t>(r) * 128u +
+                                             ((static_cast<uint32_t>(c4 >> 1) ^ static_cast<uint32_t>(r & 7)) << 4) +
+                                             (static_cast<uint32_t>(c4 & 1) << 3);
+#pragma unroll
+                        for (int piece = 0; piece < 3; ++piece) {
+                            const uint2 pk = make_uint2(q0[piece] | (q1[piece] << 16), q2[piece] | (q3[piece] << 16));
+                            *reinterpret_cast<uint2*>(sb + piece * s.piece_bytes + off) = pk;
                         }
                     }
                 }
-                if (!ok) break;
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&s.full[stage]);
-                if (++stage == kU8Stages) { stage = 0; phase ^= 1u; }
+                if (++stage == kPieceStages) { stage = 0; phase ^= 1u; }
             }
         }
     } else {
         // ------------------------------------------------------------ batch into TMEM, then epilogue
-        const int et = threadIdx.x - 32 * (1 + kLoaderWarps);
+        const int et = threadIdx.x - 32 * kFirstEpilogueWarp;
         const int q = warp & 3;  // TMEM lane quarter of this warp
         const int row = q * 32 + lane;
         const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
@@ -276,13 +314,33 @@ __global__ void __launch_bounds__(kU8Threads, 1) eval_u8_kernel(const EvalU8Args
             // Row `row` of the batch as BF16 pairs (k even in the low half).
             const uint8_t* xr = a.x + static_cast<int64_t>(row) * a.k;
             const bool live = row < a.batch;
+            const bool vec = (a.k % 16 == 0) && ((reinterpret_cast<uintptr_t>(a.x) & 15u) == 0);
+#pragma unroll 2
             for (int c0 = 0; c0 < a.k16 / 2; c0 += 16) {
+                uint32_t bytes[8];  // the 32 levels of columns c0 .. c0+15
+                const int k0 = 2 * c0;
+                if (vec && live && k0 + 32 <= a.k) {
+                    const uint4 lo4 = __ldg(reinterpret_cast<const uint4*>(xr + k0));
+                    const uint4 hi4 = __ldg(reinterpret_cast<const uint4*>(xr + k0 + 16));
+                    bytes[0] = lo4.x; bytes[1] = lo4.y; bytes[2] = lo4.z; bytes[3] = lo4.w;
+                    bytes[4] = hi4.x; bytes[5] = hi4.y; bytes[6] = hi4.z; bytes[7] = hi4.w;
+                } else {
+#pragma unroll
+                    for (int w = 0; w < 8; ++w) {
+                        uint32_t word = 0;
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) {
+                            const int kk = k0 + 4 * w + b;
+                            if (live && kk < a.k) word |= static_cast<uint32_t>(xr[kk]) << (8 * b);
+                        }
+                        bytes[w] = word;
+                    }
+                }
                 uint32_t cols[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const int k0 = 2 * (c0 + i);
-                    const uint32_t lo = (live && k0 < a.k) ? static_cast<uint32_t>(xr[k0]) : 0u;
-                    const uint32_t hi = (live && k0 + 1 < a.k) ? static_cast<uint32_t>(xr[k0 + 1]) : 0u;
+                    const uint32_t pair = bytes[i >> 1] >> (16 * (i & 1));
+                    const uint32_t lo = pair & 0xFFu, hi = (pair >> 8) & 0xFFu;
                     cols[i] = (__float_as_uint(static_cast<float>(lo)) >> 16) |
                               (__float_as_uint(static_cast<float>(hi)) & 0xFFFF0000u);
                 }
@@ -402,19 +460,37 @@ __global__ void __launch_bounds__(kU8Threads, 1) eval_u8_kernel(const EvalU8Args
     }
 }
 
+typedef CUresult (*U8EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+U8EncodeTiledFn u8_encode_fn()
+{
+    static U8EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<U8EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
 }  // namespace
 
 bool eval_u8_tc_supported(const NetLayout& net, int32_t batch, const float* pop_dev)
 {
     if (net.n_layers != 2) return false;
     const int32_t k = net.dims[0], h = net.dims[1], d_out = net.dims[2];
-    if (k % 4 != 0 || h % 16 != 0 || h > 256 || d_out > kMaxOutU8 || batch < 1 || batch > 128) return false;
+    if (k % 4 != 0 || h % 16 != 0 || h > 16 * kRowBatch || d_out > kMaxOutU8 || batch < 1 || batch > 128) return false;
     const int32_t k16 = (k + 15) / 16 * 16;
     const int32_t a_cols = (k16 / 2 + 15) / 16 * 16;
     if (h + a_cols > static_cast<int32_t>(kTmemCols)) return false;
     if (reinterpret_cast<uintptr_t>(pop_dev) & 15u) return false;
     const int32_t dpad = (d_out + 3) / 4 * 4;
-    return u8_smem_bytes(h, dpad) <= 227u * 1024u;
+    return u8_raw_stages(h, dpad) >= 2 && u8_encode_fn() != nullptr;
 }
 
 cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
@@ -443,7 +519,23 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     a.f_adj = f_adj;
     a.correct = correct;
     a.status = status;
-    const size_t smem = u8_smem_bytes(a.h, a.dpad);
+    a.raw_stages = u8_raw_stages(a.h, a.dpad);
+    if (a.raw_stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = u8_smem_bytes(a.h, a.dpad, a.raw_stages);
+    U8EncodeTiledFn enc = u8_encode_fn();
+    if (!enc) return cudaErrorNotSupported;
+    CUtensorMap tw;
+    {
+        const cuuint64_t dims[3] = { static_cast<cuuint64_t>(a.k), static_cast<cuuint64_t>(a.h),
+                                     static_cast<cuuint64_t>(pop) };
+        const cuuint64_t strides[2] = { static_cast<cuuint64_t>(a.k) * 4u, static_cast<cuuint64_t>(net.c_pad) * 4u };
+        const cuuint32_t box[3] = { static_cast<cuuint32_t>(kKStage), static_cast<cuuint32_t>(a.h), 1 };
+        const cuuint32_t es[3] = { 1, 1, 1 };
+        if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(pop_dev), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
     int dev = 0, sms = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
@@ -452,7 +544,7 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     err = cudaFuncSetAttribute(eval_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     const int grid = pop < sms ? pop : sms;
-    eval_u8_kernel<<<grid, kU8Threads, smem, stream>>>(a);
+    eval_u8_kernel<<<grid, kU8Threads, smem, stream>>>(tw, a);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,10 @@ cudaError_t launch_rank(int32_t pop, const float* f_adj, int32_t* order, cudaStr
 cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t* order,
                           int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh,
                           cudaStream_t stream);
+// Ranking and selection in one launch (one CTA, bitonic sort in shared
+// memory) when pop <= 4096; otherwise the two kernels above in sequence.
+cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t* order, int32_t* par1,
+                               int32_t* par2, int32_t* kind, float* f_inh, cudaStream_t stream);
 cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t* par1,
                          const int32_t* par2, const int32_t* kind, float* children,
                          unsigned int* status, cudaStream_t stream);

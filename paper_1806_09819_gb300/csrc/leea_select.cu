@@ -82,13 +82,10 @@ __device__ __forceinline__ int32_t pick_parent(const SelectArgs& a, const float*
     return best;
 }
 
-__global__ void __launch_bounds__(256) select_kernel(SelectArgs a, const float* __restrict__ f_adj,
-                                                     const int32_t* __restrict__ order,
-                                                     int32_t* __restrict__ par1, int32_t* __restrict__ par2,
-                                                     int32_t* __restrict__ kind, float* __restrict__ f_inh)
+// Kind, parents and inherited fitness of child j (Algorithm 1; Section 3.1).
+__device__ __forceinline__ void select_child(const SelectArgs& a, const float* f_adj, const int32_t* order, int32_t j,
+                                             int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh)
 {
-    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= a.pop) return;
     SelStream st(a.seed, a.gen, static_cast<uint32_t>(j));
     int32_t k, p1, p2;
     float fi;
@@ -113,11 +110,74 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a, const float* 
     f_inh[j] = fi;
 }
 
+__global__ void __launch_bounds__(256) select_kernel(SelectArgs a, const float* __restrict__ f_adj,
+                                                     const int32_t* __restrict__ order,
+                                                     int32_t* __restrict__ par1, int32_t* __restrict__ par2,
+                                                     int32_t* __restrict__ kind, float* __restrict__ f_inh)
+{
+    const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < a.pop) select_child(a, f_adj, order, j, par1, par2, kind, f_inh);
+}
+
 cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t* order,
                           int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh,
                           cudaStream_t stream)
 {
     select_kernel<<<(a.pop + 255) / 256, 256, 0, stream>>>(a, f_adj, order, par1, par2, kind, f_inh);
+    return cudaGetLastError();
+}
+
+// Rank and select in one CTA for populations up to kFusedMaxPop: a bitonic
+// sort of the 64-bit rank keys in shared memory (padding keys sort last),
+// then one thread per child runs the selection against the sorted order.
+constexpr int kFusedThreads = 1024;
+constexpr int kFusedMaxPop = 4096;
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+rank_select_kernel(SelectArgs a, const float* __restrict__ f_adj, int32_t* __restrict__ order_out,
+                   int32_t* __restrict__ par1, int32_t* __restrict__ par2, int32_t* __restrict__ kind,
+                   float* __restrict__ f_inh)
+{
+    __shared__ uint64_t keys[kFusedMaxPop];
+    __shared__ int32_t order[kFusedMaxPop];
+    int n = 1;
+    while (n < a.pop) n <<= 1;
+    for (int i = threadIdx.x; i < n; i += kFusedThreads) keys[i] = i < a.pop ? rank_key(f_adj[i], i) : ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (n >> 1); t += kFusedThreads) {
+                // t-th compare-exchange pair of this pass
+                const int lo = 2 * stride * (t / stride) + (t % stride);
+                const int hi = lo + stride;
+                const bool ascending = (lo & size) == 0;
+                const uint64_t x = keys[lo], y = keys[hi];
+                if ((x > y) == ascending) {
+                    keys[lo] = y;
+                    keys[hi] = x;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = threadIdx.x; r < a.pop; r += kFusedThreads) {
+        const int32_t idx = static_cast<int32_t>(keys[r] & 0xFFFFFFFFu);
+        order[r] = idx;
+        order_out[r] = idx;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < a.pop; j += kFusedThreads) select_child(a, f_adj, order, j, par1, par2, kind, f_inh);
+}
+
+cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t* order, int32_t* par1, int32_t* par2,
+                               int32_t* kind, float* f_inh, cudaStream_t stream)
+{
+    if (a.pop > kFusedMaxPop) {
+        cudaError_t err = launch_rank(a.pop, f_adj, order, stream);
+        if (err != cudaSuccess) return err;
+        return launch_select(a, f_adj, order, par1, par2, kind, f_inh, stream);
+    }
+    rank_select_kernel<<<1, kFusedThreads, 0, stream>>>(a, f_adj, order, par1, par2, kind, f_inh);
     return cudaGetLastError();
 }
 

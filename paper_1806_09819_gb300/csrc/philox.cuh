@@ -73,3 +73,39 @@ __device__ __forceinline__ bool hits(uint32_t u, uint64_t thr)
 }
 
 }  // namespace leea
+
+namespace leea {
+
+// The ten round keys of Philox4x32-10 for one seed, computed once per thread
+// so that the rounds themselves are two wide multiplies and two xors.
+struct PhiloxKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ PhiloxKeys philox_keys(uint64_t seed)
+{
+    PhiloxKeys k;
+    uint32_t a = static_cast<uint32_t>(seed), b = static_cast<uint32_t>(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        k.k0[r] = a;
+        k.k1[r] = b;
+        a += kPhiloxW0;
+        b += kPhiloxW1;
+    }
+    return k;
+}
+
+__device__ __forceinline__ uint4 philox_keyed(uint4 ctr, const PhiloxKeys& k)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * ctr.x;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * ctr.z;
+        ctr = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ ctr.y ^ k.k0[round], static_cast<uint32_t>(p1),
+                         static_cast<uint32_t>(p0 >> 32) ^ ctr.w ^ k.k1[round], static_cast<uint32_t>(p0));
+    }
+    return ctr;
+}
+
+}  // namespace leea

@@ -21,8 +21,8 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = range(6)
 TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
 KIND_ELITE, KIND_CROSSOVER, KIND_MUTATION = 0, 1, 2
 EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR = 0, 1, 2
-NUM_STAGES = 4
-STAGES = ("rank", "select", "breed", "evaluate")
+NUM_STAGES = 3
+STAGES = ("select", "breed", "evaluate")  # select = ranking + selection
 
 
 class LeeaError(RuntimeError):

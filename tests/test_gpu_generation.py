@@ -195,7 +195,7 @@ def test_profiling_counts_launches(gpu):
     for _ in range(5):
         st.leea_generation(x, y)
     prof = st.leea_profile_read()
-    assert prof["evaluate"][1] == 5 and prof["breed"][1] == 4 and prof["rank"][1] == 4
+    assert prof["evaluate"][1] == 5 and prof["breed"][1] == 4 and prof["select"][1] == 4
     assert all(ms >= 0 for ms, _ in prof.values())
     assert st.leea_profile_read()["evaluate"] == (0.0, 0)
 

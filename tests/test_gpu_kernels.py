@@ -301,7 +301,7 @@ U8_CASES = [
 def _u8_tc_shape(dims, batch):
     k, h, d_out = dims
     a_cols = ((((k + 15) // 16) * 8 + 15) // 16) * 16
-    return k % 4 == 0 and h % 16 == 0 and h <= 256 and d_out <= 16 and batch <= 128 and h + a_cols <= 512
+    return k % 4 == 0 and h % 16 == 0 and h <= 128 and d_out <= 16 and batch <= 128 and h + a_cols <= 512
 
 
 def _u8_params():
