@@ -38,8 +38,12 @@
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with key
  * (seed & 0xffffffff, seed >> 32) and counter (n >> 2, entity, generation, tag);
- * draw n of a stream is word n & 3 of that block.  Because the generator is
- * counter-based, a run is reproducible from (seed, generation) alone.
+ * draw n of a stream is word n & 3 of that block.  The per-gene crossover and
+ * mutation masks use 16-bit draws instead: draw16 i is half i & 1 (the low
+ * half for even i) of word (i >> 1) & 3 of block i >> 3, and it hits
+ * probability q iff it is below floor(q 2^16) (always when q >= 1).  Because
+ * the generator is counter-based, a run is reproducible from (seed,
+ * generation) alone.
  */
 #ifndef LEEA_H
 #define LEEA_H
@@ -159,10 +163,10 @@ leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_de
 
 /* Crossover and mutation (Section 3.2) into a separate children buffer.
  * For child j and gene i: elite -> copy of parent 1; uniform crossover ->
- * parent 2's gene iff XO draw i < floor(xo_gene_p 2^32), else parent 1's;
+ * parent 2's gene iff XO draw16 i < floor(xo_gene_p 2^16), else parent 1's;
  * arithmetic crossover -> (a + b) / 2; mutation -> a + sigma z_i on genes whose
- * MUTMASK draw i < floor(mut_rate 2^32) (all genes when mut_rate = 1), with z_i
- * the Box-Muller normal of the NORMAL stream.  parents_dev and children_dev
+ * MUTMASK draw16 i < floor(mut_rate 2^16) (all genes when mut_rate = 1), with
+ * z_i the Box-Muller normal of the NORMAL stream.  parents_dev and children_dev
  * are float[pop][c_pad] and must not overlap. */
 leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                        const leea_params* p, uint64_t seed, uint32_t gen,

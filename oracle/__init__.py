@@ -105,6 +105,10 @@ def lib() -> ctypes.CDLL:
         L.leea_cpu_index.restype = u32
         L.leea_cpu_threshold.argtypes = [dbl]
         L.leea_cpu_threshold.restype = u64
+        L.leea_cpu_draw16.argtypes = [u64, u32, u32, u32, u32]
+        L.leea_cpu_draw16.restype = u32
+        L.leea_cpu_threshold16.argtypes = [dbl]
+        L.leea_cpu_threshold16.restype = u32
         L.leea_cpu_num_params.argtypes = [vp, i32]
         L.leea_cpu_num_params.restype = i64
         L.leea_cpu_counts.argtypes = [i32, P(_CParams), P(i32), P(i32), P(i32), P(i32)]
@@ -189,6 +193,14 @@ def index(u: int, m: int) -> int:
 
 def threshold(q: float) -> int:
     return int(lib().leea_cpu_threshold(float(q)))
+
+
+def draw16(seed: int, tag: int, gen: int, ent: int, i: int) -> int:
+    return int(lib().leea_cpu_draw16(seed, tag, gen, ent, i))
+
+
+def threshold16(q: float) -> int:
+    return int(lib().leea_cpu_threshold16(float(q)))
 
 
 # ---- layout ---------------------------------------------------------------

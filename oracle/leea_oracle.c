@@ -92,6 +92,24 @@ uint64_t leea_cpu_threshold(double q)
     return (uint64_t)floor(q * 4294967296.0);
 }
 
+/* 16-bit draw i of a stream, for per-gene masks: block i >> 3 carries eight
+ * of them, two per word, the even one in the low half. */
+uint32_t leea_cpu_draw16(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t i)
+{
+    uint32_t w[4];
+    stream_block(seed, tag, gen, ent, i >> 3, w);
+    uint32_t word = w[(i >> 1) & 3u];
+    return (i & 1u) ? (word >> 16) : (word & 0xFFFFu);
+}
+
+/* A 16-bit draw hits probability q iff it is below threshold16(q). */
+uint32_t leea_cpu_threshold16(double q)
+{
+    if (!(q > 0.0)) return 0;
+    if (q >= 1.0) return 65536u;
+    return (uint32_t)floor(q * 65536.0);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Layout and operator counts                                               */
 /* ------------------------------------------------------------------------ */
@@ -336,10 +354,10 @@ int leea_cpu_select(int32_t pop, const leea_cpu_params* prm, const double* f_adj
 
 /* ------------------------------------------------------------------------ */
 /* Crossover and mutation (Section 3.2), children j0 <= j < j1.              */
-/*   uniform:     gene i from parent 2 iff its XO draw hits xo_gene_p        */
+/*   uniform:     gene i from parent 2 iff its 16-bit XO draw hits xo_gene_p */
 /*   arithmetic:  (theta_1 + theta_2) / 2                                    */
-/*   mutation:    theta_1 + sigma * N(0,1) on genes whose MUTMASK draw hits  */
-/*                mut_rate (every gene when mut_rate = 1)                    */
+/*   mutation:    theta_1 + sigma * N(0,1) on genes whose 16-bit MUTMASK     */
+/*                draw hits mut_rate (every gene when mut_rate = 1)          */
 /*   elite:       unchanged copy                                             */
 /* ------------------------------------------------------------------------ */
 int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
@@ -351,8 +369,8 @@ int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
     if (c < 0 || pop <= 0 || !valid_params(prm) || !parents || !par1 || !par2 || !kind ||
         !children || j0 < 0 || j1 > pop || j0 > j1)
         return LEEA_CPU_EINVAL;
-    uint64_t thr_xo = leea_cpu_threshold((double)prm->xo_gene_p);
-    uint64_t thr_mut = leea_cpu_threshold((double)prm->mut_rate);
+    uint32_t thr_xo = leea_cpu_threshold16((double)prm->xo_gene_p);
+    uint32_t thr_mut = leea_cpu_threshold16((double)prm->mut_rate);
     double sigma = (double)prm->sigma;
     for (int32_t j = j0; j < j1; j++) {
         if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
@@ -365,14 +383,14 @@ int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                 v = a[i];
             } else if (kind[j] == LEEA_CPU_CROSSOVER) {
                 if (prm->xo_op == 0) {
-                    uint32_t u = leea_cpu_draw(seed, LEEA_CPU_TAG_XO, gen, (uint32_t)j, (uint32_t)i);
-                    v = ((uint64_t)u < thr_xo) ? b[i] : a[i];
+                    uint32_t u = leea_cpu_draw16(seed, LEEA_CPU_TAG_XO, gen, (uint32_t)j, (uint32_t)i);
+                    v = (u < thr_xo) ? b[i] : a[i];
                 } else {
                     v = 0.5 * (a[i] + b[i]);
                 }
             } else if (kind[j] == LEEA_CPU_MUTATION) {
-                uint32_t u = leea_cpu_draw(seed, LEEA_CPU_TAG_MUTMASK, gen, (uint32_t)j, (uint32_t)i);
-                if ((uint64_t)u < thr_mut)
+                uint32_t u = leea_cpu_draw16(seed, LEEA_CPU_TAG_MUTMASK, gen, (uint32_t)j, (uint32_t)i);
+                if (u < thr_mut)
                     v = a[i] + sigma * leea_cpu_normal(seed, LEEA_CPU_TAG_NORMAL, gen, (uint32_t)j, (uint32_t)i);
                 else
                     v = a[i];

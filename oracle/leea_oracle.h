@@ -17,7 +17,10 @@
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
  * the 64-bit seed, with the counter (n >> 2, entity, generation, tag); scalar
- * draw n of a stream is word (n & 3) of that block.
+ * draw n of a stream is word (n & 3) of that block.  The per-gene crossover
+ * and mutation masks use 16-bit draws: draw16 i is half (i & 1) (low half for
+ * even i) of word ((i >> 1) & 3) of block (i >> 3), and hits probability q iff
+ * it is below floor(q 2^16) (2^16 when q >= 1).
  */
 #ifndef LEEA_ORACLE_H
 #define LEEA_ORACLE_H
@@ -72,6 +75,8 @@ double leea_cpu_u01(uint32_t u);
 double leea_cpu_normal(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t i);
 uint32_t leea_cpu_index(uint32_t u, uint32_t m);
 uint64_t leea_cpu_threshold(double q);
+uint32_t leea_cpu_draw16(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t i);
+uint32_t leea_cpu_threshold16(double q);
 
 /* ---- layout and operator counts ----------------------------------------- */
 int64_t leea_cpu_num_params(const int32_t* dims, int32_t n_dims);

@@ -13,12 +13,12 @@
 // Work items walk the children alternately from the front (elites, crossover
 // children) and the back (mutation children), so every SM mixes the
 // HBM-heavier crossover items with the arithmetic-heavier mutation items.
-// A consumer thread owns blocks of four consecutive genes (two per chunk),
-// which is exactly one Philox block of each per-gene stream.  In mutation
-// children only the Box-Muller pairs that hold a masked gene are generated,
-// and a warp first gathers them into a dense job list (ballot-free prefix
-// scan over the lanes) so that normals are computed by consecutive lanes
-// instead of by whichever lane happens to own a masked gene.  Every mbarrier
+// A consumer thread owns 8 consecutive genes of the chunk: one Philox block
+// of 16-bit mask draws (crossover or mutation mask) and two Philox blocks of
+// normals.  In mutation children only the Box-Muller pairs that hold a masked
+// gene are generated, and a warp first gathers them into a dense job list
+// (prefix scan over the lanes) so that normals are computed by consecutive
+// lanes instead of by whichever lane happens to own a masked gene.  Every mbarrier
 // wait is bounded in time; on expiry the kernel sets kStatusBreedTimeout.
 #include "leea_internal.h"
 #include "philox.cuh"
@@ -80,79 +80,57 @@ __device__ __forceinline__ float* stage_b(const BreedSmem& s, uint32_t stage)
     return reinterpret_cast<float*>(s.base + (2u * stage + 1u) * kChunkBytes);
 }
 
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(ptx::smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(ptx::smem_u32(bar))
-        : "memory");
-}
-
 __device__ __forceinline__ void raise_abort(volatile int* abort_flag, unsigned int* status)
 {
     *abort_flag = 1;
     atomicOr(status, kStatusBreedTimeout);
 }
 
-constexpr int kBlocksPerLane = 2;  // 4096-gene chunk = 1024 blocks = 512 consumers x 2
-static_assert(kChunk / 4 == kBlocksPerLane * 32 * kConsumerWarps, "consumers must tile a chunk exactly");
+constexpr int kGenesPerLane = 8;  // one Philox block of 16-bit mask draws per lane and chunk
+static_assert(kChunk == kGenesPerLane * 32 * kConsumerWarps, "consumers must tile a chunk exactly");
 
-// Zero the padding genes (>= c) of block q.
-__device__ __forceinline__ float4 clear_padding(float4 v, uint32_t q, int64_t c)
+// Bit k of the result: the 16-bit draw k (k = 0..7) of block r is below thr.
+__device__ __forceinline__ uint32_t mask8(const uint4& r, uint32_t thr)
 {
-    const int64_t i0 = 4 * static_cast<int64_t>(q);
-    if (i0 + 3 >= c) {
-        if (i0 + 0 >= c) v.x = 0.0f;
-        if (i0 + 1 >= c) v.y = 0.0f;
-        if (i0 + 2 >= c) v.z = 0.0f;
-        if (i0 + 3 >= c) v.w = 0.0f;
+    const uint32_t w[4] = { r.x, r.y, r.z, r.w };
+    uint32_t m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t u = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
+        m |= (u < thr ? 1u : 0u) << k;
     }
+    return m;
+}
+
+// Zero the padding genes (>= c) among genes i0 .. i0+3.
+__device__ __forceinline__ float4 clear_padding(float4 v, int64_t i0, int64_t c)
+{
+    if (i0 + 0 >= c) v.x = 0.0f;
+    if (i0 + 1 >= c) v.y = 0.0f;
+    if (i0 + 2 >= c) v.z = 0.0f;
+    if (i0 + 3 >= c) v.w = 0.0f;
     return v;
 }
 
-// Elite copy, uniform or arithmetic crossover of block q.
-__device__ __forceinline__ float4 cross_block(const BreedArgs& a, const PhiloxKeys& key, int32_t kind, uint32_t j,
-                                              uint32_t q, float4 va, float4 vb)
+__device__ __forceinline__ float4 select4(uint32_t m, float4 a, float4 b)
 {
-    if (kind == 1) {
-        if (a.xo_op == 0) {
-            const uint4 r = philox_keyed(make_uint4(q, j, a.gen, kTagXo), key);
-            va.x = hits(r.x, a.thr_xo) ? vb.x : va.x;
-            va.y = hits(r.y, a.thr_xo) ? vb.y : va.y;
-            va.z = hits(r.z, a.thr_xo) ? vb.z : va.z;
-            va.w = hits(r.w, a.thr_xo) ? vb.w : va.w;
-        } else {
-            va = make_float4(0.5f * (va.x + vb.x), 0.5f * (va.y + vb.y), 0.5f * (va.z + vb.z), 0.5f * (va.w + vb.w));
-        }
-    } else if (kind == kKindInvalid) {
-        const float nan = __int_as_float(0x7FC00000);
-        va = make_float4(nan, nan, nan, nan);
-    }
-    return va;
+    return make_float4((m & 1u) ? b.x : a.x, (m & 2u) ? b.y : a.y, (m & 4u) ? b.z : a.z, (m & 8u) ? b.w : a.w);
 }
 
-// Mutation of this lane's kBlocksPerLane blocks q[g] (valid where live[g]).
-// Slot s = 2 g + pair names the Box-Muller pair (genes 4q + 2 pair, +1).
-__device__ __forceinline__ void mutate_blocks(const BreedArgs& a, const PhiloxKeys& key, uint32_t j,
-                                              const uint32_t (&q)[kBlocksPerLane], const bool (&live)[kBlocksPerLane],
-                                              float4 (&v)[kBlocksPerLane], int lane)
+// Mutation of this lane's 8 genes (unit u = genes 8u .. 8u+7, live if `live`).
+// Slot s = 0..3 names the Box-Muller pair of genes 8u + 2s, 8u + 2s + 1, i.e.
+// pair s & 1 of NORMAL block 2u + (s >> 1).  A warp numbers the slots that
+// hold a masked gene (prefix scan over the lanes) and generates those normals
+// on consecutive lanes, then every lane collects its own.
+__device__ __forceinline__ void mutate_unit(const BreedArgs& a, const PhiloxKeys& key, uint32_t j, uint32_t u,
+                                            bool live, float4 (&v)[2], int lane)
 {
-    constexpr int kSlots = 2 * kBlocksPerLane;
-    uint32_t hit[kBlocksPerLane];  // 4 bits: which genes of the block mutate
-    uint32_t need = 0;             // kSlots bits: which pairs need normals
+    constexpr int kSlots = 4;
+    uint32_t hit = 0;
+    if (live) hit = mask8(philox_keyed(make_uint4(u, j, a.gen, kTagMutMask), key), a.thr_mut);
+    uint32_t need = 0;
 #pragma unroll
-    for (int g = 0; g < kBlocksPerLane; ++g) {
-        hit[g] = 0;
-        if (live[g]) {
-            const uint4 r = philox_keyed(make_uint4(q[g], j, a.gen, kTagMutMask), key);
-            hit[g] = (hits(r.x, a.thr_mut) ? 1u : 0u) | (hits(r.y, a.thr_mut) ? 2u : 0u) |
-                     (hits(r.z, a.thr_mut) ? 4u : 0u) | (hits(r.w, a.thr_mut) ? 8u : 0u);
-        }
-        need |= ((hit[g] & 3u) ? 1u : 0u) << (2 * g);
-        need |= ((hit[g] & 12u) ? 1u : 0u) << (2 * g + 1);
-    }
-    // Exclusive prefix of the per-lane job counts: jobs are numbered by lane,
-    // then by slot.
+    for (int sl = 0; sl < kSlots; ++sl) need |= ((hit >> (2 * sl)) & 3u) ? (1u << sl) : 0u;
     const uint32_t cnt = __popc(need);
     uint32_t incl = cnt;
 #pragma unroll
@@ -168,8 +146,7 @@ __device__ __forceinline__ void mutate_blocks(const BreedArgs& a, const PhiloxKe
     for (int sl = 0; sl < kSlots; ++sl) z[sl] = make_float2(0.f, 0.f);
     for (uint32_t base = 0; base < total; base += 32) {
         const uint32_t job = base + static_cast<uint32_t>(lane);
-        // Owner lane o: the last lane whose exclusive prefix is <= job.
-        int o = 0;
+        int o = 0;  // owner lane: the last lane whose exclusive prefix is <= job
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
             const int cand = o + step;
@@ -180,7 +157,6 @@ __device__ __forceinline__ void mutate_blocks(const BreedArgs& a, const PhiloxKe
         const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, o);
         float2 zz = make_float2(0.f, 0.f);
         if (job < total) {
-            // The (job - eo)-th set slot of the owner.
             uint32_t nth = job - eo, slot = 0, mm = mo;
 #pragma unroll
             for (int sl = 0; sl < kSlots; ++sl) {
@@ -190,17 +166,11 @@ __device__ __forceinline__ void mutate_blocks(const BreedArgs& a, const PhiloxKe
                 }
                 mm >>= 1;
             }
-            // Lanes of a warp own consecutive blocks (q[g] - lane is the same
-            // for every lane): shift this lane's block g to the owner's.
-            uint32_t qg = q[0];
-#pragma unroll
-            for (int g = 1; g < kBlocksPerLane; ++g)
-                if (static_cast<uint32_t>(g) == (slot >> 1)) qg = q[g];
-            const uint32_t qb = qg - static_cast<uint32_t>(lane) + static_cast<uint32_t>(o);
-            const uint4 n = philox_keyed(make_uint4(qb, j, a.gen, kTagNormal), key);
+            // Lanes of a warp own consecutive units: the owner's is u - lane + o.
+            const uint32_t uo = u - static_cast<uint32_t>(lane) + static_cast<uint32_t>(o);
+            const uint4 n = philox_keyed(make_uint4(2u * uo + (slot >> 1), j, a.gen, kTagNormal), key);
             zz = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
         }
-        // Every lane fetches the normals of its own slots numbered in this pass.
 #pragma unroll
         for (int sl = 0; sl < kSlots; ++sl) {
             const uint32_t id = excl + __popc(need & ((1u << sl) - 1u));
@@ -211,14 +181,14 @@ __device__ __forceinline__ void mutate_blocks(const BreedArgs& a, const PhiloxKe
             if (mine) z[sl] = make_float2(zx, zy);
         }
     }
-#pragma unroll
-    for (int g = 0; g < kBlocksPerLane; ++g) {
-        const float2 z0 = z[2 * g], z1 = z[2 * g + 1];
-        if (hit[g] & 1u) v[g].x = fmaf(a.sigma, z0.x, v[g].x);
-        if (hit[g] & 2u) v[g].y = fmaf(a.sigma, z0.y, v[g].y);
-        if (hit[g] & 4u) v[g].z = fmaf(a.sigma, z1.x, v[g].z);
-        if (hit[g] & 8u) v[g].w = fmaf(a.sigma, z1.y, v[g].w);
-    }
+    if (hit & 0x01u) v[0].x = fmaf(a.sigma, z[0].x, v[0].x);
+    if (hit & 0x02u) v[0].y = fmaf(a.sigma, z[0].y, v[0].y);
+    if (hit & 0x04u) v[0].z = fmaf(a.sigma, z[1].x, v[0].z);
+    if (hit & 0x08u) v[0].w = fmaf(a.sigma, z[1].y, v[0].w);
+    if (hit & 0x10u) v[1].x = fmaf(a.sigma, z[2].x, v[1].x);
+    if (hit & 0x20u) v[1].y = fmaf(a.sigma, z[2].y, v[1].y);
+    if (hit & 0x40u) v[1].z = fmaf(a.sigma, z[3].x, v[1].z);
+    if (hit & 0x80u) v[1].w = fmaf(a.sigma, z[3].y, v[1].w);
 }
 
 __global__ void __launch_bounds__(kBreedThreads, 1)
@@ -272,9 +242,9 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
                 } else {
                     const bool two = (cur_kind == 1);
                     ptx::mbar_arrive_expect_tx(&s.full[stage], two ? 2u * bytes : bytes);
-                    bulk_load(stage_a(s, stage), parents + static_cast<int64_t>(cur_p1) * a.c_pad + g0, bytes, &s.full[stage]);
+                    ptx::bulk_load(stage_a(s, stage), parents + static_cast<int64_t>(cur_p1) * a.c_pad + g0, bytes, &s.full[stage]);
                     if (two)
-                        bulk_load(stage_b(s, stage), parents + static_cast<int64_t>(cur_p2) * a.c_pad + g0, bytes,
+                        ptx::bulk_load(stage_b(s, stage), parents + static_cast<int64_t>(cur_p2) * a.c_pad + g0, bytes,
                                   &s.full[stage]);
                 }
                 issued_mask |= 1u << stage;
@@ -302,35 +272,40 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
             const float4* A = reinterpret_cast<const float4*>(stage_a(s, stage));
             const float4* B = reinterpret_cast<const float4*>(stage_b(s, stage));
             float4* O = reinterpret_cast<float4*>(children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
-            const int nq = m.len >> 2;
-            const uint32_t q0 = static_cast<uint32_t>(m.g0) >> 2;
             const uint32_t j = static_cast<uint32_t>(m.j);
-            uint32_t q[kBlocksPerLane];
-            bool live[kBlocksPerLane];
-            float4 v[kBlocksPerLane];
-#pragma unroll
-            for (int g = 0; g < kBlocksPerLane; ++g) {
-                const int t = ct + g * 32 * kConsumerWarps;
-                live[g] = t < nq;
-                q[g] = q0 + static_cast<uint32_t>(t);
-                v[g] = (live[g] && m.kind >= 0) ? A[t] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool live = ct * kGenesPerLane < m.len;
+            const uint32_t u = (static_cast<uint32_t>(m.g0) >> 3) + static_cast<uint32_t>(ct);  // 8-gene unit
+            float4 v[2] = { make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f) };
+            if (live && m.kind >= 0) {
+                v[0] = A[2 * ct];
+                v[1] = A[2 * ct + 1];
             }
             if (m.kind == 2) {
-                mutate_blocks(a, key, j, q, live, v, lane);
-            } else {
-#pragma unroll
-                for (int g = 0; g < kBlocksPerLane; ++g) {
-                    const int t = ct + g * 32 * kConsumerWarps;
-                    if (live[g]) {
-                        const float4 vb = (m.kind == 1) ? B[t] : v[g];
-                        v[g] = cross_block(a, key, m.kind, j, q[g], v[g], vb);
-                    }
+                mutate_unit(a, key, j, u, live, v, lane);
+            } else if (live && m.kind == 1) {
+                const float4 b0 = B[2 * ct], b1 = B[2 * ct + 1];
+                if (a.xo_op == 0) {
+                    const uint32_t msk = mask8(philox_keyed(make_uint4(u, j, a.gen, kTagXo), key), a.thr_xo);
+                    v[0] = select4(msk, v[0], b0);
+                    v[1] = select4(msk >> 4, v[1], b1);
+                } else {
+                    v[0] = make_float4(0.5f * (v[0].x + b0.x), 0.5f * (v[0].y + b0.y), 0.5f * (v[0].z + b0.z),
+                                       0.5f * (v[0].w + b0.w));
+                    v[1] = make_float4(0.5f * (v[1].x + b1.x), 0.5f * (v[1].y + b1.y), 0.5f * (v[1].z + b1.z),
+                                       0.5f * (v[1].w + b1.w));
                 }
+            } else if (m.kind == kKindInvalid) {
+                const float nan = __int_as_float(0x7FC00000);
+                v[0] = v[1] = make_float4(nan, nan, nan, nan);
             }
-#pragma unroll
-            for (int g = 0; g < kBlocksPerLane; ++g) {
-                const int t = ct + g * 32 * kConsumerWarps;
-                if (live[g]) O[t] = clear_padding(v[g], q[g], a.c);
+            if (live) {
+                const int64_t i0 = static_cast<int64_t>(m.g0) + kGenesPerLane * ct;
+                if (i0 + kGenesPerLane > a.c) {  // only a child's last chunk holds padding
+                    v[0] = clear_padding(v[0], i0, a.c);
+                    v[1] = clear_padding(v[1], i0 + 4, a.c);
+                }
+                O[2 * ct] = v[0];
+                O[2 * ct + 1] = v[1];
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&s.empty[stage]);

@@ -66,11 +66,12 @@ bool make_layout(const int32_t* dims, int32_t n_dims, int32_t init, NetLayout* n
     return off < (int64_t{1} << 32);  // gene indices feed 32-bit Philox counters
 }
 
-uint64_t threshold(double q)
+// Threshold of the 16-bit per-gene mask draws: a draw hits iff below it.
+uint32_t threshold16(double q)
 {
     if (!(q > 0.0)) return 0;
-    if (q >= 1.0) return uint64_t{1} << 32;
-    return static_cast<uint64_t>(std::floor(q * 4294967296.0));
+    if (q >= 1.0) return 65536u;
+    return static_cast<uint32_t>(std::floor(q * 65536.0));
 }
 
 leea_status check_params(const leea_params* p)
@@ -334,8 +335,8 @@ static BreedArgs breed_args(int32_t pop, const NetLayout& net, const leea_params
     a.c = net.c;
     a.c_pad = net.c_pad;
     a.xo_op = p->xo_op;
-    a.thr_xo = threshold(static_cast<double>(p->xo_gene_p));
-    a.thr_mut = threshold(static_cast<double>(p->mut_rate));
+    a.thr_xo = threshold16(static_cast<double>(p->xo_gene_p));
+    a.thr_mut = threshold16(static_cast<double>(p->mut_rate));
     a.sigma = p->sigma;
     a.seed = seed;
     a.gen = gen;

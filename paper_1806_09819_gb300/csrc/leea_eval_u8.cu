@@ -37,8 +37,8 @@ constexpr int kFirstLoaderWarp = 2;
 constexpr int kFirstEpilogueWarp = kFirstLoaderWarp + kLoaderWarps;
 constexpr int kU8Threads = 32 * (kFirstEpilogueWarp + 4);
 constexpr int kKStage = 64;        // K elements per stage: one 128-byte BF16 row
-constexpr int kPieceStages = 2;    // BF16 piece ring
-constexpr int kMaxRawStages = 4;   // FP32 raw ring (TMA)
+constexpr int kMaxPieceStages = 3;  // BF16 piece ring
+constexpr int kMaxRawStages = 4;    // FP32 raw ring (TMA)
 constexpr int kMaxOutU8 = 16;
 constexpr int kRowBatch = 8;       // 16-row groups a loader thread holds in registers at once
 constexpr uint32_t kTmemCols = 512;
@@ -46,7 +46,8 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr uint64_t kDrainLimitNs = 200000000ull;
 
 struct EvalU8Args {
-    int32_t pop, k, h, d_out, dpad, batch, k_stages, k16, raw_stages;
+    int32_t pop, k, h, d_out, dpad, batch, k_stages, k16, raw_stages, piece_stages;
+    uint32_t prm_bytes;  // b1, W2, b2 of one individual, rounded up to 16 bytes
     int64_t c_pad;
     float inv_div, alpha;
     uint32_t a_col;  // first TMEM column of the A operand (the accumulator uses 0 .. h-1)
@@ -61,13 +62,14 @@ struct EvalU8Args {
 };
 
 struct U8Smem {
-    uint8_t* ring;        // kPieceStages x 3 pieces x h x 128 B (1024-aligned)
+    uint8_t* ring;        // piece_stages x 3 pieces x h x 128 B (1024-aligned)
     uint8_t* raw;         // raw_stages x h x 256 B (FP32 rows of 64 K-elements)
     uint32_t piece_bytes, raw_bytes;
+    uint8_t* prm_raw;     // 2 x prm_bytes: b1, W2 (row-major), b2 as stored, bulk-copied
     float* w2t;           // [h][dpad]
     float* b1;            // [h]
     float* b2;            // [16]
-    uint64_t *full, *empty, *raw_full, *raw_empty, *acc_full, *acc_empty, *a_ready, *drain;
+    uint64_t *full, *empty, *raw_full, *raw_empty, *prm_full, *prm_empty, *acc_full, *acc_empty, *a_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
@@ -81,8 +83,10 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     s.ring = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
     s.piece_bytes = static_cast<uint32_t>(a.h) * 128u;
     s.raw_bytes = static_cast<uint32_t>(a.h) * 256u;
-    s.raw = s.ring + kPieceStages * 3u * s.piece_bytes;
+    s.raw = s.ring + a.piece_stages * 3u * s.piece_bytes;
     uint8_t* p = s.raw + a.raw_stages * s.raw_bytes;
+    s.prm_raw = p;
+    p += 2u * a.prm_bytes;
     s.w2t = reinterpret_cast<float*>(p);
     p += sizeof(float) * a.h * a.dpad;
     s.b1 = reinterpret_cast<float*>(p);
@@ -91,10 +95,12 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     p += sizeof(float) * 16;
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.full = bars;
-    s.empty = bars + kPieceStages;
-    s.raw_full = bars + 2 * kPieceStages;
+    s.empty = bars + a.piece_stages;
+    s.raw_full = bars + 2 * a.piece_stages;
     s.raw_empty = s.raw_full + a.raw_stages;
-    s.acc_full = s.raw_empty + a.raw_stages;
+    s.prm_full = s.raw_empty + a.raw_stages;
+    s.prm_empty = s.prm_full + 2;
+    s.acc_full = s.prm_empty + 2;
     s.acc_empty = s.acc_full + 1;
     s.a_ready = s.acc_full + 2;
     s.drain = s.acc_full + 3;
@@ -107,18 +113,31 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     return s;
 }
 
-size_t u8_smem_bytes(int32_t h, int32_t dpad, int32_t raw_stages)
+uint32_t u8_prm_bytes(int32_t h, int32_t d_out)
 {
-    return 1024 + static_cast<size_t>(kPieceStages) * 3 * h * 128 + static_cast<size_t>(raw_stages) * h * 256 +
-           sizeof(float) * (h * dpad + h + 16) + 8 * (2 * kPieceStages + 2 * raw_stages + 4) + 64;
+    return (static_cast<uint32_t>(h + d_out * h + d_out) * 4u + 15u) & ~15u;
 }
 
-// Deepest raw ring (2..4 stages) that fits in 227 KB of shared memory; 0 if none.
-int32_t u8_raw_stages(int32_t h, int32_t dpad)
+size_t u8_smem_bytes(int32_t h, int32_t dpad, int32_t piece_stages, int32_t raw_stages)
 {
-    for (int32_t st = kMaxRawStages; st >= 2; --st)
-        if (u8_smem_bytes(h, dpad, st) <= 227u * 1024u) return st;
-    return 0;
+    const int32_t d_out = dpad;  // upper bound for the raw parameter area
+    return 1024 + static_cast<size_t>(piece_stages) * 3 * h * 128 + static_cast<size_t>(raw_stages) * h * 256 +
+           2 * u8_prm_bytes(h, d_out) + sizeof(float) * (h * dpad + h + 16) +
+           8 * (2 * piece_stages + 2 * raw_stages + 4 + 4) + 64;
+}
+
+// Ring depths (piece, raw) that fit in 227 KB of shared memory, deepest piece
+// ring first; false if not even (2, 2) fits.
+bool u8_stages(int32_t h, int32_t dpad, int32_t* piece, int32_t* raw)
+{
+    for (int32_t ps = kMaxPieceStages; ps >= 2; --ps)
+        for (int32_t rs = kMaxRawStages; rs >= 2; --rs)
+            if (u8_smem_bytes(h, dpad, ps, rs) <= 227u * 1024u) {
+                *piece = ps;
+                *raw = rs;
+                return true;
+            }
+    return false;
 }
 
 __device__ __forceinline__ void raise_abort(const U8Smem& s, const EvalU8Args& a)
@@ -127,22 +146,25 @@ __device__ __forceinline__ void raise_abort(const U8Smem& s, const EvalU8Args& a
     atomicOr(a.status, kStatusEvalTimeout);
 }
 
-__device__ __forceinline__ uint32_t bf16_bits(float v)
+__device__ __forceinline__ uint32_t bf162_bits(__nv_bfloat162 v)
 {
-    return static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(v)));
+    return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Exact three-way split of an FP32 value into BF16 pieces (rounding to
-// nearest at each step; the remainders are exact in FP32).
-__device__ __forceinline__ void split3(float w, uint32_t& p1, uint32_t& p2, uint32_t& p3)
+// Exact three-way split of two FP32 values into packed BF16 pairs (lower K
+// index in the low half): each piece rounds the remainder of the previous
+// ones to nearest, and the remainders are exact in FP32.
+__device__ __forceinline__ void split3x2(float w0, float w1, uint32_t& p1, uint32_t& p2, uint32_t& p3)
 {
-    const __nv_bfloat16 h1 = __float2bfloat16_rn(w);
-    const float r1 = w - __bfloat162float(h1);
-    const __nv_bfloat16 h2 = __float2bfloat16_rn(r1);
-    const float r2 = r1 - __bfloat162float(h2);
-    p1 = __bfloat16_as_ushort(h1);
-    p2 = __bfloat16_as_ushort(h2);
-    p3 = bf16_bits(r2);
+    const __nv_bfloat162 h1 = __floats2bfloat162_rn(w0, w1);
+    const float2 f1 = __bfloat1622float2(h1);
+    const float r0 = w0 - f1.x, r1 = w1 - f1.y;
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0, r1);
+    const float2 f2 = __bfloat1622float2(h2);
+    const __nv_bfloat162 h3 = __floats2bfloat162_rn(r0 - f2.x, r1 - f2.y);
+    p1 = bf162_bits(h1);
+    p2 = bf162_bits(h2);
+    p3 = bf162_bits(h3);
 }
 
 __global__ void __launch_bounds__(kU8Threads, 1)
@@ -153,13 +175,17 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kPieceStages; ++i) {
+        for (int i = 0; i < a.piece_stages; ++i) {
             ptx::mbar_init(&s.full[i], kLoaderWarps);
             ptx::mbar_init(&s.empty[i], 1);
         }
         for (int i = 0; i < a.raw_stages; ++i) {
             ptx::mbar_init(&s.raw_full[i], 1);
             ptx::mbar_init(&s.raw_empty[i], kLoaderWarps);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&s.prm_full[i], 1);
+            ptx::mbar_init(&s.prm_empty[i], 128);
         }
         ptx::tma_prefetch_map(&tmap_w);
         ptx::mbar_init(s.acc_full, 1);
@@ -212,7 +238,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                         }
                     }
                     ptx::mma_commit(&s.empty[stage]);
-                    if (++stage == kPieceStages) { stage = 0; phase ^= 1u; }
+                    if (++stage == static_cast<uint32_t>(a.piece_stages)) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
                 ptx::mma_commit(s.acc_full);
@@ -227,8 +253,23 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
         if (lane == 0) {
             uint32_t stage = 0, phase = 0;
             uint32_t issued_mask = 0, parity_mask = 0;
+            uint32_t prm_issued = 0;  // units whose parameters were requested
             bool ok = true;
             for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+                {
+                    // b1, W2, b2 of individual p into parameter buffer (unit & 1).
+                    const uint32_t pb = prm_issued & 1u, pphase = (prm_issued >> 1) & 1u;
+                    if (!ptx::mbar_wait_bounded(&s.prm_empty[pb], pphase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+                        raise_abort(s, a);
+                        ok = false;
+                        break;
+                    }
+                    ptx::mbar_arrive_expect_tx(&s.prm_full[pb], a.prm_bytes);
+                    ptx::bulk_load(s.prm_raw + pb * a.prm_bytes,
+                                   a.popv + static_cast<int64_t>(p) * a.c_pad + static_cast<int64_t>(a.h) * a.k,
+                                   a.prm_bytes, &s.prm_full[pb]);
+                    ++prm_issued;
+                }
                 for (int kc = 0; kc < a.k_stages; ++kc) {
                     if (!ptx::mbar_wait_bounded(&s.raw_empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
                         raise_abort(s, a);
@@ -247,6 +288,8 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                 for (int i = 0; i < a.raw_stages; ++i)
                     if (issued_mask & (1u << i))
                         ptx::mbar_wait_bounded(&s.raw_full[i], (parity_mask >> i) & 1u, &never, kDrainLimitNs);
+                for (uint32_t u = prm_issued > 2 ? prm_issued - 2 : 0; u < prm_issued; ++u)
+                    ptx::mbar_wait_bounded(&s.prm_full[u & 1u], (u >> 1) & 1u, &never, kDrainLimitNs);
             }
         }
     } else if (warp < kFirstEpilogueWarp) {
@@ -283,25 +326,21 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                 for (int u = 0; u < kRowBatch; ++u) {
                     if (u < groups) {
                         const int r = row0 + 16 * u;
-                        uint32_t q0[3], q1[3], q2[3], q3[3];
-                        split3(v[u].x, q0[0], q0[1], q0[2]);
-                        split3(v[u].y, q1[0], q1[1], q1[2]);
-                        split3(v[u].z, q2[0], q2[1], q2[2]);
-                        split3(v[u].w, q3[0], q3[1], q3[2]);
+                        uint32_t lo[3], hi[3];  // pieces of (x, y) and of (z, w)
+                        split3x2(v[u].x, v[u].y, lo[0], lo[1], lo[2]);
+                        split3x2(v[u].z, v[u].w, hi[0], hi[1], hi[2]);
                         const uint32_t off = static_cast<uint32_t>(r) * 128u +
                                              ((static_cast<uint32_t>(c4 >> 1) ^ static_cast<uint32_t>(r & 7)) << 4) +
                                              (static_cast<uint32_t>(c4 & 1) << 3);
 #pragma unroll
-                        for (int piece = 0; piece < 3; ++piece) {
-                            const uint2 pk = make_uint2(q0[piece] | (q1[piece] << 16), q2[piece] | (q3[piece] << 16));
-                            *reinterpret_cast<uint2*>(sb + piece * s.piece_bytes + off) = pk;
-                        }
+                        for (int piece = 0; piece < 3; ++piece)
+                            *reinterpret_cast<uint2*>(sb + piece * s.piece_bytes + off) = make_uint2(lo[piece], hi[piece]);
                     }
                 }
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
                 if (lane == 0) ptx::mbar_arrive(&s.full[stage]);
-                if (++stage == kPieceStages) { stage = 0; phase ^= 1u; }
+                if (++stage == static_cast<uint32_t>(a.piece_stages)) { stage = 0; phase ^= 1u; }
             }
         }
     } else {
@@ -351,11 +390,21 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
             ptx::mbar_arrive(s.a_ready);
         }
 
-        uint32_t acc_phase = 0;
+        const int32_t label = row < a.batch ? a.y[row] : 0;
+        uint32_t acc_phase = 0, unit = 0;
         bool ok = true;
-        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
-            // Stage b1, W2 (transposed, rows padded to dpad) and b2 of individual p.
-            const float* src = a.popv + static_cast<int64_t>(p) * a.c_pad + static_cast<int64_t>(a.h) * a.k;
+        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x, ++unit) {
+            // Parameters of individual p: wait for the bulk copy, then stage
+            // b1, W2 transposed (rows padded to dpad) and b2.
+            const uint32_t pb = unit & 1u, pphase = (unit >> 1) & 1u;
+            if (et == 0) {
+                const bool got = ptx::mbar_wait_bounded(&s.prm_full[pb], pphase, s.abort_flag, kWaitLimitNs);
+                if (!got) raise_abort(s, a);
+                *s.ep_go = got ? 1 : 0;
+            }
+            ptx::named_barrier_sync(1, 128);  // A1: parameters landed (or abort)
+            if (!*s.ep_go) { ok = false; break; }
+            const float* src = reinterpret_cast<const float*>(s.prm_raw + pb * a.prm_bytes);
             for (int i = et; i < a.h; i += 128) s.b1[i] = src[i];
             for (int i = et; i < a.d_out * a.h; i += 128) {
                 const int o = i / a.h, col = i - o * a.h;
@@ -366,12 +415,13 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                 s.w2t[(i / pad) * a.dpad + a.d_out + i % pad] = 0.0f;
             }
             if (et < 16) s.b2[et] = et < a.d_out ? src[a.h + a.d_out * a.h + et] : 0.0f;
+            ptx::mbar_arrive(&s.prm_empty[pb]);
             if (et == 0) {
                 const bool got = ptx::mbar_wait_bounded(s.acc_full, acc_phase, s.abort_flag, kWaitLimitNs);
                 if (!got) raise_abort(s, a);
                 *s.ep_go = got ? 1 : 0;
             }
-            ptx::named_barrier_sync(1, 128);  // A: accumulator ready (or abort); parameters staged
+            ptx::named_barrier_sync(1, 128);  // A2: accumulator ready (or abort); parameters staged
             if (!*s.ep_go) { ok = false; break; }
             ptx::tc_fence_after();
 
@@ -418,7 +468,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
 #pragma unroll
                 for (int o = 0; o < kMaxOutU8; ++o)
                     if (o < a.d_out) se += expf(logit[o] + s.b2[o] - zmax);
-                const int32_t lbl = a.y[row];
+                const int32_t lbl = label;
                 if (lbl >= 0 && lbl < a.d_out) {
                     float zl = 0.0f;
 #pragma unroll
@@ -490,7 +540,8 @@ bool eval_u8_tc_supported(const NetLayout& net, int32_t batch, const float* pop_
     if (h + a_cols > static_cast<int32_t>(kTmemCols)) return false;
     if (reinterpret_cast<uintptr_t>(pop_dev) & 15u) return false;
     const int32_t dpad = (d_out + 3) / 4 * 4;
-    return u8_raw_stages(h, dpad) >= 2 && u8_encode_fn() != nullptr;
+    int32_t ps = 0, rs = 0;
+    return u8_stages(h, dpad, &ps, &rs) && u8_encode_fn() != nullptr;
 }
 
 cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
@@ -519,9 +570,9 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     a.f_adj = f_adj;
     a.correct = correct;
     a.status = status;
-    a.raw_stages = u8_raw_stages(a.h, a.dpad);
-    if (a.raw_stages < 2) return cudaErrorInvalidValue;
-    const size_t smem = u8_smem_bytes(a.h, a.dpad, a.raw_stages);
+    a.prm_bytes = u8_prm_bytes(a.h, a.d_out);
+    if (!u8_stages(a.h, a.dpad, &a.piece_stages, &a.raw_stages)) return cudaErrorInvalidValue;
+    const size_t smem = u8_smem_bytes(a.h, a.dpad, a.piece_stages, a.raw_stages);
     U8EncodeTiledFn enc = u8_encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tw;

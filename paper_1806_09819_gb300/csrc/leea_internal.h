@@ -36,7 +36,7 @@ struct BreedArgs {
     int32_t pop;
     int64_t c, c_pad;
     int32_t xo_op;
-    uint64_t thr_xo, thr_mut;
+    uint32_t thr_xo, thr_mut;  // 16-bit draw thresholds floor(q 2^16), 2^16 when q >= 1
     float sigma;
     uint64_t seed;
     uint32_t gen;

@@ -48,11 +48,11 @@ def test_uniform_crossover_takes_each_gene_from_one_parent(oracle_mod, q):
     frac = from_b.mean()
     n = kids.size
     assert abs(frac - q) <= 5 * np.sqrt(q * (1 - q) / n) + 1e-12
-    # The choice is the XO draw of (gen, child, gene) against floor(q 2^32).
-    thr = oracle_mod.threshold(q)
+    # The choice is the 16-bit XO draw of (gen, child, gene) against floor(q 2^16).
+    thr = oracle_mod.threshold16(q)
     for j in (0, 17):
-        for i in (0, 1, 2, 3, 100, len(kids[j]) - 1):
-            u = oracle_mod.draw(7, oracle_mod.TAG_XO, 2, j, i)
+        for i in (0, 1, 2, 3, 7, 8, 100, len(kids[j]) - 1):
+            u = oracle_mod.draw16(7, oracle_mod.TAG_XO, 2, j, i)
             assert from_b[j, i] == (u < thr) or parents[par1[j], i] == parents[par2[j], i]
 
 

@@ -109,3 +109,25 @@ def test_normal_uses_box_muller_pairs(oracle_mod):
             r0 = math.hypot(oracle_mod.normal(seed, tag, gen, ent, i), oracle_mod.normal(seed, tag, gen, ent, i + 1))
             u1 = oracle_mod.u01(oracle_mod.draw(seed, tag, gen, ent, i))
             assert abs(r0 - math.sqrt(-2.0 * math.log(u1))) < 1e-12
+
+
+def test_draw16_layout_and_threshold(oracle_mod):
+    # 16-bit draw i: half (i & 1) of word ((i >> 1) & 3) of block (i >> 3).
+    seed = 0x5EED5EED12345678
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    for tag, gen, ent in [(3, 4, 9), (4, 1, 0)]:
+        for i in range(0, 40):
+            blk = oracle_mod.philox((i >> 3, ent, gen, tag), key)
+            word = int(blk[(i >> 1) & 3])
+            expect = (word >> 16) if (i & 1) else (word & 0xFFFF)
+            assert oracle_mod.draw16(seed, tag, gen, ent, i) == expect
+    assert oracle_mod.threshold16(0.0) == 0
+    assert oracle_mod.threshold16(0.5) == 32768
+    assert oracle_mod.threshold16(1.0) == 65536
+    assert oracle_mod.threshold16(0.1) == 6553
+
+
+def test_draw16_is_uniform(oracle_mod):
+    u = np.array([oracle_mod.draw16(3, 4, 5, e, i) for e in range(4) for i in range(8192)])
+    counts = np.bincount(u >> 10, minlength=64)  # 64 equal bins
+    assert stats.chisquare(counts).pvalue > 1e-4
