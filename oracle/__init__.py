@@ -105,6 +105,14 @@ def lib() -> ctypes.CDLL:
         L.leea_cpu_index.restype = u32
         L.leea_cpu_threshold.argtypes = [dbl]
         L.leea_cpu_threshold.restype = u64
+        L.leea_cpu_round_bf16.argtypes = [dbl]
+        L.leea_cpu_round_bf16.restype = dbl
+        L.leea_cpu_round_e4m3.argtypes = [dbl]
+        L.leea_cpu_round_e4m3.restype = dbl
+        L.leea_cpu_fp8_scale_exp.argtypes = [dbl]
+        L.leea_cpu_fp8_scale_exp.restype = i32
+        L.leea_cpu_evaluate_shadow.argtypes = [i32, vp, i32, vp, i32, vp, vp, vp, i32, vp, vp]
+        L.leea_cpu_evaluate_shadow.restype = ctypes.c_int
         L.leea_cpu_draw16.argtypes = [u64, u32, u32, u32, u32]
         L.leea_cpu_draw16.restype = u32
         L.leea_cpu_threshold16.argtypes = [dbl]
@@ -201,6 +209,34 @@ def draw16(seed: int, tag: int, gen: int, ent: int, i: int) -> int:
 
 def threshold16(q: float) -> int:
     return int(lib().leea_cpu_threshold16(float(q)))
+
+
+# ---- precision form -------------------------------------------------------
+def round_bf16(x: float) -> float:
+    return float(lib().leea_cpu_round_bf16(float(x)))
+
+
+def round_e4m3(x: float) -> float:
+    return float(lib().leea_cpu_round_e4m3(float(x)))
+
+
+def fp8_scale_exp(bound: float) -> int:
+    return int(lib().leea_cpu_fp8_scale_exp(float(bound)))
+
+
+def evaluate_shadow(popv, dims, precision: int, scale_exp, x, y):
+    """Fitness with W1 replaced by its BF16 (1) or scaled FP8-e4m3 (2) shadow."""
+    d = _dims(dims)
+    pv = _f64(popv)
+    pop = pv.shape[0]
+    xv = _f64(x).reshape(-1, int(d[0]))
+    yv = _i32(y)
+    se = None if scale_exp is None else _i32(scale_exp)
+    f = np.empty(pop, dtype=np.float64)
+    cor = np.empty(pop, dtype=np.int32)
+    _check(lib().leea_cpu_evaluate_shadow(pop, _ptr(d), len(d), _ptr(pv), int(precision), _ptr(se), _ptr(xv),
+                                          _ptr(yv), xv.shape[0], _ptr(f), _ptr(cor)), "evaluate_shadow")
+    return f, cor
 
 
 # ---- layout ---------------------------------------------------------------

@@ -263,6 +263,82 @@ int leea_cpu_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Precision form: BF16 and FP8-e4m3 shadows of W1.                          */
+/* ------------------------------------------------------------------------ */
+
+/* Round x to the nearest multiple of the power of two q, ties to even. */
+static double round_to_grid(double x, double q)
+{
+    return nearbyint(x / q) * q;  /* x / q is exact; default rounding is to nearest even */
+}
+
+/* BF16: 1 sign, 8 exponent (bias 127), 7 stored mantissa bits. */
+double leea_cpu_round_bf16(double x)
+{
+    if (x == 0.0 || isnan(x) || isinf(x)) return x;
+    int e;
+    frexp(x, &e);                 /* |x| in [2^(e-1), 2^e) */
+    int lead = e - 1;
+    if (lead < -126) lead = -126; /* subnormal range: fixed quantum */
+    return round_to_grid(x, ldexp(1.0, lead - 7));
+}
+
+/* FP8-e4m3 (OCP "FN"): 1 sign, 4 exponent (bias 7), 3 mantissa bits, no
+ * infinities; largest finite 448 = 1.75 * 2^8; smallest subnormal 2^-9. */
+double leea_cpu_round_e4m3(double x)
+{
+    if (isnan(x)) return x;
+    if (isinf(x)) return x > 0 ? 448.0 : -448.0;
+    if (x == 0.0) return x;
+    int e;
+    frexp(x, &e);
+    int lead = e - 1;
+    if (lead < -6) lead = -6;     /* subnormals share the quantum 2^-9 */
+    double r = round_to_grid(x, ldexp(1.0, lead - 3));
+    if (r > 448.0) r = 448.0;     /* saturate to finite */
+    if (r < -448.0) r = -448.0;
+    return r;
+}
+
+int32_t leea_cpu_fp8_scale_exp(double bound)
+{
+    if (!(bound > 0.0)) return 0;
+    int32_t e = -200;
+    while (448.0 * ldexp(1.0, e) < bound) e++;
+    return e;
+}
+
+int leea_cpu_evaluate_shadow(int32_t pop, const int32_t* dims, int32_t n_dims,
+                             const double* popv, int32_t precision, const int32_t* scale_exp,
+                             const double* x, const int32_t* y, int32_t batch,
+                             double* f_out, int32_t* correct_out)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || pop <= 0 || !popv || precision < 0 || precision > 2 || (precision == 2 && !scale_exp))
+        return LEEA_CPU_EINVAL;
+    int64_t n_w1 = (int64_t)dims[0] * dims[1];
+    double* q = (double*)malloc(sizeof(double) * (size_t)c);
+    if (!q) return LEEA_CPU_ENOMEM;
+    int rc = LEEA_CPU_OK;
+    for (int32_t p = 0; p < pop && rc == LEEA_CPU_OK; p++) {
+        const double* theta = popv + (int64_t)p * c;
+        memcpy(q, theta, sizeof(double) * (size_t)c);
+        for (int64_t i = 0; i < n_w1; i++) {
+            if (precision == 1) {
+                q[i] = leea_cpu_round_bf16(theta[i]);
+            } else if (precision == 2) {
+                double s = ldexp(1.0, scale_exp[p]);
+                q[i] = leea_cpu_round_e4m3(theta[i] / s) * s;
+            }
+        }
+        rc = leea_cpu_evaluate(1, dims, n_dims, q, x, y, batch, f_out + p,
+                               correct_out ? correct_out + p : NULL, NULL);
+    }
+    free(q);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Sort by fitness, descending (Algorithm 1).  NaN ranks as -infinity; ties  */
 /* go to the lower index (a stable sort).                                   */
 /* ------------------------------------------------------------------------ */

@@ -101,6 +101,23 @@ int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
 int leea_cpu_inherit(int32_t pop, double alpha, const double* f_inh, const double* f,
                      int32_t first, double* f_adj);
 
+/* ---- precision form: reduced-precision shadows of W1 ---------------------- */
+/* Round to nearest even into BF16 (8 significant bits, FP32's exponent range). */
+double leea_cpu_round_bf16(double x);
+/* Round to nearest even into FP8-e4m3 with saturation to +-448 (NaN stays NaN). */
+double leea_cpu_round_e4m3(double x);
+/* Exponent e of the power-of-two FP8 scale 2^e for an upper bound on |W1|:
+ * the smallest e with 448 * 2^e >= bound (0 when bound <= 0). */
+int32_t leea_cpu_fp8_scale_exp(double bound);
+/* Fitness (Eq. 1) with W1 of every individual replaced by its shadow:
+ * precision 1 -> round_bf16(w); precision 2 -> round_e4m3(w / 2^e_p) * 2^e_p
+ * with the per-individual exponents scale_exp[p].  The rest of the net and the
+ * arithmetic stay FP64. */
+int leea_cpu_evaluate_shadow(int32_t pop, const int32_t* dims, int32_t n_dims,
+                             const double* popv, int32_t precision, const int32_t* scale_exp,
+                             const double* x, const int32_t* y, int32_t batch,
+                             double* f_out, int32_t* correct_out);
+
 /* ---- the whole algorithm as a state object -------------------------------- */
 typedef struct leea_cpu_state leea_cpu_state;
 int leea_cpu_create(int32_t pop, const int32_t* dims, int32_t n_dims,
