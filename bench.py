@@ -8,6 +8,12 @@ breed, evaluate).  The population (2 x 356 MB) is larger than L2, so no flush
 is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+                    [--config plain|precision-bf16|precision-fp8]
+
+--config precision-* measures the precision form instead (P = 4096 nets
+784-112-10, batch 256, BF16 or FP8-e4m3 shadows of W1 with FP32 accumulation
+and FP32 masters) and reports the shadow fitness against the FP64 evaluation
+of the masters on a sample of the final population.
 
 N > 1 (under torch.distributed.run) runs N independent replicas, one per GPU
 (the generation's selection needs every parent, so a run does not shard);
@@ -34,6 +40,11 @@ PARAMS = dict(xo_op=0, xo_gene_p=0.5, sel_op=0, rho=0.5, n_elite=1, p_c=0.5, sig
               alpha=1.0, init=0)
 WORKLOAD = ("P=1000 MLPs 784-112-10 (89,050 params, FP32), batch 100 synthetic 28x28 images; uniform crossover "
             "p_C=0.5, truncation rho=0.5, elitism 1, mutation sigma=0.005 on 10% of genes, alpha=1")
+PRECISION_WORKLOAD = ("P=4096 MLPs 784-112-10, batch 256 synthetic 28x28 images, {name} shadows of W1 (FP32 "
+                      "accumulation, FP32 masters); operators as the plain workload")
+CONFIGS = {"plain": dict(pop=1000, batch=100, precision=0),
+           "precision-bf16": dict(pop=4096, batch=256, precision=1),
+           "precision-fp8": dict(pop=4096, batch=256, precision=2)}
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
 STAGES = ("select", "breed", "evaluate")
 
@@ -205,6 +216,37 @@ def cpu_baseline(parents=None, f_adj=None, n_children: int = 1000):
             "seconds": secs, "network_samples_per_sec": gen_per_s * POP * BATCH}
 
 
+def precision_report(st, levels, y, precision: int, n: int = 64) -> dict:
+    """Shadow fitness of the last generation vs the oracle's FP64 evaluation of the
+    FP32 masters on the same batch, for n individuals spread over the population:
+    loss error relative to max(|f|, 1e-2), Spearman rank correlation and top-10%
+    overlap (reported, not pinned: a converged population's losses differ by less
+    than FP32 resolves), and the error against the oracle's evaluation of the
+    same shadows' values."""
+    import numpy as np
+    import oracle
+    from scipy import stats
+    oracle.build()
+    f_gpu = st.leea_raw_fitness()
+    popv = st.leea_get_population()
+    rows = np.linspace(0, len(f_gpu) - 1, n).round().astype(int)
+    x64 = levels.astype(np.float64) / 255.0
+    f64, _ = oracle.evaluate(popv[rows].astype(np.float64), DIMS, x64, y)
+    # the same individuals with their shadows' values (the library's own scale exponents)
+    _, scale_exp, _ = st.leea_get_shadow(precision)
+    fq, _ = oracle.evaluate_shadow(popv[rows].astype(np.float64), DIMS, precision, scale_exp[rows], x64, y)
+    g = f_gpu[rows].astype(np.float64)
+    err = np.abs(g - f64)
+    rel = err / np.maximum(np.abs(f64), 1e-2)  # relative, with the FP32 rule's floor for losses near 0
+    k = max(1, n // 10)
+    top = len(set(np.argsort(-g)[:k].tolist()) & set(np.argsort(-f64)[:k].tolist())) / k
+    return {"individuals": int(n), "max_rel_loss_error": float(rel.max()), "mean_rel_loss_error": float(rel.mean()),
+            "max_abs_loss_error": float(err.max()), "mean_loss_fp64": float(-f64.mean()),
+            "loss_spread_fp64": float(f64.std()), "spearman": float(stats.spearmanr(g, f64).statistic),
+            "max_rel_error_vs_quantized_oracle": float((np.abs(g - fq) / np.maximum(np.abs(fq), 1e-2)).max()),
+            "top10_overlap": float(top)}
+
+
 # --------------------------------------------------------------------------------
 # arms
 # --------------------------------------------------------------------------------
@@ -251,12 +293,14 @@ def run_native(args, rank: int, world: int, local_rank: int):
     leea.load_library()
 
     steps, warmup = args.steps, args.warmup
+    cfg = CONFIGS[args.config]
+    pop, batch, precision = cfg["pop"], cfg["batch"], cfg["precision"]
     (xtr, ytr), _ = synthetic.dataset(n_train=60000, n_test=1)
-    u8 = args.input == "u8"
+    u8 = args.input == "u8" or precision > 0
     if u8:  # the images as their 8-bit levels k (x = k / 255), as MNIST stores them
         xtr = synthetic.to_levels(xtr)
     n_batches = warmup + 1 + steps
-    idx = synthetic.batch_indices(len(ytr), BATCH, n_batches, seed=synthetic.BATCH_SEED + rank)
+    idx = synthetic.batch_indices(len(ytr), batch, n_batches, seed=synthetic.BATCH_SEED + rank)
     xs = torch.from_numpy(xtr[idx]).to(dev)       # [n_batches, B, 784], resident in HBM
     ys = torch.from_numpy(ytr[idx]).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -267,9 +311,12 @@ def run_native(args, rank: int, world: int, local_rank: int):
         else:
             st.leea_generation(xs[k], ys[k])
 
-    st = leea.LeeaState(POP, DIMS, leea.Params(**PARAMS, eval_path=args.eval_path), seed=1000 + rank, stream=stream)
+    prm = leea.Params(**PARAMS, eval_path=args.eval_path, precision=precision)
+    st = leea.LeeaState(pop, DIMS, prm, seed=1000 + rank, stream=stream)
     for k in range(warmup + 1):  # the first call evaluates the initial population
         gen(st, k)
+        if k == 0 and precision and rank == 0:
+            report_initial = precision_report(st, xs[0].cpu().numpy(), ys[0].cpu().numpy(), precision)
     torch.cuda.synchronize(dev)
     st.leea_profile_enable(True)
     st.leea_profile_read()
@@ -318,16 +365,22 @@ def run_native(args, rank: int, world: int, local_rank: int):
 
     # ---- roofline of the dominant kernel ----
     hbm_peak, sm_max_mhz, peak_src = _peaks()
-    n_e, n_c, n_m, _ = leea.leea_counts(POP, leea.Params(**PARAMS))
+    n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PARAMS))
     c = leea.leea_num_params(DIMS)
     d0, h, d_out = DIMS
     tensor_eval = args.eval_path != leea.EVAL_SIMT
+    elem = {0: 4, 1: 2, 2: 1}[precision]
+    shadow_bytes = d0 * h * elem if precision else 0  # per child written by breed, read by evaluate
     work = {
-        "breed": ("hbm", 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) / 1e9, "GB/s", hbm_peak),
+        # parents read once per use, children written (FP32 master, plus the shadow of W1)
+        "breed": ("hbm", (4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + shadow_bytes * (n_e + n_c + n_m)) / 1e9,
+                  "GB/s", hbm_peak),
         # tensor-core path: the per-individual weight stream (X stays in L2);
+        # precision form: the shadow of W1 plus b1, W2, b2 from the master;
         # CUDA-core path: FP32 FFMA work
-        "evaluate": (("hbm", 4.0 * c * POP / 1e9, "GB/s", hbm_peak) if tensor_eval else
-                     ("alu", 2.0 * POP * BATCH * (d0 * h + h * d_out) / 1e12, "TFLOP/s",
+        "evaluate": (("hbm", (shadow_bytes + 4.0 * (c - d0 * h) if precision else 4.0 * c) * pop / 1e9, "GB/s",
+                      hbm_peak) if tensor_eval else
+                     ("alu", 2.0 * pop * batch * (d0 * h + h * d_out) / 1e12, "TFLOP/s",
                       SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12)),
         "select": ("latency", None, None, None),
     }
@@ -344,29 +397,45 @@ def run_native(args, rank: int, world: int, local_rank: int):
     dom = max(("breed", "evaluate"), key=lambda n: prof[n][0])
     kd = kernels[dom]
     src = {"breed": "leea_breed.cu",
-           "evaluate": ("leea_eval_u8.cu" if u8 else "leea_eval_tc.cu") if tensor_eval else "leea_eval_simt.cu"}[dom]
+           "evaluate": (("leea_eval_shadow.cu" if precision else "leea_eval_u8.cu") if u8 else "leea_eval_tc.cu")
+           if tensor_eval else "leea_eval_simt.cu"}[dom]
     tr = TRAFFIC.get(dom)
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == _src_sha(src) else None
     roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
                 "peak_source": f"{peak_src} ({'HBM copy' if kd['unit'] == 'GB/s' else 'FP32 FFMA: 152 SM x 128 lanes x 2 x max SM clock'})"}
-    if tensor_eval:  # tensor-core work actually issued (3 passes, M padded to 128, K to the MMA step)
-        k_pad = 784 if u8 else 800
-        kernels["evaluate"]["tensor_tflops_issued"] = (3 * 2.0 * POP * 128 * k_pad * h / 1e12) / (
+    if tensor_eval:  # tensor-core work issued (passes, M padded to 128-sample tiles, K to the MMA step)
+        k_pad = {0: 784 if u8 else 800, 1: 784, 2: 800}[precision]
+        passes = {0: 3, 1: 1, 2: 2}[precision]
+        tiles = (batch + 127) // 128
+        kernels["evaluate"]["tensor_tflops_issued"] = (passes * 2.0 * pop * tiles * 128 * k_pad * h / 1e12) / (
             prof["evaluate"][0] / max(1, prof["evaluate"][1]) / 1000.0)
 
+    pname = {1: "BF16", 2: "FP8-e4m3 (per-individual power-of-two scale)"}.get(precision)
+    workload = PRECISION_WORKLOAD.format(name=pname) if precision else WORKLOAD
+    eval_kernel = ("tcgen05 " + {1: "kind::f16 on BF16 shadows", 2: "kind::f8f6f4 on FP8 shadows, 2 input pieces"}[
+        precision] + ", batch in TMEM" if precision else
+                   (("tcgen05 BF16 exact pieces, batch in TMEM" if u8 else "tcgen05 3xTF32") if tensor_eval
+                    else "CUDA-core FP32 FFMA"))
+    pop_mb = pop * leea.leea_padded_params(DIMS) * 4 / 1e6
     line = {"metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps,
             "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
+            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16 (f32 accumulate)", 2: "fp8-e4m3 (f32 accumulate)"}[
+                precision], "data": "synthetic",
+            "config": {"workload": workload, "parallelism": "replicas" if world > 1 else "single GPU",
                        "input": "uint8 levels k, x = k/255" if u8 else "float32 x",
-                       "eval_kernel": (("tcgen05 BF16 exact pieces, batch in TMEM" if u8 else "tcgen05 3xTF32")
-                                       if tensor_eval else "CUDA-core FP32 FFMA"),
-                       "l2": "inputs larger than L2 (2 population buffers of 356 MB), no flush"},
-            "network_samples_per_sec": gen_per_s * POP * BATCH,
+                       "eval_kernel": eval_kernel,
+                       "l2": f"inputs larger than L2 (2 population buffers of {pop_mb:.0f} MB), no flush"},
+            "network_samples_per_sec": gen_per_s * pop * batch,
             "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())), "roofline": roofline,
             "kernels": kernels, "clocks": clk}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if precision and rank == 0:
+        # the last generation evaluated the last end-to-end batch
+        line["precision_vs_fp64"] = {
+            "initial_population": report_initial,
+            "final_population": precision_report(st, xh[e2e_steps - 1].numpy(), yh[e2e_steps - 1].numpy(),
+                                                   precision)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not precision:
         pop_now = st.leea_get_population()
         f_now = st.leea_fitness()
         line["cpu_baseline"] = cpu_baseline(pop_now, f_now, n_children=args.cpu_children)
@@ -386,6 +455,8 @@ def main():
     ap.add_argument("--cpu-children", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eval-path", type=int, default=0, help="0 auto (tensor cores), 1 CUDA-core FP32, 2 tensor")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="plain",
+                    help="plain: the headline FP32 workload; precision-*: P=4096, batch 256, BF16/FP8 shadows")
     ap.add_argument("--input", choices=["u8", "f32"], default="u8",
                     help="minibatch as 8-bit levels (x = k/255, the images' own encoding) or as float32")
     args = ap.parse_args()

@@ -96,7 +96,7 @@ typedef struct {
     float mut_rate;     /* per-gene mutation probability; 1 = every gene      */
     float alpha;        /* inheritance weight alpha on the new fitness; 1     */
     int32_t init;       /* 0 N(0, 1/fan_in), 1 Glorot-uniform (Section 4.1)   */
-    int32_t precision;  /* 0 FP32 (only value accepted by this version)       */
+    int32_t precision;  /* 0 FP32; 1 BF16 / 2 FP8-e4m3 shadow of W1, see below */
     int32_t eval_path;  /* LEEA_EVAL_AUTO / _SIMT / _TENSOR, see below        */
 } leea_params;
 
@@ -107,6 +107,31 @@ typedef struct {
  * (X_hi W_hi + X_hi W_lo + X_lo W_hi, FP32 accumulation), which is within
  * ~1e-6 relative of FP32; LEEA_EINVAL if the shape does not allow it. */
 enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2 };
+
+/* Precision form (a throughput variant of Eq. 1; the paper itself computes in
+ * FP32).  With precision 1 or 2 the population keeps its FP32 master, which
+ * breeding updates exactly as in FP32 (small mutation steps are not rounded
+ * away), and every individual also carries a shadow of its first-layer weights
+ * W1 (genes 0 .. h d_0 - 1):
+ *  - precision 1: BF16, round-to-nearest-even of the master;
+ *  - precision 2: FP8-e4m3 of w / 2^e_p with saturation to +-448, where e_p is
+ *    the individual's scale exponent, the smallest e with 448 2^e >= B_p for
+ *    an upper bound B_p on max |W1_p|.  Shadows made from a whole population
+ *    (leea_make_shadow, leea_create, leea_set_population) take B_p = the exact
+ *    max |W1_p|.  Children take it from their parents' exact maxima: an elite
+ *    its parent's, a crossover child the larger of its parents', a mutation
+ *    child fmaf(sigma, 5.77, parent's) (5.77 bounds |z| of this library's
+ *    normals).  Breeding records each child's exact max |W1| for the next
+ *    generation.
+ * Evaluation then multiplies 8-bit inputs x = k / x_div by the shadow on the
+ * tensor cores with FP32 accumulation (the levels k are exact in BF16, and as
+ * the two FP8 pieces 16 floor(k / 16) and k mod 16), scales by 2^e_p / x_div,
+ * and computes b1, ReLU, layer 2 and the loss from the FP32 master in FP32.
+ * Requirements: n_dims == 3, d_0 % 16 == 0, h % 16 == 0, h <= 256,
+ * d_out <= 16 and h + A <= 512 with A = round_up(8 ceil(d_0 / 16), 16) for
+ * BF16 and round_up(16 ceil(d_0 / 32), 16) for FP8 (d_0 = 784: h <= 112).
+ * The state object then accepts only the 8-bit generation calls. */
+enum { LEEA_PRECISION_FP32 = 0, LEEA_PRECISION_BF16 = 1, LEEA_PRECISION_FP8 = 2 };
 
 /* Fills *out with the paper's defaults (Section 4). */
 leea_status leea_default_params(leea_params* out);
@@ -155,7 +180,8 @@ leea_status leea_rank(int32_t pop, const float* f_adj_dev, int32_t* order_dev,
  * parent 2), ties to the lower index.  f_inh = (f1 + f2)/2 after crossover,
  * f3 after mutation, the elite's own f_adj for an elite.
  * Inputs f_adj_dev float[pop], order_dev int32[pop]; outputs par1_dev,
- * par2_dev, kind_dev int32[pop] and f_inh_dev float[pop]. */
+ * par2_dev, kind_dev int32[pop] and f_inh_dev float[pop].  p->precision must
+ * be 0 here: the precision form's scale exponents come from the state object. */
 leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_dev,
                         const int32_t* order_dev, uint64_t seed, uint32_t gen,
                         int32_t* par1_dev, int32_t* par2_dev, int32_t* kind_dev,
@@ -167,7 +193,8 @@ leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_de
  * arithmetic crossover -> (a + b) / 2; mutation -> a + sigma z_i on genes whose
  * MUTMASK draw16 i < floor(mut_rate 2^16) (all genes when mut_rate = 1), with
  * z_i the Box-Muller normal of the NORMAL stream.  parents_dev and children_dev
- * are float[pop][c_pad] and must not overlap. */
+ * are float[pop][c_pad] and must not overlap.  p->precision must be 0 here:
+ * shadows of a bred population come from the state object or leea_make_shadow. */
 leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                        const leea_params* p, uint64_t seed, uint32_t gen,
                        const float* parents_dev, const int32_t* par1_dev,
@@ -202,6 +229,44 @@ leea_status leea_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims,
                              const int32_t* y_dev, int32_t batch, float alpha,
                              const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
                              int32_t* correct_dev, int32_t eval_path, void* stream);
+
+/* Bytes between consecutive individuals' shadows for `precision` (1 or 2):
+ * B h 128 with B = ceil(d_0 e / 128) blocks, e = 2 (BF16) or 1 (FP8); -1 if
+ * the arguments are invalid.  A shadow is tiled for the tensor cores: block b
+ * holds inputs [b w, (b + 1) w) (w = 128 / e) of all h rows of W1, 128 bytes
+ * per row, row o at byte 128 (b h + o) of the shadow, and within a row the
+ * 16-byte chunk c (inputs b w + c 16 / e ...) is stored at chunk position
+ * c XOR (o mod 8).  Inputs past d_0 in the last block are zero. */
+int64_t leea_shadow_stride(const int32_t* dims, int32_t n_dims, int32_t precision);
+
+/* Shadows of a whole population (see "Precision form" above): for each p,
+ * amax_dev[p] = max |W1_p| (float), scale_exp_dev[p] = e_p (precision 2 only;
+ * may be NULL for precision 1) and the shadow at shadow_dev + p * stride
+ * (stride = leea_shadow_stride; 128-byte aligned buffer), padding included. */
+leea_status leea_make_shadow(int32_t pop, const int32_t* dims, int32_t n_dims, int32_t precision,
+                             const float* pop_dev, uint8_t* shadow_dev, int32_t* scale_exp_dev,
+                             float* amax_dev, void* stream);
+
+/* Scratch bytes leea_evaluate_shadow_u8 needs for (pop, batch): 0 when
+ * batch <= 128, else 8 * ceil(batch / 128) * pop (per-tile partial sums). */
+int64_t leea_shadow_scratch_bytes(int32_t pop, int32_t batch);
+
+/* leea_evaluate_u8 with layer 1 on the shadows: x_u8_dev uint8[batch][d_0],
+ * pop_dev the FP32 master (b1, W2, b2 are read from it), shadow_dev and
+ * scale_exp_dev as leea_make_shadow writes them (scale_exp_dev unused and may be
+ * NULL for precision 1; the shadows' padding must be zero, as leea_make_shadow
+ * leaves it), x_u8_dev 16-byte aligned.  A batch above 128 samples is split into tiles of 128
+ * whose partial sums go to scratch_dev (caller-owned, scratch_bytes >=
+ * leea_shadow_scratch_bytes(pop, batch); NULL/0 allowed when that is 0) and
+ * are combined in tile order.  Other arguments and outputs as in
+ * leea_evaluate_u8. */
+leea_status leea_evaluate_shadow_u8(int32_t pop, const int32_t* dims, int32_t n_dims,
+                                    const float* pop_dev, int32_t precision,
+                                    const uint8_t* shadow_dev, const int32_t* scale_exp_dev,
+                                    const uint8_t* x_u8_dev, float x_div, const int32_t* y_dev,
+                                    int32_t batch, float alpha, const float* f_inh_dev,
+                                    float* f_raw_dev, float* f_adj_dev, int32_t* correct_dev,
+                                    float* scratch_dev, int64_t scratch_bytes, void* stream);
 
 /* Synchronises `stream`, then reads and clears this device's status word.
  * Returns LEEA_ETIMEOUT if a kernel's bounded wait gave up since the last
@@ -284,6 +349,13 @@ leea_status leea_set_generation(leea_state* s, uint32_t gen, int32_t evaluated);
  * and f_inh float[pop]; any pointer may be NULL.  Synchronises. */
 leea_status leea_get_selection(leea_state* s, int32_t* order, int32_t* par1,
                                int32_t* par2, int32_t* kind, float* f_inh);
+
+/* Precision form: the current population's shadows (uint8[pop][stride], the
+ * tiled layout of leea_shadow_stride), and per individual the FP8 scale
+ * exponents and exact max |W1| (any pointer may be NULL).  LEEA_ESTATE for an
+ * FP32 object.  Synchronises. */
+leea_status leea_get_shadow(leea_state* s, uint8_t* shadow_host, int32_t* scale_exp_host,
+                            float* amax_host);
 
 /* Generation counter g (0 before the first breed). */
 uint32_t leea_generation_index(const leea_state* s);

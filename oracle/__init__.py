@@ -111,6 +111,7 @@ def lib() -> ctypes.CDLL:
         L.leea_cpu_round_e4m3.restype = dbl
         L.leea_cpu_fp8_scale_exp.argtypes = [dbl]
         L.leea_cpu_fp8_scale_exp.restype = i32
+        L.leea_cpu_quantize_w1.argtypes = [i32, vp, i32, vp, i32, vp, vp]
         L.leea_cpu_evaluate_shadow.argtypes = [i32, vp, i32, vp, i32, vp, vp, vp, i32, vp, vp]
         L.leea_cpu_evaluate_shadow.restype = ctypes.c_int
         L.leea_cpu_draw16.argtypes = [u64, u32, u32, u32, u32]
@@ -222,6 +223,17 @@ def round_e4m3(x: float) -> float:
 
 def fp8_scale_exp(bound: float) -> int:
     return int(lib().leea_cpu_fp8_scale_exp(float(bound)))
+
+
+def quantize_w1(popv, dims, precision: int, scale_exp) -> np.ndarray:
+    """The population with W1 replaced by its BF16 (1) or scaled FP8-e4m3 (2) shadow's value."""
+    d = _dims(dims)
+    pv = _f64(popv)
+    out = np.empty_like(pv)
+    se = None if scale_exp is None else _i32(scale_exp)
+    _check(lib().leea_cpu_quantize_w1(pv.shape[0], _ptr(d), len(d), _ptr(pv), int(precision), _ptr(se), _ptr(out)),
+           "quantize_w1")
+    return out
 
 
 def evaluate_shadow(popv, dims, precision: int, scale_exp, x, y):

@@ -308,6 +308,29 @@ int32_t leea_cpu_fp8_scale_exp(double bound)
     return e;
 }
 
+int leea_cpu_quantize_w1(int32_t pop, const int32_t* dims, int32_t n_dims, const double* popv,
+                         int32_t precision, const int32_t* scale_exp, double* out)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || pop <= 0 || !popv || !out || precision < 0 || precision > 2 || (precision == 2 && !scale_exp))
+        return LEEA_CPU_EINVAL;
+    int64_t n_w1 = (int64_t)dims[0] * dims[1];
+    for (int32_t p = 0; p < pop; p++) {
+        const double* theta = popv + (int64_t)p * c;
+        double* q = out + (int64_t)p * c;
+        memmove(q, theta, sizeof(double) * (size_t)c);
+        for (int64_t i = 0; i < n_w1; i++) {
+            if (precision == 1) {
+                q[i] = leea_cpu_round_bf16(q[i]);
+            } else if (precision == 2) {
+                double s = ldexp(1.0, scale_exp[p]);
+                q[i] = leea_cpu_round_e4m3(q[i] / s) * s;
+            }
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
 int leea_cpu_evaluate_shadow(int32_t pop, const int32_t* dims, int32_t n_dims,
                              const double* popv, int32_t precision, const int32_t* scale_exp,
                              const double* x, const int32_t* y, int32_t batch,
@@ -316,23 +339,15 @@ int leea_cpu_evaluate_shadow(int32_t pop, const int32_t* dims, int32_t n_dims,
     int64_t c = leea_cpu_num_params(dims, n_dims);
     if (c < 0 || pop <= 0 || !popv || precision < 0 || precision > 2 || (precision == 2 && !scale_exp))
         return LEEA_CPU_EINVAL;
-    int64_t n_w1 = (int64_t)dims[0] * dims[1];
     double* q = (double*)malloc(sizeof(double) * (size_t)c);
     if (!q) return LEEA_CPU_ENOMEM;
     int rc = LEEA_CPU_OK;
     for (int32_t p = 0; p < pop && rc == LEEA_CPU_OK; p++) {
-        const double* theta = popv + (int64_t)p * c;
-        memcpy(q, theta, sizeof(double) * (size_t)c);
-        for (int64_t i = 0; i < n_w1; i++) {
-            if (precision == 1) {
-                q[i] = leea_cpu_round_bf16(theta[i]);
-            } else if (precision == 2) {
-                double s = ldexp(1.0, scale_exp[p]);
-                q[i] = leea_cpu_round_e4m3(theta[i] / s) * s;
-            }
-        }
-        rc = leea_cpu_evaluate(1, dims, n_dims, q, x, y, batch, f_out + p,
-                               correct_out ? correct_out + p : NULL, NULL);
+        rc = leea_cpu_quantize_w1(1, dims, n_dims, popv + (int64_t)p * c, precision,
+                                  scale_exp ? scale_exp + p : NULL, q);
+        if (rc == LEEA_CPU_OK)
+            rc = leea_cpu_evaluate(1, dims, n_dims, q, x, y, batch, f_out + p,
+                                   correct_out ? correct_out + p : NULL, NULL);
     }
     free(q);
     return rc;

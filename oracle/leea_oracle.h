@@ -109,6 +109,10 @@ double leea_cpu_round_e4m3(double x);
 /* Exponent e of the power-of-two FP8 scale 2^e for an upper bound on |W1|:
  * the smallest e with 448 * 2^e >= bound (0 when bound <= 0). */
 int32_t leea_cpu_fp8_scale_exp(double bound);
+/* The population with W1 of every individual replaced by the value of its
+ * shadow (the rule below); out may equal popv. */
+int leea_cpu_quantize_w1(int32_t pop, const int32_t* dims, int32_t n_dims, const double* popv,
+                         int32_t precision, const int32_t* scale_exp, double* out);
 /* Fitness (Eq. 1) with W1 of every individual replaced by its shadow:
  * precision 1 -> round_bf16(w); precision 2 -> round_e4m3(w / 2^e_p) * 2^e_p
  * with the per-individual exponents scale_exp[p].  The rest of the net and the

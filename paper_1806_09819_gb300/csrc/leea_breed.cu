@@ -20,6 +20,9 @@
 // (prefix scan over the lanes) so that normals are computed by consecutive
 // lanes instead of by whichever lane happens to own a masked gene.  Every mbarrier
 // wait is bounded in time; on expiry the kernel sets kStatusBreedTimeout.
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
 #include "leea_internal.h"
 #include "philox.cuh"
 #include "tc_ptx.cuh"
@@ -43,6 +46,8 @@ struct StageMeta {
     int32_t kind;    // 0 elite, 1 crossover, 2 mutation, -1 invalid parent index
     int32_t g0;      // first gene of the chunk
     int32_t len;     // genes in the chunk (multiple of 32)
+    int32_t sexp;    // precision form, FP8: exponent of the child's scale
+    int32_t pad[3];
 };
 
 struct BreedSmem {
@@ -69,6 +74,48 @@ __device__ __forceinline__ BreedSmem carve(uint8_t* raw)
 
 constexpr size_t kBreedSmemBytes =
     128 + 2 * kStages * kChunkBytes + sizeof(StageMeta) * kStages + 16 * kStages + 16;
+
+// The shadow of 8 child genes i0 .. i0+7 of W1: 8 BF16 (16 bytes) or 8 FP8-e4m3
+// of w / 2^sexp with saturation (8 bytes).  Returns max |w| of the 8 genes.
+__device__ __forceinline__ float write_shadow8(const BreedArgs& a, int32_t j, int32_t sexp, int64_t i0,
+                                               const float4 (&v)[2])
+{
+    const float mx = fmaxf(fmaxf(fmaxf(fabsf(v[0].x), fabsf(v[0].y)), fmaxf(fabsf(v[0].z), fabsf(v[0].w))),
+                           fmaxf(fmaxf(fabsf(v[1].x), fabsf(v[1].y)), fmaxf(fabsf(v[1].z), fabsf(v[1].w))));
+    // Eight genes of one row: d_0 % 16 == 0 keeps them in one 16-byte (BF16)
+    // or 8-byte (FP8) piece of a chunk.
+    const int32_t o = static_cast<int32_t>(i0 / a.sh_k);
+    const int32_t k = static_cast<int32_t>(i0 - static_cast<int64_t>(o) * a.sh_k);
+    uint8_t* dst = a.shadow + static_cast<int64_t>(j) * a.sh_stride +
+                   shadow_offset(a.sh_h, a.precision == 1 ? 2 : 1, o, k);
+    if (a.precision == 1) {
+        const __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0].x, v[0].y);
+        const __nv_bfloat162 b1 = __floats2bfloat162_rn(v[0].z, v[0].w);
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(v[1].x, v[1].y);
+        const __nv_bfloat162 b3 = __floats2bfloat162_rn(v[1].z, v[1].w);
+        uint4 w;
+        w.x = *reinterpret_cast<const uint32_t*>(&b0);
+        w.y = *reinterpret_cast<const uint32_t*>(&b1);
+        w.z = *reinterpret_cast<const uint32_t*>(&b2);
+        w.w = *reinterpret_cast<const uint32_t*>(&b3);
+        *reinterpret_cast<uint4*>(dst) = w;
+    } else {
+        const float inv = ldexpf(1.0f, -sexp);  // exact: a power of two
+        const __nv_fp8x2_storage_t q0 =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[0].x * inv, v[0].y * inv), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t q1 =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[0].z * inv, v[0].w * inv), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t q2 =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[1].x * inv, v[1].y * inv), __NV_SATFINITE, __NV_E4M3);
+        const __nv_fp8x2_storage_t q3 =
+            __nv_cvt_float2_to_fp8x2(make_float2(v[1].z * inv, v[1].w * inv), __NV_SATFINITE, __NV_E4M3);
+        uint2 w;
+        w.x = static_cast<uint32_t>(q0) | (static_cast<uint32_t>(q1) << 16);
+        w.y = static_cast<uint32_t>(q2) | (static_cast<uint32_t>(q3) << 16);
+        *reinterpret_cast<uint2*>(dst) = w;
+    }
+    return mx;
+}
 
 __device__ __forceinline__ float* stage_a(const BreedSmem& s, uint32_t stage)
 {
@@ -215,7 +262,7 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
         if (lane == 0) {
             uint32_t stage = 0, phase = 0;
             uint32_t issued_mask = 0, parity_mask = 0;  // per stage: issued at all / parity of the last issue
-            int32_t cur_j = -1, cur_kind = 0, cur_p1 = 0, cur_p2 = 0;
+            int32_t cur_j = -1, cur_kind = 0, cur_p1 = 0, cur_p2 = 0, cur_sexp = 0;
             bool ok = true;
             for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
                 if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
@@ -231,11 +278,12 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
                     cur_kind = kind[j];
                     cur_p1 = par1[j];
                     cur_p2 = par2[j];
+                    cur_sexp = (a.precision == 2) ? a.scale_exp[j] : 0;
                     if (cur_p1 < 0 || cur_p1 >= a.pop || cur_p2 < 0 || cur_p2 >= a.pop) cur_kind = kKindInvalid;
                 }
                 const int64_t g0 = static_cast<int64_t>(ck) * kChunk;
                 const int32_t len = static_cast<int32_t>(a.c_pad - g0 < kChunk ? a.c_pad - g0 : kChunk);
-                s.meta[stage] = StageMeta{ j, cur_kind, static_cast<int32_t>(g0), len };
+                s.meta[stage] = StageMeta{ j, cur_kind, static_cast<int32_t>(g0), len, cur_sexp, { 0, 0, 0 } };
                 const uint32_t bytes = static_cast<uint32_t>(len) * 4u;
                 if (cur_kind == kKindInvalid) {
                     ptx::mbar_arrive(&s.full[stage]);
@@ -306,6 +354,14 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
                 }
                 O[2 * ct] = v[0];
                 O[2 * ct + 1] = v[1];
+            }
+            if (a.precision > 0 && static_cast<int64_t>(m.g0) < a.n_w1) {  // warp-uniform
+                const int64_t i0 = static_cast<int64_t>(m.g0) + kGenesPerLane * ct;
+                float mx = 0.0f;
+                if (live && i0 < a.n_w1) mx = write_shadow8(a, m.j, m.sexp, i0, v);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+                if (lane == 0 && mx > 0.0f) atomicMax(reinterpret_cast<int*>(a.amax_out + m.j), __float_as_int(mx));
             }
             __syncwarp();
             if (lane == 0) ptx::mbar_arrive(&s.empty[stage]);

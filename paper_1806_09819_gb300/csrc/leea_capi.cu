@@ -88,7 +88,7 @@ leea_status check_params(const leea_params* p)
     if (!(p->mut_rate >= 0.0f && p->mut_rate <= 1.0f)) return fail(LEEA_EINVAL, "mut_rate not in [0,1]");
     if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
     if (p->init != 0 && p->init != 1) return fail(LEEA_EINVAL, "init must be 0 or 1");
-    if (p->precision != 0) return fail(LEEA_EINVAL, "precision must be 0 (FP32)");
+    if (p->precision < 0 || p->precision > 2) return fail(LEEA_EINVAL, "precision must be 0, 1 or 2");
     if (p->eval_path < LEEA_EVAL_AUTO || p->eval_path > LEEA_EVAL_TENSOR)
         return fail(LEEA_EINVAL, "eval_path must be LEEA_EVAL_AUTO, _SIMT or _TENSOR");
     return LEEA_OK;
@@ -214,6 +214,35 @@ leea_status check_eval_shape(const NetLayout& net, int32_t batch)
     return LEEA_OK;
 }
 
+int64_t shadow_stride_of(const NetLayout& net, int32_t precision)
+{
+    return shadow_stride_bytes(net.dims[0], net.dims[1], precision == 1 ? 2 : 1);
+}
+
+leea_status check_shadow_shape(const NetLayout& net, int32_t precision)
+{
+    if (precision != 1 && precision != 2) return fail(LEEA_EINVAL, "precision must be 1 (BF16) or 2 (FP8)");
+    if (!eval_shadow_supported(net, precision, 1))
+        return fail(LEEA_EINVAL, "the precision form needs n_dims == 3, d_0 %% 16 == 0, h %% 16 == 0, h <= 256, "
+                                 "d_out <= 16 and h plus the batch tile's TMEM columns <= 512 (d_0 = 784: h <= 112)");
+    return LEEA_OK;
+}
+
+leea_status dispatch_eval_shadow(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
+                                 const uint8_t* shadow, const int32_t* scale_exp, const uint8_t* x, float x_div,
+                                 const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                                 float* f_adj, int32_t* correct, float* scratch, cudaStream_t stream)
+{
+    if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
+    unsigned int* status = device_status_ptr();
+    if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+    LEEA_CUDA_TRY(launch_eval_shadow(net, pop, pop_dev, precision, shadow, shadow_stride_of(net, precision),
+                                     scale_exp, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct, scratch,
+                                     status, stream),
+                  "shadow evaluate kernel");
+    return LEEA_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------
@@ -318,6 +347,7 @@ leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_de
     leea_status st = check_pop(pop);
     if (st) return st;
     if ((st = check_params(p))) return st;
+    if (p->precision != 0) return fail(LEEA_EINVAL, "leea_select takes precision 0; use the state object");
     if (!f_adj_dev || !order_dev || !par1_dev || !par2_dev || !kind_dev || !f_inh_dev)
         return fail(LEEA_EINVAL, "NULL device pointer");
     const SelectArgs a = select_args(pop, p, seed, gen);
@@ -351,6 +381,8 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims, const l
     leea_status st = check_pop(pop);
     if (st) return st;
     if ((st = check_params(p))) return st;
+    if (p->precision != 0)
+        return fail(LEEA_EINVAL, "leea_breed takes precision 0; use the state object or leea_make_shadow");
     NetLayout net;
     if (!make_layout(dims, n_dims, p->init, &net)) return fail(LEEA_EINVAL, "invalid dims");
     if (!parents_dev || !par1_dev || !par2_dev || !kind_dev || !children_dev)
@@ -402,6 +434,65 @@ leea_status leea_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims, c
     if (eval_path < LEEA_EVAL_AUTO || eval_path > LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "bad eval_path");
     return dispatch_eval_u8(net, pop, pop_dev, x_u8_dev, x_div, y_dev, batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev,
                             correct_dev, eval_path, static_cast<cudaStream_t>(stream));
+}
+
+int64_t leea_shadow_stride(const int32_t* dims, int32_t n_dims, int32_t precision)
+{
+    NetLayout net;
+    if (!make_layout(dims, n_dims, 0, &net) || net.n_layers != 2 || (precision != 1 && precision != 2)) return -1;
+    return shadow_stride_of(net, precision);
+}
+
+leea_status leea_make_shadow(int32_t pop, const int32_t* dims, int32_t n_dims, int32_t precision,
+                             const float* pop_dev, uint8_t* shadow_dev, int32_t* scale_exp_dev, float* amax_dev,
+                             void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if ((st = check_shadow_shape(net, precision))) return st;
+    if (!pop_dev || !shadow_dev || !amax_dev || (precision == 2 && !scale_exp_dev))
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    if ((reinterpret_cast<uintptr_t>(pop_dev) & 15u) || (reinterpret_cast<uintptr_t>(shadow_dev) & 127u))
+        return fail(LEEA_EINVAL, "population must be 16-byte and shadow 128-byte aligned");
+    LEEA_CUDA_TRY(launch_make_shadow(pop, net.dims[0], net.dims[1], net.c_pad, pop_dev, precision, shadow_dev,
+                                     shadow_stride_of(net, precision), scale_exp_dev, amax_dev,
+                                     static_cast<cudaStream_t>(stream)),
+                  "make shadow kernel");
+    return LEEA_OK;
+}
+
+int64_t leea_shadow_scratch_bytes(int32_t pop, int32_t batch)
+{
+    if (pop <= 0 || batch <= 0) return 0;
+    return static_cast<int64_t>(eval_shadow_scratch_bytes(pop, batch));
+}
+
+leea_status leea_evaluate_shadow_u8(int32_t pop, const int32_t* dims, int32_t n_dims, const float* pop_dev,
+                                    int32_t precision, const uint8_t* shadow_dev, const int32_t* scale_exp_dev,
+                                    const uint8_t* x_u8_dev, float x_div, const int32_t* y_dev, int32_t batch,
+                                    float alpha, const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
+                                    int32_t* correct_dev, float* scratch_dev, int64_t scratch_bytes, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if ((st = check_shadow_shape(net, precision))) return st;
+    if (batch <= 0) return fail(LEEA_EINVAL, "batch must be >= 1");
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
+    if (!pop_dev || !shadow_dev || !x_u8_dev || !y_dev || !f_raw_dev || (precision == 2 && !scale_exp_dev))
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    if ((reinterpret_cast<uintptr_t>(pop_dev) & 15u) || (reinterpret_cast<uintptr_t>(shadow_dev) & 127u) ||
+        (reinterpret_cast<uintptr_t>(x_u8_dev) & 15u))
+        return fail(LEEA_EINVAL, "population, x (16-byte) and shadow (128-byte) must be aligned");
+    const int64_t need = static_cast<int64_t>(eval_shadow_scratch_bytes(pop, batch));
+    if (need > 0 && (!scratch_dev || scratch_bytes < need))
+        return fail(LEEA_EINVAL, "batch %d needs %lld scratch bytes", batch, static_cast<long long>(need));
+    return dispatch_eval_shadow(net, pop, pop_dev, precision, shadow_dev, scale_exp_dev, x_u8_dev, x_div, y_dev,
+                                batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev, correct_dev, scratch_dev,
+                                static_cast<cudaStream_t>(stream));
 }
 
 leea_status leea_device_status(void* stream, uint32_t* flags_out)
@@ -466,6 +557,13 @@ struct leea_state {
     int64_t y_stage_cap;
     bool profiling;
     ProfileRing* prof;
+    // precision form (prm.precision > 0)
+    uint8_t* shadow[2];  // W1 shadows, paired with popbuf[0] / popbuf[1]
+    float* amax[2];      // exact max |W1| per individual, paired likewise
+    int32_t* scale_exp;  // FP8 scale exponents of the current population
+    int64_t sh_stride;
+    float* scratch;      // per-tile partial sums for batch > 128
+    size_t scratch_bytes;
 };
 
 namespace {
@@ -485,6 +583,12 @@ void free_state(leea_state* s)
     cudaFree(s->kind);
     cudaFree(s->x_stage);
     cudaFree(s->y_stage);
+    cudaFree(s->shadow[0]);
+    cudaFree(s->shadow[1]);
+    cudaFree(s->amax[0]);
+    cudaFree(s->amax[1]);
+    cudaFree(s->scale_exp);
+    cudaFree(s->scratch);
     if (s->prof) {
         if (s->prof->created)
             for (int st = 0; st < LEEA_NUM_STAGES; ++st)
@@ -532,6 +636,14 @@ struct StageScope {
     }
 };
 
+// Shadows, exponents and maxima of the current population from its master.
+cudaError_t refresh_shadow(leea_state* s)
+{
+    return launch_make_shadow(s->pop, s->net.dims[0], s->net.dims[1], s->net.c_pad, s->popbuf[s->cur],
+                              s->prm.precision, s->shadow[s->cur], s->sh_stride, s->scale_exp, s->amax[s->cur],
+                              s->stream);
+}
+
 leea_status check_state(leea_state* s)
 {
     if (!s) return fail(LEEA_EINVAL, "state is NULL");
@@ -560,6 +672,10 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         delete s;
         return fail(LEEA_EINVAL, "the state object evaluates d_0-h-d_out nets (n_dims == 3, d_out <= 32)");
     }
+    if (p->precision != 0 && (st = check_shadow_shape(s->net, p->precision))) {
+        delete s;
+        return st;
+    }
     s->pop = pop;
     s->prm = *p;
     s->seed = seed;
@@ -576,12 +692,22 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
     if (err == cudaSuccess) err = cudaMalloc(&s->par1, sizeof(int32_t) * np);
     if (err == cudaSuccess) err = cudaMalloc(&s->par2, sizeof(int32_t) * np);
     if (err == cudaSuccess) err = cudaMalloc(&s->kind, sizeof(int32_t) * np);
+    if (p->precision != 0) {
+        s->sh_stride = shadow_stride_of(s->net, p->precision);
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b) err = cudaMalloc(&s->shadow[b], np * s->sh_stride);
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b) err = cudaMalloc(&s->amax[b], sizeof(float) * np);
+        if (err == cudaSuccess) err = cudaMalloc(&s->scale_exp, sizeof(int32_t) * np);
+        if (err == cudaSuccess) err = cudaMemsetAsync(s->scale_exp, 0, sizeof(int32_t) * np, s->stream);
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b)  // zero padding of the tiled layout
+            err = cudaMemsetAsync(s->shadow[b], 0, np * s->sh_stride, s->stream);
+    }
     if (err != cudaSuccess) {
         free_state(s);
         return cuda_fail(err, "leea_create allocation");
     }
     err = cudaMemsetAsync(s->popbuf[1], 0, pop_bytes, s->stream);
     if (err == cudaSuccess) err = launch_init(s->net, pop, p->init, seed, s->popbuf[0], s->stream);
+    if (err == cudaSuccess && p->precision != 0) err = refresh_shadow(s);
     if (err != cudaSuccess) {
         free_state(s);
         return cuda_fail(err, "leea_create init");
@@ -598,19 +724,52 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
     if ((st = check_eval_shape(s->net, batch))) return st;
     if (!x_dev || !y_dev) return fail(LEEA_EINVAL, "NULL minibatch pointer");
     if (u8 && (!(x_div > 0.0f) || std::isinf(x_div))) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
+    const int32_t prec = s->prm.precision;
+    if (prec != 0) {
+        if (!u8) return fail(LEEA_EINVAL, "the precision form evaluates 8-bit inputs (leea_generation_u8*)");
+        if (s->prm.eval_path == LEEA_EVAL_SIMT)
+            return fail(LEEA_EINVAL, "the precision form runs on the tensor cores (eval_path SIMT not allowed)");
+        if (reinterpret_cast<uintptr_t>(x_dev) & 15u) return fail(LEEA_EINVAL, "x must be 16-byte aligned");
+        const size_t need = eval_shadow_scratch_bytes(s->pop, batch);
+        if (need > s->scratch_bytes) {
+            LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "scratch sync");
+            cudaFree(s->scratch);
+            s->scratch = nullptr;
+            s->scratch_bytes = 0;
+            LEEA_CUDA_TRY(cudaMalloc(&s->scratch, need), "scratch allocation");
+            s->scratch_bytes = need;
+        }
+    }
     const bool first = !s->evaluated;
     if (!first) {
         const uint32_t g = s->gen + 1;
         {
             StageScope sc(s, 0);
-            const SelectArgs a = select_args(s->pop, &s->prm, s->seed, g);
+            SelectArgs a = select_args(s->pop, &s->prm, s->seed, g);
+            if (prec != 0) {
+                a.precision = prec;
+                a.sigma = s->prm.sigma;
+                a.amax_in = s->amax[s->cur];
+                a.scale_exp_out = s->scale_exp;
+                a.amax_out = s->amax[s->cur ^ 1];
+            }
             LEEA_CUDA_TRY(launch_rank_select(a, s->f_adj, s->order, s->par1, s->par2, s->kind, s->f_inh, s->stream),
                           "rank/select kernel");
             sc.done();
         }
         {
             StageScope sc(s, 1);
-            const BreedArgs a = breed_args(s->pop, s->net, &s->prm, s->seed, g);
+            BreedArgs a = breed_args(s->pop, s->net, &s->prm, s->seed, g);
+            if (prec != 0) {
+                a.precision = prec;
+                a.n_w1 = static_cast<int64_t>(s->net.dims[0]) * s->net.dims[1];
+                a.sh_k = s->net.dims[0];
+                a.sh_h = s->net.dims[1];
+                a.shadow = s->shadow[s->cur ^ 1];
+                a.sh_stride = s->sh_stride;
+                a.scale_exp = s->scale_exp;
+                a.amax_out = s->amax[s->cur ^ 1];
+            }
             unsigned int* status = device_status_ptr();
             if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
             LEEA_CUDA_TRY(launch_breed(a, s->popbuf[s->cur], s->par1, s->par2, s->kind, s->popbuf[s->cur ^ 1],
@@ -623,7 +782,12 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
     }
     {
         StageScope sc(s, 2);
-        if (u8)
+        if (prec != 0)
+            st = dispatch_eval_shadow(s->net, s->pop, s->popbuf[s->cur], prec, s->shadow[s->cur], s->scale_exp,
+                                      static_cast<const uint8_t*>(x_dev), x_div, y_dev, batch, s->prm.alpha,
+                                      first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct, s->scratch,
+                                      s->stream);
+        else if (u8)
             st = dispatch_eval_u8(s->net, s->pop, s->popbuf[s->cur], static_cast<const uint8_t*>(x_dev), x_div, y_dev,
                                   batch, s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,
                                   s->prm.eval_path, s->stream);
@@ -771,8 +935,29 @@ leea_status leea_set_population(leea_state* s, const float* in_host)
                                     sizeof(float) * s->net.c, sizeof(float) * s->net.c, s->pop,
                                     cudaMemcpyHostToDevice, s->stream),
                   "population copy");
+    if (s->prm.precision != 0) LEEA_CUDA_TRY(refresh_shadow(s), "make shadow kernel");
     LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "population sync");
     return LEEA_OK;
+}
+
+leea_status leea_get_shadow(leea_state* s, uint8_t* shadow_host, int32_t* scale_exp_host, float* amax_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (s->prm.precision == 0) return fail(LEEA_ESTATE, "the object computes in FP32 and has no shadows");
+    if (shadow_host)
+        LEEA_CUDA_TRY(cudaMemcpyAsync(shadow_host, s->shadow[s->cur], static_cast<size_t>(s->sh_stride) * s->pop,
+                                      cudaMemcpyDeviceToHost, s->stream),
+                      "shadow copy");
+    if (scale_exp_host)
+        LEEA_CUDA_TRY(cudaMemcpyAsync(scale_exp_host, s->scale_exp, sizeof(int32_t) * s->pop, cudaMemcpyDeviceToHost,
+                                      s->stream),
+                      "scale copy");
+    if (amax_host)
+        LEEA_CUDA_TRY(cudaMemcpyAsync(amax_host, s->amax[s->cur], sizeof(float) * s->pop, cudaMemcpyDeviceToHost,
+                                      s->stream),
+                      "amax copy");
+    return check_device_status(s->stream, nullptr);
 }
 
 leea_status leea_set_fitness(leea_state* s, const float* f_adj_host)

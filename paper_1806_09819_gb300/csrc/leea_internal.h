@@ -25,11 +25,21 @@ struct NetLayout {
     int64_t c_pad;                     // device stride, multiple of 32
 };
 
+// Bound on |z| for a Box-Muller normal of this library: the radius
+// sqrt(-2 ln u1) with u1 >= 2^-24 is at most 5.7683.
+constexpr float kNormalBound = 5.77f;
+
 struct SelectArgs {
     int32_t pop, n_elite, n_cross, pool;
     int32_t sel_op, tour_k;
     uint64_t seed;
     uint32_t gen;
+    // precision form (precision 0: unused)
+    int32_t precision;
+    float sigma;
+    const float* amax_in;     // exact max |W1| of each parent
+    int32_t* scale_exp_out;   // FP8: exponent of each child's power-of-two scale
+    float* amax_out;          // zeroed here; breed accumulates each child's max |W1|
 };
 
 struct BreedArgs {
@@ -40,7 +50,43 @@ struct BreedArgs {
     float sigma;
     uint64_t seed;
     uint32_t gen;
+    // precision form (precision 0: unused): shadow of W1 (genes 0 .. n_w1-1)
+    int32_t precision;        // 1 BF16, 2 FP8-e4m3 scaled by 2^scale_exp[child]
+    int64_t n_w1;             // multiple of 8
+    int32_t sh_k, sh_h;       // d_0 and h: W1 is sh_h rows of sh_k
+    uint8_t* shadow;          // child j's shadow at shadow + j * sh_stride (tiled, see shadow_offset)
+    int64_t sh_stride;        // bytes, multiple of 128
+    const int32_t* scale_exp;
+    float* amax_out;          // atomic max of |W1| per child
 };
+
+// Tiled shadow layout.  An individual's W1 shadow is a sequence of blocks, one
+// per 128 bytes of a row (64 BF16 or 128 FP8 inputs): block b holds K-elements
+// [b kw, (b+1) kw) of all h rows, 128 bytes per row, with 16-byte chunk c of
+// row o stored at chunk position c ^ (o & 7) -- the 128-byte swizzle the
+// tensor core reads K-major operands in.  A block is thus copied to shared
+// memory verbatim; elements past d_0 in the last block are zero.
+__host__ __device__ inline int32_t shadow_blocks(int32_t k, int32_t elem) { return (k * elem + 127) / 128; }
+__host__ __device__ inline int64_t shadow_stride_bytes(int32_t k, int32_t h, int32_t elem)
+{
+    return static_cast<int64_t>(shadow_blocks(k, elem)) * h * 128;
+}
+__host__ __device__ inline int64_t shadow_offset(int32_t h, int32_t elem, int32_t o, int32_t k)
+{
+    const int32_t byte = k * elem;  // within the row
+    const int32_t b = byte >> 7, c = (byte >> 4) & 7, w = byte & 15;
+    return (static_cast<int64_t>(b) * h + o) * 128 + (((c ^ (o & 7)) << 4) | w);
+}
+
+// Device exponent of the FP8 scale: smallest e with 448 * 2^e >= bound.
+__host__ __device__ inline int32_t fp8_scale_exp(float bound)
+{
+    if (!(bound > 0.0f)) return 0;
+    int ex = 0;
+    frexpf(bound, &ex);            // bound in [2^(ex-1), 2^ex)
+    const int32_t lead = ex - 1;
+    return bound <= ldexpf(1.75f, lead) ? lead - 8 : lead - 7;
+}
 
 cudaError_t launch_init(const NetLayout& net, int32_t pop, int32_t init, uint64_t seed,
                         float* pop_dev, cudaStream_t stream);
@@ -55,6 +101,19 @@ cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t*
 cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t* par1,
                          const int32_t* par2, const int32_t* kind, float* children,
                          unsigned int* status, cudaStream_t stream);
+// Precision form: shadows of W1 for a whole population from its FP32 master
+// (exact max |W1| per individual, FP8 exponents from it).
+cudaError_t launch_make_shadow(int32_t pop, int32_t k, int32_t h, int64_t c_pad, const float* pop_dev,
+                               int32_t precision, uint8_t* shadow, int64_t sh_stride, int32_t* scale_exp, float* amax,
+                               cudaStream_t stream);
+// Evaluation of 8-bit inputs against BF16 / FP8 shadows of W1 (tcgen05).
+bool eval_shadow_supported(const NetLayout& net, int32_t precision, int32_t batch);
+size_t eval_shadow_scratch_bytes(int32_t pop, int32_t batch);
+cudaError_t launch_eval_shadow(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
+                               const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp,
+                               const uint8_t* x, float x_div, const int32_t* y, int32_t batch, float alpha,
+                               const float* f_inh, float* f_raw, float* f_adj, int32_t* correct, float* scratch,
+                               unsigned int* status, cudaStream_t stream);
 // Evaluation of d_0-h-d_out nets (one hidden layer), SIMT FP32.
 cudaError_t launch_eval_simt(const NetLayout& net, int32_t pop, const float* pop_dev,
                              const float* x, const int32_t* y, int32_t batch, float alpha,

@@ -108,6 +108,18 @@ __device__ __forceinline__ void select_child(const SelectArgs& a, const float* f
     par1[j] = p1;
     par2[j] = p2;
     f_inh[j] = fi;
+    if (a.precision > 0) {
+        a.amax_out[j] = 0.0f;
+        if (a.precision == 2) {
+            // Upper bound on the child's max |W1|: a crossover gene (either
+            // parent's, or their mean) is bounded by the larger parent bound; a
+            // mutation adds at most sigma * kNormalBound.
+            float bound = a.amax_in[p1];
+            if (k == kKindCross) bound = fmaxf(bound, a.amax_in[p2]);
+            else if (k == kKindMut) bound = fmaf(a.sigma, kNormalBound, bound);
+            a.scale_exp_out[j] = fp8_scale_exp(bound);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) select_kernel(SelectArgs a, const float* __restrict__ f_adj,

@@ -21,6 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = range(6)
 TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
 KIND_ELITE, KIND_CROSSOVER, KIND_MUTATION = 0, 1, 2
 EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR = 0, 1, 2
+PRECISION_FP32, PRECISION_BF16, PRECISION_FP8 = 0, 1, 2
 NUM_STAGES = 3
 STAGES = ("select", "breed", "evaluate")  # select = ranking + selection
 
@@ -58,7 +59,7 @@ class Params:
     mut_rate: float = 1.0
     alpha: float = 1.0
     init: int = 0
-    precision: int = 0
+    precision: int = 0  # PRECISION_FP32, PRECISION_BF16 or PRECISION_FP8
     eval_path: int = 0  # EVAL_AUTO, EVAL_SIMT or EVAL_TENSOR
 
     def c_struct(self) -> leea_params:
@@ -91,6 +92,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_breed": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp],
         "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, i32, vp],
         "leea_device_status": [vp, P(u32)],
+        "leea_shadow_stride": ([vp, i32, i32], i64),
+        "leea_make_shadow": [i32, vp, i32, i32, vp, vp, vp, vp, vp],
+        "leea_shadow_scratch_bytes": ([i32, i32], i64),
+        "leea_evaluate_shadow_u8": [i32, vp, i32, vp, i32, vp, vp, vp, f32, vp, i32, f32, vp, vp, vp, vp, vp, i64,
+                                    vp],
+        "leea_get_shadow": [vp, vp, vp, vp],
         "leea_evaluate_u8": [i32, vp, i32, vp, vp, f32, vp, i32, f32, vp, vp, vp, vp, i32, vp],
         "leea_generation_u8": [vp, vp, f32, vp, i32],
         "leea_generation_u8_host": [vp, vp, f32, vp, i32],
@@ -133,7 +140,9 @@ def exported_symbols() -> list[str]:
             "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
             "leea_get_population", "leea_set_population", "leea_set_fitness", "leea_set_generation",
             "leea_get_selection", "leea_generation_index", "leea_state_num_params",
-            "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy"]
+            "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy",
+            "leea_shadow_stride", "leea_make_shadow", "leea_shadow_scratch_bytes", "leea_evaluate_shadow_u8",
+            "leea_get_shadow"]
 
 
 def _check(rc: int) -> None:
@@ -232,6 +241,33 @@ def leea_evaluate_u8(pop: int, dims, pop_dev, x_u8_dev, x_div: float, y_dev, bat
     _check(load_library().leea_evaluate_u8(pop, _hp(d), len(d), _dptr(pop_dev), _dptr(x_u8_dev), float(x_div),
                                            _dptr(y_dev), batch, float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev),
                                            _dptr(f_adj_dev), _dptr(correct_dev), int(eval_path), _stream(stream)))
+
+
+def leea_shadow_stride(dims, precision: int) -> int:
+    d = _dims(dims)
+    return int(load_library().leea_shadow_stride(_hp(d), len(d), int(precision)))
+
+
+def leea_make_shadow(pop: int, dims, precision: int, pop_dev, shadow_dev, scale_exp_dev, amax_dev,
+                     stream=None) -> None:
+    d = _dims(dims)
+    _check(load_library().leea_make_shadow(pop, _hp(d), len(d), int(precision), _dptr(pop_dev), _dptr(shadow_dev),
+                                           _dptr(scale_exp_dev), _dptr(amax_dev), _stream(stream)))
+
+
+def leea_shadow_scratch_bytes(pop: int, batch: int) -> int:
+    return int(load_library().leea_shadow_scratch_bytes(pop, batch))
+
+
+def leea_evaluate_shadow_u8(pop: int, dims, pop_dev, precision: int, shadow_dev, scale_exp_dev, x_u8_dev,
+                            x_div: float, y_dev, batch: int, alpha: float, f_inh_dev, f_raw_dev, f_adj_dev=None,
+                            correct_dev=None, scratch_dev=None, stream=None) -> None:
+    d = _dims(dims)
+    nbytes = 0 if scratch_dev is None else scratch_dev.numel() * scratch_dev.element_size()
+    _check(load_library().leea_evaluate_shadow_u8(
+        pop, _hp(d), len(d), _dptr(pop_dev), int(precision), _dptr(shadow_dev), _dptr(scale_exp_dev),
+        _dptr(x_u8_dev), float(x_div), _dptr(y_dev), batch, float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev),
+        _dptr(f_adj_dev), _dptr(correct_dev), _dptr(scratch_dev), nbytes, _stream(stream)))
 
 
 def leea_device_status(stream=None) -> int:
@@ -337,6 +373,14 @@ class LeeaState:
         f_inh = np.empty(self.pop, dtype=np.float32)
         _check(self.lib.leea_get_selection(self._h, *[_hp(a) for a in ints], _hp(f_inh)))
         return (*ints, f_inh)
+
+    def leea_get_shadow(self, precision: int):
+        """(shadow uint8[pop][stride] in the tiled layout, scale_exp int32[pop], amax float32[pop])."""
+        sh = np.empty((self.pop, leea_shadow_stride(self.dims, precision)), dtype=np.uint8)
+        se = np.empty(self.pop, dtype=np.int32)
+        am = np.empty(self.pop, dtype=np.float32)
+        _check(self.lib.leea_get_shadow(self._h, _hp(sh), _hp(se), _hp(am)))
+        return sh, se, am
 
     @property
     def gen(self) -> int:

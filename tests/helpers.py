@@ -59,3 +59,48 @@ def assert_genes_close(gpu, ref, sigma: float, what="genes"):
     tol = 2.0 ** -23 * np.abs(ref) + 1e-6 * sigma * 8.0 + 1e-30
     bad = np.abs(gpu - ref) > tol
     assert not bad.any(), f"{what}: {bad.sum()} genes outside tolerance, first {np.argwhere(bad)[:3].tolist()}"
+
+
+def decode_bf16(bits) -> np.ndarray:
+    """Values (float64) of BF16 bit patterns (uint16): the upper half of an FP32."""
+    b = np.asarray(bits, dtype=np.uint16).astype(np.uint32) << 16
+    return b.view(np.float32).astype(np.float64)
+
+
+def _e4m3_table() -> np.ndarray:
+    """Value of each of the 256 FP8-e4m3 codes (OCP 8-bit floating point: 1 sign,
+    4 exponent bits with bias 7, 3 mantissa bits; exponent 0 subnormal; S.1111.111
+    NaN; no infinities)."""
+    t = np.empty(256, dtype=np.float64)
+    for b in range(256):
+        s, e, m = b >> 7, (b >> 3) & 15, b & 7
+        if e == 15 and m == 7:
+            v = np.nan
+        elif e == 0:
+            v = m * 2.0 ** -9
+        else:
+            v = (1.0 + m / 8.0) * 2.0 ** (e - 7)
+        t[b] = -v if s else v
+    return t
+
+
+E4M3_TABLE = _e4m3_table()
+
+
+def decode_e4m3(codes) -> np.ndarray:
+    return E4M3_TABLE[np.asarray(codes, dtype=np.uint8)]
+
+
+def untile_shadow(raw, k: int, h: int, elem: int) -> np.ndarray:
+    """Row-major bytes (uint8[pop][h][k elem]) of shadows in the tiled layout:
+    block b holds bytes [128 b, 128 b + 128) of every row, row o at 128 (b h + o),
+    its 16-byte chunk c at chunk position c ^ (o % 8)."""
+    raw = np.asarray(raw, dtype=np.uint8)
+    pop = raw.shape[0]
+    nb = (k * elem + 127) // 128
+    t = raw[:, :nb * h * 128].reshape(pop, nb, h, 8, 16)
+    o = np.arange(h)[:, None]
+    pos = np.arange(8)[None, :] ^ (o % 8)                    # position of chunk c in row o
+    rows = t[:, :, np.arange(h)[:, None], pos, :]            # [pop, nb, h, 8 (c), 16]
+    rows = rows.transpose(0, 2, 1, 3, 4).reshape(pop, h, nb * 128)
+    return np.ascontiguousarray(rows[:, :, :k * elem])

@@ -69,6 +69,7 @@ def test_shadow_evaluation(oracle_mod, precision):
                 q[p, i] = oracle_mod.round_e4m3(popv[p, i] / s) * s
     f_ref, _ = oracle_mod.evaluate(q, dims, x, y)
     np.testing.assert_array_equal(f, f_ref)
+    np.testing.assert_array_equal(oracle_mod.quantize_w1(popv, dims, precision, se), q)
     # The shadow's loss error against the FP64 master is small but not zero.
     f64, _ = oracle_mod.evaluate(popv, dims, x, y)
     err = np.abs(f - f64) / np.abs(f64)
@@ -83,3 +84,18 @@ def test_precision_zero_is_plain_evaluation(oracle_mod):
     x, y = synthetic.make_split(8, seed=5)
     f0, _ = oracle_mod.evaluate_shadow(popv, dims, 0, None, x, y)
     np.testing.assert_array_equal(f0, oracle_mod.evaluate(popv, dims, x, y)[0])
+
+
+def test_test_decoders_match_library():
+    # The tests' BF16 and FP8 decoders against PyTorch's CPU conversions.
+    from helpers import decode_bf16, decode_e4m3
+    codes = np.arange(256, dtype=np.uint8)
+    ref = torch.from_numpy(codes.copy()).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = decode_e4m3(codes)
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    np.testing.assert_array_equal(got[ok], ref[ok])
+    bits = np.random.default_rng(1).integers(0, 2 ** 16, size=5000).astype(np.uint16)
+    bits = bits[(bits & 0x7F80) != 0x7F80]  # finite patterns
+    ref = torch.from_numpy(bits.view(np.int16).copy()).view(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(decode_bf16(bits), ref)
