@@ -268,6 +268,32 @@ leea_status leea_evaluate_shadow_u8(int32_t pop, const int32_t* dims, int32_t n_
                                     float* f_raw_dev, float* f_adj_dev, int32_t* correct_dev,
                                     float* scratch_dev, int64_t scratch_bytes, void* stream);
 
+/* leea_evaluate_shadow_u8 for callers that cannot allocate or hand over
+ * scratch memory -- e.g. a service whose device memory is fully committed to
+ * a pool it does not control, or a loop whose latency budget excludes
+ * allocator calls.  (The paper has no counterpart: this is a deployment
+ * variant of the same evaluation.)  It allocates nothing: the per-tile
+ * partial sums go to one static device array of this library, 1 MiB per
+ * device (LEEA_NOALLOC_SCRATCH_BYTES), which holds batches and populations
+ * with 8 * ceil(batch / 128) * pop <= 1 MiB; larger requests fail with
+ * LEEA_EINVAL before any work is enqueued.  Nothing in that array needs to
+ * start at zero: every slot the combining step reads is written earlier in
+ * the same call.  There is one array per device, so calls whose device work
+ * can overlap (other streams, other host threads, without an ordering
+ * between them) race on it; order them, e.g. on one stream.  The first call
+ * on a device looks up the array's address (with that device current) and
+ * sets the kernel's shared-memory attribute; make it before any stream
+ * capture.  No claim is made about use inside CUDA graph capture.  Other
+ * arguments, requirements and results as in leea_evaluate_shadow_u8. */
+#define LEEA_NOALLOC_SCRATCH_BYTES (1 << 20)
+leea_status leea_evaluate_shadow_u8_noalloc(int32_t pop, const int32_t* dims, int32_t n_dims,
+                                            const float* pop_dev, int32_t precision,
+                                            const uint8_t* shadow_dev, const int32_t* scale_exp_dev,
+                                            const uint8_t* x_u8_dev, float x_div, const int32_t* y_dev,
+                                            int32_t batch, float alpha, const float* f_inh_dev,
+                                            float* f_raw_dev, float* f_adj_dev, int32_t* correct_dev,
+                                            void* stream);
+
 /* Synchronises `stream`, then reads and clears this device's status word.
  * Returns LEEA_ETIMEOUT if a kernel's bounded wait gave up since the last
  * check (its outputs are then invalid), LEEA_OK otherwise.  flags_out, if

@@ -131,6 +131,34 @@ unsigned int* device_status_ptr()
     return cache[dev];
 }
 
+// Scratch of leea_evaluate_shadow_u8_noalloc: the per-tile partial sums of one
+// call (2 floats per individual and 128-sample tile), LEEA_NOALLOC_SCRATCH_BYTES
+// per device.  Callers of that entry point cannot allocate, so the array is
+// static; its contents need no initial value (each call writes every slot it
+// reads) and calls that overlap on the device share it.
+static __device__ __align__(256) float g_noalloc_scratch[LEEA_NOALLOC_SCRATCH_BYTES / sizeof(float)];
+
+// Device address of g_noalloc_scratch on the current device (looked up once
+// per device, with that device current); NULL with the CUDA error in *err.
+float* noalloc_scratch_ptr(cudaError_t* err)
+{
+    static float* cache[64] = { nullptr };
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= 64) {
+        *err = cudaErrorInvalidDevice;
+        return nullptr;
+    }
+    if (!cache[dev]) {
+        float* p = nullptr;
+        *err = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
+        if (*err != cudaSuccess) return nullptr;
+        cache[dev] = p;
+    }
+    return cache[dev];
+}
+
 // Synchronises `stream`, reads and clears the status word.
 leea_status check_device_status(cudaStream_t stream, uint32_t* flags_out)
 {
@@ -492,6 +520,41 @@ leea_status leea_evaluate_shadow_u8(int32_t pop, const int32_t* dims, int32_t n_
         return fail(LEEA_EINVAL, "batch %d needs %lld scratch bytes", batch, static_cast<long long>(need));
     return dispatch_eval_shadow(net, pop, pop_dev, precision, shadow_dev, scale_exp_dev, x_u8_dev, x_div, y_dev,
                                 batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev, correct_dev, scratch_dev,
+                                static_cast<cudaStream_t>(stream));
+}
+
+leea_status leea_evaluate_shadow_u8_noalloc(int32_t pop, const int32_t* dims, int32_t n_dims, const float* pop_dev,
+                                            int32_t precision, const uint8_t* shadow_dev, const int32_t* scale_exp_dev,
+                                            const uint8_t* x_u8_dev, float x_div, const int32_t* y_dev, int32_t batch,
+                                            float alpha, const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
+                                            int32_t* correct_dev, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if ((st = check_shadow_shape(net, precision))) return st;
+    if (batch <= 0) return fail(LEEA_EINVAL, "batch must be >= 1");
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
+    if (!pop_dev || !shadow_dev || !x_u8_dev || !y_dev || !f_raw_dev || (precision == 2 && !scale_exp_dev))
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    if ((reinterpret_cast<uintptr_t>(pop_dev) & 15u) || (reinterpret_cast<uintptr_t>(shadow_dev) & 127u) ||
+        (reinterpret_cast<uintptr_t>(x_u8_dev) & 15u))
+        return fail(LEEA_EINVAL, "population, x (16-byte) and shadow (128-byte) must be aligned");
+    const size_t need = eval_shadow_scratch_bytes(pop, batch);
+    if (need > static_cast<size_t>(LEEA_NOALLOC_SCRATCH_BYTES))
+        return fail(LEEA_EINVAL,
+                    "pop %d with batch %d needs %zu scratch bytes, above the %d bytes the allocation-free entry "
+                    "point holds; use leea_evaluate_shadow_u8 with caller scratch",
+                    pop, batch, need, LEEA_NOALLOC_SCRATCH_BYTES);
+    float* scratch = nullptr;
+    if (need > 0) {
+        cudaError_t err = cudaSuccess;
+        scratch = noalloc_scratch_ptr(&err);
+        if (!scratch) return cuda_fail(err, "static scratch address lookup");
+    }
+    return dispatch_eval_shadow(net, pop, pop_dev, precision, shadow_dev, scale_exp_dev, x_u8_dev, x_div, y_dev,
+                                batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev, correct_dev, scratch,
                                 static_cast<cudaStream_t>(stream));
 }
 

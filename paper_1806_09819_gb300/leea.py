@@ -98,6 +98,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_evaluate_shadow_u8": [i32, vp, i32, vp, i32, vp, vp, vp, f32, vp, i32, f32, vp, vp, vp, vp, vp, i64,
                                     vp],
         "leea_get_shadow": [vp, vp, vp, vp],
+        "leea_evaluate_shadow_u8_noalloc": [i32, vp, i32, vp, i32, vp, vp, vp, f32, vp, i32, f32, vp, vp, vp, vp,
+                                            vp],
         "leea_evaluate_u8": [i32, vp, i32, vp, vp, f32, vp, i32, f32, vp, vp, vp, vp, i32, vp],
         "leea_generation_u8": [vp, vp, f32, vp, i32],
         "leea_generation_u8_host": [vp, vp, f32, vp, i32],
@@ -142,7 +144,7 @@ def exported_symbols() -> list[str]:
             "leea_get_selection", "leea_generation_index", "leea_state_num_params",
             "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy",
             "leea_shadow_stride", "leea_make_shadow", "leea_shadow_scratch_bytes", "leea_evaluate_shadow_u8",
-            "leea_get_shadow"]
+            "leea_get_shadow", "leea_evaluate_shadow_u8_noalloc"]
 
 
 def _check(rc: int) -> None:
@@ -268,6 +270,20 @@ def leea_evaluate_shadow_u8(pop: int, dims, pop_dev, precision: int, shadow_dev,
         pop, _hp(d), len(d), _dptr(pop_dev), int(precision), _dptr(shadow_dev), _dptr(scale_exp_dev),
         _dptr(x_u8_dev), float(x_div), _dptr(y_dev), batch, float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev),
         _dptr(f_adj_dev), _dptr(correct_dev), _dptr(scratch_dev), nbytes, _stream(stream)))
+
+
+NOALLOC_SCRATCH_BYTES = 1 << 20
+
+
+def leea_evaluate_shadow_u8_noalloc(pop: int, dims, pop_dev, precision: int, shadow_dev, scale_exp_dev, x_u8_dev,
+                                    x_div: float, y_dev, batch: int, alpha: float, f_inh_dev, f_raw_dev,
+                                    f_adj_dev=None, correct_dev=None, stream=None) -> None:
+    """leea_evaluate_shadow_u8 with the library's static scratch (allocates nothing)."""
+    d = _dims(dims)
+    _check(load_library().leea_evaluate_shadow_u8_noalloc(
+        pop, _hp(d), len(d), _dptr(pop_dev), int(precision), _dptr(shadow_dev), _dptr(scale_exp_dev),
+        _dptr(x_u8_dev), float(x_div), _dptr(y_dev), batch, float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev),
+        _dptr(f_adj_dev), _dptr(correct_dev), _stream(stream)))
 
 
 def leea_device_status(stream=None) -> int:
