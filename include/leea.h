@@ -128,8 +128,9 @@ enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2 };
  * the two FP8 pieces 16 floor(k / 16) and k mod 16), scales by 2^e_p / x_div,
  * and computes b1, ReLU, layer 2 and the loss from the FP32 master in FP32.
  * Requirements: n_dims == 3, d_0 % 16 == 0, h % 16 == 0, h <= 256,
- * d_out <= 16 and h + A <= 512 with A = round_up(8 ceil(d_0 / 16), 16) for
- * BF16 and round_up(16 ceil(d_0 / 32), 16) for FP8 (d_0 = 784: h <= 112).
+ * d_out <= 16 and A <= 496 with A = round_up(8 ceil(d_0 / 16), 16) for BF16
+ * and round_up(16 ceil(d_0 / 32), 16) for FP8 (the batch tile's tensor-memory
+ * columns; the hidden units are processed in chunks of at most 512 - A).
  * The state object then accepts only the 8-bit generation calls. */
 enum { LEEA_PRECISION_FP32 = 0, LEEA_PRECISION_BF16 = 1, LEEA_PRECISION_FP8 = 2 };
 

@@ -252,7 +252,7 @@ leea_status check_shadow_shape(const NetLayout& net, int32_t precision)
     if (precision != 1 && precision != 2) return fail(LEEA_EINVAL, "precision must be 1 (BF16) or 2 (FP8)");
     if (!eval_shadow_supported(net, precision, 1))
         return fail(LEEA_EINVAL, "the precision form needs n_dims == 3, d_0 %% 16 == 0, h %% 16 == 0, h <= 256, "
-                                 "d_out <= 16 and h plus the batch tile's TMEM columns <= 512 (d_0 = 784: h <= 112)");
+                                 "d_out <= 16 and at most 496 TMEM columns for the batch tile");
     return LEEA_OK;
 }
 

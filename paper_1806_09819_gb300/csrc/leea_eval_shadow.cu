@@ -4,26 +4,36 @@
 // of the net (b1, W2, b2) and the softmax cross-entropy use the FP32 master.
 //
 // Inputs are 8-bit levels x = k / x_div.  The A operand (a tile of 128
-// samples) is written once per CTA into tensor memory: for BF16 shadows the
-// levels themselves (exact), for FP8 shadows two exact pieces 16 floor(k/16)
-// and k mod 16 accumulated by two MMAs.  The B operand, the shadow of W1, is
+// samples) is written into tensor memory: for BF16 shadows the levels
+// themselves (exact), for FP8 shadows two exact pieces 16 floor(k/16) and
+// k mod 16 accumulated by two MMAs.  The B operand, the shadow of W1, is
 // stored pre-tiled and pre-swizzled (shadow_offset), so each pipeline stage is
-// one contiguous bulk copy of h x 128 bytes straight into the layout the
-// tensor core reads.  FP8 products are scaled by the child's power-of-two
-// factor 2^scale_exp in the epilogue.
+// one contiguous bulk copy of (hidden rows) x 128 bytes straight into the
+// layout the tensor core reads.  FP8 products are scaled by the child's
+// power-of-two factor 2^scale_exp in the epilogue.
 //
-// A batch above 128 samples is split over groups of CTAs, one 128-sample tile
-// per group (each keeps its tile resident in TMEM); the groups write partial
-// loss sums to scratch memory and a second kernel combines them in tile order.
+// The hidden units are processed in chunks of at most 128 (the accumulator
+// shares the 512 TMEM columns with the batch tile); the epilogue keeps each
+// sample's partial logits in registers across an individual's chunks.  A
+// batch above 128 samples is split into 128-sample tiles handled by
+// different CTAs, whose partial loss sums go to scratch memory and are
+// combined in tile order by a second kernel.
+//
+// One kernel serves a single run (the work split arithmetically over the
+// grid) and many independent runs at once (the batching form): then each
+// CTA walks its own list of segments -- (run, sample tile, range of
+// individuals) -- from a device table, reloading the batch tile into TMEM
+// when the run or the tile changes.
 //
 // Warp roles (persistent CTAs, one per SM):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
-//   warp 1      copy producer: the batch tile (once), then per individual its
-//               b1, W2, b2 and the shadow blocks, by bulk copy
-//   warps 2-17  batch tile into TMEM once; then the epilogue, four warps per
-//               TMEM lane quarter, each taking a quarter of the hidden units.
-//               The accumulator goes to registers at once (h <= 128) so that
-//               the next individual's MMAs overlap the epilogue's arithmetic.
+//   warp 1      copy producer: per individual its b1, W2, b2, then per hidden
+//               chunk the shadow blocks, by bulk copy
+//   warps 2-17  batch tile into TMEM (per segment that needs it); then the
+//               epilogue, four warps per TMEM lane quarter, each taking a
+//               quarter of a chunk's hidden units.  The accumulator goes to
+//               registers at once so that the next chunk's MMAs overlap the
+//               epilogue's arithmetic.
 // Every mbarrier wait is bounded in time (kStatusEvalTimeout on expiry).
 #include <cuda.h>
 #include <cuda_fp8.h>
@@ -41,36 +51,27 @@ constexpr int kShEpiThreads = 32 * kShEpiWarps;
 constexpr int kShThreads = 32 * (2 + kShEpiWarps);
 constexpr int kFirstEpiWarp = 2;
 constexpr int kShMaxOut = 16;
-constexpr int kShStages = 8;
-constexpr int kShRegCols = 32;  // accumulator columns a thread holds in registers (h <= 128)
+constexpr int kShMaxChunk = 128;   // hidden units per chunk at most
+constexpr int kShRegCols = kShMaxChunk / kShSlots;  // accumulator columns a thread holds
 constexpr uint32_t kShTmemCols = 512;
 constexpr uint64_t kShWaitNs = 2000000000ull;
 constexpr uint64_t kShDrainNs = 200000000ull;
 
 struct EvalShArgs {
-    int32_t pop, k, h, d_out, dpad, batch, precision, k_elems_stage, k_stages, k_mma, m_tiles, stages;
-    int64_t c_pad, sh_stride;
-    float inv_div, alpha;
-    uint32_t a_col, a_piece_cols, a_total_cols, prm_bytes, ring_bytes;
-    const float* popv;
-    const uint8_t* shadow;
-    const uint8_t* x;
-    const int32_t* y;
-    const float* f_inh;
-    const int32_t* scale_exp;
-    float* f_raw;
-    float* f_adj;
-    int32_t* correct;
-    float* scratch;  // m_tiles > 1: [m_tiles][pop] loss sums, then [m_tiles][pop] correct counts
+    int32_t k, d_out, dpad, k_elems_stage, k_stages, k_mma, stages;
+    uint32_t a_col, a_piece_cols, a_total_cols, prm_bytes_max, stage_bytes;
+    const ShadowRun* runs;   // many runs: device table; NULL: the single run run0
+    const ShadowSeg* segs;   // many runs: CTA b walks segs[seg_off[b] .. seg_off[b+1])
+    const int32_t* seg_off;
+    ShadowRun run0;
     unsigned int* status;
 };
 
 struct ShSmem {
-    uint8_t* ring;  // also holds the batch tile before the first stage
-    uint32_t stage_bytes;
+    uint8_t* ring;
     uint8_t* prm_raw;
     float *w2t, *b2, *part;
-    uint64_t *full, *empty, *prm_full, *prm_empty, *acc_full, *acc_empty, *a_ready, *drain, *x_full;
+    uint64_t *full, *empty, *prm_full, *prm_empty, *acc_full, *acc_empty, *a_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
@@ -78,33 +79,26 @@ struct ShSmem {
     int32_t* red_ok;
 };
 
-uint32_t sh_prm_bytes(int32_t h, int32_t d_out)
+__host__ __device__ inline uint32_t sh_prm_bytes(int32_t h, int32_t d_out)
 {
     return (static_cast<uint32_t>(h + d_out * h + d_out) * 4u + 15u) & ~15u;
 }
 
-uint32_t sh_ring_bytes(int32_t h, int32_t k, int32_t stages)
+size_t sh_smem_bytes(int32_t h_max, int32_t cw_max, int32_t dpad, int32_t stages)
 {
-    const uint32_t ring = static_cast<uint32_t>(stages) * h * 128u, xtile = 128u * static_cast<uint32_t>(k);
-    return ring > xtile ? ring : xtile;
+    return 1024 + static_cast<size_t>(stages) * cw_max * 128 + 2 * sh_prm_bytes(h_max, dpad) +
+           sizeof(float) * (h_max * dpad + 16 + (kShSlots - 1) * 128 * kShMaxOut) + 8 * (2 * stages + 8) + 64;
 }
 
-size_t sh_smem_bytes(int32_t h, int32_t k, int32_t dpad, int32_t stages)
-{
-    return 1024 + sh_ring_bytes(h, k, stages) + 2 * sh_prm_bytes(h, dpad) +
-           sizeof(float) * (h * dpad + 16 + (kShSlots - 1) * 128 * kShMaxOut) + 8 * (2 * stages + 9) + 64;
-}
-
-__device__ __forceinline__ ShSmem carve(uint8_t* raw, const EvalShArgs& a)
+__device__ __forceinline__ ShSmem carve(uint8_t* raw, const EvalShArgs& a, int32_t h_max)
 {
     ShSmem s;
     s.ring = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
-    s.stage_bytes = static_cast<uint32_t>(a.h) * 128u;
-    uint8_t* p = s.ring + a.ring_bytes;
+    uint8_t* p = s.ring + a.stages * a.stage_bytes;
     s.prm_raw = p;
-    p += 2u * a.prm_bytes;
+    p += 2u * a.prm_bytes_max;
     s.w2t = reinterpret_cast<float*>(p);
-    p += sizeof(float) * a.h * a.dpad;
+    p += sizeof(float) * h_max * a.dpad;
     s.b2 = reinterpret_cast<float*>(p);
     p += sizeof(float) * 16;
     s.part = reinterpret_cast<float*>(p);  // [slot 1..3][128][kShMaxOut] partial logits
@@ -118,8 +112,7 @@ __device__ __forceinline__ ShSmem carve(uint8_t* raw, const EvalShArgs& a)
     s.acc_empty = s.acc_full + 1;
     s.a_ready = s.acc_full + 2;
     s.drain = s.acc_full + 3;
-    s.x_full = s.acc_full + 4;
-    uint32_t* w = reinterpret_cast<uint32_t*>(s.acc_full + 5);
+    uint32_t* w = reinterpret_cast<uint32_t*>(s.acc_full + 4);
     s.tmem_holder = w;
     s.abort_flag = reinterpret_cast<volatile int*>(w + 1);
     s.ep_go = reinterpret_cast<int*>(w + 2);
@@ -151,17 +144,108 @@ __device__ __forceinline__ uint32_t e4m3_bits(float v)
     return static_cast<uint32_t>(__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3));
 }
 
+__device__ __forceinline__ const ShadowRun& run_of(const EvalShArgs& a, int32_t r)
+{
+    return a.runs ? a.runs[r] : a.run0;
+}
+
+__device__ __forceinline__ int32_t seg_count(const EvalShArgs& a)
+{
+    return a.runs ? a.seg_off[blockIdx.x + 1] - a.seg_off[blockIdx.x] : 1;
+}
+
+// Segment i of this CTA.  A single run splits its m_tiles x pop work over the
+// grid: CTA b takes tile b % m_tiles and a contiguous share of the individuals.
+__device__ __forceinline__ ShadowSeg seg_at(const EvalShArgs& a, int32_t i)
+{
+    if (a.runs) return a.segs[a.seg_off[blockIdx.x] + i];
+    const int32_t mt = blockIdx.x % a.run0.m_tiles, g = blockIdx.x / a.run0.m_tiles;
+    const int32_t groups = gridDim.x / a.run0.m_tiles;
+    const int64_t pop = a.run0.pop;
+    return ShadowSeg{ 0, mt, static_cast<int32_t>(pop * g / groups), static_cast<int32_t>(pop * (g + 1) / groups) };
+}
+
+// Whether segment i needs a batch tile other than the one in TMEM: the first
+// non-empty segment, or one whose run or tile differs from the last non-empty one.
+__device__ __forceinline__ bool new_tile(const EvalShArgs& a, int32_t i, const ShadowSeg& sg)
+{
+    for (int32_t j = i - 1; j >= 0; --j) {
+        const ShadowSeg prev = seg_at(a, j);
+        if (prev.p0 < prev.p1) return prev.run != sg.run || prev.mt != sg.mt;
+    }
+    return true;
+}
+
+__device__ __forceinline__ int32_t chunk_width(const ShadowRun& r, int32_t c)
+{
+    const int32_t r0 = c * r.cw;
+    return r.h - r0 < r.cw ? r.h - r0 : r.cw;
+}
+
+// Writes this thread's share of the batch tile (TMEM lane `row`) into the A
+// region: 16-column groups [c16_0, c16_1), levels read from global memory 16
+// bytes at a time.
+template <int PREC>
+__device__ __forceinline__ void fill_tile(const EvalShArgs& a, const ShadowRun& r, int32_t mt, int row,
+                                          uint32_t c16_0, uint32_t c16_1, uint32_t taddr)
+{
+    const int32_t srow = mt * 128 + row;
+    const bool live = srow < r.batch;
+    const uint4* xrow = reinterpret_cast<const uint4*>(r.x + static_cast<int64_t>(live ? srow : 0) * a.k);
+    const uint32_t kw = static_cast<uint32_t>(a.k) / 4;  // 32-bit words of levels in a row
+    for (uint32_t c16 = c16_0; c16 < c16_1; ++c16) {
+        const uint32_t c0 = 16 * c16;
+        uint32_t cols[16];
+        if (PREC == 1) {
+            // columns c0 .. c0+15 hold levels 2 c0 .. 2 c0 + 31: words c0/2 .. c0/2 + 7
+            const uint32_t w0 = c0 >> 1;
+            uint4 q[2];
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+                q[t] = (live && w0 + 4 * t < kw) ? __ldg(xrow + (w0 >> 2) + t) : make_uint4(0u, 0u, 0u, 0u);
+            const uint32_t wd[8] = { q[0].x, q[0].y, q[0].z, q[0].w, q[1].x, q[1].y, q[1].z, q[1].w };
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t pr = wd[i >> 1] >> (16 * (i & 1));
+                cols[i] = (__float_as_uint(static_cast<float>(pr & 0xFFu)) >> 16) |
+                          (__float_as_uint(static_cast<float>((pr >> 8) & 0xFFu)) & 0xFFFF0000u);
+            }
+        } else {
+            // column c: piece (c >= piece_cols), levels of word c - piece * piece_cols;
+            // groups of 4 columns never straddle a piece boundary (piece_cols % 8 == 0).
+#pragma unroll
+            for (int g4 = 0; g4 < 4; ++g4) {
+                const uint32_t c = c0 + 4 * g4;
+                const bool valid = c < 2u * a.a_piece_cols;
+                const uint32_t piece = c >= a.a_piece_cols ? 1u : 0u;
+                const uint32_t wi = c - piece * a.a_piece_cols;
+                const uint4 q = (live && valid && wi < kw) ? __ldg(xrow + (wi >> 2)) : make_uint4(0u, 0u, 0u, 0u);
+                const uint32_t wd[4] = { q.x, q.y, q.z, q.w };
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t lv = (wd[t] >> (8 * b)) & 0xFFu;
+                        const float pv = piece == 0 ? static_cast<float>(lv & 0xF0u) : static_cast<float>(lv & 15u);
+                        word |= e4m3_bits(pv) << (8 * b);
+                    }
+                    cols[4 * g4 + t] = word;
+                }
+            }
+        }
+        ptx::tmem_st16(taddr + c0, cols);
+    }
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kShThreads, 1)
-eval_shadow_kernel(const EvalShArgs a)
+eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
 {
     extern __shared__ uint8_t smem_raw[];
-    const ShSmem s = carve(smem_raw, a);
+    const ShSmem s = carve(smem_raw, a, h_max);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = blockIdx.x % a.m_tiles;  // this CTA's 128-sample tile
-    const int g = blockIdx.x / a.m_tiles;   // individuals g, g + groups, ...
-    const int groups = gridDim.x / a.m_tiles;
-    const int tile_rows = min(128, a.batch - mt * 128);
+    const int32_t nseg = seg_count(a);
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < a.stages; ++i) {
@@ -176,7 +260,6 @@ eval_shadow_kernel(const EvalShArgs a)
         ptx::mbar_init(s.acc_empty, kShEpiThreads);
         ptx::mbar_init(s.a_ready, kShEpiThreads);
         ptx::mbar_init(s.drain, 1);
-        ptx::mbar_init(s.x_full, 1);
         *s.abort_flag = 0;
         *s.ep_go = 0;
         ptx::fence_mbar_init();
@@ -190,55 +273,69 @@ eval_shadow_kernel(const EvalShArgs a)
     if (warp == 0) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = PREC == 1 ? ptx::idesc_bf16(128, static_cast<uint32_t>(a.h))
-                                             : ptx::idesc_e4m3(128, static_cast<uint32_t>(a.h));
-            bool ok = ptx::mbar_wait_bounded(s.a_ready, 0u, s.abort_flag, kShWaitNs);
-            if (!ok) raise_abort(s, a);
-            ptx::tc_fence_after();
-            uint32_t stage = 0, phase = 0, acc_phase = 0;
+            bool ok = true;
+            uint32_t stage = 0, phase = 0, acc_phase = 0, tiles = 0;
             const uint32_t ring = ptx::smem_u32(s.ring);
-            for (int p = g; ok && p < a.pop; p += groups) {
-                if (!ptx::mbar_wait_bounded(s.acc_empty, acc_phase ^ 1u, s.abort_flag, kShWaitNs)) {
-                    raise_abort(s, a);
-                    ok = false;
-                    break;
-                }
-                ptx::tc_fence_after();
-                bool first = true;
-                for (int kc = 0; kc < a.k_stages; ++kc) {
-                    // The stage was filled by the copy engine (async proxy, like the
-                    // MMA's operand reads): the mbarrier completion orders it.
-                    if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kShWaitNs)) {
+            for (int32_t si = 0; ok && si < nseg; ++si) {
+                const ShadowSeg sg = seg_at(a, si);
+                const ShadowRun& r = run_of(a, sg.run);
+                if (sg.p0 >= sg.p1) continue;
+                if (new_tile(a, si, sg)) {  // the epilogue wrote this segment's batch tile
+                    if (!ptx::mbar_wait_bounded(s.a_ready, tiles & 1u, s.abort_flag, kShWaitNs)) {
                         raise_abort(s, a);
                         ok = false;
                         break;
                     }
-                    const uint32_t sb = ring + stage * s.stage_bytes;
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {  // 4 MMA K-steps of 32 bytes per 128-byte row
-                        const int kg = kc * a.k_elems_stage + kk * (a.k_elems_stage / 4);
-                        if (kg >= a.k_mma) break;
-                        const uint64_t bd = ptx::smem_desc_sw128(sb + kk * 32u);
-                        if (PREC == 1) {
-                            ptx::mma_f16_tmem_a(tmem_base, tmem_base + a.a_col + static_cast<uint32_t>(kg >> 1), bd,
-                                                idesc, first ? 0u : 1u);
-                            first = false;
-                        } else {
-#pragma unroll
-                            for (int piece = 0; piece < 2; ++piece) {
-                                const uint32_t at = tmem_base + a.a_col + piece * a.a_piece_cols +
-                                                    static_cast<uint32_t>(kg >> 2);
-                                ptx::mma_f8_tmem_a(tmem_base, at, bd, idesc, first ? 0u : 1u);
-                                first = false;
-                            }
-                        }
-                    }
-                    ptx::mma_commit(&s.empty[stage]);
-                    if (++stage == static_cast<uint32_t>(a.stages)) { stage = 0; phase ^= 1u; }
+                    ++tiles;
+                    ptx::tc_fence_after();
                 }
-                if (!ok) break;
-                ptx::mma_commit(s.acc_full);
-                acc_phase ^= 1u;
+                for (int32_t p = sg.p0; ok && p < sg.p1; ++p) {
+                    for (int32_t c = 0; ok && c < r.n_chunks; ++c) {
+                        const uint32_t width = static_cast<uint32_t>(chunk_width(r, c));
+                        const uint32_t idesc = PREC == 1 ? ptx::idesc_bf16(128, width) : ptx::idesc_e4m3(128, width);
+                        if (!ptx::mbar_wait_bounded(s.acc_empty, acc_phase ^ 1u, s.abort_flag, kShWaitNs)) {
+                            raise_abort(s, a);
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        bool first = true;
+                        for (int kc = 0; kc < a.k_stages; ++kc) {
+                            // Stages are filled by the copy engine (async proxy, like the
+                            // MMA's operand reads): the mbarrier completion orders them.
+                            if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kShWaitNs)) {
+                                raise_abort(s, a);
+                                ok = false;
+                                break;
+                            }
+                            const uint32_t sb = ring + stage * a.stage_bytes;
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {  // 4 MMA K-steps of 32 bytes per 128-byte row
+                                const int kg = kc * a.k_elems_stage + kk * (a.k_elems_stage / 4);
+                                if (kg >= a.k_mma) break;
+                                const uint64_t bd = ptx::smem_desc_sw128(sb + kk * 32u);
+                                if (PREC == 1) {
+                                    ptx::mma_f16_tmem_a(tmem_base, tmem_base + a.a_col + static_cast<uint32_t>(kg >> 1),
+                                                        bd, idesc, first ? 0u : 1u);
+                                    first = false;
+                                } else {
+#pragma unroll
+                                    for (int piece = 0; piece < 2; ++piece) {
+                                        const uint32_t at = tmem_base + a.a_col + piece * a.a_piece_cols +
+                                                            static_cast<uint32_t>(kg >> 2);
+                                        ptx::mma_f8_tmem_a(tmem_base, at, bd, idesc, first ? 0u : 1u);
+                                        first = false;
+                                    }
+                                }
+                            }
+                            ptx::mma_commit(&s.empty[stage]);
+                            if (++stage == static_cast<uint32_t>(a.stages)) { stage = 0; phase ^= 1u; }
+                        }
+                        if (!ok) break;
+                        ptx::mma_commit(s.acc_full);
+                        acc_phase ^= 1u;
+                    }
+                }
             }
             ptx::mma_commit(s.drain);
             volatile int never = 0;
@@ -249,47 +346,47 @@ eval_shadow_kernel(const EvalShArgs a)
         if (lane == 0) {
             uint32_t stage = 0, phase = 0, issued_mask = 0, parity_mask = 0, prm_issued = 0;
             bool ok = true;
-            // The batch tile (rows mt*128 .. +tile_rows, d_0 bytes each) into the ring.
-            const uint32_t x_bytes = static_cast<uint32_t>(tile_rows) * static_cast<uint32_t>(a.k);
-            ptx::mbar_arrive_expect_tx(s.x_full, x_bytes);
-            ptx::bulk_load(s.ring, a.x + static_cast<int64_t>(mt) * 128 * a.k, x_bytes, s.x_full);
-            // The ring is free again once the tile sits in TMEM.
-            if (!ptx::mbar_wait_bounded(s.a_ready, 0u, s.abort_flag, kShWaitNs)) {
-                raise_abort(s, a);
-                ok = false;
-            }
-            for (int p = g; ok && p < a.pop; p += groups) {
-                {
-                    const uint32_t pb = prm_issued & 1u, pphase = (prm_issued >> 1) & 1u;
-                    if (!ptx::mbar_wait_bounded(&s.prm_empty[pb], pphase ^ 1u, s.abort_flag, kShWaitNs)) {
-                        raise_abort(s, a);
-                        ok = false;
-                        break;
+            for (int32_t si = 0; ok && si < nseg; ++si) {
+                const ShadowSeg sg = seg_at(a, si);
+                const ShadowRun& r = run_of(a, sg.run);
+                const uint32_t prm_bytes = sh_prm_bytes(r.h, a.d_out);
+                for (int32_t p = sg.p0; ok && p < sg.p1; ++p) {
+                    {
+                        const uint32_t pb = prm_issued & 1u, pphase = (prm_issued >> 1) & 1u;
+                        if (!ptx::mbar_wait_bounded(&s.prm_empty[pb], pphase ^ 1u, s.abort_flag, kShWaitNs)) {
+                            raise_abort(s, a);
+                            ok = false;
+                            break;
+                        }
+                        ptx::mbar_arrive_expect_tx(&s.prm_full[pb], prm_bytes);
+                        ptx::bulk_load(s.prm_raw + pb * a.prm_bytes_max,
+                                       r.popv + static_cast<int64_t>(p) * r.c_pad + static_cast<int64_t>(r.h) * a.k,
+                                       prm_bytes, &s.prm_full[pb]);
+                        ++prm_issued;
                     }
-                    ptx::mbar_arrive_expect_tx(&s.prm_full[pb], a.prm_bytes);
-                    ptx::bulk_load(s.prm_raw + pb * a.prm_bytes,
-                                   a.popv + static_cast<int64_t>(p) * a.c_pad + static_cast<int64_t>(a.h) * a.k,
-                                   a.prm_bytes, &s.prm_full[pb]);
-                    ++prm_issued;
-                }
-                const uint8_t* src = a.shadow + static_cast<int64_t>(p) * a.sh_stride;
-                for (int kc = 0; kc < a.k_stages; ++kc) {
-                    if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kShWaitNs)) {
-                        raise_abort(s, a);
-                        ok = false;
-                        break;
+                    const uint8_t* src = r.shadow + static_cast<int64_t>(p) * r.sh_stride;
+                    for (int32_t c = 0; ok && c < r.n_chunks; ++c) {
+                        const uint32_t bytes = static_cast<uint32_t>(chunk_width(r, c)) * 128u;
+                        for (int kc = 0; kc < a.k_stages; ++kc) {
+                            if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kShWaitNs)) {
+                                raise_abort(s, a);
+                                ok = false;
+                                break;
+                            }
+                            // rows [c cw, c cw + width) of block kc: contiguous in the tiled layout
+                            ptx::mbar_arrive_expect_tx(&s.full[stage], bytes);
+                            ptx::bulk_load(s.ring + stage * a.stage_bytes,
+                                           src + (static_cast<int64_t>(kc) * r.h + static_cast<int64_t>(c) * r.cw) * 128,
+                                           bytes, &s.full[stage]);
+                            issued_mask |= 1u << stage;
+                            parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
+                            if (++stage == static_cast<uint32_t>(a.stages)) { stage = 0; phase ^= 1u; }
+                        }
                     }
-                    ptx::mbar_arrive_expect_tx(&s.full[stage], s.stage_bytes);
-                    ptx::bulk_load(s.ring + stage * s.stage_bytes, src + static_cast<int64_t>(kc) * s.stage_bytes,
-                                   s.stage_bytes, &s.full[stage]);
-                    issued_mask |= 1u << stage;
-                    parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
-                    if (++stage == static_cast<uint32_t>(a.stages)) { stage = 0; phase ^= 1u; }
                 }
             }
             if (!ok) {  // let copies in flight land before the CTA exits
                 volatile int never = 0;
-                ptx::mbar_wait_bounded(s.x_full, 0u, &never, kShDrainNs);
                 for (int i = 0; i < a.stages; ++i)
                     if (issued_mask & (1u << i))
                         ptx::mbar_wait_bounded(&s.full[i], (parity_mask >> i) & 1u, &never, kShDrainNs);
@@ -298,203 +395,169 @@ eval_shadow_kernel(const EvalShArgs a)
             }
         }
     } else {
-        // ------------------------------------------------------------ batch tile into TMEM, then epilogue
+        // ------------------------------------------------------------ batch tiles into TMEM, epilogue
         const int et = threadIdx.x - 32 * kFirstEpiWarp;  // 0 .. kShEpiThreads-1
         const int q = warp & 3;                           // TMEM lane quarter
-        const int slot = (warp - kFirstEpiWarp) >> 2;     // which quarter of the columns
+        const int slot = (warp - kFirstEpiWarp) >> 2;     // which quarter of a chunk's columns
         const int row = q * 32 + lane;
-        const int srow = mt * 128 + row;  // sample held by this TMEM lane
         const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
-        bool ok = ptx::mbar_wait_bounded(s.x_full, 0u, s.abort_flag, kShWaitNs);
-        if (!ok) raise_abort(s, a);
-        {
-            // Levels 4i .. 4i+3 of this row from the staged tile (zero outside).
-            const uint32_t* xrow = reinterpret_cast<const uint32_t*>(s.ring + static_cast<size_t>(row) * a.k);
-            const bool live = ok && row < tile_rows;
-            const uint32_t n16 = a.a_total_cols / 16, c16_0 = n16 * slot / kShSlots,
-                           c16_1 = n16 * (slot + 1) / kShSlots;
-            for (uint32_t c16 = c16_0; c16 < c16_1; ++c16) {
-                const uint32_t c0 = 16 * c16;
-                uint32_t cols[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const uint32_t c = c0 + i;
-                    uint32_t word = 0;
-                    if (PREC == 1) {  // levels 2c, 2c+1 as BF16 (exact)
-                        const uint32_t wi = c >> 1;
-                        const uint32_t lw = (live && 4 * wi < static_cast<uint32_t>(a.k)) ? xrow[wi] : 0u;
-                        const uint32_t pr = lw >> (16 * (c & 1u));
-                        word = (__float_as_uint(static_cast<float>(pr & 0xFFu)) >> 16) |
-                               (__float_as_uint(static_cast<float>((pr >> 8) & 0xFFu)) & 0xFFFF0000u);
-                    } else if (c < 2u * a.a_piece_cols) {  // piece 0: 16 floor(k/16); piece 1: k mod 16
-                        const uint32_t piece = c >= a.a_piece_cols ? 1u : 0u;
-                        const uint32_t wi = c - piece * a.a_piece_cols;
-                        const uint32_t lw = (live && 4 * wi < static_cast<uint32_t>(a.k)) ? xrow[wi] : 0u;
+        const uint32_t n16 = a.a_total_cols / 16;
+        bool ok = true;
+        uint32_t acc_phase = 0, unit = 0;
+        for (int32_t si = 0; ok && si < nseg; ++si) {
+            const ShadowSeg sg = seg_at(a, si);
+            const ShadowRun& r = run_of(a, sg.run);
+            if (sg.p0 >= sg.p1) continue;
+            if (new_tile(a, si, sg)) {
+                // Every MMA that read the previous tile has completed: its last
+                // accumulator was handed over before this point.
+                fill_tile<PREC>(a, r, sg.mt, row, n16 * slot / kShSlots, n16 * (slot + 1) / kShSlots,
+                                tmem_base + lane_addr + a.a_col);
+                ptx::tmem_st_wait();
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(s.a_ready);
+            }
+            const int32_t srow = sg.mt * 128 + row;  // sample held by this TMEM lane
+            const int32_t label = srow < r.batch ? r.y[srow] : 0;
+            for (int32_t p = sg.p0; ok && p < sg.p1; ++p, ++unit) {
+                const uint32_t pb = unit & 1u, pphase = (unit >> 1) & 1u;
+                if (et == 0) {
+                    const bool got = ptx::mbar_wait_bounded(&s.prm_full[pb], pphase, s.abort_flag, kShWaitNs);
+                    if (!got) raise_abort(s, a);
+                    *s.ep_go = got ? 1 : 0;
+                }
+                ptx::named_barrier_sync(1, kShEpiThreads);  // A1: parameters landed (or abort)
+                if (!*s.ep_go) { ok = false; break; }
+                // b1 is read in place; W2 (d_out rows of h) is staged transposed,
+                // one hidden unit (column) per thread.
+                const float* src = reinterpret_cast<const float*>(s.prm_raw + pb * a.prm_bytes_max);
+                const float* b1 = src;
+                for (int col = et; col < r.h; col += kShEpiThreads) {
+                    float4* dst = reinterpret_cast<float4*>(s.w2t + col * a.dpad);
+                    for (int o4 = 0; o4 < a.dpad / 4; ++o4) {
+                        float v[4];
 #pragma unroll
                         for (int t = 0; t < 4; ++t) {
-                            const uint32_t lv = (lw >> (8 * t)) & 0xFFu;
-                            const float pv = piece == 0 ? static_cast<float>(lv & 0xF0u) : static_cast<float>(lv & 15u);
-                            word |= e4m3_bits(pv) << (8 * t);
+                            const int o = 4 * o4 + t;
+                            v[t] = o < a.d_out ? src[r.h + o * r.h + col] : 0.0f;
+                        }
+                        dst[o4] = make_float4(v[0], v[1], v[2], v[3]);
+                    }
+                }
+                if (et < 16) s.b2[et] = et < a.d_out ? src[r.h + a.d_out * r.h + et] : 0.0f;
+
+                // D * (w_scale / x_div): the FP8 shadow stores w / 2^e.
+                const float scale = PREC == 2 ? ldexpf(r.inv_div, r.scale_exp[p]) : r.inv_div;
+                float logit[kShMaxOut];
+#pragma unroll
+                for (int o = 0; o < kShMaxOut; ++o) logit[o] = 0.0f;
+                // hidden unit col: ReLU(D * scale + b1), then its layer-2 contributions
+                auto hidden = [&](int col, float d) {
+                    const float hv = fmaxf(fmaf(d, scale, b1[col]), 0.0f);
+                    const float4* wr = reinterpret_cast<const float4*>(s.w2t + col * a.dpad);
+#pragma unroll
+                    for (int o4 = 0; o4 < kShMaxOut / 4; ++o4) {
+                        if (4 * o4 < a.d_out) {
+                            const float4 w = wr[o4];
+                            logit[4 * o4 + 0] = fmaf(w.x, hv, logit[4 * o4 + 0]);
+                            logit[4 * o4 + 1] = fmaf(w.y, hv, logit[4 * o4 + 1]);
+                            logit[4 * o4 + 2] = fmaf(w.z, hv, logit[4 * o4 + 2]);
+                            logit[4 * o4 + 3] = fmaf(w.w, hv, logit[4 * o4 + 3]);
                         }
                     }
-                    cols[i] = word;
-                }
-                ptx::tmem_st16(tmem_base + lane_addr + a.a_col + c0, cols);
-            }
-        }
-        ptx::tmem_st_wait();
-        ptx::tc_fence_before();
-        ptx::mbar_arrive(s.a_ready);
-
-        const int32_t label = srow < a.batch ? a.y[srow] : 0;
-        // This thread's accumulator columns: 8-column chunks [j0, j1) of the h / 8.
-        const int n8 = a.h / 8, j0 = n8 * slot / kShSlots, j1 = n8 * (slot + 1) / kShSlots;
-        uint32_t acc_phase = 0, unit = 0;
-        for (int p = g; ok && p < a.pop; p += groups, ++unit) {
-            const uint32_t pb = unit & 1u, pphase = (unit >> 1) & 1u;
-            if (et == 0) {
-                const bool got = ptx::mbar_wait_bounded(&s.prm_full[pb], pphase, s.abort_flag, kShWaitNs);
-                if (!got) raise_abort(s, a);
-                *s.ep_go = got ? 1 : 0;
-            }
-            ptx::named_barrier_sync(1, kShEpiThreads);  // A1: parameters landed (or abort)
-            if (!*s.ep_go) { ok = false; break; }
-            // b1 is read in place; W2 (d_out rows of h) is staged transposed,
-            // one hidden unit (column) per thread.
-            const float* src = reinterpret_cast<const float*>(s.prm_raw + pb * a.prm_bytes);
-            const float* b1 = src;
-            for (int col = et; col < a.h; col += kShEpiThreads) {
-                float4* dst = reinterpret_cast<float4*>(s.w2t + col * a.dpad);
-                for (int o4 = 0; o4 < a.dpad / 4; ++o4) {
-                    float v[4];
-#pragma unroll
-                    for (int t = 0; t < 4; ++t) {
-                        const int o = 4 * o4 + t;
-                        v[t] = o < a.d_out ? src[a.h + o * a.h + col] : 0.0f;
+                };
+                for (int32_t c = 0; ok && c < r.n_chunks; ++c) {
+                    if (et == 0) {
+                        const bool got = ptx::mbar_wait_bounded(s.acc_full, acc_phase, s.abort_flag, kShWaitNs);
+                        if (!got) raise_abort(s, a);
+                        *s.ep_go = got ? 1 : 0;
                     }
-                    dst[o4] = make_float4(v[0], v[1], v[2], v[3]);
-                }
-            }
-            if (et < 16) s.b2[et] = et < a.d_out ? src[a.h + a.d_out * a.h + et] : 0.0f;
-            if (et == 0) {
-                const bool got = ptx::mbar_wait_bounded(s.acc_full, acc_phase, s.abort_flag, kShWaitNs);
-                if (!got) raise_abort(s, a);
-                *s.ep_go = got ? 1 : 0;
-            }
-            ptx::named_barrier_sync(1, kShEpiThreads);  // A2: accumulator ready (or abort); parameters staged
-            if (!*s.ep_go) { ok = false; break; }
-            ptx::tc_fence_after();
-
-            // D * (w_scale / x_div): the FP8 shadow stores w / 2^e.
-            const float scale = PREC == 2 ? ldexpf(a.inv_div, a.scale_exp[p]) : a.inv_div;
-            float logit[kShMaxOut];
+                    ptx::named_barrier_sync(1, kShEpiThreads);  // A2: accumulator ready; parameters staged
+                    if (!*s.ep_go) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    // This thread's columns: 8-column groups [j0, j1) of the chunk's width / 8,
+                    // read into registers at once; then the accumulator is handed back.
+                    const int32_t r0 = c * r.cw, n8 = chunk_width(r, c) / 8;
+                    const int32_t j0 = n8 * slot / kShSlots, j1 = n8 * (slot + 1) / kShSlots;
+                    uint32_t dreg[kShRegCols];
 #pragma unroll
-            for (int o = 0; o < kShMaxOut; ++o) logit[o] = 0.0f;
-            // hidden unit col: ReLU(D * scale + b1), then its layer-2 contributions
-            auto hidden = [&](int col, float d) {
-                const float hv = fmaxf(fmaf(d, scale, b1[col]), 0.0f);
-                const float4* wr = reinterpret_cast<const float4*>(s.w2t + col * a.dpad);
-#pragma unroll
-                for (int o4 = 0; o4 < kShMaxOut / 4; ++o4) {
-                    if (4 * o4 < a.d_out) {
-                        const float4 w = wr[o4];
-                        logit[4 * o4 + 0] = fmaf(w.x, hv, logit[4 * o4 + 0]);
-                        logit[4 * o4 + 1] = fmaf(w.y, hv, logit[4 * o4 + 1]);
-                        logit[4 * o4 + 2] = fmaf(w.z, hv, logit[4 * o4 + 2]);
-                        logit[4 * o4 + 3] = fmaf(w.w, hv, logit[4 * o4 + 3]);
-                    }
-                }
-            };
-            if (j1 - j0 <= kShRegCols / 8) {
-                // This thread's accumulator columns into registers, then hand the
-                // accumulator back so the next individual's MMAs overlap this math.
-                uint32_t dreg[kShRegCols];
-#pragma unroll
-                for (int j = 0; j < kShRegCols / 8; ++j)
-                    if (j0 + j < j1)
-                        ptx::tmem_ld8_nowait(tmem_base + lane_addr + static_cast<uint32_t>(8 * (j0 + j)),
-                                             *reinterpret_cast<uint32_t(*)[8]>(dreg + 8 * j));
-                ptx::tmem_ld_wait();
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(s.acc_empty);
-#pragma unroll
-                for (int c = 0; c < kShRegCols; ++c)
-                    if (j0 + c / 8 < j1) hidden(8 * j0 + c, __uint_as_float(dreg[c]));
-            } else {
-                for (int j = j0; j < j1; ++j) {
-                    uint32_t r8[8];
-                    ptx::tmem_ld8_nowait(tmem_base + lane_addr + static_cast<uint32_t>(8 * j), r8);
+                    for (int j = 0; j < kShRegCols / 8; ++j)
+                        if (j0 + j < j1)
+                            ptx::tmem_ld8_nowait(tmem_base + lane_addr + static_cast<uint32_t>(8 * (j0 + j)),
+                                                 *reinterpret_cast<uint32_t(*)[8]>(dreg + 8 * j));
                     ptx::tmem_ld_wait();
+                    ptx::tc_fence_before();
+                    ptx::mbar_arrive(s.acc_empty);
+                    acc_phase ^= 1u;
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) hidden(8 * j + t, __uint_as_float(r8[t]));
+                    for (int cc = 0; cc < kShRegCols; ++cc)
+                        if (j0 + cc / 8 < j1) hidden(r0 + 8 * j0 + cc, __uint_as_float(dreg[cc]));
                 }
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(s.acc_empty);
-            }
-            acc_phase ^= 1u;
-            ptx::mbar_arrive(&s.prm_empty[pb]);  // b1 no longer read
+                if (!ok) break;
+                ptx::mbar_arrive(&s.prm_empty[pb]);  // b1 no longer read
 
-            if (slot) {
-                float4* dst = reinterpret_cast<float4*>(s.part + ((slot - 1) * 128 + row) * kShMaxOut);
+                if (slot) {
+                    float4* dst = reinterpret_cast<float4*>(s.part + ((slot - 1) * 128 + row) * kShMaxOut);
 #pragma unroll
-                for (int o4 = 0; o4 < kShMaxOut / 4; ++o4)
-                    dst[o4] = make_float4(logit[4 * o4], logit[4 * o4 + 1], logit[4 * o4 + 2], logit[4 * o4 + 3]);
-            }
-            ptx::named_barrier_sync(1, kShEpiThreads);  // C: partial logits of slots 1..3 written
-            if (!slot) {
-                float loss = 0.0f;
-                int32_t good = 0;
-                if (srow < a.batch) {
+                    for (int o4 = 0; o4 < kShMaxOut / 4; ++o4)
+                        dst[o4] = make_float4(logit[4 * o4], logit[4 * o4 + 1], logit[4 * o4 + 2], logit[4 * o4 + 3]);
+                }
+                ptx::named_barrier_sync(1, kShEpiThreads);  // C: partial logits of slots 1..3 written
+                if (!slot) {
+                    float loss = 0.0f;
+                    int32_t good = 0;
+                    if (srow < r.batch) {
 #pragma unroll
-                    for (int o = 0; o < kShMaxOut; ++o) {
-                        float z = logit[o];
+                        for (int o = 0; o < kShMaxOut; ++o) {
+                            float z = logit[o];
 #pragma unroll
-                        for (int r = 0; r < kShSlots - 1; ++r) z += s.part[(r * 128 + row) * kShMaxOut + o];
-                        logit[o] = z + s.b2[o];
-                    }
-                    float zmax = logit[0];
-                    int arg = 0;
+                            for (int t = 0; t < kShSlots - 1; ++t) z += s.part[(t * 128 + row) * kShMaxOut + o];
+                            logit[o] = z + s.b2[o];
+                        }
+                        float zmax = logit[0];
+                        int arg = 0;
 #pragma unroll
-                    for (int o = 1; o < kShMaxOut; ++o) {
-                        if (o < a.d_out && logit[o] > zmax) { zmax = logit[o]; arg = o; }
-                    }
-                    float se = 0.0f;
-#pragma unroll
-                    for (int o = 0; o < kShMaxOut; ++o)
-                        if (o < a.d_out) se += expf(logit[o] - zmax);
-                    if (label >= 0 && label < a.d_out) {
-                        float zl = 0.0f;
+                        for (int o = 1; o < kShMaxOut; ++o) {
+                            if (o < a.d_out && logit[o] > zmax) { zmax = logit[o]; arg = o; }
+                        }
+                        float se = 0.0f;
 #pragma unroll
                         for (int o = 0; o < kShMaxOut; ++o)
-                            if (o == label) zl = logit[o];
-                        loss = logf(se) + zmax - zl;
-                        good = (arg == label) ? 1 : 0;
-                    } else {
-                        loss = __int_as_float(0x7FC00000);
+                            if (o < a.d_out) se += expf(logit[o] - zmax);
+                        if (label >= 0 && label < a.d_out) {
+                            float zl = 0.0f;
+#pragma unroll
+                            for (int o = 0; o < kShMaxOut; ++o)
+                                if (o == label) zl = logit[o];
+                            loss = logf(se) + zmax - zl;
+                            good = (arg == label) ? 1 : 0;
+                        } else {
+                            loss = __int_as_float(0x7FC00000);
+                        }
+                    }
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
+                        good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
+                    }
+                    if (lane == 0) {
+                        s.red_loss[q] = loss;
+                        s.red_ok[q] = good;
                     }
                 }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
-                    good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
-                }
-                if (lane == 0) {
-                    s.red_loss[q] = loss;
-                    s.red_ok[q] = good;
-                }
-            }
-            ptx::named_barrier_sync(1, kShEpiThreads);  // B: quarter sums written; staged data no longer read
-            if (et == 0) {
-                const float total = ((s.red_loss[0] + s.red_loss[1]) + s.red_loss[2]) + s.red_loss[3];
-                const int32_t n_ok = s.red_ok[0] + s.red_ok[1] + s.red_ok[2] + s.red_ok[3];
-                if (a.m_tiles == 1) {
-                    const float f = -(total / static_cast<float>(a.batch));
-                    a.f_raw[p] = f;
-                    if (a.f_adj) a.f_adj[p] = a.f_inh ? (1.0f - a.alpha) * a.f_inh[p] + a.alpha * f : f;
-                    if (a.correct) a.correct[p] = n_ok;
-                } else {
-                    a.scratch[static_cast<int64_t>(mt) * a.pop + p] = total;
-                    a.scratch[static_cast<int64_t>(a.m_tiles + mt) * a.pop + p] = static_cast<float>(n_ok);
+                ptx::named_barrier_sync(1, kShEpiThreads);  // B: quarter sums written; staged data no longer read
+                if (et == 0) {
+                    const float total = ((s.red_loss[0] + s.red_loss[1]) + s.red_loss[2]) + s.red_loss[3];
+                    const int32_t n_ok = s.red_ok[0] + s.red_ok[1] + s.red_ok[2] + s.red_ok[3];
+                    if (r.m_tiles == 1) {
+                        const float f = -(total / static_cast<float>(r.batch));
+                        r.f_raw[p] = f;
+                        if (r.f_adj) r.f_adj[p] = r.f_inh ? (1.0f - r.alpha) * r.f_inh[p] + r.alpha * f : f;
+                        if (r.correct) r.correct[p] = n_ok;
+                    } else {
+                        r.scratch[static_cast<int64_t>(sg.mt) * r.pop + p] = total;
+                        r.scratch[static_cast<int64_t>(r.m_tiles + sg.mt) * r.pop + p] = static_cast<float>(n_ok);
+                    }
                 }
             }
         }
@@ -509,43 +572,86 @@ eval_shadow_kernel(const EvalShArgs a)
     }
 }
 
-// Sums the per-tile partial losses of each individual in tile order.
-__global__ void combine_tiles_kernel(int32_t pop, int32_t m_tiles, int32_t batch, float alpha,
-                                     const float* __restrict__ scratch, const float* __restrict__ f_inh,
-                                     float* __restrict__ f_raw, float* __restrict__ f_adj,
-                                     int32_t* __restrict__ correct)
+// Sums the per-tile partial losses of each individual in tile order; one
+// grid row (blockIdx.y) per run, runs with a single tile skipped.
+__global__ void combine_tiles_kernel(const __grid_constant__ EvalShArgs a)
 {
+    const ShadowRun& r = run_of(a, blockIdx.y);
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= pop) return;
+    if (r.m_tiles < 2 || p >= r.pop) return;
     float total = 0.0f, ok = 0.0f;
-    for (int mt = 0; mt < m_tiles; ++mt) {
-        total += scratch[static_cast<int64_t>(mt) * pop + p];
-        ok += scratch[static_cast<int64_t>(m_tiles + mt) * pop + p];
+    for (int mt = 0; mt < r.m_tiles; ++mt) {
+        total += r.scratch[static_cast<int64_t>(mt) * r.pop + p];
+        ok += r.scratch[static_cast<int64_t>(r.m_tiles + mt) * r.pop + p];
     }
-    const float f = -(total / static_cast<float>(batch));
-    f_raw[p] = f;
-    if (f_adj) f_adj[p] = f_inh ? (1.0f - alpha) * f_inh[p] + alpha * f : f;
-    if (correct) correct[p] = static_cast<int32_t>(ok);
+    const float f = -(total / static_cast<float>(r.batch));
+    r.f_raw[p] = f;
+    if (r.f_adj) r.f_adj[p] = r.f_inh ? (1.0f - r.alpha) * r.f_inh[p] + r.alpha * f : f;
+    if (r.correct) r.correct[p] = static_cast<int32_t>(ok);
 }
 
-int32_t sh_stages_for(int32_t h, int32_t k, int32_t dpad)
+int32_t sh_stages_for(int32_t h_max, int32_t cw_max, int32_t dpad)
 {
-    int32_t stages = kShStages;
-    while (stages > 2 && sh_smem_bytes(h, k, dpad, stages) > 227u * 1024u) --stages;
+    int32_t stages = 8;
+    while (stages > 2 && sh_smem_bytes(h_max, cw_max, dpad, stages) > 227u * 1024u) --stages;
     return stages;
 }
 
+// The shared part of the arguments for k = d_0 inputs.
+EvalShArgs common_args(int32_t k, int32_t d_out, int32_t precision, int32_t h_max, int32_t cw_max)
+{
+    EvalShArgs a{};
+    a.k = k;
+    a.d_out = d_out;
+    a.dpad = (d_out + 3) / 4 * 4;
+    a.k_elems_stage = precision == 1 ? 64 : 128;
+    a.k_stages = (k + a.k_elems_stage - 1) / a.k_elems_stage;
+    a.k_mma = precision == 1 ? (k + 15) / 16 * 16 : (k + 31) / 32 * 32;
+    a.a_col = static_cast<uint32_t>(cw_max);
+    a.a_total_cols = sh_a_cols(precision, k, &a.a_piece_cols);
+    a.prm_bytes_max = sh_prm_bytes(h_max, d_out);
+    a.stage_bytes = static_cast<uint32_t>(cw_max) * 128u;
+    a.stages = sh_stages_for(h_max, cw_max, a.dpad);
+    return a;
+}
+
+cudaError_t launch(const EvalShArgs& a, int32_t precision, int32_t h_max, int32_t cw_max, int grid,
+                   int32_t n_runs, int32_t pop_max, bool any_tiles, cudaStream_t stream)
+{
+    // At least half of the shared memory, so that one CTA (which holds all 512
+    // TMEM columns) is resident per SM.
+    size_t smem = sh_smem_bytes(h_max, cw_max, a.dpad, a.stages);
+    if (smem < 116u * 1024u) smem = 116u * 1024u;
+    auto kernel = precision == 1 ? eval_shadow_kernel<1> : eval_shadow_kernel<2>;
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    kernel<<<grid, kShThreads, smem, stream>>>(a, h_max);
+    err = cudaGetLastError();
+    if (err != cudaSuccess || !any_tiles) return err;
+    combine_tiles_kernel<<<dim3((pop_max + 255) / 256, n_runs), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+int32_t eval_shadow_max_chunk(int32_t precision, int32_t k)
+{
+    uint32_t piece = 0;
+    const uint32_t a_cols = sh_a_cols(precision, k, &piece);
+    if (a_cols >= kShTmemCols) return 0;
+    int32_t cw = static_cast<int32_t>(kShTmemCols - a_cols) / 16 * 16;
+    return cw > kShMaxChunk ? kShMaxChunk : cw;
+}
 
 bool eval_shadow_supported(const NetLayout& net, int32_t precision, int32_t batch)
 {
     if (net.n_layers != 2 || (precision != 1 && precision != 2)) return false;
     const int32_t k = net.dims[0], h = net.dims[1], d_out = net.dims[2];
     if (k % 16 != 0 || h % 16 != 0 || h > 256 || d_out > kShMaxOut || batch < 1) return false;
-    uint32_t piece = 0;
-    if (static_cast<uint32_t>(h) + sh_a_cols(precision, k, &piece) > kShTmemCols) return false;
+    const int32_t cw = eval_shadow_max_chunk(precision, k);
+    if (cw < 16) return false;
     const int32_t dpad = (d_out + 3) / 4 * 4;
-    return sh_smem_bytes(h, k, dpad, sh_stages_for(h, k, dpad)) <= 227u * 1024u;
+    return sh_smem_bytes(h, cw, dpad, sh_stages_for(h, cw, dpad)) <= 227u * 1024u;
 }
 
 size_t eval_shadow_scratch_bytes(int32_t pop, int32_t batch)
@@ -554,68 +660,75 @@ size_t eval_shadow_scratch_bytes(int32_t pop, int32_t batch)
     return m_tiles > 1 ? sizeof(float) * 2 * static_cast<size_t>(m_tiles) * pop : 0;
 }
 
+ShadowRun shadow_run(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
+                     const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp, const uint8_t* x,
+                     float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                     float* f_adj, int32_t* correct, float* scratch, int32_t chunk)
+{
+    ShadowRun r{};
+    r.pop = pop;
+    r.h = net.dims[1];
+    r.batch = batch;
+    r.m_tiles = (batch + 127) / 128;
+    const int32_t cw_max = eval_shadow_max_chunk(precision, net.dims[0]);
+    int32_t cw = chunk > 0 && chunk <= cw_max ? chunk : cw_max;
+    if (cw > r.h) cw = r.h;
+    // Equal chunks when the hidden units need several: ceil(h / n) rounded up to 16.
+    const int32_t n = (r.h + cw - 1) / cw;
+    r.cw = ((r.h + n - 1) / n + 15) / 16 * 16;
+    r.n_chunks = (r.h + r.cw - 1) / r.cw;
+    r.c_pad = net.c_pad;
+    r.sh_stride = sh_stride;
+    r.inv_div = static_cast<float>(1.0 / static_cast<double>(x_div));
+    r.alpha = alpha;
+    r.popv = pop_dev;
+    r.shadow = shadow;
+    r.x = x;
+    r.y = y;
+    r.f_inh = f_inh;
+    r.scale_exp = scale_exp;
+    r.f_raw = f_raw;
+    r.f_adj = f_adj;
+    r.correct = correct;
+    r.scratch = scratch;
+    return r;
+}
+
 cudaError_t launch_eval_shadow(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
                                const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp,
                                const uint8_t* x, float x_div, const int32_t* y, int32_t batch, float alpha,
                                const float* f_inh, float* f_raw, float* f_adj, int32_t* correct, float* scratch,
-                               unsigned int* status, cudaStream_t stream)
+                               unsigned int* status, cudaStream_t stream, int32_t chunk)
 {
-    EvalShArgs a{};
-    a.pop = pop;
-    a.k = net.dims[0];
-    a.h = net.dims[1];
-    a.d_out = net.dims[2];
-    a.dpad = (a.d_out + 3) / 4 * 4;
-    a.batch = batch;
-    a.precision = precision;
-    a.k_elems_stage = precision == 1 ? 64 : 128;
-    a.k_stages = (a.k + a.k_elems_stage - 1) / a.k_elems_stage;
-    a.k_mma = precision == 1 ? (a.k + 15) / 16 * 16 : (a.k + 31) / 32 * 32;
-    a.m_tiles = (batch + 127) / 128;
-    a.c_pad = net.c_pad;
-    a.sh_stride = sh_stride;
-    a.inv_div = static_cast<float>(1.0 / static_cast<double>(x_div));
-    a.alpha = alpha;
-    a.a_col = static_cast<uint32_t>(a.h);
-    a.a_total_cols = sh_a_cols(precision, a.k, &a.a_piece_cols);
-    a.prm_bytes = sh_prm_bytes(a.h, a.d_out);
-    a.popv = pop_dev;
-    a.shadow = shadow;
-    a.x = x;
-    a.y = y;
-    a.f_inh = f_inh;
-    a.scale_exp = scale_exp;
-    a.f_raw = f_raw;
-    a.f_adj = f_adj;
-    a.correct = correct;
-    a.scratch = scratch;
+    const ShadowRun r = shadow_run(net, pop, pop_dev, precision, shadow, sh_stride, scale_exp, x, x_div, y, batch,
+                                   alpha, f_inh, f_raw, f_adj, correct, scratch, chunk);
+    if (r.m_tiles > 1 && !scratch) return cudaErrorInvalidValue;
+    EvalShArgs a = common_args(net.dims[0], net.dims[2], precision, r.h, r.cw);
+    a.run0 = r;
     a.status = status;
-    if (a.m_tiles > 1 && !scratch) return cudaErrorInvalidValue;
-    a.stages = sh_stages_for(a.h, a.k, a.dpad);
-    a.ring_bytes = sh_ring_bytes(a.h, a.k, a.stages);
-    // At least half of the shared memory, so that one CTA (which holds all 512
-    // TMEM columns) is resident per SM.
-    size_t smem = sh_smem_bytes(a.h, a.k, a.dpad, a.stages);
-    if (smem < 116u * 1024u) smem = 116u * 1024u;
-
     int dev = 0, sms = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    auto kernel = precision == 1 ? eval_shadow_kernel<1> : eval_shadow_kernel<2>;
-    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (err != cudaSuccess) return err;
     // Whole groups of m_tiles CTAs, no more groups than individuals.
-    int groups = sms / a.m_tiles;
+    int groups = sms / r.m_tiles;
     if (groups < 1) groups = 1;
     if (groups > pop) groups = pop;
-    kernel<<<groups * a.m_tiles, kShThreads, smem, stream>>>(a);
-    err = cudaGetLastError();
-    if (err != cudaSuccess || a.m_tiles == 1) return err;
-    combine_tiles_kernel<<<(pop + 255) / 256, 256, 0, stream>>>(pop, a.m_tiles, batch, alpha, scratch, f_inh, f_raw,
-                                                               f_adj, correct);
-    return cudaGetLastError();
+    return launch(a, precision, r.h, r.cw, groups * r.m_tiles, 1, pop, r.m_tiles > 1, stream);
+}
+
+cudaError_t launch_eval_shadow_runs(int32_t k, int32_t d_out, int32_t precision, int32_t h_max, int32_t cw_max,
+                                    int32_t n_runs, int32_t pop_max, bool any_tiles, const ShadowRun* runs_dev,
+                                    const ShadowSeg* segs_dev, const int32_t* seg_off_dev, int32_t grid,
+                                    unsigned int* status, cudaStream_t stream)
+{
+    EvalShArgs a = common_args(k, d_out, precision, h_max, cw_max);
+    a.runs = runs_dev;
+    a.segs = segs_dev;
+    a.seg_off = seg_off_dev;
+    a.status = status;
+    return launch(a, precision, h_max, cw_max, grid, n_runs, pop_max, any_tiles, stream);
 }
 
 }  // namespace leea

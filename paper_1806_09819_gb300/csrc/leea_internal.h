@@ -107,13 +107,47 @@ cudaError_t launch_make_shadow(int32_t pop, int32_t k, int32_t h, int64_t c_pad,
                                int32_t precision, uint8_t* shadow, int64_t sh_stride, int32_t* scale_exp, float* amax,
                                cudaStream_t stream);
 // Evaluation of 8-bit inputs against BF16 / FP8 shadows of W1 (tcgen05).
+// One run's evaluation problem; hidden units in n_chunks chunks of cw (the
+// last one possibly narrower), batch in m_tiles tiles of 128 samples.
+struct ShadowRun {
+    int32_t pop, h, batch, m_tiles, cw, n_chunks;
+    int64_t c_pad, sh_stride;
+    float inv_div, alpha;
+    const float* popv;
+    const uint8_t* shadow;
+    const uint8_t* x;
+    const int32_t* y;
+    const float* f_inh;
+    const int32_t* scale_exp;
+    float* f_raw;
+    float* f_adj;
+    int32_t* correct;
+    float* scratch;  // m_tiles > 1: 2 m_tiles pop floats of per-tile partial sums
+};
+// Individuals [p0, p1) of run `run` on its 128-sample tile mt.
+struct ShadowSeg {
+    int32_t run, mt, p0, p1;
+};
 bool eval_shadow_supported(const NetLayout& net, int32_t precision, int32_t batch);
 size_t eval_shadow_scratch_bytes(int32_t pop, int32_t batch);
+// Widest hidden chunk the tensor memory leaves room for next to the batch tile.
+int32_t eval_shadow_max_chunk(int32_t precision, int32_t k);
+// chunk: hidden units per chunk (multiple of 16), 0 for the widest.
+ShadowRun shadow_run(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
+                     const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp, const uint8_t* x,
+                     float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                     float* f_adj, int32_t* correct, float* scratch, int32_t chunk);
 cudaError_t launch_eval_shadow(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
                                const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp,
                                const uint8_t* x, float x_div, const int32_t* y, int32_t batch, float alpha,
                                const float* f_inh, float* f_raw, float* f_adj, int32_t* correct, float* scratch,
-                               unsigned int* status, cudaStream_t stream);
+                               unsigned int* status, cudaStream_t stream, int32_t chunk = 0);
+// Many runs of d_0-h_r-d_out nets in one launch: runs_dev[n_runs], CTA b walks
+// segs_dev[seg_off_dev[b] .. seg_off_dev[b+1]); h_max and cw_max bound every run's.
+cudaError_t launch_eval_shadow_runs(int32_t k, int32_t d_out, int32_t precision, int32_t h_max, int32_t cw_max,
+                                    int32_t n_runs, int32_t pop_max, bool any_tiles, const ShadowRun* runs_dev,
+                                    const ShadowSeg* segs_dev, const int32_t* seg_off_dev, int32_t grid,
+                                    unsigned int* status, cudaStream_t stream);
 // Evaluation of d_0-h-d_out nets (one hidden layer), SIMT FP32.
 cudaError_t launch_eval_simt(const NetLayout& net, int32_t pop, const float* pop_dev,
                              const float* x, const int32_t* y, int32_t batch, float alpha,

@@ -104,6 +104,8 @@ SHADOW_CASES = [
     ([64, 16, 4], 160, 128),
     ([128, 256, 10], 7, 77),
     ([96, 48, 16], 11, 513),
+    ([784, 256, 10], 13, 100),   # hidden units in 3 chunks (96, 96, 64)
+    ([784, 160, 10], 6, 200),    # 2 chunks of 80, 2 sample tiles
 ]
 
 
@@ -158,8 +160,10 @@ def test_evaluate_shadow_argument_errors(gpu):
     small = torch.empty(3, dtype=torch.float32, device="cuda")
     with pytest.raises(gpu.LeeaError, match="scratch"):
         gpu.leea_evaluate_shadow_u8(pop, dims, pd, 1, sh, se, x, 255.0, y, batch, 1.0, None, f, scratch_dev=small)
-    with pytest.raises(gpu.LeeaError):  # h = 128 with d_0 = 784 does not fit the tensor memory
-        gpu.leea_make_shadow(pop, [784, 128, 10], 1, pd, sh, se, f)
+    with pytest.raises(gpu.LeeaError):  # h above 256
+        gpu.leea_make_shadow(pop, [784, 272, 10], 1, pd, sh, se, f)
+    with pytest.raises(gpu.LeeaError):  # d_0 not a multiple of 16
+        gpu.leea_make_shadow(pop, [780, 32, 10], 1, pd, sh, se, f)
     with pytest.raises(gpu.LeeaError):
         gpu.leea_evaluate_shadow_u8(pop, dims, pd, 3, sh, se, x, 255.0, y, 100, 1.0, None, f)
     # 13 blocks of 64 BF16 inputs, 7 blocks of 128 FP8 inputs, 32 rows of 128 bytes each
@@ -239,8 +243,8 @@ def test_state_full_size_sampled(gpu, oracle_mod, precision):
 
 def test_precision_state_errors(gpu):
     torch = _torch()
-    with pytest.raises(gpu.LeeaError):  # h = 128 and d_0 = 784 do not fit the tensor memory
-        gpu.LeeaState(8, [784, 128, 10], gpu.Params(precision=1), seed=1)
+    with pytest.raises(gpu.LeeaError):  # d_0 not a multiple of 16
+        gpu.LeeaState(8, [780, 128, 10], gpu.Params(precision=1), seed=1)
     st = gpu.LeeaState(8, [784, 32, 10], gpu.Params(precision=2), seed=1)
     try:
         x = torch.zeros((16, 784), dtype=torch.float32, device="cuda")
