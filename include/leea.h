@@ -400,6 +400,112 @@ leea_status leea_profile_enable(leea_state* s, int32_t enable);
  * number of launches since the last read, and resets both. */
 leea_status leea_profile_read(leea_state* s, double* ms_out, int64_t* launches_out);
 
+/* ---------------------------------------------------------------------- */
+/* Batching form: many independent runs advanced together                   */
+/* ---------------------------------------------------------------------- */
+
+/* One run of the batching form: `pop` nets d_in-hidden-d_out (pop <= 4096),
+ * minibatches of `batch` samples, its own seed (streams as in leea_create),
+ * and `chunk`, the hidden units per tensor-core pass of its evaluation (a
+ * multiple of 16; 0 = the widest the tensor memory allows) -- the tile shape
+ * an autotuner chooses. */
+typedef struct {
+    int32_t pop, hidden, batch, chunk;
+    uint64_t seed;
+} leea_run_spec;
+
+typedef struct leea_multi leea_multi;
+
+/* Creates n_runs runs of Algorithm 1 that share d_in, d_out and the operator
+ * parameters p; p->precision must be 1 or 2 (the batching form evaluates on
+ * the tensor cores through BF16 or FP8 shadows; see "Precision form").  Each
+ * run is initialised from its seed as leea_create would.  All later calls
+ * enqueue on `stream`.  Minibatches and per-individual results are PACKED
+ * over the runs: run r owns rows [batch_off[r], batch_off[r] + batch_r) of a
+ * uint8[total_rows][d_in] minibatch (and of its int32[total_rows] labels),
+ * and entries [pop_off[r], pop_off[r] + pop_r) of the float[total_pop]
+ * fitness arrays (leea_multi_layout). */
+leea_status leea_multi_create(int32_t n_runs, const leea_run_spec* runs, int32_t d_in, int32_t d_out,
+                              const leea_params* p, void* stream, leea_multi** out);
+
+/* Packed offsets (int64[n_runs] each, either may be NULL) and totals. */
+leea_status leea_multi_layout(const leea_multi* m, int64_t* batch_off, int64_t* pop_off,
+                              int64_t* total_rows, int64_t* total_pop);
+
+/* The evaluation shape run `run` uses: hidden units per chunk, chunks per
+ * individual and 128-sample tiles per batch (any pointer may be NULL). */
+leea_status leea_multi_run_shape(const leea_multi* m, int32_t run, int32_t* chunk, int32_t* n_chunks,
+                                 int32_t* m_tiles);
+
+/* The object's own packed minibatch buffers.  A caller that writes the next
+ * minibatch there (on the object's stream) saves the copy of
+ * leea_multi_generation_u8. */
+leea_status leea_multi_batch_buffers(leea_multi* m, uint8_t** x_dev, int32_t** y_dev);
+
+/* One generation of every run on the packed minibatch (levels, x = k / x_div).
+ * The first call evaluates every initial population.  Each later call
+ * increments the common generation counter g and then, for all runs at once,
+ * ranks and selects (one launch), breeds (one persistent launch over the work
+ * items of every run) and evaluates (one persistent launch whose CTAs walk
+ * precomputed segments of (run, sample tile, individuals)).  These launches
+ * are captured into a CUDA graph on the first breeding call of each buffer
+ * parity and replayed afterwards; the kernels read g from device memory.  A
+ * call with another x_div rebuilds the evaluation tables and the graphs.
+ * x_dev / y_dev are copied into the object's buffers unless they are those
+ * buffers.  Enqueue only. */
+leea_status leea_multi_generation_u8(leea_multi* m, const uint8_t* x_dev, float x_div, const int32_t* y_dev);
+
+/* The same with the packed minibatch in host memory (copied on the stream). */
+leea_status leea_multi_generation_u8_host(leea_multi* m, const uint8_t* x_host, float x_div,
+                                          const int32_t* y_host);
+
+/* Packed f_adj (and correct counts, if not NULL) of every run.  Synchronises. */
+leea_status leea_multi_fitness(leea_multi* m, float* f_adj_host, int32_t* correct_host);
+
+/* Packed raw fitness of the last evaluation.  Synchronises. */
+leea_status leea_multi_raw_fitness(leea_multi* m, float* f_raw_host);
+
+/* Run `run`'s current population, float[pop][c] logical layout.  Synchronises. */
+leea_status leea_multi_get_population(leea_multi* m, int32_t run, float* out_host);
+
+/* Replaces run `run`'s current population (its shadows are rebuilt). */
+leea_status leea_multi_set_population(leea_multi* m, int32_t run, const float* in_host);
+
+/* Replaces the packed f_adj of every run. */
+leea_status leea_multi_set_fitness(leea_multi* m, const float* f_adj_host);
+
+/* Sets the generation counter and whether the populations count as evaluated. */
+leea_status leea_multi_set_generation(leea_multi* m, uint32_t gen, int32_t evaluated);
+
+/* Run `run`'s ranking and selection of the last breed (any pointer may be
+ * NULL; int32 / float arrays of its pop).  Synchronises. */
+leea_status leea_multi_get_selection(leea_multi* m, int32_t run, int32_t* order, int32_t* par1,
+                                     int32_t* par2, int32_t* kind, float* f_inh);
+
+/* Run `run`'s current shadows (uint8[pop][leea_shadow_stride]), FP8 scale
+ * exponents and exact max |W1| (any pointer may be NULL).  Synchronises. */
+leea_status leea_multi_get_shadow(leea_multi* m, int32_t run, uint8_t* shadow_host, int32_t* scale_exp_host,
+                                  float* amax_host);
+
+/* Generation counter g (0 before the first breed). */
+uint32_t leea_multi_generation_index(const leea_multi* m);
+
+/* Per-stage timing: while enabled, generations run as direct launches (not
+ * the graph) between CUDA events; stages as LEEA_NUM_STAGES, each stage one
+ * launch covering every run. */
+leea_status leea_multi_profile_enable(leea_multi* m, int32_t enable);
+leea_status leea_multi_profile_read(leea_multi* m, double* ms_out, int64_t* launches_out);
+
+/* Frees the object and its device memory (synchronises its stream first). */
+void leea_multi_destroy(leea_multi* m);
+
+/* Autotuner support: mean time in ms of `reps` shadow evaluations of a
+ * population of `pop` random nets d_in-hidden-d_out on a batch of `batch`
+ * samples with `chunk` hidden units per pass, on the current device and
+ * the legacy default stream.  Allocates and frees its own buffers. */
+leea_status leea_tune_shadow_eval(int32_t precision, int32_t d_in, int32_t hidden, int32_t d_out, int32_t batch,
+                                  int32_t pop, int32_t chunk, int32_t reps, float* ms_out);
+
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* leea_last_error(void);
 

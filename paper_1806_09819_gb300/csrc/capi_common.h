@@ -1,0 +1,43 @@
+// capi_common.h -- helpers the C ABI's translation units share: error
+// reporting, argument checks, layout and the per-step kernel arguments.
+#pragma once
+#include "leea.h"
+#include "leea_internal.h"
+
+#include <cuda_runtime.h>
+
+namespace leea {
+namespace capi {
+
+// Records a message for leea_last_error() and returns st.
+leea_status fail(leea_status st, const char* fmt, ...);
+// LEEA_ENOMEM for an allocation failure, LEEA_ECUDA otherwise.
+leea_status cuda_fail(cudaError_t err, const char* what);
+
+// Section 3.2's gene offsets and Section 4.1's init scales of a net.
+bool make_layout(const int32_t* dims, int32_t n_dims, int32_t init, NetLayout* net);
+// floor(q 2^16), 2^16 when q >= 1: the 16-bit draw threshold of probability q.
+uint32_t threshold16(double q);
+leea_status check_params(const leea_params* p);
+leea_status check_pop(int32_t pop);
+// Elites, crossover and mutation children and the truncation pool (Algorithm 1).
+void counts_of(int32_t pop, const leea_params* p, int32_t* ne, int32_t* nc, int32_t* nm, int32_t* pool);
+// This device's status word (bounded waits report here).
+unsigned int* device_status_ptr();
+// Synchronises the stream, then reads and clears the status word.
+leea_status check_device_status(cudaStream_t stream, uint32_t* flags_out);
+
+int64_t shadow_stride_of(const NetLayout& net, int32_t precision);
+leea_status check_shadow_shape(const NetLayout& net, int32_t precision);
+
+SelectArgs select_args(int32_t pop, const leea_params* p, uint64_t seed, uint32_t gen);
+BreedArgs breed_args(int32_t pop, const NetLayout& net, const leea_params* p, uint64_t seed, uint32_t gen);
+
+}  // namespace capi
+}  // namespace leea
+
+#define LEEA_CUDA_TRY(expr, what)                                      \
+    do {                                                               \
+        cudaError_t err_ = (expr);                                     \
+        if (err_ != cudaSuccess) return leea::capi::cuda_fail(err_, what); \
+    } while (0)

@@ -47,7 +47,8 @@ struct StageMeta {
     int32_t g0;      // first gene of the chunk
     int32_t len;     // genes in the chunk (multiple of 32)
     int32_t sexp;    // precision form, FP8: exponent of the child's scale
-    int32_t pad[3];
+    int32_t run;     // many runs: index of the child's run
+    int32_t pad[2];
 };
 
 struct BreedSmem {
@@ -169,12 +170,12 @@ __device__ __forceinline__ float4 select4(uint32_t m, float4 a, float4 b)
 // pair s & 1 of NORMAL block 2u + (s >> 1).  A warp numbers the slots that
 // hold a masked gene (prefix scan over the lanes) and generates those normals
 // on consecutive lanes, then every lane collects its own.
-__device__ __forceinline__ void mutate_unit(const BreedArgs& a, const PhiloxKeys& key, uint32_t j, uint32_t u,
-                                            bool live, float4 (&v)[2], int lane)
+__device__ __forceinline__ void mutate_unit(const BreedArgs& a, uint32_t gen, const PhiloxKeys& key, uint32_t j,
+                                            uint32_t u, bool live, float4 (&v)[2], int lane)
 {
     constexpr int kSlots = 4;
     uint32_t hit = 0;
-    if (live) hit = mask8(philox_keyed(make_uint4(u, j, a.gen, kTagMutMask), key), a.thr_mut);
+    if (live) hit = mask8(philox_keyed(make_uint4(u, j, gen, kTagMutMask), key), a.thr_mut);
     uint32_t need = 0;
 #pragma unroll
     for (int sl = 0; sl < kSlots; ++sl) need |= ((hit >> (2 * sl)) & 3u) ? (1u << sl) : 0u;
@@ -215,7 +216,7 @@ __device__ __forceinline__ void mutate_unit(const BreedArgs& a, const PhiloxKeys
             }
             // Lanes of a warp own consecutive units: the owner's is u - lane + o.
             const uint32_t uo = u - static_cast<uint32_t>(lane) + static_cast<uint32_t>(o);
-            const uint4 n = philox_keyed(make_uint4(2u * uo + (slot >> 1), j, a.gen, kTagNormal), key);
+            const uint4 n = philox_keyed(make_uint4(2u * uo + (slot >> 1), j, gen, kTagNormal), key);
             zz = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
         }
 #pragma unroll
@@ -238,10 +239,25 @@ __device__ __forceinline__ void mutate_unit(const BreedArgs& a, const PhiloxKeys
     if (hit & 0x80u) v[1].w = fmaf(a.sigma, z[3].y, v[1].w);
 }
 
+// The run owning global work item `it`: the last one whose first item is <= it.
+__device__ __forceinline__ int32_t run_of_item(const BreedRun* runs, int32_t n_runs, int64_t it)
+{
+    int32_t lo = 0, hi = n_runs - 1;
+    while (lo < hi) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if (runs[mid].item0 <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// MULTI = false: one run (run0), generation in run0.a.gen.  MULTI = true: the
+// runs of a device table, whose work items are numbered consecutively, and
+// the generation read from gen_dev.
+template <bool MULTI>
 __global__ void __launch_bounds__(kBreedThreads, 1)
-breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ parents,
-             const int32_t* __restrict__ par1, const int32_t* __restrict__ par2, const int32_t* __restrict__ kind,
-             float* __restrict__ children, unsigned int* __restrict__ status)
+breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__ runs, int32_t n_runs,
+             int64_t n_items, const uint32_t* __restrict__ gen_dev, unsigned int* __restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
     const BreedSmem s = carve(smem_raw);
@@ -256,13 +272,12 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
     }
     __syncthreads();
 
-    const int64_t n_items = static_cast<int64_t>(a.pop) * chunks_per_child;
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t stage = 0, phase = 0;
             uint32_t issued_mask = 0, parity_mask = 0;  // per stage: issued at all / parity of the last issue
-            int32_t cur_j = -1, cur_kind = 0, cur_p1 = 0, cur_p2 = 0, cur_sexp = 0;
+            int32_t cur_j = -1, cur_run = -1, cur_kind = 0, cur_p1 = 0, cur_p2 = 0, cur_sexp = 0;
             bool ok = true;
             for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
                 if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
@@ -270,30 +285,36 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
                     ok = false;
                     break;
                 }
-                const int32_t ci = static_cast<int32_t>(it / chunks_per_child);
-                const int32_t ck = static_cast<int32_t>(it - static_cast<int64_t>(ci) * chunks_per_child);
+                const int32_t ri = MULTI ? run_of_item(runs, n_runs, it) : 0;
+                const BreedRun& R = MULTI ? runs[ri] : run0;
+                const BreedArgs& a = R.a;
+                const int64_t li = it - R.item0;
+                const int32_t ci = static_cast<int32_t>(li / R.chunks);
+                const int32_t ck = static_cast<int32_t>(li - static_cast<int64_t>(ci) * R.chunks);
                 const int32_t j = (ci & 1) ? a.pop - 1 - (ci >> 1) : (ci >> 1);
-                if (j != cur_j) {
+                if (j != cur_j || ri != cur_run) {
                     cur_j = j;
-                    cur_kind = kind[j];
-                    cur_p1 = par1[j];
-                    cur_p2 = par2[j];
+                    cur_run = ri;
+                    cur_kind = R.kind[j];
+                    cur_p1 = R.par1[j];
+                    cur_p2 = R.par2[j];
                     cur_sexp = (a.precision == 2) ? a.scale_exp[j] : 0;
                     if (cur_p1 < 0 || cur_p1 >= a.pop || cur_p2 < 0 || cur_p2 >= a.pop) cur_kind = kKindInvalid;
                 }
                 const int64_t g0 = static_cast<int64_t>(ck) * kChunk;
                 const int32_t len = static_cast<int32_t>(a.c_pad - g0 < kChunk ? a.c_pad - g0 : kChunk);
-                s.meta[stage] = StageMeta{ j, cur_kind, static_cast<int32_t>(g0), len, cur_sexp, { 0, 0, 0 } };
+                s.meta[stage] = StageMeta{ j, cur_kind, static_cast<int32_t>(g0), len, cur_sexp, ri, { 0, 0 } };
                 const uint32_t bytes = static_cast<uint32_t>(len) * 4u;
                 if (cur_kind == kKindInvalid) {
                     ptx::mbar_arrive(&s.full[stage]);
                 } else {
                     const bool two = (cur_kind == 1);
                     ptx::mbar_arrive_expect_tx(&s.full[stage], two ? 2u * bytes : bytes);
-                    ptx::bulk_load(stage_a(s, stage), parents + static_cast<int64_t>(cur_p1) * a.c_pad + g0, bytes, &s.full[stage]);
+                    ptx::bulk_load(stage_a(s, stage), R.parents + static_cast<int64_t>(cur_p1) * a.c_pad + g0, bytes,
+                                   &s.full[stage]);
                     if (two)
-                        ptx::bulk_load(stage_b(s, stage), parents + static_cast<int64_t>(cur_p2) * a.c_pad + g0, bytes,
-                                  &s.full[stage]);
+                        ptx::bulk_load(stage_b(s, stage), R.parents + static_cast<int64_t>(cur_p2) * a.c_pad + g0, bytes,
+                                       &s.full[stage]);
                 }
                 issued_mask |= 1u << stage;
                 parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
@@ -309,7 +330,9 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
     } else {
         // ------------------------------------------------------------ consumers
         const int ct = threadIdx.x - 32;
-        const PhiloxKeys key = philox_keys(a.seed);
+        const uint32_t gen = MULTI ? *gen_dev : run0.a.gen;
+        PhiloxKeys key = philox_keys(run0.a.seed);
+        int32_t key_run = MULTI ? -1 : 0;  // the run `key` belongs to
         uint32_t stage = 0, phase = 0;
         for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
             if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kWaitLimitNs)) {
@@ -317,9 +340,15 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
                 break;
             }
             const StageMeta m = s.meta[stage];
+            const BreedRun& R = MULTI ? runs[m.run] : run0;
+            const BreedArgs& a = R.a;
+            if (MULTI && m.run != key_run) {
+                key = philox_keys(a.seed);
+                key_run = m.run;
+            }
             const float4* A = reinterpret_cast<const float4*>(stage_a(s, stage));
             const float4* B = reinterpret_cast<const float4*>(stage_b(s, stage));
-            float4* O = reinterpret_cast<float4*>(children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
+            float4* O = reinterpret_cast<float4*>(R.children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
             const uint32_t j = static_cast<uint32_t>(m.j);
             const bool live = ct * kGenesPerLane < m.len;
             const uint32_t u = (static_cast<uint32_t>(m.g0) >> 3) + static_cast<uint32_t>(ct);  // 8-gene unit
@@ -329,11 +358,11 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
                 v[1] = A[2 * ct + 1];
             }
             if (m.kind == 2) {
-                mutate_unit(a, key, j, u, live, v, lane);
+                mutate_unit(a, gen, key, j, u, live, v, lane);
             } else if (live && m.kind == 1) {
                 const float4 b0 = B[2 * ct], b1 = B[2 * ct + 1];
                 if (a.xo_op == 0) {
-                    const uint32_t msk = mask8(philox_keyed(make_uint4(u, j, a.gen, kTagXo), key), a.thr_xo);
+                    const uint32_t msk = mask8(philox_keyed(make_uint4(u, j, gen, kTagXo), key), a.thr_xo);
                     v[0] = select4(msk, v[0], b0);
                     v[1] = select4(msk >> 4, v[1], b1);
                 } else {
@@ -373,22 +402,58 @@ breed_kernel(BreedArgs a, int32_t chunks_per_child, const float* __restrict__ pa
 
 }  // namespace
 
-cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t* par1, const int32_t* par2,
-                         const int32_t* kind, float* children, unsigned int* status, cudaStream_t stream)
+int32_t breed_chunks(int64_t c_pad) { return static_cast<int32_t>((c_pad + kChunk - 1) / kChunk); }
+
+namespace {
+
+cudaError_t breed_grid(int64_t items, int* grid)
 {
-    const int32_t chunks = static_cast<int32_t>((a.c_pad + kChunk - 1) / kChunk);
     int dev = 0, sms = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(breed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    *grid = static_cast<int>(items < sms ? (items > 0 ? items : 1) : sms);
+    return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t* par1, const int32_t* par2,
+                         const int32_t* kind, float* children, unsigned int* status, cudaStream_t stream)
+{
+    BreedRun r{};
+    r.a = a;
+    r.parents = parents;
+    r.par1 = par1;
+    r.par2 = par2;
+    r.kind = kind;
+    r.children = children;
+    r.chunks = breed_chunks(a.c_pad);
+    r.item0 = 0;
+    const int64_t items = static_cast<int64_t>(a.pop) * r.chunks;
+    int grid = 0;
+    cudaError_t err = breed_grid(items, &grid);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(breed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(kBreedSmemBytes));
     if (err != cudaSuccess) return err;
-    const int64_t items = static_cast<int64_t>(a.pop) * chunks;
-    const int grid = static_cast<int>(items < sms ? items : sms);
-    breed_kernel<<<grid, kBreedThreads, kBreedSmemBytes, stream>>>(a, chunks, parents, par1, par2, kind, children,
-                                                                 status);
+    breed_kernel<false><<<grid, kBreedThreads, kBreedSmemBytes, stream>>>(r, nullptr, 1, items, nullptr, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_breed_runs(const BreedRun* runs_dev, int32_t n_runs, int64_t n_items, const uint32_t* gen_dev,
+                              unsigned int* status, cudaStream_t stream)
+{
+    int grid = 0;
+    cudaError_t err = breed_grid(n_items, &grid);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(breed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               static_cast<int>(kBreedSmemBytes));
+    if (err != cudaSuccess) return err;
+    const BreedRun none{};
+    breed_kernel<true><<<grid, kBreedThreads, kBreedSmemBytes, stream>>>(none, runs_dev, n_runs, n_items, gen_dev,
+                                                                       status);
     return cudaGetLastError();
 }
 

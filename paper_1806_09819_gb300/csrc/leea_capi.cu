@@ -3,6 +3,7 @@
 // them together in the order of Algorithm 1.
 #include "leea.h"
 #include "leea_internal.h"
+#include "capi_common.h"
 
 #include <cuda_runtime.h>
 
@@ -14,7 +15,8 @@
 
 using namespace leea;
 
-namespace {
+namespace leea {
+namespace capi {
 
 thread_local char g_error[1024] = "";
 
@@ -34,11 +36,6 @@ leea_status cuda_fail(cudaError_t err, const char* what)
     return fail(LEEA_ECUDA, "%s: %s", what, cudaGetErrorString(err));
 }
 
-#define LEEA_CUDA_TRY(expr, what)                         \
-    do {                                                  \
-        cudaError_t err_ = (expr);                        \
-        if (err_ != cudaSuccess) return cuda_fail(err_, what); \
-    } while (0)
 
 // Offsets of Section 3.2's direct encoding, plus the initialisation scale of
 // each weight matrix (Section 4.1).
@@ -271,7 +268,42 @@ leea_status dispatch_eval_shadow(const NetLayout& net, int32_t pop, const float*
     return LEEA_OK;
 }
 
-}  // namespace
+SelectArgs select_args(int32_t pop, const leea_params* p, uint64_t seed, uint32_t gen)
+{
+    SelectArgs a{};
+    int32_t ne, nc, nm, pl;
+    counts_of(pop, p, &ne, &nc, &nm, &pl);
+    a.pop = pop;
+    a.n_elite = ne;
+    a.n_cross = nc;
+    a.pool = pl;
+    a.sel_op = p->sel_op;
+    a.tour_k = p->tour_k;
+    a.seed = seed;
+    a.gen = gen;
+    return a;
+}
+
+BreedArgs breed_args(int32_t pop, const NetLayout& net, const leea_params* p, uint64_t seed,
+                            uint32_t gen)
+{
+    BreedArgs a{};
+    a.pop = pop;
+    a.c = net.c;
+    a.c_pad = net.c_pad;
+    a.xo_op = p->xo_op;
+    a.thr_xo = threshold16(static_cast<double>(p->xo_gene_p));
+    a.thr_mut = threshold16(static_cast<double>(p->mut_rate));
+    a.sigma = p->sigma;
+    a.seed = seed;
+    a.gen = gen;
+    return a;
+}
+
+}  // namespace capi
+}  // namespace leea
+
+using namespace leea::capi;
 
 // ------------------------------------------------------------------------
 // Plain functions
@@ -352,22 +384,6 @@ leea_status leea_rank(int32_t pop, const float* f_adj_dev, int32_t* order_dev, v
     return LEEA_OK;
 }
 
-static SelectArgs select_args(int32_t pop, const leea_params* p, uint64_t seed, uint32_t gen)
-{
-    SelectArgs a{};
-    int32_t ne, nc, nm, pl;
-    counts_of(pop, p, &ne, &nc, &nm, &pl);
-    a.pop = pop;
-    a.n_elite = ne;
-    a.n_cross = nc;
-    a.pool = pl;
-    a.sel_op = p->sel_op;
-    a.tour_k = p->tour_k;
-    a.seed = seed;
-    a.gen = gen;
-    return a;
-}
-
 leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_dev,
                         const int32_t* order_dev, uint64_t seed, uint32_t gen, int32_t* par1_dev,
                         int32_t* par2_dev, int32_t* kind_dev, float* f_inh_dev, void* stream)
@@ -383,22 +399,6 @@ leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_de
                                 static_cast<cudaStream_t>(stream)),
                   "select kernel");
     return LEEA_OK;
-}
-
-static BreedArgs breed_args(int32_t pop, const NetLayout& net, const leea_params* p, uint64_t seed,
-                            uint32_t gen)
-{
-    BreedArgs a{};
-    a.pop = pop;
-    a.c = net.c;
-    a.c_pad = net.c_pad;
-    a.xo_op = p->xo_op;
-    a.thr_xo = threshold16(static_cast<double>(p->xo_gene_p));
-    a.thr_mut = threshold16(static_cast<double>(p->mut_rate));
-    a.sigma = p->sigma;
-    a.seed = seed;
-    a.gen = gen;
-    return a;
 }
 
 leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_params* p,

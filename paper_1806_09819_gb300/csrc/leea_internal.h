@@ -101,6 +101,30 @@ cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t*
 cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t* par1,
                          const int32_t* par2, const int32_t* kind, float* children,
                          unsigned int* status, cudaStream_t stream);
+
+// Many runs at once (the batching form).  Each kernel reads the generation g
+// from gen_dev, so that a captured CUDA graph replays with the next g.
+struct SelectRun {
+    SelectArgs a;  // a.gen unused
+    const float* f_adj;
+    int32_t *order, *par1, *par2, *kind;
+    float* f_inh;
+};
+// CTA r: rank + select of run r (pop <= 4096).
+cudaError_t launch_rank_select_runs(const SelectRun* runs_dev, int32_t n_runs, const uint32_t* gen_dev,
+                                    cudaStream_t stream);
+struct BreedRun {
+    BreedArgs a;         // a.gen unused
+    const float* parents;
+    const int32_t *par1, *par2, *kind;
+    float* children;
+    int32_t chunks;      // work items per child
+    int64_t item0;       // first of the run's pop * chunks items in the global list
+};
+cudaError_t launch_breed_runs(const BreedRun* runs_dev, int32_t n_runs, int64_t n_items, const uint32_t* gen_dev,
+                              unsigned int* status, cudaStream_t stream);
+// Items (chunks of genes) per child of a net with c_pad padded genes.
+int32_t breed_chunks(int64_t c_pad);
 // Precision form: shadows of W1 for a whole population from its FP32 master
 // (exact max |W1| per individual, FP8 exponents from it).
 cudaError_t launch_make_shadow(int32_t pop, int32_t k, int32_t h, int64_t c_pad, const float* pop_dev,

@@ -145,10 +145,10 @@ cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t
 constexpr int kFusedThreads = 1024;
 constexpr int kFusedMaxPop = 4096;
 
-__global__ void __launch_bounds__(kFusedThreads, 1)
-rank_select_kernel(SelectArgs a, const float* __restrict__ f_adj, int32_t* __restrict__ order_out,
-                   int32_t* __restrict__ par1, int32_t* __restrict__ par2, int32_t* __restrict__ kind,
-                   float* __restrict__ f_inh)
+__device__ __forceinline__ void rank_select_body(const SelectArgs& a, const float* __restrict__ f_adj,
+                                                 int32_t* __restrict__ order_out, int32_t* __restrict__ par1,
+                                                 int32_t* __restrict__ par2, int32_t* __restrict__ kind,
+                                                 float* __restrict__ f_inh)
 {
     __shared__ uint64_t keys[kFusedMaxPop];
     __shared__ int32_t order[kFusedMaxPop];
@@ -181,6 +181,25 @@ rank_select_kernel(SelectArgs a, const float* __restrict__ f_adj, int32_t* __res
     for (int j = threadIdx.x; j < a.pop; j += kFusedThreads) select_child(a, f_adj, order, j, par1, par2, kind, f_inh);
 }
 
+__global__ void __launch_bounds__(kFusedThreads, 1)
+rank_select_kernel(SelectArgs a, const float* __restrict__ f_adj, int32_t* __restrict__ order_out,
+                   int32_t* __restrict__ par1, int32_t* __restrict__ par2, int32_t* __restrict__ kind,
+                   float* __restrict__ f_inh)
+{
+    rank_select_body(a, f_adj, order_out, par1, par2, kind, f_inh);
+}
+
+// Many runs at once: CTA r ranks and selects run r; the generation is read
+// from device memory (so that a captured graph can be replayed).
+__global__ void __launch_bounds__(kFusedThreads, 1)
+rank_select_runs_kernel(const SelectRun* __restrict__ runs, const uint32_t* __restrict__ gen_dev)
+{
+    const SelectRun& r = runs[blockIdx.x];
+    SelectArgs a = r.a;
+    a.gen = *gen_dev;
+    rank_select_body(a, r.f_adj, r.order, r.par1, r.par2, r.kind, r.f_inh);
+}
+
 cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t* order, int32_t* par1, int32_t* par2,
                                int32_t* kind, float* f_inh, cudaStream_t stream)
 {
@@ -190,6 +209,13 @@ cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t*
         return launch_select(a, f_adj, order, par1, par2, kind, f_inh, stream);
     }
     rank_select_kernel<<<1, kFusedThreads, 0, stream>>>(a, f_adj, order, par1, par2, kind, f_inh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rank_select_runs(const SelectRun* runs_dev, int32_t n_runs, const uint32_t* gen_dev,
+                                    cudaStream_t stream)
+{
+    rank_select_runs_kernel<<<n_runs, kFusedThreads, 0, stream>>>(runs_dev, gen_dev);
     return cudaGetLastError();
 }
 

@@ -32,6 +32,11 @@ class LeeaError(RuntimeError):
         self.status = status
 
 
+class leea_run_spec(ctypes.Structure):
+    _fields_ = [("pop", ctypes.c_int32), ("hidden", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("chunk", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
 class leea_params(ctypes.Structure):
     _fields_ = [
         ("xo_op", ctypes.c_int32), ("xo_gene_p", ctypes.c_float),
@@ -120,6 +125,25 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_state_num_params": ([vp], i64),
         "leea_profile_enable": [vp, i32],
         "leea_profile_read": [vp, vp, vp],
+        "leea_multi_create": [i32, vp, i32, i32, P(leea_params), vp, P(vp)],
+        "leea_multi_layout": [vp, vp, vp, vp, vp],
+        "leea_multi_run_shape": [vp, i32, vp, vp, vp],
+        "leea_multi_batch_buffers": [vp, P(vp), P(vp)],
+        "leea_multi_generation_u8": [vp, vp, f32, vp],
+        "leea_multi_generation_u8_host": [vp, vp, f32, vp],
+        "leea_multi_fitness": [vp, vp, vp],
+        "leea_multi_raw_fitness": [vp, vp],
+        "leea_multi_get_population": [vp, i32, vp],
+        "leea_multi_set_population": [vp, i32, vp],
+        "leea_multi_set_fitness": [vp, vp],
+        "leea_multi_set_generation": [vp, u32, i32],
+        "leea_multi_get_selection": [vp, i32, vp, vp, vp, vp, vp],
+        "leea_multi_get_shadow": [vp, i32, vp, vp, vp],
+        "leea_multi_generation_index": ([vp], u32),
+        "leea_multi_profile_enable": [vp, i32],
+        "leea_multi_profile_read": [vp, vp, vp],
+        "leea_multi_destroy": ([vp], None),
+        "leea_tune_shadow_eval": [i32, i32, i32, i32, i32, i32, i32, i32, P(f32)],
         "leea_last_error": ([], ctypes.c_char_p),
         "leea_destroy": ([vp], None),
     }
@@ -144,7 +168,13 @@ def exported_symbols() -> list[str]:
             "leea_get_selection", "leea_generation_index", "leea_state_num_params",
             "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy",
             "leea_shadow_stride", "leea_make_shadow", "leea_shadow_scratch_bytes", "leea_evaluate_shadow_u8",
-            "leea_get_shadow", "leea_evaluate_shadow_u8_noalloc"]
+            "leea_get_shadow", "leea_evaluate_shadow_u8_noalloc",
+            "leea_multi_create", "leea_multi_layout", "leea_multi_run_shape", "leea_multi_batch_buffers",
+            "leea_multi_generation_u8", "leea_multi_generation_u8_host", "leea_multi_fitness",
+            "leea_multi_raw_fitness", "leea_multi_get_population", "leea_multi_set_population",
+            "leea_multi_set_fitness", "leea_multi_set_generation", "leea_multi_get_selection",
+            "leea_multi_get_shadow", "leea_multi_generation_index", "leea_multi_profile_enable",
+            "leea_multi_profile_read", "leea_multi_destroy", "leea_tune_shadow_eval"]
 
 
 def _check(rc: int) -> None:
@@ -411,3 +441,144 @@ class LeeaState:
         n = np.zeros(NUM_STAGES, dtype=np.int64)
         _check(self.lib.leea_profile_read(self._h, _hp(ms), _hp(n)))
         return {STAGES[k]: (float(ms[k]), int(n[k])) for k in range(NUM_STAGES)}
+
+
+# ---- the batching form -------------------------------------------------------------
+@dataclass
+class RunSpec:
+    """One run of the batching form (fields of ``leea_run_spec``)."""
+    pop: int
+    hidden: int
+    batch: int
+    chunk: int = 0
+    seed: int = 0
+
+
+class MultiRun:
+    """Many independent runs advanced together (``leea_multi_create`` ... ``leea_multi_destroy``).
+    Minibatches and per-individual results are packed over the runs (see ``layout``)."""
+
+    def __init__(self, specs, d_in: int, d_out: int, prm: Params, stream=None):
+        self.lib = load_library()
+        self.specs = list(specs)
+        self.n_runs = len(self.specs)
+        self.d_in, self.d_out = d_in, d_out
+        arr = (leea_run_spec * self.n_runs)(*[leea_run_spec(sp.pop, sp.hidden, sp.batch, sp.chunk, sp.seed)
+                                               for sp in self.specs])
+        self._cp = prm.c_struct()
+        h = ctypes.c_void_p()
+        _check(self.lib.leea_multi_create(self.n_runs, ctypes.cast(arr, ctypes.c_void_p), d_in, d_out,
+                                          ctypes.byref(self._cp), _stream(stream), ctypes.byref(h)))
+        self._h = h
+        self.batch_off = np.zeros(self.n_runs, dtype=np.int64)
+        self.pop_off = np.zeros(self.n_runs, dtype=np.int64)
+        tr, tp = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.leea_multi_layout(h, _hp(self.batch_off), _hp(self.pop_off), ctypes.byref(tr),
+                                          ctypes.byref(tp)))
+        self.total_rows, self.total_pop = tr.value, tp.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            self.lib.leea_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run_shape(self, run: int):
+        """(chunk, n_chunks, m_tiles) of run `run`'s evaluation."""
+        v = [ctypes.c_int32() for _ in range(3)]
+        _check(self.lib.leea_multi_run_shape(self._h, run, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def batch_buffers(self):
+        x, y = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(self.lib.leea_multi_batch_buffers(self._h, ctypes.byref(x), ctypes.byref(y)))
+        return x.value, y.value
+
+    def generation_u8(self, x_dev, y_dev, x_div: float = 255.0) -> None:
+        _check(self.lib.leea_multi_generation_u8(self._h, _dptr(x_dev), float(x_div), _dptr(y_dev)))
+
+    def generation_u8_host(self, x_host, y_host, x_div: float = 255.0) -> None:
+        xh = x_host if not isinstance(x_host, np.ndarray) else np.ascontiguousarray(x_host, dtype=np.uint8)
+        yh = y_host if not isinstance(y_host, np.ndarray) else np.ascontiguousarray(y_host, dtype=np.int32)
+        xp = _hp(xh) if isinstance(xh, np.ndarray) else xh.data_ptr()
+        yp = _hp(yh) if isinstance(yh, np.ndarray) else yh.data_ptr()
+        _check(self.lib.leea_multi_generation_u8_host(self._h, xp, float(x_div), yp))
+
+    def fitness(self, with_correct: bool = False):
+        f = np.empty(self.total_pop, dtype=np.float32)
+        cor = np.empty(self.total_pop, dtype=np.int32) if with_correct else None
+        _check(self.lib.leea_multi_fitness(self._h, _hp(f), None if cor is None else _hp(cor)))
+        return (f, cor) if with_correct else f
+
+    def raw_fitness(self) -> np.ndarray:
+        f = np.empty(self.total_pop, dtype=np.float32)
+        _check(self.lib.leea_multi_raw_fitness(self._h, _hp(f)))
+        return f
+
+    def run_slice(self, run: int) -> slice:
+        return slice(int(self.pop_off[run]), int(self.pop_off[run]) + self.specs[run].pop)
+
+    def rows_slice(self, run: int) -> slice:
+        return slice(int(self.batch_off[run]), int(self.batch_off[run]) + self.specs[run].batch)
+
+    def num_params(self, run: int) -> int:
+        return leea_num_params([self.d_in, self.specs[run].hidden, self.d_out])
+
+    def get_population(self, run: int) -> np.ndarray:
+        out = np.empty((self.specs[run].pop, self.num_params(run)), dtype=np.float32)
+        _check(self.lib.leea_multi_get_population(self._h, run, _hp(out)))
+        return out
+
+    def set_population(self, run: int, popv) -> None:
+        a = np.ascontiguousarray(np.asarray(popv, dtype=np.float32))
+        assert a.shape == (self.specs[run].pop, self.num_params(run))
+        _check(self.lib.leea_multi_set_population(self._h, run, _hp(a)))
+
+    def set_fitness(self, f_adj) -> None:
+        a = np.ascontiguousarray(np.asarray(f_adj, dtype=np.float32))
+        assert a.shape == (self.total_pop,)
+        _check(self.lib.leea_multi_set_fitness(self._h, _hp(a)))
+
+    def set_generation(self, gen: int, evaluated: bool) -> None:
+        _check(self.lib.leea_multi_set_generation(self._h, gen, int(evaluated)))
+
+    def get_selection(self, run: int):
+        n = self.specs[run].pop
+        ints = [np.empty(n, dtype=np.int32) for _ in range(4)]
+        f_inh = np.empty(n, dtype=np.float32)
+        _check(self.lib.leea_multi_get_selection(self._h, run, *[_hp(a) for a in ints], _hp(f_inh)))
+        return (*ints, f_inh)
+
+    def get_shadow(self, run: int, precision: int):
+        sp = self.specs[run]
+        sh = np.empty((sp.pop, leea_shadow_stride([self.d_in, sp.hidden, self.d_out], precision)), dtype=np.uint8)
+        se = np.empty(sp.pop, dtype=np.int32)
+        am = np.empty(sp.pop, dtype=np.float32)
+        _check(self.lib.leea_multi_get_shadow(self._h, run, _hp(sh), _hp(se), _hp(am)))
+        return sh, se, am
+
+    @property
+    def gen(self) -> int:
+        return int(self.lib.leea_multi_generation_index(self._h))
+
+    def profile_enable(self, on: bool = True) -> None:
+        _check(self.lib.leea_multi_profile_enable(self._h, int(on)))
+
+    def profile_read(self):
+        ms = np.zeros(NUM_STAGES, dtype=np.float64)
+        n = np.zeros(NUM_STAGES, dtype=np.int64)
+        _check(self.lib.leea_multi_profile_read(self._h, _hp(ms), _hp(n)))
+        return {STAGES[k]: (float(ms[k]), int(n[k])) for k in range(NUM_STAGES)}
+
+
+def leea_tune_shadow_eval(precision: int, d_in: int, hidden: int, d_out: int, batch: int, pop: int, chunk: int,
+                          reps: int = 5) -> float:
+    ms = ctypes.c_float()
+    _check(load_library().leea_tune_shadow_eval(precision, d_in, hidden, d_out, batch, pop, chunk, reps,
+                                                ctypes.byref(ms)))
+    return float(ms.value)

@@ -100,3 +100,15 @@ def test_oracle_and_library_share_no_code():
     here = os.path.dirname(os.path.abspath(__file__))
     otext = open(os.path.join(here, "..", "oracle", "leea_oracle.c")).read()
     assert "philox.cuh" not in otext and "leea.h\"" not in otext
+
+
+def test_autotune_candidates():
+    from paper_1806_09819_gb300 import autotune
+    # 784 inputs: the batch tile takes 400 TMEM columns in either precision, leaving 112
+    assert autotune.max_chunk(1, 784) == 112 and autotune.max_chunk(2, 784) == 112
+    assert autotune.max_chunk(1, 64) == 128
+    assert autotune.effective_chunk(256, 112) == 96      # 3 equal chunks
+    assert autotune.effective_chunk(112, 112) == 112
+    assert autotune.effective_chunk(48, 112) == 48
+    c = autotune.candidates(1, 784, 256)
+    assert c[0] == 96 and all(16 <= x <= 112 and x % 16 == 0 for x in c) and len(set(c)) == len(c)
