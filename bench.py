@@ -8,12 +8,16 @@ breed, evaluate).  The population (2 x 356 MB) is larger than L2, so no flush
 is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--config plain|precision-bf16|precision-fp8]
+                    [--config plain|precision-bf16|precision-fp8|batching]
 
 --config precision-* measures the precision form instead (P = 4096 nets
 784-112-10, batch 256, BF16 or FP8-e4m3 shadows of W1 with FP32 accumulation
 and FP32 masters) and reports the shadow fitness against the FP64 evaluation
-of the masters on a sample of the final population.
+of the masters on a sample of the final population.  --config batching
+measures the batching form: 64 independent runs (P in [50, 2000], h in
+[16, 256], batch in [8, 512], log-uniform from a fixed seed; BF16 shadows)
+advanced together, one CUDA graph per generation, tile shapes from the
+autotuner; the value counts every run's generations.
 
 N > 1 (under torch.distributed.run) runs N independent replicas, one per GPU
 (the generation's selection needs every parent, so a run does not shard);
@@ -44,7 +48,27 @@ PRECISION_WORKLOAD = ("P=4096 MLPs 784-112-10, batch 256 synthetic 28x28 images,
                       "accumulation, FP32 masters); operators as the plain workload")
 CONFIGS = {"plain": dict(pop=1000, batch=100, precision=0),
            "precision-bf16": dict(pop=4096, batch=256, precision=1),
-           "precision-fp8": dict(pop=4096, batch=256, precision=2)}
+           "precision-fp8": dict(pop=4096, batch=256, precision=2),
+           "batching": dict(runs=64, pop=(50, 2000), hidden=(16, 256), batch=(8, 512), precision=1, seed=4242)}
+BATCHING_WORKLOAD = ("64 independent LEEA runs of 784-h-10 MLPs, P in [50,2000], h in [16,256] (multiple of 16), "
+                     "batch in [8,512], log-uniform (seed 4242); BF16 shadows of W1, FP32 masters; operators as the "
+                     "plain workload; one CUDA graph per generation, hidden chunks from the autotuner")
+
+
+def batching_specs(cfg: dict):
+    """The batching workload's runs: (pop, hidden, batch, seed), log-uniform from a fixed seed."""
+    import numpy as np
+    rng = np.random.default_rng(cfg["seed"])
+
+    def logu(lo, hi):
+        return float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+    out = []
+    for r in range(cfg["runs"]):
+        pop = int(round(logu(*cfg["pop"])))
+        hidden = int(min(cfg["hidden"][1], max(cfg["hidden"][0], 16 * round(logu(*cfg["hidden"]) / 16))))
+        batch = int(round(logu(*cfg["batch"])))
+        out.append((pop, hidden, batch, 5000 + r))
+    return out
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ_NOMINAL = 152, 128, 2070.0
 STAGES = ("select", "breed", "evaluate")
 
@@ -277,6 +301,132 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def run_batching(args, rank: int, world: int, local_rank: int):
+    """The batching form: every run's generations per second, one graph per generation."""
+    import numpy as np
+    import torch
+    from paper_1806_09819_gb300 import autotune
+    from paper_1806_09819_gb300 import build as B
+    from paper_1806_09819_gb300 import leea, synthetic
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = dist_init(world, True)
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(dist, dev)
+    B.build()
+    leea.load_library()
+    cfg = CONFIGS["batching"]
+    steps, warmup = args.steps, args.warmup
+    runs = batching_specs(cfg)
+    specs = [leea.RunSpec(pop=p, hidden=h, batch=b, seed=s + 100 * rank) for p, h, b, s in runs]
+    specs, _ = autotune.tune(specs, DIMS[0], DIMS[2], cfg["precision"])
+    prm = leea.Params(**PARAMS, precision=cfg["precision"])
+    stream = torch.cuda.current_stream(dev)
+    m = leea.MultiRun(specs, DIMS[0], DIMS[2], prm, stream=stream)
+    # a pool of packed minibatches (each run's batch drawn from the synthetic training set)
+    (xtr, ytr), _ = synthetic.dataset(n_train=60000, n_test=1)
+    lv = synthetic.to_levels(xtr)
+    n_pool = 16
+    rng = np.random.default_rng(synthetic.BATCH_SEED + rank)
+    xs = np.empty((n_pool, m.total_rows, DIMS[0]), dtype=np.uint8)
+    ys = np.empty((n_pool, m.total_rows), dtype=np.int32)
+    for k in range(n_pool):
+        for r, sp in enumerate(specs):
+            idx = rng.choice(len(ytr), size=sp.batch, replace=False)
+            xs[k, m.rows_slice(r)] = lv[idx]
+            ys[k, m.rows_slice(r)] = ytr[idx]
+    xd, yd = torch.from_numpy(xs).to(dev), torch.from_numpy(ys).to(dev)
+    for k in range(warmup + 1):
+        m.generation_u8(xd[k % n_pool], yd[k % n_pool])
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(_gpu_id_for(local_rank))
+    clocks.start()
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    mark = clocks.mark()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(steps):
+        m.generation_u8(xd[k % n_pool], yd[k % n_pool])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist, dev)
+    clk = clocks.stop(mark)
+    ms_max = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
+    n_runs = len(specs)
+    gen_per_s = world * n_runs * steps / (ms_max / 1000.0)
+    samples_per_gen = sum(sp.pop * sp.batch for sp in specs)
+
+    # per-stage times: direct launches between events (same kernels as the graph)
+    prof_steps = min(steps, 200)
+    m.profile_enable(True)
+    for k in range(prof_steps):
+        m.generation_u8(xd[k % n_pool], yd[k % n_pool])
+    prof = m.profile_read()
+    m.profile_enable(False)
+
+    # end to end: packed host minibatch in, packed fitness out
+    e2e_steps = max(10, min(steps, 500))
+    xh = torch.from_numpy(xs).pin_memory()
+    yh = torch.from_numpy(ys).pin_memory()
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    f_host = None
+    for k in range(e2e_steps):
+        m.generation_u8_host(xh[k % n_pool], yh[k % n_pool])
+        f_host = m.fitness()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": world * n_runs * e2e_steps / t_e2e, "unit": "run-generations/s",
+           "h2d_bytes_per_step": int(xs[0].nbytes + ys[0].nbytes), "d2h_bytes_per_step": int(f_host.nbytes),
+           "steps": e2e_steps}
+
+    hbm_peak, _, peak_src = _peaks()
+    breed_b = evaluate_b = 0.0
+    for sp in specs:
+        dims = [DIMS[0], sp.hidden, DIMS[2]]
+        c = leea.leea_num_params(dims)
+        n_e, n_c, n_m, _ = leea.leea_counts(sp.pop, leea.Params(**PARAMS))
+        shadow = DIMS[0] * sp.hidden * 2
+        breed_b += 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + shadow * sp.pop
+        evaluate_b += (shadow + 4.0 * (c - DIMS[0] * sp.hidden)) * sp.pop
+    work = {"breed": breed_b / 1e9, "evaluate": evaluate_b / 1e9}
+    kernels = {}
+    tot = sum(v[0] for v in prof.values())
+    for name in STAGES:
+        ms, launches = prof[name]
+        per = ms / max(1, launches)
+        entry = {"launches": launches, "ms_per_launch": per, "share": ms / max(1e-12, tot)}
+        if name in work:
+            ach = work[name] / (per / 1000.0)
+            entry.update({"bound": "hbm", "achieved": ach, "unit": "GB/s", "peak": hbm_peak, "frac": ach / hbm_peak})
+        kernels[name] = entry
+    dom = max(("breed", "evaluate"), key=lambda n: prof[n][0])
+    kd = kernels[dom]
+    line = {"metric": "run-generations/sec of 64 uneven LEEA runs advanced together (batching form)",
+            "value": gen_per_s, "unit": "run-generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 (f32 accumulate)", "data": "synthetic",
+            "config": {"workload": BATCHING_WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "runs": [{"pop": sp.pop, "hidden": sp.hidden, "batch": sp.batch, "chunk": sp.chunk}
+                                for sp in specs],
+                       "l2": "inputs larger than L2 (populations of all runs, 2 buffers), no flush"},
+            "network_samples_per_sec": gen_per_s / n_runs * samples_per_gen,
+            "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values()) + prof_steps),
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": kd["achieved"], "peak": kd["peak"],
+                         "unit": "GB/s", "frac": kd["frac"], "traffic": None,
+                         "peak_source": f"{peak_src} (HBM copy)"},
+            "kernels": kernels, "clocks": clk}
+    m.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_native(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -295,6 +445,8 @@ def run_native(args, rank: int, world: int, local_rank: int):
     steps, warmup = args.steps, args.warmup
     cfg = CONFIGS[args.config]
     pop, batch, precision = cfg["pop"], cfg["batch"], cfg["precision"]
+    if args.pop or args.batch:  # a smaller case of the same kernels, for profiling; not a bench value
+        pop, batch = args.pop or pop, args.batch or batch
     (xtr, ytr), _ = synthetic.dataset(n_train=60000, n_test=1)
     u8 = args.input == "u8" or precision > 0
     if u8:  # the images as their 8-bit levels k (x = k / 255), as MNIST stores them
@@ -413,6 +565,8 @@ def run_native(args, rank: int, world: int, local_rank: int):
 
     pname = {1: "BF16", 2: "FP8-e4m3 (per-individual power-of-two scale)"}.get(precision)
     workload = PRECISION_WORKLOAD.format(name=pname) if precision else WORKLOAD
+    if (pop, batch) != (cfg["pop"], cfg["batch"]):
+        workload = f"PROFILING OVERRIDE P={pop}, batch {batch} (not the benchmark workload): " + workload
     eval_kernel = ("tcgen05 " + {1: "kind::f16 on BF16 shadows", 2: "kind::f8f6f4 on FP8 shadows, 2 input pieces"}[
         precision] + ", batch in TMEM" if precision else
                    (("tcgen05 BF16 exact pieces, batch in TMEM" if u8 else "tcgen05 3xTF32") if tensor_eval
@@ -456,7 +610,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eval-path", type=int, default=0, help="0 auto (tensor cores), 1 CUDA-core FP32, 2 tensor")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="plain",
-                    help="plain: the headline FP32 workload; precision-*: P=4096, batch 256, BF16/FP8 shadows")
+                    help="plain: the headline FP32 workload; precision-*: P=4096, batch 256, BF16/FP8 shadows; "
+                         "batching: 64 uneven runs together")
+    ap.add_argument("--pop", type=int, default=0, help="override the population size (small profiling cases)")
+    ap.add_argument("--batch", type=int, default=0, help="override the batch size (small profiling cases)")
     ap.add_argument("--input", choices=["u8", "f32"], default="u8",
                     help="minibatch as 8-bit levels (x = k/255, the images' own encoding) or as float32")
     args = ap.parse_args()
@@ -465,6 +622,8 @@ def main():
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "batching":
+        run_batching(args, rank, world, local_rank)
     else:
         run_native(args, rank, world, local_rank)
 
