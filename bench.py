@@ -74,7 +74,10 @@ STAGES = ("select", "breed", "evaluate")
 
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
-TRAFFIC = {}
+TRAFFIC = {
+    "breed": {"bytes_per_launch": 711.07e6, "src_sha": "2c5af01472ae1ede", "capture": "P=1000 plain workload"},
+    "evaluate": {"bytes_per_launch": 359.41e6, "src_sha": "70524052f2d2df6f", "capture": "P=1000 plain workload"},
+}
 
 
 def _peaks():
@@ -551,7 +554,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
     src = {"breed": "leea_breed.cu",
            "evaluate": (("leea_eval_shadow.cu" if precision else "leea_eval_u8.cu") if u8 else "leea_eval_tc.cu")
            if tensor_eval else "leea_eval_simt.cu"}[dom]
-    tr = TRAFFIC.get(dom)
+    tr = TRAFFIC.get(dom) if (args.config, pop, batch, u8) == ("plain", POP, BATCH, True) else None
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == _src_sha(src) else None
     roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
