@@ -140,6 +140,21 @@ def lib() -> ctypes.CDLL:
         L.leea_cpu_generation_index.restype = u32
         L.leea_cpu_destroy.argtypes = [vp]
         L.leea_cpu_destroy.restype = None
+        L.leea_cpu_mlp_num_params.argtypes = [i32, i32, i32]
+        L.leea_cpu_mlp_num_params.restype = i64
+        L.leea_cpu_mlp_init.argtypes = [i32, i32, i32, u64, vp]
+        L.leea_cpu_mlp_forward.argtypes = [i32, i32, i32, i32, vp, vp, vp]
+        L.leea_cpu_mlp_loss_grad.argtypes = [i32, i32, i32, i32, vp, vp, vp, vp, vp]
+        L.leea_cpu_adam.argtypes = [i64, vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl]
+        L.leea_cpu_select_recipes.argtypes = [i32, P(_CParams), vp, vp, u64, u32, i32, vp, vp, vp, vp, vp]
+        L.leea_cpu_breed_entities.argtypes = [i32, vp, i32, P(_CParams), u64, u32, vp, vp, vp, vp, vp, i32, vp]
+        L.leea_cpu_recipe_stats.argtypes = [vp, i32, P(_CParams), u64, u32, vp, vp, i32, vp, vp]
+        L.leea_cpu_descriptors.argtypes = [i32, vp, i32, P(_CParams), u64, u32, vp, vp, vp, vp, vp, vp, vp, i32,
+                                           vp, i32, vp]
+        for name in ("leea_cpu_mlp_init", "leea_cpu_mlp_forward", "leea_cpu_mlp_loss_grad", "leea_cpu_adam",
+                     "leea_cpu_select_recipes", "leea_cpu_breed_entities", "leea_cpu_recipe_stats",
+                     "leea_cpu_descriptors"):
+            getattr(L, name).restype = ctypes.c_int
         for name in ("leea_cpu_counts", "leea_cpu_init", "leea_cpu_evaluate", "leea_cpu_rank",
                      "leea_cpu_select", "leea_cpu_breed", "leea_cpu_inherit", "leea_cpu_create",
                      "leea_cpu_generation", "leea_cpu_fitness", "leea_cpu_best_params",
@@ -396,3 +411,105 @@ class State:
         _check(lib().leea_cpu_get_selection(self._h, *[_ptr(a) for a in arrs], _ptr(f_inh)),
                "get_selection")
         return (*arrs, f_inh)
+
+
+# ---- surrogate form (no counterpart in the paper) --------------------------------
+RECIPE_ENTITY0 = 0x40000000
+TAG_SURR_INIT = 6
+
+
+def _u32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.uint32))
+
+
+def mlp_num_params(d_in: int, h1: int, h2: int) -> int:
+    return int(lib().leea_cpu_mlp_num_params(d_in, h1, h2))
+
+
+def mlp_init(d_in: int, h1: int, h2: int, seed: int) -> np.ndarray:
+    theta = np.empty(mlp_num_params(d_in, h1, h2), dtype=np.float64)
+    _check(lib().leea_cpu_mlp_init(d_in, h1, h2, seed, _ptr(theta)), "mlp_init")
+    return theta
+
+
+def mlp_forward(theta, x, d_in: int, h1: int, h2: int) -> np.ndarray:
+    xv = _f64(x).reshape(-1, d_in)
+    y = np.empty(xv.shape[0], dtype=np.float64)
+    _check(lib().leea_cpu_mlp_forward(xv.shape[0], d_in, h1, h2, _ptr(_f64(theta)), _ptr(xv), _ptr(y)),
+           "mlp_forward")
+    return y
+
+
+def mlp_loss_grad(theta, x, t, d_in: int, h1: int, h2: int):
+    """(mean squared error, gradient) of the MLP's predictions against t."""
+    xv = _f64(x).reshape(-1, d_in)
+    tv = _f64(t)
+    th = _f64(theta)
+    grad = np.empty_like(th)
+    loss = ctypes.c_double()
+    _check(lib().leea_cpu_mlp_loss_grad(xv.shape[0], d_in, h1, h2, _ptr(th), _ptr(xv), _ptr(tv),
+                                        ctypes.byref(loss), _ptr(grad)), "mlp_loss_grad")
+    return float(loss.value), grad
+
+
+def adam(theta, grad, m, v, step: int, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+         eps: float = 1e-8):
+    """One Adam step; returns new (theta, m, v)."""
+    th, mm, vv = _f64(theta).copy(), _f64(m).copy(), _f64(v).copy()
+    _check(lib().leea_cpu_adam(th.shape[0], _ptr(th), _ptr(_f64(grad)), _ptr(mm), _ptr(vv), step, lr, beta1, beta2,
+                               eps), "adam")
+    return th, mm, vv
+
+
+def select_recipes(prm: Params, f_adj, order, seed: int, gen: int, mult: int):
+    """(par1, par2, kind, f_inh, entity) of the mult (n_C + n_M) recipes."""
+    f = _f64(f_adj)
+    pop = f.shape[0]
+    _, n_c, n_m, _ = counts(pop, prm)
+    n = mult * (n_c + n_m)
+    par1, par2, kind = (np.empty(n, dtype=np.int32) for _ in range(3))
+    f_inh = np.empty(n, dtype=np.float64)
+    ent = np.empty(n, dtype=np.uint32)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_select_recipes(pop, ctypes.byref(cp), _ptr(f), _ptr(_i32(order)), seed, gen, mult,
+                                         _ptr(par1), _ptr(par2), _ptr(kind), _ptr(f_inh), _ptr(ent)),
+           "select_recipes")
+    return par1, par2, kind, f_inh, ent
+
+
+def breed_entities(prm: Params, dims, seed: int, gen: int, parents, par1, par2, kind, entity) -> np.ndarray:
+    d = _dims(dims)
+    pv = _f64(parents)
+    n = len(kind)
+    out = np.empty((n, pv.shape[1]), dtype=np.float64)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_breed_entities(pv.shape[0], _ptr(d), len(d), ctypes.byref(cp), seed, gen, _ptr(pv),
+                                         _ptr(_i32(par1)), _ptr(_i32(par2)), _ptr(_i32(kind)), _ptr(_u32(entity)),
+                                         n, _ptr(out)), "breed_entities")
+    return out
+
+
+def recipe_stats(prm: Params, dims, seed: int, gen: int, kind, entity):
+    """(xo_frac, mut_norm) per recipe."""
+    d = _dims(dims)
+    n = len(kind)
+    xf, mn = np.empty(n, dtype=np.float64), np.empty(n, dtype=np.float64)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_recipe_stats(_ptr(d), len(d), ctypes.byref(cp), seed, gen, _ptr(_i32(kind)),
+                                       _ptr(_u32(entity)), n, _ptr(xf), _ptr(mn)), "recipe_stats")
+    return xf, mn
+
+
+def descriptors(prm: Params, dims, seed: int, gen: int, parents, f_adj, par1, par2, kind, f_inh, entity, probe_x):
+    """float64[n][5 + n_probe d_out] descriptors of the recipes."""
+    d = _dims(dims)
+    pv = _f64(parents)
+    px = _f64(probe_x).reshape(-1, int(d[0]))
+    n = len(kind)
+    out = np.empty((n, 5 + px.shape[0] * int(d[-1])), dtype=np.float64)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_descriptors(pv.shape[0], _ptr(d), len(d), ctypes.byref(cp), seed, gen, _ptr(pv),
+                                      _ptr(_f64(f_adj)), _ptr(_i32(par1)), _ptr(_i32(par2)), _ptr(_i32(kind)),
+                                      _ptr(_f64(f_inh)), _ptr(_u32(entity)), n, _ptr(px), px.shape[0], _ptr(out)),
+           "descriptors")
+    return out

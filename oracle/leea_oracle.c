@@ -451,6 +451,39 @@ int leea_cpu_select(int32_t pop, const leea_cpu_params* prm, const double* f_adj
 /*                draw hits mut_rate (every gene when mut_rate = 1)          */
 /*   elite:       unchanged copy                                             */
 /* ------------------------------------------------------------------------ */
+/* Child out (c genes) of the given kind from parents a, b, drawing from the
+ * streams of Philox entity `ent`. */
+static int breed_child(int64_t c, const leea_cpu_params* prm, uint64_t seed, uint32_t gen, uint32_t ent,
+                       int32_t kind, const double* a, const double* b, double* out)
+{
+    uint32_t thr_xo = leea_cpu_threshold16((double)prm->xo_gene_p);
+    uint32_t thr_mut = leea_cpu_threshold16((double)prm->mut_rate);
+    double sigma = (double)prm->sigma;
+    for (int64_t i = 0; i < c; i++) {
+        double v;
+        if (kind == LEEA_CPU_ELITE) {
+            v = a[i];
+        } else if (kind == LEEA_CPU_CROSSOVER) {
+            if (prm->xo_op == 0) {
+                uint32_t u = leea_cpu_draw16(seed, LEEA_CPU_TAG_XO, gen, ent, (uint32_t)i);
+                v = (u < thr_xo) ? b[i] : a[i];
+            } else {
+                v = 0.5 * (a[i] + b[i]);
+            }
+        } else if (kind == LEEA_CPU_MUTATION) {
+            uint32_t u = leea_cpu_draw16(seed, LEEA_CPU_TAG_MUTMASK, gen, ent, (uint32_t)i);
+            if (u < thr_mut)
+                v = a[i] + sigma * leea_cpu_normal(seed, LEEA_CPU_TAG_NORMAL, gen, ent, (uint32_t)i);
+            else
+                v = a[i];
+        } else {
+            return LEEA_CPU_EINVAL;
+        }
+        out[i] = v;
+    }
+    return LEEA_CPU_OK;
+}
+
 int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                    const leea_cpu_params* prm, uint64_t seed, uint32_t gen,
                    const double* parents, const int32_t* par1, const int32_t* par2,
@@ -460,36 +493,11 @@ int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
     if (c < 0 || pop <= 0 || !valid_params(prm) || !parents || !par1 || !par2 || !kind ||
         !children || j0 < 0 || j1 > pop || j0 > j1)
         return LEEA_CPU_EINVAL;
-    uint32_t thr_xo = leea_cpu_threshold16((double)prm->xo_gene_p);
-    uint32_t thr_mut = leea_cpu_threshold16((double)prm->mut_rate);
-    double sigma = (double)prm->sigma;
     for (int32_t j = j0; j < j1; j++) {
         if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
-        const double* a = parents + (int64_t)par1[j] * c;
-        const double* b = parents + (int64_t)par2[j] * c;
-        double* out = children + (int64_t)(j - j0) * c;
-        for (int64_t i = 0; i < c; i++) {
-            double v;
-            if (kind[j] == LEEA_CPU_ELITE) {
-                v = a[i];
-            } else if (kind[j] == LEEA_CPU_CROSSOVER) {
-                if (prm->xo_op == 0) {
-                    uint32_t u = leea_cpu_draw16(seed, LEEA_CPU_TAG_XO, gen, (uint32_t)j, (uint32_t)i);
-                    v = (u < thr_xo) ? b[i] : a[i];
-                } else {
-                    v = 0.5 * (a[i] + b[i]);
-                }
-            } else if (kind[j] == LEEA_CPU_MUTATION) {
-                uint32_t u = leea_cpu_draw16(seed, LEEA_CPU_TAG_MUTMASK, gen, (uint32_t)j, (uint32_t)i);
-                if (u < thr_mut)
-                    v = a[i] + sigma * leea_cpu_normal(seed, LEEA_CPU_TAG_NORMAL, gen, (uint32_t)j, (uint32_t)i);
-                else
-                    v = a[i];
-            } else {
-                return LEEA_CPU_EINVAL;
-            }
-            out[i] = v;
-        }
+        int rc = breed_child(c, prm, seed, gen, (uint32_t)j, kind[j], parents + (int64_t)par1[j] * c,
+                             parents + (int64_t)par2[j] * c, children + (int64_t)(j - j0) * c);
+        if (rc != LEEA_CPU_OK) return rc;
     }
     return LEEA_CPU_OK;
 }
@@ -658,4 +666,297 @@ int leea_cpu_get_selection(const leea_cpu_state* s, int32_t* order, int32_t* par
 uint32_t leea_cpu_generation_index(const leea_cpu_state* s)
 {
     return s ? s->gen : 0;
+}
+
+/* ======================================================================== */
+/* Surrogate form (a learned pre-screen of offspring; the paper has no       */
+/* counterpart).  Offspring are first "recipes" -- a kind, parents and the   */
+/* Philox entity whose streams make the child -- described by a feature     */
+/* vector, scored by a small MLP, and only the best are made and evaluated. */
+/* ======================================================================== */
+
+int64_t leea_cpu_mlp_num_params(int32_t d_in, int32_t h1, int32_t h2)
+{
+    if (d_in <= 0 || h1 <= 0 || h2 <= 0) return -1;
+    return (int64_t)h1 * d_in + h1 + (int64_t)h2 * h1 + h2 + h2 + 1;
+}
+
+/* Glorot-uniform weights, U(-a, a) with a = sqrt(6 / (fan_in + fan_out)),
+ * from Philox stream (SURR_INIT, generation 0, entity 0, draw = parameter
+ * index); zero biases. */
+int leea_cpu_mlp_init(int32_t d_in, int32_t h1, int32_t h2, uint64_t seed, double* theta)
+{
+    int64_t np = leea_cpu_mlp_num_params(d_in, h1, h2);
+    if (np < 0 || !theta) return LEEA_CPU_EINVAL;
+    const int32_t fin[3] = { d_in, h1, h2 }, fout[3] = { h1, h2, 1 };
+    int64_t i = 0;
+    for (int l = 0; l < 3; l++) {
+        double a = sqrt(6.0 / (double)(fin[l] + fout[l]));
+        for (int64_t k = 0; k < (int64_t)fin[l] * fout[l]; k++, i++) {
+            double u = leea_cpu_u01(leea_cpu_draw(seed, LEEA_CPU_TAG_SURR_INIT, 0, 0, (uint32_t)i));
+            theta[i] = a * (2.0 * u - 1.0);
+        }
+        for (int32_t k = 0; k < fout[l]; k++, i++) theta[i] = 0.0;
+    }
+    return LEEA_CPU_OK;
+}
+
+/* y_r = w3 . relu(W2 relu(W1 x_r + b1) + b2) + b3 for rows r < n of x[n][d_in];
+ * hidden activations are also returned when a1 / a2 are not NULL. */
+static void mlp_row(int32_t d_in, int32_t h1, int32_t h2, const double* theta, const double* x,
+                    double* a1, double* a2, double* y)
+{
+    const double* W1 = theta;
+    const double* b1 = W1 + (int64_t)h1 * d_in;
+    const double* W2 = b1 + h1;
+    const double* b2 = W2 + (int64_t)h2 * h1;
+    const double* w3 = b2 + h2;
+    const double b3 = w3[h2];
+    for (int32_t u = 0; u < h1; u++) {
+        double z = b1[u];
+        for (int32_t k = 0; k < d_in; k++) z += W1[(int64_t)u * d_in + k] * x[k];
+        a1[u] = z > 0.0 ? z : 0.0;
+    }
+    for (int32_t u = 0; u < h2; u++) {
+        double z = b2[u];
+        for (int32_t k = 0; k < h1; k++) z += W2[(int64_t)u * h1 + k] * a1[k];
+        a2[u] = z > 0.0 ? z : 0.0;
+    }
+    double out = b3;
+    for (int32_t u = 0; u < h2; u++) out += w3[u] * a2[u];
+    *y = out;
+}
+
+int leea_cpu_mlp_forward(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const double* theta,
+                         const double* x, double* y)
+{
+    if (n < 0 || leea_cpu_mlp_num_params(d_in, h1, h2) < 0 || !theta || (n > 0 && (!x || !y)))
+        return LEEA_CPU_EINVAL;
+    double* a1 = (double*)malloc(sizeof(double) * (size_t)h1);
+    double* a2 = (double*)malloc(sizeof(double) * (size_t)h2);
+    if (!a1 || !a2) {
+        free(a1);
+        free(a2);
+        return LEEA_CPU_ENOMEM;
+    }
+    for (int32_t r = 0; r < n; r++) mlp_row(d_in, h1, h2, theta, x + (int64_t)r * d_in, a1, a2, y + r);
+    free(a1);
+    free(a2);
+    return LEEA_CPU_OK;
+}
+
+/* Mean squared error L = (1/n) sum_r (y_r - t_r)^2 and dL/dtheta by the chain
+ * rule (backpropagation through the two ReLU layers). */
+int leea_cpu_mlp_loss_grad(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const double* theta,
+                           const double* x, const double* t, double* loss, double* grad)
+{
+    int64_t np = leea_cpu_mlp_num_params(d_in, h1, h2);
+    if (n <= 0 || np < 0 || !theta || !x || !t || !loss || !grad) return LEEA_CPU_EINVAL;
+    const double* W2 = theta + (int64_t)h1 * d_in + h1;
+    const double* w3 = W2 + (int64_t)h2 * h1 + h2;
+    double* gW1 = grad;
+    double* gb1 = gW1 + (int64_t)h1 * d_in;
+    double* gW2 = gb1 + h1;
+    double* gb2 = gW2 + (int64_t)h2 * h1;
+    double* gw3 = gb2 + h2;
+    double* gb3 = gw3 + h2;
+    for (int64_t i = 0; i < np; i++) grad[i] = 0.0;
+    double* a1 = (double*)malloc(sizeof(double) * (size_t)h1);
+    double* a2 = (double*)malloc(sizeof(double) * (size_t)h2);
+    double* d1 = (double*)malloc(sizeof(double) * (size_t)h1);
+    double* d2 = (double*)malloc(sizeof(double) * (size_t)h2);
+    if (!a1 || !a2 || !d1 || !d2) {
+        free(a1);
+        free(a2);
+        free(d1);
+        free(d2);
+        return LEEA_CPU_ENOMEM;
+    }
+    double sum = 0.0;
+    for (int32_t r = 0; r < n; r++) {
+        const double* xr = x + (int64_t)r * d_in;
+        double y;
+        mlp_row(d_in, h1, h2, theta, xr, a1, a2, &y);
+        double e = y - t[r];
+        sum += e * e;
+        double dy = 2.0 * e / (double)n;            /* dL/dy_r */
+        *gb3 += dy;
+        for (int32_t u = 0; u < h2; u++) {
+            gw3[u] += dy * a2[u];
+            d2[u] = a2[u] > 0.0 ? dy * w3[u] : 0.0;  /* dL/dz2_u */
+        }
+        for (int32_t k = 0; k < h1; k++) d1[k] = 0.0;
+        for (int32_t u = 0; u < h2; u++) {
+            gb2[u] += d2[u];
+            for (int32_t k = 0; k < h1; k++) {
+                gW2[(int64_t)u * h1 + k] += d2[u] * a1[k];
+                d1[k] += d2[u] * W2[(int64_t)u * h1 + k];
+            }
+        }
+        for (int32_t u = 0; u < h1; u++) {
+            double du = a1[u] > 0.0 ? d1[u] : 0.0;  /* dL/dz1_u */
+            gb1[u] += du;
+            for (int32_t k = 0; k < d_in; k++) gW1[(int64_t)u * d_in + k] += du * xr[k];
+        }
+    }
+    *loss = sum / (double)n;
+    free(a1);
+    free(a2);
+    free(d1);
+    free(d2);
+    return LEEA_CPU_OK;
+}
+
+/* One Adam step (Kingma & Ba, ICLR 2015) at step number `step` (1, 2, ...):
+ * m <- b1 m + (1 - b1) g;  v <- b2 v + (1 - b2) g^2;
+ * theta <- theta - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps). */
+int leea_cpu_adam(int64_t n_params, double* theta, const double* grad, double* m, double* v, int64_t step,
+                  double lr, double beta1, double beta2, double eps)
+{
+    if (n_params < 0 || step < 1 || !theta || !grad || !m || !v) return LEEA_CPU_EINVAL;
+    double c1 = 1.0 - pow(beta1, (double)step), c2 = 1.0 - pow(beta2, (double)step);
+    for (int64_t i = 0; i < n_params; i++) {
+        m[i] = beta1 * m[i] + (1.0 - beta1) * grad[i];
+        v[i] = beta2 * v[i] + (1.0 - beta2) * grad[i] * grad[i];
+        theta[i] -= lr * (m[i] / c1) / (sqrt(v[i] / c2) + eps);
+    }
+    return LEEA_CPU_OK;
+}
+
+/* The recipes of one generation: mult x (n_C + n_M) virtual offspring.
+ * Recipe r < mult n_C is a crossover, the rest mutations; recipe r draws
+ * its parents (as a child of that kind in leea_cpu_select) and later its
+ * genes from the streams of Philox entity LEEA_CPU_RECIPE_ENTITY0 + r. */
+int leea_cpu_select_recipes(int32_t pop, const leea_cpu_params* prm, const double* f_adj,
+                            const int32_t* order, uint64_t seed, uint32_t gen, int32_t mult,
+                            int32_t* par1, int32_t* par2, int32_t* kind, double* f_inh, uint32_t* entity)
+{
+    if (pop <= 0 || mult < 1 || !valid_params(prm) || !f_adj || !order || !par1 || !par2 || !kind || !f_inh ||
+        !entity)
+        return LEEA_CPU_EINVAL;
+    int32_t n_e, n_c, n_m, pool;
+    leea_cpu_counts(pop, prm, &n_e, &n_c, &n_m, &pool);
+    uint32_t k_draws = (prm->sel_op == 0) ? 1u : (uint32_t)prm->tour_k;
+    int32_t n_r = mult * (n_c + n_m);
+    for (int32_t r = 0; r < n_r; r++) {
+        uint32_t ent = LEEA_CPU_RECIPE_ENTITY0 + (uint32_t)r;
+        entity[r] = ent;
+        if (r < mult * n_c) {
+            kind[r] = LEEA_CPU_CROSSOVER;
+            par1[r] = pick_parent(pop, prm, f_adj, order, pool, seed, gen, ent, 0);
+            par2[r] = pick_parent(pop, prm, f_adj, order, pool, seed, gen, ent, k_draws);
+            f_inh[r] = 0.5 * (f_adj[par1[r]] + f_adj[par2[r]]);
+        } else {
+            kind[r] = LEEA_CPU_MUTATION;
+            par1[r] = pick_parent(pop, prm, f_adj, order, pool, seed, gen, ent, 0);
+            par2[r] = par1[r];
+            f_inh[r] = f_adj[par1[r]];
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
+/* n children with explicit Philox entities (leea_cpu_breed uses entity = j). */
+int leea_cpu_breed_entities(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm,
+                            uint64_t seed, uint32_t gen, const double* parents, const int32_t* par1,
+                            const int32_t* par2, const int32_t* kind, const uint32_t* entity, int32_t n,
+                            double* children)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || pop <= 0 || n < 0 || !valid_params(prm) || !parents || !par1 || !par2 || !kind || !entity ||
+        (n > 0 && !children))
+        return LEEA_CPU_EINVAL;
+    for (int32_t j = 0; j < n; j++) {
+        if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
+        int rc = breed_child(c, prm, seed, gen, entity[j], kind[j], parents + (int64_t)par1[j] * c,
+                             parents + (int64_t)par2[j] * c, children + (int64_t)j * c);
+        if (rc != LEEA_CPU_OK) return rc;
+    }
+    return LEEA_CPU_OK;
+}
+
+/* How far a recipe moves from its first parent: the fraction of the c genes
+ * a uniform crossover takes from parent 2 (0.5 for arithmetic crossover, 0
+ * for a mutation or an elite), and the length sigma ||z (.) m|| of the
+ * mutation step over the masked genes (0 unless a mutation). */
+int leea_cpu_recipe_stats(const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm, uint64_t seed,
+                          uint32_t gen, const int32_t* kind, const uint32_t* entity, int32_t n, double* xo_frac,
+                          double* mut_norm)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || n < 0 || !valid_params(prm) || (n > 0 && (!kind || !entity || !xo_frac || !mut_norm)))
+        return LEEA_CPU_EINVAL;
+    uint32_t thr_xo = leea_cpu_threshold16((double)prm->xo_gene_p);
+    uint32_t thr_mut = leea_cpu_threshold16((double)prm->mut_rate);
+    for (int32_t j = 0; j < n; j++) {
+        xo_frac[j] = 0.0;
+        mut_norm[j] = 0.0;
+        if (kind[j] == LEEA_CPU_CROSSOVER) {
+            if (prm->xo_op == 1) {
+                xo_frac[j] = 0.5;
+            } else {
+                int64_t hits = 0;
+                for (int64_t i = 0; i < c; i++)
+                    if (leea_cpu_draw16(seed, LEEA_CPU_TAG_XO, gen, entity[j], (uint32_t)i) < thr_xo) hits++;
+                xo_frac[j] = (double)hits / (double)c;
+            }
+        } else if (kind[j] == LEEA_CPU_MUTATION) {
+            double ss = 0.0;
+            for (int64_t i = 0; i < c; i++)
+                if (leea_cpu_draw16(seed, LEEA_CPU_TAG_MUTMASK, gen, entity[j], (uint32_t)i) < thr_mut) {
+                    double z = leea_cpu_normal(seed, LEEA_CPU_TAG_NORMAL, gen, entity[j], (uint32_t)i);
+                    ss += z * z;
+                }
+            mut_norm[j] = (double)prm->sigma * sqrt(ss);
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
+/* Descriptor of each recipe (row of width 5 + n_probe d_out):
+ * [f_adj of parent 1, f_adj of parent 2, f_inh, xo_frac, mut_norm, then the
+ *  logits of the child (made by breed_child) on the n_probe probe inputs,
+ *  sample-major].  Only two-layer nets (n_dims == 3). */
+int leea_cpu_descriptors(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm,
+                         uint64_t seed, uint32_t gen, const double* parents, const double* f_adj,
+                         const int32_t* par1, const int32_t* par2, const int32_t* kind, const double* f_inh,
+                         const uint32_t* entity, int32_t n, const double* probe_x, int32_t n_probe, double* desc)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || n_dims != 3 || pop <= 0 || n < 0 || n_probe <= 0 || !valid_params(prm) || !parents || !f_adj ||
+        !probe_x || (n > 0 && (!par1 || !par2 || !kind || !f_inh || !entity || !desc)))
+        return LEEA_CPU_EINVAL;
+    int32_t d_out = dims[2];
+    int64_t width = 5 + (int64_t)n_probe * d_out;
+    double* child = (double*)malloc(sizeof(double) * (size_t)c);
+    double* logits = (double*)malloc(sizeof(double) * (size_t)n_probe * d_out);
+    int32_t* y = (int32_t*)calloc((size_t)n_probe, sizeof(int32_t));
+    if (!child || !logits || !y) {
+        free(child);
+        free(logits);
+        free(y);
+        return LEEA_CPU_ENOMEM;
+    }
+    int rc = LEEA_CPU_OK;
+    for (int32_t j = 0; j < n && rc == LEEA_CPU_OK; j++) {
+        if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) {
+            rc = LEEA_CPU_EINVAL;
+            break;
+        }
+        double* row = desc + (int64_t)j * width;
+        row[0] = f_adj[par1[j]];
+        row[1] = f_adj[par2[j]];
+        row[2] = f_inh[j];
+        rc = leea_cpu_recipe_stats(dims, n_dims, prm, seed, gen, kind + j, entity + j, 1, row + 3, row + 4);
+        if (rc == LEEA_CPU_OK)
+            rc = breed_child(c, prm, seed, gen, entity[j], kind[j], parents + (int64_t)par1[j] * c,
+                             parents + (int64_t)par2[j] * c, child);
+        double f;
+        if (rc == LEEA_CPU_OK) rc = leea_cpu_evaluate(1, dims, n_dims, child, probe_x, y, n_probe, &f, NULL, logits);
+        for (int64_t k = 0; rc == LEEA_CPU_OK && k < (int64_t)n_probe * d_out; k++) row[5 + k] = logits[k];
+    }
+    free(child);
+    free(logits);
+    free(y);
+    return rc;
 }

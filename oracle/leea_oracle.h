@@ -44,8 +44,12 @@ enum {
     LEEA_CPU_TAG_SEL = 2,     /* entity = child, n = draw index             */
     LEEA_CPU_TAG_XO = 3,      /* entity = child, n = gene                   */
     LEEA_CPU_TAG_MUTMASK = 4, /* entity = child, n = gene                   */
-    LEEA_CPU_TAG_NORMAL = 5   /* entity = child, n = gene                   */
+    LEEA_CPU_TAG_NORMAL = 5,  /* entity = child, n = gene                   */
+    LEEA_CPU_TAG_SURR_INIT = 6 /* surrogate weights: entity 0, n = parameter */
 };
+
+/* Philox entity of recipe r of the surrogate form: LEEA_CPU_RECIPE_ENTITY0 + r. */
+#define LEEA_CPU_RECIPE_ENTITY0 0x40000000u
 
 /* How a child of the next generation is made (Algorithm 1). */
 enum { LEEA_CPU_ELITE = 0, LEEA_CPU_CROSSOVER = 1, LEEA_CPU_MUTATION = 2 };
@@ -121,6 +125,38 @@ int leea_cpu_evaluate_shadow(int32_t pop, const int32_t* dims, int32_t n_dims,
                              const double* popv, int32_t precision, const int32_t* scale_exp,
                              const double* x, const int32_t* y, int32_t batch,
                              double* f_out, int32_t* correct_out);
+
+/* ---- surrogate form (no counterpart in the paper) ------------------------- */
+/* MLP d_in -> h1 -> h2 -> 1 with ReLU; parameters theta, flat:
+ * W1 [h1][d_in], b1 [h1], W2 [h2][h1], b2 [h2], w3 [h2], b3. */
+int64_t leea_cpu_mlp_num_params(int32_t d_in, int32_t h1, int32_t h2);
+int leea_cpu_mlp_init(int32_t d_in, int32_t h1, int32_t h2, uint64_t seed, double* theta);
+int leea_cpu_mlp_forward(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const double* theta,
+                         const double* x, double* y);
+/* L = mean (y - t)^2 and its gradient. */
+int leea_cpu_mlp_loss_grad(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const double* theta,
+                           const double* x, const double* t, double* loss, double* grad);
+/* One Adam step (Kingma & Ba 2015) with bias correction, step = 1, 2, ... */
+int leea_cpu_adam(int64_t n_params, double* theta, const double* grad, double* m, double* v, int64_t step,
+                  double lr, double beta1, double beta2, double eps);
+/* The mult (n_C + n_M) recipes of a generation: kinds, parents, f_inh, entities. */
+int leea_cpu_select_recipes(int32_t pop, const leea_cpu_params* prm, const double* f_adj,
+                            const int32_t* order, uint64_t seed, uint32_t gen, int32_t mult,
+                            int32_t* par1, int32_t* par2, int32_t* kind, double* f_inh, uint32_t* entity);
+/* n children with explicit Philox entities. */
+int leea_cpu_breed_entities(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm,
+                            uint64_t seed, uint32_t gen, const double* parents, const int32_t* par1,
+                            const int32_t* par2, const int32_t* kind, const uint32_t* entity, int32_t n,
+                            double* children);
+/* Crossover fraction and mutation step length of each recipe. */
+int leea_cpu_recipe_stats(const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm, uint64_t seed,
+                          uint32_t gen, const int32_t* kind, const uint32_t* entity, int32_t n, double* xo_frac,
+                          double* mut_norm);
+/* Descriptors [f1, f2, f_inh, xo_frac, mut_norm, probe logits (n_probe x d_out)]. */
+int leea_cpu_descriptors(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm,
+                         uint64_t seed, uint32_t gen, const double* parents, const double* f_adj,
+                         const int32_t* par1, const int32_t* par2, const int32_t* kind, const double* f_inh,
+                         const uint32_t* entity, int32_t n, const double* probe_x, int32_t n_probe, double* desc);
 
 /* ---- the whole algorithm as a state object -------------------------------- */
 typedef struct leea_cpu_state leea_cpu_state;
