@@ -506,6 +506,44 @@ void leea_multi_destroy(leea_multi* m);
 leea_status leea_tune_shadow_eval(int32_t precision, int32_t d_in, int32_t hidden, int32_t d_out, int32_t batch,
                                   int32_t pop, int32_t chunk, int32_t reps, float* ms_out);
 
+/* ---------------------------------------------------------------------- */
+/* Surrogate form: the learned pre-screen of offspring (no counterpart in   */
+/* the paper)                                                               */
+/* ---------------------------------------------------------------------- */
+
+/* The surrogate is an MLP d_in -> h1 -> h2 -> 1 with ReLU after the two
+ * hidden layers, FP32.  Parameters theta, flat: W1 [h1][d_in] (row-major),
+ * b1 [h1], W2 [h2][h1], b2 [h2], w3 [h2], b3 [1].  Every sum runs in a
+ * fixed order, so results do not depend on scheduling. */
+int64_t leea_surrogate_num_params(int32_t d_in, int32_t h1, int32_t h2);
+
+/* Glorot-uniform weights U(-a, a), a = sqrt(6 / (fan_in + fan_out)), from the
+ * Philox stream (tag 6, generation 0, entity 0; draw n = parameter index);
+ * zero biases.  theta_dev: float[leea_surrogate_num_params]. */
+leea_status leea_surrogate_init(int32_t d_in, int32_t h1, int32_t h2, uint64_t seed, float* theta_dev,
+                                void* stream);
+
+/* y_dev[r] = MLP(x_dev[r]) for rows r < n of x_dev (float[n][d_in]). */
+leea_status leea_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta_dev,
+                                   const float* x_dev, float* y_dev, void* stream);
+
+/* Floats of workspace leea_surrogate_loss_grad needs for n rows:
+ * n (2 + 2 h1 + 2 h2). */
+int64_t leea_surrogate_work_floats(int32_t n, int32_t h1, int32_t h2);
+
+/* *loss_dev = (1/n) sum_r (y_r - t_r)^2 and grad_dev = its gradient with
+ * respect to theta (backpropagation), for targets t_dev[n]. */
+leea_status leea_surrogate_loss_grad(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta_dev,
+                                     const float* x_dev, const float* t_dev, float* loss_dev, float* grad_dev,
+                                     float* work_dev, int64_t work_floats, void* stream);
+
+/* One Adam step (Kingma & Ba, ICLR 2015) at step number `step` (1, 2, ...):
+ * m = beta1 m + (1 - beta1) g; v = beta2 v + (1 - beta2) g^2;
+ * theta -= lr (m / (1 - beta1^step)) / (sqrt(v / (1 - beta2^step)) + eps). */
+leea_status leea_surrogate_adam(int64_t n_params, float* theta_dev, const float* grad_dev, float* m_dev,
+                                float* v_dev, int64_t step, float lr, float beta1, float beta2, float eps,
+                                void* stream);
+
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* leea_last_error(void);
 

@@ -194,6 +194,23 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
                               float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
                               float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
                               cudaStream_t stream);
+// Surrogate form: the MLP d_in -> h1 -> h2 -> 1 (leea_surrogate.cu).
+int64_t surrogate_num_params(int32_t d_in, int32_t h1, int32_t h2);
+size_t surrogate_forward_smem(int32_t d_in, int32_t h1, int32_t h2);
+// Workspace of launch_surrogate_loss_grad, in floats.
+size_t surrogate_work_floats(int32_t n, int32_t h1, int32_t h2);
+cudaError_t launch_surrogate_init(int32_t d_in, int32_t h1, int32_t h2, uint64_t seed, float* theta,
+                                  cudaStream_t stream);
+// y[n] = MLP(x[n][d_in]); a1 [n][h1] and a2 [n][h2] (ReLU outputs) kept when not NULL.
+cudaError_t launch_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta,
+                                     const float* x, float* y, float* a1, float* a2, cudaStream_t stream);
+// loss = mean (y - t)^2 and its gradient (all in-order sums).
+cudaError_t launch_surrogate_loss_grad(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta,
+                                       const float* x, const float* t, float* loss, float* grad, float* work,
+                                       cudaStream_t stream);
+cudaError_t launch_surrogate_adam(int64_t n_params, float* theta, const float* grad, float* m, float* v, int64_t step,
+                                  float lr, float beta1, float beta2, float eps, cudaStream_t stream);
+
 cudaError_t launch_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
                                uint32_t n0, int64_t count, uint32_t* out, cudaStream_t stream);
 cudaError_t launch_normal_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,

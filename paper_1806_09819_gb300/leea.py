@@ -144,6 +144,12 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_multi_profile_read": [vp, vp, vp],
         "leea_multi_destroy": ([vp], None),
         "leea_tune_shadow_eval": [i32, i32, i32, i32, i32, i32, i32, i32, P(f32)],
+        "leea_surrogate_num_params": ([i32, i32, i32], i64),
+        "leea_surrogate_init": [i32, i32, i32, u64, vp, vp],
+        "leea_surrogate_forward": [i32, i32, i32, i32, vp, vp, vp, vp],
+        "leea_surrogate_work_floats": ([i32, i32, i32], i64),
+        "leea_surrogate_loss_grad": [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, i64, vp],
+        "leea_surrogate_adam": [i64, vp, vp, vp, vp, i64, f32, f32, f32, f32, vp],
         "leea_last_error": ([], ctypes.c_char_p),
         "leea_destroy": ([vp], None),
     }
@@ -174,7 +180,9 @@ def exported_symbols() -> list[str]:
             "leea_multi_raw_fitness", "leea_multi_get_population", "leea_multi_set_population",
             "leea_multi_set_fitness", "leea_multi_set_generation", "leea_multi_get_selection",
             "leea_multi_get_shadow", "leea_multi_generation_index", "leea_multi_profile_enable",
-            "leea_multi_profile_read", "leea_multi_destroy", "leea_tune_shadow_eval"]
+            "leea_multi_profile_read", "leea_multi_destroy", "leea_tune_shadow_eval",
+            "leea_surrogate_num_params", "leea_surrogate_init", "leea_surrogate_forward",
+            "leea_surrogate_work_floats", "leea_surrogate_loss_grad", "leea_surrogate_adam"]
 
 
 def _check(rc: int) -> None:
@@ -582,3 +590,35 @@ def leea_tune_shadow_eval(precision: int, d_in: int, hidden: int, d_out: int, ba
     _check(load_library().leea_tune_shadow_eval(precision, d_in, hidden, d_out, batch, pop, chunk, reps,
                                                 ctypes.byref(ms)))
     return float(ms.value)
+
+
+# ---- surrogate MLP (row level) ------------------------------------------------------
+def leea_surrogate_num_params(d_in: int, h1: int, h2: int) -> int:
+    return int(load_library().leea_surrogate_num_params(d_in, h1, h2))
+
+
+def leea_surrogate_init(d_in: int, h1: int, h2: int, seed: int, theta_dev, stream=None) -> None:
+    _check(load_library().leea_surrogate_init(d_in, h1, h2, seed, _dptr(theta_dev), _stream(stream)))
+
+
+def leea_surrogate_forward(n: int, d_in: int, h1: int, h2: int, theta_dev, x_dev, y_dev, stream=None) -> None:
+    _check(load_library().leea_surrogate_forward(n, d_in, h1, h2, _dptr(theta_dev), _dptr(x_dev), _dptr(y_dev),
+                                                 _stream(stream)))
+
+
+def leea_surrogate_work_floats(n: int, h1: int, h2: int) -> int:
+    return int(load_library().leea_surrogate_work_floats(n, h1, h2))
+
+
+def leea_surrogate_loss_grad(n: int, d_in: int, h1: int, h2: int, theta_dev, x_dev, t_dev, loss_dev, grad_dev,
+                             work_dev, stream=None) -> None:
+    _check(load_library().leea_surrogate_loss_grad(n, d_in, h1, h2, _dptr(theta_dev), _dptr(x_dev), _dptr(t_dev),
+                                                   _dptr(loss_dev), _dptr(grad_dev), _dptr(work_dev),
+                                                   work_dev.numel(), _stream(stream)))
+
+
+def leea_surrogate_adam(n_params: int, theta_dev, grad_dev, m_dev, v_dev, step: int, lr: float = 1e-3,
+                        beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None) -> None:
+    _check(load_library().leea_surrogate_adam(n_params, _dptr(theta_dev), _dptr(grad_dev), _dptr(m_dev),
+                                              _dptr(v_dev), step, float(lr), float(beta1), float(beta2), float(eps),
+                                              _stream(stream)))
