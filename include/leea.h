@@ -511,6 +511,41 @@ leea_status leea_tune_shadow_eval(int32_t precision, int32_t d_in, int32_t hidde
 /* the paper)                                                               */
 /* ---------------------------------------------------------------------- */
 
+/* Recipes: the virtual offspring of one generation, mult x (n_C + n_M) of
+ * them (n_C, n_M as leea_counts gives them for pop).  Recipe r < mult n_C is
+ * a crossover, the rest mutations.  Recipe r draws its parents like a child
+ * of that kind in leea_select, and later its genes, from the Philox streams
+ * of entity 2^30 + r.  -1 if the arguments are invalid. */
+int32_t leea_num_recipes(int32_t pop, const leea_params* p, int32_t mult);
+
+/* The recipes (int32 / float / uint32 arrays of leea_num_recipes entries) from
+ * the population's f_adj_dev and its ranking order_dev (leea_rank); f_inh as
+ * for a child of the same kind. */
+leea_status leea_select_recipes(int32_t pop, const leea_params* p, const float* f_adj_dev, const int32_t* order_dev,
+                                uint64_t seed, uint32_t gen, int32_t mult, int32_t* par1_dev, int32_t* par2_dev,
+                                int32_t* kind_dev, float* f_inh_dev, uint32_t* entity_dev, void* stream);
+
+/* leea_breed for n_children children of n_parents parents, child j drawing
+ * from the Philox streams of entity entity_dev[j] (materialising recipes). */
+leea_status leea_breed_entities(int32_t n_parents, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                                uint64_t seed, uint32_t gen, const float* parents_dev, const int32_t* par1_dev,
+                                const int32_t* par2_dev, const int32_t* kind_dev, const uint32_t* entity_dev,
+                                int32_t n_children, float* children_dev, void* stream);
+
+/* Descriptors of n recipes, float[n][5 + n_probe d_out] (fused breed + probe:
+ * the children's genes are made on the fly and never written):
+ * [f_adj of parent 1, f_adj of parent 2, f_inh, the fraction of the c genes a
+ * uniform crossover takes from parent 2 (0.5 arithmetic, 0 otherwise), the
+ * mutation step length sigma ||z (.) m|| over the masked genes (0 otherwise),
+ * then the child's logits on the probe inputs probe_dev (float[n_probe][d_0]),
+ * sample-major].  entity_dev NULL: entity = recipe index.  Two-layer nets,
+ * d_0 % 16 == 0, 16 <= h <= 256 with h % 16 == 0, d_out <= 16, n_probe <= 32. */
+leea_status leea_descriptors(int32_t n_parents, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                             uint64_t seed, uint32_t gen, const float* parents_dev, const float* f_adj_dev,
+                             const int32_t* par1_dev, const int32_t* par2_dev, const int32_t* kind_dev,
+                             const float* f_inh_dev, const uint32_t* entity_dev, int32_t n,
+                             const float* probe_dev, int32_t n_probe, float* desc_dev, void* stream);
+
 /* The surrogate is an MLP d_in -> h1 -> h2 -> 1 with ReLU after the two
  * hidden layers, FP32.  Parameters theta, flat: W1 [h1][d_in] (row-major),
  * b1 [h1], W2 [h2][h1], b2 [h2], w3 [h2], b3 [1].  Every sum runs in a

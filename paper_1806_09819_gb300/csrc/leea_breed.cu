@@ -299,7 +299,8 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
                     cur_p1 = R.par1[j];
                     cur_p2 = R.par2[j];
                     cur_sexp = (a.precision == 2) ? a.scale_exp[j] : 0;
-                    if (cur_p1 < 0 || cur_p1 >= a.pop || cur_p2 < 0 || cur_p2 >= a.pop) cur_kind = kKindInvalid;
+                    const int32_t n_par = a.n_parents > 0 ? a.n_parents : a.pop;
+                    if (cur_p1 < 0 || cur_p1 >= n_par || cur_p2 < 0 || cur_p2 >= n_par) cur_kind = kKindInvalid;
                 }
                 const int64_t g0 = static_cast<int64_t>(ck) * kChunk;
                 const int32_t len = static_cast<int32_t>(a.c_pad - g0 < kChunk ? a.c_pad - g0 : kChunk);
@@ -349,7 +350,7 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
             const float4* A = reinterpret_cast<const float4*>(stage_a(s, stage));
             const float4* B = reinterpret_cast<const float4*>(stage_b(s, stage));
             float4* O = reinterpret_cast<float4*>(R.children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
-            const uint32_t j = static_cast<uint32_t>(m.j);
+            const uint32_t j = a.entity ? a.entity[m.j] : static_cast<uint32_t>(m.j);  // Philox entity
             const bool live = ct * kGenesPerLane < m.len;
             const uint32_t u = (static_cast<uint32_t>(m.g0) >> 3) + static_cast<uint32_t>(ct);  // 8-gene unit
             float4 v[2] = { make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f) };

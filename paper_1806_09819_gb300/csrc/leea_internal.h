@@ -58,6 +58,10 @@ struct BreedArgs {
     int64_t sh_stride;        // bytes, multiple of 128
     const int32_t* scale_exp;
     float* amax_out;          // atomic max of |W1| per child
+    // surrogate form: child j draws from the streams of Philox entity entity[j]
+    // (NULL: entity j); parents are indices below n_parents (0: pop)
+    const uint32_t* entity;
+    int32_t n_parents;
 };
 
 // Tiled shadow layout.  An individual's W1 shadow is a sequence of blocks, one
@@ -194,6 +198,30 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
                               float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
                               float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
                               cudaStream_t stream);
+// Surrogate form: recipes (virtual offspring) and their descriptors.
+constexpr uint32_t kRecipeEntity0 = 0x40000000u;  // Philox entity of recipe r: kRecipeEntity0 + r
+// Recipes r < mult n_cross are crossovers, the rest mutations; parents as
+// select_child picks them, from the streams of entity kRecipeEntity0 + r.
+cudaError_t launch_select_recipes(const SelectArgs& a, int32_t mult, const float* f_adj, const int32_t* order,
+                                  int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh, uint32_t* entity,
+                                  cudaStream_t stream);
+struct ProbeArgs {
+    int32_t k, h, d_out, n_probe, width, xo_op;
+    int64_t c, c_pad;
+    uint32_t thr_xo, thr_mut, gen;
+    float sigma;
+    uint64_t seed;
+    const float* parents;
+    const float* f_adj;
+    const int32_t *par1, *par2, *kind;
+    const float* f_inh;
+    const uint32_t* entity;  // NULL: entity = recipe index
+    const float* probe;      // float[n_probe][k]
+    float* desc;             // float[n][width], width = 5 + n_probe d_out
+};
+bool probe_supported(int32_t k, int32_t h, int32_t d_out, int32_t n_probe);
+cudaError_t launch_descriptors(const ProbeArgs& a, int32_t n_recipes, cudaStream_t stream);
+
 // Surrogate form: the MLP d_in -> h1 -> h2 -> 1 (leea_surrogate.cu).
 int64_t surrogate_num_params(int32_t d_in, int32_t h1, int32_t h2);
 size_t surrogate_forward_smem(int32_t d_in, int32_t h1, int32_t h2);

@@ -122,6 +122,40 @@ __device__ __forceinline__ void select_child(const SelectArgs& a, const float* f
     }
 }
 
+// Recipe r of the surrogate form: a crossover (r < mult n_cross) or a
+// mutation, parents picked as for a child of that kind from the streams of
+// entity kRecipeEntity0 + r.
+__global__ void __launch_bounds__(256) select_recipes_kernel(SelectArgs a, int32_t mult, const float* __restrict__ f_adj,
+                                                             const int32_t* __restrict__ order,
+                                                             int32_t* __restrict__ par1, int32_t* __restrict__ par2,
+                                                             int32_t* __restrict__ kind, float* __restrict__ f_inh,
+                                                             uint32_t* __restrict__ entity)
+{
+    const int32_t n = mult * (a.pop - a.n_elite);
+    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const uint32_t ent = kRecipeEntity0 + static_cast<uint32_t>(r);
+    SelStream st(a.seed, a.gen, ent);
+    const uint32_t draws = a.sel_op == 0 ? 1u : static_cast<uint32_t>(a.tour_k);
+    int32_t p1, p2, k;
+    float fi;
+    if (r < mult * a.n_cross) {
+        k = kKindCross;
+        p1 = pick_parent(a, f_adj, order, st, 0u);
+        p2 = pick_parent(a, f_adj, order, st, draws);
+        fi = 0.5f * (f_adj[p1] + f_adj[p2]);
+    } else {
+        k = kKindMut;
+        p1 = p2 = pick_parent(a, f_adj, order, st, 0u);
+        fi = f_adj[p1];
+    }
+    kind[r] = k;
+    par1[r] = p1;
+    par2[r] = p2;
+    f_inh[r] = fi;
+    entity[r] = ent;
+}
+
 __global__ void __launch_bounds__(256) select_kernel(SelectArgs a, const float* __restrict__ f_adj,
                                                      const int32_t* __restrict__ order,
                                                      int32_t* __restrict__ par1, int32_t* __restrict__ par2,
@@ -209,6 +243,16 @@ cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t*
         return launch_select(a, f_adj, order, par1, par2, kind, f_inh, stream);
     }
     rank_select_kernel<<<1, kFusedThreads, 0, stream>>>(a, f_adj, order, par1, par2, kind, f_inh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_recipes(const SelectArgs& a, int32_t mult, const float* f_adj, const int32_t* order,
+                                  int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh, uint32_t* entity,
+                                  cudaStream_t stream)
+{
+    const int32_t n = mult * (a.pop - a.n_elite);
+    if (n <= 0) return cudaSuccess;
+    select_recipes_kernel<<<(n + 255) / 256, 256, 0, stream>>>(a, mult, f_adj, order, par1, par2, kind, f_inh, entity);
     return cudaGetLastError();
 }
 

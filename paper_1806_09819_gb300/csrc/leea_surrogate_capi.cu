@@ -88,4 +88,103 @@ leea_status leea_surrogate_adam(int64_t n_params, float* theta_dev, const float*
     return LEEA_OK;
 }
 
+int32_t leea_num_recipes(int32_t pop, const leea_params* p, int32_t mult)
+{
+    if (pop < 1 || !p || mult < 1 || check_params(p)) return -1;
+    int32_t ne, nc, nm, pool;
+    counts_of(pop, p, &ne, &nc, &nm, &pool);
+    return mult * (nc + nm);
+}
+
+leea_status leea_select_recipes(int32_t pop, const leea_params* p, const float* f_adj_dev, const int32_t* order_dev,
+                                uint64_t seed, uint32_t gen, int32_t mult, int32_t* par1_dev, int32_t* par2_dev,
+                                int32_t* kind_dev, float* f_inh_dev, uint32_t* entity_dev, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if ((st = check_params(p))) return st;
+    if (mult < 1 || static_cast<int64_t>(mult) * pop > (1 << 26)) return fail(LEEA_EINVAL, "mult must be >= 1");
+    if (!f_adj_dev || !order_dev || !par1_dev || !par2_dev || !kind_dev || !f_inh_dev || !entity_dev)
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    const SelectArgs a = select_args(pop, p, seed, gen);
+    LEEA_CUDA_TRY(launch_select_recipes(a, mult, f_adj_dev, order_dev, par1_dev, par2_dev, kind_dev, f_inh_dev,
+                                        entity_dev, static_cast<cudaStream_t>(stream)),
+                  "recipe selection kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_breed_entities(int32_t n_parents, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                                uint64_t seed, uint32_t gen, const float* parents_dev, const int32_t* par1_dev,
+                                const int32_t* par2_dev, const int32_t* kind_dev, const uint32_t* entity_dev,
+                                int32_t n_children, float* children_dev, void* stream)
+{
+    leea_status st = check_pop(n_parents);
+    if (st) return st;
+    if ((st = check_pop(n_children))) return st;
+    if ((st = check_params(p))) return st;
+    if (p->precision != 0) return fail(LEEA_EINVAL, "leea_breed_entities takes precision 0");
+    NetLayout net;
+    if (!make_layout(dims, n_dims, p->init, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if (!parents_dev || !par1_dev || !par2_dev || !kind_dev || !entity_dev || !children_dev)
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    if ((reinterpret_cast<uintptr_t>(parents_dev) | reinterpret_cast<uintptr_t>(children_dev)) & 15u)
+        return fail(LEEA_EINVAL, "population buffers must be 16-byte aligned");
+    BreedArgs a = breed_args(n_children, net, p, seed, gen);
+    a.entity = entity_dev;
+    a.n_parents = n_parents;
+    unsigned int* status = device_status_ptr();
+    if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+    LEEA_CUDA_TRY(launch_breed(a, parents_dev, par1_dev, par2_dev, kind_dev, children_dev, status,
+                               static_cast<cudaStream_t>(stream)),
+                  "breed kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_descriptors(int32_t n_parents, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                             uint64_t seed, uint32_t gen, const float* parents_dev, const float* f_adj_dev,
+                             const int32_t* par1_dev, const int32_t* par2_dev, const int32_t* kind_dev,
+                             const float* f_inh_dev, const uint32_t* entity_dev, int32_t n,
+                             const float* probe_dev, int32_t n_probe, float* desc_dev, void* stream)
+{
+    leea_status st = check_pop(n_parents);
+    if (st) return st;
+    if ((st = check_params(p))) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, p->init, &net) || net.n_layers != 2)
+        return fail(LEEA_EINVAL, "descriptors take d_0-h-d_out nets (n_dims == 3)");
+    if (!probe_supported(net.dims[0], net.dims[1], net.dims[2], n_probe))
+        return fail(LEEA_EINVAL, "descriptors need d_0 %% 16 == 0, h %% 16 == 0, 16 <= h <= 256, d_out <= 16 and "
+                                 "1 <= n_probe <= 32");
+    if (n < 0) return fail(LEEA_EINVAL, "n must be >= 0");
+    if (n == 0) return LEEA_OK;
+    if (!parents_dev || !f_adj_dev || !par1_dev || !par2_dev || !kind_dev || !f_inh_dev || !probe_dev || !desc_dev)
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    if (reinterpret_cast<uintptr_t>(parents_dev) & 15u) return fail(LEEA_EINVAL, "parents must be 16-byte aligned");
+    ProbeArgs a{};
+    a.k = net.dims[0];
+    a.h = net.dims[1];
+    a.d_out = net.dims[2];
+    a.n_probe = n_probe;
+    a.width = 5 + n_probe * net.dims[2];
+    a.xo_op = p->xo_op;
+    a.c = net.c;
+    a.c_pad = net.c_pad;
+    a.thr_xo = threshold16(static_cast<double>(p->xo_gene_p));
+    a.thr_mut = threshold16(static_cast<double>(p->mut_rate));
+    a.gen = gen;
+    a.sigma = p->sigma;
+    a.seed = seed;
+    a.parents = parents_dev;
+    a.f_adj = f_adj_dev;
+    a.par1 = par1_dev;
+    a.par2 = par2_dev;
+    a.kind = kind_dev;
+    a.f_inh = f_inh_dev;
+    a.entity = entity_dev;
+    a.probe = probe_dev;
+    a.desc = desc_dev;
+    LEEA_CUDA_TRY(launch_descriptors(a, n, static_cast<cudaStream_t>(stream)), "probe kernel");
+    return LEEA_OK;
+}
+
 }  // extern "C"

@@ -144,6 +144,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_multi_profile_read": [vp, vp, vp],
         "leea_multi_destroy": ([vp], None),
         "leea_tune_shadow_eval": [i32, i32, i32, i32, i32, i32, i32, i32, P(f32)],
+        "leea_num_recipes": ([i32, P(leea_params), i32], i32),
+        "leea_select_recipes": [i32, P(leea_params), vp, vp, u64, u32, i32, vp, vp, vp, vp, vp, vp],
+        "leea_breed_entities": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, i32, vp, vp],
+        "leea_descriptors": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp, vp, i32, vp, i32,
+                             vp, vp],
         "leea_surrogate_num_params": ([i32, i32, i32], i64),
         "leea_surrogate_init": [i32, i32, i32, u64, vp, vp],
         "leea_surrogate_forward": [i32, i32, i32, i32, vp, vp, vp, vp],
@@ -182,7 +187,8 @@ def exported_symbols() -> list[str]:
             "leea_multi_get_shadow", "leea_multi_generation_index", "leea_multi_profile_enable",
             "leea_multi_profile_read", "leea_multi_destroy", "leea_tune_shadow_eval",
             "leea_surrogate_num_params", "leea_surrogate_init", "leea_surrogate_forward",
-            "leea_surrogate_work_floats", "leea_surrogate_loss_grad", "leea_surrogate_adam"]
+            "leea_surrogate_work_floats", "leea_surrogate_loss_grad", "leea_surrogate_adam",
+            "leea_num_recipes", "leea_select_recipes", "leea_breed_entities", "leea_descriptors"]
 
 
 def _check(rc: int) -> None:
@@ -622,3 +628,37 @@ def leea_surrogate_adam(n_params: int, theta_dev, grad_dev, m_dev, v_dev, step: 
     _check(load_library().leea_surrogate_adam(n_params, _dptr(theta_dev), _dptr(grad_dev), _dptr(m_dev),
                                               _dptr(v_dev), step, float(lr), float(beta1), float(beta2), float(eps),
                                               _stream(stream)))
+
+
+# ---- recipes and descriptors (surrogate form) ---------------------------------------
+def leea_num_recipes(pop: int, prm: Params, mult: int) -> int:
+    cp = prm.c_struct()
+    return int(load_library().leea_num_recipes(pop, ctypes.byref(cp), mult))
+
+
+def leea_select_recipes(pop: int, prm: Params, f_adj_dev, order_dev, seed: int, gen: int, mult: int, par1_dev,
+                        par2_dev, kind_dev, f_inh_dev, entity_dev, stream=None) -> None:
+    cp = prm.c_struct()
+    _check(load_library().leea_select_recipes(pop, ctypes.byref(cp), _dptr(f_adj_dev), _dptr(order_dev), seed, gen,
+                                              mult, _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev),
+                                              _dptr(f_inh_dev), _dptr(entity_dev), _stream(stream)))
+
+
+def leea_breed_entities(n_parents: int, dims, prm: Params, seed: int, gen: int, parents_dev, par1_dev, par2_dev,
+                        kind_dev, entity_dev, n_children: int, children_dev, stream=None) -> None:
+    d = _dims(dims)
+    cp = prm.c_struct()
+    _check(load_library().leea_breed_entities(n_parents, _hp(d), len(d), ctypes.byref(cp), seed, gen,
+                                              _dptr(parents_dev), _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev),
+                                              _dptr(entity_dev), n_children, _dptr(children_dev), _stream(stream)))
+
+
+def leea_descriptors(n_parents: int, dims, prm: Params, seed: int, gen: int, parents_dev, f_adj_dev, par1_dev,
+                     par2_dev, kind_dev, f_inh_dev, entity_dev, n: int, probe_dev, n_probe: int, desc_dev,
+                     stream=None) -> None:
+    d = _dims(dims)
+    cp = prm.c_struct()
+    _check(load_library().leea_descriptors(n_parents, _hp(d), len(d), ctypes.byref(cp), seed, gen, _dptr(parents_dev),
+                                           _dptr(f_adj_dev), _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev),
+                                           _dptr(f_inh_dev), _dptr(entity_dev), n, _dptr(probe_dev), n_probe,
+                                           _dptr(desc_dev), _stream(stream)))

@@ -98,3 +98,90 @@ def test_surrogate_argument_errors(gpu):
         gpu.leea_surrogate_loss_grad(5, 3, 4, 4, th, x, th, th, th, torch.empty(3, device="cuda"))
     with pytest.raises(gpu.LeeaError):
         gpu.leea_surrogate_adam(10, th, th, th, th, 0)
+
+
+# ---- recipes, their materialisation and descriptors ------------------------------------
+PRM_S = dict(sigma=0.05, mut_rate=0.2, n_elite=2, p_c=0.5, xo_gene_p=0.5)
+
+
+def _recipes(gpu, oracle_mod, pop=40, mult=4, seed=7, gen=3, **extra):
+    import torch
+    rng = np.random.default_rng(pop)
+    f = rng.normal(-2.3, 0.2, size=pop).astype(np.float32)
+    prm = gpu.Params(**PRM_S, **extra)
+    n = gpu.leea_num_recipes(pop, prm, mult)
+    fd = _t(f)
+    order = torch.empty(pop, dtype=torch.int32, device="cuda")
+    gpu.leea_rank(pop, fd, order)
+    p1, p2, kind, ent = (torch.empty(n, dtype=torch.int32, device="cuda") for _ in range(4))
+    f_inh = torch.empty(n, dtype=torch.float32, device="cuda")
+    gpu.leea_select_recipes(pop, prm, fd, order, seed, gen, mult, p1, p2, kind, f_inh, ent)
+    return f, order, (p1, p2, kind, f_inh, ent)
+
+
+@pytest.mark.parametrize("sel_op", [0, 1])
+def test_recipes_bit_exact(gpu, oracle_mod, sel_op):
+    pop, mult = 40, 4
+    f, order, (p1, p2, kind, f_inh, ent) = _recipes(gpu, oracle_mod, pop, mult, sel_op=sel_op, tour_k=3)
+    oprm = oracle_mod.Params(**PRM_S, sel_op=sel_op, tour_k=3)
+    o_order = oracle_mod.rank(f.astype(np.float64))
+    np.testing.assert_array_equal(order.cpu().numpy(), o_order)
+    r1, r2, rk, rinh, rent = oracle_mod.select_recipes(oprm, f.astype(np.float64), o_order, 7, 3, mult)
+    np.testing.assert_array_equal(p1.cpu().numpy(), r1)
+    np.testing.assert_array_equal(p2.cpu().numpy(), r2)
+    np.testing.assert_array_equal(kind.cpu().numpy(), rk)
+    np.testing.assert_array_equal(ent.cpu().numpy().view(np.uint32), rent)
+    np.testing.assert_allclose(f_inh.cpu().numpy(), rinh, rtol=2 ** -23, atol=0)
+
+
+def test_breed_entities_matches_oracle(gpu, oracle_mod):
+    import torch
+    from helpers import assert_genes_close, to_device_pop
+    dims = [64, 32, 10]
+    pop, mult = 24, 2
+    f, order, (p1, p2, kind, f_inh, ent) = _recipes(gpu, oracle_mod, pop, mult)
+    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    parents = np.random.default_rng(4).normal(0, 0.3, size=(pop, c)).astype(np.float32)
+    n = kind.numel()
+    kids = torch.zeros((n, cp), dtype=torch.float32, device="cuda")
+    gpu.leea_breed_entities(pop, dims, gpu.Params(**PRM_S), 7, 3, to_device_pop(parents, cp), p1, p2, kind, ent, n,
+                            kids)
+    assert gpu.leea_device_status() == 0
+    ref = oracle_mod.breed_entities(oracle_mod.Params(**PRM_S), dims, 7, 3, parents.astype(np.float64),
+                                    p1.cpu().numpy(), p2.cpu().numpy(), kind.cpu().numpy(),
+                                    ent.cpu().numpy().view(np.uint32))
+    assert_genes_close(kids[:, :c].cpu().numpy(), ref, PRM_S["sigma"])
+
+
+@pytest.mark.parametrize("dims,n_probe", [([784, 112, 10], 32), ([64, 32, 10], 32), ([128, 256, 16], 7),
+                                          ([96, 16, 3], 1)])
+@pytest.mark.parametrize("xo_op", [0, 1])
+def test_descriptors_match_oracle(gpu, oracle_mod, dims, n_probe, xo_op):
+    import torch
+    from helpers import to_device_pop
+    pop, mult = 20, 2
+    prm = gpu.Params(**PRM_S, xo_op=xo_op)
+    oprm = oracle_mod.Params(**PRM_S, xo_op=xo_op)
+    f, order, (p1, p2, kind, f_inh, ent) = _recipes(gpu, oracle_mod, pop, mult)
+    # add two elite-kind rows (plain copies) at the end
+    kind_h = np.concatenate([kind.cpu().numpy(), [0, 0]]).astype(np.int32)
+    p1_h = np.concatenate([p1.cpu().numpy(), [3, 5]]).astype(np.int32)
+    p2_h = np.concatenate([p2.cpu().numpy(), [3, 5]]).astype(np.int32)
+    inh_h = np.concatenate([f_inh.cpu().numpy(), f[[3, 5]]]).astype(np.float32)
+    ent_h = np.concatenate([ent.cpu().numpy().view(np.uint32), [11, 12]]).astype(np.uint32)
+    n = kind_h.size
+    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    parents = np.random.default_rng(dims[1]).normal(0, 0.1, size=(pop, c)).astype(np.float32)
+    probe = (np.random.default_rng(5).integers(0, 256, size=(n_probe, dims[0])) / 255.0).astype(np.float32)
+    desc = torch.empty((n, 5 + n_probe * dims[-1]), dtype=torch.float32, device="cuda")
+    gpu.leea_descriptors(pop, dims, prm, 7, 3, to_device_pop(parents, cp), _t(f), _t(p1_h).int(), _t(p2_h).int(),
+                         _t(kind_h).int(), _t(inh_h), torch.from_numpy(ent_h.view(np.int32)).cuda(), n, _t(probe),
+                         n_probe, desc)
+    got = desc.cpu().numpy().astype(np.float64)
+    ref = oracle_mod.descriptors(oprm, dims, 7, 3, parents.astype(np.float64), f.astype(np.float64), p1_h, p2_h,
+                                 kind_h, inh_h.astype(np.float64), ent_h, probe.astype(np.float64))
+    np.testing.assert_array_equal(got[:, :3], ref[:, :3].astype(np.float32))
+    np.testing.assert_allclose(got[:, 3], ref[:, 3], rtol=1e-6, atol=0)
+    np.testing.assert_allclose(got[:, 4], ref[:, 4], rtol=1e-5, atol=0)
+    scale = np.abs(ref[:, 5:]).max()
+    np.testing.assert_allclose(got[:, 5:], ref[:, 5:], rtol=1e-4, atol=1e-5 * scale)
