@@ -579,6 +579,90 @@ leea_status leea_surrogate_adam(int64_t n_params, float* theta_dev, const float*
                                 float* v_dev, int64_t step, float lr, float beta1, float beta2, float eps,
                                 void* stream);
 
+/* The surrogate form as a state object.  Every breeding generation:
+ *  1. draws the recipes (leea_select_recipes, mult of them per offspring slot)
+ *     and their descriptors (leea_descriptors on the probe inputs);
+ *  2. standardises the descriptors (per-column mean and deviation over this
+ *     generation's recipes, as fitness and logits drift while the population
+ *     learns) and scores them with the MLP;
+ *  3. fills the P - n_E offspring slots either with the best-scored recipes
+ *     (the pre-screen) or, while the pre-screen is off, with the recipes the
+ *     plain EA would make (the first n_C crossover and first n_M mutation
+ *     recipes, ignoring the scores), and picks an audit sample of
+ *     round(audit_frac (R - P + n_E)) of the other recipes, evenly spaced in
+ *     score order (index order while the pre-screen is off);
+ *  4. makes and evaluates the offspring and the audit sample;
+ *  5. measures the Spearman correlation of scores and measured fitness over
+ *     offspring + audit, which switches the pre-screen on for the next
+ *     generation iff the generation index has reached `warmup` and the
+ *     correlation is at least min_spearman; and
+ *  6. appends the rows (standardised descriptor, fitness z-scored within the
+ *     generation) to a ring of `history` generations and takes train_steps
+ *     Adam steps on consecutive windows of train_batch rows.
+ * No step waits for the host.  Elites are copied as in Algorithm 1. */
+typedef struct {
+    int32_t mult;           /* recipes per offspring slot; 4                         */
+    int32_t n_probe;        /* probe inputs (1..32); 32                              */
+    int32_t hidden1;        /* MLP hidden widths; 64, 64                             */
+    int32_t hidden2;
+    int32_t train_steps;    /* Adam steps per generation; 16                         */
+    int32_t train_batch;    /* rows per step; 256                                    */
+    int32_t history;        /* generations of rows kept; 4                           */
+    int32_t warmup;         /* first generation that may use the pre-screen; 3       */
+    float lr;               /* Adam learning rate; 1e-3 (betas 0.9, 0.999, eps 1e-8) */
+    float audit_frac;       /* audit sample, fraction of the recipes left out; 0.05  */
+    float min_spearman;     /* audit correlation needed for the pre-screen; 0.2      */
+    uint64_t seed;          /* MLP initialisation                                    */
+} leea_surrogate_params;
+
+typedef struct leea_surr leea_surr;
+
+leea_status leea_surrogate_default_params(leea_surrogate_params* out);
+
+/* Creates the object for `pop` nets d_0-h-d_out (p->precision 0: FP32
+ * evaluation, 1: BF16 shadows), initialised from `seed` as leea_create does,
+ * with probe_host = float[n_probe][d_0] probe inputs (copied). */
+leea_status leea_surr_create(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                             const leea_surrogate_params* sp, uint64_t seed, const float* probe_host, void* stream,
+                             leea_surr** out);
+/* One generation (the first call only evaluates), minibatch of 8-bit levels. */
+leea_status leea_surr_generation_u8(leea_surr* s, const uint8_t* x_dev, float x_div, const int32_t* y_dev,
+                                    int32_t batch);
+leea_status leea_surr_generation_u8_host(leea_surr* s, const uint8_t* x_host, float x_div, const int32_t* y_host,
+                                         int32_t batch);
+leea_status leea_surr_fitness(leea_surr* s, float* f_adj_host, int32_t* correct_host);
+/* Raw fitness of the population and (if not NULL) of the audit sample. */
+leea_status leea_surr_raw_fitness(leea_surr* s, float* f_raw_host, float* f_audit_host);
+leea_status leea_surr_get_population(leea_surr* s, float* out_host);
+leea_status leea_surr_set_population(leea_surr* s, const float* in_host);
+leea_status leea_surr_set_fitness(leea_surr* s, const float* f_adj_host);
+leea_status leea_surr_set_generation(leea_surr* s, uint32_t gen, int32_t evaluated);
+/* Forces the pre-screen flag for the next generation (tests and ablations). */
+leea_status leea_surr_set_screen(leea_surr* s, int32_t use_screen);
+/* Recipes R, audit size, descriptor width and MLP parameter count. */
+leea_status leea_surr_layout(const leea_surr* s, int32_t* n_recipes, int32_t* n_audit, int32_t* width,
+                             int64_t* n_theta);
+/* The last breeding generation's recipes, descriptors (float[R][width]),
+ * scores, the recipe of each training row (offspring, then audit) and the
+ * offspring slots' parents, kinds, entities and f_inh.  Any pointer may be
+ * NULL.  Synchronises. */
+leea_status leea_surr_get_step(leea_surr* s, int32_t* r_par1, int32_t* r_par2, int32_t* r_kind, float* r_f_inh,
+                               uint32_t* r_entity, float* desc, float* pred, int32_t* row_recipe, int32_t* c_par1,
+                               int32_t* c_par2, int32_t* c_kind, uint32_t* c_entity, float* c_f_inh);
+/* The MLP parameters and the descriptor standardisation (any may be NULL). */
+leea_status leea_surr_get_surrogate(leea_surr* s, float* theta_host, float* mu_host, float* sd_host);
+/* Per breeding generation (the last min(n_max, count)): audit Spearman,
+ * whether the pre-screen chose the offspring, and the last training loss. */
+leea_status leea_surr_stats(leea_surr* s, int64_t n_max, float* spearman, int32_t* screened, float* loss,
+                            int64_t* n_out);
+uint32_t leea_surr_generation_index(const leea_surr* s);
+/* Per-stage CUDA-event timing, five stages: recipes + descriptors, scores +
+ * choice, breeding, evaluation, audit + training. */
+#define LEEA_SURR_STAGES 5
+leea_status leea_surr_profile_enable(leea_surr* s, int32_t enable);
+leea_status leea_surr_profile_read(leea_surr* s, double* ms_out, int64_t* generations_out);
+void leea_surr_destroy(leea_surr* s);
+
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* leea_last_error(void);
 

@@ -37,6 +37,13 @@ class leea_run_spec(ctypes.Structure):
                 ("chunk", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
+class leea_surrogate_params(ctypes.Structure):
+    _fields_ = [("mult", ctypes.c_int32), ("n_probe", ctypes.c_int32), ("hidden1", ctypes.c_int32),
+                ("hidden2", ctypes.c_int32), ("train_steps", ctypes.c_int32), ("train_batch", ctypes.c_int32),
+                ("history", ctypes.c_int32), ("warmup", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("audit_frac", ctypes.c_float), ("min_spearman", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
 class leea_params(ctypes.Structure):
     _fields_ = [
         ("xo_op", ctypes.c_int32), ("xo_gene_p", ctypes.c_float),
@@ -155,6 +162,25 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_surrogate_work_floats": ([i32, i32, i32], i64),
         "leea_surrogate_loss_grad": [i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, i64, vp],
         "leea_surrogate_adam": [i64, vp, vp, vp, vp, i64, f32, f32, f32, f32, vp],
+        "leea_surrogate_default_params": [P(leea_surrogate_params)],
+        "leea_surr_create": [i32, vp, i32, P(leea_params), P(leea_surrogate_params), u64, vp, vp, P(vp)],
+        "leea_surr_generation_u8": [vp, vp, f32, vp, i32],
+        "leea_surr_generation_u8_host": [vp, vp, f32, vp, i32],
+        "leea_surr_fitness": [vp, vp, vp],
+        "leea_surr_raw_fitness": [vp, vp, vp],
+        "leea_surr_get_population": [vp, vp],
+        "leea_surr_set_population": [vp, vp],
+        "leea_surr_set_fitness": [vp, vp],
+        "leea_surr_set_generation": [vp, u32, i32],
+        "leea_surr_set_screen": [vp, i32],
+        "leea_surr_layout": [vp, vp, vp, vp, vp],
+        "leea_surr_get_step": [vp] + [vp] * 13,
+        "leea_surr_get_surrogate": [vp, vp, vp, vp],
+        "leea_surr_stats": [vp, i64, vp, vp, vp, vp],
+        "leea_surr_generation_index": ([vp], u32),
+        "leea_surr_profile_enable": [vp, i32],
+        "leea_surr_profile_read": [vp, vp, vp],
+        "leea_surr_destroy": ([vp], None),
         "leea_last_error": ([], ctypes.c_char_p),
         "leea_destroy": ([vp], None),
     }
@@ -188,7 +214,12 @@ def exported_symbols() -> list[str]:
             "leea_multi_profile_read", "leea_multi_destroy", "leea_tune_shadow_eval",
             "leea_surrogate_num_params", "leea_surrogate_init", "leea_surrogate_forward",
             "leea_surrogate_work_floats", "leea_surrogate_loss_grad", "leea_surrogate_adam",
-            "leea_num_recipes", "leea_select_recipes", "leea_breed_entities", "leea_descriptors"]
+            "leea_num_recipes", "leea_select_recipes", "leea_breed_entities", "leea_descriptors",
+            "leea_surrogate_default_params", "leea_surr_create", "leea_surr_generation_u8",
+            "leea_surr_generation_u8_host", "leea_surr_fitness", "leea_surr_raw_fitness", "leea_surr_get_population",
+            "leea_surr_set_population", "leea_surr_set_fitness", "leea_surr_set_generation", "leea_surr_set_screen",
+            "leea_surr_layout", "leea_surr_get_step", "leea_surr_get_surrogate", "leea_surr_stats",
+            "leea_surr_generation_index", "leea_surr_profile_enable", "leea_surr_profile_read", "leea_surr_destroy"]
 
 
 def _check(rc: int) -> None:
@@ -662,3 +693,140 @@ def leea_descriptors(n_parents: int, dims, prm: Params, seed: int, gen: int, par
                                            _dptr(f_adj_dev), _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev),
                                            _dptr(f_inh_dev), _dptr(entity_dev), n, _dptr(probe_dev), n_probe,
                                            _dptr(desc_dev), _stream(stream)))
+
+
+# ---- the surrogate form as a state object ---------------------------------------------
+SURR_STAGES = ("recipes", "scores", "breed", "evaluate", "training")
+
+
+@dataclass
+class SurrogateParams:
+    """Fields of ``leea_surrogate_params``; defaults as ``leea_surrogate_default_params``."""
+    mult: int = 4
+    n_probe: int = 32
+    hidden1: int = 64
+    hidden2: int = 64
+    train_steps: int = 16
+    train_batch: int = 256
+    history: int = 4
+    warmup: int = 3
+    lr: float = 1e-3
+    audit_frac: float = 0.05
+    min_spearman: float = 0.2
+    seed: int = 0x5EED5EED
+
+    def c_struct(self) -> leea_surrogate_params:
+        return leea_surrogate_params(**{f.name: getattr(self, f.name) for f in fields(SurrogateParams)})
+
+
+class SurrState:
+    """The surrogate form (``leea_surr_create`` ... ``leea_surr_destroy``)."""
+
+    def __init__(self, pop: int, dims, prm: Params, sp: SurrogateParams, seed: int, probe, stream=None):
+        self.lib = load_library()
+        self.pop = pop
+        self.dims = _dims(dims)
+        self._cp, self._sp = prm.c_struct(), sp.c_struct()
+        self.probe = np.ascontiguousarray(np.asarray(probe, dtype=np.float32))
+        h = ctypes.c_void_p()
+        _check(self.lib.leea_surr_create(pop, _hp(self.dims), len(self.dims), ctypes.byref(self._cp),
+                                         ctypes.byref(self._sp), seed, _hp(self.probe), _stream(stream),
+                                         ctypes.byref(h)))
+        self._h = h
+        self.c = leea_num_params(self.dims)
+        v = [ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()]
+        _check(self.lib.leea_surr_layout(h, *[ctypes.byref(x) for x in v]))
+        self.n_recipes, self.n_audit, self.width, self.n_theta = (x.value for x in v)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            self.lib.leea_surr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def generation_u8(self, x_dev, y_dev, x_div: float = 255.0) -> None:
+        _check(self.lib.leea_surr_generation_u8(self._h, _dptr(x_dev), float(x_div), _dptr(y_dev), int(y_dev.numel())))
+
+    def generation_u8_host(self, x_host, y_host, x_div: float = 255.0) -> None:
+        _check(self.lib.leea_surr_generation_u8_host(self._h, x_host.data_ptr(), float(x_div), y_host.data_ptr(),
+                                                     int(y_host.numel())))
+
+    def fitness(self, with_correct: bool = False):
+        f = np.empty(self.pop, dtype=np.float32)
+        cor = np.empty(self.pop, dtype=np.int32) if with_correct else None
+        _check(self.lib.leea_surr_fitness(self._h, _hp(f), None if cor is None else _hp(cor)))
+        return (f, cor) if with_correct else f
+
+    def raw_fitness(self):
+        f = np.empty(self.pop, dtype=np.float32)
+        fa = np.empty(max(self.n_audit, 1), dtype=np.float32)
+        _check(self.lib.leea_surr_raw_fitness(self._h, _hp(f), _hp(fa)))
+        return f, fa[:self.n_audit]
+
+    def get_population(self) -> np.ndarray:
+        out = np.empty((self.pop, self.c), dtype=np.float32)
+        _check(self.lib.leea_surr_get_population(self._h, _hp(out)))
+        return out
+
+    def set_population(self, popv) -> None:
+        a = np.ascontiguousarray(np.asarray(popv, dtype=np.float32))
+        _check(self.lib.leea_surr_set_population(self._h, _hp(a)))
+
+    def set_fitness(self, f_adj) -> None:
+        a = np.ascontiguousarray(np.asarray(f_adj, dtype=np.float32))
+        _check(self.lib.leea_surr_set_fitness(self._h, _hp(a)))
+
+    def set_generation(self, gen: int, evaluated: bool) -> None:
+        _check(self.lib.leea_surr_set_generation(self._h, gen, int(evaluated)))
+
+    def set_screen(self, on: bool) -> None:
+        _check(self.lib.leea_surr_set_screen(self._h, int(on)))
+
+    def get_step(self) -> dict:
+        R, P = self.n_recipes, self.pop
+        out = dict(r_par1=np.empty(R, np.int32), r_par2=np.empty(R, np.int32), r_kind=np.empty(R, np.int32),
+                   r_f_inh=np.empty(R, np.float32), r_entity=np.empty(R, np.uint32),
+                   desc=np.empty((R, self.width), np.float32), pred=np.empty(R, np.float32),
+                   row_recipe=np.empty(self.n_rows(), np.int32),
+                   c_par1=np.empty(P, np.int32), c_par2=np.empty(P, np.int32), c_kind=np.empty(P, np.int32),
+                   c_entity=np.empty(P, np.uint32), c_f_inh=np.empty(P, np.float32))
+        keys = ["r_par1", "r_par2", "r_kind", "r_f_inh", "r_entity", "desc", "pred", "row_recipe", "c_par1", "c_par2",
+                "c_kind", "c_entity", "c_f_inh"]
+        _check(self.lib.leea_surr_get_step(self._h, *[_hp(out[k]) for k in keys]))
+        return out
+
+    def n_rows(self) -> int:
+        return self.n_recipes // max(1, self._sp.mult) + self.n_audit
+
+    def get_surrogate(self):
+        th = np.empty(self.n_theta, np.float32)
+        mu, sd = np.empty(self.width, np.float32), np.empty(self.width, np.float32)
+        _check(self.lib.leea_surr_get_surrogate(self._h, _hp(th), _hp(mu), _hp(sd)))
+        return th, mu, sd
+
+    def stats(self, n_max: int = 1 << 16):
+        rho = np.empty(n_max, np.float32)
+        scr = np.empty(n_max, np.int32)
+        loss = np.empty(n_max, np.float32)
+        n = ctypes.c_int64()
+        _check(self.lib.leea_surr_stats(self._h, n_max, _hp(rho), _hp(scr), _hp(loss), ctypes.byref(n)))
+        k = n.value
+        return rho[:k], scr[:k], loss[:k]
+
+    @property
+    def gen(self) -> int:
+        return int(self.lib.leea_surr_generation_index(self._h))
+
+    def profile_enable(self, on: bool = True) -> None:
+        _check(self.lib.leea_surr_profile_enable(self._h, int(on)))
+
+    def profile_read(self):
+        ms = np.zeros(len(SURR_STAGES), dtype=np.float64)
+        n = ctypes.c_int64()
+        _check(self.lib.leea_surr_profile_read(self._h, _hp(ms), ctypes.byref(n)))
+        return {SURR_STAGES[k]: float(ms[k]) for k in range(len(SURR_STAGES))}, int(n.value)
