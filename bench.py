@@ -8,7 +8,7 @@ breed, evaluate).  The population (2 x 356 MB) is larger than L2, so no flush
 is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--config plain|precision-bf16|precision-fp8|batching]
+                    [--config plain|precision-bf16|precision-fp8|batching|surrogate]
 
 --config precision-* measures the precision form instead (P = 4096 nets
 784-112-10, batch 256, BF16 or FP8-e4m3 shadows of W1 with FP32 accumulation
@@ -17,7 +17,12 @@ of the masters on a sample of the final population.  --config batching
 measures the batching form: 64 independent runs (P in [50, 2000], h in
 [16, 256], batch in [8, 512], log-uniform from a fixed seed; BF16 shadows)
 advanced together, one CUDA graph per generation, tile shapes from the
-autotuner; the value counts every run's generations.
+autotuner; the value counts every run's generations.  --config surrogate
+runs the surrogate form (population 2048 nets 784-112-10, 4 x 2047 recipes
+per generation of which the best-scored 2047 are made, BF16 evaluation, MLP
+pre-screen trained online) and the plain FP32 path on the same batches, and
+reports both generation rates and synthetic-test accuracy curves, and the
+time each needs to reach the accuracy both attain.
 
 N > 1 (under torch.distributed.run) runs N independent replicas, one per GPU
 (the generation's selection needs every parent, so a run does not shard);
@@ -49,7 +54,12 @@ PRECISION_WORKLOAD = ("P=4096 MLPs 784-112-10, batch 256 synthetic 28x28 images,
 CONFIGS = {"plain": dict(pop=1000, batch=100, precision=0),
            "precision-bf16": dict(pop=4096, batch=256, precision=1),
            "precision-fp8": dict(pop=4096, batch=256, precision=2),
-           "batching": dict(runs=64, pop=(50, 2000), hidden=(16, 256), batch=(8, 512), precision=1, seed=4242)}
+           "batching": dict(runs=64, pop=(50, 2000), hidden=(16, 256), batch=(8, 512), precision=1, seed=4242),
+           "surrogate": dict(pop=2048, batch=100, precision=1, mult=4, n_probe=32)}
+SURROGATE_WORKLOAD = ("surrogate form: population 2048 MLPs 784-112-10, 4 recipes per offspring slot (8,188 per "
+                      "generation), the best-scored 2,047 made and evaluated (BF16 shadows) plus a 5% audit sample; "
+                      "MLP 325-64-64-1 trained online; batch 100 synthetic images; plain EA: the same population, "
+                      "operators and batches in FP32")
 BATCHING_WORKLOAD = ("64 independent LEEA runs of 784-h-10 MLPs, P in [50,2000], h in [16,256] (multiple of 16), "
                      "batch in [8,512], log-uniform (seed 4242); BF16 shadows of W1, FP32 masters; operators as the "
                      "plain workload; one CUDA graph per generation, hidden chunks from the autotuner")
@@ -430,6 +440,105 @@ def run_batching(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
+def run_surrogate(args, rank: int, world: int, local_rank: int):
+    """The surrogate form against the plain FP32 path: generations/s and test accuracy."""
+    import numpy as np
+    import torch
+    from paper_1806_09819_gb300 import build as B
+    from paper_1806_09819_gb300 import leea, synthetic
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = dist_init(world, True)
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(dist, dev)
+    B.build()
+    leea.load_library()
+    cfg = CONFIGS["surrogate"]
+    pop, batch = cfg["pop"], cfg["batch"]
+    gens = args.steps
+    every = max(1, gens // 12)
+    (xtr, ytr), (xte, yte) = synthetic.dataset(n_train=60000, n_test=10000)
+    lv_tr, lv_te = synthetic.to_levels(xtr), synthetic.to_levels(xte)
+    idx = synthetic.batch_indices(len(ytr), batch, gens + 1, seed=synthetic.BATCH_SEED + rank)
+    xs = torch.from_numpy(lv_tr[idx]).to(dev)
+    ys = torch.from_numpy(ytr[idx]).to(dev)
+    xt, yt = torch.from_numpy(lv_te).to(dev), torch.from_numpy(yte).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    cp = leea.leea_padded_params(DIMS)
+
+    def test_acc(params):
+        pd = torch.zeros((1, cp), dtype=torch.float32, device=dev)
+        pd[0, :params.size] = torch.from_numpy(params)
+        f = torch.empty(1, dtype=torch.float32, device=dev)
+        cor = torch.empty(1, dtype=torch.int32, device=dev)
+        leea.leea_evaluate_u8(1, DIMS, pd, xt, 255.0, yt, len(yte), 1.0, None, f, None, cor, stream=stream)
+        return float(cor.item()) / len(yte)
+
+    def run(make, step, best):
+        obj = make()
+        ms, curve = 0.0, []
+        step(obj, 0)  # evaluates the initial population
+        for g in range(1, gens + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(obj, g)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            if g % every == 0 or g == gens:
+                curve.append((g, ms, test_acc(best(obj))))
+        return obj, curve
+
+    prm_plain = leea.Params(**PARAMS)
+    plain, curve_p = run(lambda: leea.LeeaState(pop, DIMS, prm_plain, seed=31 + rank, stream=stream),
+                         lambda st, g: st.leea_generation_u8(xs[g], ys[g], 255.0), lambda st: st.leea_best_params())
+    plain.close()
+    sp = leea.SurrogateParams(mult=cfg["mult"], n_probe=cfg["n_probe"])
+    probe = xte[:cfg["n_probe"]].astype(np.float32)
+    prm_s = leea.Params(**PARAMS, precision=cfg["precision"])
+    surr, curve_s = run(lambda: leea.SurrState(pop, DIMS, prm_s, sp, seed=31 + rank, probe=probe, stream=stream),
+                        lambda st, g: st.generation_u8(xs[g], ys[g], 255.0), lambda st: st.best_params())
+    rho, screened, loss = surr.stats()
+    surr.profile_enable(True)
+    for g in range(min(gens, 50)):
+        surr.generation_u8(xs[g % (gens + 1)], ys[g % (gens + 1)], 255.0)
+    prof, n_prof = surr.profile_read()
+    surr.close()
+
+    def time_to(curve, acc):
+        for g, ms, a in curve:
+            if a >= acc:
+                return g, ms
+        return None, None
+    target = min(curve_p[-1][2], curve_s[-1][2])
+    gp, tp = time_to(curve_p, target)
+    gs, ts = time_to(curve_s, target)
+    gen_s = gens / (curve_s[-1][1] / 1000.0)
+    gen_p = gens / (curve_p[-1][1] / 1000.0)
+    line = {"metric": "generations/sec of the surrogate form (population 2048, 8,188 offspring recipes per "
+                      "generation, 784-112-10, batch 100, BF16) and its time-to-accuracy against plain FP32",
+            "value": world * gen_s, "unit": "generations/s", "n_gpus": world, "steps": gens, "warmup": 0,
+            "ms_per_step": curve_s[-1][1] / gens, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 eval, f32 surrogate", "data": "synthetic",
+            "config": {"workload": SURROGATE_WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "populations larger than L2, no flush"},
+            "plain_fp32": {"generations_per_sec": gen_p, "accuracy_curve": curve_p},
+            "surrogate_bf16": {"generations_per_sec": gen_s, "accuracy_curve": curve_s,
+                               "audit_spearman_mean_last_half": float(np.mean(rho[len(rho) // 2:])) if len(rho) else None,
+                               "prescreen_generations": int(screened.sum()), "generations": int(len(screened)),
+                               "stage_ms_per_generation": {k: v / max(1, n_prof) for k, v in prof.items()}},
+            "time_to_accuracy": {"accuracy": target, "plain_generations": gp, "plain_ms": tp,
+                                 "surrogate_generations": gs, "surrogate_ms": ts,
+                                 "speedup": (tp / ts) if tp and ts else None},
+            "gpu_launches": None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
 def run_native(args, rank: int, world: int, local_rank: int):
     import numpy as np
     import torch
@@ -627,6 +736,8 @@ def main():
         run_reference(args, rank, world)
     elif args.config == "batching":
         run_batching(args, rank, world, local_rank)
+    elif args.config == "surrogate":
+        run_surrogate(args, rank, world, local_rank)
     else:
         run_native(args, rank, world, local_rank)
 

@@ -655,6 +655,9 @@ leea_status leea_surr_get_surrogate(leea_surr* s, float* theta_host, float* mu_h
  * whether the pre-screen chose the offspring, and the last training loss. */
 leea_status leea_surr_stats(leea_surr* s, int64_t n_max, float* spearman, int32_t* screened, float* loss,
                             int64_t* n_out);
+/* Genes (float[c]) of the individual with the highest f_adj (ties to the
+ * lower index, NaN as -infinity).  Synchronises. */
+leea_status leea_surr_best_params(leea_surr* s, float* out_host, int64_t c);
 uint32_t leea_surr_generation_index(const leea_surr* s);
 /* Per-stage CUDA-event timing, five stages: recipes + descriptors, scores +
  * choice, breeding, evaluation, audit + training. */

@@ -217,28 +217,20 @@ __global__ void targets_kernel(int32_t n_rows, int32_t k, int32_t n_elite, const
     }
 }
 
-// Rank key: larger value first, NaN last, ties to the lower index.
-__device__ __forceinline__ bool before(float a, int32_t ia, float b, int32_t ib)
-{
-    const float x = a != a ? -INFINITY : a, y = b != b ? -INFINITY : b;
-    return x > y || (x == y && ia < ib);
-}
-
-// Spearman rank correlation of the rows' predictions and measurements; sets
-// the pre-screen flag for the next generation.
-__global__ void __launch_bounds__(1024) audit_kernel(int32_t n, const float* __restrict__ pred_rows,
-                                                     const float* __restrict__ meas, float* __restrict__ stat,
-                                                     int32_t* __restrict__ use_screen, int32_t allow, float min_rho)
+// Spearman rank correlation of the rows' predictions and measurements from
+// their two rankings (rank_kernel: larger first, NaN last, ties to the lower
+// index); sets the pre-screen flag for the next generation.
+__global__ void __launch_bounds__(1024) audit_kernel(int32_t n, const int32_t* __restrict__ order_p,
+                                                     const int32_t* __restrict__ order_m, int32_t* __restrict__ rank_m,
+                                                     float* __restrict__ stat, int32_t* __restrict__ use_screen,
+                                                     int32_t allow, float min_rho)
 {
     __shared__ double red[1024];
+    for (int32_t i = threadIdx.x; i < n; i += 1024) rank_m[order_m[i]] = i;
+    __syncthreads();
     double d2 = 0.0;
-    for (int32_t i = threadIdx.x; i < n; i += 1024) {
-        int32_t rp = 0, rm = 0;
-        for (int32_t j = 0; j < n; ++j) {
-            rp += before(pred_rows[j], j, pred_rows[i], i) ? 1 : 0;
-            rm += before(meas[j], j, meas[i], i) ? 1 : 0;
-        }
-        const double d = static_cast<double>(rp - rm);
+    for (int32_t i = threadIdx.x; i < n; i += 1024) {  // row order_p[i] has score rank i
+        const double d = static_cast<double>(i - rank_m[order_p[i]]);
         d2 += d * d;
     }
     red[threadIdx.x] = d2;
@@ -256,7 +248,6 @@ __global__ void __launch_bounds__(1024) audit_kernel(int32_t n, const float* __r
     }
 }
 
-// recipes + descriptors, scores + choice, breed, evaluate, audit + training
 constexpr int kSurrStages = 5;
 
 }  // namespace
@@ -298,6 +289,7 @@ struct leea_surr {
     float *mu = nullptr, *sd = nullptr, *probe = nullptr;
     float *x_hist = nullptr, *t_hist = nullptr, *meas = nullptr, *pred_rows = nullptr;
     int32_t* row_recipe = nullptr;
+    int32_t *rank_p = nullptr, *rank_m = nullptr, *rank_tmp = nullptr;  // audit rankings
     int32_t* use_screen = nullptr;
     float* stats = nullptr;  // per breeding generation: spearman, screened, loss
     int64_t stats_cap = 0, adam_step = 0;
@@ -327,7 +319,7 @@ void free_surr(leea_surr* s)
                      s->r_entity, s->a_par1, s->a_par2, s->a_kind, s->a_entity, s->a_pop, s->a_amax, s->a_f,
                      s->a_shadow, s->theta, s->adam_m, s->adam_v, s->grad, s->work, s->loss, s->mu, s->sd,
                      s->probe, s->x_hist, s->t_hist, s->meas, s->pred_rows, s->row_recipe, s->use_screen,
-                     s->stats, s->scratch, s->x_stage, s->y_stage };
+                     s->stats, s->scratch, s->x_stage, s->y_stage, s->rank_p, s->rank_m, s->rank_tmp };
     for (void* p : ptrs) cudaFree(p);
     for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
     delete s;
@@ -509,8 +501,11 @@ leea_status surr_breed_generation(leea_surr* s, const uint8_t* x, float x_div, c
     targets_kernel<<<1, 256, 0, st>>>(s->rows, s->k, s->n_elite, s->f_raw, s->a_f, s->pred, s->row_recipe, s->meas,
                                       s->pred_rows, t_slot);
     const int64_t stat_i = s->breeds < s->stats_cap ? s->breeds : s->stats_cap - 1;
-    audit_kernel<<<1, 1024, 0, st>>>(s->rows, s->pred_rows, s->meas, s->stats + 3 * stat_i, s->use_screen,
-                                     static_cast<int32_t>(g) >= s->sp.warmup ? 1 : 0, s->sp.min_spearman);
+    LEEA_CUDA_TRY(launch_rank(s->rows, s->pred_rows, s->rank_p, st), "rank kernel");
+    LEEA_CUDA_TRY(launch_rank(s->rows, s->meas, s->rank_m, st), "rank kernel");
+    audit_kernel<<<1, 1024, 0, st>>>(s->rows, s->rank_p, s->rank_m, s->rank_tmp, s->stats + 3 * stat_i,
+                                     s->use_screen, static_cast<int32_t>(g) >= s->sp.warmup ? 1 : 0,
+                                     s->sp.min_spearman);
     gather_rows_kernel<<<s->rows, 128, 0, st>>>(s->rows, s->width, s->row_recipe, s->x_std, x_slot);
     LEEA_CUDA_TRY(cudaGetLastError(), "audit kernels");
     const int64_t filled = (s->breeds + 1 < s->sp.history ? s->breeds + 1 : s->sp.history) * s->rows;
@@ -657,6 +652,9 @@ leea_status leea_surr_create(int32_t pop, const int32_t* dims, int32_t n_dims, c
     if (err == cudaSuccess) err = alloc(&s->meas, static_cast<size_t>(s->rows));
     if (err == cudaSuccess) err = alloc(&s->pred_rows, static_cast<size_t>(s->rows));
     if (err == cudaSuccess) err = alloc(&s->row_recipe, static_cast<size_t>(s->rows));
+    if (err == cudaSuccess) err = alloc(&s->rank_p, static_cast<size_t>(s->rows));
+    if (err == cudaSuccess) err = alloc(&s->rank_m, static_cast<size_t>(s->rows));
+    if (err == cudaSuccess) err = alloc(&s->rank_tmp, static_cast<size_t>(s->rows));
     if (err == cudaSuccess) err = alloc(&s->use_screen, 1);
     if (err == cudaSuccess) err = alloc(&s->stats, static_cast<size_t>(3 * s->stats_cap));
     if (err != cudaSuccess) {
@@ -902,6 +900,27 @@ leea_status leea_surr_stats(leea_surr* s, int64_t n_max, float* spearman, int32_
         if (loss) loss[i] = buf[3 * i + 2];
     }
     return LEEA_OK;
+}
+
+leea_status leea_surr_best_params(leea_surr* s, float* out_host, int64_t c)
+{
+    leea_status st = check_surr(s);
+    if (st) return st;
+    if (!s->evaluated) return fail(LEEA_ESTATE, "no generation has been evaluated yet");
+    if (!out_host || c != s->net.c) return fail(LEEA_EINVAL, "out_host NULL or c != %lld", (long long)s->net.c);
+    std::vector<float> f(static_cast<size_t>(s->pop));
+    LEEA_CUDA_TRY(cudaMemcpyAsync(f.data(), s->f_adj, sizeof(float) * s->pop, cudaMemcpyDeviceToHost, s->stream),
+                  "fitness copy");
+    if ((st = check_device_status(s->stream, nullptr))) return st;
+    int32_t best = 0;  // highest f_adj, NaN as -infinity, ties to the lower index
+    for (int32_t p = 1; p < s->pop; ++p) {
+        const float a = std::isnan(f[p]) ? -INFINITY : f[p], b = std::isnan(f[best]) ? -INFINITY : f[best];
+        if (a > b) best = p;
+    }
+    LEEA_CUDA_TRY(cudaMemcpyAsync(out_host, s->popbuf[s->cur] + static_cast<int64_t>(best) * s->net.c_pad,
+                                  sizeof(float) * static_cast<size_t>(c), cudaMemcpyDeviceToHost, s->stream),
+                  "best params copy");
+    return check_device_status(s->stream, nullptr);
 }
 
 uint32_t leea_surr_generation_index(const leea_surr* s) { return s ? s->gen : 0u; }

@@ -17,7 +17,7 @@ namespace leea {
 namespace {
 
 constexpr uint32_t kTagSurrInit = 6;
-constexpr int kRows = 32;      // rows per forward CTA
+constexpr int kRows = 32;      // rows per forward CTA at most (fewer for small n: more CTAs)
 constexpr int kFwdThreads = 256;
 
 struct MlpView {
@@ -62,26 +62,26 @@ __global__ void surr_init_kernel(int32_t d_in, int32_t h1, int32_t h2, uint64_t 
     }
 }
 
-// Forward for kRows rows per CTA; a1 / a2 (the ReLU outputs) are kept for
+// Forward for `rpc` rows per CTA; a1 / a2 (the ReLU outputs) are kept for
 // the backward pass when not NULL.  Dot products run over k in order.
 __global__ void __launch_bounds__(kFwdThreads)
-surr_forward_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* __restrict__ theta,
+surr_forward_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, int32_t rpc, const float* __restrict__ theta,
                     const float* __restrict__ x, float* __restrict__ y, float* __restrict__ a1_out,
                     float* __restrict__ a2_out)
 {
     extern __shared__ float sm[];
-    float* xs = sm;                       // [kRows][d_in]
-    float* s1 = xs + kRows * d_in;        // [kRows][h1]
-    float* s2 = s1 + kRows * h1;          // [kRows][h2]
+    float* xs = sm;                       // [rpc][d_in]
+    float* s1 = xs + rpc * d_in;          // [rpc][h1]
+    float* s2 = s1 + rpc * h1;            // [rpc][h2]
     const MlpView p = view(theta, d_in, h1, h2);
-    const int32_t r0 = blockIdx.x * kRows;
-    const int32_t rows = n - r0 < kRows ? n - r0 : kRows;
-    for (int i = threadIdx.x; i < kRows * d_in; i += kFwdThreads) {
+    const int32_t r0 = blockIdx.x * rpc;
+    const int32_t rows = n - r0 < rpc ? n - r0 : rpc;
+    for (int i = threadIdx.x; i < rpc * d_in; i += kFwdThreads) {
         const int r = i / d_in;
         xs[i] = r < rows ? x[static_cast<int64_t>(r0 + r) * d_in + (i - r * d_in)] : 0.0f;
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < kRows * h1; o += kFwdThreads) {
+    for (int o = threadIdx.x; o < rpc * h1; o += kFwdThreads) {
         const int r = o / h1, u = o - r * h1;
         const float* w = p.W1 + static_cast<int64_t>(u) * d_in;
         const float* xr = xs + r * d_in;
@@ -90,7 +90,7 @@ surr_forward_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float
         s1[o] = fmaxf(z, 0.0f);
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < kRows * h2; o += kFwdThreads) {
+    for (int o = threadIdx.x; o < rpc * h2; o += kFwdThreads) {
         const int r = o / h2, u = o - r * h2;
         const float* w = p.W2 + static_cast<int64_t>(u) * h1;
         const float* ar = s1 + r * h1;
@@ -229,7 +229,9 @@ cudaError_t launch_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_
     cudaError_t err = cudaFuncSetAttribute(surr_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    surr_forward_kernel<<<(n + kRows - 1) / kRows, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+    // rows per CTA: 32 when the rows fill the GPU several times, fewer otherwise
+    const int32_t rpc = n >= 32 * 512 ? 32 : (n >= 8 * 512 ? 8 : 2);
+    surr_forward_kernel<<<(n + rpc - 1) / rpc, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, rpc, theta, x, y, a1, a2);
     return cudaGetLastError();
 }
 

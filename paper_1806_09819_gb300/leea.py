@@ -177,6 +177,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_surr_get_step": [vp] + [vp] * 13,
         "leea_surr_get_surrogate": [vp, vp, vp, vp],
         "leea_surr_stats": [vp, i64, vp, vp, vp, vp],
+        "leea_surr_best_params": [vp, vp, i64],
         "leea_surr_generation_index": ([vp], u32),
         "leea_surr_profile_enable": [vp, i32],
         "leea_surr_profile_read": [vp, vp, vp],
@@ -219,7 +220,8 @@ def exported_symbols() -> list[str]:
             "leea_surr_generation_u8_host", "leea_surr_fitness", "leea_surr_raw_fitness", "leea_surr_get_population",
             "leea_surr_set_population", "leea_surr_set_fitness", "leea_surr_set_generation", "leea_surr_set_screen",
             "leea_surr_layout", "leea_surr_get_step", "leea_surr_get_surrogate", "leea_surr_stats",
-            "leea_surr_generation_index", "leea_surr_profile_enable", "leea_surr_profile_read", "leea_surr_destroy"]
+            "leea_surr_generation_index", "leea_surr_profile_enable", "leea_surr_profile_read", "leea_surr_destroy",
+            "leea_surr_best_params"]
 
 
 def _check(rc: int) -> None:
@@ -802,6 +804,11 @@ class SurrState:
 
     def n_rows(self) -> int:
         return self.n_recipes // max(1, self._sp.mult) + self.n_audit
+
+    def best_params(self) -> np.ndarray:
+        out = np.empty(self.c, dtype=np.float32)
+        _check(self.lib.leea_surr_best_params(self._h, _hp(out), self.c))
+        return out
 
     def get_surrogate(self):
         th = np.empty(self.n_theta, np.float32)
