@@ -2,20 +2,27 @@
 // minibatches of 8-bit image levels, x = k / x_div with k in [0, 255] (MNIST's
 // encoding), on the tcgen05 tensor cores with FP32-class accuracy.
 //
-// The integers k are exact in BF16, and every FP32 weight is split exactly into
-// three BF16 pieces w = w1 + w2 + w3 (8 significant bits each).  So
-// D = K W1_p^T = sum_i K w_i is formed from exact products, and only the FP32
-// accumulation in the tensor core rounds.  The epilogue scales by 1 / x_div.
+// The integers k are exact in FP16, and every FP32 weight, scaled by 2^8, is
+// split into two FP16 pieces: w1 = fp16(2^8 w) and w2 = fp16(2^8 w - w1), with
+// the remainder exact in FP32.  So |2^8 w - w1 - w2| <= max(2^-22 2^8 |w|,
+// 2^-25): a 22-bit significand against FP32's 24, and D = K (w1 + w2)^T is
+// formed from exact products; only the FP32 accumulation in the tensor core
+// rounds.  The epilogue scales by 2^-8 / x_div.  An individual with a weight
+// |w| >= 128 (its scaled w1 could overflow FP16) is flagged by the converters,
+// and the epilogue forms its layer 1 with FP32 FFMA from global memory instead
+// of the accumulator, so every weight range is evaluated in FP32 accuracy.
 //
 // The batch (<= 128 samples) is written once per CTA into tensor memory as
-// the MMA's A operand (lane = sample, two BF16 per column), so shared memory
-// only carries the weight pieces: per 64-wide K stage, 3 x h rows of 128
-// bytes in the 128-byte swizzled K-major layout.
+// the MMA's A operand (lane = sample, two FP16 per column), so shared memory
+// only carries the weight pieces: per 64-wide K stage, 2 x h rows of 128
+// bytes in the 128-byte swizzled K-major layout.  Two pieces cost two MMAs per
+// 16 inputs (the tensor core's per-instruction cost, not its FLOP rate, bounds
+// this kernel at h = 112).
 //
 // Warp roles (persistent CTA, one per SM, individuals strided by gridDim.x):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
 //   warp 1      TMA producer: FP32 W1 tiles (h rows x 64 K) into a raw ring
-//   warps 2-9   converters: split each raw tile into three BF16 pieces and
+//   warps 2-9   converters: split each raw tile into two FP16 pieces and
 //               store them swizzled into the piece ring the MMAs read
 //   warps 10-13 write the batch into TMEM once; then the epilogue (bias,
 //               ReLU, layer 2 with W2 staged transposed in shared memory,
@@ -23,7 +30,7 @@
 // Every mbarrier wait is bounded in time; on expiry the kernel sets
 // kStatusEvalTimeout, drains its MMAs and exits.
 #include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "leea_internal.h"
 #include "tc_ptx.cuh"
@@ -37,11 +44,15 @@ constexpr int kFirstLoaderWarp = 2;
 constexpr int kFirstEpilogueWarp = kFirstLoaderWarp + kLoaderWarps;
 constexpr int kU8Threads = 32 * (kFirstEpilogueWarp + 4);
 constexpr int kKStage = 64;        // K elements per stage: one 128-byte BF16 row
-constexpr int kMaxPieceStages = 3;  // BF16 piece ring
-constexpr int kMaxRawStages = 4;    // FP32 raw ring (TMA)
+constexpr int kPieces = 2;          // FP16 pieces per weight
+constexpr int kMaxPieceStages = 3;  // piece ring
+constexpr int kMaxRawStages = 6;    // FP32 raw ring (TMA)
 constexpr int kMaxOutU8 = 16;
 constexpr int kRowBatch = 8;       // 16-row groups a loader thread holds in registers at once
+constexpr int kXGroups = 7;        // 32-level groups of the batch row loaded at once
 constexpr uint32_t kTmemCols = 512;
+constexpr float kPieceScale = 256.0f;   // 2^8: weights enter the pieces as 2^8 w
+constexpr float kPieceRange = 128.0f;   // |w| below this: 2^8 |w| < 2^15, finite in FP16
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr uint64_t kDrainLimitNs = 200000000ull;
 
@@ -62,17 +73,21 @@ struct EvalU8Args {
 };
 
 struct U8Smem {
-    uint8_t* ring;        // piece_stages x 3 pieces x h x 128 B (1024-aligned)
+    uint8_t* ring;        // piece_stages x kPieces x h x 128 B (1024-aligned)
     uint8_t* raw;         // raw_stages x h x 256 B (FP32 rows of 64 K-elements)
     uint32_t piece_bytes, raw_bytes;
     uint8_t* prm_raw;     // 2 x prm_bytes: b1, W2 (row-major), b2 as stored, bulk-copied
     float* w2t;           // [h][dpad]
     float* b1;            // [h]
     float* b2;            // [16]
+    float* hbuf;          // [batch][h + 4]: the accumulator, staged so TMEM is released early
     uint64_t *full, *empty, *raw_full, *raw_empty, *prm_full, *prm_empty, *acc_full, *acc_empty, *a_ready, *drain;
+    uint64_t* conv_done;  // [2]: the converters finished individual (unit) u, by u & 1
+    uint64_t* x_loaded;   // the epilogue warps have read the batch from global memory
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
+    uint32_t* flag_unit;  // [2]: u + 1 if individual (unit) u has a weight outside the piece range
     float* red_loss;
     int32_t* red_ok;
 };
@@ -83,7 +98,7 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     s.ring = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
     s.piece_bytes = static_cast<uint32_t>(a.h) * 128u;
     s.raw_bytes = static_cast<uint32_t>(a.h) * 256u;
-    s.raw = s.ring + a.piece_stages * 3u * s.piece_bytes;
+    s.raw = s.ring + a.piece_stages * kPieces * s.piece_bytes;
     uint8_t* p = s.raw + a.raw_stages * s.raw_bytes;
     s.prm_raw = p;
     p += 2u * a.prm_bytes;
@@ -93,6 +108,8 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     p += sizeof(float) * a.h;
     s.b2 = reinterpret_cast<float*>(p);
     p += sizeof(float) * 16;
+    s.hbuf = reinterpret_cast<float*>(p);
+    p += sizeof(float) * a.batch * (a.h + 4);
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.full = bars;
     s.empty = bars + a.piece_stages;
@@ -104,10 +121,13 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     s.acc_empty = s.acc_full + 1;
     s.a_ready = s.acc_full + 2;
     s.drain = s.acc_full + 3;
-    uint32_t* w = reinterpret_cast<uint32_t*>(s.acc_full + 4);
+    s.conv_done = s.acc_full + 4;
+    s.x_loaded = s.acc_full + 6;
+    uint32_t* w = reinterpret_cast<uint32_t*>(s.acc_full + 7);
     s.tmem_holder = w;
     s.abort_flag = reinterpret_cast<volatile int*>(w + 1);
     s.ep_go = reinterpret_cast<int*>(w + 2);
+    s.flag_unit = w + 12;
     s.red_loss = reinterpret_cast<float*>(w + 4);
     s.red_ok = reinterpret_cast<int32_t*>(w + 8);
     return s;
@@ -118,21 +138,23 @@ uint32_t u8_prm_bytes(int32_t h, int32_t d_out)
     return (static_cast<uint32_t>(h + d_out * h + d_out) * 4u + 15u) & ~15u;
 }
 
-size_t u8_smem_bytes(int32_t h, int32_t dpad, int32_t piece_stages, int32_t raw_stages)
+size_t u8_smem_bytes(int32_t h, int32_t dpad, int32_t batch, int32_t piece_stages, int32_t raw_stages)
 {
     const int32_t d_out = dpad;  // upper bound for the raw parameter area
-    return 1024 + static_cast<size_t>(piece_stages) * 3 * h * 128 + static_cast<size_t>(raw_stages) * h * 256 +
+    return 1024 + static_cast<size_t>(piece_stages) * kPieces * h * 128 + static_cast<size_t>(raw_stages) * h * 256 +
            2 * u8_prm_bytes(h, d_out) + sizeof(float) * (h * dpad + h + 16) +
-           8 * (2 * piece_stages + 2 * raw_stages + 4 + 4) + 64;
+           sizeof(float) * static_cast<size_t>(batch) * (h + 4) + 8 * (2 * piece_stages + 2 * raw_stages + 4 + 7) +
+           64;
 }
 
-// Ring depths (piece, raw) that fit in 227 KB of shared memory, deepest piece
-// ring first; false if not even (2, 2) fits.
-bool u8_stages(int32_t h, int32_t dpad, int32_t* piece, int32_t* raw)
+// Ring depths (piece, raw) that fit in 227 KB of shared memory, deepest raw
+// ring first (the raw ring holds the HBM loads in flight, the piece ring only
+// decouples converters from MMAs); false if not even (2, 2) fits.
+bool u8_stages(int32_t h, int32_t dpad, int32_t batch, int32_t* piece, int32_t* raw)
 {
-    for (int32_t ps = kMaxPieceStages; ps >= 2; --ps)
-        for (int32_t rs = kMaxRawStages; rs >= 2; --rs)
-            if (u8_smem_bytes(h, dpad, ps, rs) <= 227u * 1024u) {
+    for (int32_t rs = kMaxRawStages; rs >= 2; --rs)
+        for (int32_t ps = kMaxPieceStages; ps >= 2; --ps)
+            if (u8_smem_bytes(h, dpad, batch, ps, rs) <= 227u * 1024u) {
                 *piece = ps;
                 *raw = rs;
                 return true;
@@ -146,25 +168,27 @@ __device__ __forceinline__ void raise_abort(const U8Smem& s, const EvalU8Args& a
     atomicOr(a.status, kStatusEvalTimeout);
 }
 
-__device__ __forceinline__ uint32_t bf162_bits(__nv_bfloat162 v)
+__device__ __forceinline__ uint32_t half2_bits(__half2 v)
 {
     return *reinterpret_cast<uint32_t*>(&v);
 }
 
-// Exact three-way split of two FP32 values into packed BF16 pairs (lower K
-// index in the low half): each piece rounds the remainder of the previous
-// ones to nearest, and the remainders are exact in FP32.
-__device__ __forceinline__ void split3x2(float w0, float w1, uint32_t& p1, uint32_t& p2, uint32_t& p3)
+// Two FP32 weights (lower K index in the low half) as packed FP16 pieces of
+// 2^8 w: p1 rounds 2^8 w to nearest, p2 rounds the remainder, which is exact
+// in FP32.
+__device__ __forceinline__ void split2x2(float w0, float w1, uint32_t& p1, uint32_t& p2)
 {
-    const __nv_bfloat162 h1 = __floats2bfloat162_rn(w0, w1);
-    const float2 f1 = __bfloat1622float2(h1);
-    const float r0 = w0 - f1.x, r1 = w1 - f1.y;
-    const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0, r1);
-    const float2 f2 = __bfloat1622float2(h2);
-    const __nv_bfloat162 h3 = __floats2bfloat162_rn(r0 - f2.x, r1 - f2.y);
-    p1 = bf162_bits(h1);
-    p2 = bf162_bits(h2);
-    p3 = bf162_bits(h3);
+    const float s0 = w0 * kPieceScale, s1 = w1 * kPieceScale;
+    const __half2 h1 = __floats2half2_rn(s0, s1);
+    const float2 f1 = __half22float2(h1);
+    p1 = half2_bits(h1);
+    p2 = half2_bits(__floats2half2_rn(s0 - f1.x, s1 - f1.y));
+}
+
+__device__ __forceinline__ bool out_of_piece_range(const float4& v)
+{
+    return fabsf(v.x) >= kPieceRange || fabsf(v.y) >= kPieceRange || fabsf(v.z) >= kPieceRange ||
+           fabsf(v.w) >= kPieceRange;
 }
 
 __global__ void __launch_bounds__(kU8Threads, 1)
@@ -192,8 +216,13 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
         ptx::mbar_init(s.acc_empty, 128);
         ptx::mbar_init(s.a_ready, 128);
         ptx::mbar_init(s.drain, 1);
+        ptx::mbar_init(&s.conv_done[0], kLoaderWarps);
+        ptx::mbar_init(&s.conv_done[1], kLoaderWarps);
+        ptx::mbar_init(s.x_loaded, 128);
         *s.abort_flag = 0;
         *s.ep_go = 0;
+        s.flag_unit[0] = 0;
+        s.flag_unit[1] = 0;
         ptx::fence_mbar_init();
     }
     if (warp == 0) ptx::tmem_alloc(s.tmem_holder, kTmemCols);
@@ -205,7 +234,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
     if (warp == 0) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t idesc = ptx::idesc_bf16(128, static_cast<uint32_t>(a.h));
+            const uint32_t idesc = ptx::idesc_f16(128, static_cast<uint32_t>(a.h));
             bool ok = ptx::mbar_wait_bounded(s.a_ready, 0u, s.abort_flag, kWaitLimitNs);
             if (!ok) raise_abort(s, a);
             ptx::tc_fence_after();
@@ -225,14 +254,14 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                         break;
                     }
                     ptx::tc_fence_after();
-                    const uint32_t sb = ring + stage * 3u * s.piece_bytes;
+                    const uint32_t sb = ring + stage * kPieces * s.piece_bytes;
 #pragma unroll
                     for (int kk = 0; kk < kKStage / 16; ++kk) {
                         const int kg = kc * kKStage + kk * 16;
                         if (kg >= a.k16) break;
                         const uint32_t a_tmem = tmem_base + a.a_col + static_cast<uint32_t>(kg >> 1);
 #pragma unroll
-                        for (int piece = 0; piece < 3; ++piece) {
+                        for (int piece = 0; piece < kPieces; ++piece) {
                             const uint64_t bd = ptx::smem_desc_sw128(sb + piece * s.piece_bytes + kk * 32u);
                             ptx::mma_f16_tmem_a(tmem_base, a_tmem, bd, idesc, (kc | kk | piece) != 0 ? 1u : 0u);
                         }
@@ -254,7 +283,10 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
             uint32_t stage = 0, phase = 0;
             uint32_t issued_mask = 0, parity_mask = 0;
             uint32_t prm_issued = 0;  // units whose parameters were requested
-            bool ok = true;
+            // The batch loads go first: queued behind the first weight tiles
+            // of every SM they take several times as long.
+            bool ok = ptx::mbar_wait_bounded(s.x_loaded, 0u, s.abort_flag, kWaitLimitNs);
+            if (!ok) raise_abort(s, a);
             for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
                 {
                     // b1, W2, b2 of individual p into parameter buffer (unit & 1).
@@ -298,9 +330,9 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
         const int lt = threadIdx.x - 32 * kFirstLoaderWarp;
         const int row0 = lt >> 4, c4 = lt & 15;
         const int groups = a.h >> 4;
-        uint32_t rstage = 0, rphase = 0, stage = 0, phase = 0;
+        uint32_t rstage = 0, rphase = 0, stage = 0, phase = 0, unit = 0;
         bool ok = true;
-        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x, ++unit) {
             for (int kc = 0; kc < a.k_stages; ++kc) {
                 if (!ptx::mbar_wait_bounded(&s.raw_full[rstage], rphase, s.abort_flag, kWaitLimitNs)) {
                     raise_abort(s, a);
@@ -321,25 +353,32 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                     ok = false;
                     break;
                 }
-                uint8_t* sb = s.ring + stage * 3u * s.piece_bytes;
+                uint8_t* sb = s.ring + stage * kPieces * s.piece_bytes;
+                bool bad = false;
 #pragma unroll
                 for (int u = 0; u < kRowBatch; ++u) {
                     if (u < groups) {
                         const int r = row0 + 16 * u;
-                        uint32_t lo[3], hi[3];  // pieces of (x, y) and of (z, w)
-                        split3x2(v[u].x, v[u].y, lo[0], lo[1], lo[2]);
-                        split3x2(v[u].z, v[u].w, hi[0], hi[1], hi[2]);
+                        uint32_t lo[kPieces], hi[kPieces];  // pieces of (x, y) and of (z, w)
+                        split2x2(v[u].x, v[u].y, lo[0], lo[1]);
+                        split2x2(v[u].z, v[u].w, hi[0], hi[1]);
+                        bad |= out_of_piece_range(v[u]);
                         const uint32_t off = static_cast<uint32_t>(r) * 128u +
                                              ((static_cast<uint32_t>(c4 >> 1) ^ static_cast<uint32_t>(r & 7)) << 4) +
                                              (static_cast<uint32_t>(c4 & 1) << 3);
 #pragma unroll
-                        for (int piece = 0; piece < 3; ++piece)
+                        for (int piece = 0; piece < kPieces; ++piece)
                             *reinterpret_cast<uint2*>(sb + piece * s.piece_bytes + off) = make_uint2(lo[piece], hi[piece]);
                     }
                 }
+                if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) s.flag_unit[unit & 1u] = unit + 1u;
                 ptx::fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) ptx::mbar_arrive(&s.full[stage]);
+                if (lane == 0) {
+                    ptx::mbar_arrive(&s.full[stage]);
+                    // the flag (if any) is released to the epilogue with this arrival
+                    if (kc == a.k_stages - 1) ptx::mbar_arrive(&s.conv_done[unit & 1u]);
+                }
                 if (++stage == static_cast<uint32_t>(a.piece_stages)) { stage = 0; phase ^= 1u; }
             }
         }
@@ -354,37 +393,54 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
             const uint8_t* xr = a.x + static_cast<int64_t>(row) * a.k;
             const bool live = row < a.batch;
             const bool vec = (a.k % 16 == 0) && ((reinterpret_cast<uintptr_t>(a.x) & 15u) == 0);
-#pragma unroll 2
-            for (int c0 = 0; c0 < a.k16 / 2; c0 += 16) {
-                uint32_t bytes[8];  // the 32 levels of columns c0 .. c0+15
-                const int k0 = 2 * c0;
-                if (vec && live && k0 + 32 <= a.k) {
-                    const uint4 lo4 = __ldg(reinterpret_cast<const uint4*>(xr + k0));
-                    const uint4 hi4 = __ldg(reinterpret_cast<const uint4*>(xr + k0 + 16));
-                    bytes[0] = lo4.x; bytes[1] = lo4.y; bytes[2] = lo4.z; bytes[3] = lo4.w;
-                    bytes[4] = hi4.x; bytes[5] = hi4.y; bytes[6] = hi4.z; bytes[7] = hi4.w;
-                } else {
+            // kXGroups groups of 16 columns (32 levels) per round: their loads
+            // are all in flight at once, so the fill costs a few memory
+            // latencies, not one per group.
+            const int n_groups = (a.k16 + 31) / 32;  // the last may hold 8 columns past k16 / 2, zero
+            for (int g0 = 0; g0 < n_groups; g0 += kXGroups) {
+                uint4 lv[kXGroups][2];
 #pragma unroll
-                    for (int w = 0; w < 8; ++w) {
-                        uint32_t word = 0;
+                for (int b = 0; b < kXGroups; ++b) {
+                    const int k0 = 32 * (g0 + b);
+                    if (!live || g0 + b >= n_groups) {
+                        lv[b][0] = make_uint4(0u, 0u, 0u, 0u);
+                        lv[b][1] = lv[b][0];
+                    } else if (vec && k0 + 32 <= a.k) {
+                        lv[b][0] = __ldg(reinterpret_cast<const uint4*>(xr + k0));
+                        lv[b][1] = __ldg(reinterpret_cast<const uint4*>(xr + k0 + 16));
+                    } else {
+                        uint32_t wds[8];
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) {
-                            const int kk = k0 + 4 * w + b;
-                            if (live && kk < a.k) word |= static_cast<uint32_t>(xr[kk]) << (8 * b);
+                        for (int w = 0; w < 8; ++w) {
+                            uint32_t word = 0;
+#pragma unroll
+                            for (int q8 = 0; q8 < 4; ++q8) {
+                                const int kk = k0 + 4 * w + q8;
+                                if (kk < a.k) word |= static_cast<uint32_t>(xr[kk]) << (8 * q8);
+                            }
+                            wds[w] = word;
                         }
-                        bytes[w] = word;
+                        lv[b][0] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
+                        lv[b][1] = make_uint4(wds[4], wds[5], wds[6], wds[7]);
                     }
                 }
-                uint32_t cols[16];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const uint32_t pair = bytes[i >> 1] >> (16 * (i & 1));
-                    const uint32_t lo = pair & 0xFFu, hi = (pair >> 8) & 0xFFu;
-                    cols[i] = (__float_as_uint(static_cast<float>(lo)) >> 16) |
-                              (__float_as_uint(static_cast<float>(hi)) & 0xFFFF0000u);
+                for (int b = 0; b < kXGroups; ++b) {
+                    if (g0 + b < n_groups) {
+                        const uint32_t bytes[8] = { lv[b][0].x, lv[b][0].y, lv[b][0].z, lv[b][0].w,
+                                                    lv[b][1].x, lv[b][1].y, lv[b][1].z, lv[b][1].w };
+                        uint32_t cols[16];
+#pragma unroll
+                        for (int i = 0; i < 16; ++i) {
+                            const uint32_t pair = bytes[i >> 1] >> (16 * (i & 1));
+                            const uint32_t lo = pair & 0xFFu, hi = (pair >> 8) & 0xFFu;
+                            cols[i] = half2_bits(__floats2half2_rn(static_cast<float>(lo), static_cast<float>(hi)));
+                        }
+                        ptx::tmem_st16(tmem_base + lane_addr + a.a_col + static_cast<uint32_t>(16 * (g0 + b)), cols);
+                    }
                 }
-                ptx::tmem_st16(tmem_base + lane_addr + a.a_col + static_cast<uint32_t>(c0), cols);
             }
+            ptx::mbar_arrive(s.x_loaded);
             ptx::tmem_st_wait();
             ptx::tc_fence_before();
             ptx::mbar_arrive(s.a_ready);
@@ -417,20 +473,60 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
             if (et < 16) s.b2[et] = et < a.d_out ? src[a.h + a.d_out * a.h + et] : 0.0f;
             ptx::mbar_arrive(&s.prm_empty[pb]);
             if (et == 0) {
-                const bool got = ptx::mbar_wait_bounded(s.acc_full, acc_phase, s.abort_flag, kWaitLimitNs);
+                bool got = ptx::mbar_wait_bounded(s.acc_full, acc_phase, s.abort_flag, kWaitLimitNs) &&
+                           ptx::mbar_wait_bounded(&s.conv_done[unit & 1u], (unit >> 1) & 1u, s.abort_flag,
+                                                  kWaitLimitNs);
                 if (!got) raise_abort(s, a);
-                *s.ep_go = got ? 1 : 0;
+                *s.ep_go = !got ? 0 : (s.flag_unit[unit & 1u] == unit + 1u ? 2 : 1);
             }
             ptx::named_barrier_sync(1, 128);  // A2: accumulator ready (or abort); parameters staged
-            if (!*s.ep_go) { ok = false; break; }
+            const int go = *s.ep_go;
+            if (!go) { ok = false; break; }
             ptx::tc_fence_after();
+            // Individuals with a weight outside the piece range: layer 1 by FP32
+            // FFMA from global memory, k in order, in the accumulator's units.
+            const float* w1p = a.popv + static_cast<int64_t>(p) * a.c_pad;
+            const uint8_t* xrow = a.x + static_cast<int64_t>(row < a.batch ? row : 0) * a.k;
+
+            // Stage this lane's accumulator row in shared memory and release
+            // TMEM, so the next individual's MMAs overlap the rest of the
+            // epilogue (rows >= batch take part in the collective loads only).
+            float* hrow = s.hbuf + (row < a.batch ? row : 0) * (a.h + 4);
+            for (int c = 0; c < a.h; c += 16) {
+                float v[16];
+                ptx::tmem_ld16(tmem_base + lane_addr + static_cast<uint32_t>(c), v);
+                if (row < a.batch) {
+#pragma unroll
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4*>(hrow + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
+            }
+            ptx::tc_fence_before();
+            ptx::mbar_arrive(s.acc_empty);
+            acc_phase ^= 1u;
 
             float logit[kMaxOutU8];
 #pragma unroll
             for (int o = 0; o < kMaxOutU8; ++o) logit[o] = 0.0f;
-            for (int c = 0; c < a.h; c += 16) {
+            for (int c = 0; row < a.batch && c < a.h; c += 16) {
                 float v[16];
-                ptx::tmem_ld16(tmem_base + lane_addr + static_cast<uint32_t>(c), v);
+#pragma unroll
+                for (int j = 0; j < 16; j += 4) {
+                    const float4 t4 = *reinterpret_cast<const float4*>(hrow + c + j);
+                    v[j] = t4.x;
+                    v[j + 1] = t4.y;
+                    v[j + 2] = t4.z;
+                    v[j + 3] = t4.w;
+                }
+                if (go == 2) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float* wr = w1p + static_cast<int64_t>(c + j) * a.k;
+                        float acc = 0.0f;
+                        for (int kk = 0; kk < a.k; ++kk) acc = fmaf(wr[kk], static_cast<float>(xrow[kk]), acc);
+                        v[j] = acc * kPieceScale;
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int col = c + j;
@@ -448,9 +544,6 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                     }
                 }
             }
-            ptx::tc_fence_before();
-            ptx::mbar_arrive(s.acc_empty);
-            acc_phase ^= 1u;
 
             float loss = 0.0f;
             int32_t good = 0;
@@ -541,7 +634,7 @@ bool eval_u8_tc_supported(const NetLayout& net, int32_t batch, const float* pop_
     if (reinterpret_cast<uintptr_t>(pop_dev) & 15u) return false;
     const int32_t dpad = (d_out + 3) / 4 * 4;
     int32_t ps = 0, rs = 0;
-    return u8_stages(h, dpad, &ps, &rs) && u8_encode_fn() != nullptr;
+    return u8_stages(h, dpad, batch, &ps, &rs) && u8_encode_fn() != nullptr;
 }
 
 cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
@@ -559,7 +652,7 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     a.k16 = (a.k + 15) / 16 * 16;
     a.k_stages = (a.k + kKStage - 1) / kKStage;
     a.c_pad = net.c_pad;
-    a.inv_div = static_cast<float>(1.0 / static_cast<double>(x_div));
+    a.inv_div = static_cast<float>(1.0 / (static_cast<double>(x_div) * kPieceScale));
     a.alpha = alpha;
     a.a_col = static_cast<uint32_t>(a.h);
     a.popv = pop_dev;
@@ -571,8 +664,8 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     a.correct = correct;
     a.status = status;
     a.prm_bytes = u8_prm_bytes(a.h, a.d_out);
-    if (!u8_stages(a.h, a.dpad, &a.piece_stages, &a.raw_stages)) return cudaErrorInvalidValue;
-    const size_t smem = u8_smem_bytes(a.h, a.dpad, a.piece_stages, a.raw_stages);
+    if (!u8_stages(a.h, a.dpad, a.batch, &a.piece_stages, &a.raw_stages)) return cudaErrorInvalidValue;
+    const size_t smem = u8_smem_bytes(a.h, a.dpad, a.batch, a.piece_stages, a.raw_stages);
     U8EncodeTiledFn enc = u8_encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tw;

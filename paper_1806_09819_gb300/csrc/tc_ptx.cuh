@@ -161,6 +161,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(uint32_t m, uint32_t n)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
 }
 
+// Instruction descriptor: D = F32, A = B = FP16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_f16(uint32_t m, uint32_t n)
+{
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((n >> 3) << 17) | ((m >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
                                          uint32_t accumulate)
 {

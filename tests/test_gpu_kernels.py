@@ -371,6 +371,31 @@ def test_evaluate_u8_clones_and_zero_weights(gpu):
     assert f[3] == f[4] == f[5] == f[6]
 
 
+def test_evaluate_u8_tensor_weights_outside_the_piece_range(gpu, oracle_mod):
+    # Weights with |w| >= 128 do not fit the tensor path's FP16 pieces; those
+    # individuals take the FP32 fallback. 400 individuals put several of them
+    # on one CTA in consecutive and non-consecutive turns; the others, and
+    # 127.5 (just inside the range), stay on the tensor path.
+    torch = _torch()
+    dims, pop, batch = [784, 112, 10], 400, 100
+    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    popv = synthetic.random_population(pop, c, seed=21, scale=0.05)
+    for p_, w_ in ((3, 300.0), (155, -128.0), (307, 1.0e6), (160, 200.0), (9, 127.5), (161, -127.5)):
+        popv[p_, (p_ * 37) % (dims[0] * dims[1])] = w_
+    x, y = synthetic.make_split(batch, seed=6)
+    levels = synthetic.to_levels(x)
+    pd = to_device_pop(popv, cp)
+    f_raw = torch.empty(pop, dtype=torch.float32, device="cuda")
+    cor = torch.empty(pop, dtype=torch.int32, device="cuda")
+    gpu.leea_evaluate_u8(pop, dims, pd, torch.from_numpy(levels).cuda(), 255.0, torch.from_numpy(y).cuda(), batch,
+                         1.0, None, f_raw, None, cor, eval_path=gpu.EVAL_TENSOR)
+    assert gpu.leea_device_status() == 0
+    f_ref, cor_ref, logits = oracle_mod.evaluate(popv.astype(np.float64), dims, levels.astype(np.float64) / 255.0, y,
+                                                 want_logits=True)
+    assert_fitness_close(f_raw.cpu().numpy(), f_ref)
+    assert_correct_close(cor.cpu().numpy(), cor_ref, logits)
+
+
 def test_u8_and_float_inputs_agree(gpu):
     # The same images as float x = k/255 and as levels k: both paths within
     # the fitness tolerance of each other at the full workload size.
