@@ -83,7 +83,8 @@ struct U8Smem {
     float* hbuf;          // [batch][h + 4]: the accumulator, staged so TMEM is released early
     uint64_t *full, *empty, *raw_full, *raw_empty, *prm_full, *prm_empty, *acc_full, *acc_empty, *a_ready, *drain;
     uint64_t* conv_done;  // [2]: the converters finished individual (unit) u, by u & 1
-    uint64_t* x_loaded;   // the epilogue warps have read the batch from global memory
+    uint64_t* x_loaded;   // the epilogue warps have read the batch (rings free for the weights)
+    uint64_t* x_full;     // a chunk of the batch landed in the staging area (the idle rings)
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
@@ -123,7 +124,8 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     s.drain = s.acc_full + 3;
     s.conv_done = s.acc_full + 4;
     s.x_loaded = s.acc_full + 6;
-    uint32_t* w = reinterpret_cast<uint32_t*>(s.acc_full + 7);
+    s.x_full = s.acc_full + 7;
+    uint32_t* w = reinterpret_cast<uint32_t*>(s.acc_full + 8);
     s.tmem_holder = w;
     s.abort_flag = reinterpret_cast<volatile int*>(w + 1);
     s.ep_go = reinterpret_cast<int*>(w + 2);
@@ -143,7 +145,7 @@ size_t u8_smem_bytes(int32_t h, int32_t dpad, int32_t batch, int32_t piece_stage
     const int32_t d_out = dpad;  // upper bound for the raw parameter area
     return 1024 + static_cast<size_t>(piece_stages) * kPieces * h * 128 + static_cast<size_t>(raw_stages) * h * 256 +
            2 * u8_prm_bytes(h, d_out) + sizeof(float) * (h * dpad + h + 16) +
-           sizeof(float) * static_cast<size_t>(batch) * (h + 4) + 8 * (2 * piece_stages + 2 * raw_stages + 4 + 7) +
+           sizeof(float) * static_cast<size_t>(batch) * (h + 4) + 8 * (2 * piece_stages + 2 * raw_stages + 4 + 8) +
            64;
 }
 
@@ -219,6 +221,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
         ptx::mbar_init(&s.conv_done[0], kLoaderWarps);
         ptx::mbar_init(&s.conv_done[1], kLoaderWarps);
         ptx::mbar_init(s.x_loaded, 128);
+        ptx::mbar_init(s.x_full, 1);
         *s.abort_flag = 0;
         *s.ep_go = 0;
         s.flag_unit[0] = 0;
@@ -389,55 +392,79 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
         const int row = q * 32 + lane;
         const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
         {
-            // Row `row` of the batch as BF16 pairs (k even in the low half).
+            // Row `row` of the batch into TMEM as FP16 pairs (lower k in the low
+            // half); group g = levels 32 g .. 32 g + 31 = columns 16 g .. 16 g + 15.
+            // The last group may reach 8 columns past k16 / 2; levels >= k are 0.
+            auto put_group = [&](int g, const uint32_t (&bytes)[8]) {
+                uint32_t cols[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const uint32_t pair = bytes[i >> 1] >> (16 * (i & 1));
+                    const uint32_t lo = pair & 0xFFu, hi = (pair >> 8) & 0xFFu;
+                    cols[i] = half2_bits(__floats2half2_rn(static_cast<float>(lo), static_cast<float>(hi)));
+                }
+                ptx::tmem_st16(tmem_base + lane_addr + a.a_col + static_cast<uint32_t>(16 * g), cols);
+            };
             const uint8_t* xr = a.x + static_cast<int64_t>(row) * a.k;
             const bool live = row < a.batch;
-            const bool vec = (a.k % 16 == 0) && ((reinterpret_cast<uintptr_t>(a.x) & 15u) == 0);
-            // kXGroups groups of 16 columns (32 levels) per round: their loads
-            // are all in flight at once, so the fill costs a few memory
-            // latencies, not one per group.
-            const int n_groups = (a.k16 + 31) / 32;  // the last may hold 8 columns past k16 / 2, zero
-            for (int g0 = 0; g0 < n_groups; g0 += kXGroups) {
-                uint4 lv[kXGroups][2];
+            const int n_groups = (a.k16 + 31) / 32;
+            const uint32_t region = static_cast<uint32_t>(a.piece_stages) * kPieces * s.piece_bytes +
+                                    static_cast<uint32_t>(a.raw_stages) * s.raw_bytes;
+            // Staged: chunks of every row land by bulk copies in the rings,
+            // which stay idle until the batch is in TMEM (one memory latency
+            // per chunk; one chunk at d_0 = 784 and h = 112).  Row stride
+            // kc + 16 bytes keeps the per-row reads free of bank conflicts.
+            const int kc = min(32 * n_groups, static_cast<int>((region / static_cast<uint32_t>(a.batch) - 16u) / 32u * 32u));
+            const bool staged = (a.k % 16 == 0) && ((reinterpret_cast<uintptr_t>(a.x) & 15u) == 0) && kc >= 32;
+            if (staged) {
+                const int stride = kc + 16;
+                uint32_t xphase = 0;
+                for (int k0 = 0; k0 < a.k16; k0 += kc, xphase ^= 1u) {
+                    const int bytes = min(kc, a.k - k0);  // multiple of 16
+                    if (et == 0) ptx::mbar_arrive_expect_tx(s.x_full, static_cast<uint32_t>(a.batch * bytes));
+                    if (live) ptx::bulk_load(s.ring + row * stride, xr + k0, static_cast<uint32_t>(bytes), s.x_full);
+                    const bool got = ptx::mbar_wait_bounded(s.x_full, xphase, s.abort_flag, kWaitLimitNs);
+                    if (!got) {  // let this chunk's copies land before anything reuses the rings
+                        raise_abort(s, a);
+                        volatile int never = 0;
+                        ptx::mbar_wait_bounded(s.x_full, xphase, &never, kDrainLimitNs);
+                    }
+                    const uint8_t* src = s.ring + (live ? row : 0) * stride;
+                    for (int g = 0; g < kc / 32 && k0 + 32 * g < a.k16; ++g) {
+                        uint32_t wds[8] = { 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u };
+                        if (live && got) {
+                            const uint4 v0 = *reinterpret_cast<const uint4*>(src + 32 * g);
+                            const uint4 v1 = *reinterpret_cast<const uint4*>(src + 32 * g + 16);
+                            wds[0] = v0.x; wds[1] = v0.y; wds[2] = v0.z; wds[3] = v0.w;
+                            if (k0 + 32 * g + 16 < a.k) { wds[4] = v1.x; wds[5] = v1.y; wds[6] = v1.z; wds[7] = v1.w; }
+                        }
+                        put_group(k0 / 32 + g, wds);
+                    }
+                    ptx::named_barrier_sync(1, 128);  // staging area read before the next chunk lands
+                }
+            } else {
+                // Direct: kXGroups groups per round, their loads all in flight.
+                for (int g0 = 0; g0 < n_groups; g0 += kXGroups) {
+                    uint32_t lv[kXGroups][8];
 #pragma unroll
-                for (int b = 0; b < kXGroups; ++b) {
-                    const int k0 = 32 * (g0 + b);
-                    if (!live || g0 + b >= n_groups) {
-                        lv[b][0] = make_uint4(0u, 0u, 0u, 0u);
-                        lv[b][1] = lv[b][0];
-                    } else if (vec && k0 + 32 <= a.k) {
-                        lv[b][0] = __ldg(reinterpret_cast<const uint4*>(xr + k0));
-                        lv[b][1] = __ldg(reinterpret_cast<const uint4*>(xr + k0 + 16));
-                    } else {
-                        uint32_t wds[8];
+                    for (int b = 0; b < kXGroups; ++b) {
+                        const int k0 = 32 * (g0 + b);
 #pragma unroll
                         for (int w = 0; w < 8; ++w) {
                             uint32_t word = 0;
+                            if (live && g0 + b < n_groups) {
 #pragma unroll
-                            for (int q8 = 0; q8 < 4; ++q8) {
-                                const int kk = k0 + 4 * w + q8;
-                                if (kk < a.k) word |= static_cast<uint32_t>(xr[kk]) << (8 * q8);
+                                for (int q8 = 0; q8 < 4; ++q8) {
+                                    const int kk = k0 + 4 * w + q8;
+                                    if (kk < a.k) word |= static_cast<uint32_t>(__ldg(xr + kk)) << (8 * q8);
+                                }
                             }
-                            wds[w] = word;
+                            lv[b][w] = word;
                         }
-                        lv[b][0] = make_uint4(wds[0], wds[1], wds[2], wds[3]);
-                        lv[b][1] = make_uint4(wds[4], wds[5], wds[6], wds[7]);
                     }
-                }
 #pragma unroll
-                for (int b = 0; b < kXGroups; ++b) {
-                    if (g0 + b < n_groups) {
-                        const uint32_t bytes[8] = { lv[b][0].x, lv[b][0].y, lv[b][0].z, lv[b][0].w,
-                                                    lv[b][1].x, lv[b][1].y, lv[b][1].z, lv[b][1].w };
-                        uint32_t cols[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) {
-                            const uint32_t pair = bytes[i >> 1] >> (16 * (i & 1));
-                            const uint32_t lo = pair & 0xFFu, hi = (pair >> 8) & 0xFFu;
-                            cols[i] = half2_bits(__floats2half2_rn(static_cast<float>(lo), static_cast<float>(hi)));
-                        }
-                        ptx::tmem_st16(tmem_base + lane_addr + a.a_col + static_cast<uint32_t>(16 * (g0 + b)), cols);
-                    }
+                    for (int b = 0; b < kXGroups; ++b)
+                        if (g0 + b < n_groups) put_group(g0 + b, lv[b]);
                 }
             }
             ptx::mbar_arrive(s.x_loaded);
