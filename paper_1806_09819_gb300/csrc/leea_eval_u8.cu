@@ -30,6 +30,8 @@
 // Every mbarrier wait is bounded in time; on expiry the kernel sets
 // kStatusEvalTimeout, drains its MMAs and exits.
 #include <cuda.h>
+
+#include <algorithm>
 #include <cuda_fp16.h>
 
 #include "leea_internal.h"
@@ -62,6 +64,10 @@ struct EvalU8Args {
     int64_t c_pad;
     float inv_div, alpha;
     uint32_t a_col;  // first TMEM column of the A operand (the accumulator uses 0 .. h-1)
+    // Batch staging: chunks of x_kc levels per row at stride x_stride, from
+    // byte x_off of the rings (the tail of the region: the piece ring and the
+    // last raw stages); raw stages below x_off may load before the batch is in.
+    int32_t x_staged, x_kc, x_stride, x_off, n_early;
     const float* popv;
     const uint8_t* x;
     const int32_t* y;
@@ -73,8 +79,8 @@ struct EvalU8Args {
 };
 
 struct U8Smem {
-    uint8_t* ring;        // piece_stages x kPieces x h x 128 B (1024-aligned)
-    uint8_t* raw;         // raw_stages x h x 256 B (FP32 rows of 64 K-elements)
+    uint8_t* raw;         // raw_stages x h x 256 B (FP32 rows of 64 K-elements), 1024-aligned
+    uint8_t* ring;        // piece_stages x kPieces x h x 128 B, right after (1024-aligned: h % 4 == 0)
     uint32_t piece_bytes, raw_bytes;
     uint8_t* prm_raw;     // 2 x prm_bytes: b1, W2 (row-major), b2 as stored, bulk-copied
     float* w2t;           // [h][dpad]
@@ -96,11 +102,11 @@ struct U8Smem {
 __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
 {
     U8Smem s;
-    s.ring = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
+    s.raw = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
     s.piece_bytes = static_cast<uint32_t>(a.h) * 128u;
     s.raw_bytes = static_cast<uint32_t>(a.h) * 256u;
-    s.raw = s.ring + a.piece_stages * kPieces * s.piece_bytes;
-    uint8_t* p = s.raw + a.raw_stages * s.raw_bytes;
+    s.ring = s.raw + a.raw_stages * s.raw_bytes;
+    uint8_t* p = s.ring + a.piece_stages * kPieces * s.piece_bytes;
     s.prm_raw = p;
     p += 2u * a.prm_bytes;
     s.w2t = reinterpret_cast<float*>(p);
@@ -286,10 +292,12 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
             uint32_t stage = 0, phase = 0;
             uint32_t issued_mask = 0, parity_mask = 0;
             uint32_t prm_issued = 0;  // units whose parameters were requested
-            // The batch loads go first: queued behind the first weight tiles
-            // of every SM they take several times as long.
-            bool ok = ptx::mbar_wait_bounded(s.x_loaded, 0u, s.abort_flag, kWaitLimitNs);
-            if (!ok) raise_abort(s, a);
+            // Raw stages that overlap the batch staging area wait until the
+            // batch is in TMEM (without staging, all do: the batch's own loads
+            // queued behind every SM's first weight tiles took several times
+            // as long).
+            uint32_t raw_issued = 0;
+            bool ok = true;
             for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
                 {
                     // b1, W2, b2 of individual p into parameter buffer (unit & 1).
@@ -306,6 +314,13 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                     ++prm_issued;
                 }
                 for (int kc = 0; kc < a.k_stages; ++kc) {
+                    if (raw_issued == static_cast<uint32_t>(a.n_early) &&
+                        !ptx::mbar_wait_bounded(s.x_loaded, 0u, s.abort_flag, kWaitLimitNs)) {
+                        raise_abort(s, a);
+                        ok = false;
+                        break;
+                    }
+                    ++raw_issued;
                     if (!ptx::mbar_wait_bounded(&s.raw_empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
                         raise_abort(s, a);
                         ok = false;
@@ -334,7 +349,9 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
         const int row0 = lt >> 4, c4 = lt & 15;
         const int groups = a.h >> 4;
         uint32_t rstage = 0, rphase = 0, stage = 0, phase = 0, unit = 0;
-        bool ok = true;
+        // the piece ring doubles as the batch staging area until the batch is in
+        bool ok = ptx::mbar_wait_bounded(s.x_loaded, 0u, s.abort_flag, kWaitLimitNs);
+        if (!ok) raise_abort(s, a);
         for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x, ++unit) {
             for (int kc = 0; kc < a.k_stages; ++kc) {
                 if (!ptx::mbar_wait_bounded(&s.raw_full[rstage], rphase, s.abort_flag, kWaitLimitNs)) {
@@ -395,41 +412,40 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
             // Row `row` of the batch into TMEM as FP16 pairs (lower k in the low
             // half); group g = levels 32 g .. 32 g + 31 = columns 16 g .. 16 g + 15.
             // The last group may reach 8 columns past k16 / 2; levels >= k are 0.
+            // A level k < 1024 is exact in FP16 as (1024 + k) - 1024, and 1024 + k
+            // has the bit pattern 0x6400 | k: one byte permute builds two of
+            // them, one packed subtraction makes the pair exact.
             auto put_group = [&](int g, const uint32_t (&bytes)[8]) {
+                const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
                 uint32_t cols[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    const uint32_t pair = bytes[i >> 1] >> (16 * (i & 1));
-                    const uint32_t lo = pair & 0xFFu, hi = (pair >> 8) & 0xFFu;
-                    cols[i] = half2_bits(__floats2half2_rn(static_cast<float>(lo), static_cast<float>(hi)));
+                    const uint32_t biased = __byte_perm(bytes[i >> 1], 0x64646464u, (i & 1) ? 0x4342u : 0x4140u);
+                    cols[i] = half2_bits(__hsub2(*reinterpret_cast<const __half2*>(&biased), k1024));
                 }
                 ptx::tmem_st16(tmem_base + lane_addr + a.a_col + static_cast<uint32_t>(16 * g), cols);
             };
             const uint8_t* xr = a.x + static_cast<int64_t>(row) * a.k;
             const bool live = row < a.batch;
             const int n_groups = (a.k16 + 31) / 32;
-            const uint32_t region = static_cast<uint32_t>(a.piece_stages) * kPieces * s.piece_bytes +
-                                    static_cast<uint32_t>(a.raw_stages) * s.raw_bytes;
-            // Staged: chunks of every row land by bulk copies in the rings,
-            // which stay idle until the batch is in TMEM (one memory latency
-            // per chunk; one chunk at d_0 = 784 and h = 112).  Row stride
-            // kc + 16 bytes keeps the per-row reads free of bank conflicts.
-            const int kc = min(32 * n_groups, static_cast<int>((region / static_cast<uint32_t>(a.batch) - 16u) / 32u * 32u));
-            const bool staged = (a.k % 16 == 0) && ((reinterpret_cast<uintptr_t>(a.x) & 15u) == 0) && kc >= 32;
-            if (staged) {
-                const int stride = kc + 16;
+            // Staged: chunks of every row land by bulk copies in the tail of
+            // the rings, which stays idle until the batch is in TMEM (one
+            // memory latency per chunk; one chunk at d_0 = 784 and h = 112).
+            if (a.x_staged) {
+                const int kc = a.x_kc, stride = a.x_stride;
+                uint8_t* xs = s.raw + a.x_off;
                 uint32_t xphase = 0;
                 for (int k0 = 0; k0 < a.k16; k0 += kc, xphase ^= 1u) {
                     const int bytes = min(kc, a.k - k0);  // multiple of 16
                     if (et == 0) ptx::mbar_arrive_expect_tx(s.x_full, static_cast<uint32_t>(a.batch * bytes));
-                    if (live) ptx::bulk_load(s.ring + row * stride, xr + k0, static_cast<uint32_t>(bytes), s.x_full);
+                    if (live) ptx::bulk_load(xs + row * stride, xr + k0, static_cast<uint32_t>(bytes), s.x_full);
                     const bool got = ptx::mbar_wait_bounded(s.x_full, xphase, s.abort_flag, kWaitLimitNs);
                     if (!got) {  // let this chunk's copies land before anything reuses the rings
                         raise_abort(s, a);
                         volatile int never = 0;
                         ptx::mbar_wait_bounded(s.x_full, xphase, &never, kDrainLimitNs);
                     }
-                    const uint8_t* src = s.ring + (live ? row : 0) * stride;
+                    const uint8_t* src = xs + (live ? row : 0) * stride;
                     for (int g = 0; g < kc / 32 && k0 + 32 * g < a.k16; ++g) {
                         uint32_t wds[8] = { 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u };
                         if (live && got) {
@@ -693,6 +709,19 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     a.prm_bytes = u8_prm_bytes(a.h, a.d_out);
     if (!u8_stages(a.h, a.dpad, a.batch, &a.piece_stages, &a.raw_stages)) return cudaErrorInvalidValue;
     const size_t smem = u8_smem_bytes(a.h, a.dpad, a.batch, a.piece_stages, a.raw_stages);
+    {
+        // Batch staging in the tail of the rings: row stride kc + 16 bytes
+        // (kc a multiple of 32) keeps the per-row 16-byte reads conflict-free.
+        const int32_t raw_bytes = a.h * 256;
+        const int32_t region = a.piece_stages * kPieces * a.h * 128 + a.raw_stages * raw_bytes;
+        const int32_t n_groups = (a.k16 + 31) / 32;
+        const int32_t kc = std::min(32 * n_groups, (region / a.batch - 16) / 32 * 32);
+        a.x_staged = (a.k % 16 == 0) && ((reinterpret_cast<uintptr_t>(x) & 15u) == 0) && kc >= 32;
+        a.x_kc = kc;
+        a.x_stride = kc + 16;
+        a.x_off = region - a.batch * a.x_stride;
+        a.n_early = a.x_staged ? std::min(a.raw_stages, a.x_off / raw_bytes) : 0;
+    }
     U8EncodeTiledFn enc = u8_encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tw;
