@@ -86,7 +86,7 @@ STAGES = ("select", "breed", "evaluate")
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 TRAFFIC = {
     "breed": {"bytes_per_launch": 711.07e6, "src_sha": "2c5af01472ae1ede", "capture": "P=1000 plain workload"},
-    "evaluate": {"bytes_per_launch": 359.41e6, "src_sha": "70524052f2d2df6f", "capture": "P=1000 plain workload"},
+    "evaluate": {"bytes_per_launch": 359.42e6, "src_sha": "149fda2e1617c56a", "capture": "P=1000 plain workload"},
 }
 
 
@@ -670,7 +670,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
                 "peak_source": f"{peak_src} ({'HBM copy' if kd['unit'] == 'GB/s' else 'FP32 FFMA: 152 SM x 128 lanes x 2 x max SM clock'})"}
     if tensor_eval:  # tensor-core work issued (passes, M padded to 128-sample tiles, K to the MMA step)
         k_pad = {0: 784 if u8 else 800, 1: 784, 2: 800}[precision]
-        passes = {0: 3, 1: 1, 2: 2}[precision]
+        passes = {0: 2 if u8 else 3, 1: 1, 2: 2}[precision]  # u8: two FP16 weight pieces; float: 3xTF32
         tiles = (batch + 127) // 128
         kernels["evaluate"]["tensor_tflops_issued"] = (passes * 2.0 * pop * tiles * 128 * k_pad * h / 1e12) / (
             prof["evaluate"][0] / max(1, prof["evaluate"][1]) / 1000.0)
@@ -681,7 +681,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
         workload = f"PROFILING OVERRIDE P={pop}, batch {batch} (not the benchmark workload): " + workload
     eval_kernel = ("tcgen05 " + {1: "kind::f16 on BF16 shadows", 2: "kind::f8f6f4 on FP8 shadows, 2 input pieces"}[
         precision] + ", batch in TMEM" if precision else
-                   (("tcgen05 BF16 exact pieces, batch in TMEM" if u8 else "tcgen05 3xTF32") if tensor_eval
+                   (("tcgen05 FP16 two-piece weights, batch in TMEM" if u8 else "tcgen05 3xTF32") if tensor_eval
                     else "CUDA-core FP32 FFMA"))
     pop_mb = pop * leea.leea_padded_params(DIMS) * 4 / 1e6
     line = {"metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps,
