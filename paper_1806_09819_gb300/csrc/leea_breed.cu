@@ -16,9 +16,10 @@
 // A consumer thread owns 8 consecutive genes of the chunk: one Philox block
 // of 16-bit mask draws (crossover or mutation mask) and two Philox blocks of
 // normals.  In mutation children only the Box-Muller pairs that hold a masked
-// gene are generated, and a warp first gathers them into a dense job list
-// (prefix scan over the lanes) so that normals are computed by consecutive
-// lanes instead of by whichever lane happens to own a masked gene.  Every mbarrier
+// gene are generated, and a warp first gathers them into a dense job list in
+// shared memory (one ballot per pair slot) so that normals are computed by
+// consecutive lanes instead of by whichever lane happens to own a masked
+// gene; the normals go back through the same list.  Every mbarrier
 // wait is bounded in time; on expiry the kernel sets kStatusBreedTimeout.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
@@ -51,9 +52,13 @@ struct StageMeta {
     int32_t pad[2];
 };
 
+constexpr int kJobSlots = 4 * 32;  // Box-Muller pairs of a warp's 32 units
+
 struct BreedSmem {
     uint8_t* base;   // stage i: parent 1 at base + 2i chunks, parent 2 at base + (2i+1) chunks
     StageMeta* meta;
+    float2* job_z;      // [kConsumerWarps][kJobSlots]: normals of a warp's job list
+    uint8_t* job_code;  // [kConsumerWarps][kJobSlots]: owner lane << 2 | pair slot
     uint64_t* full;
     uint64_t* empty;
     volatile int* abort_flag;
@@ -67,14 +72,18 @@ __device__ __forceinline__ BreedSmem carve(uint8_t* raw)
     uint8_t* p = base + 2 * kStages * kChunkBytes;
     s.meta = reinterpret_cast<StageMeta*>(p);
     p += sizeof(StageMeta) * kStages;
+    s.job_z = reinterpret_cast<float2*>(p);
+    p += sizeof(float2) * kConsumerWarps * kJobSlots;
+    s.job_code = p;
+    p += kConsumerWarps * kJobSlots;
     s.full = reinterpret_cast<uint64_t*>(p);
     s.empty = s.full + kStages;
     s.abort_flag = reinterpret_cast<volatile int*>(s.empty + kStages);
     return s;
 }
 
-constexpr size_t kBreedSmemBytes =
-    128 + 2 * kStages * kChunkBytes + sizeof(StageMeta) * kStages + 16 * kStages + 16;
+constexpr size_t kBreedSmemBytes = 128 + 2 * kStages * kChunkBytes + sizeof(StageMeta) * kStages +
+                                   (sizeof(float2) + 1) * kConsumerWarps * kJobSlots + 16 * kStages + 16;
 
 // The shadow of 8 child genes i0 .. i0+7 of W1: 8 BF16 (16 bytes) or 8 FP8-e4m3
 // of w / 2^sexp with saturation (8 bytes).  Returns max |w| of the 8 genes.
@@ -167,68 +176,41 @@ __device__ __forceinline__ float4 select4(uint32_t m, float4 a, float4 b)
 
 // Mutation of this lane's 8 genes (unit u = genes 8u .. 8u+7, live if `live`).
 // Slot s = 0..3 names the Box-Muller pair of genes 8u + 2s, 8u + 2s + 1, i.e.
-// pair s & 1 of NORMAL block 2u + (s >> 1).  A warp numbers the slots that
-// hold a masked gene (prefix scan over the lanes) and generates those normals
-// on consecutive lanes, then every lane collects its own.
+// pair s & 1 of NORMAL block 2u + (s >> 1).  The warp lists the slots that
+// hold a masked gene, slot by slot (one ballot each), in its shared-memory job
+// list; consecutive lanes compute the listed normals and every lane reads its
+// own back.  Each normal depends only on its (unit, slot) counter.
 __device__ __forceinline__ void mutate_unit(const BreedArgs& a, uint32_t gen, const PhiloxKeys& key, uint32_t j,
-                                            uint32_t u, bool live, float4 (&v)[2], int lane)
+                                            uint32_t u, bool live, float4 (&v)[2], int lane, float2* job_z,
+                                            uint8_t* job_code)
 {
     constexpr int kSlots = 4;
     uint32_t hit = 0;
     if (live) hit = mask8(philox_keyed(make_uint4(u, j, gen, kTagMutMask), key), a.thr_mut);
-    uint32_t need = 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t idx[kSlots], total = 0;
 #pragma unroll
-    for (int sl = 0; sl < kSlots; ++sl) need |= ((hit >> (2 * sl)) & 3u) ? (1u << sl) : 0u;
-    const uint32_t cnt = __popc(need);
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t o = __shfl_up_sync(0xFFFFFFFFu, incl, off);
-        if (lane >= off) incl += o;
+    for (int sl = 0; sl < kSlots; ++sl) {
+        const bool need = ((hit >> (2 * sl)) & 3u) != 0u;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, need);
+        idx[sl] = total + __popc(b & lt);
+        if (need) job_code[idx[sl]] = static_cast<uint8_t>((lane << 2) | sl);
+        total += __popc(b);
     }
-    const uint32_t excl = incl - cnt;
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-
+    __syncwarp();
+    for (uint32_t job = static_cast<uint32_t>(lane); job < total; job += 32) {
+        const uint32_t code = job_code[job];
+        const uint32_t o = code >> 2, slot = code & 3u;
+        // Lanes of a warp own consecutive units: the owner's is u - lane + o.
+        const uint32_t uo = u - static_cast<uint32_t>(lane) + o;
+        const uint4 n = philox_keyed(make_uint4(2u * uo + (slot >> 1), j, gen, kTagNormal), key);
+        job_z[job] = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
+    }
+    __syncwarp();
     float2 z[kSlots];
 #pragma unroll
-    for (int sl = 0; sl < kSlots; ++sl) z[sl] = make_float2(0.f, 0.f);
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t job = base + static_cast<uint32_t>(lane);
-        int o = 0;  // owner lane: the last lane whose exclusive prefix is <= job
-#pragma unroll
-        for (int step = 16; step > 0; step >>= 1) {
-            const int cand = o + step;
-            const uint32_t e = __shfl_sync(0xFFFFFFFFu, excl, cand & 31);
-            if (cand < 32 && e <= job) o = cand;
-        }
-        const uint32_t mo = __shfl_sync(0xFFFFFFFFu, need, o);
-        const uint32_t eo = __shfl_sync(0xFFFFFFFFu, excl, o);
-        float2 zz = make_float2(0.f, 0.f);
-        if (job < total) {
-            uint32_t nth = job - eo, slot = 0, mm = mo;
-#pragma unroll
-            for (int sl = 0; sl < kSlots; ++sl) {
-                if (mm & 1u) {
-                    if (nth == 0) { slot = sl; break; }
-                    --nth;
-                }
-                mm >>= 1;
-            }
-            // Lanes of a warp own consecutive units: the owner's is u - lane + o.
-            const uint32_t uo = u - static_cast<uint32_t>(lane) + static_cast<uint32_t>(o);
-            const uint4 n = philox_keyed(make_uint4(2u * uo + (slot >> 1), j, gen, kTagNormal), key);
-            zz = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
-        }
-#pragma unroll
-        for (int sl = 0; sl < kSlots; ++sl) {
-            const uint32_t id = excl + __popc(need & ((1u << sl) - 1u));
-            const bool mine = ((need >> sl) & 1u) && id >= base && id < base + 32;
-            const int src = mine ? static_cast<int>(id - base) : lane;
-            const float zx = __shfl_sync(0xFFFFFFFFu, zz.x, src);
-            const float zy = __shfl_sync(0xFFFFFFFFu, zz.y, src);
-            if (mine) z[sl] = make_float2(zx, zy);
-        }
-    }
+    for (int sl = 0; sl < kSlots; ++sl)
+        z[sl] = ((hit >> (2 * sl)) & 3u) ? job_z[idx[sl]] : make_float2(0.f, 0.f);
     if (hit & 0x01u) v[0].x = fmaf(a.sigma, z[0].x, v[0].x);
     if (hit & 0x02u) v[0].y = fmaf(a.sigma, z[0].y, v[0].y);
     if (hit & 0x04u) v[0].z = fmaf(a.sigma, z[1].x, v[0].z);
@@ -237,6 +219,7 @@ __device__ __forceinline__ void mutate_unit(const BreedArgs& a, uint32_t gen, co
     if (hit & 0x20u) v[1].y = fmaf(a.sigma, z[2].y, v[1].y);
     if (hit & 0x40u) v[1].z = fmaf(a.sigma, z[3].x, v[1].z);
     if (hit & 0x80u) v[1].w = fmaf(a.sigma, z[3].y, v[1].w);
+    __syncwarp();  // the list is reused by the next unit
 }
 
 // The run owning global work item `it`: the last one whose first item is <= it.
@@ -359,7 +342,8 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
                 v[1] = A[2 * ct + 1];
             }
             if (m.kind == 2) {
-                mutate_unit(a, gen, key, j, u, live, v, lane);
+                const int cw = warp - 1;  // consumer warp
+                mutate_unit(a, gen, key, j, u, live, v, lane, s.job_z + cw * kJobSlots, s.job_code + cw * kJobSlots);
             } else if (live && m.kind == 1) {
                 const float4 b0 = B[2 * ct], b1 = B[2 * ct + 1];
                 if (a.xo_op == 0) {
