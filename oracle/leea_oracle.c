@@ -951,6 +951,10 @@ int leea_cpu_descriptors(int32_t pop, const int32_t* dims, int32_t n_dims, const
         if (rc == LEEA_CPU_OK)
             rc = breed_child(c, prm, seed, gen, entity[j], kind[j], parents + (int64_t)par1[j] * c,
                              parents + (int64_t)par2[j] * c, child);
+        /* precision >= 1: the child's W1 as the precision form holds it, the
+         * FP32 gene rounded to BF16 (nearest even) */
+        if (rc == LEEA_CPU_OK && prm->precision >= 1)
+            for (int64_t i = 0; i < (int64_t)dims[0] * dims[1]; i++) child[i] = leea_cpu_round_bf16((double)(float)child[i]);
         double f;
         if (rc == LEEA_CPU_OK) rc = leea_cpu_evaluate(1, dims, n_dims, child, probe_x, y, n_probe, &f, NULL, logits);
         for (int64_t k = 0; rc == LEEA_CPU_OK && k < (int64_t)n_probe * d_out; k++) row[5 + k] = logits[k];

@@ -152,7 +152,9 @@ int leea_cpu_breed_entities(int32_t pop, const int32_t* dims, int32_t n_dims, co
 int leea_cpu_recipe_stats(const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm, uint64_t seed,
                           uint32_t gen, const int32_t* kind, const uint32_t* entity, int32_t n, double* xo_frac,
                           double* mut_norm);
-/* Descriptors [f1, f2, f_inh, xo_frac, mut_norm, probe logits (n_probe x d_out)]. */
+/* Descriptors [f1, f2, f_inh, xo_frac, mut_norm, probe logits (n_probe x d_out)].
+ * prm->precision >= 1: the logits use the child's W1 rounded to FP32, then to
+ * BF16 (nearest even), as the precision form holds it. */
 int leea_cpu_descriptors(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_cpu_params* prm,
                          uint64_t seed, uint32_t gen, const double* parents, const double* f_adj,
                          const int32_t* par1, const int32_t* par2, const int32_t* kind, const double* f_inh,

@@ -181,3 +181,25 @@ def test_descriptors_hold_parent_fitness_stats_and_probe_logits(oracle_mod):
     kids = oracle_mod.breed_entities(prm, DIMS, 3, 9, popv, p1, p2, kind, ent)
     _, _, logits = oracle_mod.evaluate(kids, DIMS, probe, np.zeros(5, dtype=np.int32), want_logits=True)
     np.testing.assert_array_equal(desc[:, 5:], logits.reshape(kind.size, -1))
+
+
+def test_bf16_descriptors_use_the_bf16_child(oracle_mod):
+    # precision 1: the logits are those of the child whose W1 is its FP32 value
+    # rounded to BF16 (quantize_w1 is pinned to torch's bfloat16 rounding);
+    # the other columns do not change.
+    popv, f = _population(oracle_mod, pop=16, seed=6)
+    prm = oracle_mod.Params(**PRM)
+    prm_b = oracle_mod.Params(**PRM, precision=1)
+    order = oracle_mod.rank(f)
+    p1, p2, kind, f_inh, ent = oracle_mod.select_recipes(prm, f, order, 3, 9, 2)
+    probe = np.random.default_rng(8).uniform(0, 1, size=(4, DIMS[0]))
+    d32 = oracle_mod.descriptors(prm, DIMS, 3, 9, popv, f, p1, p2, kind, f_inh, ent, probe)
+    d16 = oracle_mod.descriptors(prm_b, DIMS, 3, 9, popv, f, p1, p2, kind, f_inh, ent, probe)
+    np.testing.assert_array_equal(d16[:, :5], d32[:, :5])
+    kids = oracle_mod.breed_entities(prm, DIMS, 3, 9, popv, p1, p2, kind, ent)
+    n_w1 = DIMS[0] * DIMS[1]
+    q = kids.copy()
+    q[:, :n_w1] = oracle_mod.quantize_w1(kids.astype(np.float32).astype(np.float64), DIMS, 1, None)[:, :n_w1]
+    _, _, logits = oracle_mod.evaluate(q, DIMS, probe, np.zeros(4, dtype=np.int32), want_logits=True)
+    np.testing.assert_array_equal(d16[:, 5:], logits.reshape(kind.size, -1))
+    assert np.abs(d16[:, 5:] - d32[:, 5:]).max() > 0  # the rounding is visible
