@@ -94,8 +94,9 @@ __device__ __forceinline__ float write_shadow8(const BreedArgs& a, int32_t j, in
                            fmaxf(fmaxf(fabsf(v[1].x), fabsf(v[1].y)), fmaxf(fabsf(v[1].z), fabsf(v[1].w))));
     // Eight genes of one row: d_0 % 16 == 0 keeps them in one 16-byte (BF16)
     // or 8-byte (FP8) piece of a chunk.
-    const int32_t o = static_cast<int32_t>(i0 / a.sh_k);
-    const int32_t k = static_cast<int32_t>(i0 - static_cast<int64_t>(o) * a.sh_k);
+    const int32_t i32 = static_cast<int32_t>(i0);  // a W1 gene: i0 < h d_0 < 2^31
+    const int32_t o = i32 / a.sh_k;
+    const int32_t k = i32 - o * a.sh_k;
     uint8_t* dst = a.shadow + static_cast<int64_t>(j) * a.sh_stride +
                    shadow_offset(a.sh_h, a.precision == 1 ? 2 : 1, o, k);
     if (a.precision == 1) {
@@ -316,7 +317,12 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
         const int ct = threadIdx.x - 32;
         const uint32_t gen = MULTI ? *gen_dev : run0.a.gen;
         PhiloxKeys key = philox_keys(run0.a.seed);
-        int32_t key_run = MULTI ? -1 : 0;  // the run `key` belongs to
+        // The current run's arguments and generator keys, held in registers
+        // while consecutive items belong to the same run (many runs: the
+        // table lives in global memory).
+        BreedArgs a = run0.a;
+        float* children = run0.children;
+        int32_t cur_run = MULTI ? -1 : 0;
         uint32_t stage = 0, phase = 0;
         for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
             if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kWaitLimitNs)) {
@@ -324,15 +330,15 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
                 break;
             }
             const StageMeta m = s.meta[stage];
-            const BreedRun& R = MULTI ? runs[m.run] : run0;
-            const BreedArgs& a = R.a;
-            if (MULTI && m.run != key_run) {
+            if (MULTI && m.run != cur_run) {
+                a = runs[m.run].a;
+                children = runs[m.run].children;
                 key = philox_keys(a.seed);
-                key_run = m.run;
+                cur_run = m.run;
             }
             const float4* A = reinterpret_cast<const float4*>(stage_a(s, stage));
             const float4* B = reinterpret_cast<const float4*>(stage_b(s, stage));
-            float4* O = reinterpret_cast<float4*>(R.children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
+            float4* O = reinterpret_cast<float4*>(children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
             const uint32_t j = a.entity ? a.entity[m.j] : static_cast<uint32_t>(m.j);  // Philox entity
             const bool live = ct * kGenesPerLane < m.len;
             const uint32_t u = (static_cast<uint32_t>(m.g0) >> 3) + static_cast<uint32_t>(ct);  // 8-gene unit

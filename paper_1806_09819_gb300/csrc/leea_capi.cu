@@ -176,6 +176,8 @@ leea_status check_device_status(cudaStream_t stream, uint32_t* flags_out)
         return fail(LEEA_ETIMEOUT, "a tensor-core evaluation wait timed out; its fitness values are invalid");
     if (v & kStatusBreedTimeout)
         return fail(LEEA_ETIMEOUT, "a breed kernel wait timed out; the children are invalid");
+    if (v & kStatusProbeTimeout)
+        return fail(LEEA_ETIMEOUT, "a tensor-core probe wait timed out; the descriptors are invalid");
     return LEEA_OK;
 }
 

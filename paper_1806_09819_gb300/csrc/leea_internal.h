@@ -12,6 +12,7 @@ constexpr int kMaxLayers = 15;
 // Bits of the device status word (set by kernels, read and cleared by the host).
 constexpr unsigned int kStatusEvalTimeout = 1u;   // a bounded mbarrier wait of the tensor-core eval gave up
 constexpr unsigned int kStatusBreedTimeout = 2u;  // a bounded mbarrier wait of the breed kernel gave up
+constexpr unsigned int kStatusProbeTimeout = 4u;  // a bounded mbarrier wait of the tensor-core probe gave up
 
 // Per-layer offsets of a net, computed on the host (logical gene order of
 // Section 3.2: W_l rows out x in, then b_l).
@@ -207,6 +208,7 @@ cudaError_t launch_select_recipes(const SelectArgs& a, int32_t mult, const float
                                   cudaStream_t stream);
 struct ProbeArgs {
     int32_t k, h, d_out, n_probe, width, xo_op;
+    int32_t precision;       // 0: FP32 child (CUDA cores); >= 1: the child's W1 in BF16 (tensor cores)
     int64_t c, c_pad;
     uint32_t thr_xo, thr_mut, gen;
     float sigma;
@@ -218,9 +220,13 @@ struct ProbeArgs {
     const uint32_t* entity;  // NULL: entity = recipe index
     const float* probe;      // float[n_probe][k]
     float* desc;             // float[n][width], width = 5 + n_probe d_out
+    unsigned int* status;    // device status word (bounded waits of the tensor-core probe)
 };
-bool probe_supported(int32_t k, int32_t h, int32_t d_out, int32_t n_probe);
+bool probe_supported(int32_t k, int32_t h, int32_t d_out, int32_t n_probe, int32_t precision);
+// precision 0: probe_kernel (leea_probe.cu); >= 1: probe_tc_kernel (leea_probe_tc.cu).
 cudaError_t launch_descriptors(const ProbeArgs& a, int32_t n_recipes, cudaStream_t stream);
+bool probe_tc_supported(int32_t k, int32_t h, int32_t d_out, int32_t n_probe);
+cudaError_t launch_descriptors_tc(const ProbeArgs& a, int32_t n_recipes, cudaStream_t stream);
 
 // Surrogate form: the MLP d_in -> h1 -> h2 -> 1 (leea_surrogate.cu).
 int64_t surrogate_num_params(int32_t d_in, int32_t h1, int32_t h2);

@@ -230,8 +230,9 @@ probe_kernel(const __grid_constant__ ProbeArgs a)
 
 }  // namespace
 
-bool probe_supported(int32_t k, int32_t h, int32_t d_out, int32_t n_probe)
+bool probe_supported(int32_t k, int32_t h, int32_t d_out, int32_t n_probe, int32_t precision)
 {
+    if (precision >= 1) return probe_tc_supported(k, h, d_out, n_probe);
     return k % 16 == 0 && h % 16 == 0 && h >= 16 && h <= kMaxHidden && d_out >= 1 && d_out <= 16 && n_probe >= 1 &&
            n_probe <= kMaxProbe;
 }
@@ -239,6 +240,7 @@ bool probe_supported(int32_t k, int32_t h, int32_t d_out, int32_t n_probe)
 cudaError_t launch_descriptors(const ProbeArgs& a, int32_t n_recipes, cudaStream_t stream)
 {
     if (n_recipes <= 0) return cudaSuccess;
+    if (a.precision >= 1) return launch_descriptors_tc(a, n_recipes, stream);
     const size_t smem = sizeof(float) * (static_cast<size_t>(kKT) * a.h + kKT * kMaxProbe + kMaxProbe * a.h +
                                          static_cast<size_t>(a.d_out) * a.h + 16 + kProbeThreads);
     cudaError_t err = cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -423,6 +423,9 @@ leea_status surr_breed_generation(leea_surr* s, const uint8_t* x, float x_div, c
     pa.entity = s->r_entity;
     pa.probe = s->probe;
     pa.desc = s->desc;
+    pa.precision = s->prm.precision;
+    pa.status = device_status_ptr();
+    if (!pa.status) return fail(LEEA_ECUDA, "device status word unavailable");
     LEEA_CUDA_TRY(launch_descriptors(pa, s->n_rec, st), "probe kernel");
     mark(s, 0, 1);
     // 2. scores and the choice
@@ -578,11 +581,11 @@ leea_status leea_surr_create(int32_t pop, const int32_t* dims, int32_t n_dims, c
     leea_surr* s = new (std::nothrow) leea_surr();
     if (!s) return fail(LEEA_ENOMEM, "host allocation failed");
     if (!make_layout(dims, n_dims, p->init, &s->net) || s->net.n_layers != 2 ||
-        !probe_supported(s->net.dims[0], s->net.dims[1], s->net.dims[2], sp->n_probe) ||
+        !probe_supported(s->net.dims[0], s->net.dims[1], s->net.dims[2], sp->n_probe, p->precision) ||
         (p->precision == 1 && check_shadow_shape(s->net, 1))) {
         delete s;
         return fail(LEEA_EINVAL, "the surrogate form needs d_0-h-d_out nets with d_0 %% 16 == 0, h %% 16 == 0, "
-                                 "16 <= h <= 256, d_out <= 16");
+                                 "16 <= h <= 256 (<= 128 in BF16), d_out <= 16");
     }
     s->pop = pop;
     s->prm = *p;

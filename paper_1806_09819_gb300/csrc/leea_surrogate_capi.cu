@@ -152,9 +152,9 @@ leea_status leea_descriptors(int32_t n_parents, const int32_t* dims, int32_t n_d
     NetLayout net;
     if (!make_layout(dims, n_dims, p->init, &net) || net.n_layers != 2)
         return fail(LEEA_EINVAL, "descriptors take d_0-h-d_out nets (n_dims == 3)");
-    if (!probe_supported(net.dims[0], net.dims[1], net.dims[2], n_probe))
-        return fail(LEEA_EINVAL, "descriptors need d_0 %% 16 == 0, h %% 16 == 0, 16 <= h <= 256, d_out <= 16 and "
-                                 "1 <= n_probe <= 32");
+    if (!probe_supported(net.dims[0], net.dims[1], net.dims[2], n_probe, p->precision))
+        return fail(LEEA_EINVAL, "descriptors need d_0 %% 16 == 0, h %% 16 == 0, 16 <= h <= 256 (<= 128 with "
+                                 "precision >= 1), d_out <= 16 and 1 <= n_probe <= 32");
     if (n < 0) return fail(LEEA_EINVAL, "n must be >= 0");
     if (n == 0) return LEEA_OK;
     if (!parents_dev || !f_adj_dev || !par1_dev || !par2_dev || !kind_dev || !f_inh_dev || !probe_dev || !desc_dev)
@@ -183,6 +183,10 @@ leea_status leea_descriptors(int32_t n_parents, const int32_t* dims, int32_t n_d
     a.entity = entity_dev;
     a.probe = probe_dev;
     a.desc = desc_dev;
+    a.precision = p->precision;
+    a.status = device_status_ptr();
+    if (!a.status) return fail(LEEA_ECUDA, "device status word unavailable");
+    if (reinterpret_cast<uintptr_t>(probe_dev) & 3u) return fail(LEEA_EINVAL, "probe must be 4-byte aligned");
     LEEA_CUDA_TRY(launch_descriptors(a, n, static_cast<cudaStream_t>(stream)), "probe kernel");
     return LEEA_OK;
 }

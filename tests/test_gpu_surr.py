@@ -47,7 +47,7 @@ def test_surrogate_generation_matches_oracle(gpu, oracle_mod, precision, screen)
         st.generation_u8(torch.from_numpy(levels).cuda(), torch.from_numpy(y).cuda())
         assert st.gen == 6
         step = st.get_step()
-        oprm = oracle_mod.Params(**PRM)
+        oprm = oracle_mod.Params(**PRM, precision=precision)
         f64 = f_adj.astype(np.float64)
         order = oracle_mod.rank(f64)
         r1, r2, rk, rinh, rent = oracle_mod.select_recipes(oprm, f64, order, 9, 6, 3)

@@ -154,14 +154,19 @@ def test_breed_entities_matches_oracle(gpu, oracle_mod):
 
 
 @pytest.mark.parametrize("dims,n_probe", [([784, 112, 10], 32), ([64, 32, 10], 32), ([128, 256, 16], 7),
-                                          ([96, 16, 3], 1)])
+                                          ([96, 16, 3], 1), ([784, 128, 10], 20)])
 @pytest.mark.parametrize("xo_op", [0, 1])
-def test_descriptors_match_oracle(gpu, oracle_mod, dims, n_probe, xo_op):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_descriptors_match_oracle(gpu, oracle_mod, dims, n_probe, xo_op, precision):
+    # precision 0: the FP32 child on the CUDA cores; 1: the child's W1 in BF16
+    # on the tensor cores (h <= 128), against the oracle's BF16 rounding of it
     import torch
     from helpers import to_device_pop
+    if precision == 1 and dims[1] > 128:
+        pytest.skip("the tensor-core probe takes h <= 128")
     pop, mult = 20, 2
-    prm = gpu.Params(**PRM_S, xo_op=xo_op)
-    oprm = oracle_mod.Params(**PRM_S, xo_op=xo_op)
+    prm = gpu.Params(**PRM_S, xo_op=xo_op, precision=precision)
+    oprm = oracle_mod.Params(**PRM_S, xo_op=xo_op, precision=precision)
     f, order, (p1, p2, kind, f_inh, ent) = _recipes(gpu, oracle_mod, pop, mult)
     # add two elite-kind rows (plain copies) at the end
     kind_h = np.concatenate([kind.cpu().numpy(), [0, 0]]).astype(np.int32)
@@ -184,4 +189,23 @@ def test_descriptors_match_oracle(gpu, oracle_mod, dims, n_probe, xo_op):
     np.testing.assert_allclose(got[:, 3], ref[:, 3], rtol=1e-6, atol=0)
     np.testing.assert_allclose(got[:, 4], ref[:, 4], rtol=1e-5, atol=0)
     scale = np.abs(ref[:, 5:]).max()
-    np.testing.assert_allclose(got[:, 5:], ref[:, 5:], rtol=1e-4, atol=1e-5 * scale)
+    if precision == 0:
+        np.testing.assert_allclose(got[:, 5:], ref[:, 5:], rtol=1e-4, atol=1e-5 * scale)
+        return
+    # BF16: against the oracle's evaluation of the same FP32 children (made by
+    # leea_breed_entities, itself checked against the oracle) rounded to BF16
+    kids = torch.zeros((n, cp), dtype=torch.float32, device="cuda")
+    gpu.leea_breed_entities(pop, dims, gpu.Params(**PRM_S, xo_op=xo_op), 7, 3, to_device_pop(parents, cp),
+                            _t(p1_h).int(), _t(p2_h).int(), _t(kind_h).int(),
+                            torch.from_numpy(ent_h.view(np.int32)).cuda(), n, kids)
+    q = oracle_mod.quantize_w1(kids[:, :c].cpu().numpy().astype(np.float64), dims, 1, None)
+    _, _, same = oracle_mod.evaluate(q, dims, probe.astype(np.float64), np.zeros(n_probe, dtype=np.int32),
+                                     want_logits=True)
+    np.testing.assert_allclose(got[:, 5:], same.reshape(n, -1), rtol=1e-4, atol=1e-5 * scale)
+    # and against the oracle's own children: an FP32 child gene one ulp off the
+    # oracle's may round to the neighbouring BF16 value, which moves a logit by
+    # up to ulp_bf16(w) max|x| max|W2| per such gene
+    err = np.abs(got[:, 5:] - ref[:, 5:])
+    tight = err <= 1e-4 * np.abs(ref[:, 5:]) + 1e-5 * scale
+    flip = 2.0 ** -7 * np.abs(parents).max() * 1.5 * np.abs(probe).max() * np.abs(parents).max() * 1.5
+    assert tight.mean() >= 0.999 and (err <= 2 * flip + 1e-5 * scale).all(), (tight.mean(), err.max(), flip)
