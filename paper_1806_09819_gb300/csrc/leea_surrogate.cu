@@ -5,8 +5,10 @@
 // offspring be made and evaluated.
 //
 // Parameters, flat FP32: W1 [h1][d_in], b1 [h1], W2 [h2][h1], b2 [h2],
-// w3 [h2], b3.  Every reduction runs in a fixed order, so results do not
-// depend on scheduling.
+// w3 [h2], b3.  Every reduction runs in a fixed order (a dot product: lane l
+// of a warp sums k = l, l + 32, ... in order, then a fixed butterfly over the
+// lanes; a gradient: 8 row segments in order, then the segments in order),
+// so results do not depend on scheduling.
 #include "leea_internal.h"
 #include "philox.cuh"
 
@@ -18,7 +20,10 @@ namespace {
 
 constexpr uint32_t kTagSurrInit = 6;
 constexpr int kRows = 32;      // rows per forward CTA at most (fewer for small n: more CTAs)
-constexpr int kFwdThreads = 256;
+constexpr int kFwdWarps = 8;
+constexpr int kFwdThreads = 32 * kFwdWarps;
+constexpr int kSegs = 8;       // row segments of the gradient
+constexpr int kGradParams = 32;  // parameters per gradient CTA (one per lane, a warp per segment)
 
 struct MlpView {
     const float *W1, *b1, *W2, *b2, *w3, *b3;
@@ -62,48 +67,69 @@ __global__ void surr_init_kernel(int32_t d_in, int32_t h1, int32_t h2, uint64_t 
     }
 }
 
-// Forward for `rpc` rows per CTA; a1 / a2 (the ReLU outputs) are kept for
-// the backward pass when not NULL.  Dot products run over k in order.
+// Sum of v over the 32 lanes, the same fixed butterfly in every lane.
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+    return v;
+}
+
+// out[r][u] = act(b[u] + sum_k W[u][k] in[r][k]) for R rows: warp w takes
+// units u = w, w + 8, ...; lane l sums k = l, l + 32, ... (coalesced rows of
+// W), then the lanes combine.
+template <int R>
+__device__ __forceinline__ void dense_rows(const float* __restrict__ W, const float* __restrict__ b, int32_t n_in,
+                                           int32_t n_out, const float* in, float* out, bool relu, int warp, int lane)
+{
+    for (int u = warp; u < n_out; u += kFwdWarps) {
+        float acc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0.0f;
+        const float* w = W + static_cast<int64_t>(u) * n_in;
+        for (int k = lane; k < n_in; k += 32) {
+            const float wk = __ldg(w + k);
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = fmaf(wk, in[r * n_in + k], acc[r]);
+        }
+        const float bu = __ldg(b + u);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float z = warp_sum(acc[r]) + bu;
+            if (lane == 0) out[r * n_out + u] = relu ? fmaxf(z, 0.0f) : z;
+        }
+    }
+}
+
+// Forward for R rows per CTA; a1 / a2 (the ReLU outputs) are kept for the
+// backward pass when not NULL.
+template <int R>
 __global__ void __launch_bounds__(kFwdThreads)
-surr_forward_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, int32_t rpc, const float* __restrict__ theta,
+surr_forward_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* __restrict__ theta,
                     const float* __restrict__ x, float* __restrict__ y, float* __restrict__ a1_out,
                     float* __restrict__ a2_out)
 {
     extern __shared__ float sm[];
-    float* xs = sm;                       // [rpc][d_in]
-    float* s1 = xs + rpc * d_in;          // [rpc][h1]
-    float* s2 = s1 + rpc * h1;            // [rpc][h2]
+    float* xs = sm;                     // [R][d_in]
+    float* s1 = xs + R * d_in;          // [R][h1]
+    float* s2 = s1 + R * h1;            // [R][h2]
+    float* s3 = s2 + R * h2;            // [R]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const MlpView p = view(theta, d_in, h1, h2);
-    const int32_t r0 = blockIdx.x * rpc;
-    const int32_t rows = n - r0 < rpc ? n - r0 : rpc;
-    for (int i = threadIdx.x; i < rpc * d_in; i += kFwdThreads) {
+    const int32_t r0 = blockIdx.x * R;
+    const int32_t rows = n - r0 < R ? n - r0 : R;
+    for (int i = threadIdx.x; i < R * d_in; i += kFwdThreads) {
         const int r = i / d_in;
         xs[i] = r < rows ? x[static_cast<int64_t>(r0 + r) * d_in + (i - r * d_in)] : 0.0f;
     }
     __syncthreads();
-    for (int o = threadIdx.x; o < rpc * h1; o += kFwdThreads) {
-        const int r = o / h1, u = o - r * h1;
-        const float* w = p.W1 + static_cast<int64_t>(u) * d_in;
-        const float* xr = xs + r * d_in;
-        float z = p.b1[u];
-        for (int k = 0; k < d_in; ++k) z = fmaf(w[k], xr[k], z);
-        s1[o] = fmaxf(z, 0.0f);
-    }
+    dense_rows<R>(p.W1, p.b1, d_in, h1, xs, s1, true, warp, lane);
     __syncthreads();
-    for (int o = threadIdx.x; o < rpc * h2; o += kFwdThreads) {
-        const int r = o / h2, u = o - r * h2;
-        const float* w = p.W2 + static_cast<int64_t>(u) * h1;
-        const float* ar = s1 + r * h1;
-        float z = p.b2[u];
-        for (int k = 0; k < h1; ++k) z = fmaf(w[k], ar[k], z);
-        s2[o] = fmaxf(z, 0.0f);
-    }
+    dense_rows<R>(p.W2, p.b2, h1, h2, s1, s2, true, warp, lane);
     __syncthreads();
-    for (int r = threadIdx.x; r < rows; r += kFwdThreads) {
-        float z = p.b3[0];
-        for (int u = 0; u < h2; ++u) z = fmaf(p.w3[u], s2[r * h2 + u], z);
-        y[r0 + r] = z;
-    }
+    if (warp == 0) dense_rows<R>(p.w3, p.b3, h2, 1, s2, s3, false, 0, lane);
+    __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += kFwdThreads) y[r0 + r] = s3[r];
     if (a1_out)
         for (int o = threadIdx.x; o < rows * h1; o += kFwdThreads) a1_out[static_cast<int64_t>(r0) * h1 + o] = s1[o];
     if (a2_out)
@@ -134,37 +160,52 @@ __global__ void surr_backrow_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t
     }
 }
 
-// One thread per parameter: its gradient summed over the rows in order.
-__global__ void surr_grad_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* __restrict__ x,
-                                 const float* __restrict__ a1, const float* __restrict__ a2,
-                                 const float* __restrict__ dy, const float* __restrict__ d1,
-                                 const float* __restrict__ d2, float* __restrict__ grad)
+// Gradient: parameter i's sum over the rows, in kSegs segments of rows
+// (warp = segment, lane = parameter: coalesced rows of x / a1 / a2), each
+// summed in row order, then the segments in order.
+__global__ void __launch_bounds__(32 * kSegs)
+surr_grad_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* __restrict__ x,
+                 const float* __restrict__ a1, const float* __restrict__ a2, const float* __restrict__ dy,
+                 const float* __restrict__ d1, const float* __restrict__ d2, float* __restrict__ grad)
 {
+    __shared__ float part[kSegs][kGradParams];
+    const int seg = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t n1 = static_cast<int64_t>(h1) * d_in, n2 = static_cast<int64_t>(h2) * h1;
     const int64_t total = n1 + h1 + n2 + h2 + h2 + 1;
-    const int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-    if (i >= total) return;
+    const int64_t i = blockIdx.x * static_cast<int64_t>(kGradParams) + lane;
+    const int32_t per = (n + kSegs - 1) / kSegs;
+    const int32_t ra = seg * per, rb = ra + per < n ? ra + per : n;
     float s = 0.0f;
-    if (i < n1) {  // W1[u][k]: sum_r d1[r][u] x[r][k]
-        const int64_t u = i / d_in, k = i - u * d_in;
-        for (int32_t r = 0; r < n; ++r) s = fmaf(d1[static_cast<int64_t>(r) * h1 + u], x[static_cast<int64_t>(r) * d_in + k], s);
-    } else if (i < n1 + h1) {
-        const int64_t u = i - n1;
-        for (int32_t r = 0; r < n; ++r) s += d1[static_cast<int64_t>(r) * h1 + u];
-    } else if (i < n1 + h1 + n2) {  // W2[u][k]: sum_r d2[r][u] a1[r][k]
-        const int64_t j = i - n1 - h1, u = j / h1, k = j - u * h1;
-        for (int32_t r = 0; r < n; ++r)
-            s = fmaf(d2[static_cast<int64_t>(r) * h2 + u], a1[static_cast<int64_t>(r) * h1 + k], s);
-    } else if (i < n1 + h1 + n2 + h2) {
-        const int64_t u = i - n1 - h1 - n2;
-        for (int32_t r = 0; r < n; ++r) s += d2[static_cast<int64_t>(r) * h2 + u];
-    } else if (i < n1 + h1 + n2 + h2 + h2) {  // w3[u]: sum_r dy_r a2[r][u]
-        const int64_t u = i - n1 - h1 - n2 - h2;
-        for (int32_t r = 0; r < n; ++r) s = fmaf(dy[r], a2[static_cast<int64_t>(r) * h2 + u], s);
-    } else {
-        for (int32_t r = 0; r < n; ++r) s += dy[r];
+    if (i < total) {
+        if (i < n1) {  // W1[u][k]: sum_r d1[r][u] x[r][k]
+            const int64_t u = i / d_in, k = i - u * d_in;
+            for (int32_t r = ra; r < rb; ++r)
+                s = fmaf(d1[static_cast<int64_t>(r) * h1 + u], x[static_cast<int64_t>(r) * d_in + k], s);
+        } else if (i < n1 + h1) {
+            const int64_t u = i - n1;
+            for (int32_t r = ra; r < rb; ++r) s += d1[static_cast<int64_t>(r) * h1 + u];
+        } else if (i < n1 + h1 + n2) {  // W2[u][k]: sum_r d2[r][u] a1[r][k]
+            const int64_t j = i - n1 - h1, u = j / h1, k = j - u * h1;
+            for (int32_t r = ra; r < rb; ++r)
+                s = fmaf(d2[static_cast<int64_t>(r) * h2 + u], a1[static_cast<int64_t>(r) * h1 + k], s);
+        } else if (i < n1 + h1 + n2 + h2) {
+            const int64_t u = i - n1 - h1 - n2;
+            for (int32_t r = ra; r < rb; ++r) s += d2[static_cast<int64_t>(r) * h2 + u];
+        } else if (i < n1 + h1 + n2 + h2 + h2) {  // w3[u]: sum_r dy_r a2[r][u]
+            const int64_t u = i - n1 - h1 - n2 - h2;
+            for (int32_t r = ra; r < rb; ++r) s = fmaf(dy[r], a2[static_cast<int64_t>(r) * h2 + u], s);
+        } else {
+            for (int32_t r = ra; r < rb; ++r) s += dy[r];
+        }
     }
-    grad[i] = s;
+    part[seg][lane] = s;
+    __syncthreads();
+    if (seg == 0 && i < total) {
+        float g = part[0][lane];
+#pragma unroll
+        for (int t = 1; t < kSegs; ++t) g += part[t][lane];
+        grad[i] = g;
+    }
 }
 
 // Mean squared error over the rows, one CTA, fixed-order tree.
@@ -210,7 +251,7 @@ int64_t surrogate_num_params(int32_t d_in, int32_t h1, int32_t h2)
 
 size_t surrogate_forward_smem(int32_t d_in, int32_t h1, int32_t h2)
 {
-    return sizeof(float) * kRows * static_cast<size_t>(d_in + h1 + h2);
+    return sizeof(float) * kRows * static_cast<size_t>(d_in + h1 + h2 + 1);
 }
 
 cudaError_t launch_surrogate_init(int32_t d_in, int32_t h1, int32_t h2, uint64_t seed, float* theta,
@@ -225,13 +266,19 @@ cudaError_t launch_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_
                                      const float* x, float* y, float* a1, float* a2, cudaStream_t stream)
 {
     if (n <= 0) return cudaSuccess;
-    const size_t smem = surrogate_forward_smem(d_in, h1, h2);
-    cudaError_t err = cudaFuncSetAttribute(surr_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(smem));
+    // rows per CTA: 32 when the rows fill the GPU, 8 for small batches (more CTAs)
+    const bool wide = n >= 32 * 128;
+    const int32_t rpc = wide ? 32 : 8;
+    const size_t smem = sizeof(float) * rpc * static_cast<size_t>(d_in + h1 + h2 + 1);
+    cudaError_t err = wide ? cudaFuncSetAttribute(surr_forward_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  static_cast<int>(smem))
+                           : cudaFuncSetAttribute(surr_forward_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    // rows per CTA: 32 when the rows fill the GPU several times, fewer otherwise
-    const int32_t rpc = n >= 32 * 512 ? 32 : (n >= 8 * 512 ? 8 : 2);
-    surr_forward_kernel<<<(n + rpc - 1) / rpc, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, rpc, theta, x, y, a1, a2);
+    if (wide)
+        surr_forward_kernel<32><<<(n + 31) / 32, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+    else
+        surr_forward_kernel<8><<<(n + 7) / 8, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
     return cudaGetLastError();
 }
 
@@ -251,8 +298,8 @@ cudaError_t launch_surrogate_loss_grad(int32_t n, int32_t d_in, int32_t h1, int3
     surr_loss_kernel<<<1, 256, 0, stream>>>(n, yv, t, loss);
     surr_backrow_kernel<<<n, 64, sizeof(float) * h2, stream>>>(n, d_in, h1, h2, theta, yv, t, a1, a2, dy, d1, d2);
     const int64_t total = surrogate_num_params(d_in, h1, h2);
-    surr_grad_kernel<<<static_cast<int>((total + 127) / 128), 128, 0, stream>>>(n, d_in, h1, h2, x, a1, a2, dy, d1,
-                                                                              d2, grad);
+    surr_grad_kernel<<<static_cast<int>((total + kGradParams - 1) / kGradParams), 32 * kSegs, 0, stream>>>(
+        n, d_in, h1, h2, x, a1, a2, dy, d1, d2, grad);
     return cudaGetLastError();
 }
 
