@@ -15,13 +15,13 @@
 // (columns 32 + s), one instruction of N = 64, summed in the epilogue.
 //
 // Persistent CTA (one per SM), recipes strided by gridDim.x.  Warp roles:
-//   warps 0-11   producers: the child's genes, 8 per lane and Philox block,
+//   warps 0-15   producers: the child's genes, 8 per lane and Philox block,
 //                for one 64-input K block of W1 at a time (128 rows x 128 B
 //                in the 128-byte swizzled K-major layout, rows >= h unused),
 //                then b1, W2, b2 into a tail buffer, and per-thread crossover
 //                hits and sums of z^2 for the descriptor
-//   warp 12      TMEM allocation; one thread issues the MMAs
-//   warps 13-16  stage the probe pieces once; then per recipe the epilogue:
+//   warp 16      TMEM allocation; one thread issues the MMAs
+//   warps 17-20  stage the probe pieces once; then per recipe the epilogue:
 //                accumulator (TMEM lane = hidden unit) + b1, ReLU into shared
 //                memory, layer 2 in FP32, the descriptor row
 // Accumulators and tail buffers are double-buffered, so a recipe's epilogue
@@ -40,7 +40,7 @@ namespace leea {
 namespace {
 
 constexpr uint32_t kTagXo = 3, kTagMutMask = 4, kTagNormal = 5;
-constexpr int kProducerWarps = 12;
+constexpr int kProducerWarps = 16;
 constexpr int kPT = 32 * kProducerWarps;         // producer threads
 constexpr int kMmaWarp = kProducerWarps;
 constexpr int kFirstEpiWarp = kProducerWarps + 1;
@@ -144,6 +144,27 @@ __device__ __forceinline__ uint32_t mask8(const uint4& r, uint32_t thr)
         m |= (u < thr ? 1u : 0u) << t;
     }
     return m;
+}
+
+__device__ __forceinline__ void prefetch_l2(const float* p)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<uint64_t>(p)));
+}
+
+// Prefetches into L2 the parent genes of this thread's units of K block kb
+// (the producers' loads then wait on L2, not on HBM).
+__device__ __forceinline__ void prefetch_kb(const ProbeArgs& a, int kb, const float* pa, const float* pb, bool two,
+                                            int pt)
+{
+    const int kw = a.k - kb * kKB < kKB ? a.k - kb * kKB : kKB;
+    for (int u = pt; u < 8 * a.h; u += kPT) {
+        const int o = u >> 3, jc = u & 7;
+        if (8 * jc < kw) {
+            const int64_t i = static_cast<int64_t>(o) * a.k + kb * kKB + 8 * jc;
+            prefetch_l2(pa + i);
+            if (two) prefetch_l2(pb + i);
+        }
+    }
 }
 
 __device__ __forceinline__ uint32_t bf162_bits(__nv_bfloat162 v)
@@ -280,7 +301,12 @@ probe_tc_kernel(const __grid_constant__ ProbeArgs a, int32_t n)
             const float* pb = a.parents + static_cast<int64_t>(a.par2[r]) * a.c_pad;
             uint32_t hits = 0;
             float zz = 0.0f;
+            if (q == 0) {
+                prefetch_kb(a, 0, pa, pb, kind == 1, pt);
+                if (n_kb > 1) prefetch_kb(a, 1, pa, pb, kind == 1, pt);
+            }
             for (int kb = 0; kb < n_kb; ++kb) {
+                if (kb + 2 < n_kb) prefetch_kb(a, kb + 2, pa, pb, kind == 1, pt);
                 if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
                     raise_abort(s, a.status);
                     ok = false;
@@ -309,6 +335,14 @@ probe_tc_kernel(const __grid_constant__ ProbeArgs a, int32_t n)
                 if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
             if (!ok) break;
+            const int rn = r + gridDim.x;  // the next recipe's first K blocks
+            if (rn < n) {
+                const int32_t kn = a.kind[rn];
+                const float* pan = a.parents + static_cast<int64_t>(a.par1[rn]) * a.c_pad;
+                const float* pbn = a.parents + static_cast<int64_t>(a.par2[rn]) * a.c_pad;
+                prefetch_kb(a, 0, pan, pbn, kn == 1, pt);
+                if (n_kb > 1) prefetch_kb(a, 1, pan, pbn, kn == 1, pt);
+            }
             // b1, W2, b2 (genes h k .. c - 1) into tail buffer q & 1
             const uint32_t tb = static_cast<uint32_t>(q) & 1u, tpar = (static_cast<uint32_t>(q) >> 1) & 1u;
             if (!ptx::mbar_wait_bounded(&s.tempty[tb], tpar ^ 1u, s.abort_flag, kWaitLimitNs)) {

@@ -266,19 +266,29 @@ cudaError_t launch_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_
                                      const float* x, float* y, float* a1, float* a2, cudaStream_t stream)
 {
     if (n <= 0) return cudaSuccess;
-    // rows per CTA: 32 when the rows fill the GPU, 8 for small batches (more CTAs)
-    const bool wide = n >= 32 * 128;
-    const int32_t rpc = wide ? 32 : 8;
+    // rows per CTA: enough CTAs to spread over the SMs, as many rows as that
+    // allows (each CTA streams all of W1 once)
+    const int32_t rpc = n >= 32 * 128 ? 32 : (n >= 8 * 128 ? 8 : 2);
     const size_t smem = sizeof(float) * rpc * static_cast<size_t>(d_in + h1 + h2 + 1);
-    cudaError_t err = wide ? cudaFuncSetAttribute(surr_forward_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  static_cast<int>(smem))
-                           : cudaFuncSetAttribute(surr_forward_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  static_cast<int>(smem));
+    const int grid = (n + rpc - 1) / rpc;
+    cudaError_t err;
+    if (rpc == 32) {
+        err = cudaFuncSetAttribute(surr_forward_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem));
+        if (err == cudaSuccess)
+            surr_forward_kernel<32><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+    } else if (rpc == 8) {
+        err = cudaFuncSetAttribute(surr_forward_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem));
+        if (err == cudaSuccess)
+            surr_forward_kernel<8><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+    } else {
+        err = cudaFuncSetAttribute(surr_forward_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   static_cast<int>(smem));
+        if (err == cudaSuccess)
+            surr_forward_kernel<2><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+    }
     if (err != cudaSuccess) return err;
-    if (wide)
-        surr_forward_kernel<32><<<(n + 31) / 32, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
-    else
-        surr_forward_kernel<8><<<(n + 7) / 8, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
     return cudaGetLastError();
 }
 
