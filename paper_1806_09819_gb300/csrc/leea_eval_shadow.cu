@@ -70,7 +70,7 @@ struct EvalShArgs {
 struct ShSmem {
     uint8_t* ring;
     uint8_t* prm_raw;
-    float *w2t, *b2, *part;
+    float *b2, *part;
     uint64_t *full, *empty, *prm_full, *prm_empty, *acc_full, *acc_empty, *a_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
@@ -87,7 +87,7 @@ __host__ __device__ inline uint32_t sh_prm_bytes(int32_t h, int32_t d_out)
 size_t sh_smem_bytes(int32_t h_max, int32_t cw_max, int32_t dpad, int32_t stages)
 {
     return 1024 + static_cast<size_t>(stages) * cw_max * 128 + 2 * sh_prm_bytes(h_max, dpad) +
-           sizeof(float) * (h_max * dpad + 16 + (kShSlots - 1) * 128 * kShMaxOut) + 8 * (2 * stages + 8) + 64;
+           sizeof(float) * (16 + (kShSlots - 1) * 128 * kShMaxOut) + 8 * (2 * stages + 8) + 64;
 }
 
 __device__ __forceinline__ ShSmem carve(uint8_t* raw, const EvalShArgs& a, int32_t h_max)
@@ -97,8 +97,6 @@ __device__ __forceinline__ ShSmem carve(uint8_t* raw, const EvalShArgs& a, int32
     uint8_t* p = s.ring + a.stages * a.stage_bytes;
     s.prm_raw = p;
     p += 2u * a.prm_bytes_max;
-    s.w2t = reinterpret_cast<float*>(p);
-    p += sizeof(float) * h_max * a.dpad;
     s.b2 = reinterpret_cast<float*>(p);
     p += sizeof(float) * 16;
     s.part = reinterpret_cast<float*>(p);  // [slot 1..3][128][kShMaxOut] partial logits
@@ -428,22 +426,11 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                 }
                 ptx::named_barrier_sync(1, kShEpiThreads);  // A1: parameters landed (or abort)
                 if (!*s.ep_go) { ok = false; break; }
-                // b1 is read in place; W2 (d_out rows of h) is staged transposed,
-                // one hidden unit (column) per thread.
+                // b1 and W2 (d_out rows of h) are read in place: a thread's columns
+                // are contiguous, so 16-byte loads serve 4 hidden units (h % 16 == 0).
                 const float* src = reinterpret_cast<const float*>(s.prm_raw + pb * a.prm_bytes_max);
                 const float* b1 = src;
-                for (int col = et; col < r.h; col += kShEpiThreads) {
-                    float4* dst = reinterpret_cast<float4*>(s.w2t + col * a.dpad);
-                    for (int o4 = 0; o4 < a.dpad / 4; ++o4) {
-                        float v[4];
-#pragma unroll
-                        for (int t = 0; t < 4; ++t) {
-                            const int o = 4 * o4 + t;
-                            v[t] = o < a.d_out ? src[r.h + o * r.h + col] : 0.0f;
-                        }
-                        dst[o4] = make_float4(v[0], v[1], v[2], v[3]);
-                    }
-                }
+                const float* w2 = src + r.h;
                 if (et < 16) s.b2[et] = et < a.d_out ? src[r.h + a.d_out * r.h + et] : 0.0f;
 
                 // D * (w_scale / x_div): the FP8 shadow stores w / 2^e.
@@ -451,21 +438,6 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                 float logit[kShMaxOut];
 #pragma unroll
                 for (int o = 0; o < kShMaxOut; ++o) logit[o] = 0.0f;
-                // hidden unit col: ReLU(D * scale + b1), then its layer-2 contributions
-                auto hidden = [&](int col, float d) {
-                    const float hv = fmaxf(fmaf(d, scale, b1[col]), 0.0f);
-                    const float4* wr = reinterpret_cast<const float4*>(s.w2t + col * a.dpad);
-#pragma unroll
-                    for (int o4 = 0; o4 < kShMaxOut / 4; ++o4) {
-                        if (4 * o4 < a.d_out) {
-                            const float4 w = wr[o4];
-                            logit[4 * o4 + 0] = fmaf(w.x, hv, logit[4 * o4 + 0]);
-                            logit[4 * o4 + 1] = fmaf(w.y, hv, logit[4 * o4 + 1]);
-                            logit[4 * o4 + 2] = fmaf(w.z, hv, logit[4 * o4 + 2]);
-                            logit[4 * o4 + 3] = fmaf(w.w, hv, logit[4 * o4 + 3]);
-                        }
-                    }
-                };
                 for (int32_t c = 0; ok && c < r.n_chunks; ++c) {
                     if (et == 0) {
                         const bool got = ptx::mbar_wait_bounded(s.acc_full, acc_phase, s.abort_flag, kShWaitNs);
@@ -489,9 +461,39 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                     ptx::tc_fence_before();
                     ptx::mbar_arrive(s.acc_empty);
                     acc_phase ^= 1u;
+                    // hidden units col0 .. col0 + ncol - 1: ReLU(D * scale + b1), then
+                    // per output its layer-2 sum over them in column order (each
+                    // logit accumulates over the hidden units in order across chunks)
+                    const int32_t col0 = r0 + 8 * j0, ncol = 8 * (j1 - j0);
+                    // (the activations replace the accumulator values in place)
 #pragma unroll
-                    for (int cc = 0; cc < kShRegCols; ++cc)
-                        if (j0 + cc / 8 < j1) hidden(r0 + 8 * j0 + cc, __uint_as_float(dreg[cc]));
+                    for (int cc = 0; cc < kShRegCols; cc += 4) {
+                        if (cc < ncol) {
+                            const float4 b4 = *reinterpret_cast<const float4*>(b1 + col0 + cc);
+                            dreg[cc] = __float_as_uint(fmaxf(fmaf(__uint_as_float(dreg[cc]), scale, b4.x), 0.0f));
+                            dreg[cc + 1] = __float_as_uint(fmaxf(fmaf(__uint_as_float(dreg[cc + 1]), scale, b4.y), 0.0f));
+                            dreg[cc + 2] = __float_as_uint(fmaxf(fmaf(__uint_as_float(dreg[cc + 2]), scale, b4.z), 0.0f));
+                            dreg[cc + 3] = __float_as_uint(fmaxf(fmaf(__uint_as_float(dreg[cc + 3]), scale, b4.w), 0.0f));
+                        }
+                    }
+#pragma unroll
+                    for (int o = 0; o < kShMaxOut; ++o) {
+                        if (o < a.d_out) {
+                            const float* wr = w2 + o * r.h + col0;
+                            float acc = logit[o];
+#pragma unroll
+                            for (int cc = 0; cc < kShRegCols; cc += 4) {
+                                if (cc < ncol) {
+                                    const float4 w = *reinterpret_cast<const float4*>(wr + cc);
+                                    acc = fmaf(w.x, __uint_as_float(dreg[cc]), acc);
+                                    acc = fmaf(w.y, __uint_as_float(dreg[cc + 1]), acc);
+                                    acc = fmaf(w.z, __uint_as_float(dreg[cc + 2]), acc);
+                                    acc = fmaf(w.w, __uint_as_float(dreg[cc + 3]), acc);
+                                }
+                            }
+                            logit[o] = acc;
+                        }
+                    }
                 }
                 if (!ok) break;
                 ptx::mbar_arrive(&s.prm_empty[pb]);  // b1 no longer read
