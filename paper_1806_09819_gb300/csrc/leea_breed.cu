@@ -13,6 +13,8 @@
 // Work items walk the children alternately from the front (elites, crossover
 // children) and the back (mutation children), so every SM mixes the
 // HBM-heavier crossover items with the arithmetic-heavier mutation items.
+// With many runs each CTA takes a contiguous range of items, so that it
+// meets few run boundaries (each one reloads the run's arguments).
 // A consumer thread owns 8 consecutive genes of the chunk: one Philox block
 // of 16-bit mask draws (crossover or mutation mask) and two Philox blocks of
 // normals.  In mutation children only the Box-Muller pairs that hold a masked
@@ -246,6 +248,11 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
     extern __shared__ uint8_t smem_raw[];
     const BreedSmem s = carve(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // Items of this CTA: many runs, a contiguous range; one run, every gridDim.x-th
+    // (neighbouring CTAs then work on neighbouring children, which share parents in L2).
+    const int64_t it_begin = MULTI ? n_items * blockIdx.x / gridDim.x : blockIdx.x;
+    const int64_t it_end = MULTI ? n_items * (blockIdx.x + 1) / gridDim.x : n_items;
+    const int64_t it_step = MULTI ? 1 : gridDim.x;
     if (threadIdx.x == 0) {
         for (int i = 0; i < kStages; ++i) {
             ptx::mbar_init(&s.full[i], 1);
@@ -263,7 +270,7 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
             uint32_t issued_mask = 0, parity_mask = 0;  // per stage: issued at all / parity of the last issue
             int32_t cur_j = -1, cur_run = -1, cur_kind = 0, cur_p1 = 0, cur_p2 = 0, cur_sexp = 0;
             bool ok = true;
-            for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+            for (int64_t it = it_begin; it < it_end; it += it_step) {
                 if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
                     raise_abort(s.abort_flag, status);
                     ok = false;
@@ -324,7 +331,7 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
         float* children = run0.children;
         int32_t cur_run = MULTI ? -1 : 0;
         uint32_t stage = 0, phase = 0;
-        for (int64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+        for (int64_t it = it_begin; it < it_end; it += it_step) {
             if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kWaitLimitNs)) {
                 raise_abort(s.abort_flag, status);
                 break;
