@@ -51,6 +51,8 @@ constexpr int kShEpiThreads = 32 * kShEpiWarps;
 constexpr int kShThreads = 32 * (2 + kShEpiWarps);
 constexpr int kFirstEpiWarp = 2;
 constexpr int kShMaxOut = 16;
+constexpr int kShPartStride = kShMaxOut + 4;  // floats per sample row of partial logits: 16-byte
+                                              // accesses of 8 consecutive rows hit distinct banks
 constexpr int kShMaxChunk = 128;   // hidden units per chunk at most
 constexpr int kShRegCols = kShMaxChunk / kShSlots;  // accumulator columns a thread holds
 constexpr uint32_t kShTmemCols = 512;
@@ -87,7 +89,7 @@ __host__ __device__ inline uint32_t sh_prm_bytes(int32_t h, int32_t d_out)
 size_t sh_smem_bytes(int32_t h_max, int32_t cw_max, int32_t dpad, int32_t stages)
 {
     return 1024 + static_cast<size_t>(stages) * cw_max * 128 + 2 * sh_prm_bytes(h_max, dpad) +
-           sizeof(float) * (16 + (kShSlots - 1) * 128 * kShMaxOut) + 8 * (2 * stages + 8) + 64;
+           sizeof(float) * (16 + (kShSlots - 1) * 128 * kShPartStride) + 8 * (2 * stages + 8) + 64;
 }
 
 __device__ __forceinline__ ShSmem carve(uint8_t* raw, const EvalShArgs& a, int32_t h_max)
@@ -99,8 +101,8 @@ __device__ __forceinline__ ShSmem carve(uint8_t* raw, const EvalShArgs& a, int32
     p += 2u * a.prm_bytes_max;
     s.b2 = reinterpret_cast<float*>(p);
     p += sizeof(float) * 16;
-    s.part = reinterpret_cast<float*>(p);  // [slot 1..3][128][kShMaxOut] partial logits
-    p += sizeof(float) * (kShSlots - 1) * 128 * kShMaxOut;
+    s.part = reinterpret_cast<float*>(p);  // [slot 1..3][128][kShPartStride] partial logits
+    p += sizeof(float) * (kShSlots - 1) * 128 * kShPartStride;
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.full = bars;
     s.empty = bars + a.stages;
@@ -499,7 +501,7 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                 ptx::mbar_arrive(&s.prm_empty[pb]);  // b1 no longer read
 
                 if (slot) {
-                    float4* dst = reinterpret_cast<float4*>(s.part + ((slot - 1) * 128 + row) * kShMaxOut);
+                    float4* dst = reinterpret_cast<float4*>(s.part + ((slot - 1) * 128 + row) * kShPartStride);
 #pragma unroll
                     for (int o4 = 0; o4 < kShMaxOut / 4; ++o4)
                         dst[o4] = make_float4(logit[4 * o4], logit[4 * o4 + 1], logit[4 * o4 + 2], logit[4 * o4 + 3]);
@@ -510,12 +512,21 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                     int32_t good = 0;
                     if (srow < r.batch) {
 #pragma unroll
-                        for (int o = 0; o < kShMaxOut; ++o) {
-                            float z = logit[o];
+                        for (int t = 0; t < kShSlots - 1; ++t) {  // slot order 1, 2, 3 per output
+                            const float4* srcp = reinterpret_cast<const float4*>(s.part + (t * 128 + row) * kShPartStride);
 #pragma unroll
-                            for (int t = 0; t < kShSlots - 1; ++t) z += s.part[(t * 128 + row) * kShMaxOut + o];
-                            logit[o] = z + s.b2[o];
+                            for (int o4 = 0; o4 < kShMaxOut / 4; ++o4) {
+                                if (4 * o4 < a.d_out) {
+                                    const float4 v = srcp[o4];
+                                    logit[4 * o4] += v.x;
+                                    logit[4 * o4 + 1] += v.y;
+                                    logit[4 * o4 + 2] += v.z;
+                                    logit[4 * o4 + 3] += v.w;
+                                }
+                            }
                         }
+#pragma unroll
+                        for (int o = 0; o < kShMaxOut; ++o) logit[o] += s.b2[o];
                         float zmax = logit[0];
                         int arg = 0;
 #pragma unroll
