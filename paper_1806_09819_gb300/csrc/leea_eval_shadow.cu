@@ -54,6 +54,7 @@ constexpr int kShMaxOut = 16;
 constexpr int kShPartStride = kShMaxOut + 4;  // floats per sample row of partial logits: 16-byte
                                               // accesses of 8 consecutive rows hit distinct banks
 constexpr int kShMaxChunk = 128;   // hidden units per chunk at most
+constexpr int kShStageBlocks = 2;  // shadow blocks (128 bytes of every row) per pipeline stage
 constexpr int kShRegCols = kShMaxChunk / kShSlots;  // accumulator columns a thread holds
 constexpr uint32_t kShTmemCols = 512;
 constexpr uint64_t kShWaitNs = 2000000000ull;
@@ -88,7 +89,7 @@ __host__ __device__ inline uint32_t sh_prm_bytes(int32_t h, int32_t d_out)
 
 size_t sh_smem_bytes(int32_t h_max, int32_t cw_max, int32_t dpad, int32_t stages)
 {
-    return 1024 + static_cast<size_t>(stages) * cw_max * 128 + 2 * sh_prm_bytes(h_max, dpad) +
+    return 1024 + static_cast<size_t>(stages) * kShStageBlocks * cw_max * 128 + 2 * sh_prm_bytes(h_max, dpad) +
            sizeof(float) * (16 + (kShSlots - 1) * 128 * kShPartStride) + 8 * (2 * stages + 8) + 64;
 }
 
@@ -300,7 +301,7 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                         }
                         ptx::tc_fence_after();
                         bool first = true;
-                        for (int kc = 0; kc < a.k_stages; ++kc) {
+                        for (int kc = 0; kc < a.k_stages; kc += kShStageBlocks) {
                             // Stages are filled by the copy engine (async proxy, like the
                             // MMA's operand reads): the mbarrier completion orders them.
                             if (!ptx::mbar_wait_bounded(&s.full[stage], phase, s.abort_flag, kShWaitNs)) {
@@ -308,10 +309,11 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                                 ok = false;
                                 break;
                             }
-                            const uint32_t sb = ring + stage * a.stage_bytes;
+                            for (int blk = 0; blk < kShStageBlocks && kc + blk < a.k_stages; ++blk) {
+                            const uint32_t sb = ring + stage * a.stage_bytes + blk * width * 128u;
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {  // 4 MMA K-steps of 32 bytes per 128-byte row
-                                const int kg = kc * a.k_elems_stage + kk * (a.k_elems_stage / 4);
+                                const int kg = (kc + blk) * a.k_elems_stage + kk * (a.k_elems_stage / 4);
                                 if (kg >= a.k_mma) break;
                                 const uint64_t bd = ptx::smem_desc_sw128(sb + kk * 32u);
                                 if (PREC == 1) {
@@ -327,6 +329,7 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                                         first = false;
                                     }
                                 }
+                            }
                             }
                             ptx::mma_commit(&s.empty[stage]);
                             if (++stage == static_cast<uint32_t>(a.stages)) { stage = 0; phase ^= 1u; }
@@ -367,17 +370,21 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
                     const uint8_t* src = r.shadow + static_cast<int64_t>(p) * r.sh_stride;
                     for (int32_t c = 0; ok && c < r.n_chunks; ++c) {
                         const uint32_t bytes = static_cast<uint32_t>(chunk_width(r, c)) * 128u;
-                        for (int kc = 0; kc < a.k_stages; ++kc) {
+                        for (int kc = 0; kc < a.k_stages; kc += kShStageBlocks) {
                             if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kShWaitNs)) {
                                 raise_abort(s, a);
                                 ok = false;
                                 break;
                             }
-                            // rows [c cw, c cw + width) of block kc: contiguous in the tiled layout
-                            ptx::mbar_arrive_expect_tx(&s.full[stage], bytes);
-                            ptx::bulk_load(s.ring + stage * a.stage_bytes,
-                                           src + (static_cast<int64_t>(kc) * r.h + static_cast<int64_t>(c) * r.cw) * 128,
-                                           bytes, &s.full[stage]);
+                            // rows [c cw, c cw + width) of blocks kc, kc + 1: each contiguous in
+                            // the tiled layout, one after the other in the stage
+                            const int nb = kc + kShStageBlocks <= a.k_stages ? kShStageBlocks : a.k_stages - kc;
+                            ptx::mbar_arrive_expect_tx(&s.full[stage], bytes * static_cast<uint32_t>(nb));
+                            for (int blk = 0; blk < nb; ++blk)
+                                ptx::bulk_load(s.ring + stage * a.stage_bytes + blk * bytes,
+                                               src + (static_cast<int64_t>(kc + blk) * r.h +
+                                                      static_cast<int64_t>(c) * r.cw) * 128,
+                                               bytes, &s.full[stage]);
                             issued_mask |= 1u << stage;
                             parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
                             if (++stage == static_cast<uint32_t>(a.stages)) { stage = 0; phase ^= 1u; }
@@ -605,7 +612,7 @@ __global__ void combine_tiles_kernel(const __grid_constant__ EvalShArgs a)
 
 int32_t sh_stages_for(int32_t h_max, int32_t cw_max, int32_t dpad)
 {
-    int32_t stages = 8;
+    int32_t stages = 8 / kShStageBlocks;
     while (stages > 2 && sh_smem_bytes(h_max, cw_max, dpad, stages) > 227u * 1024u) --stages;
     return stages;
 }
@@ -623,7 +630,7 @@ EvalShArgs common_args(int32_t k, int32_t d_out, int32_t precision, int32_t h_ma
     a.a_col = static_cast<uint32_t>(cw_max);
     a.a_total_cols = sh_a_cols(precision, k, &a.a_piece_cols);
     a.prm_bytes_max = sh_prm_bytes(h_max, d_out);
-    a.stage_bytes = static_cast<uint32_t>(cw_max) * 128u;
+    a.stage_bytes = static_cast<uint32_t>(kShStageBlocks * cw_max) * 128u;
     a.stages = sh_stages_for(h_max, cw_max, a.dpad);
     return a;
 }
