@@ -21,33 +21,38 @@ __device__ __forceinline__ uint64_t rank_key(float f, int32_t idx)
     return (static_cast<uint64_t>(~asc) << 32) | static_cast<uint32_t>(idx);
 }
 
-// Rank by counting: the rank of i is the number of keys below its own.  Each
-// thread owns one individual and scans every key through a shared tile; at
-// the population sizes of the method (<= a few 10^4) this is a handful of
-// microseconds and needs no scratch memory.
+// Rank by counting: the rank of i is the number of keys below its own.  A
+// warp owns one individual: its lanes scan the keys of a shared tile (the
+// CTA's 8 warps share it), then the counts are summed over the lanes.  At
+// the population sizes of the method (<= a few 10^4) this is a few
+// microseconds spread over many SMs and needs no scratch memory.
 constexpr int kRankTile = 2048;
+constexpr int kRankWarps = 8;
 
-__global__ void __launch_bounds__(256) rank_kernel(int32_t pop, const float* __restrict__ f_adj,
-                                                   int32_t* __restrict__ order)
+__global__ void __launch_bounds__(32 * kRankWarps) rank_kernel(int32_t pop, const float* __restrict__ f_adj,
+                                                              int32_t* __restrict__ order)
 {
     __shared__ uint64_t tile[kRankTile];
-    const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t mine = i < pop ? rank_key(f_adj[i], i) : ~0ull;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t i = blockIdx.x * kRankWarps + warp;
+    const uint64_t mine = i < pop ? rank_key(f_adj[i], i) : 0ull;
     int32_t r = 0;
     for (int32_t base = 0; base < pop; base += kRankTile) {
         const int32_t n = pop - base < kRankTile ? pop - base : kRankTile;
         __syncthreads();
         for (int32_t t = threadIdx.x; t < n; t += blockDim.x) tile[t] = rank_key(f_adj[base + t], base + t);
         __syncthreads();
-#pragma unroll 8
-        for (int32_t t = 0; t < n; ++t) r += tile[t] < mine ? 1 : 0;
+#pragma unroll 4
+        for (int32_t t = lane; t < n; t += 32) r += tile[t] < mine ? 1 : 0;
     }
-    if (i < pop) order[r] = i;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) r += __shfl_xor_sync(0xFFFFFFFFu, r, off);
+    if (lane == 0 && i < pop) order[r] = i;
 }
 
 cudaError_t launch_rank(int32_t pop, const float* f_adj, int32_t* order, cudaStream_t stream)
 {
-    rank_kernel<<<(pop + 255) / 256, 256, 0, stream>>>(pop, f_adj, order);
+    rank_kernel<<<(pop + kRankWarps - 1) / kRankWarps, 32 * kRankWarps, 0, stream>>>(pop, f_adj, order);
     return cudaGetLastError();
 }
 
@@ -178,6 +183,7 @@ cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t
 // then one thread per child runs the selection against the sorted order.
 constexpr int kFusedThreads = 1024;
 constexpr int kFusedMaxPop = 4096;
+constexpr int kSplitMinPop = 512;  // from here on: rank_kernel + select_kernel (measured at P = 1000)
 
 __device__ __forceinline__ void rank_select_body(const SelectArgs& a, const float* __restrict__ f_adj,
                                                  int32_t* __restrict__ order_out, int32_t* __restrict__ par1,
@@ -237,7 +243,9 @@ rank_select_runs_kernel(const SelectRun* __restrict__ runs, const uint32_t* __re
 cudaError_t launch_rank_select(const SelectArgs& a, const float* f_adj, int32_t* order, int32_t* par1, int32_t* par2,
                                int32_t* kind, float* f_inh, cudaStream_t stream)
 {
-    if (a.pop > kFusedMaxPop) {
+    // The fused single-CTA kernel serves small populations, where one launch
+    // beats two; above kSplitMinPop the ranking spread over many SMs wins.
+    if (a.pop > kFusedMaxPop || a.pop >= kSplitMinPop) {
         cudaError_t err = launch_rank(a.pop, f_adj, order, stream);
         if (err != cudaSuccess) return err;
         return launch_select(a, f_adj, order, par1, par2, kind, f_inh, stream);
