@@ -102,6 +102,72 @@ def test_surrogate_generation_matches_oracle(gpu, oracle_mod, precision, screen)
         st.close()
 
 
+def test_surrogate_full_size_sampled(gpu, oracle_mod):
+    """One pre-screened generation at the benchmark's size and launch shape
+    (population 2048, 784-112-10, 4 recipes per slot = 8,188 recipes, 32
+    probe images, BF16): every recipe bit-exact; sampled descriptors, scores,
+    made children and their fitness against the oracle."""
+    import torch
+    pop, dims, batch = 2048, [784, 112, 10], 100
+    prm_d = dict(sigma=0.005, mut_rate=0.1, n_elite=1, p_c=0.5)
+    (xtr, ytr), (xte, _) = synthetic.dataset(n_train=2000, n_test=64)
+    probe = xte[:32]
+    sp = gpu.SurrogateParams(mult=4, n_probe=32, warmup=0)
+    st = gpu.SurrState(pop, dims, gpu.Params(**prm_d, precision=1), sp, seed=13, probe=probe)
+    try:
+        c = st.c
+        parents = synthetic.random_population(pop, c, seed=8, scale=0.05)
+        f_adj = np.random.default_rng(2).normal(-2.3, 0.3, size=pop).astype(np.float32)
+        st.set_population(parents)
+        st.set_fitness(f_adj)
+        st.set_generation(11, True)
+        st.set_screen(True)
+        theta0, _, _ = st.get_surrogate()
+        levels = synthetic.to_levels(xtr[:batch])
+        y = ytr[:batch]
+        st.generation_u8(torch.from_numpy(levels).cuda(), torch.from_numpy(y).cuda())
+        step = st.get_step()
+        oprm = oracle_mod.Params(**prm_d, precision=1)
+        f64 = f_adj.astype(np.float64)
+        order = oracle_mod.rank(f64)
+        r1, r2, rk, rinh, rent = oracle_mod.select_recipes(oprm, f64, order, 13, 12, 4)
+        assert st.n_recipes == r1.size == 8188
+        np.testing.assert_array_equal(step["r_par1"], r1)
+        np.testing.assert_array_equal(step["r_par2"], r2)
+        np.testing.assert_array_equal(step["r_kind"], rk)
+        np.testing.assert_array_equal(step["r_entity"], rent)
+        sample = np.array([0, 1, 2047, 4093, 4094, 4095, 6000, 8187])
+        p64 = parents.astype(np.float64)
+        ref = oracle_mod.descriptors(oprm, dims, 13, 12, p64, f64, r1[sample], r2[sample], rk[sample],
+                                     step["r_f_inh"][sample].astype(np.float64), rent[sample], probe.astype(np.float64))
+        got = step["desc"][sample].astype(np.float64)
+        np.testing.assert_array_equal(got[:, :3], ref[:, :3].astype(np.float32))
+        np.testing.assert_allclose(got[:, 3:5], ref[:, 3:5], rtol=1e-5, atol=0)
+        scale = np.abs(ref[:, 5:]).max()
+        err = np.abs(got[:, 5:] - ref[:, 5:])
+        # (an FP32 child gene one ulp off the oracle's may round to the other
+        # BF16 neighbour: a few logits move by up to a BF16 ulp of a weight)
+        assert (err <= 1e-4 * np.abs(ref[:, 5:]) + 1e-4 * scale).mean() >= 0.999, err.max()
+        assert err.max() <= 1e-2 * scale
+        # scores of the sampled recipes: the oracle MLP on the standardised descriptors
+        _, mu, sd = st.get_surrogate()
+        xs = (step["desc"][sample].astype(np.float64) - mu.astype(np.float64)) / sd.astype(np.float64)
+        pred_ref = oracle_mod.mlp_forward(theta0.astype(np.float64), xs, st.width, 64, 64)
+        np.testing.assert_allclose(step["pred"][sample], pred_ref, rtol=1e-4, atol=1e-4 * np.abs(pred_ref).max())
+        # sampled made children and their fitness on the batch
+        kids = st.get_population()
+        slots = np.array([1, 2, 1000, 2046, 2047])
+        ref_kids = oracle_mod.breed_entities(oprm, dims, 13, 12, p64, step["c_par1"][slots], step["c_par2"][slots],
+                                             step["c_kind"][slots], step["c_entity"][slots])
+        assert_genes_close(kids[slots], ref_kids, prm_d["sigma"])
+        f_raw, _ = st.raw_fitness()
+        q = oracle_mod.quantize_w1(kids[slots].astype(np.float64), dims, 1, None)
+        f_ref, _ = oracle_mod.evaluate(q, dims, levels.astype(np.float64) / 255.0, y)
+        assert_fitness_close(f_raw[slots], f_ref, "children")
+    finally:
+        st.close()
+
+
 def test_trained_surrogate_ranks_offspring_better_than_inherited_fitness(gpu):
     """On the synthetic task: after a few generations of online training the
     network's scores rank the audited offspring (made and evaluated whatever
