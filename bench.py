@@ -132,6 +132,13 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
+def job_rate(world: int, units_per_rank: float, ms_local: float, dist, device=None):
+    """(slowest rank's ms, whole-job units per second): every rank processed
+    units_per_rank units; the job took as long as its slowest rank."""
+    ms_max = max_over_ranks(ms_local, dist, device)
+    return ms_max, world * units_per_rank / (ms_max / 1000.0)
+
+
 def barrier(dist, device=None):
     if dist is None:
         return
@@ -602,8 +609,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
     ms = ev0.elapsed_time(ev1)
     prof = st.leea_profile_read()
     st.leea_profile_enable(False)
-    ms_max = max_over_ranks(ms, dist, dev)
-    gen_per_s = world * steps / (ms_max / 1000.0)
+    ms_max, gen_per_s = job_rate(world, steps, ms, dist, dev)
 
     # ---- end to end through the host-buffer entry point ----
     e2e_steps = max(10, min(steps, 1000))
