@@ -375,9 +375,8 @@ def run_batching(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize(dev)
     barrier(dist, dev)
     clk = clocks.stop(mark)
-    ms_max = max_over_ranks(ev0.elapsed_time(ev1), dist, dev)
     n_runs = len(specs)
-    gen_per_s = world * n_runs * steps / (ms_max / 1000.0)
+    ms_max, gen_per_s = job_rate(world, n_runs * steps, ev0.elapsed_time(ev1), dist, dev)
     samples_per_gen = sum(sp.pop * sp.batch for sp in specs)
 
     # per-stage times: direct launches between events (same kernels as the graph)
