@@ -132,6 +132,15 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
+def kernels_per_generation(pop: int, batch: int, precision: int) -> dict:
+    """Kernel launches per stage of one state-object generation: ranking and
+    selection run as one kernel below 512 nets and as two above; the shadow
+    evaluation adds a combining kernel when the batch spans several 128-sample
+    tiles."""
+    return {"select": 2 if pop >= 512 else 1, "breed": 1,
+            "evaluate": 1 + (1 if precision > 0 and batch > 128 else 0)}
+
+
 def job_rate(world: int, units_per_rank: float, ms_local: float, dist, device=None):
     """(slowest rank's ms, whole-job units per second): every rank processed
     units_per_rank units; the job took as long as its slowest rank."""
@@ -698,7 +707,8 @@ def run_native(args, rank: int, world: int, local_rank: int):
                        "eval_kernel": eval_kernel,
                        "l2": f"inputs larger than L2 (2 population buffers of {pop_mb:.0f} MB), no flush"},
             "network_samples_per_sec": gen_per_s * pop * batch,
-            "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values())), "roofline": roofline,
+            "e2e": e2e, "gpu_launches": int(sum(v[1] * kernels_per_generation(pop, batch, precision)[k]
+                                                for k, v in prof.items())), "roofline": roofline,
             "kernels": kernels, "clocks": clk}
     if precision and rank == 0:
         # the last generation evaluated the last end-to-end batch
