@@ -244,6 +244,12 @@ cudaError_t launch_surrogate_loss_grad(int32_t n, int32_t d_in, int32_t h1, int3
                                        cudaStream_t stream);
 cudaError_t launch_surrogate_adam(int64_t n_params, float* theta, const float* grad, float* m, float* v, int64_t step,
                                   float lr, float beta1, float beta2, float eps, cudaStream_t stream);
+// One training step of the state object: forward with the per-row deltas,
+// the gradient with the Adam update (step number `step`) fused, and the loss
+// only when `loss` is not NULL.  work: surrogate_work_floats(n, h1, h2).
+cudaError_t launch_surrogate_train_step(int32_t n, int32_t d_in, int32_t h1, int32_t h2, float* theta, const float* x,
+                                        const float* t, float* loss, float* work, float* m, float* v, int64_t step,
+                                        float lr, float beta1, float beta2, float eps, cudaStream_t stream);
 
 cudaError_t launch_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
                                uint32_t n0, int64_t count, uint32_t* out, cudaStream_t stream);

@@ -515,13 +515,12 @@ leea_status surr_breed_generation(leea_surr* s, const uint8_t* x, float x_div, c
     for (int32_t step = 0; step < s->sp.train_steps; ++step) {
         const int64_t off = (static_cast<int64_t>(step) * s->sp.train_batch) % filled;
         const int32_t n = static_cast<int32_t>(filled - off < s->sp.train_batch ? filled - off : s->sp.train_batch);
-        LEEA_CUDA_TRY(launch_surrogate_loss_grad(n, s->width, s->sp.hidden1, s->sp.hidden2, s->theta,
-                                                 s->x_hist + off * s->width, s->t_hist + off, s->loss, s->grad,
-                                                 s->work, st),
-                      "surrogate gradient");
-        LEEA_CUDA_TRY(launch_surrogate_adam(s->n_theta, s->theta, s->grad, s->adam_m, s->adam_v, ++s->adam_step,
-                                            s->sp.lr, 0.9f, 0.999f, 1e-8f, st),
-                      "surrogate Adam");
+        const bool last = step + 1 == s->sp.train_steps;  // the recorded loss is the last step's
+        LEEA_CUDA_TRY(launch_surrogate_train_step(n, s->width, s->sp.hidden1, s->sp.hidden2, s->theta,
+                                                  s->x_hist + off * s->width, s->t_hist + off,
+                                                  last ? s->loss : nullptr, s->work, s->adam_m, s->adam_v,
+                                                  ++s->adam_step, s->sp.lr, 0.9f, 0.999f, 1e-8f, st),
+                      "surrogate training step");
     }
     if (s->sp.train_steps > 0)
         LEEA_CUDA_TRY(cudaMemcpyAsync(s->stats + 3 * stat_i + 2, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, st),

@@ -102,12 +102,16 @@ __device__ __forceinline__ void dense_rows(const float* __restrict__ W, const fl
 }
 
 // Forward for R rows per CTA; a1 / a2 (the ReLU outputs) are kept for the
-// backward pass when not NULL.
+// backward pass when not NULL.  With targets t (then a1, a2, dy, d1, d2 are
+// all given) the same CTA also takes its rows' backward pass up to the
+// per-row deltas: dy = 2 (y - t) / n, d2 = dy w3 (.) [a2 > 0],
+// d1 = (W2^T d2) (.) [a1 > 0] (sums over the h2 units in order).
 template <int R>
 __global__ void __launch_bounds__(kFwdThreads)
 surr_forward_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* __restrict__ theta,
                     const float* __restrict__ x, float* __restrict__ y, float* __restrict__ a1_out,
-                    float* __restrict__ a2_out)
+                    float* __restrict__ a2_out, const float* __restrict__ t, float* __restrict__ dy,
+                    float* __restrict__ d1, float* __restrict__ d2)
 {
     extern __shared__ float sm[];
     float* xs = sm;                     // [R][d_in]
@@ -134,39 +138,57 @@ surr_forward_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float
         for (int o = threadIdx.x; o < rows * h1; o += kFwdThreads) a1_out[static_cast<int64_t>(r0) * h1 + o] = s1[o];
     if (a2_out)
         for (int o = threadIdx.x; o < rows * h2; o += kFwdThreads) a2_out[static_cast<int64_t>(r0) * h2 + o] = s2[o];
+    if (!t) return;
+    // deltas: s3 <- dy, s2 <- d2 (in place), then d1 per (row, hidden unit)
+    __syncthreads();
+    for (int r = threadIdx.x; r < rows; r += kFwdThreads) {
+        const float g = 2.0f * (s3[r] - t[r0 + r]) / static_cast<float>(n);
+        s3[r] = g;
+        dy[r0 + r] = g;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < rows * h2; o += kFwdThreads) {
+        const int r = o / h2, u = o - r * h2;
+        const float v = s2[o] > 0.0f ? s3[r] * p.w3[u] : 0.0f;
+        s2[o] = v;
+        d2[static_cast<int64_t>(r0) * h2 + o] = v;
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < rows * h1; o += kFwdThreads) {
+        const int r = o / h1, k = o - r * h1;
+        float sum = 0.0f;
+        for (int u = 0; u < h2; ++u) sum = fmaf(s2[r * h2 + u], p.W2[static_cast<int64_t>(u) * h1 + k], sum);
+        d1[static_cast<int64_t>(r0) * h1 + o] = s1[o] > 0.0f ? sum : 0.0f;
+    }
 }
 
-// Per row: dy = 2 (y - t) / n, d2 = dy w3 (.) [a2 > 0], d1 = (W2^T d2) (.) [a1 > 0].
-__global__ void surr_backrow_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* __restrict__ theta,
-                                    const float* __restrict__ y, const float* __restrict__ t,
-                                    const float* __restrict__ a1, const float* __restrict__ a2,
-                                    float* __restrict__ dy, float* __restrict__ d1, float* __restrict__ d2)
+struct AdamArgs {
+    float* theta;
+    float *m, *v;
+    float lr, beta1, beta2, eps, c1, c2;
+};
+
+// One Adam update of parameter i with gradient g (Kingma & Ba).
+__device__ __forceinline__ void adam_update(const AdamArgs& ad, int64_t i, float g)
 {
-    const MlpView p = view(theta, d_in, h1, h2);
-    const int32_t r = blockIdx.x;
-    extern __shared__ float sd2[];  // [h2]
-    const float g = 2.0f * (y[r] - t[r]) / static_cast<float>(n);
-    for (int u = threadIdx.x; u < h2; u += blockDim.x) {
-        const float v = a2[static_cast<int64_t>(r) * h2 + u] > 0.0f ? g * p.w3[u] : 0.0f;
-        sd2[u] = v;
-        d2[static_cast<int64_t>(r) * h2 + u] = v;
-    }
-    if (threadIdx.x == 0) dy[r] = g;
-    __syncthreads();
-    for (int k = threadIdx.x; k < h1; k += blockDim.x) {
-        float s = 0.0f;
-        for (int u = 0; u < h2; ++u) s = fmaf(sd2[u], p.W2[static_cast<int64_t>(u) * h1 + k], s);
-        d1[static_cast<int64_t>(r) * h1 + k] = a1[static_cast<int64_t>(r) * h1 + k] > 0.0f ? s : 0.0f;
-    }
+    const float mi = fmaf(ad.beta1, ad.m[i], (1.0f - ad.beta1) * g);
+    const float vi = fmaf(ad.beta2, ad.v[i], (1.0f - ad.beta2) * g * g);
+    ad.m[i] = mi;
+    ad.v[i] = vi;
+    ad.theta[i] -= ad.lr * (mi / ad.c1) / (sqrtf(vi / ad.c2) + ad.eps);
 }
 
 // Gradient: parameter i's sum over the rows, in kSegs segments of rows
 // (warp = segment, lane = parameter: coalesced rows of x / a1 / a2), each
-// summed in row order, then the segments in order.
+// summed in row order, then the segments in order.  ADAM: the parameter is
+// updated at once instead of writing its gradient (the gradient reads no
+// parameter, so the update cannot race with another CTA).
+template <bool ADAM>
 __global__ void __launch_bounds__(32 * kSegs)
 surr_grad_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* __restrict__ x,
                  const float* __restrict__ a1, const float* __restrict__ a2, const float* __restrict__ dy,
-                 const float* __restrict__ d1, const float* __restrict__ d2, float* __restrict__ grad)
+                 const float* __restrict__ d1, const float* __restrict__ d2, float* __restrict__ grad,
+                 const AdamArgs ad)
 {
     __shared__ float part[kSegs][kGradParams];
     const int seg = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -204,7 +226,10 @@ surr_grad_kernel(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* _
         float g = part[0][lane];
 #pragma unroll
         for (int t = 1; t < kSegs; ++t) g += part[t][lane];
-        grad[i] = g;
+        if (ADAM)
+            adam_update(ad, i, g);
+        else
+            grad[i] = g;
     }
 }
 
@@ -233,12 +258,7 @@ __global__ void surr_adam_kernel(int64_t n, float* __restrict__ theta, const flo
 {
     for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n;
          i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const float g = grad[i];
-        const float mi = fmaf(beta1, m[i], (1.0f - beta1) * g);
-        const float vi = fmaf(beta2, v[i], (1.0f - beta2) * g * g);
-        m[i] = mi;
-        v[i] = vi;
-        theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        adam_update(AdamArgs{ theta, m, v, lr, beta1, beta2, eps, c1, c2 }, i, grad[i]);
     }
 }
 
@@ -262,8 +282,10 @@ cudaError_t launch_surrogate_init(int32_t d_in, int32_t h1, int32_t h2, uint64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta,
-                                     const float* x, float* y, float* a1, float* a2, cudaStream_t stream)
+namespace {
+
+cudaError_t forward_rows(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta, const float* x, float* y,
+                         float* a1, float* a2, const float* t, float* dy, float* d1, float* d2, cudaStream_t stream)
 {
     if (n <= 0) return cudaSuccess;
     // rows per CTA: enough CTAs to spread over the SMs, as many rows as that
@@ -276,20 +298,31 @@ cudaError_t launch_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_
         err = cudaFuncSetAttribute(surr_forward_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(smem));
         if (err == cudaSuccess)
-            surr_forward_kernel<32><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+            surr_forward_kernel<32><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2, t, dy,
+                                                                         d1, d2);
     } else if (rpc == 8) {
         err = cudaFuncSetAttribute(surr_forward_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(smem));
         if (err == cudaSuccess)
-            surr_forward_kernel<8><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+            surr_forward_kernel<8><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2, t, dy,
+                                                                         d1, d2);
     } else {
         err = cudaFuncSetAttribute(surr_forward_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    static_cast<int>(smem));
         if (err == cudaSuccess)
-            surr_forward_kernel<2><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2);
+            surr_forward_kernel<2><<<grid, kFwdThreads, smem, stream>>>(n, d_in, h1, h2, theta, x, y, a1, a2, t, dy,
+                                                                         d1, d2);
     }
     if (err != cudaSuccess) return err;
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_surrogate_forward(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta,
+                                     const float* x, float* y, float* a1, float* a2, cudaStream_t stream)
+{
+    return forward_rows(n, d_in, h1, h2, theta, x, y, a1, a2, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
 cudaError_t launch_surrogate_loss_grad(int32_t n, int32_t d_in, int32_t h1, int32_t h2, const float* theta,
@@ -303,13 +336,34 @@ cudaError_t launch_surrogate_loss_grad(int32_t n, int32_t d_in, int32_t h1, int3
     float* a2 = a1 + static_cast<int64_t>(n) * h1;
     float* d1 = a2 + static_cast<int64_t>(n) * h2;
     float* d2 = d1 + static_cast<int64_t>(n) * h1;
-    cudaError_t err = launch_surrogate_forward(n, d_in, h1, h2, theta, x, yv, a1, a2, stream);
+    cudaError_t err = forward_rows(n, d_in, h1, h2, theta, x, yv, a1, a2, t, dy, d1, d2, stream);
     if (err != cudaSuccess) return err;
     surr_loss_kernel<<<1, 256, 0, stream>>>(n, yv, t, loss);
-    surr_backrow_kernel<<<n, 64, sizeof(float) * h2, stream>>>(n, d_in, h1, h2, theta, yv, t, a1, a2, dy, d1, d2);
     const int64_t total = surrogate_num_params(d_in, h1, h2);
-    surr_grad_kernel<<<static_cast<int>((total + kGradParams - 1) / kGradParams), 32 * kSegs, 0, stream>>>(
-        n, d_in, h1, h2, x, a1, a2, dy, d1, d2, grad);
+    surr_grad_kernel<false><<<static_cast<int>((total + kGradParams - 1) / kGradParams), 32 * kSegs, 0, stream>>>(
+        n, d_in, h1, h2, x, a1, a2, dy, d1, d2, grad, AdamArgs{});
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surrogate_train_step(int32_t n, int32_t d_in, int32_t h1, int32_t h2, float* theta, const float* x,
+                                        const float* t, float* loss, float* work, float* m, float* v, int64_t step,
+                                        float lr, float beta1, float beta2, float eps, cudaStream_t stream)
+{
+    float* yv = work;
+    float* dy = yv + n;
+    float* a1 = dy + n;
+    float* a2 = a1 + static_cast<int64_t>(n) * h1;
+    float* d1 = a2 + static_cast<int64_t>(n) * h2;
+    float* d2 = d1 + static_cast<int64_t>(n) * h1;
+    cudaError_t err = forward_rows(n, d_in, h1, h2, theta, x, yv, a1, a2, t, dy, d1, d2, stream);
+    if (err != cudaSuccess) return err;
+    if (loss) surr_loss_kernel<<<1, 256, 0, stream>>>(n, yv, t, loss);
+    AdamArgs ad{ theta, m, v, lr, beta1, beta2, eps,
+                 static_cast<float>(1.0 - std::pow(static_cast<double>(beta1), static_cast<double>(step))),
+                 static_cast<float>(1.0 - std::pow(static_cast<double>(beta2), static_cast<double>(step))) };
+    const int64_t total = surrogate_num_params(d_in, h1, h2);
+    surr_grad_kernel<true><<<static_cast<int>((total + kGradParams - 1) / kGradParams), 32 * kSegs, 0, stream>>>(
+        n, d_in, h1, h2, x, a1, a2, dy, d1, d2, nullptr, ad);
     return cudaGetLastError();
 }
 
