@@ -132,6 +132,9 @@ def max_over_ranks(value: float, dist, device=None) -> float:
     return float(t.item())
 
 
+PROFILE_EVERY = 8  # generations per profiled one inside the timed region
+
+
 def kernels_per_generation(pop: int, batch: int, precision: int) -> dict:
     """Kernel launches per stage of one state-object generation: ranking and
     selection run as one kernel below 512 nets and as two above; the shadow
@@ -609,6 +612,9 @@ def run_native(args, rank: int, world: int, local_rank: int):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for k in range(steps):
+        # per-kernel CUDA events on every PROFILE_EVERY-th generation only: events
+        # between kernels cost time and stop a kernel from starting early
+        st.leea_profile_enable(k % PROFILE_EVERY == 0)
         gen(st, warmup + 1 + k)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
@@ -703,12 +709,14 @@ def run_native(args, rank: int, world: int, local_rank: int):
             "vs_baseline": None, "dtype": {0: "f32", 1: "bf16 (f32 accumulate)", 2: "fp8-e4m3 (f32 accumulate)"}[
                 precision], "data": "synthetic",
             "config": {"workload": workload, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "kernel_timing": f"CUDA events around each kernel of every {PROFILE_EVERY}th generation "
+                                        "inside the timed region",
                        "input": "uint8 levels k, x = k/255" if u8 else "float32 x",
                        "eval_kernel": eval_kernel,
                        "l2": f"inputs larger than L2 (2 population buffers of {pop_mb:.0f} MB), no flush"},
             "network_samples_per_sec": gen_per_s * pop * batch,
-            "e2e": e2e, "gpu_launches": int(sum(v[1] * kernels_per_generation(pop, batch, precision)[k]
-                                                for k, v in prof.items())), "roofline": roofline,
+            "e2e": e2e, "gpu_launches": int(steps * sum(kernels_per_generation(pop, batch, precision).values())),
+            "roofline": roofline,
             "kernels": kernels, "clocks": clk}
     if precision and rank == 0:
         # the last generation evaluated the last end-to-end batch

@@ -246,6 +246,7 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
              int64_t n_items, const uint32_t* __restrict__ gen_dev, unsigned int* __restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
+    ptx::grid_dep_launch();  // the evaluation that follows may stage its batch meanwhile
     const BreedSmem s = carve(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Items of this CTA: many runs, a contiguous range; one run, every gridDim.x-th

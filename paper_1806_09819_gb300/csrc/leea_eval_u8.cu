@@ -289,6 +289,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
     } else if (warp == 1) {
         // ------------------------------------------------------------ TMA producer (raw FP32 tiles)
         if (lane == 0) {
+            ptx::grid_dep_wait();  // the population comes from the previous kernel (breeding)
             uint32_t stage = 0, phase = 0;
             uint32_t issued_mask = 0, parity_mask = 0;
             uint32_t prm_issued = 0;  // units whose parameters were requested
@@ -562,6 +563,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const EvalU8Args a)
                     v[j + 3] = t4.w;
                 }
                 if (go == 2) {
+                    ptx::grid_dep_wait();
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float* wr = w1p + static_cast<int64_t>(c + j) * a.k;
@@ -744,8 +746,20 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     err = cudaFuncSetAttribute(eval_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     const int grid = pop < sms ? pop : sms;
-    eval_u8_kernel<<<grid, kU8Threads, smem, stream>>>(tw, a);
-    return cudaGetLastError();
+    // Programmatic stream serialisation: CTAs may start (barriers, TMEM, the
+    // batch into TMEM) while the previous kernel finishes; the producer waits
+    // for it before it reads the population.
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kU8Threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, eval_u8_kernel, tw, a);
 }
 
 }  // namespace leea

@@ -70,6 +70,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     }
 }
 
+// ---- programmatic dependent launch ---------------------------------------------------
+// Lets the next kernel on the stream (launched with programmatic stream
+// serialisation) start its independent prologue before this grid ends.
+__device__ __forceinline__ void grid_dep_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+// Waits until the previous grid on the stream has completed and its memory
+// is visible (returns at once when there is no such dependency).
+__device__ __forceinline__ void grid_dep_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ---- TMA -------------------------------------------------------------------------
 __device__ __forceinline__ void tma_prefetch_map(const void* map)
 {
