@@ -347,6 +347,7 @@ eval_shadow_kernel(const __grid_constant__ EvalShArgs a, int32_t h_max)
     } else if (warp == 1) {
         // ------------------------------------------------------------ copy producer
         if (lane == 0) {
+            ptx::grid_dep_wait();  // shadows and masters come from the previous kernel (breeding)
             uint32_t stage = 0, phase = 0, issued_mask = 0, parity_mask = 0, prm_issued = 0;
             bool ok = true;
             for (int32_t si = 0; ok && si < nseg; ++si) {
@@ -645,8 +646,20 @@ cudaError_t launch(const EvalShArgs& a, int32_t precision, int32_t h_max, int32_
     auto kernel = precision == 1 ? eval_shadow_kernel<1> : eval_shadow_kernel<2>;
     cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    kernel<<<grid, kShThreads, smem, stream>>>(a, h_max);
-    err = cudaGetLastError();
+    // Programmatic stream serialisation: CTAs may start (barriers, TMEM, the
+    // batch tile) while the previous kernel finishes; the copy producer waits
+    // for it before it reads shadows and masters.
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kShThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    err = cudaLaunchKernelEx(&cfg, kernel, a, h_max);
     if (err != cudaSuccess || !any_tiles) return err;
     combine_tiles_kernel<<<dim3((pop_max + 255) / 256, n_runs), 256, 0, stream>>>(a);
     return cudaGetLastError();
