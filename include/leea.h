@@ -221,8 +221,11 @@ leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
  * bytes, as MNIST's are).  The tensor-core path needs batch <= 128,
  * d_0 % 4 == 0, h % 16 == 0, h <= 128, h + round_up(8 ceil(d_0 / 16), 16) <= 512
  * and d_out <= 16.  It forms layer 1 from exact products: the levels are exact
- * in BF16 and each weight is split exactly into three BF16 pieces, so only
- * the tensor core's FP32 accumulation rounds.  Otherwise, or with
+ * in FP16 and each weight, scaled by 2^8, is split into two FP16 pieces
+ * (|2^8 w - w1 - w2| <= max(2^-22 2^8 |w|, 2^-25), a 22-bit significand),
+ * so besides that split only the tensor core's FP32 accumulation rounds; an
+ * individual with a weight |w| >= 128 gets its layer 1 in FP32 FFMA
+ * instead.  Otherwise, or with
  * LEEA_EVAL_SIMT, the CUDA-core kernel computes x = k / x_div in FP32.
  * x_div must be finite and > 0. */
 leea_status leea_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims,
@@ -539,7 +542,11 @@ leea_status leea_breed_entities(int32_t n_parents, const int32_t* dims, int32_t 
  * mutation step length sigma ||z (.) m|| over the masked genes (0 otherwise),
  * then the child's logits on the probe inputs probe_dev (float[n_probe][d_0]),
  * sample-major].  entity_dev NULL: entity = recipe index.  Two-layer nets,
- * d_0 % 16 == 0, 16 <= h <= 256 with h % 16 == 0, d_out <= 16, n_probe <= 32. */
+ * d_0 % 16 == 0, 16 <= h <= 256 with h % 16 == 0, d_out <= 16, n_probe <= 32.
+ * p->precision 0: the logits of the FP32 child (CUDA cores); >= 1: of the
+ * child with W1 rounded to BF16 (nearest even) as the precision form holds
+ * it, on the tensor cores, the probe inputs carried as two BF16 pieces
+ * (needs h <= 128; probe_dev 4-byte aligned). */
 leea_status leea_descriptors(int32_t n_parents, const int32_t* dims, int32_t n_dims, const leea_params* p,
                              uint64_t seed, uint32_t gen, const float* parents_dev, const float* f_adj_dev,
                              const int32_t* par1_dev, const int32_t* par2_dev, const int32_t* kind_dev,
