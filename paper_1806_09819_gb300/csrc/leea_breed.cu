@@ -247,6 +247,7 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
 {
     extern __shared__ uint8_t smem_raw[];
     ptx::grid_dep_launch();  // the evaluation that follows may stage its batch meanwhile
+    ptx::grid_dep_wait();    // the selection comes from the previous kernel
     const BreedSmem s = carve(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Items of this CTA: many runs, a contiguous range; one run, every gridDim.x-th
@@ -437,8 +438,8 @@ cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t
     err = cudaFuncSetAttribute(breed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                static_cast<int>(kBreedSmemBytes));
     if (err != cudaSuccess) return err;
-    breed_kernel<false><<<grid, kBreedThreads, kBreedSmemBytes, stream>>>(r, nullptr, 1, items, nullptr, status);
-    return cudaGetLastError();
+    return launch_pdl(breed_kernel<false>, dim3(grid), dim3(kBreedThreads), kBreedSmemBytes, stream, r,
+                      static_cast<const BreedRun*>(nullptr), 1, items, static_cast<const uint32_t*>(nullptr), status);
 }
 
 cudaError_t launch_breed_runs(const BreedRun* runs_dev, int32_t n_runs, int64_t n_items, const uint32_t* gen_dev,

@@ -3,6 +3,7 @@
 // inheritance values) plus the tournament alternative.
 #include "leea_internal.h"
 #include "philox.cuh"
+#include "tc_ptx.cuh"
 
 namespace leea {
 
@@ -33,6 +34,8 @@ __global__ void __launch_bounds__(32 * kRankWarps) rank_kernel(int32_t pop, cons
                                                               int32_t* __restrict__ order)
 {
     __shared__ uint64_t tile[kRankTile];
+    ptx::grid_dep_launch();
+    ptx::grid_dep_wait();  // f_adj comes from the previous kernel
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t i = blockIdx.x * kRankWarps + warp;
     const uint64_t mine = i < pop ? rank_key(f_adj[i], i) : 0ull;
@@ -52,8 +55,8 @@ __global__ void __launch_bounds__(32 * kRankWarps) rank_kernel(int32_t pop, cons
 
 cudaError_t launch_rank(int32_t pop, const float* f_adj, int32_t* order, cudaStream_t stream)
 {
-    rank_kernel<<<(pop + kRankWarps - 1) / kRankWarps, 32 * kRankWarps, 0, stream>>>(pop, f_adj, order);
-    return cudaGetLastError();
+    return launch_pdl(rank_kernel, dim3((pop + kRankWarps - 1) / kRankWarps), dim3(32 * kRankWarps), 0, stream, pop,
+                      f_adj, order);
 }
 
 // Draw n of child j's SEL stream, caching the current Philox block.
@@ -166,6 +169,8 @@ __global__ void __launch_bounds__(256) select_kernel(SelectArgs a, const float* 
                                                      int32_t* __restrict__ par1, int32_t* __restrict__ par2,
                                                      int32_t* __restrict__ kind, float* __restrict__ f_inh)
 {
+    ptx::grid_dep_launch();
+    ptx::grid_dep_wait();  // the ranking comes from the previous kernel
     const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < a.pop) select_child(a, f_adj, order, j, par1, par2, kind, f_inh);
 }
@@ -174,8 +179,8 @@ cudaError_t launch_select(const SelectArgs& a, const float* f_adj, const int32_t
                           int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh,
                           cudaStream_t stream)
 {
-    select_kernel<<<(a.pop + 255) / 256, 256, 0, stream>>>(a, f_adj, order, par1, par2, kind, f_inh);
-    return cudaGetLastError();
+    return launch_pdl(select_kernel, dim3((a.pop + 255) / 256), dim3(256), 0, stream, a, f_adj, order, par1, par2, kind,
+                      f_inh);
 }
 
 // Rank and select in one CTA for populations up to kFusedMaxPop: a bitonic
