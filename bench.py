@@ -85,8 +85,8 @@ STAGES = ("select", "breed", "evaluate")
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 TRAFFIC = {
-    "breed": {"bytes_per_launch": 707.41e6, "src_sha": "71c9e1a9f4e5724a", "capture": "P=1000 plain workload"},
-    "evaluate": {"bytes_per_launch": 359.38e6, "src_sha": "149fda2e1617c56a", "capture": "P=1000 plain workload"},
+    "breed": {"bytes_per_launch": 706.54e6, "src_sha": "53af562611246ce0", "capture": "P=1000 plain workload"},
+    "evaluate": {"bytes_per_launch": 359.37e6, "src_sha": "d972b174f2e01544", "capture": "P=1000 plain workload"},
 }
 
 
