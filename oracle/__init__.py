@@ -25,7 +25,9 @@ _HDR = os.path.join(_HERE, "leea_oracle.h")
 _OUT = os.path.join(_HERE, "_build", "libleea_oracle.so")
 
 TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
+TAG_SIGMA = 7
 ELITE, CROSSOVER, MUTATION = 0, 1, 2
+SIGMA_CONST, SIGMA_DECAY, SIGMA_SELF = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -65,6 +67,9 @@ class Params:
     alpha: float = 1.0      # 1.0 disables inheritance
     init: int = 0           # 0 N(0, 1/fan_in), 1 Glorot-uniform
     precision: int = 0      # 0 FP32, 1 BF16 shadow, 2 FP8 shadow
+    sigma_ctl: int = 0      # SIGMA_CONST, SIGMA_DECAY or SIGMA_SELF (Section 3.2)
+    sigma_k: float = 1.0    # decay: breed i uses sigma * 0.99 ** (i / sigma_k)
+    tau: float = 0.1        # self-adaptive: sigma' = sigma * exp(tau * N(0, 1))
 
 
 class _CParams(ctypes.Structure):
@@ -75,7 +80,8 @@ class _CParams(ctypes.Structure):
         ("p_e", ctypes.c_float), ("p_c", ctypes.c_float),
         ("sigma", ctypes.c_float), ("mut_rate", ctypes.c_float),
         ("alpha", ctypes.c_float), ("init", ctypes.c_int32),
-        ("precision", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("sigma_ctl", ctypes.c_int32),
+        ("sigma_k", ctypes.c_float), ("tau", ctypes.c_float),
     ]
 
 
@@ -127,6 +133,12 @@ def lib() -> ctypes.CDLL:
         L.leea_cpu_select.argtypes = [i32, P(_CParams), vp, vp, u64, u32, vp, vp, vp, vp]
         L.leea_cpu_breed.argtypes = [i32, vp, i32, P(_CParams), u64, u32, vp, vp, vp, vp, i32, i32, vp]
         L.leea_cpu_inherit.argtypes = [i32, dbl, vp, vp, i32, vp]
+        L.leea_cpu_sigma_schedule.argtypes = [P(_CParams), u32]
+        L.leea_cpu_sigma_schedule.restype = dbl
+        L.leea_cpu_select_sigma.argtypes = [i32, P(_CParams), u64, u32, vp, vp, vp, vp, vp]
+        L.leea_cpu_breed_sigma.argtypes = [i32, vp, i32, P(_CParams), u64, u32, vp, vp, vp, vp, vp, i32, i32, vp]
+        L.leea_cpu_get_sigma.argtypes = [vp, vp]
+        L.leea_cpu_set_sigma.argtypes = [vp, vp]
         L.leea_cpu_create.argtypes = [i32, vp, i32, P(_CParams), u64, P(vp)]
         L.leea_cpu_generation.argtypes = [vp, vp, vp, i32]
         L.leea_cpu_fitness.argtypes = [vp, vp, vp, vp]
@@ -338,6 +350,38 @@ def breed(prm: Params, dims, seed: int, gen: int, parents, par1, par2, kind,
     return out
 
 
+def sigma_schedule(prm: Params, gen: int) -> float:
+    """Mutation strength of the breed with generation counter gen (Section 3.2)."""
+    cp = _cparams(prm)
+    return float(lib().leea_cpu_sigma_schedule(ctypes.byref(cp), gen))
+
+
+def select_sigma(prm: Params, seed: int, gen: int, par1, par2, kind, sigma_in) -> np.ndarray:
+    """Self-adaptive control: the children's sigma genes from their parents'."""
+    si = _f64(sigma_in)
+    out = np.empty_like(si)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_select_sigma(si.shape[0], ctypes.byref(cp), seed, gen, _ptr(_i32(par1)),
+                                       _ptr(_i32(par2)), _ptr(_i32(kind)), _ptr(si), _ptr(out)),
+           "select_sigma")
+    return out
+
+
+def breed_sigma(prm: Params, dims, seed: int, gen: int, parents, par1, par2, kind, sigma_child,
+                j0: int = 0, j1: int | None = None) -> np.ndarray:
+    """breed() with mutation strength sigma_child[j] for child j."""
+    d = _dims(dims)
+    pv = _f64(parents)
+    pop = pv.shape[0]
+    j1 = pop if j1 is None else j1
+    out = np.empty((j1 - j0, pv.shape[1]), dtype=np.float64)
+    cp = _cparams(prm)
+    _check(lib().leea_cpu_breed_sigma(pop, _ptr(d), len(d), ctypes.byref(cp), seed, gen, _ptr(pv),
+                                      _ptr(_i32(par1)), _ptr(_i32(par2)), _ptr(_i32(kind)),
+                                      _ptr(_f64(sigma_child)), j0, j1, _ptr(out)), "breed_sigma")
+    return out
+
+
 def inherit(alpha: float, f_inh, f, first: bool) -> np.ndarray:
     fv = _f64(f)
     fi = None if f_inh is None else _f64(f_inh)
@@ -403,6 +447,15 @@ class State:
     @property
     def gen(self) -> int:
         return int(lib().leea_cpu_generation_index(self._h))
+
+    def sigma(self) -> np.ndarray:
+        """Sigma genes (self-adaptive control) or the next breed's strength, per individual."""
+        out = np.empty(self.pop, dtype=np.float64)
+        _check(lib().leea_cpu_get_sigma(self._h, _ptr(out)), "get_sigma")
+        return out
+
+    def set_sigma(self, sigma) -> None:
+        _check(lib().leea_cpu_set_sigma(self._h, _ptr(_f64(sigma))), "set_sigma")
 
     def selection(self):
         """Returns (order, par1, par2, kind, f_inh) of the last breed."""

@@ -166,6 +166,9 @@ static int valid_params(const leea_cpu_params* prm)
     if (!(prm->alpha >= 0.0f && prm->alpha <= 1.0f)) return 0;
     if (prm->init != 0 && prm->init != 1) return 0;
     if (prm->precision < 0 || prm->precision > 2) return 0;
+    if (prm->sigma_ctl < LEEA_CPU_SIGMA_CONST || prm->sigma_ctl > LEEA_CPU_SIGMA_SELF) return 0;
+    if (prm->sigma_ctl == LEEA_CPU_SIGMA_DECAY && !(prm->sigma_k > 0.0f && !isinf(prm->sigma_k))) return 0;
+    if (prm->sigma_ctl == LEEA_CPU_SIGMA_SELF && !(prm->tau >= 0.0f && !isinf(prm->tau))) return 0;
     return 1;
 }
 
@@ -453,12 +456,11 @@ int leea_cpu_select(int32_t pop, const leea_cpu_params* prm, const double* f_adj
 /* ------------------------------------------------------------------------ */
 /* Child out (c genes) of the given kind from parents a, b, drawing from the
  * streams of Philox entity `ent`. */
-static int breed_child(int64_t c, const leea_cpu_params* prm, uint64_t seed, uint32_t gen, uint32_t ent,
-                       int32_t kind, const double* a, const double* b, double* out)
+static int breed_child(int64_t c, const leea_cpu_params* prm, double sigma, uint64_t seed, uint32_t gen,
+                       uint32_t ent, int32_t kind, const double* a, const double* b, double* out)
 {
     uint32_t thr_xo = leea_cpu_threshold16((double)prm->xo_gene_p);
     uint32_t thr_mut = leea_cpu_threshold16((double)prm->mut_rate);
-    double sigma = (double)prm->sigma;
     for (int64_t i = 0; i < c; i++) {
         double v;
         if (kind == LEEA_CPU_ELITE) {
@@ -495,8 +497,69 @@ int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
         return LEEA_CPU_EINVAL;
     for (int32_t j = j0; j < j1; j++) {
         if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
-        int rc = breed_child(c, prm, seed, gen, (uint32_t)j, kind[j], parents + (int64_t)par1[j] * c,
-                             parents + (int64_t)par2[j] * c, children + (int64_t)(j - j0) * c);
+        int rc = breed_child(c, prm, (double)prm->sigma, seed, gen, (uint32_t)j, kind[j],
+                             parents + (int64_t)par1[j] * c, parents + (int64_t)par2[j] * c,
+                             children + (int64_t)(j - j0) * c);
+        if (rc != LEEA_CPU_OK) return rc;
+    }
+    return LEEA_CPU_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Control of the mutation strength (Section 3.2).                          */
+/*   constant:       sigma in every breed                                   */
+/*   decay:          breed i (i = 0 for the first) uses sigma 0.99^(i/k)    */
+/*   self-adaptive:  each individual carries a sigma gene; a mutation child */
+/*                   first mutates its parent's gene, sigma' = sigma        */
+/*                   exp(tau N(0,1)), then its weights with sigma'; a       */
+/*                   crossover child takes the mean of its parents' genes   */
+/* ------------------------------------------------------------------------ */
+double leea_cpu_sigma_schedule(const leea_cpu_params* prm, uint32_t gen)
+{
+    double sigma = (double)prm->sigma;
+    if (prm->sigma_ctl != LEEA_CPU_SIGMA_DECAY) return sigma;
+    double i = gen > 0 ? (double)(gen - 1u) : 0.0;
+    return sigma * pow(0.99, i / (double)prm->sigma_k);
+}
+
+int leea_cpu_select_sigma(int32_t pop, const leea_cpu_params* prm, uint64_t seed, uint32_t gen,
+                          const int32_t* par1, const int32_t* par2, const int32_t* kind,
+                          const double* sigma_in, double* sigma_out)
+{
+    if (pop <= 0 || !valid_params(prm) || !par1 || !par2 || !kind || !sigma_in || !sigma_out)
+        return LEEA_CPU_EINVAL;
+    for (int32_t j = 0; j < pop; j++) {
+        if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
+        double s1 = sigma_in[par1[j]];
+        if (kind[j] == LEEA_CPU_ELITE) {
+            sigma_out[j] = s1;
+        } else if (kind[j] == LEEA_CPU_CROSSOVER) {
+            sigma_out[j] = 0.5 * (s1 + sigma_in[par2[j]]);
+        } else if (kind[j] == LEEA_CPU_MUTATION) {
+            double z = leea_cpu_normal(seed, LEEA_CPU_TAG_SIGMA, gen, (uint32_t)j, 0u);
+            sigma_out[j] = s1 * exp((double)prm->tau * z);
+        } else {
+            return LEEA_CPU_EINVAL;
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_breed_sigma(int32_t pop, const int32_t* dims, int32_t n_dims,
+                         const leea_cpu_params* prm, uint64_t seed, uint32_t gen,
+                         const double* parents, const int32_t* par1, const int32_t* par2,
+                         const int32_t* kind, const double* sigma_child, int32_t j0, int32_t j1,
+                         double* children)
+{
+    int64_t c = leea_cpu_num_params(dims, n_dims);
+    if (c < 0 || pop <= 0 || !valid_params(prm) || !parents || !par1 || !par2 || !kind ||
+        !sigma_child || !children || j0 < 0 || j1 > pop || j0 > j1)
+        return LEEA_CPU_EINVAL;
+    for (int32_t j = j0; j < j1; j++) {
+        if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
+        int rc = breed_child(c, prm, sigma_child[j], seed, gen, (uint32_t)j, kind[j],
+                             parents + (int64_t)par1[j] * c, parents + (int64_t)par2[j] * c,
+                             children + (int64_t)(j - j0) * c);
         if (rc != LEEA_CPU_OK) return rc;
     }
     return LEEA_CPU_OK;
@@ -528,6 +591,7 @@ struct leea_cpu_state {
     int32_t evaluated;
     double *cur, *next;
     double *f_adj, *f_raw, *f_inh;
+    double *sig_cur, *sig_next;  /* sigma genes (self-adaptive) or the breed's strength */
     int32_t *correct, *order, *par1, *par2, *kind;
 };
 
@@ -536,6 +600,7 @@ void leea_cpu_destroy(leea_cpu_state* s)
     if (!s) return;
     free(s->cur); free(s->next);
     free(s->f_adj); free(s->f_raw); free(s->f_inh);
+    free(s->sig_cur); free(s->sig_next);
     free(s->correct); free(s->order); free(s->par1); free(s->par2); free(s->kind);
     free(s);
 }
@@ -562,11 +627,14 @@ int leea_cpu_create(int32_t pop, const int32_t* dims, int32_t n_dims,
     s->par1 = (int32_t*)calloc(np, sizeof(int32_t));
     s->par2 = (int32_t*)calloc(np, sizeof(int32_t));
     s->kind = (int32_t*)calloc(np, sizeof(int32_t));
+    s->sig_cur = (double*)calloc(np, sizeof(double));
+    s->sig_next = (double*)calloc(np, sizeof(double));
     if (!s->cur || !s->next || !s->f_adj || !s->f_raw || !s->f_inh || !s->correct ||
-        !s->order || !s->par1 || !s->par2 || !s->kind) {
+        !s->order || !s->par1 || !s->par2 || !s->kind || !s->sig_cur || !s->sig_next) {
         leea_cpu_destroy(s);
         return LEEA_CPU_ENOMEM;
     }
+    for (size_t p = 0; p < np; p++) s->sig_cur[p] = (double)prm->sigma;  /* initial sigma genes */
     leea_cpu_init(pop, dims, n_dims, prm->init, seed, s->cur);
     *out = s;
     return LEEA_CPU_OK;
@@ -584,10 +652,19 @@ int leea_cpu_generation(leea_cpu_state* s, const double* x, const int32_t* y, in
         rc = leea_cpu_select(s->pop, &s->prm, s->f_adj, s->order, s->seed, g,
                              s->par1, s->par2, s->kind, s->f_inh);
         if (rc) return rc;
-        rc = leea_cpu_breed(s->pop, s->dims, s->n_dims, &s->prm, s->seed, g, s->cur,
-                            s->par1, s->par2, s->kind, 0, s->pop, s->next);
+        if (s->prm.sigma_ctl == LEEA_CPU_SIGMA_SELF) {
+            rc = leea_cpu_select_sigma(s->pop, &s->prm, s->seed, g, s->par1, s->par2, s->kind,
+                                       s->sig_cur, s->sig_next);
+            if (rc) return rc;
+        } else {
+            double sigma = leea_cpu_sigma_schedule(&s->prm, g);
+            for (int32_t j = 0; j < s->pop; j++) s->sig_next[j] = sigma;
+        }
+        rc = leea_cpu_breed_sigma(s->pop, s->dims, s->n_dims, &s->prm, s->seed, g, s->cur,
+                                  s->par1, s->par2, s->kind, s->sig_next, 0, s->pop, s->next);
         if (rc) return rc;
         double* t = s->cur; s->cur = s->next; s->next = t;
+        t = s->sig_cur; s->sig_cur = s->sig_next; s->sig_next = t;
         s->gen = g;
     }
     rc = leea_cpu_evaluate(s->pop, s->dims, s->n_dims, s->cur, x, y, batch,
@@ -666,6 +743,23 @@ int leea_cpu_get_selection(const leea_cpu_state* s, int32_t* order, int32_t* par
 uint32_t leea_cpu_generation_index(const leea_cpu_state* s)
 {
     return s ? s->gen : 0;
+}
+
+int leea_cpu_get_sigma(const leea_cpu_state* s, double* out)
+{
+    if (!s || !out) return LEEA_CPU_EINVAL;
+    for (int32_t p = 0; p < s->pop; p++)
+        out[p] = s->prm.sigma_ctl == LEEA_CPU_SIGMA_SELF ? s->sig_cur[p]
+                                                         : leea_cpu_sigma_schedule(&s->prm, s->gen + 1u);
+    return LEEA_CPU_OK;
+}
+
+int leea_cpu_set_sigma(leea_cpu_state* s, const double* in)
+{
+    if (!s || !in) return LEEA_CPU_EINVAL;
+    if (s->prm.sigma_ctl != LEEA_CPU_SIGMA_SELF) return LEEA_CPU_ESTATE;
+    memcpy(s->sig_cur, in, sizeof(double) * (size_t)s->pop);
+    return LEEA_CPU_OK;
 }
 
 /* ======================================================================== */
@@ -868,7 +962,7 @@ int leea_cpu_breed_entities(int32_t pop, const int32_t* dims, int32_t n_dims, co
         return LEEA_CPU_EINVAL;
     for (int32_t j = 0; j < n; j++) {
         if (par1[j] < 0 || par1[j] >= pop || par2[j] < 0 || par2[j] >= pop) return LEEA_CPU_EINVAL;
-        int rc = breed_child(c, prm, seed, gen, entity[j], kind[j], parents + (int64_t)par1[j] * c,
+        int rc = breed_child(c, prm, (double)prm->sigma, seed, gen, entity[j], kind[j], parents + (int64_t)par1[j] * c,
                              parents + (int64_t)par2[j] * c, children + (int64_t)j * c);
         if (rc != LEEA_CPU_OK) return rc;
     }
@@ -949,7 +1043,7 @@ int leea_cpu_descriptors(int32_t pop, const int32_t* dims, int32_t n_dims, const
         row[2] = f_inh[j];
         rc = leea_cpu_recipe_stats(dims, n_dims, prm, seed, gen, kind + j, entity + j, 1, row + 3, row + 4);
         if (rc == LEEA_CPU_OK)
-            rc = breed_child(c, prm, seed, gen, entity[j], kind[j], parents + (int64_t)par1[j] * c,
+            rc = breed_child(c, prm, (double)prm->sigma, seed, gen, entity[j], kind[j], parents + (int64_t)par1[j] * c,
                              parents + (int64_t)par2[j] * c, child);
         /* precision >= 1: the child's W1 as the precision form holds it, the
          * FP32 gene rounded to BF16 (nearest even) */

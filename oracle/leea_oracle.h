@@ -45,8 +45,12 @@ enum {
     LEEA_CPU_TAG_XO = 3,      /* entity = child, n = gene                   */
     LEEA_CPU_TAG_MUTMASK = 4, /* entity = child, n = gene                   */
     LEEA_CPU_TAG_NORMAL = 5,  /* entity = child, n = gene                   */
-    LEEA_CPU_TAG_SURR_INIT = 6 /* surrogate weights: entity 0, n = parameter */
+    LEEA_CPU_TAG_SURR_INIT = 6, /* surrogate weights: entity 0, n = parameter */
+    LEEA_CPU_TAG_SIGMA = 7      /* self-adaptive sigma: entity = child, n = 0 */
 };
+
+/* Control of the mutation strength (Section 3.2). */
+enum { LEEA_CPU_SIGMA_CONST = 0, LEEA_CPU_SIGMA_DECAY = 1, LEEA_CPU_SIGMA_SELF = 2 };
 
 /* Philox entity of recipe r of the surrogate form: LEEA_CPU_RECIPE_ENTITY0 + r. */
 #define LEEA_CPU_RECIPE_ENTITY0 0x40000000u
@@ -70,6 +74,9 @@ typedef struct {
     float alpha;       /* inheritance weight on the fresh evaluation           */
     int32_t init;      /* 0 N(0, 1/fan_in), 1 Glorot-uniform (Section 4.1)     */
     int32_t precision; /* 0 FP32, 1 BF16 shadow, 2 FP8-e4m3 shadow             */
+    int32_t sigma_ctl; /* LEEA_CPU_SIGMA_*: constant, decay, self-adaptive     */
+    float sigma_k;     /* decay: sigma_i = sigma 0.99^(i / sigma_k)            */
+    float tau;         /* self-adaptive: sigma' = sigma exp(tau N(0,1))        */
 } leea_cpu_params;
 
 /* ---- random number streams ------------------------------------------- */
@@ -104,6 +111,27 @@ int leea_cpu_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                    const int32_t* kind, int32_t j0, int32_t j1, double* children);
 int leea_cpu_inherit(int32_t pop, double alpha, const double* f_inh, const double* f,
                      int32_t first, double* f_adj);
+
+/* ---- control of the mutation strength (Section 3.2) ---------------------- */
+/* Mutation strength of the breed with generation counter gen (>= 1), which is
+ * breed number i = gen - 1: constant sigma, or sigma 0.99^(i / sigma_k) under
+ * decay.  (Self-adaptive control has no schedule; this returns sigma, the
+ * initial value of every sigma gene.) */
+double leea_cpu_sigma_schedule(const leea_cpu_params* prm, uint32_t gen);
+/* Self-adaptive control: the sigma gene of each child from its parents'.
+ * Elite: a copy; crossover: the arithmetic mean of the parents' genes;
+ * mutation: sigma_parent exp(tau z) with z the normal of draw 0 of the SIGMA
+ * stream of (gen, child). */
+int leea_cpu_select_sigma(int32_t pop, const leea_cpu_params* prm, uint64_t seed, uint32_t gen,
+                          const int32_t* par1, const int32_t* par2, const int32_t* kind,
+                          const double* sigma_in, double* sigma_out);
+/* leea_cpu_breed with mutation strength sigma_child[j] for child j
+ * (j0 <= j < j1; the array is indexed by the absolute child index). */
+int leea_cpu_breed_sigma(int32_t pop, const int32_t* dims, int32_t n_dims,
+                         const leea_cpu_params* prm, uint64_t seed, uint32_t gen,
+                         const double* parents, const int32_t* par1, const int32_t* par2,
+                         const int32_t* kind, const double* sigma_child, int32_t j0, int32_t j1,
+                         double* children);
 
 /* ---- precision form: reduced-precision shadows of W1 ---------------------- */
 /* Round to nearest even into BF16 (8 significant bits, FP32's exponent range). */
@@ -174,6 +202,11 @@ int leea_cpu_set_generation(leea_cpu_state* s, uint32_t gen, int32_t evaluated);
 int leea_cpu_get_selection(const leea_cpu_state* s, int32_t* order, int32_t* par1,
                            int32_t* par2, int32_t* kind, double* f_inh);
 uint32_t leea_cpu_generation_index(const leea_cpu_state* s);
+/* Sigma of each individual of the current population: its sigma gene under
+ * self-adaptive control, else the strength the next breed uses. */
+int leea_cpu_get_sigma(const leea_cpu_state* s, double* out);
+/* Replaces the sigma genes (self-adaptive control only, else ESTATE). */
+int leea_cpu_set_sigma(leea_cpu_state* s, const double* in);
 void leea_cpu_destroy(leea_cpu_state* s);
 
 #ifdef __cplusplus
