@@ -75,7 +75,8 @@ enum {
     LEEA_TAG_SEL = 2,      /* entity = child, n = selection draw            */
     LEEA_TAG_XO = 3,       /* entity = child, n = gene index                */
     LEEA_TAG_MUTMASK = 4,  /* entity = child, n = gene index                */
-    LEEA_TAG_NORMAL = 5    /* entity = child, n = gene index                */
+    LEEA_TAG_NORMAL = 5,   /* entity = child, n = gene index                */
+    LEEA_TAG_SIGMA = 7     /* entity = child, n = 0: self-adaptive sigma    */
 };
 
 /* How child j of the next generation is made (Algorithm 1). */
@@ -98,7 +99,26 @@ typedef struct {
     int32_t init;       /* 0 N(0, 1/fan_in), 1 Glorot-uniform (Section 4.1)   */
     int32_t precision;  /* 0 FP32; 1 BF16 / 2 FP8-e4m3 shadow of W1, see below */
     int32_t eval_path;  /* LEEA_EVAL_AUTO / _SIMT / _TENSOR, see below        */
+    int32_t sigma_ctl;  /* LEEA_SIGMA_CONST / _DECAY / _SELF, see below        */
+    float sigma_k;      /* decay rate k (> 0) of LEEA_SIGMA_DECAY; 1          */
+    float tau;          /* learning rate tau (>= 0) of LEEA_SIGMA_SELF; 0.1   */
 } leea_params;
+
+/* Control of the mutation strength (Section 3.2).
+ *  - CONST: every breed mutates with sigma.
+ *  - DECAY: breed number i (i = 0 for the first breed, generation counter
+ *    g = i + 1) mutates with sigma 0.99^(i / sigma_k), computed in double on
+ *    the host and rounded to FP32.
+ *  - SELF: every individual carries a sigma gene, initially sigma.  A mutation
+ *    child j first mutates its parent's gene, sigma_j = sigma_parent
+ *    exp(tau z) with z the Box-Muller normal of draw 0 of the SIGMA stream of
+ *    (g, j), then its weights with sigma_j; a crossover child takes the
+ *    arithmetic mean of its parents' genes, an elite copies its own.  The
+ *    genes are FP32 (expf on the device).
+ * DECAY and SELF are properties of a run: the state object (leea_create)
+ * applies them; the step entry points leea_select / leea_breed, the batching
+ * form and the surrogate form take CONST only (LEEA_EINVAL otherwise). */
+enum { LEEA_SIGMA_CONST = 0, LEEA_SIGMA_DECAY = 1, LEEA_SIGMA_SELF = 2 };
 
 /* Evaluation kernels.  AUTO takes the tensor-core kernel when the shape
  * allows it (d_0 % 4 == 0, h % 16 == 0, h <= 256, d_out <= 16, 16-byte aligned
@@ -182,7 +202,8 @@ leea_status leea_rank(int32_t pop, const float* f_adj_dev, int32_t* order_dev,
  * f3 after mutation, the elite's own f_adj for an elite.
  * Inputs f_adj_dev float[pop], order_dev int32[pop]; outputs par1_dev,
  * par2_dev, kind_dev int32[pop] and f_inh_dev float[pop].  p->precision must
- * be 0 here: the precision form's scale exponents come from the state object. */
+ * be 0 and p->sigma_ctl LEEA_SIGMA_CONST here: the precision form's scale
+ * exponents and the sigma genes come from the state object. */
 leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_dev,
                         const int32_t* order_dev, uint64_t seed, uint32_t gen,
                         int32_t* par1_dev, int32_t* par2_dev, int32_t* kind_dev,
@@ -194,8 +215,10 @@ leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_de
  * arithmetic crossover -> (a + b) / 2; mutation -> a + sigma z_i on genes whose
  * MUTMASK draw16 i < floor(mut_rate 2^16) (all genes when mut_rate = 1), with
  * z_i the Box-Muller normal of the NORMAL stream.  parents_dev and children_dev
- * are float[pop][c_pad] and must not overlap.  p->precision must be 0 here:
- * shadows of a bred population come from the state object or leea_make_shadow. */
+ * are float[pop][c_pad] and must not overlap.  p->precision must be 0 here
+ * (shadows of a bred population come from the state object or
+ * leea_make_shadow), and p->sigma_ctl LEEA_SIGMA_CONST (a decaying strength is
+ * passed as p->sigma of each call). */
 leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                        const leea_params* p, uint64_t seed, uint32_t gen,
                        const float* parents_dev, const int32_t* par1_dev,
@@ -389,6 +412,15 @@ leea_status leea_get_shadow(leea_state* s, uint8_t* shadow_host, int32_t* scale_
 
 /* Generation counter g (0 before the first breed). */
 uint32_t leea_generation_index(const leea_state* s);
+
+/* Mutation strength of each individual of the current population
+ * (float[pop]): its sigma gene under LEEA_SIGMA_SELF, otherwise the strength
+ * the next breed uses.  Synchronises. */
+leea_status leea_get_sigma(leea_state* s, float* sigma_host);
+
+/* Replaces the sigma genes (float[pop], each finite and >= 0); LEEA_ESTATE
+ * unless the object runs LEEA_SIGMA_SELF. */
+leea_status leea_set_sigma(leea_state* s, const float* sigma_host);
 
 /* c of the object's nets, or -1 for NULL. */
 int64_t leea_state_num_params(const leea_state* s);

@@ -19,6 +19,8 @@ bool make_layout(const int32_t* dims, int32_t n_dims, int32_t init, NetLayout* n
 // floor(q 2^16), 2^16 when q >= 1: the 16-bit draw threshold of probability q.
 uint32_t threshold16(double q);
 leea_status check_params(const leea_params* p);
+// LEEA_EINVAL unless p->sigma_ctl is LEEA_SIGMA_CONST (calls outside the state object).
+leea_status require_const_sigma(const leea_params* p, const char* what);
 leea_status check_pop(int32_t pop);
 // Elites, crossover and mutation children and the truncation pool (Algorithm 1).
 void counts_of(int32_t pop, const leea_params* p, int32_t* ne, int32_t* nc, int32_t* nm, int32_t* pool);

@@ -51,7 +51,8 @@ struct StageMeta {
     int32_t len;     // genes in the chunk (multiple of 32)
     int32_t sexp;    // precision form, FP8: exponent of the child's scale
     int32_t run;     // many runs: index of the child's run
-    int32_t pad[2];
+    float sigma;     // the child's mutation strength
+    int32_t pad;
 };
 
 constexpr int kJobSlots = 4 * 32;  // Box-Muller pairs of a warp's 32 units
@@ -183,8 +184,8 @@ __device__ __forceinline__ float4 select4(uint32_t m, float4 a, float4 b)
 // hold a masked gene, slot by slot (one ballot each), in its shared-memory job
 // list; consecutive lanes compute the listed normals and every lane reads its
 // own back.  Each normal depends only on its (unit, slot) counter.
-__device__ __forceinline__ void mutate_unit(const BreedArgs& a, uint32_t gen, const PhiloxKeys& key, uint32_t j,
-                                            uint32_t u, bool live, float4 (&v)[2], int lane, float2* job_z,
+__device__ __forceinline__ void mutate_unit(const BreedArgs& a, float sigma, uint32_t gen, const PhiloxKeys& key,
+                                            uint32_t j, uint32_t u, bool live, float4 (&v)[2], int lane, float2* job_z,
                                             uint8_t* job_code)
 {
     constexpr int kSlots = 4;
@@ -214,14 +215,14 @@ __device__ __forceinline__ void mutate_unit(const BreedArgs& a, uint32_t gen, co
 #pragma unroll
     for (int sl = 0; sl < kSlots; ++sl)
         z[sl] = ((hit >> (2 * sl)) & 3u) ? job_z[idx[sl]] : make_float2(0.f, 0.f);
-    if (hit & 0x01u) v[0].x = fmaf(a.sigma, z[0].x, v[0].x);
-    if (hit & 0x02u) v[0].y = fmaf(a.sigma, z[0].y, v[0].y);
-    if (hit & 0x04u) v[0].z = fmaf(a.sigma, z[1].x, v[0].z);
-    if (hit & 0x08u) v[0].w = fmaf(a.sigma, z[1].y, v[0].w);
-    if (hit & 0x10u) v[1].x = fmaf(a.sigma, z[2].x, v[1].x);
-    if (hit & 0x20u) v[1].y = fmaf(a.sigma, z[2].y, v[1].y);
-    if (hit & 0x40u) v[1].z = fmaf(a.sigma, z[3].x, v[1].z);
-    if (hit & 0x80u) v[1].w = fmaf(a.sigma, z[3].y, v[1].w);
+    if (hit & 0x01u) v[0].x = fmaf(sigma, z[0].x, v[0].x);
+    if (hit & 0x02u) v[0].y = fmaf(sigma, z[0].y, v[0].y);
+    if (hit & 0x04u) v[0].z = fmaf(sigma, z[1].x, v[0].z);
+    if (hit & 0x08u) v[0].w = fmaf(sigma, z[1].y, v[0].w);
+    if (hit & 0x10u) v[1].x = fmaf(sigma, z[2].x, v[1].x);
+    if (hit & 0x20u) v[1].y = fmaf(sigma, z[2].y, v[1].y);
+    if (hit & 0x40u) v[1].z = fmaf(sigma, z[3].x, v[1].z);
+    if (hit & 0x80u) v[1].w = fmaf(sigma, z[3].y, v[1].w);
     __syncwarp();  // the list is reused by the next unit
 }
 
@@ -271,6 +272,7 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
             uint32_t stage = 0, phase = 0;
             uint32_t issued_mask = 0, parity_mask = 0;  // per stage: issued at all / parity of the last issue
             int32_t cur_j = -1, cur_run = -1, cur_kind = 0, cur_p1 = 0, cur_p2 = 0, cur_sexp = 0;
+            float cur_sigma = 0.0f;
             bool ok = true;
             for (int64_t it = it_begin; it < it_end; it += it_step) {
                 if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
@@ -292,12 +294,13 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
                     cur_p1 = R.par1[j];
                     cur_p2 = R.par2[j];
                     cur_sexp = (a.precision == 2) ? a.scale_exp[j] : 0;
+                    cur_sigma = a.sigma_child ? a.sigma_child[j] : a.sigma;
                     const int32_t n_par = a.n_parents > 0 ? a.n_parents : a.pop;
                     if (cur_p1 < 0 || cur_p1 >= n_par || cur_p2 < 0 || cur_p2 >= n_par) cur_kind = kKindInvalid;
                 }
                 const int64_t g0 = static_cast<int64_t>(ck) * kChunk;
                 const int32_t len = static_cast<int32_t>(a.c_pad - g0 < kChunk ? a.c_pad - g0 : kChunk);
-                s.meta[stage] = StageMeta{ j, cur_kind, static_cast<int32_t>(g0), len, cur_sexp, ri, { 0, 0 } };
+                s.meta[stage] = StageMeta{ j, cur_kind, static_cast<int32_t>(g0), len, cur_sexp, ri, cur_sigma, 0 };
                 const uint32_t bytes = static_cast<uint32_t>(len) * 4u;
                 if (cur_kind == kKindInvalid) {
                     ptx::mbar_arrive(&s.full[stage]);
@@ -358,7 +361,8 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
             }
             if (m.kind == 2) {
                 const int cw = warp - 1;  // consumer warp
-                mutate_unit(a, gen, key, j, u, live, v, lane, s.job_z + cw * kJobSlots, s.job_code + cw * kJobSlots);
+                mutate_unit(a, m.sigma, gen, key, j, u, live, v, lane, s.job_z + cw * kJobSlots,
+                            s.job_code + cw * kJobSlots);
             } else if (live && m.kind == 1) {
                 const float4 b0 = B[2 * ct], b1 = B[2 * ct + 1];
                 if (a.xo_op == 0) {

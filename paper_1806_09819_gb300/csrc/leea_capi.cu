@@ -88,6 +88,19 @@ leea_status check_params(const leea_params* p)
     if (p->precision < 0 || p->precision > 2) return fail(LEEA_EINVAL, "precision must be 0, 1 or 2");
     if (p->eval_path < LEEA_EVAL_AUTO || p->eval_path > LEEA_EVAL_TENSOR)
         return fail(LEEA_EINVAL, "eval_path must be LEEA_EVAL_AUTO, _SIMT or _TENSOR");
+    if (p->sigma_ctl < LEEA_SIGMA_CONST || p->sigma_ctl > LEEA_SIGMA_SELF)
+        return fail(LEEA_EINVAL, "sigma_ctl must be LEEA_SIGMA_CONST, _DECAY or _SELF");
+    if (p->sigma_ctl == LEEA_SIGMA_DECAY && !(p->sigma_k > 0.0f && !std::isinf(p->sigma_k)))
+        return fail(LEEA_EINVAL, "sigma_k must be finite and > 0");
+    if (p->sigma_ctl == LEEA_SIGMA_SELF && !(p->tau >= 0.0f && !std::isinf(p->tau)))
+        return fail(LEEA_EINVAL, "tau must be finite and >= 0");
+    return LEEA_OK;
+}
+
+leea_status require_const_sigma(const leea_params* p, const char* what)
+{
+    if (p->sigma_ctl != LEEA_SIGMA_CONST)
+        return fail(LEEA_EINVAL, "%s takes sigma_ctl LEEA_SIGMA_CONST; sigma control runs in the state object", what);
     return LEEA_OK;
 }
 
@@ -331,6 +344,9 @@ leea_status leea_default_params(leea_params* out)
     out->init = 0;
     out->precision = 0;
     out->eval_path = LEEA_EVAL_AUTO;
+    out->sigma_ctl = LEEA_SIGMA_CONST;
+    out->sigma_k = 1.0f;
+    out->tau = 0.1f;
     return LEEA_OK;
 }
 
@@ -394,6 +410,7 @@ leea_status leea_select(int32_t pop, const leea_params* p, const float* f_adj_de
     if (st) return st;
     if ((st = check_params(p))) return st;
     if (p->precision != 0) return fail(LEEA_EINVAL, "leea_select takes precision 0; use the state object");
+    if ((st = require_const_sigma(p, "leea_select"))) return st;
     if (!f_adj_dev || !order_dev || !par1_dev || !par2_dev || !kind_dev || !f_inh_dev)
         return fail(LEEA_EINVAL, "NULL device pointer");
     const SelectArgs a = select_args(pop, p, seed, gen);
@@ -413,6 +430,7 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims, const l
     if ((st = check_params(p))) return st;
     if (p->precision != 0)
         return fail(LEEA_EINVAL, "leea_breed takes precision 0; use the state object or leea_make_shadow");
+    if ((st = require_const_sigma(p, "leea_breed"))) return st;
     NetLayout net;
     if (!make_layout(dims, n_dims, p->init, &net)) return fail(LEEA_EINVAL, "invalid dims");
     if (!parents_dev || !par1_dev || !par2_dev || !kind_dev || !children_dev)
@@ -629,6 +647,8 @@ struct leea_state {
     int64_t sh_stride;
     float* scratch;      // per-tile partial sums for batch > 128
     size_t scratch_bytes;
+    // self-adaptive mutation strength (prm.sigma_ctl == LEEA_SIGMA_SELF)
+    float* sigma[2];     // sigma genes, paired with popbuf[0] / popbuf[1]
 };
 
 namespace {
@@ -654,6 +674,8 @@ void free_state(leea_state* s)
     cudaFree(s->amax[1]);
     cudaFree(s->scale_exp);
     cudaFree(s->scratch);
+    cudaFree(s->sigma[0]);
+    cudaFree(s->sigma[1]);
     if (s->prof) {
         if (s->prof->created)
             for (int st = 0; st < LEEA_NUM_STAGES; ++st)
@@ -707,6 +729,15 @@ cudaError_t refresh_shadow(leea_state* s)
     return launch_make_shadow(s->pop, s->net.dims[0], s->net.dims[1], s->net.c_pad, s->popbuf[s->cur],
                               s->prm.precision, s->shadow[s->cur], s->sh_stride, s->scale_exp, s->amax[s->cur],
                               s->stream);
+}
+
+// Mutation strength of the breed with generation counter g >= 1, breed number
+// i = g - 1 (Section 3.2): sigma, or sigma 0.99^(i / k) under decay.
+float sigma_of_breed(const leea_params& p, uint32_t g)
+{
+    if (p.sigma_ctl != LEEA_SIGMA_DECAY) return p.sigma;
+    const double i = g > 0 ? static_cast<double>(g - 1u) : 0.0;
+    return static_cast<float>(static_cast<double>(p.sigma) * std::pow(0.99, i / static_cast<double>(p.sigma_k)));
 }
 
 leea_status check_state(leea_state* s)
@@ -766,6 +797,14 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         for (int b = 0; b < 2 && err == cudaSuccess; ++b)  // zero padding of the tiled layout
             err = cudaMemsetAsync(s->shadow[b], 0, np * s->sh_stride, s->stream);
     }
+    if (p->sigma_ctl == LEEA_SIGMA_SELF) {
+        for (int b = 0; b < 2 && err == cudaSuccess; ++b) err = cudaMalloc(&s->sigma[b], sizeof(float) * np);
+        if (err == cudaSuccess) {  // every individual starts with the sigma gene p->sigma
+            std::vector<float> init(np, p->sigma);
+            err = cudaMemcpyAsync(s->sigma[0], init.data(), sizeof(float) * np, cudaMemcpyHostToDevice, s->stream);
+            if (err == cudaSuccess) err = cudaStreamSynchronize(s->stream);
+        }
+    }
     if (err != cudaSuccess) {
         free_state(s);
         return cuda_fail(err, "leea_create allocation");
@@ -808,12 +847,19 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
     const bool first = !s->evaluated;
     if (!first) {
         const uint32_t g = s->gen + 1;
+        const float sigma_g = sigma_of_breed(s->prm, g);
+        const bool self = s->prm.sigma_ctl == LEEA_SIGMA_SELF;
         {
             StageScope sc(s, 0);
             SelectArgs a = select_args(s->pop, &s->prm, s->seed, g);
+            a.sigma = sigma_g;
+            if (self) {
+                a.tau = s->prm.tau;
+                a.sigma_in = s->sigma[s->cur];
+                a.sigma_out = s->sigma[s->cur ^ 1];
+            }
             if (prec != 0) {
                 a.precision = prec;
-                a.sigma = s->prm.sigma;
                 a.amax_in = s->amax[s->cur];
                 a.scale_exp_out = s->scale_exp;
                 a.amax_out = s->amax[s->cur ^ 1];
@@ -825,6 +871,8 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         {
             StageScope sc(s, 1);
             BreedArgs a = breed_args(s->pop, s->net, &s->prm, s->seed, g);
+            a.sigma = sigma_g;
+            if (self) a.sigma_child = s->sigma[s->cur ^ 1];
             if (prec != 0) {
                 a.precision = prec;
                 a.n_w1 = static_cast<int64_t>(s->net.dims[0]) * s->net.dims[1];
@@ -1062,6 +1110,39 @@ leea_status leea_get_selection(leea_state* s, int32_t* order, int32_t* par1, int
 }
 
 uint32_t leea_generation_index(const leea_state* s) { return s ? s->gen : 0u; }
+
+leea_status leea_get_sigma(leea_state* s, float* sigma_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!sigma_host) return fail(LEEA_EINVAL, "sigma_host is NULL");
+    const size_t np = static_cast<size_t>(s->pop);
+    if (s->prm.sigma_ctl == LEEA_SIGMA_SELF) {
+        LEEA_CUDA_TRY(cudaMemcpyAsync(sigma_host, s->sigma[s->cur], sizeof(float) * np, cudaMemcpyDeviceToHost,
+                                      s->stream),
+                      "sigma copy");
+        return check_device_status(s->stream, nullptr);
+    }
+    const float next = sigma_of_breed(s->prm, s->gen + 1u);
+    for (size_t p = 0; p < np; ++p) sigma_host[p] = next;
+    return LEEA_OK;
+}
+
+leea_status leea_set_sigma(leea_state* s, const float* sigma_host)
+{
+    leea_status st = check_state(s);
+    if (st) return st;
+    if (!sigma_host) return fail(LEEA_EINVAL, "sigma_host is NULL");
+    if (s->prm.sigma_ctl != LEEA_SIGMA_SELF) return fail(LEEA_ESTATE, "sigma genes exist under LEEA_SIGMA_SELF only");
+    for (int32_t p = 0; p < s->pop; ++p)
+        if (!(sigma_host[p] >= 0.0f) || std::isinf(sigma_host[p]))
+            return fail(LEEA_EINVAL, "sigma gene %d must be finite and >= 0", p);
+    LEEA_CUDA_TRY(cudaMemcpyAsync(s->sigma[s->cur], sigma_host, sizeof(float) * static_cast<size_t>(s->pop),
+                                  cudaMemcpyHostToDevice, s->stream),
+                  "sigma copy");
+    LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "sigma copy");
+    return LEEA_OK;
+}
 
 int64_t leea_state_num_params(const leea_state* s) { return s ? s->net.c : -1; }
 

@@ -61,6 +61,10 @@ struct SelectArgs {
     const float* amax_in;     // exact max |W1| of each parent
     int32_t* scale_exp_out;   // FP8: exponent of each child's power-of-two scale
     float* amax_out;          // zeroed here; breed accumulates each child's max |W1|
+    // self-adaptive mutation strength (NULL sigma_out: sigma above for every child)
+    float tau;
+    const float* sigma_in;    // parents' sigma genes
+    float* sigma_out;         // children's sigma genes
 };
 
 struct BreedArgs {
@@ -83,6 +87,8 @@ struct BreedArgs {
     // (NULL: entity j); parents are indices below n_parents (0: pop)
     const uint32_t* entity;
     int32_t n_parents;
+    // self-adaptive mutation strength: child j mutates with sigma_child[j] (NULL: sigma)
+    const float* sigma_child;
 };
 
 // Tiled shadow layout.  An individual's W1 shadow is a sequence of blocks, one

@@ -373,6 +373,7 @@ leea_status leea_multi_create(int32_t n_runs, const leea_run_spec* specs, int32_
     if (st) return st;
     if (p->precision != 1 && p->precision != 2)
         return fail(LEEA_EINVAL, "the batching form evaluates through BF16 or FP8 shadows: precision 1 or 2");
+    if ((st = require_const_sigma(p, "the batching form"))) return st;
     leea_multi* m = new (std::nothrow) leea_multi();
     if (!m) return fail(LEEA_ENOMEM, "host allocation failed");
     m->n_runs = n_runs;

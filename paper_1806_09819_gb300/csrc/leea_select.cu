@@ -8,6 +8,7 @@
 namespace leea {
 
 constexpr uint32_t kTagSel = 2;
+constexpr uint32_t kTagSigma = 7;
 constexpr int32_t kKindElite = 0, kKindCross = 1, kKindMut = 2;
 
 // A 64-bit key whose ascending order is: fitness descending (NaN as -inf,
@@ -116,6 +117,21 @@ __device__ __forceinline__ void select_child(const SelectArgs& a, const float* f
     par1[j] = p1;
     par2[j] = p2;
     f_inh[j] = fi;
+    // Mutation strength of the child (Section 3.2): constant or scheduled, or
+    // under self-adaptation its sigma gene -- the elite's own, the mean of the
+    // crossover parents', or the mutation parent's times exp(tau z), z from
+    // draw 0 of the child's SIGMA stream.
+    float sigma = a.sigma;
+    if (a.sigma_out) {
+        sigma = a.sigma_in[p1];
+        if (k == kKindCross) {
+            sigma = 0.5f * (sigma + a.sigma_in[p2]);
+        } else if (k == kKindMut) {
+            const uint4 w = stream_block(a.seed, kTagSigma, a.gen, static_cast<uint32_t>(j), 0u);
+            sigma *= expf(a.tau * box_muller(w.x, w.y).x);
+        }
+        a.sigma_out[j] = sigma;
+    }
     if (a.precision > 0) {
         a.amax_out[j] = 0.0f;
         if (a.precision == 2) {
@@ -124,7 +140,7 @@ __device__ __forceinline__ void select_child(const SelectArgs& a, const float* f
             // mutation adds at most sigma * kNormalBound.
             float bound = a.amax_in[p1];
             if (k == kKindCross) bound = fmaxf(bound, a.amax_in[p2]);
-            else if (k == kKindMut) bound = fmaf(a.sigma, kNormalBound, bound);
+            else if (k == kKindMut) bound = fmaf(sigma, kNormalBound, bound);
             a.scale_exp_out[j] = fp8_scale_exp(bound);
         }
     }

@@ -573,6 +573,7 @@ leea_status leea_surr_create(int32_t pop, const int32_t* dims, int32_t n_dims, c
     if (!sp || !probe_host) return fail(LEEA_EINVAL, "surrogate params and probe inputs are required");
     if (p->precision != 0 && p->precision != 1)
         return fail(LEEA_EINVAL, "the surrogate form evaluates in FP32 (precision 0) or BF16 (precision 1)");
+    if ((st = require_const_sigma(p, "the surrogate form"))) return st;
     if (sp->mult < 1 || sp->n_probe < 1 || sp->n_probe > 32 || sp->hidden1 < 1 || sp->hidden1 > 256 ||
         sp->hidden2 < 1 || sp->hidden2 > 256 || sp->train_steps < 0 || sp->train_batch < 1 || sp->history < 1 ||
         sp->warmup < 0 || !(sp->lr > 0.0f) || !(sp->audit_frac >= 0.0f && sp->audit_frac <= 1.0f))

@@ -103,6 +103,7 @@ leea_status leea_select_recipes(int32_t pop, const leea_params* p, const float* 
     leea_status st = check_pop(pop);
     if (st) return st;
     if ((st = check_params(p))) return st;
+    if ((st = require_const_sigma(p, "leea_select_recipes"))) return st;
     if (mult < 1 || static_cast<int64_t>(mult) * pop > (1 << 26)) return fail(LEEA_EINVAL, "mult must be >= 1");
     if (!f_adj_dev || !order_dev || !par1_dev || !par2_dev || !kind_dev || !f_inh_dev || !entity_dev)
         return fail(LEEA_EINVAL, "NULL device pointer");
@@ -123,6 +124,7 @@ leea_status leea_breed_entities(int32_t n_parents, const int32_t* dims, int32_t 
     if ((st = check_pop(n_children))) return st;
     if ((st = check_params(p))) return st;
     if (p->precision != 0) return fail(LEEA_EINVAL, "leea_breed_entities takes precision 0");
+    if ((st = require_const_sigma(p, "leea_breed_entities"))) return st;
     NetLayout net;
     if (!make_layout(dims, n_dims, p->init, &net)) return fail(LEEA_EINVAL, "invalid dims");
     if (!parents_dev || !par1_dev || !par2_dev || !kind_dev || !entity_dev || !children_dev)
@@ -149,6 +151,7 @@ leea_status leea_descriptors(int32_t n_parents, const int32_t* dims, int32_t n_d
     leea_status st = check_pop(n_parents);
     if (st) return st;
     if ((st = check_params(p))) return st;
+    if ((st = require_const_sigma(p, "leea_descriptors"))) return st;
     NetLayout net;
     if (!make_layout(dims, n_dims, p->init, &net) || net.n_layers != 2)
         return fail(LEEA_EINVAL, "descriptors take d_0-h-d_out nets (n_dims == 3)");

@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(_PKG, "_build", "libleea.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = range(6)
 TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
+TAG_SIGMA = 7
+SIGMA_CONST, SIGMA_DECAY, SIGMA_SELF = 0, 1, 2
 KIND_ELITE, KIND_CROSSOVER, KIND_MUTATION = 0, 1, 2
 EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR = 0, 1, 2
 PRECISION_FP32, PRECISION_BF16, PRECISION_FP8 = 0, 1, 2
@@ -53,6 +55,7 @@ class leea_params(ctypes.Structure):
         ("sigma", ctypes.c_float), ("mut_rate", ctypes.c_float),
         ("alpha", ctypes.c_float), ("init", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("eval_path", ctypes.c_int32),
+        ("sigma_ctl", ctypes.c_int32), ("sigma_k", ctypes.c_float), ("tau", ctypes.c_float),
     ]
 
 
@@ -73,6 +76,9 @@ class Params:
     init: int = 0
     precision: int = 0  # PRECISION_FP32, PRECISION_BF16 or PRECISION_FP8
     eval_path: int = 0  # EVAL_AUTO, EVAL_SIMT or EVAL_TENSOR
+    sigma_ctl: int = 0  # SIGMA_CONST, SIGMA_DECAY or SIGMA_SELF (Section 3.2)
+    sigma_k: float = 1.0
+    tau: float = 0.1
 
     def c_struct(self) -> leea_params:
         return leea_params(**{f.name: getattr(self, f.name) for f in fields(Params)})
@@ -129,6 +135,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_set_generation": [vp, u32, i32],
         "leea_get_selection": [vp, vp, vp, vp, vp, vp],
         "leea_generation_index": ([vp], u32),
+        "leea_get_sigma": [vp, vp],
+        "leea_set_sigma": [vp, vp],
         "leea_state_num_params": ([vp], i64),
         "leea_profile_enable": [vp, i32],
         "leea_profile_read": [vp, vp, vp],
@@ -203,7 +211,8 @@ def exported_symbols() -> list[str]:
             "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
             "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
             "leea_get_population", "leea_set_population", "leea_set_fitness", "leea_set_generation",
-            "leea_get_selection", "leea_generation_index", "leea_state_num_params",
+            "leea_get_selection", "leea_generation_index", "leea_state_num_params", "leea_get_sigma",
+            "leea_set_sigma",
             "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy",
             "leea_shadow_stride", "leea_make_shadow", "leea_shadow_scratch_bytes", "leea_evaluate_shadow_u8",
             "leea_get_shadow", "leea_evaluate_shadow_u8_noalloc",
@@ -474,6 +483,17 @@ class LeeaState:
         am = np.empty(self.pop, dtype=np.float32)
         _check(self.lib.leea_get_shadow(self._h, _hp(sh), _hp(se), _hp(am)))
         return sh, se, am
+
+    def leea_get_sigma(self) -> np.ndarray:
+        """Sigma genes (SIGMA_SELF) or the next breed's strength, float32[pop]."""
+        out = np.empty(self.pop, dtype=np.float32)
+        _check(self.lib.leea_get_sigma(self._h, _hp(out)))
+        return out
+
+    def leea_set_sigma(self, sigma) -> None:
+        a = np.ascontiguousarray(np.asarray(sigma, dtype=np.float32))
+        assert a.shape == (self.pop,)
+        _check(self.lib.leea_set_sigma(self._h, _hp(a)))
 
     @property
     def gen(self) -> int:

@@ -47,6 +47,10 @@ def test_default_params_are_the_papers(lib, oracle_mod):
         assert getattr(d, f) == getattr(o, f)
     for f in ("xo_gene_p", "rho", "p_e", "p_c", "sigma", "mut_rate", "alpha"):
         assert np.float32(getattr(d, f)) == np.float32(getattr(o, f))
+    # Constant mutation strength by default; the decay rate and tau (which the
+    # paper does not state) are the same readings on both sides.
+    assert d.sigma_ctl == o.sigma_ctl == leea.SIGMA_CONST
+    assert np.float32(d.sigma_k) == np.float32(o.sigma_k) and np.float32(d.tau) == np.float32(o.tau)
 
 
 @pytest.mark.parametrize("dims", [[784, 112, 10], [784, 32, 10], [2, 2, 2], [196, 256, 128, 64, 10], [3, 1]])
@@ -85,6 +89,17 @@ def test_argument_errors_are_reported_before_any_work(lib):
     rc = lib.leea_create(10, d.ctypes.data_as(ctypes.c_void_p), 3, ctypes.byref(bad), 1, None, ctypes.byref(h))
     assert rc == leea.EINVAL and h.value is None
     assert b"sigma" in lib.leea_last_error()
+    for kw, word in ((dict(sigma_ctl=3), b"sigma_ctl"), (dict(sigma_ctl=leea.SIGMA_DECAY, sigma_k=0.0), b"sigma_k"),
+                     (dict(sigma_ctl=leea.SIGMA_SELF, tau=-0.5), b"tau")):
+        bad = leea.Params(**kw).c_struct()
+        rc = lib.leea_create(10, d.ctypes.data_as(ctypes.c_void_p), 3, ctypes.byref(bad), 1, None, ctypes.byref(h))
+        assert rc == leea.EINVAL and h.value is None
+        assert word in lib.leea_last_error()
+    # Outside the state object the mutation strength is a constant argument.
+    self_p = leea.Params(sigma_ctl=leea.SIGMA_SELF).c_struct()
+    n = ctypes.c_void_p(16)  # never dereferenced: the check comes first
+    rc = lib.leea_select(10, ctypes.byref(self_p), n, n, 1, 1, n, n, n, n, None)
+    assert rc == leea.EINVAL and b"sigma_ctl" in lib.leea_last_error()
     d4 = np.array([196, 256, 128, 64, 10], dtype=np.int32)
     good = leea.Params().c_struct()
     rc = lib.leea_create(10, d4.ctypes.data_as(ctypes.c_void_p), 5, ctypes.byref(good), 1, None, ctypes.byref(h))
