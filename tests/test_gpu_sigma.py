@@ -62,7 +62,10 @@ def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=21, gen0=40, sample=N
             # elites and crossover children: one FP32 rounding; mutation children: expf in FP32
             np.testing.assert_allclose(sig_gpu, sig_ref, rtol=1e-6, atol=0)
             moved = ok == oracle_mod.MUTATION
-            assert (sig_gpu[moved] != sig0[o1[moved]]).mean() > 0.99
+            if prm["tau"] > 0:
+                assert (sig_gpu[moved] != sig0[o1[moved]]).mean() > 0.99
+            else:  # exp(0 z) = 1: the parent's gene
+                np.testing.assert_array_equal(sig_gpu[moved], sig0[o1[moved]])
         else:
             sig_ref = np.full(pop, oracle_mod.sigma_schedule(o_prm, gen0 + 1))
             np.testing.assert_allclose(sig_gpu, oracle_mod.sigma_schedule(o_prm, gen0 + 2), rtol=2 ** -23)
