@@ -125,8 +125,16 @@ enum { LEEA_SIGMA_CONST = 0, LEEA_SIGMA_DECAY = 1, LEEA_SIGMA_SELF = 2 };
  * buffers) and the CUDA-core kernel otherwise.  SIMT: exact FP32 FFMA on the
  * CUDA cores.  TENSOR: tcgen05 tensor cores with a three-term TF32 split
  * (X_hi W_hi + X_hi W_lo + X_lo W_hi, FP32 accumulation), which is within
- * ~1e-6 relative of FP32; LEEA_EINVAL if the shape does not allow it. */
-enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2 };
+ * ~1e-6 relative of FP32; LEEA_EINVAL if the shape does not allow it.
+ * FUSED (state object, 8-bit generation calls, precision 0): every breeding
+ * generation makes and evaluates each child in one kernel
+ * (leea_breed_evaluate_u8), so the evaluation does not read the new
+ * population back from memory; the children are bit-identical to
+ * leea_breed's.  It needs d_0 % 16 == 0, h % 16 == 0, h <= 128, d_out <= 16,
+ * batch <= 128 (LEEA_EINVAL otherwise); the first evaluation uses the
+ * tensor-core kernel.  AUTO takes FUSED for 8-bit generation calls of an FP32
+ * object whenever the shape allows it. */
+enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2, LEEA_EVAL_FUSED = 3 };
 
 /* Precision form (a throughput variant of Eq. 1; the paper itself computes in
  * FP32).  With precision 1 or 2 the population keeps its FP32 master, which
@@ -224,6 +232,26 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                        const float* parents_dev, const int32_t* par1_dev,
                        const int32_t* par2_dev, const int32_t* kind_dev,
                        float* children_dev, void* stream);
+
+/* leea_breed followed by leea_evaluate_u8 of the children with inheritance
+ * (Section 3.2, Eq. 1, Section 3.1), in one kernel: each child is made in
+ * shared memory from its parents, written to children_dev and evaluated from
+ * there on the tensor cores (8-bit inputs x = k / x_div; the numerics of
+ * leea_evaluate_u8's tensor-core path, with layer 2 summed over the two
+ * halves of the hidden units).  Children are bit-identical to leea_breed's.
+ * n_dims == 3 with d_0 % 16 == 0, h % 16 == 0, h <= 128, d_out <= 16;
+ * batch <= 128; parents_dev and children_dev 16-byte aligned and not
+ * overlapping; p->precision 0 and p->sigma_ctl LEEA_SIGMA_CONST.  f_inh_dev
+ * (float[pop], may be NULL for f_adj = f), f_raw_dev (written), f_adj_dev and
+ * correct_dev (may be NULL). */
+leea_status leea_breed_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims,
+                                   const leea_params* p, uint64_t seed, uint32_t gen,
+                                   const float* parents_dev, const int32_t* par1_dev,
+                                   const int32_t* par2_dev, const int32_t* kind_dev,
+                                   float* children_dev, const uint8_t* x_u8_dev, float x_div,
+                                   const int32_t* y_dev, int32_t batch, float alpha,
+                                   const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
+                                   int32_t* correct_dev, void* stream);
 
 /* Fitness of every individual on one minibatch (Eq. 1) and inheritance
  * (Section 3.1).  f = -(1/batch) sum_b CE(softmax(z_b), y_b) computed in FP32
@@ -427,7 +455,8 @@ int64_t leea_state_num_params(const leea_state* s);
 
 /* Per-stage timing with CUDA events recorded on the object's stream around
  * each kernel of leea_generation.  Stages: 0 ranking + selection (one fused
- * launch for pop <= 4096), 1 breeding, 2 evaluation. */
+ * launch for pop <= 4096), 1 breeding (with the evaluation under
+ * LEEA_EVAL_FUSED), 2 evaluation (no launch after a fused breed). */
 #define LEEA_NUM_STAGES 3
 leea_status leea_profile_enable(leea_state* s, int32_t enable);
 

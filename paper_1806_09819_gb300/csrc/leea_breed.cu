@@ -26,6 +26,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include "breed_ops.cuh"
 #include "leea_internal.h"
 #include "philox.cuh"
 #include "tc_ptx.cuh"
@@ -34,7 +35,6 @@ namespace leea {
 
 namespace {
 
-constexpr uint32_t kTagXo = 3, kTagMutMask = 4, kTagNormal = 5;
 constexpr int kConsumerWarps = 16;
 constexpr int kBreedThreads = 32 * (1 + kConsumerWarps);
 constexpr int kChunk = 4096;                // genes per work item
@@ -150,19 +150,6 @@ __device__ __forceinline__ void raise_abort(volatile int* abort_flag, unsigned i
 constexpr int kGenesPerLane = 8;  // one Philox block of 16-bit mask draws per lane and chunk
 static_assert(kChunk == kGenesPerLane * 32 * kConsumerWarps, "consumers must tile a chunk exactly");
 
-// Bit k of the result: the 16-bit draw k (k = 0..7) of block r is below thr.
-__device__ __forceinline__ uint32_t mask8(const uint4& r, uint32_t thr)
-{
-    const uint32_t w[4] = { r.x, r.y, r.z, r.w };
-    uint32_t m = 0;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t u = (k & 1) ? (w[k >> 1] >> 16) : (w[k >> 1] & 0xFFFFu);
-        m |= (u < thr ? 1u : 0u) << k;
-    }
-    return m;
-}
-
 // Zero the padding genes (>= c) among genes i0 .. i0+3.
 __device__ __forceinline__ float4 clear_padding(float4 v, int64_t i0, int64_t c)
 {
@@ -171,59 +158,6 @@ __device__ __forceinline__ float4 clear_padding(float4 v, int64_t i0, int64_t c)
     if (i0 + 2 >= c) v.z = 0.0f;
     if (i0 + 3 >= c) v.w = 0.0f;
     return v;
-}
-
-__device__ __forceinline__ float4 select4(uint32_t m, float4 a, float4 b)
-{
-    return make_float4((m & 1u) ? b.x : a.x, (m & 2u) ? b.y : a.y, (m & 4u) ? b.z : a.z, (m & 8u) ? b.w : a.w);
-}
-
-// Mutation of this lane's 8 genes (unit u = genes 8u .. 8u+7, live if `live`).
-// Slot s = 0..3 names the Box-Muller pair of genes 8u + 2s, 8u + 2s + 1, i.e.
-// pair s & 1 of NORMAL block 2u + (s >> 1).  The warp lists the slots that
-// hold a masked gene, slot by slot (one ballot each), in its shared-memory job
-// list; consecutive lanes compute the listed normals and every lane reads its
-// own back.  Each normal depends only on its (unit, slot) counter.
-__device__ __forceinline__ void mutate_unit(const BreedArgs& a, float sigma, uint32_t gen, const PhiloxKeys& key,
-                                            uint32_t j, uint32_t u, bool live, float4 (&v)[2], int lane, float2* job_z,
-                                            uint8_t* job_code)
-{
-    constexpr int kSlots = 4;
-    uint32_t hit = 0;
-    if (live) hit = mask8(philox_keyed(make_uint4(u, j, gen, kTagMutMask), key), a.thr_mut);
-    const uint32_t lt = (1u << lane) - 1u;
-    uint32_t idx[kSlots], total = 0;
-#pragma unroll
-    for (int sl = 0; sl < kSlots; ++sl) {
-        const bool need = ((hit >> (2 * sl)) & 3u) != 0u;
-        const uint32_t b = __ballot_sync(0xFFFFFFFFu, need);
-        idx[sl] = total + __popc(b & lt);
-        if (need) job_code[idx[sl]] = static_cast<uint8_t>((lane << 2) | sl);
-        total += __popc(b);
-    }
-    __syncwarp();
-    for (uint32_t job = static_cast<uint32_t>(lane); job < total; job += 32) {
-        const uint32_t code = job_code[job];
-        const uint32_t o = code >> 2, slot = code & 3u;
-        // Lanes of a warp own consecutive units: the owner's is u - lane + o.
-        const uint32_t uo = u - static_cast<uint32_t>(lane) + o;
-        const uint4 n = philox_keyed(make_uint4(2u * uo + (slot >> 1), j, gen, kTagNormal), key);
-        job_z[job] = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
-    }
-    __syncwarp();
-    float2 z[kSlots];
-#pragma unroll
-    for (int sl = 0; sl < kSlots; ++sl)
-        z[sl] = ((hit >> (2 * sl)) & 3u) ? job_z[idx[sl]] : make_float2(0.f, 0.f);
-    if (hit & 0x01u) v[0].x = fmaf(sigma, z[0].x, v[0].x);
-    if (hit & 0x02u) v[0].y = fmaf(sigma, z[0].y, v[0].y);
-    if (hit & 0x04u) v[0].z = fmaf(sigma, z[1].x, v[0].z);
-    if (hit & 0x08u) v[0].w = fmaf(sigma, z[1].y, v[0].w);
-    if (hit & 0x10u) v[1].x = fmaf(sigma, z[2].x, v[1].x);
-    if (hit & 0x20u) v[1].y = fmaf(sigma, z[2].y, v[1].y);
-    if (hit & 0x40u) v[1].z = fmaf(sigma, z[3].x, v[1].z);
-    if (hit & 0x80u) v[1].w = fmaf(sigma, z[3].y, v[1].w);
-    __syncwarp();  // the list is reused by the next unit
 }
 
 // The run owning global work item `it`: the last one whose first item is <= it.
@@ -360,9 +294,11 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
                 v[1] = A[2 * ct + 1];
             }
             if (m.kind == 2) {
+                // Lanes of a warp own consecutive units: lane o owns u - lane + o.
                 const int cw = warp - 1;  // consumer warp
-                mutate_unit(a, m.sigma, gen, key, j, u, live, v, lane, s.job_z + cw * kJobSlots,
-                            s.job_code + cw * kJobSlots);
+                const uint32_t hit = live ? mask8(philox_keyed(make_uint4(u, j, gen, kTagMutMask), key), a.thr_mut) : 0u;
+                mutate8(m.sigma, gen, key, j, hit, v, lane, s.job_z + cw * kJobSlots, s.job_code + cw * kJobSlots,
+                        [&](uint32_t o) { return u - static_cast<uint32_t>(lane) + o; });
             } else if (live && m.kind == 1) {
                 const float4 b0 = B[2 * ct], b1 = B[2 * ct + 1];
                 if (a.xo_op == 0) {
@@ -370,10 +306,8 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
                     v[0] = select4(msk, v[0], b0);
                     v[1] = select4(msk >> 4, v[1], b1);
                 } else {
-                    v[0] = make_float4(0.5f * (v[0].x + b0.x), 0.5f * (v[0].y + b0.y), 0.5f * (v[0].z + b0.z),
-                                       0.5f * (v[0].w + b0.w));
-                    v[1] = make_float4(0.5f * (v[1].x + b1.x), 0.5f * (v[1].y + b1.y), 0.5f * (v[1].z + b1.z),
-                                       0.5f * (v[1].w + b1.w));
+                    v[0] = mean4(v[0], b0);
+                    v[1] = mean4(v[1], b1);
                 }
             } else if (m.kind == kKindInvalid) {
                 const float nan = __int_as_float(0x7FC00000);

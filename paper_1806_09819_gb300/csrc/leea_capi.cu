@@ -86,8 +86,10 @@ leea_status check_params(const leea_params* p)
     if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
     if (p->init != 0 && p->init != 1) return fail(LEEA_EINVAL, "init must be 0 or 1");
     if (p->precision < 0 || p->precision > 2) return fail(LEEA_EINVAL, "precision must be 0, 1 or 2");
-    if (p->eval_path < LEEA_EVAL_AUTO || p->eval_path > LEEA_EVAL_TENSOR)
-        return fail(LEEA_EINVAL, "eval_path must be LEEA_EVAL_AUTO, _SIMT or _TENSOR");
+    if (p->eval_path < LEEA_EVAL_AUTO || p->eval_path > LEEA_EVAL_FUSED)
+        return fail(LEEA_EINVAL, "eval_path must be LEEA_EVAL_AUTO, _SIMT, _TENSOR or _FUSED");
+    if (p->eval_path == LEEA_EVAL_FUSED && p->precision != 0)
+        return fail(LEEA_EINVAL, "the fused breed + evaluate path takes precision 0");
     if (p->sigma_ctl < LEEA_SIGMA_CONST || p->sigma_ctl > LEEA_SIGMA_SELF)
         return fail(LEEA_EINVAL, "sigma_ctl must be LEEA_SIGMA_CONST, _DECAY or _SELF");
     if (p->sigma_ctl == LEEA_SIGMA_DECAY && !(p->sigma_k > 0.0f && !std::isinf(p->sigma_k)))
@@ -447,6 +449,42 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims, const l
     LEEA_CUDA_TRY(launch_breed(a, parents_dev, par1_dev, par2_dev, kind_dev, children_dev, status,
                                static_cast<cudaStream_t>(stream)),
                   "breed kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_breed_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims, const leea_params* p,
+                                   uint64_t seed, uint32_t gen, const float* parents_dev, const int32_t* par1_dev,
+                                   const int32_t* par2_dev, const int32_t* kind_dev, float* children_dev,
+                                   const uint8_t* x_u8_dev, float x_div, const int32_t* y_dev, int32_t batch,
+                                   float alpha, const float* f_inh_dev, float* f_raw_dev, float* f_adj_dev,
+                                   int32_t* correct_dev, void* stream)
+{
+    leea_status st = check_pop(pop);
+    if (st) return st;
+    if ((st = check_params(p))) return st;
+    if (p->precision != 0) return fail(LEEA_EINVAL, "leea_breed_evaluate_u8 takes precision 0");
+    if ((st = require_const_sigma(p, "leea_breed_evaluate_u8"))) return st;
+    NetLayout net;
+    if (!make_layout(dims, n_dims, p->init, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if ((st = check_eval_shape(net, batch))) return st;
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
+    if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
+    if (!parents_dev || !par1_dev || !par2_dev || !kind_dev || !children_dev || !x_u8_dev || !y_dev || !f_raw_dev)
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    const size_t bytes = sizeof(float) * static_cast<size_t>(pop) * static_cast<size_t>(net.c_pad);
+    const char* pa = reinterpret_cast<const char*>(parents_dev);
+    const char* ch = reinterpret_cast<const char*>(children_dev);
+    if (pa < ch + bytes && ch < pa + bytes) return fail(LEEA_EINVAL, "parents and children overlap");
+    if (!breed_eval_u8_supported(net, batch, parents_dev, children_dev))
+        return fail(LEEA_EINVAL, "the fused breed + evaluate kernel needs n_dims == 3, d_0 %% 16 == 0, h %% 16 == 0, "
+                                 "h <= 128, d_out <= 16, batch <= 128 and 16-byte aligned populations");
+    const BreedArgs a = breed_args(pop, net, p, seed, gen);
+    unsigned int* status = device_status_ptr();
+    if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+    LEEA_CUDA_TRY(launch_breed_eval_u8(a, net, parents_dev, par1_dev, par2_dev, kind_dev, children_dev, x_u8_dev,
+                                       x_div, y_dev, batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev, correct_dev, status,
+                                       static_cast<cudaStream_t>(stream)),
+                  "breed + evaluate kernel");
     return LEEA_OK;
 }
 
@@ -845,6 +883,18 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         }
     }
     const bool first = !s->evaluated;
+    // Breed and evaluate in one kernel: 8-bit inputs of an FP32 object, when
+    // asked for (FUSED) or when the shape allows it (AUTO).
+    bool fused = false;
+    if (u8 && prec == 0 && (s->prm.eval_path == LEEA_EVAL_AUTO || s->prm.eval_path == LEEA_EVAL_FUSED)) {
+        const bool ok = breed_eval_u8_supported(s->net, batch, s->popbuf[0], s->popbuf[1]);
+        if (s->prm.eval_path == LEEA_EVAL_FUSED && !ok)
+            return fail(LEEA_EINVAL, "the fused breed + evaluate path needs d_0 %% 16 == 0, h %% 16 == 0, h <= 128, "
+                                     "d_out <= 16 and batch <= 128");
+        fused = ok;
+    }
+    if (!u8 && s->prm.eval_path == LEEA_EVAL_FUSED)
+        return fail(LEEA_EINVAL, "the fused breed + evaluate path takes 8-bit inputs (leea_generation_u8*)");
     if (!first) {
         const uint32_t g = s->gen + 1;
         const float sigma_g = sigma_of_breed(s->prm, g);
@@ -867,6 +917,23 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
             LEEA_CUDA_TRY(launch_rank_select(a, s->f_adj, s->order, s->par1, s->par2, s->kind, s->f_inh, s->stream),
                           "rank/select kernel");
             sc.done();
+        }
+        if (fused) {
+            StageScope sc(s, 1);
+            BreedArgs a = breed_args(s->pop, s->net, &s->prm, s->seed, g);
+            a.sigma = sigma_g;
+            if (self) a.sigma_child = s->sigma[s->cur ^ 1];
+            unsigned int* status = device_status_ptr();
+            if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+            LEEA_CUDA_TRY(launch_breed_eval_u8(a, s->net, s->popbuf[s->cur], s->par1, s->par2, s->kind,
+                                               s->popbuf[s->cur ^ 1], static_cast<const uint8_t*>(x_dev), x_div,
+                                               y_dev, batch, s->prm.alpha, s->f_inh, s->f_raw, s->f_adj, s->correct,
+                                               status, s->stream),
+                          "breed + evaluate kernel");
+            sc.done();
+            s->cur ^= 1;
+            s->gen = g;
+            return LEEA_OK;
         }
         {
             StageScope sc(s, 1);

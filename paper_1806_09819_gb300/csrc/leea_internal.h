@@ -225,6 +225,16 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
                               float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
                               float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
                               cudaStream_t stream);
+// Crossover, mutation and evaluation of every child in one kernel (8-bit
+// inputs; d_0 % 16 == 0, h % 16 == 0, h <= 128, d_out <= 16, batch <= 128,
+// 16-byte aligned populations).  Operators and streams from b (b.pop children
+// of b.pop parents); results as launch_eval_u8_tc with the children.
+bool breed_eval_u8_supported(const NetLayout& net, int32_t batch, const float* parents, const float* children);
+cudaError_t launch_breed_eval_u8(const BreedArgs& b, const NetLayout& net, const float* parents, const int32_t* par1,
+                                 const int32_t* par2, const int32_t* kind, float* children, const uint8_t* x,
+                                 float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                                 float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
+                                 cudaStream_t stream);
 // Surrogate form: recipes (virtual offspring) and their descriptors.
 constexpr uint32_t kRecipeEntity0 = 0x40000000u;  // Philox entity of recipe r: kRecipeEntity0 + r
 // Recipes r < mult n_cross are crossovers, the rest mutations; parents as

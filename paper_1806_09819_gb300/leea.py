@@ -22,7 +22,7 @@ TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
 TAG_SIGMA = 7
 SIGMA_CONST, SIGMA_DECAY, SIGMA_SELF = 0, 1, 2
 KIND_ELITE, KIND_CROSSOVER, KIND_MUTATION = 0, 1, 2
-EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR = 0, 1, 2
+EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR, EVAL_FUSED = 0, 1, 2, 3
 PRECISION_FP32, PRECISION_BF16, PRECISION_FP8 = 0, 1, 2
 NUM_STAGES = 3
 STAGES = ("select", "breed", "evaluate")  # select = ranking + selection
@@ -108,6 +108,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_rank": [i32, vp, vp, vp],
         "leea_select": [i32, P(leea_params), vp, vp, u64, u32, vp, vp, vp, vp, vp],
         "leea_breed": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp],
+        "leea_breed_evaluate_u8": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp, f32, vp, i32, f32,
+                                   vp, vp, vp, vp, vp],
         "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, i32, vp],
         "leea_device_status": [vp, P(u32)],
         "leea_shadow_stride": ([vp, i32, i32], i64),
@@ -206,7 +208,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
 def exported_symbols() -> list[str]:
     """Names of the entry points the binding expects the library to export."""
     return ["leea_default_params", "leea_num_params", "leea_padded_params", "leea_counts",
-            "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_evaluate",
+            "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_breed_evaluate_u8",
+            "leea_evaluate",
             "leea_device_status", "leea_evaluate_u8", "leea_generation_u8", "leea_generation_u8_host",
             "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
             "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
@@ -313,6 +316,18 @@ def leea_breed(pop: int, dims, prm: Params, seed: int, gen: int, parents_dev, pa
     _check(load_library().leea_breed(pop, _hp(d), len(d), ctypes.byref(cp), seed, gen, _dptr(parents_dev),
                                      _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev), _dptr(children_dev),
                                      _stream(stream)))
+
+
+def leea_breed_evaluate_u8(pop: int, dims, prm: Params, seed: int, gen: int, parents_dev, par1_dev, par2_dev,
+                           kind_dev, children_dev, x_u8_dev, x_div: float, y_dev, batch: int, alpha: float, f_inh_dev,
+                           f_raw_dev, f_adj_dev=None, correct_dev=None, stream=None) -> None:
+    d = _dims(dims)
+    cp = prm.c_struct()
+    _check(load_library().leea_breed_evaluate_u8(pop, _hp(d), len(d), ctypes.byref(cp), seed, gen, _dptr(parents_dev),
+                                                 _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev),
+                                                 _dptr(children_dev), _dptr(x_u8_dev), float(x_div), _dptr(y_dev),
+                                                 batch, float(alpha), _dptr(f_inh_dev), _dptr(f_raw_dev),
+                                                 _dptr(f_adj_dev), _dptr(correct_dev), _stream(stream)))
 
 
 def leea_evaluate(pop: int, dims, pop_dev, x_dev, y_dev, batch: int, alpha: float, f_inh_dev,
