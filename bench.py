@@ -87,6 +87,7 @@ STAGES = ("select", "breed", "evaluate")
 TRAFFIC = {
     "breed": {"bytes_per_launch": 706.54e6, "src_sha": "53af562611246ce0", "capture": "P=1000 plain workload"},
     "evaluate": {"bytes_per_launch": 359.37e6, "src_sha": "d972b174f2e01544", "capture": "P=1000 plain workload"},
+    "breed_evaluate": {"bytes_per_launch": None, "src_sha": None, "capture": "P=1000 plain workload"},
 }
 
 
@@ -135,13 +136,16 @@ def max_over_ranks(value: float, dist, device=None) -> float:
 PROFILE_EVERY = 8  # generations per profiled one inside the timed region
 
 
-def kernels_per_generation(pop: int, batch: int, precision: int) -> dict:
+def kernels_per_generation(pop: int, batch: int, precision: int, fused: bool = False) -> dict:
     """Kernel launches per stage of one state-object generation: ranking and
-    selection run as one kernel below 512 nets and as two above; the shadow
+    selection run as one kernel below 512 nets and as two above; breeding and
+    evaluation are one fused kernel on the 8-bit FP32 path, else two; the shadow
     evaluation adds a combining kernel when the batch spans several 128-sample
     tiles."""
-    return {"select": 2 if pop >= 512 else 1, "breed": 1,
-            "evaluate": 1 + (1 if precision > 0 and batch > 128 else 0)}
+    sel = 2 if pop >= 512 else 1
+    if fused:
+        return {"select": sel, "breed_evaluate": 1}
+    return {"select": sel, "breed": 1, "evaluate": 1 + (1 if precision > 0 and batch > 128 else 0)}
 
 
 def job_rate(world: int, units_per_rank: float, ms_local: float, dist, device=None):
@@ -624,6 +628,10 @@ def run_native(args, rank: int, world: int, local_rank: int):
     prof = st.leea_profile_read()
     st.leea_profile_enable(False)
     ms_max, gen_per_s = job_rate(world, steps, ms, dist, dev)
+    # Breeding and evaluation ran as one kernel (stage 1) when stage 2 has no launch.
+    fused = prof["evaluate"][1] == 0 and prof["breed"][1] > 0
+    if fused:
+        prof = {"select": prof["select"], "breed_evaluate": prof["breed"]}
 
     # ---- end to end through the host-buffer entry point ----
     e2e_steps = max(10, min(steps, 1000))
@@ -668,8 +676,12 @@ def run_native(args, rank: int, world: int, local_rank: int):
                       SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12)),
         "select": ("latency", None, None, None),
     }
+    # fused: the breed's bytes (parents in, children out); the evaluation's
+    # weight stream is gone (the minibatch stays in L2)
+    work["breed_evaluate"] = work["breed"]
+    names = ("select", "breed_evaluate") if fused else STAGES
     kernels = {}
-    for name in STAGES:
+    for name in names:
         tot_ms, launches = prof[name]
         per = tot_ms / max(1, launches)
         bound, units, unit, peak = work[name]
@@ -678,9 +690,9 @@ def run_native(args, rank: int, world: int, local_rank: int):
             ach = units / (per / 1000.0)
             entry.update({"bound": bound, "achieved": ach, "unit": unit, "peak": peak, "frac": ach / peak})
         kernels[name] = entry
-    dom = max(("breed", "evaluate"), key=lambda n: prof[n][0])
+    dom = "breed_evaluate" if fused else max(("breed", "evaluate"), key=lambda n: prof[n][0])
     kd = kernels[dom]
-    src = {"breed": "leea_breed.cu",
+    src = {"breed": "leea_breed.cu", "breed_evaluate": "leea_breed_eval.cu",
            "evaluate": (("leea_eval_shadow.cu" if precision else "leea_eval_u8.cu") if u8 else "leea_eval_tc.cu")
            if tensor_eval else "leea_eval_simt.cu"}[dom]
     tr = TRAFFIC.get(dom) if (args.config, pop, batch, u8) == ("plain", POP, BATCH, True) else None
@@ -692,8 +704,9 @@ def run_native(args, rank: int, world: int, local_rank: int):
         k_pad = {0: 784 if u8 else 800, 1: 784, 2: 800}[precision]
         passes = {0: 2 if u8 else 3, 1: 1, 2: 2}[precision]  # u8: two FP16 weight pieces; float: 3xTF32
         tiles = (batch + 127) // 128
-        kernels["evaluate"]["tensor_tflops_issued"] = (passes * 2.0 * pop * tiles * 128 * k_pad * h / 1e12) / (
-            prof["evaluate"][0] / max(1, prof["evaluate"][1]) / 1000.0)
+        ev = "breed_evaluate" if fused else "evaluate"
+        kernels[ev]["tensor_tflops_issued"] = (passes * 2.0 * pop * tiles * 128 * k_pad * h / 1e12) / (
+            prof[ev][0] / max(1, prof[ev][1]) / 1000.0)
 
     pname = {1: "BF16", 2: "FP8-e4m3 (per-individual power-of-two scale)"}.get(precision)
     workload = PRECISION_WORKLOAD.format(name=pname) if precision else WORKLOAD
@@ -703,6 +716,8 @@ def run_native(args, rank: int, world: int, local_rank: int):
         precision] + ", batch in TMEM" if precision else
                    (("tcgen05 FP16 two-piece weights, batch in TMEM" if u8 else "tcgen05 3xTF32") if tensor_eval
                     else "CUDA-core FP32 FFMA"))
+    if fused:
+        eval_kernel = "fused breed + evaluate (children made in shared memory, written once, fed to " + eval_kernel + ")"
     pop_mb = pop * leea.leea_padded_params(DIMS) * 4 / 1e6
     line = {"metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps,
             "warmup": warmup, "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak",
@@ -715,7 +730,8 @@ def run_native(args, rank: int, world: int, local_rank: int):
                        "eval_kernel": eval_kernel,
                        "l2": f"inputs larger than L2 (2 population buffers of {pop_mb:.0f} MB), no flush"},
             "network_samples_per_sec": gen_per_s * pop * batch,
-            "e2e": e2e, "gpu_launches": int(steps * sum(kernels_per_generation(pop, batch, precision).values())),
+            "e2e": e2e,
+            "gpu_launches": int(steps * sum(kernels_per_generation(pop, batch, precision, fused).values())),
             "roofline": roofline,
             "kernels": kernels, "clocks": clk}
     if precision and rank == 0:
@@ -743,7 +759,9 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-children", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--eval-path", type=int, default=0, help="0 auto (tensor cores), 1 CUDA-core FP32, 2 tensor")
+    ap.add_argument("--eval-path", type=int, default=0,
+                    help="0 auto (fused breed + evaluate where it applies), 1 CUDA-core FP32, 2 tensor cores as a "
+                         "separate kernel, 3 fused")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="plain",
                     help="plain: the headline FP32 workload; precision-*: P=4096, batch 256, BF16/FP8 shadows; "
                          "batching: 64 uneven runs together")
