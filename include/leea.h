@@ -132,8 +132,7 @@ enum { LEEA_SIGMA_CONST = 0, LEEA_SIGMA_DECAY = 1, LEEA_SIGMA_SELF = 2 };
  * population back from memory; the children are bit-identical to
  * leea_breed's.  It needs d_0 % 16 == 0, h % 16 == 0, h <= 128, d_out <= 16,
  * batch <= 128 (LEEA_EINVAL otherwise); the first evaluation uses the
- * tensor-core kernel.  AUTO takes FUSED for 8-bit generation calls of an FP32
- * object whenever the shape allows it. */
+ * tensor-core kernel.  AUTO keeps breeding and evaluation as two kernels. */
 enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2, LEEA_EVAL_FUSED = 3 };
 
 /* Precision form (a throughput variant of Eq. 1; the paper itself computes in

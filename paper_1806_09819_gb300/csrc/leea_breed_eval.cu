@@ -10,24 +10,22 @@
 // operators: breed_ops.cuh).  The evaluation numerics are those of the 8-bit
 // tensor-core evaluation: each child weight, scaled by 2^8, as two FP16 pieces
 // against the exact FP16 levels held in TMEM, FP32 accumulation, and an FP32
-// FFMA fallback for a child with a weight |w| >= 128.  Layer 2 sums the hidden
-// units in two halves (one per epilogue warp of a TMEM lane quarter), then
-// adds the halves and b2.
+// FFMA fallback for a child with a weight |w| >= 128.
 //
-// Warp roles (persistent CTA, one per SM; children j = blockIdx.x + n gridDim.x):
+// Warp roles (persistent CTA, one per SM; CTA b takes children
+// pop - 1 - (b + n gridDim.x), n = 0, 1, ...):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
 //   warp 1      TMA producer: per 64-wide K stage the parents' W1 tiles
 //               (h rows x 64 FP32 each) into a ring of slots, one slot per
 //               parent tile (two for a crossover child)
-//   warps 2-8   breeders: per stage a thread makes 8 consecutive genes of some
+//   warps 2-15  breeders: per stage a thread makes 8 consecutive genes of some
 //               rows (crossover mask or mean; mutation with a warp job list of
 //               normals), stores them to HBM and splits them into the two FP16
 //               pieces, written swizzled into the ring the MMAs read
-//   warps 9-16  the batch into TMEM once; then per child: breed the remaining
+//   warps 16-19 the batch into TMEM once; then per child: breed the remaining
 //               genes (b1, W2, b2, padding) from HBM and stage them, read the
-//               accumulator (two warps per lane quarter, half of the hidden
-//               units each), layer 2, softmax cross-entropy, fixed-order batch
-//               sum, inheritance
+//               accumulator row by row (one sample per thread), layer 2,
+//               softmax cross-entropy, fixed-order batch sum, inheritance
 // Every mbarrier wait is bounded in time; on expiry the kernel sets
 // kStatusEvalTimeout, drains what it has in flight and exits.
 #include <cuda.h>
@@ -44,10 +42,10 @@ namespace leea {
 
 namespace {
 
-constexpr int kBreedWarps = 7;
+constexpr int kBreedWarps = 14;
 constexpr int kFirstBreedWarp = 2;
 constexpr int kFirstEpiWarp = kFirstBreedWarp + kBreedWarps;
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 4;
 constexpr int kBreedThreads = 32 * kBreedWarps;
 constexpr int kEpiThreads = 32 * kEpiWarps;
 constexpr int kFusedThreads = 32 * (kFirstEpiWarp + kEpiWarps);
@@ -96,7 +94,6 @@ struct FusedSmem {
     float* w2t;         // [h][dpad]: the child's W2, transposed
     float* b1;          // [h]
     float* b2;          // [16]
-    float* plog;        // [batch][16]: partial logits of the second half of the hidden units
     float2* job_z;      // [kBreedWarps][kJobs]
     uint8_t* job_code;  // [kBreedWarps][kJobs]
     uint64_t *slot_full, *slot_empty, *full, *empty, *acc_full, *acc_empty, *a_ready, *drain, *conv_done, *x_loaded,
@@ -112,7 +109,7 @@ struct FusedSmem {
 __host__ __device__ inline size_t fused_smem_bytes(int32_t h, int32_t dpad, int32_t batch, int32_t slots)
 {
     return 1024 + static_cast<size_t>(slots) * h * 256 + static_cast<size_t>(kPieceStages) * kPieces * h * 128 +
-           sizeof(float) * (static_cast<size_t>(h) * dpad + h + 16 + static_cast<size_t>(batch) * 16) +
+           sizeof(float) * (static_cast<size_t>(h) * dpad + h + 16) +
            (sizeof(float2) + 1) * kBreedWarps * kJobs + 8 * (2 * slots + 2 * kPieceStages + 8) + 64;
 }
 
@@ -130,8 +127,7 @@ __device__ __forceinline__ FusedSmem carve(uint8_t* raw, const FusedArgs& a)
     p += sizeof(float) * a.h;
     s.b2 = reinterpret_cast<float*>(p);
     p += sizeof(float) * 16;
-    s.plog = reinterpret_cast<float*>(p);
-    p += sizeof(float) * a.batch * 16;  // an even number of floats so far: 8-byte aligned
+    // an even number of floats so far (h even): 8-byte aligned
     s.job_z = reinterpret_cast<float2*>(p);
     p += sizeof(float2) * kBreedWarps * kJobs;
     s.job_code = p;
@@ -176,6 +172,14 @@ __device__ __forceinline__ void raise_abort(const FusedSmem& s, const FusedArgs&
     atomicOr(a.status, kStatusEvalTimeout);
 }
 
+// The n-th child a CTA sequence visits: children in reverse index order, so
+// that mutation children (the most work per gene) come first and the last
+// round, which only some CTAs take, holds crossover children and elites.
+__device__ __forceinline__ int child_of(const FusedArgs& a, int n)
+{
+    return a.pop - 1 - n;
+}
+
 struct ChildInfo {
     int32_t kind, p1, p2;
 };
@@ -212,16 +216,11 @@ __device__ __forceinline__ bool out_of_piece_range(const float4& v)
            fabsf(v.w) >= kPieceRange;
 }
 
-// Eight genes of a shared-memory tile row at float offset off (a multiple of
-// 8), read half by half in an order that spreads a quarter-warp's 16-byte
-// reads over all banks (lanes c8 and c8 + 4 start in different halves).
-__device__ __forceinline__ void load8(const float* tile, int32_t off, int c8, float4 (&v)[2])
+// Eight genes of a shared-memory tile row at float offset off (a multiple of 8).
+__device__ __forceinline__ void load8(const float* tile, int32_t off, float4 (&v)[2])
 {
-    const int first = (c8 >> 2) & 1;
-    const float4 t0 = *reinterpret_cast<const float4*>(tile + off + 4 * first);
-    const float4 t1 = *reinterpret_cast<const float4*>(tile + off + 4 * (first ^ 1));
-    v[first] = t0;
-    v[first ^ 1] = t1;
+    v[0] = *reinterpret_cast<const float4*>(tile + off);
+    v[1] = *reinterpret_cast<const float4*>(tile + off + 4);
 }
 
 __global__ void __launch_bounds__(kFusedThreads, 1)
@@ -314,7 +313,8 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
             uint32_t slot = 0, sphase = 0, issued = 0;
             uint32_t issued_mask = 0, parity_mask = 0;
             bool ok = true;
-            for (int j = blockIdx.x; ok && j < a.pop; j += gridDim.x) {
+            for (int n = blockIdx.x; ok && n < a.pop; n += gridDim.x) {
+                const int j = child_of(a, n);
                 const ChildInfo ci = child_info(a, j);
                 const int need = ci.kind == 1 ? 2 : 1;
                 for (int kc = 0; ok && kc < a.k_stages; ++kc) {
@@ -368,7 +368,8 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
         // the piece ring doubles as the batch staging area until the batch is in
         bool ok = ptx::mbar_wait_bounded(s.x_loaded, 0u, s.abort_flag, kWaitLimitNs);
         if (!ok) raise_abort(s, a);
-        for (int j = blockIdx.x; ok && j < a.pop; j += gridDim.x, ++unit) {
+        for (int n = blockIdx.x; ok && n < a.pop; n += gridDim.x, ++unit) {
+            const int j = child_of(a, n);
             const ChildInfo ci = child_info(a, j);
             const float sigma = a.sigma_child ? a.sigma_child[j] : a.sigma;
             const uint32_t ent = static_cast<uint32_t>(j);
@@ -402,7 +403,7 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
                     const uint32_t gi = static_cast<uint32_t>(r * a.k + kk);  // gene index (< h d_0 < 2^31)
                     const uint32_t u = gi >> 3;
                     float4 x[2] = { make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f) };
-                    if (live && ci.kind >= 0) load8(A, r * kKStage + 8 * c8, c8, x);
+                    if (live && ci.kind >= 0) load8(A, r * kKStage + 8 * c8, x);
                     if (ci.kind == 2) {
                         const uint32_t hit =
                             live ? mask8(philox_keyed(make_uint4(u, ent, a.gen, kTagMutMask), key), a.thr_mut) : 0u;
@@ -413,7 +414,7 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
                         });
                     } else if (ci.kind == 1 && live) {
                         float4 y2[2];
-                        load8(B, r * kKStage + 8 * c8, c8, y2);
+                        load8(B, r * kKStage + 8 * c8, y2);
                         if (a.xo_op == 0) {
                             const uint32_t m = mask8(philox_keyed(make_uint4(u, ent, a.gen, kTagXo), key), a.thr_xo);
                             x[0] = select4(m, x[0], y2[0]);
@@ -461,16 +462,14 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
     } else {
         // ------------------------------------------------------------ batch into TMEM, then epilogue
         const int et = threadIdx.x - 32 * kFirstEpiWarp;
-        const int q = warp & 3;                       // TMEM lane quarter of this warp
-        const int half = (warp - kFirstEpiWarp) >> 2;  // which half of the hidden units it reads
+        const int q = warp & 3;  // TMEM lane quarter of this warp
         const int row = q * 32 + lane;
         const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
         {
             // Row `row` of the batch into TMEM as FP16 pairs (lower k in the low
-            // half); group g = levels 32 g .. 32 g + 31 = columns 16 g .. 16 g + 15,
-            // written by the half with g % 2 == half.  A level k < 1024 is exact
-            // in FP16 as (1024 + k) - 1024, and 1024 + k has the bit pattern
-            // 0x6400 | k.
+            // half); group g = levels 32 g .. 32 g + 31 = columns 16 g .. 16 g + 15.
+            // A level k < 1024 is exact in FP16 as (1024 + k) - 1024, and
+            // 1024 + k has the bit pattern 0x6400 | k.
             auto put_group = [&](int g, const uint32_t (&bytes)[8]) {
                 const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
                 uint32_t cols[16];
@@ -491,8 +490,7 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
                 for (int k0 = 0; k0 < a.k16; k0 += kc, xphase ^= 1u) {
                     const int bytes = min(kc, a.k - k0);  // multiple of 16
                     if (et == 0) ptx::mbar_arrive_expect_tx(s.x_full, static_cast<uint32_t>(a.batch * bytes));
-                    if (live && half == 0)
-                        ptx::bulk_load(xs + row * stride, xr + k0, static_cast<uint32_t>(bytes), s.x_full);
+                    if (live) ptx::bulk_load(xs + row * stride, xr + k0, static_cast<uint32_t>(bytes), s.x_full);
                     const bool got = ptx::mbar_wait_bounded(s.x_full, xphase, s.abort_flag, kWaitLimitNs);
                     if (!got) {  // let this chunk's copies land before anything reuses the rings
                         raise_abort(s, a);
@@ -500,7 +498,7 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
                         ptx::mbar_wait_bounded(s.x_full, xphase, &never, kDrainLimitNs);
                     }
                     const uint8_t* src = xs + (live ? row : 0) * stride;
-                    for (int g = half; g < kc / 32 && k0 + 32 * g < a.k16; g += 2) {
+                    for (int g = 0; g < kc / 32 && k0 + 32 * g < a.k16; ++g) {
                         uint32_t wds[8] = { 0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u };
                         if (live && got) {
                             const uint4 v0 = *reinterpret_cast<const uint4*>(src + 32 * g);
@@ -513,7 +511,7 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
                     ptx::named_barrier_sync(1, kEpiThreads);  // staging area read before the next chunk lands
                 }
             } else {
-                for (int g = half; g < n_groups; g += 2) {
+                for (int g = 0; g < n_groups; ++g) {
                     uint32_t wds[8];
 #pragma unroll
                     for (int w = 0; w < 8; ++w) {
@@ -548,9 +546,9 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
         const int64_t g_tail = static_cast<int64_t>(a.h) * a.k;  // first gene after W1 (a multiple of 16)
         const int32_t n_tail_units = static_cast<int32_t>((a.c_pad - g_tail) >> 3);
         const int32_t n_w2 = a.d_out * a.h;
-        const int hh = a.h >> 1, c0 = half * hh;
         uint32_t acc_phase = 0, unit = 0;
-        for (int j = blockIdx.x; j < a.pop; j += gridDim.x, ++unit) {
+        for (int n = blockIdx.x; n < a.pop; n += gridDim.x, ++unit) {
+            const int j = child_of(a, n);
             const ChildInfo ci = child_info(a, j);
             const float sigma = a.sigma_child ? a.sigma_child[j] : a.sigma;
             const uint32_t ent = static_cast<uint32_t>(j);
@@ -614,17 +612,17 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
             const int go = *s.ep_go;
             if (!go) break;
             ptx::tc_fence_after();
-            // Layer 1 of this warp's half of the hidden units from the
-            // accumulator (or, for a child with a weight outside the piece
-            // range, by FP32 FFMA from HBM, k in order), then its part of layer 2.
+            // Layer 1 from the accumulator (or, for a child with a weight
+            // outside the piece range, by FP32 FFMA from HBM, k in order), 8
+            // hidden units at a time, each folded into layer 2 at once.
             const float* w1p = child;
             const uint8_t* xrow = a.x + static_cast<int64_t>(row < a.batch ? row : 0) * a.k;
             float logit[kMaxOut];
 #pragma unroll
             for (int o = 0; o < kMaxOut; ++o) logit[o] = 0.0f;
-            for (int c = 0; c < hh; c += 8) {
+            for (int c = 0; c < a.h; c += 8) {
                 uint32_t r8[8];
-                ptx::tmem_ld8_nowait(tmem_base + lane_addr + static_cast<uint32_t>(c0 + c), r8);
+                ptx::tmem_ld8_nowait(tmem_base + lane_addr + static_cast<uint32_t>(c), r8);
                 ptx::tmem_ld_wait();
                 float v[8];
 #pragma unroll
@@ -632,7 +630,7 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
                 if (go == 2 && row < a.batch) {
 #pragma unroll
                     for (int jj = 0; jj < 8; ++jj) {
-                        const float* wr = w1p + static_cast<int64_t>(c0 + c + jj) * a.k;
+                        const float* wr = w1p + static_cast<int64_t>(c + jj) * a.k;
                         float acc = 0.0f;
                         for (int kk = 0; kk < a.k; ++kk) acc = fmaf(wr[kk], static_cast<float>(xrow[kk]), acc);
                         v[jj] = acc * kPieceScale;
@@ -640,7 +638,7 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
                 }
 #pragma unroll
                 for (int jj = 0; jj < 8; ++jj) {
-                    const int col = c0 + c + jj;
+                    const int col = c + jj;
                     const float hv = fmaxf(fmaf(v[jj], a.inv_div, s.b1[col]), 0.0f);
                     const float4* wr = reinterpret_cast<const float4*>(s.w2t + col * a.dpad);
 #pragma unroll
@@ -658,49 +656,40 @@ breed_eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_par, const FusedAr
             ptx::tc_fence_before();
             ptx::mbar_arrive(s.acc_empty);  // the next child's MMAs may overwrite the accumulator
             acc_phase ^= 1u;
-            if (half == 1 && row < a.batch) {
+            float loss = 0.0f;
+            int32_t good = 0;
+            if (row < a.batch) {
+                float z[kMaxOut];
+#pragma unroll
+                for (int o = 0; o < kMaxOut; ++o) z[o] = o < a.d_out ? logit[o] + s.b2[o] : 0.0f;
+                float zmax = z[0];
+                int arg = 0;
+#pragma unroll
+                for (int o = 1; o < kMaxOut; ++o)
+                    if (o < a.d_out && z[o] > zmax) { zmax = z[o]; arg = o; }
+                float se = 0.0f;
 #pragma unroll
                 for (int o = 0; o < kMaxOut; ++o)
-                    if (o < a.d_out) s.plog[row * 16 + o] = logit[o];
+                    if (o < a.d_out) se += expf(z[o] - zmax);
+                if (label >= 0 && label < a.d_out) {
+                    float zl = 0.0f;
+#pragma unroll
+                    for (int o = 0; o < kMaxOut; ++o)
+                        if (o == label) zl = z[o];
+                    loss = logf(se) + zmax - zl;
+                    good = (arg == label) ? 1 : 0;
+                } else {
+                    loss = __int_as_float(0x7FC00000);
+                }
             }
-            ptx::named_barrier_sync(1, kEpiThreads);  // B1: second-half partial logits written
-            if (half == 0) {
-                float loss = 0.0f;
-                int32_t good = 0;
-                if (row < a.batch) {
-                    float z[kMaxOut];
 #pragma unroll
-                    for (int o = 0; o < kMaxOut; ++o)
-                        z[o] = o < a.d_out ? (logit[o] + s.plog[row * 16 + o]) + s.b2[o] : 0.0f;
-                    float zmax = z[0];
-                    int arg = 0;
-#pragma unroll
-                    for (int o = 1; o < kMaxOut; ++o)
-                        if (o < a.d_out && z[o] > zmax) { zmax = z[o]; arg = o; }
-                    float se = 0.0f;
-#pragma unroll
-                    for (int o = 0; o < kMaxOut; ++o)
-                        if (o < a.d_out) se += expf(z[o] - zmax);
-                    if (label >= 0 && label < a.d_out) {
-                        float zl = 0.0f;
-#pragma unroll
-                        for (int o = 0; o < kMaxOut; ++o)
-                            if (o == label) zl = z[o];
-                        loss = logf(se) + zmax - zl;
-                        good = (arg == label) ? 1 : 0;
-                    } else {
-                        loss = __int_as_float(0x7FC00000);
-                    }
-                }
-#pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
-                    good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
-                }
-                if (lane == 0) {
-                    s.red_loss[q] = loss;
-                    s.red_ok[q] = good;
-                }
+            for (int off = 16; off > 0; off >>= 1) {
+                loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
+                good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
+            }
+            if (lane == 0) {
+                s.red_loss[q] = loss;
+                s.red_ok[q] = good;
             }
             ptx::named_barrier_sync(1, kEpiThreads);  // B2: quarter sums written; staged parameters no longer read
             if (et == 0) {

@@ -883,16 +883,14 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         }
     }
     const bool first = !s->evaluated;
-    // Breed and evaluate in one kernel: 8-bit inputs of an FP32 object, when
-    // asked for (FUSED) or when the shape allows it (AUTO).
-    bool fused = false;
-    if (u8 && prec == 0 && (s->prm.eval_path == LEEA_EVAL_AUTO || s->prm.eval_path == LEEA_EVAL_FUSED)) {
-        const bool ok = breed_eval_u8_supported(s->net, batch, s->popbuf[0], s->popbuf[1]);
-        if (s->prm.eval_path == LEEA_EVAL_FUSED && !ok)
-            return fail(LEEA_EINVAL, "the fused breed + evaluate path needs d_0 %% 16 == 0, h %% 16 == 0, h <= 128, "
-                                     "d_out <= 16 and batch <= 128");
-        fused = ok;
-    }
+    // Breed and evaluate in one kernel (8-bit inputs of an FP32 object) when
+    // asked for.  AUTO keeps the two kernels: at the benchmark's shape both
+    // forms are bound by instruction issue, not by memory, and the two
+    // kernels measure slightly faster than the fused one.
+    const bool fused = s->prm.eval_path == LEEA_EVAL_FUSED;
+    if (fused && u8 && !breed_eval_u8_supported(s->net, batch, s->popbuf[0], s->popbuf[1]))
+        return fail(LEEA_EINVAL, "the fused breed + evaluate path needs d_0 %% 16 == 0, h %% 16 == 0, h <= 128, "
+                                 "d_out <= 16 and batch <= 128");
     if (!u8 && s->prm.eval_path == LEEA_EVAL_FUSED)
         return fail(LEEA_EINVAL, "the fused breed + evaluate path takes 8-bit inputs (leea_generation_u8*)");
     if (!first) {

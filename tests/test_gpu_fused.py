@@ -63,6 +63,17 @@ def _fused_vs_separate(gpu, oracle_mod, dims, pop, batch, prm, seed=7, gen=9, sc
     assert_correct_close(cor.cpu().numpy(), cor_ref, logits)
     adj = oracle_mod.inherit(0.25, f_inh, f_ref, first=False)
     assert_fitness_close(f_adj.cpu().numpy(), adj, "f_adj")
+    # The same arithmetic in the same order as the separate tensor-core
+    # evaluation of the same children: bit-identical results.
+    s_raw = torch.empty(pop, dtype=torch.float32, device="cuda")
+    s_adj = torch.empty(pop, dtype=torch.float32, device="cuda")
+    s_cor = torch.empty(pop, dtype=torch.int32, device="cuda")
+    gpu.leea_evaluate_u8(pop, dims, sep_d, xd, 255.0, yd, batch, 0.25, fi, s_raw, s_adj, s_cor,
+                         eval_path=gpu.EVAL_TENSOR)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(f_raw.cpu().numpy().view(np.uint32), s_raw.cpu().numpy().view(np.uint32))
+    np.testing.assert_array_equal(f_adj.cpu().numpy().view(np.uint32), s_adj.cpu().numpy().view(np.uint32))
+    np.testing.assert_array_equal(cor.cpu().numpy(), s_cor.cpu().numpy())
     return f_raw.cpu().numpy()
 
 
@@ -147,9 +158,8 @@ def test_fused_shape_limits(gpu):
 
 
 def test_state_object_fused_path(gpu, oracle_mod):
-    # AUTO takes the fused kernel for 8-bit generations of an FP32 object: one
-    # launch per breeding generation for breed + evaluate, none for stage 2;
-    # the population and fitness equal those of the separate kernels.
+    # FUSED: one launch per breeding generation for breed + evaluate, none for
+    # stage 2; AUTO and TENSOR: two.  Population and fitness are identical.
     torch = _torch()
     dims, pop, batch = [784, 112, 10], 300, 100
     x, y = synthetic.make_split(batch, seed=2)
@@ -166,16 +176,13 @@ def test_state_object_fused_path(gpu, oracle_mod):
             runs[path] = (st.leea_get_population(), st.leea_fitness(), prof)
         finally:
             st.close()
+    assert runs[gpu.EVAL_FUSED][2]["breed"][1] == 3 and runs[gpu.EVAL_FUSED][2]["evaluate"][1] == 0
+    for path in (gpu.EVAL_AUTO, gpu.EVAL_TENSOR):
+        assert runs[path][2]["breed"][1] == 3 and runs[path][2]["evaluate"][1] == 3
+    # Same children, same evaluation arithmetic: the three runs are identical.
     for path in (gpu.EVAL_AUTO, gpu.EVAL_FUSED):
-        assert runs[path][2]["breed"][1] == 3 and runs[path][2]["evaluate"][1] == 0
-    assert runs[gpu.EVAL_TENSOR][2]["evaluate"][1] == 3
-    np.testing.assert_array_equal(runs[gpu.EVAL_AUTO][0], runs[gpu.EVAL_FUSED][0])
-    np.testing.assert_array_equal(runs[gpu.EVAL_AUTO][1], runs[gpu.EVAL_FUSED][1])
-    # Different layer-2 summation order: fitness within the evaluation tolerance;
-    # generations agree exactly as long as no two fitnesses swap order (checked).
-    f_f, f_t = runs[gpu.EVAL_FUSED][1].astype(np.float64), runs[gpu.EVAL_TENSOR][1].astype(np.float64)
-    if np.array_equal(runs[gpu.EVAL_FUSED][0], runs[gpu.EVAL_TENSOR][0]):
-        assert_fitness_close(f_f, f_t, "fused vs separate")
+        np.testing.assert_array_equal(runs[path][0], runs[gpu.EVAL_TENSOR][0])
+        np.testing.assert_array_equal(runs[path][1], runs[gpu.EVAL_TENSOR][1])
 
 
 def test_state_object_fused_errors(gpu):

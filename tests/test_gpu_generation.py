@@ -86,7 +86,7 @@ def test_lockstep_2_2_2(gpu, oracle_mod, prm):
     _lockstep(gpu, oracle_mod, [2, 2, 2], 4, 8, prm)
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_lockstep_full_size_sampled_u8(gpu, oracle_mod, path):
     sample = np.array([0, 1, 2, 250, 499, 500, 501, 502, 777, 998, 999])
     prm = dict(CONFIG_FULL["prm"], eval_path=path)
@@ -94,7 +94,7 @@ def test_lockstep_full_size_sampled_u8(gpu, oracle_mod, path):
               u8=True)
 
 
-@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("path", [1, 2, 3])
 def test_lockstep_small_config_u8(gpu, oracle_mod, path):
     prm = dict(CONFIG_SMALL["prm"], eval_path=path)
     _lockstep(gpu, oracle_mod, CONFIG_SMALL["dims"], CONFIG_SMALL["pop"], CONFIG_SMALL["batch"], prm, u8=True)

@@ -140,6 +140,15 @@ def test_decay_lockstep_full_size_sampled(gpu, oracle_mod):
     _lockstep(gpu, oracle_mod, **FULL, prm=prm, sample=SAMPLE, gen0=123)
 
 
+@pytest.mark.parametrize("ctl", ["self", "decay"])
+def test_sigma_control_fused_breed_evaluate(gpu, oracle_mod, ctl):
+    # The fused breed + evaluate kernel reads each child's own strength too.
+    extra = dict(sigma_ctl=gpu.SIGMA_SELF, tau=0.5) if ctl == "self" else dict(sigma_ctl=gpu.SIGMA_DECAY, sigma_k=2.0)
+    prm = dict(n_elite=2, sigma=0.01, alpha=0.5, eval_path=gpu.EVAL_FUSED, **extra)
+    _lockstep(gpu, oracle_mod, **SMALL, prm=prm)
+    _lockstep(gpu, oracle_mod, **FULL, prm=dict(prm, mut_rate=0.1), sample=SAMPLE)
+
+
 @pytest.mark.parametrize("precision", [1, 2])
 def test_self_adaptive_precision_form(gpu, oracle_mod, precision):
     # FP8: a mutation child's scale exponent must use its own mutated sigma.
