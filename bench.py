@@ -87,7 +87,7 @@ STAGES = ("select", "breed", "evaluate")
 TRAFFIC = {
     "breed": {"bytes_per_launch": 706.54e6, "src_sha": "53af562611246ce0", "capture": "P=1000 plain workload"},
     "evaluate": {"bytes_per_launch": 359.37e6, "src_sha": "d972b174f2e01544", "capture": "P=1000 plain workload"},
-    "breed_evaluate": {"bytes_per_launch": None, "src_sha": None, "capture": "P=1000 plain workload"},
+    "breed_evaluate": {"bytes_per_launch": 738.19e6, "src_sha": "23e25d83744d9797", "capture": "P=1000 plain workload"},
 }
 
 
