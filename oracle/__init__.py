@@ -130,6 +130,7 @@ def lib() -> ctypes.CDLL:
         L.leea_cpu_init.argtypes = [i32, vp, i32, i32, u64, vp]
         L.leea_cpu_evaluate.argtypes = [i32, vp, i32, vp, vp, vp, i32, vp, vp, vp]
         L.leea_cpu_rank.argtypes = [i32, vp, vp]
+        L.leea_cpu_maxpool2x2.argtypes = [i32, i32, i32, vp, vp]
         L.leea_cpu_select.argtypes = [i32, P(_CParams), vp, vp, u64, u32, vp, vp, vp, vp]
         L.leea_cpu_breed.argtypes = [i32, vp, i32, P(_CParams), u64, u32, vp, vp, vp, vp, i32, i32, vp]
         L.leea_cpu_inherit.argtypes = [i32, dbl, vp, vp, i32, vp]
@@ -314,6 +315,14 @@ def evaluate(popv, dims, x, y, want_logits: bool = False):
     _check(lib().leea_cpu_evaluate(pop, _ptr(d), len(d), _ptr(pv), _ptr(xv), _ptr(yv), batch,
                                    _ptr(f), _ptr(cor), _ptr(logits)), "evaluate")
     return (f, cor, logits) if want_logits else (f, cor)
+
+
+def maxpool2x2(x, h: int, w: int) -> np.ndarray:
+    """Section 4.1's input stage: 2x2 max-pooling of images x[b] (h x w, row-major)."""
+    xv = _f64(x).reshape(-1, h * w)
+    out = np.empty((xv.shape[0], (h // 2) * (w // 2)), dtype=np.float64)
+    _check(lib().leea_cpu_maxpool2x2(xv.shape[0], h, w, _ptr(xv), _ptr(out)), "maxpool2x2")
+    return out
 
 
 def rank(f_adj) -> np.ndarray:

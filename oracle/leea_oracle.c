@@ -203,6 +203,34 @@ int leea_cpu_init(int32_t pop, const int32_t* dims, int32_t n_dims, int32_t init
 }
 
 /* ------------------------------------------------------------------------ */
+/* Input stage of the paper's network (Section 4.1): 2x2 max-pooling          */
+/* ------------------------------------------------------------------------ */
+int leea_cpu_maxpool2x2(int32_t batch, int32_t h, int32_t w, const double* x, double* out)
+{
+    if (batch < 0 || h <= 0 || w <= 0 || (h & 1) || (w & 1) || (batch > 0 && (!x || !out)))
+        return LEEA_CPU_EINVAL;
+    int32_t ho = h / 2, wo = w / 2;
+    for (int32_t b = 0; b < batch; b++) {
+        const double* img = x + (int64_t)b * h * w;
+        double* o = out + (int64_t)b * ho * wo;
+        for (int32_t i = 0; i < ho; i++) {
+            for (int32_t j = 0; j < wo; j++) {
+                double m = img[(2 * i) * w + 2 * j];
+                double c;
+                c = img[(2 * i) * w + 2 * j + 1];
+                if (c > m) m = c;
+                c = img[(2 * i + 1) * w + 2 * j];
+                if (c > m) m = c;
+                c = img[(2 * i + 1) * w + 2 * j + 1];
+                if (c > m) m = c;
+                o[i * wo + j] = m;
+            }
+        }
+    }
+    return LEEA_CPU_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Fitness (Eq. 1): negative mean cross-entropy of the softmax output over   */
 /* the batch; hidden layers use ReLU (Section 4.1).  Also counts correct    */
 /* argmax predictions, ties to the lowest class.                            */

@@ -101,6 +101,11 @@ int leea_cpu_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
                       const double* popv, const double* x, const int32_t* y,
                       int32_t batch, double* f_out, int32_t* correct_out,
                       double* logits_out);
+/* The input stage of the paper's network (Section 4.1): 2x2 max-pooling of
+ * each image x[b] (h rows of w pixels, row-major; h and w even) into
+ * out[b] ((h/2) x (w/2), row-major): out[i][j] is the largest of the four
+ * pixels (2i, 2j), (2i, 2j+1), (2i+1, 2j), (2i+1, 2j+1). */
+int leea_cpu_maxpool2x2(int32_t batch, int32_t h, int32_t w, const double* x, double* out);
 int leea_cpu_rank(int32_t pop, const double* f_adj, int32_t* order);
 int leea_cpu_select(int32_t pop, const leea_cpu_params* prm, const double* f_adj,
                     const int32_t* order, uint64_t seed, uint32_t gen,

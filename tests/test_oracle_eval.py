@@ -124,3 +124,20 @@ def test_bad_labels_are_rejected(oracle_mod):
     popv = np.zeros((1, oracle_mod.num_params(dims)))
     with pytest.raises(oracle_mod.OracleError):
         oracle_mod.evaluate(popv, dims, np.ones((2, 4)), np.array([0, 2], dtype=np.int32))
+
+
+def test_maxpool_matches_library_reduction(oracle_mod):
+    # Section 4.1's input stage against numpy's reshape-and-max on 28x28 images
+    # (and a non-square shape); ties and the block layout decide every value.
+    rng = np.random.default_rng(8)
+    for h, w, n in ((28, 28, 17), (6, 10, 3)):
+        x = rng.integers(0, 256, size=(n, h, w)).astype(np.float64)
+        x[0, :2, :2] = 7.0  # a block of equal pixels
+        ref = x.reshape(n, h // 2, 2, w // 2, 2).max(axis=(2, 4)).reshape(n, -1)
+        np.testing.assert_array_equal(oracle_mod.maxpool2x2(x, h, w), ref)
+    # The pixel positions matter: a single bright pixel lands in its block.
+    x = np.zeros((1, 4, 4))
+    x[0, 3, 0] = 5.0
+    np.testing.assert_array_equal(oracle_mod.maxpool2x2(x, 4, 4), [[0.0, 0.0, 5.0, 0.0]])
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.maxpool2x2(np.zeros((1, 3 * 4)), 3, 4)
