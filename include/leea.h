@@ -232,6 +232,17 @@ leea_status leea_breed(int32_t pop, const int32_t* dims, int32_t n_dims,
                        const int32_t* par2_dev, const int32_t* kind_dev,
                        float* children_dev, void* stream);
 
+/* The input stage of the paper's network (Section 4.1): 2x2 max-pooling of
+ * each image x[b] (h rows of w values, row-major; h and w even) into
+ * out[b] ((h/2) x (w/2), row-major), out[i][j] = the largest of the pixels
+ * (2i, 2j), (2i, 2j+1), (2i+1, 2j), (2i+1, 2j+1).  For 8-bit levels the max
+ * of levels is a level, so pooling commutes with x = k / x_div.
+ * x_dev: [batch][h*w]; out_dev: [batch][(h/2)*(w/2)]. */
+leea_status leea_maxpool2x2(int32_t batch, int32_t h, int32_t w, const float* x_dev,
+                            float* out_dev, void* stream);
+leea_status leea_maxpool2x2_u8(int32_t batch, int32_t h, int32_t w, const uint8_t* x_dev,
+                               uint8_t* out_dev, void* stream);
+
 /* leea_breed followed by leea_evaluate_u8 of the children with inheritance
  * (Section 3.2, Eq. 1, Section 3.1), in one kernel: each child is made in
  * shared memory from its parents, written to children_dev and evaluated from
@@ -258,7 +269,10 @@ leea_status leea_breed_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_d
  * lowest class); f_adj = (1 - alpha) f_inh + alpha f, or f_adj = f when
  * f_inh_dev is NULL (the first evaluation).  Reductions have a fixed order,
  * so identical individuals get bitwise identical results.
- * n_dims must be 3 (d_0-h-d_out with d_out <= 32).  f_adj_dev and
+ * n_dims == 3 (d_0-h-d_out with d_out <= 32), or n_dims > 3 with every layer
+ * input and hidden width <= 256 and d_out <= 32 (the paper's 196-256-128-64-10,
+ * Section 4.1): such nets evaluate in FP32 on the CUDA cores (eval_path AUTO
+ * or SIMT), layer by layer with ReLU between layers.  f_adj_dev and
  * correct_dev may be NULL; f_raw_dev may not.  eval_path: LEEA_EVAL_*. */
 leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
                           const float* pop_dev, const float* x_dev, const int32_t* y_dev,
@@ -373,7 +387,10 @@ typedef struct leea_state leea_state;
 
 /* Allocates two population buffers of pop x c_pad floats plus per-individual
  * arrays on the current device, and enqueues the initialisation on `stream`,
- * which every later call of this object uses.  *out receives the object. */
+ * which every later call of this object uses.  *out receives the object.
+ * Nets: n_dims == 3 with d_out <= 32, or n_dims > 3 (several hidden layers,
+ * every layer input and hidden width <= 256, d_out <= 32; precision 0,
+ * eval_path AUTO or SIMT: FP32 on the CUDA cores). */
 leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims,
                         const leea_params* p, uint64_t seed, void* stream,
                         leea_state** out);

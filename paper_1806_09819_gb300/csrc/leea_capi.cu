@@ -201,6 +201,12 @@ leea_status dispatch_eval(const NetLayout& net, int32_t pop, const float* pop_de
                           const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
                           float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream)
 {
+    if (net.n_layers > 2) {  // several hidden layers: CUDA-core FP32
+        if (path == LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "nets with several hidden layers evaluate on CUDA cores");
+        LEEA_CUDA_TRY(launch_eval_mlp(net, pop, pop_dev, x, y, batch, alpha, f_inh, f_raw, f_adj, correct, stream),
+                      "evaluate kernel");
+        return LEEA_OK;
+    }
     const bool tc_ok = eval_tc_supported(net, batch, pop_dev, x);
     if (path == LEEA_EVAL_TENSOR && !tc_ok)
         return fail(LEEA_EINVAL, "tensor-core evaluation needs d_0 %% 4 == 0, h %% 16 == 0, h <= 256, "
@@ -223,6 +229,13 @@ leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop
                              float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream)
 {
     if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
+    if (net.n_layers > 2) {  // several hidden layers: CUDA-core FP32
+        if (path == LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "nets with several hidden layers evaluate on CUDA cores");
+        LEEA_CUDA_TRY(launch_eval_mlp_u8(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
+                                         stream),
+                      "evaluate kernel");
+        return LEEA_OK;
+    }
     const bool tc_ok = eval_u8_tc_supported(net, batch, pop_dev);
     if (path == LEEA_EVAL_TENSOR && !tc_ok)
         return fail(LEEA_EINVAL, "tensor-core evaluation of 8-bit inputs needs batch <= 128, d_0 %% 4 == 0, "
@@ -250,8 +263,10 @@ leea_status check_pop(int32_t pop)
 
 leea_status check_eval_shape(const NetLayout& net, int32_t batch)
 {
-    if (net.n_layers != 2) return fail(LEEA_EINVAL, "evaluation supports n_dims == 3 (d_0-h-d_out)");
-    if (net.dims[2] > 32) return fail(LEEA_EINVAL, "evaluation supports d_out <= 32");
+    if (net.n_layers < 2) return fail(LEEA_EINVAL, "evaluation needs a hidden layer (n_dims >= 3)");
+    if (net.dims[net.n_layers] > 32) return fail(LEEA_EINVAL, "evaluation supports d_out <= 32");
+    if (net.n_layers > 2 && !eval_mlp_supported(net))
+        return fail(LEEA_EINVAL, "nets with several hidden layers need every layer input and hidden width <= 256");
     if (batch <= 0) return fail(LEEA_EINVAL, "batch must be >= 1");
     return LEEA_OK;
 }
@@ -520,6 +535,26 @@ leea_status leea_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims, c
     if (eval_path < LEEA_EVAL_AUTO || eval_path > LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "bad eval_path");
     return dispatch_eval_u8(net, pop, pop_dev, x_u8_dev, x_div, y_dev, batch, alpha, f_inh_dev, f_raw_dev, f_adj_dev,
                             correct_dev, eval_path, static_cast<cudaStream_t>(stream));
+}
+
+leea_status leea_maxpool2x2(int32_t batch, int32_t h, int32_t w, const float* x_dev, float* out_dev, void* stream)
+{
+    if (batch < 0 || h <= 0 || w <= 0 || (h & 1) || (w & 1))
+        return fail(LEEA_EINVAL, "max-pooling needs batch >= 0 and even h, w >= 2");
+    if (batch > 0 && (!x_dev || !out_dev)) return fail(LEEA_EINVAL, "NULL device pointer");
+    LEEA_CUDA_TRY(launch_maxpool2x2(batch, h, w, x_dev, out_dev, static_cast<cudaStream_t>(stream)), "max-pool kernel");
+    return LEEA_OK;
+}
+
+leea_status leea_maxpool2x2_u8(int32_t batch, int32_t h, int32_t w, const uint8_t* x_dev, uint8_t* out_dev,
+                               void* stream)
+{
+    if (batch < 0 || h <= 0 || w <= 0 || (h & 1) || (w & 1))
+        return fail(LEEA_EINVAL, "max-pooling needs batch >= 0 and even h, w >= 2");
+    if (batch > 0 && (!x_dev || !out_dev)) return fail(LEEA_EINVAL, "NULL device pointer");
+    LEEA_CUDA_TRY(launch_maxpool2x2_u8(batch, h, w, x_dev, out_dev, static_cast<cudaStream_t>(stream)),
+                  "max-pool kernel");
+    return LEEA_OK;
 }
 
 int64_t leea_shadow_stride(const int32_t* dims, int32_t n_dims, int32_t precision)
@@ -802,9 +837,16 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         delete s;
         return fail(LEEA_EINVAL, "invalid dims");
     }
-    if (s->net.n_layers != 2 || s->net.dims[2] > 32) {
+    if (s->net.n_layers < 2 || s->net.dims[s->net.n_layers] > 32 ||
+        (s->net.n_layers > 2 && !eval_mlp_supported(s->net))) {
         delete s;
-        return fail(LEEA_EINVAL, "the state object evaluates d_0-h-d_out nets (n_dims == 3, d_out <= 32)");
+        return fail(LEEA_EINVAL, "the state object evaluates nets with hidden layers (n_dims >= 3), d_out <= 32, and "
+                                 "with several hidden layers every layer input and hidden width <= 256");
+    }
+    if (s->net.n_layers > 2 && (p->precision != 0 || p->eval_path == LEEA_EVAL_TENSOR ||
+                                p->eval_path == LEEA_EVAL_FUSED)) {
+        delete s;
+        return fail(LEEA_EINVAL, "nets with several hidden layers evaluate in FP32 on the CUDA cores");
     }
     if (p->precision != 0 && (st = check_shadow_shape(s->net, p->precision))) {
         delete s;

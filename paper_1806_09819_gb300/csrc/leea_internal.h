@@ -225,6 +225,19 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
                               float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
                               float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
                               cudaStream_t stream);
+// Evaluation of nets with several hidden layers (n_dims >= 3; every layer
+// input and hidden width <= 256, d_out <= 32), FP32 on the CUDA cores; and the
+// 2x2 max-pooling input stage of the paper's network (h, w even).
+bool eval_mlp_supported(const NetLayout& net);
+cudaError_t launch_eval_mlp(const NetLayout& net, int32_t pop, const float* pop_dev, const float* x, const int32_t* y,
+                            int32_t batch, float alpha, const float* f_inh, float* f_raw, float* f_adj,
+                            int32_t* correct, cudaStream_t stream);
+cudaError_t launch_eval_mlp_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
+                               const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                               float* f_adj, int32_t* correct, cudaStream_t stream);
+cudaError_t launch_maxpool2x2(int32_t batch, int32_t h, int32_t w, const float* x, float* out, cudaStream_t stream);
+cudaError_t launch_maxpool2x2_u8(int32_t batch, int32_t h, int32_t w, const uint8_t* x, uint8_t* out,
+                                 cudaStream_t stream);
 // Crossover, mutation and evaluation of every child in one kernel (8-bit
 // inputs; d_0 % 16 == 0, h % 16 == 0, h <= 128, d_out <= 16, batch <= 128,
 // 16-byte aligned populations).  Operators and streams from b (b.pop children

@@ -108,6 +108,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_rank": [i32, vp, vp, vp],
         "leea_select": [i32, P(leea_params), vp, vp, u64, u32, vp, vp, vp, vp, vp],
         "leea_breed": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp],
+        "leea_maxpool2x2": [i32, i32, i32, vp, vp, vp],
+        "leea_maxpool2x2_u8": [i32, i32, i32, vp, vp, vp],
         "leea_breed_evaluate_u8": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, vp, f32, vp, i32, f32,
                                    vp, vp, vp, vp, vp],
         "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, i32, vp],
@@ -209,6 +211,7 @@ def exported_symbols() -> list[str]:
     """Names of the entry points the binding expects the library to export."""
     return ["leea_default_params", "leea_num_params", "leea_padded_params", "leea_counts",
             "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_breed_evaluate_u8",
+            "leea_maxpool2x2", "leea_maxpool2x2_u8",
             "leea_evaluate",
             "leea_device_status", "leea_evaluate_u8", "leea_generation_u8", "leea_generation_u8_host",
             "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
@@ -316,6 +319,12 @@ def leea_breed(pop: int, dims, prm: Params, seed: int, gen: int, parents_dev, pa
     _check(load_library().leea_breed(pop, _hp(d), len(d), ctypes.byref(cp), seed, gen, _dptr(parents_dev),
                                      _dptr(par1_dev), _dptr(par2_dev), _dptr(kind_dev), _dptr(children_dev),
                                      _stream(stream)))
+
+
+def leea_maxpool2x2(batch: int, h: int, w: int, x_dev, out_dev, stream=None) -> None:
+    """2x2 max-pooling of [batch][h*w] images (float32 or uint8 tensors) into [batch][(h/2)*(w/2)]."""
+    fn = load_library().leea_maxpool2x2_u8 if x_dev.dtype.itemsize == 1 else load_library().leea_maxpool2x2
+    _check(fn(int(batch), int(h), int(w), _dptr(x_dev), _dptr(out_dev), _stream(stream)))
 
 
 def leea_breed_evaluate_u8(pop: int, dims, prm: Params, seed: int, gen: int, parents_dev, par1_dev, par2_dev,

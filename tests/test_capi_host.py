@@ -100,9 +100,14 @@ def test_argument_errors_are_reported_before_any_work(lib):
     n = ctypes.c_void_p(16)  # never dereferenced: the check comes first
     rc = lib.leea_select(10, ctypes.byref(self_p), n, n, 1, 1, n, n, n, n, None)
     assert rc == leea.EINVAL and b"sigma_ctl" in lib.leea_last_error()
-    d4 = np.array([196, 256, 128, 64, 10], dtype=np.int32)
+    # Several hidden layers: every layer input and hidden width <= 256, FP32 only.
     good = leea.Params().c_struct()
+    d4 = np.array([784, 256, 128, 64, 10], dtype=np.int32)
     rc = lib.leea_create(10, d4.ctypes.data_as(ctypes.c_void_p), 5, ctypes.byref(good), 1, None, ctypes.byref(h))
+    assert rc == leea.EINVAL and b"256" in lib.leea_last_error()
+    d4 = np.array([196, 256, 128, 64, 10], dtype=np.int32)
+    bf16 = leea.Params(precision=1).c_struct()
+    rc = lib.leea_create(10, d4.ctypes.data_as(ctypes.c_void_p), 5, ctypes.byref(bf16), 1, None, ctypes.byref(h))
     assert rc == leea.EINVAL
 
 
