@@ -286,8 +286,8 @@ def test_evaluate_bad_label_gives_nan_and_errors(gpu):
     assert np.isnan(f_raw.cpu().numpy()).all()
     with pytest.raises(gpu.LeeaError):
         gpu.leea_evaluate(2, dims, pd, x, y, 0, 1.0, None, f_raw)
-    with pytest.raises(gpu.LeeaError):
-        gpu.leea_evaluate(2, [4, 3, 3, 2], pd, x, y, 3, 1.0, None, f_raw)
+    with pytest.raises(gpu.LeeaError):  # d_out > 32: rejected before any launch
+        gpu.leea_evaluate(2, [4, 3, 3, 40], pd, x, y, 3, 1.0, None, f_raw)
 
 
 # ---- evaluation of 8-bit inputs (x = k / 255) ------------------------------------------------
