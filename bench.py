@@ -8,7 +8,7 @@ breed, evaluate).  The population (2 x 356 MB) is larger than L2, so no flush
 is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--config plain|precision-bf16|precision-fp8|batching|surrogate]
+                    [--config plain|precision-bf16|precision-fp8|batching|surrogate|paper-net]
 
 --config precision-* measures the precision form instead (P = 4096 nets
 784-112-10, batch 256, BF16 or FP8-e4m3 shadows of W1 with FP32 accumulation
@@ -51,7 +51,14 @@ WORKLOAD = ("P=1000 MLPs 784-112-10 (89,050 params, FP32), batch 100 synthetic 2
             "p_C=0.5, truncation rho=0.5, elitism 1, mutation sigma=0.005 on 10% of genes, alpha=1")
 PRECISION_WORKLOAD = ("P=4096 MLPs 784-112-10, batch 256 synthetic 28x28 images, {name} shadows of W1 (FP32 "
                       "accumulation, FP32 masters); operators as the plain workload")
+PAPER_POP, PAPER_DIMS, PAPER_BATCH = 2000, [196, 256, 128, 64, 10], 1024
+PAPER_PARAMS = dict(xo_op=0, xo_gene_p=0.5, sel_op=0, rho=0.5, n_elite=-1, p_e=0.05, p_c=0.75, sigma=0.001,
+                    mut_rate=1.0, alpha=1.0, init=1)
+PAPER_WORKLOAD = ("the paper's network (Section 4.1): 2x2 max-pool of 28x28 synthetic images, then 196-256-128-64-10 "
+                  "(92,042 params, FP32); lambda=2000, batch 1024, uniform crossover p_C=0.75, p_E=0.05, "
+                  "rho=0.5, sigma=0.001 on every gene, alpha=1 (Section 4.5); the max-pool runs in every step")
 CONFIGS = {"plain": dict(pop=1000, batch=100, precision=0),
+           "paper-net": dict(pop=PAPER_POP, batch=PAPER_BATCH, precision=0),
            "precision-bf16": dict(pop=4096, batch=256, precision=1),
            "precision-fp8": dict(pop=4096, batch=256, precision=2),
            "batching": dict(runs=64, pop=(50, 2000), hidden=(16, 256), batch=(8, 512), precision=1, seed=4242),
@@ -335,6 +342,158 @@ def run_reference(args, rank: int, world: int):
             "e2e": {"value": gen_per_s, "unit": "generations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "network_samples_per_sec": gen_per_s * POP * BATCH}
     print(json.dumps(line), flush=True)
+
+
+def paper_cpu_baseline(parents, f_adj, pooled64, y, n_children: int) -> dict:
+    """The oracle on one generation of the paper's network: rank + select all
+    lambda children, breed and evaluate n_children of them (strided)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    prm = oracle.Params(**PAPER_PARAMS)
+    par64, f64 = parents.astype(np.float64), f_adj.astype(np.float64)
+    t0 = time.perf_counter()
+    order = oracle.rank(f64)
+    p1, p2, kind, f_inh = oracle.select(prm, f64, order, 0, 1)
+    rows = np.linspace(0, PAPER_POP - 1, n_children).round().astype(int)
+    kids = np.concatenate([oracle.breed(prm, PAPER_DIMS, 0, 1, par64, p1, p2, kind, j0=int(j), j1=int(j) + 1)
+                           for j in rows])
+    f, _ = oracle.evaluate(kids, PAPER_DIMS, pooled64, y)
+    oracle.inherit(float(prm.alpha), f_inh[rows], f, first=False)
+    secs = time.perf_counter() - t0
+    gen_per_s = (n_children / PAPER_POP) / secs
+    return {"value": gen_per_s, "unit": "generations/s", "cores": 1, "kind": "oracle",
+            "sample": f"one generation's rank+select over all {PAPER_POP} nets, breed+evaluate of {n_children} of "
+                      f"the {PAPER_POP} children (strided), batch {PAPER_BATCH}; value = ({n_children}/{PAPER_POP}) "
+                      "/ seconds", "seconds": secs, "network_samples_per_sec": gen_per_s * PAPER_POP * PAPER_BATCH}
+
+
+def run_paper_net(args, rank: int, world: int, local_rank: int):
+    """The paper's own network and its large-population setting (Sections 4.1, 4.5)."""
+    import numpy as np
+    import torch
+    from paper_1806_09819_gb300 import build as B
+    from paper_1806_09819_gb300 import leea, synthetic
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = dist_init(world, True)
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(dist, dev)
+    B.build()
+    leea.load_library()
+    steps, warmup = args.steps, args.warmup
+    pop, batch, dims = PAPER_POP, PAPER_BATCH, PAPER_DIMS
+    (xtr, ytr), _ = synthetic.dataset(n_train=60000, n_test=1)
+    xtr = synthetic.to_levels(xtr)  # [60000, 784] 8-bit levels of 28x28 images
+    n_batches = warmup + 1 + steps
+    idx = synthetic.batch_indices(len(ytr), batch, n_batches, seed=synthetic.BATCH_SEED + rank)
+    xs = torch.from_numpy(xtr[idx]).to(dev)  # raw images, resident in HBM
+    ys = torch.from_numpy(ytr[idx]).to(dev)
+    pooled = torch.empty((batch, 196), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(st, xk, yk):
+        leea.leea_maxpool2x2(batch, 28, 28, xk, pooled, stream=stream)
+        st.leea_generation_u8(pooled, yk, 255.0)
+
+    st = leea.LeeaState(pop, dims, leea.Params(**PAPER_PARAMS), seed=1000 + rank, stream=stream)
+    for k in range(warmup + 1):  # the first call evaluates the initial population
+        step(st, xs[k], ys[k])
+    torch.cuda.synchronize(dev)
+    st.leea_profile_enable(True)
+    st.leea_profile_read()
+    clocks = ClockSampler(_gpu_id_for(local_rank))
+    clocks.start()
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    mark = clocks.mark()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for k in range(steps):
+        st.leea_profile_enable(k % PROFILE_EVERY == 0)
+        step(st, xs[warmup + 1 + k], ys[warmup + 1 + k])
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist, dev)
+    clk = clocks.stop(mark)
+    ms = ev0.elapsed_time(ev1)
+    prof = st.leea_profile_read()
+    st.leea_profile_enable(False)
+    ms_max, gen_per_s = job_rate(world, steps, ms, dist, dev)
+
+    # end to end: the raw batch from pinned host memory, pooled, a generation, the fitness read back
+    e2e_steps = max(10, min(steps, 200))
+    sel = idx[np.arange(e2e_steps) % n_batches]
+    xh = torch.from_numpy(xtr[sel]).pin_memory()
+    yh = torch.from_numpy(ytr[sel]).pin_memory()
+    xd = torch.empty((batch, 784), dtype=torch.uint8, device=dev)
+    yd = torch.empty(batch, dtype=torch.int32, device=dev)
+    f_host = None
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        xd.copy_(xh[k], non_blocking=True)
+        yd.copy_(yh[k], non_blocking=True)
+        step(st, xd, yd)
+        f_host = st.leea_fitness()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": world * e2e_steps / t_e2e, "unit": "generations/s",
+           "h2d_bytes_per_step": int(xh[0].numel() + yh[0].numel() * 4), "d2h_bytes_per_step": int(f_host.nbytes),
+           "steps": e2e_steps}
+
+    hbm_peak, sm_max_mhz, peak_src = _peaks()
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+    n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PAPER_PARAMS))
+    c = leea.leea_num_params(dims)
+    macs = sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+    work = {"breed": ("hbm", 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) / 1e9, "GB/s", hbm_peak),
+            "evaluate": ("alu", 2.0 * pop * batch * macs / 1e12, "TFLOP/s", fp32_peak),
+            "select": ("latency", None, None, None)}
+    kernels = {}
+    for name in STAGES:
+        tot_ms, launches = prof[name]
+        per = tot_ms / max(1, launches)
+        bound, units, unit, peak = work[name]
+        entry = {"launches": launches, "ms_per_launch": per,
+                 "share": tot_ms / max(1e-12, sum(v[0] for v in prof.values()))}
+        if units is not None:
+            ach = units / (per / 1000.0)
+            entry.update({"bound": bound, "achieved": ach, "unit": unit, "peak": peak, "frac": ach / peak})
+        kernels[name] = entry
+    kd = kernels["evaluate"]
+    roofline = {"kernel": "evaluate", "bound": "alu", "achieved": kd["achieved"], "peak": kd["peak"],
+                "unit": "TFLOP/s", "frac": kd["frac"], "traffic": None,
+                "peak_source": "derived: FP32 FFMA, 152 SM x 128 lanes x 2 x max SM clock (no measured FP32 peak)"}
+    line = {"metric": "generations/sec and network·samples/sec, the paper's 92k-parameter network at lambda=2000, "
+                      "batch 1024; % of roofline",
+            "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": PAPER_WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "kernel_timing": f"CUDA events around each kernel of every {PROFILE_EVERY}th generation "
+                                        "inside the timed region",
+                       "input": "uint8 levels k of 28x28 images, x = k/255, pooled on the GPU each step",
+                       "eval_kernel": "CUDA-core FP32, layers chained in shared memory (32-sample tiles)",
+                       "l2": f"inputs larger than L2 (2 population buffers of "
+                             f"{pop * leea.leea_padded_params(dims) * 4 / 1e6:.0f} MB), no flush"},
+            "network_samples_per_sec": gen_per_s * pop * batch, "e2e": e2e,
+            "gpu_launches": int(steps * (1 + sum(kernels_per_generation(pop, batch, 0).values()))),
+            "roofline": roofline, "kernels": kernels, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        x_last = xtr[idx[warmup + steps]].astype(np.float64)
+        import oracle
+        oracle.build()
+        pooled_h = oracle.maxpool2x2(x_last, 28, 28) / 255.0
+        line["cpu_baseline"] = paper_cpu_baseline(st.leea_get_population(), st.leea_fitness(), pooled_h,
+                                                  ytr[idx[warmup + steps]], n_children=min(args.cpu_children, 40))
+    st.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_batching(args, rank: int, world: int, local_rank: int):
@@ -764,7 +923,8 @@ def main():
                          "separate kernel, 3 fused")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="plain",
                     help="plain: the headline FP32 workload; precision-*: P=4096, batch 256, BF16/FP8 shadows; "
-                         "batching: 64 uneven runs together")
+                         "batching: 64 uneven runs together; paper-net: the paper's 196-256-128-64-10 behind 2x2 "
+                         "max-pooling at lambda=2000, batch 1024")
     ap.add_argument("--pop", type=int, default=0, help="override the population size (small profiling cases)")
     ap.add_argument("--batch", type=int, default=0, help="override the batch size (small profiling cases)")
     ap.add_argument("--input", choices=["u8", "f32"], default="u8",
@@ -775,6 +935,8 @@ def main():
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "paper-net":
+        run_paper_net(args, rank, world, local_rank)
     elif args.config == "batching":
         run_batching(args, rank, world, local_rank)
     elif args.config == "surrogate":
