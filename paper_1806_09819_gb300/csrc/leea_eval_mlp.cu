@@ -59,7 +59,8 @@ __device__ __forceinline__ void mlp_layer(const float* __restrict__ W, const flo
         for (int j = 0; j < TO; ++j) acc[i][j] = 0.0f;
 
     // Weight chunk c: WT[kk][o] = W[o][16 c + kk]; thread t stages rows o = t / 16
-    // + 16 u of input kk = t % 16 (a row's 16 inputs are 64 contiguous bytes).
+    // + 16 u of input kk = t % 16 (a warp's loads cover two rows' 64 contiguous
+    // bytes each), double-buffered through registers.  Inputs past K get zeros.
     constexpr int kRowsPerPass = kMlpThreads / kKC;  // 16
     const int n_chunks = (K + kKC - 1) / kKC;
     const int kk_l = tid % kKC, o_l = tid / kKC;
@@ -87,10 +88,12 @@ __device__ __forceinline__ void mlp_layer(const float* __restrict__ W, const flo
         const int buf = c & 1;
         if (c + 1 < n_chunks) load_chunk(c + 1);
         const float* wb = wt + buf * kKC * kWStride;
-        const int k0 = c * kKC;
-        const int kn = min(kKC, K - k0);
-        for (int kk = 0; kk < kn; ++kk) {
-            const float4 a = *reinterpret_cast<const float4*>(act_in + (k0 + kk) * kActStride + 4 * sg);
+        const float* ab = act_in + c * kKC * kActStride + 4 * sg;
+        // Inputs past K (up to K rounded to 16) hold zero weights and zero
+        // activations: the input tile and every hidden layer write zeros there.
+#pragma unroll
+        for (int kk = 0; kk < kKC; ++kk) {
+            const float4 a = *reinterpret_cast<const float4*>(ab + kk * kActStride);
             float w[TO];
             if constexpr (TO % 4 == 0) {
 #pragma unroll
@@ -119,13 +122,17 @@ __device__ __forceinline__ void mlp_layer(const float* __restrict__ W, const flo
 #pragma unroll
     for (int j = 0; j < TO; ++j) {
         const int o = og * TO + j;
-        if (o < N) {
+        if (!last && o >= N && o < ((N + kKC - 1) / kKC) * kKC) {
+            *reinterpret_cast<float4*>(act_out + o * kActStride + 4 * sg) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (o < N) {
             const float bo = __ldg(b + o);
+            if (last) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float v = acc[i][j] + bo;
-                if (last) logits[(4 * sg + i) * kLogitStride + o] = v;
-                else act_out[o * kActStride + 4 * sg + i] = fmaxf(v, 0.0f);
+                for (int i = 0; i < 4; ++i) logits[(4 * sg + i) * kLogitStride + o] = acc[i][j] + bo;
+            } else {  // 4 samples of output o: one 16-byte store
+                *reinterpret_cast<float4*>(act_out + o * kActStride + 4 * sg) =
+                    make_float4(fmaxf(acc[0][j] + bo, 0.0f), fmaxf(acc[1][j] + bo, 0.0f),
+                                fmaxf(acc[2][j] + bo, 0.0f), fmaxf(acc[3][j] + bo, 0.0f));
             }
         }
     }
@@ -151,10 +158,12 @@ eval_mlp_kernel(const MlpArgs e, const float* __restrict__ popv, const XT* __res
     int32_t n_ok = 0;
     for (int b0 = 0; b0 < e.batch; b0 += kTS) {
         // Input tile, k-major; samples past the batch are zero.
-        for (int idx = tid; idx < kTS * d0; idx += kMlpThreads) {
-            const int s = idx / d0, k = idx - s * d0;
-            act[0][k * kActStride + s] =
-                b0 + s < e.batch ? mlp_input(x[static_cast<int64_t>(b0 + s) * d0 + k], e.x_div) : 0.0f;
+        const int d0r = (d0 + kKC - 1) / kKC * kKC;  // rows up to the chunk boundary: zero past d0
+        for (int idx = tid; idx < kTS * d0r; idx += kMlpThreads) {
+            const int s = idx / d0r, k = idx - s * d0r;
+            act[0][k * kActStride + s] = (b0 + s < e.batch && k < d0)
+                                             ? mlp_input(x[static_cast<int64_t>(b0 + s) * d0 + k], e.x_div)
+                                             : 0.0f;
         }
         __syncthreads();
         for (int l = 0; l < e.n_layers; ++l) {
