@@ -92,8 +92,8 @@ STAGES = ("select", "breed", "evaluate")
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 TRAFFIC = {
-    "breed": {"bytes_per_launch": 706.54e6, "src_sha": "53af562611246ce0", "capture": "P=1000 plain workload"},
-    "evaluate": {"bytes_per_launch": 359.37e6, "src_sha": "d972b174f2e01544", "capture": "P=1000 plain workload"},
+    "breed": {"bytes_per_launch": 707.47e6, "src_sha": "c8e7e85a0e65db99", "capture": "P=1000 plain workload"},
+    "evaluate": {"bytes_per_launch": 359.45e6, "src_sha": "d972b174f2e01544", "capture": "P=1000 plain workload"},
     "breed_evaluate": {"bytes_per_launch": 738.19e6, "src_sha": "23e25d83744d9797", "capture": "P=1000 plain workload"},
 }
 
