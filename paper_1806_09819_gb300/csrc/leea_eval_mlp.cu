@@ -2,27 +2,28 @@
 // as the paper's own 196-256-128-64-10 behind 2x2 max-pooling (Section 4.1),
 // exact FP32 on the CUDA cores; and the max-pooling input stage itself.
 //
-// One CTA per individual walks the batch in tiles of 32 samples.  Each layer
-// is a [32 x K] x [K x N] product: the activations stay in shared memory,
+// One CTA per individual walks the batch in tiles of 64 samples.  Each layer
+// is a [64 x K] x [K x N] product: the activations stay in shared memory,
 // k-major (act[k][s], so a thread reads 4 samples of one input with one
 // 128-bit load), and the weights W_l (N rows of K, the gene order) pass
-// through shared memory transposed in chunks of 16 inputs, double-buffered
+// through shared memory transposed in chunks of 32 inputs, double-buffered
 // through registers.  A thread owns 4 samples x TO outputs (TO = N / 32
-// rounded up), so 256 threads cover 32 samples x up to 256 outputs in one pass.
+// rounded up), so 512 threads cover 64 samples x up to 256 outputs in one pass.
 // Hidden layers add the bias and apply ReLU into the other activation
-// buffer; the last layer leaves the logits in shared memory, where one warp
-// takes the softmax cross-entropy of its 32 samples (maximum subtracted,
-// FP32) and the argmax.  The per-tile loss sums are added in tile order:
-// identical individuals give bitwise identical fitness.
+// buffer; the last layer leaves the logits in shared memory, where the first
+// two warps take the softmax cross-entropy of the tile's 64 samples, a thread
+// per sample (maximum subtracted, FP32), and the argmax.  Each tile's two warp
+// sums are added in order, the tiles in order: identical individuals give
+// bitwise identical fitness.
 #include "leea_internal.h"
 
 namespace leea {
 
 namespace {
 
-constexpr int kMlpThreads = 256;
-constexpr int kTS = 32;         // samples per tile
-constexpr int kKC = 16;         // inputs per weight chunk
+constexpr int kMlpThreads = 512;
+constexpr int kTS = 64;         // samples per tile
+constexpr int kKC = 32;         // inputs per weight chunk
 constexpr int kMaxWidth = 256;  // widest layer input / hidden layer
 constexpr int kMaxOutMlp = 32;
 constexpr int kActStride = kTS + 4;          // act[k][s] row stride (floats)
@@ -50,17 +51,17 @@ __device__ __forceinline__ void mlp_layer(const float* __restrict__ W, const flo
                                           bool last, const float* act_in, float* act_out, float* logits, float* wt)
 {
     const int tid = threadIdx.x;
-    const int sg = tid & 7;   // samples 4 sg .. 4 sg + 3
-    const int og = tid >> 3;  // outputs og TO .. og TO + TO - 1
+    const int sg = tid & 15;  // samples 4 sg .. 4 sg + 3
+    const int og = tid >> 4;  // outputs og TO .. og TO + TO - 1
     float acc[4][TO];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < TO; ++j) acc[i][j] = 0.0f;
 
-    // Weight chunk c: WT[kk][o] = W[o][16 c + kk]; thread t stages rows o = t / 16
-    // + 16 u of input kk = t % 16 (a warp's loads cover two rows' 64 contiguous
-    // bytes each), double-buffered through registers.  Inputs past K get zeros.
+    // Weight chunk c: WT[kk][o] = W[o][32 c + kk]; thread t stages rows o = t / 32
+    // + 16 u of input kk = t % 32 (a warp's loads cover one row's 128 contiguous
+    // bytes), double-buffered through registers.  Inputs past K get zeros.
     constexpr int kRowsPerPass = kMlpThreads / kKC;  // 16
     const int n_chunks = (K + kKC - 1) / kKC;
     const int kk_l = tid % kKC, o_l = tid / kKC;
@@ -89,7 +90,7 @@ __device__ __forceinline__ void mlp_layer(const float* __restrict__ W, const flo
         if (c + 1 < n_chunks) load_chunk(c + 1);
         const float* wb = wt + buf * kKC * kWStride;
         const float* ab = act_in + c * kKC * kActStride + 4 * sg;
-        // Inputs past K (up to K rounded to 16) hold zero weights and zero
+        // Inputs past K (up to K rounded to 32) hold zero weights and zero
         // activations: the input tile and every hidden layer write zeros there.
 #pragma unroll
         for (int kk = 0; kk < kKC; ++kk) {
@@ -140,7 +141,7 @@ __device__ __forceinline__ void mlp_layer(const float* __restrict__ W, const flo
 }
 
 template <typename XT>
-__global__ void __launch_bounds__(kMlpThreads, 2)
+__global__ void __launch_bounds__(kMlpThreads, 1)
 eval_mlp_kernel(const MlpArgs e, const float* __restrict__ popv, const XT* __restrict__ x,
                 const int32_t* __restrict__ y, const float* __restrict__ f_inh, float* __restrict__ f_raw,
                 float* __restrict__ f_adj, int32_t* __restrict__ correct)
@@ -150,6 +151,8 @@ eval_mlp_kernel(const MlpArgs e, const float* __restrict__ popv, const XT* __res
     float* act[2] = { smem, smem + kMaxWidth * kActStride };
     float* wt = smem + 2 * kMaxWidth * kActStride;  // [2][kKC][kWStride]
     float* logits = wt + 2 * kKC * kWStride;        // [kTS][kLogitStride]
+    float* red = logits + kTS * kLogitStride;        // [2]: per-warp loss sums of a tile
+    int32_t* red_ok = reinterpret_cast<int32_t*>(red + 2);
     const int tid = threadIdx.x;
     const int p = blockIdx.x;
     const float* net = popv + static_cast<int64_t>(p) * e.c_pad;
@@ -159,11 +162,12 @@ eval_mlp_kernel(const MlpArgs e, const float* __restrict__ popv, const XT* __res
     for (int b0 = 0; b0 < e.batch; b0 += kTS) {
         // Input tile, k-major; samples past the batch are zero.
         const int d0r = (d0 + kKC - 1) / kKC * kKC;  // rows up to the chunk boundary: zero past d0
-        for (int idx = tid; idx < kTS * d0r; idx += kMlpThreads) {
-            const int s = idx / d0r, k = idx - s * d0r;
-            act[0][k * kActStride + s] = (b0 + s < e.batch && k < d0)
-                                             ? mlp_input(x[static_cast<int64_t>(b0 + s) * d0 + k], e.x_div)
-                                             : 0.0f;
+        for (int sk = tid; sk < kTS * kMaxWidth; sk += kMlpThreads) {
+            const int s = sk / kMaxWidth, k = sk % kMaxWidth;  // powers of two: shifts
+            if (k < d0r)
+                act[0][k * kActStride + s] = (b0 + s < e.batch && k < d0)
+                                                 ? mlp_input(x[static_cast<int64_t>(b0 + s) * d0 + k], e.x_div)
+                                                 : 0.0f;
         }
         __syncthreads();
         for (int l = 0; l < e.n_layers; ++l) {
@@ -179,7 +183,7 @@ eval_mlp_kernel(const MlpArgs e, const float* __restrict__ popv, const XT* __res
             else if (to <= 4) mlp_layer<4>(W, b, K, N, last, in, out, logits, wt);
             else mlp_layer<8>(W, b, K, N, last, in, out, logits, wt);
         }
-        if (tid < 32) {
+        if (tid < kTS) {  // one sample per thread of the first two warps
             const int s = tid;
             float loss = 0.0f;
             int32_t good = 0;
@@ -204,12 +208,16 @@ eval_mlp_kernel(const MlpArgs e, const float* __restrict__ popv, const XT* __res
                 loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
                 good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
             }
-            if (tid == 0) {
-                total += loss;
-                n_ok += good;
+            if ((tid & 31) == 0) {
+                red[tid >> 5] = loss;
+                red_ok[tid >> 5] = good;
             }
         }
         __syncthreads();  // the logits and activations are rewritten by the next tile
+        if (tid == 0) {   // the tile's two warp sums, in order
+            total += red[0] + red[1];
+            n_ok += red_ok[0] + red_ok[1];
+        }
     }
     if (tid == 0) {
         const float f = -(total / static_cast<float>(e.batch));
