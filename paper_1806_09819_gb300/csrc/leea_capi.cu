@@ -229,11 +229,22 @@ leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop
                              float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream)
 {
     if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
-    if (net.n_layers > 2) {  // several hidden layers: CUDA-core FP32
-        if (path == LEEA_EVAL_TENSOR) return fail(LEEA_EINVAL, "nets with several hidden layers evaluate on CUDA cores");
-        LEEA_CUDA_TRY(launch_eval_mlp_u8(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
-                                         stream),
-                      "evaluate kernel");
+    if (net.n_layers > 2) {  // several hidden layers
+        const bool tc = eval_mlp_tc_supported(net, pop_dev);
+        if (path == LEEA_EVAL_TENSOR && !tc)
+            return fail(LEEA_EINVAL, "tensor-core evaluation of deeper nets needs three hidden layers, widths multiples "
+                                     "of 16 in [16, 256] summing to <= 512, d_0 %% 4 == 0, d_0 <= 256, d_out <= 16");
+        if (tc && path != LEEA_EVAL_SIMT) {
+            unsigned int* status = device_status_ptr();
+            if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+            LEEA_CUDA_TRY(launch_eval_mlp_tc(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
+                                             status, stream),
+                          "evaluate kernel");
+        } else {
+            LEEA_CUDA_TRY(launch_eval_mlp_u8(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj,
+                                             correct, stream),
+                          "evaluate kernel");
+        }
         return LEEA_OK;
     }
     const bool tc_ok = eval_u8_tc_supported(net, batch, pop_dev);
@@ -843,10 +854,10 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         return fail(LEEA_EINVAL, "the state object evaluates nets with hidden layers (n_dims >= 3), d_out <= 32, and "
                                  "with several hidden layers every layer input and hidden width <= 256");
     }
-    if (s->net.n_layers > 2 && (p->precision != 0 || p->eval_path == LEEA_EVAL_TENSOR ||
-                                p->eval_path == LEEA_EVAL_FUSED)) {
+    if (s->net.n_layers > 2 && (p->precision != 0 || p->eval_path == LEEA_EVAL_FUSED)) {
         delete s;
-        return fail(LEEA_EINVAL, "nets with several hidden layers evaluate in FP32 on the CUDA cores");
+        return fail(LEEA_EINVAL, "nets with several hidden layers evaluate FP32 populations, breeding and evaluation "
+                                 "as separate kernels");
     }
     if (p->precision != 0 && (st = check_shadow_shape(s->net, p->precision))) {
         delete s;

@@ -144,8 +144,9 @@ template <typename XT>
 __global__ void __launch_bounds__(kMlpThreads, 1)
 eval_mlp_kernel(const MlpArgs e, const float* __restrict__ popv, const XT* __restrict__ x,
                 const int32_t* __restrict__ y, const float* __restrict__ f_inh, float* __restrict__ f_raw,
-                float* __restrict__ f_adj, int32_t* __restrict__ correct)
+                float* __restrict__ f_adj, int32_t* __restrict__ correct, const int32_t* __restrict__ only)
 {
+    if (only && only[blockIdx.x] == 0) return;  // only the marked individuals
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
     float* act[2] = { smem, smem + kMaxWidth * kActStride };
@@ -265,13 +266,13 @@ MlpArgs mlp_args(const NetLayout& net, int32_t batch, float alpha, float x_div)
 template <typename XT>
 cudaError_t launch_mlp(const NetLayout& net, int32_t pop, const float* pop_dev, const XT* x, float x_div,
                        const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw, float* f_adj,
-                       int32_t* correct, cudaStream_t stream)
+                       int32_t* correct, cudaStream_t stream, const int32_t* only = nullptr)
 {
     cudaError_t err = cudaFuncSetAttribute(eval_mlp_kernel<XT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(kMlpSmemBytes));
     if (err != cudaSuccess) return err;
     eval_mlp_kernel<XT><<<pop, kMlpThreads, kMlpSmemBytes, stream>>>(mlp_args(net, batch, alpha, x_div), pop_dev, x, y,
-                                                                    f_inh, f_raw, f_adj, correct);
+                                                                    f_inh, f_raw, f_adj, correct, only);
     return cudaGetLastError();
 }
 
@@ -297,6 +298,15 @@ cudaError_t launch_eval_mlp_u8(const NetLayout& net, int32_t pop, const float* p
                                float* f_adj, int32_t* correct, cudaStream_t stream)
 {
     return launch_mlp<uint8_t>(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct, stream);
+}
+
+cudaError_t launch_eval_mlp_u8_only(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
+                                    float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                                    float* f_raw, float* f_adj, int32_t* correct, const int32_t* only,
+                                    cudaStream_t stream)
+{
+    return launch_mlp<uint8_t>(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct, stream,
+                               only);
 }
 
 template <typename XT>

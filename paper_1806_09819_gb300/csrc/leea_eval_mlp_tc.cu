@@ -1,0 +1,547 @@
+// leea_eval_mlp_tc.cu -- fitness (Eq. 1) of nets with three hidden layers such
+// as the paper's 196-256-128-64-10 (Section 4.1), on the tcgen05 tensor cores
+// with FP32-class accuracy, for minibatches of 8-bit levels x = k / x_div.
+//
+// A unit is one individual on one 128-sample tile.  Layers 1-3 are MMAs with
+// the samples as M = 128 and FP32 accumulation in tensor memory (columns
+// [0, d1), [d1, d1 + d2), [d1 + d2, d1 + d2 + d3)):
+//   layer 1     A = the tile's levels k, exact in FP16; B = 2^8 W1 as two FP16
+//               pieces hi = fp16(2^8 w), lo = fp16(2^8 w - hi) (the remainder is
+//               exact in FP32): 2 MMAs per 16 inputs, only the accumulation rounds
+//   layers 2, 3 A = 2^8 h of the layer below and B = 2^8 W, both as two FP16
+//               pieces: hi.hi + hi.lo + lo.hi, 3 MMAs per 16 inputs; the dropped
+//               lo.lo term is below 2^-21 of the product
+// The epilogue adds the bias and applies ReLU in FP32, splits the activations
+// for the next layer, and computes layer 4 (d3 -> d_out), the softmax
+// cross-entropy and the loss sums in FP32, tiles in order.  A weight or an
+// activation with |v| >= 128 (2^8 |v| could overflow its FP16 piece) marks the
+// individual; the CUDA-core kernel then recomputes its fitness in FP32.
+//
+// Warp roles (persistent CTA, one per SM; individuals strided by gridDim.x,
+// their tiles in order):
+//   warp 0      TMEM allocation and the single MMA-issuing thread
+//   warps 1-8   converters: each 64-input block of W1, W2, W3 into the two
+//               FP16 pieces, 128-byte swizzled, in a shared-memory slot
+//   warps 9-12  the epilogue (TMEM lane = sample): the tile's levels as the
+//               layer-1 operand, the activations of layers 1 and 2 as the
+//               next operands, layer 4 and the loss
+// The phases of a unit run in sequence (one weight slot, one activation
+// region).  Every wait is bounded; on expiry the kernel sets
+// kStatusEvalTimeout and exits.
+#include <cuda.h>
+
+#include <cuda_fp16.h>
+
+#include <mutex>
+
+#include "leea_internal.h"
+#include "tc_ptx.cuh"
+
+namespace leea {
+
+namespace {
+
+constexpr int kConvWarps = 8;
+constexpr int kFirstConvWarp = 1;
+constexpr int kFirstEpiWarp = kFirstConvWarp + kConvWarps;
+constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kEpiThreads = 128;
+constexpr int kTcThreads = 32 * (kFirstEpiWarp + 4);
+constexpr int kTile = 128;                      // samples per unit (MMA M)
+constexpr uint32_t kBlockBytes = kTile * 128;   // one 64-input block of a 128-row operand
+constexpr uint32_t kHalfRegion = 4 * kBlockBytes;  // 64 KB: one piece of up to 256 inputs
+constexpr uint32_t kRegionBytes = 2 * kHalfRegion;  // activations: hi piece, lo piece
+constexpr uint32_t kSlotBytes = 2 * 256 * 128;      // weights: two pieces of up to 256 rows
+constexpr int kMaxOutTc = 16;
+constexpr uint32_t kTmemCols = 512;
+constexpr float kPieceScale = 256.0f;
+constexpr float kPieceRange = 128.0f;
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+constexpr uint64_t kDrainLimitNs = 200000000ull;
+
+struct MlpTcArgs {
+    int32_t pop, batch, n_tiles;
+    int32_t dims[5];     // d0, d1, d2, d3, d_out
+    int32_t k16[3];      // inputs of layers 1-3 rounded up to 16
+    int64_t c_pad;
+    int64_t w_off[4], b_off[4];
+    float inv_div;       // 2^-8 / x_div: layer-1 accumulator units to x units
+    float alpha;
+    const float* popv;
+    const uint8_t* x;
+    const int32_t* y;
+    const float* f_inh;
+    float* f_raw;
+    float* f_adj;
+    int32_t* correct;
+    int32_t* flagged;    // [pop], zeroed before the launch: 1 = recompute in FP32
+    unsigned int* status;
+};
+
+struct TcSmem {
+    uint8_t* region;  // activations: hi piece [0, 64 KB), lo piece [64 KB, 128 KB); the levels in the hi part
+    uint8_t* slot;    // weights: hi piece then lo piece, N x 128 bytes each per 64-input block
+    float *b1, *b2, *b3, *w4t, *b4;
+    uint64_t *slot_full, *slot_empty, *x_ready, *d_full, *h_ready, *drain;
+    uint32_t* tmem_holder;
+    volatile int* abort_flag;
+    int* ep_go;
+    float* red_loss;
+    int32_t* red_ok;
+};
+
+__host__ __device__ inline size_t tc_param_floats(const int32_t* dims)
+{
+    return static_cast<size_t>(dims[1] + dims[2] + dims[3] + dims[3] * kMaxOutTc + kMaxOutTc);
+}
+
+__host__ __device__ inline size_t tc_smem_bytes(const int32_t* dims)
+{
+    return 1024 + kRegionBytes + kSlotBytes + sizeof(float) * tc_param_floats(dims) + 8 * 16 + 64;
+}
+
+__device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
+{
+    TcSmem s;
+    s.region = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
+    s.slot = s.region + kRegionBytes;
+    float* f = reinterpret_cast<float*>(s.slot + kSlotBytes);
+    s.b1 = f;
+    s.b2 = s.b1 + a.dims[1];
+    s.b3 = s.b2 + a.dims[2];
+    s.w4t = s.b3 + a.dims[3];
+    s.b4 = s.w4t + a.dims[3] * kMaxOutTc;
+    uint8_t* p = reinterpret_cast<uint8_t*>(s.b4 + kMaxOutTc);
+    p += (8u - (reinterpret_cast<uintptr_t>(p) & 7u)) & 7u;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(p);
+    s.slot_full = bars;
+    s.slot_empty = bars + 1;
+    s.x_ready = bars + 2;
+    s.d_full = bars + 3;   // [3]
+    s.h_ready = bars + 6;  // [2]
+    s.drain = bars + 8;
+    uint32_t* w = reinterpret_cast<uint32_t*>(bars + 9);
+    s.tmem_holder = w;
+    s.abort_flag = reinterpret_cast<volatile int*>(w + 1);
+    s.ep_go = reinterpret_cast<int*>(w + 2);
+    s.red_loss = reinterpret_cast<float*>(w + 3);
+    s.red_ok = reinterpret_cast<int32_t*>(w + 7);
+    return s;
+}
+
+__device__ __forceinline__ void raise_abort(const TcSmem& s, const MlpTcArgs& a)
+{
+    *s.abort_flag = 1;
+    atomicOr(a.status, kStatusEvalTimeout);
+}
+
+__device__ __forceinline__ uint32_t half2_bits(__half2 v)
+{
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// Two FP32 values as packed FP16 pieces of 2^8 v (lower index in the low half).
+__device__ __forceinline__ void split2x2(float v0, float v1, uint32_t& p1, uint32_t& p2)
+{
+    const float s0 = v0 * kPieceScale, s1 = v1 * kPieceScale;
+    const __half2 h1 = __floats2half2_rn(s0, s1);
+    const float2 f1 = __half22float2(h1);
+    p1 = half2_bits(h1);
+    p2 = half2_bits(__floats2half2_rn(s0 - f1.x, s1 - f1.y));
+}
+
+// Byte offset of 16-byte chunk `ch` (inputs 8 ch .. 8 ch + 7 of a 64-input
+// block) of row r in the 128-byte swizzled K-major layout.
+__device__ __forceinline__ uint32_t swz(int r, int ch)
+{
+    return static_cast<uint32_t>(r) * 128u + ((static_cast<uint32_t>(ch) ^ static_cast<uint32_t>(r & 7)) << 4);
+}
+
+__device__ __forceinline__ int layer_blocks(const MlpTcArgs& a, int l) { return (a.k16[l] + 63) / 64; }
+
+__global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcArgs a)
+{
+    extern __shared__ uint8_t smem_raw[];
+    const TcSmem s = carve(smem_raw, a);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int d1 = a.dims[1], d2 = a.dims[2], d3 = a.dims[3], d_out = a.dims[4];
+    const uint32_t col[3] = { 0u, static_cast<uint32_t>(d1), static_cast<uint32_t>(d1 + d2) };
+
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(s.slot_full, kConvWarps);
+        ptx::mbar_init(s.slot_empty, 1);
+        ptx::mbar_init(s.x_ready, kEpiThreads);
+        for (int i = 0; i < 3; ++i) ptx::mbar_init(&s.d_full[i], 1);
+        for (int i = 0; i < 2; ++i) ptx::mbar_init(&s.h_ready[i], kEpiThreads);
+        ptx::mbar_init(s.drain, 1);
+        *s.abort_flag = 0;
+        *s.ep_go = 0;
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) ptx::tmem_alloc(s.tmem_holder, kTmemCols);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem_base = *s.tmem_holder;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t region = ptx::smem_u32(s.region), slot = ptx::smem_u32(s.slot);
+            uint32_t unit = 0, sphase = 0;
+            bool ok = true;
+            for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+                for (int t = 0; ok && t < a.n_tiles; ++t, ++unit) {
+                    if (!ptx::mbar_wait_bounded(s.x_ready, unit & 1u, s.abort_flag, kWaitLimitNs)) {
+                        raise_abort(s, a);
+                        ok = false;
+                        break;
+                    }
+                    for (int l = 0; ok && l < 3; ++l) {
+                        if (l > 0 && !ptx::mbar_wait_bounded(&s.h_ready[l - 1], unit & 1u, s.abort_flag,
+                                                             kWaitLimitNs)) {
+                            raise_abort(s, a);
+                            ok = false;
+                            break;
+                        }
+                        ptx::tc_fence_after();
+                        const uint32_t n = static_cast<uint32_t>(a.dims[l + 1]);
+                        const uint32_t idesc = ptx::idesc_f16(kTile, n);
+                        const uint32_t d_tmem = tmem_base + col[l];
+                        const int blocks = layer_blocks(a, l);
+                        for (int kb = 0; kb < blocks; ++kb) {
+                            if (!ptx::mbar_wait_bounded(s.slot_full, sphase, s.abort_flag, kWaitLimitNs)) {
+                                raise_abort(s, a);
+                                ok = false;
+                                break;
+                            }
+                            sphase ^= 1u;
+                            ptx::tc_fence_after();
+#pragma unroll
+                            for (int kk = 0; kk < 4; ++kk) {
+                                const int kg = kb * 64 + kk * 16;
+                                if (kg >= a.k16[l]) break;
+                                const uint32_t a_hi = region + kb * kBlockBytes + kk * 32u;
+                                const uint32_t b_hi = slot + kk * 32u;
+                                const uint32_t b_lo = slot + n * 128u + kk * 32u;
+                                const uint32_t first = (kb | kk) == 0 ? 0u : 1u;
+                                ptx::mma_f16(d_tmem, ptx::smem_desc_sw128(a_hi), ptx::smem_desc_sw128(b_hi), idesc,
+                                             first);
+                                ptx::mma_f16(d_tmem, ptx::smem_desc_sw128(a_hi), ptx::smem_desc_sw128(b_lo), idesc,
+                                             1u);
+                                if (l > 0)
+                                    ptx::mma_f16(d_tmem, ptx::smem_desc_sw128(a_hi + kHalfRegion),
+                                                 ptx::smem_desc_sw128(b_hi), idesc, 1u);
+                            }
+                            ptx::mma_commit(s.slot_empty);
+                        }
+                        if (ok) ptx::mma_commit(&s.d_full[l]);
+                    }
+                }
+            }
+            ptx::mma_commit(s.drain);
+            volatile int never = 0;
+            ptx::mbar_wait_bounded(s.drain, 0u, &never, ok ? kWaitLimitNs : kDrainLimitNs);
+        }
+    } else if (warp < kFirstEpiWarp) {
+        // ------------------------------------------------------------ converters
+        // Item i of a block: row n = i / 8, inputs 8 (i % 8) .. + 7 of the block.
+        const int ct = threadIdx.x - 32 * kFirstConvWarp;
+        uint32_t sphase = 0;
+        bool ok = true;
+        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+            const float* net = a.popv + static_cast<int64_t>(p) * a.c_pad;
+            bool bad = false;
+            for (int t = 0; ok && t < a.n_tiles; ++t) {
+                for (int l = 0; ok && l < 3; ++l) {
+                    const int K = a.dims[l], N = a.dims[l + 1];
+                    const float* W = net + a.w_off[l];
+                    const int blocks = layer_blocks(a, l);
+                    for (int kb = 0; kb < blocks; ++kb) {
+                        if (!ptx::mbar_wait_bounded(s.slot_empty, sphase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+                            raise_abort(s, a);
+                            ok = false;
+                            break;
+                        }
+                        sphase ^= 1u;
+                        for (int i = ct; i < N * 8; i += kConvThreads) {
+                            const int n = i >> 3, ch = i & 7;
+                            const int k = kb * 64 + 8 * ch;
+                            float v[8];
+                            if (k < K) {
+                                const float4* src = reinterpret_cast<const float4*>(W + static_cast<int64_t>(n) * K + k);
+                                const float4 v0 = __ldg(src);
+                                const float4 v1 = k + 4 < K ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                                v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
+                                v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+                            }
+                            uint32_t hi[4], lo[4];
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                split2x2(v[2 * e], v[2 * e + 1], hi[e], lo[e]);
+                                bad |= fabsf(v[2 * e]) >= kPieceRange || fabsf(v[2 * e + 1]) >= kPieceRange;
+                            }
+                            const uint32_t off = swz(n, ch);
+                            *reinterpret_cast<uint4*>(s.slot + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                            *reinterpret_cast<uint4*>(s.slot + N * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                        }
+                        ptx::fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) ptx::mbar_arrive(s.slot_full);
+                    }
+                }
+            }
+            if (bad) a.flagged[p] = 1;  // read by the FP32 recomputation after this kernel
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int et = threadIdx.x - 32 * kFirstEpiWarp;
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
+        uint32_t unit = 0;
+        bool ok = true;
+        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+            const float* net = a.popv + static_cast<int64_t>(p) * a.c_pad;
+            // Biases and layer 4 of individual p (row-major W4 -> [d3][16]).
+            ptx::named_barrier_sync(1, kEpiThreads);  // the previous individual's parameters are no longer read
+            for (int i = et; i < d1; i += kEpiThreads) s.b1[i] = net[a.b_off[0] + i];
+            for (int i = et; i < d2; i += kEpiThreads) s.b2[i] = net[a.b_off[1] + i];
+            for (int i = et; i < d3; i += kEpiThreads) s.b3[i] = net[a.b_off[2] + i];
+            for (int i = et; i < d3 * kMaxOutTc; i += kEpiThreads) {
+                const int c = i / kMaxOutTc, o = i % kMaxOutTc;
+                s.w4t[i] = o < d_out ? net[a.w_off[3] + static_cast<int64_t>(o) * d3 + c] : 0.0f;
+            }
+            if (et < kMaxOutTc) s.b4[et] = et < d_out ? net[a.b_off[3] + et] : 0.0f;
+            ptx::named_barrier_sync(1, kEpiThreads);
+            float total = 0.0f;
+            int32_t n_ok = 0;
+            bool bad = false;
+            for (int t = 0; t < a.n_tiles; ++t, ++unit) {
+                // (1) the tile's levels as FP16 into the hi part of the region
+                const int smp = t * kTile + row;
+                const bool live = smp < a.batch;
+                const uint8_t* xr = a.x + static_cast<int64_t>(live ? smp : 0) * a.dims[0];
+                for (int k0 = 0; k0 < a.k16[0]; k0 += 8) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int k = k0 + 2 * e;
+                        const float l0 = (live && k < a.dims[0]) ? static_cast<float>(__ldg(xr + k)) : 0.0f;
+                        const float l1 = (live && k + 1 < a.dims[0]) ? static_cast<float>(__ldg(xr + k + 1)) : 0.0f;
+                        w[e] = half2_bits(__floats2half2_rn(l0, l1));
+                    }
+                    *reinterpret_cast<uint4*>(s.region + (k0 >> 6) * kBlockBytes + swz(row, (k0 & 63) >> 3)) =
+                        make_uint4(w[0], w[1], w[2], w[3]);
+                }
+                ptx::fence_proxy_async_smem();
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(s.x_ready);
+                // (2), (3) layers 1 and 2: bias, ReLU, split for the next layer
+                for (int l = 0; l < 3; ++l) {
+                    if (et == 0) {
+                        const bool got = ptx::mbar_wait_bounded(&s.d_full[l], unit & 1u, s.abort_flag, kWaitLimitNs);
+                        if (!got) raise_abort(s, a);
+                        *s.ep_go = got ? 1 : 0;
+                    }
+                    ptx::named_barrier_sync(1, kEpiThreads);
+                    if (!*s.ep_go) { ok = false; break; }
+                    ptx::tc_fence_after();
+                    const int N = a.dims[l + 1];
+                    const float* bias = l == 0 ? s.b1 : (l == 1 ? s.b2 : s.b3);
+                    const float scale = l == 0 ? a.inv_div : 1.0f / (kPieceScale * kPieceScale);
+                    if (l < 2) {
+                        for (int c = 0; c < N; c += 16) {
+                            float v[16];
+                            ptx::tmem_ld16(tmem_base + lane_addr + col[l] + static_cast<uint32_t>(c), v);
+                            uint32_t hi[8], lo[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const float h0 = fmaxf(fmaf(v[2 * e], scale, bias[c + 2 * e]), 0.0f);
+                                const float h1 = fmaxf(fmaf(v[2 * e + 1], scale, bias[c + 2 * e + 1]), 0.0f);
+                                bad |= h0 >= kPieceRange || h1 >= kPieceRange;
+                                split2x2(h0, h1, hi[e], lo[e]);
+                            }
+                            uint8_t* dst = s.region + (c >> 6) * kBlockBytes;
+                            const int ch = (c & 63) >> 3;
+                            *reinterpret_cast<uint4*>(dst + swz(row, ch)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                            *reinterpret_cast<uint4*>(dst + swz(row, ch + 1)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+                            *reinterpret_cast<uint4*>(dst + kHalfRegion + swz(row, ch)) =
+                                make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                            *reinterpret_cast<uint4*>(dst + kHalfRegion + swz(row, ch + 1)) =
+                                make_uint4(lo[4], lo[5], lo[6], lo[7]);
+                        }
+                        ptx::fence_proxy_async_smem();
+                        ptx::tc_fence_before();
+                        ptx::mbar_arrive(&s.h_ready[l]);
+                    } else {
+                        // layer 3's ReLU, then layer 4 and the loss in FP32
+                        float logit[kMaxOutTc];
+#pragma unroll
+                        for (int o = 0; o < kMaxOutTc; ++o) logit[o] = 0.0f;
+                        for (int c = 0; c < N; c += 16) {
+                            float v[16];
+                            ptx::tmem_ld16(tmem_base + lane_addr + col[l] + static_cast<uint32_t>(c), v);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                const float h = fmaxf(fmaf(v[j], scale, bias[c + j]), 0.0f);
+                                const float4* wr = reinterpret_cast<const float4*>(s.w4t + (c + j) * kMaxOutTc);
+#pragma unroll
+                                for (int o4 = 0; o4 < kMaxOutTc / 4; ++o4) {
+                                    if (4 * o4 < d_out) {
+                                        const float4 w4 = wr[o4];
+                                        logit[4 * o4 + 0] = fmaf(w4.x, h, logit[4 * o4 + 0]);
+                                        logit[4 * o4 + 1] = fmaf(w4.y, h, logit[4 * o4 + 1]);
+                                        logit[4 * o4 + 2] = fmaf(w4.z, h, logit[4 * o4 + 2]);
+                                        logit[4 * o4 + 3] = fmaf(w4.w, h, logit[4 * o4 + 3]);
+                                    }
+                                }
+                            }
+                        }
+                        ptx::tc_fence_before();
+                        float loss = 0.0f;
+                        int32_t good = 0;
+                        if (live) {
+                            float z[kMaxOutTc];
+#pragma unroll
+                            for (int o = 0; o < kMaxOutTc; ++o) z[o] = o < d_out ? logit[o] + s.b4[o] : 0.0f;
+                            float zmax = z[0];
+                            int arg = 0;
+#pragma unroll
+                            for (int o = 1; o < kMaxOutTc; ++o)
+                                if (o < d_out && z[o] > zmax) { zmax = z[o]; arg = o; }
+                            float se = 0.0f;
+#pragma unroll
+                            for (int o = 0; o < kMaxOutTc; ++o)
+                                if (o < d_out) se += expf(z[o] - zmax);
+                            const int32_t lbl = a.y[smp];
+                            if (lbl >= 0 && lbl < d_out) {
+                                float zl = 0.0f;
+#pragma unroll
+                                for (int o = 0; o < kMaxOutTc; ++o)
+                                    if (o == lbl) zl = z[o];
+                                loss = logf(se) + zmax - zl;
+                                good = arg == lbl ? 1 : 0;
+                            } else {
+                                loss = __int_as_float(0x7FC00000);
+                            }
+                        }
+#pragma unroll
+                        for (int off = 16; off > 0; off >>= 1) {
+                            loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
+                            good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
+                        }
+                        if (lane == 0) {
+                            s.red_loss[q] = loss;
+                            s.red_ok[q] = good;
+                        }
+                        ptx::named_barrier_sync(1, kEpiThreads);
+                        if (et == 0) {
+                            total += ((s.red_loss[0] + s.red_loss[1]) + s.red_loss[2]) + s.red_loss[3];
+                            n_ok += s.red_ok[0] + s.red_ok[1] + s.red_ok[2] + s.red_ok[3];
+                        }
+                    }
+                }
+                if (!ok) break;
+            }
+            if (!ok) break;
+            if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) a.flagged[p] = 1;
+            if (et == 0) {
+                const float f = -(total / static_cast<float>(a.batch));
+                a.f_raw[p] = f;
+                if (a.f_adj) a.f_adj[p] = a.f_inh ? (1.0f - a.alpha) * a.f_inh[p] + a.alpha * f : f;
+                if (a.correct) a.correct[p] = n_ok;
+            }
+        }
+    }
+
+    ptx::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        ptx::tc_fence_after();
+        ptx::tmem_dealloc(tmem_base, kTmemCols);
+    }
+}
+
+// Library-owned flag array for the recomputation, grown on demand.
+int32_t* flag_buffer(int32_t pop)
+{
+    static std::mutex mu;
+    static int32_t* buf = nullptr;
+    static int32_t cap = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (pop > cap) {
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        cap = 0;
+        if (cudaMalloc(&buf, sizeof(int32_t) * static_cast<size_t>(pop)) != cudaSuccess) return nullptr;
+        cap = pop;
+    }
+    return buf;
+}
+
+}  // namespace
+
+bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev)
+{
+    if (net.n_layers != 4) return false;
+    const int32_t d0 = net.dims[0], d1 = net.dims[1], d2 = net.dims[2], d3 = net.dims[3], d_out = net.dims[4];
+    if (d0 % 4 != 0 || d0 > 256 || d_out > kMaxOutTc) return false;
+    for (int32_t n : { d1, d2, d3 })
+        if (n % 16 != 0 || n < 16 || n > 256) return false;
+    if (d1 + d2 + d3 > static_cast<int32_t>(kTmemCols)) return false;
+    for (int l = 0; l < 3; ++l)
+        if (net.w_off[l] % 4 != 0) return false;
+    if (reinterpret_cast<uintptr_t>(pop_dev) & 15u) return false;
+    return tc_smem_bytes(net.dims) <= 227u * 1024u;
+}
+
+cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
+                               const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                               float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream)
+{
+    MlpTcArgs a{};
+    a.pop = pop;
+    a.batch = batch;
+    a.n_tiles = (batch + kTile - 1) / kTile;
+    for (int l = 0; l <= 4; ++l) a.dims[l] = net.dims[l];
+    for (int l = 0; l < 3; ++l) a.k16[l] = (net.dims[l] + 15) / 16 * 16;
+    a.c_pad = net.c_pad;
+    for (int l = 0; l < 4; ++l) {
+        a.w_off[l] = net.w_off[l];
+        a.b_off[l] = net.b_off[l];
+    }
+    a.inv_div = static_cast<float>(1.0 / (static_cast<double>(x_div) * kPieceScale));
+    a.alpha = alpha;
+    a.popv = pop_dev;
+    a.x = x;
+    a.y = y;
+    a.f_inh = f_inh;
+    a.f_raw = f_raw;
+    a.f_adj = f_adj;
+    a.correct = correct;
+    a.status = status;
+    a.flagged = flag_buffer(pop);
+    if (!a.flagged) return cudaErrorMemoryAllocation;
+    cudaError_t err = cudaMemsetAsync(a.flagged, 0, sizeof(int32_t) * static_cast<size_t>(pop), stream);
+    if (err != cudaSuccess) return err;
+    const size_t smem = tc_smem_bytes(net.dims);
+    err = cudaFuncSetAttribute(eval_mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (err != cudaSuccess) return err;
+    int dev = 0, sms = 0;
+    if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+    if ((err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return err;
+    const int grid = pop < sms ? pop : sms;
+    eval_mlp_tc_kernel<<<grid, kTcThreads, smem, stream>>>(a);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // Individuals with a weight or activation outside the FP16 pieces' range:
+    // their fitness again, in FP32 on the CUDA cores.
+    return launch_eval_mlp_u8_only(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
+                                   a.flagged, stream);
+}
+
+}  // namespace leea

@@ -235,6 +235,20 @@ cudaError_t launch_eval_mlp(const NetLayout& net, int32_t pop, const float* pop_
 cudaError_t launch_eval_mlp_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
                                const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
                                float* f_adj, int32_t* correct, cudaStream_t stream);
+// The same, only for the individuals p with only[p] != 0.
+cudaError_t launch_eval_mlp_u8_only(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
+                                    float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
+                                    float* f_raw, float* f_adj, int32_t* correct, const int32_t* only,
+                                    cudaStream_t stream);
+// Nets with three hidden layers (the paper's 196-256-128-64-10) on the tensor
+// cores for 8-bit inputs: d0 % 4 == 0, d0 <= 256, hidden widths multiples of 16
+// in [16, 256] summing to <= 512, d_out <= 16; FP32-class accuracy (FP16
+// operand pieces), individuals with a weight or activation |v| >= 128
+// recomputed in FP32 on the CUDA cores.
+bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev);
+cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
+                               const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
+                               float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream);
 cudaError_t launch_maxpool2x2(int32_t batch, int32_t h, int32_t w, const float* x, float* out, cudaStream_t stream);
 cudaError_t launch_maxpool2x2_u8(int32_t batch, int32_t h, int32_t w, const uint8_t* x, uint8_t* out,
                                  cudaStream_t stream);

@@ -89,16 +89,72 @@ def test_mlp_evaluate_matches_oracle(gpu, oracle_mod, dims, pop, batch, inp):
     assert fr[0].view(np.uint32) == fr[pop - 1].view(np.uint32)
 
 
+def _eval_u8(gpu, dims, popv, levels, y, path, f_inh=None, alpha=1.0):
+    torch = _torch()
+    pop, batch = popv.shape[0], levels.shape[0]
+    pd = to_device_pop(popv, gpu.leea_padded_params(dims))
+    f_raw = torch.empty(pop, dtype=torch.float32, device="cuda")
+    f_adj = torch.empty(pop, dtype=torch.float32, device="cuda")
+    cor = torch.empty(pop, dtype=torch.int32, device="cuda")
+    fi = None if f_inh is None else torch.from_numpy(f_inh).cuda()
+    gpu.leea_evaluate_u8(pop, dims, pd, torch.from_numpy(levels).cuda(), 255.0, torch.from_numpy(y).cuda(), batch,
+                         alpha, fi, f_raw, f_adj, cor, eval_path=path)
+    torch.cuda.synchronize()
+    return f_raw.cpu().numpy(), f_adj.cpu().numpy(), cor.cpu().numpy()
+
+
+TC_CASES = [(PAPER_DIMS, 6, 1024), (PAPER_DIMS, 5, 129), (PAPER_DIMS, 3, 1), (PAPER_DIMS, 160, 100),
+            ([64, 48, 32, 16, 4], 7, 200), ([256, 256, 128, 128, 16], 3, 77)]
+
+
+@pytest.mark.parametrize("dims,pop,batch", TC_CASES, ids=lambda v: str(v))
+def test_mlp_tensor_cores_match_oracle(gpu, oracle_mod, dims, pop, batch):
+    # Three hidden layers on tcgen05 (FP16 operand pieces, FP32 accumulation):
+    # within the evaluation tolerance of the FP64 oracle, like the FP32 kernel.
+    c = gpu.leea_num_params(dims)
+    popv = synthetic.random_population(pop, c, seed=c + batch + 1, scale=0.12)
+    rng = np.random.default_rng(batch + 5)
+    levels = rng.integers(0, 256, size=(batch, dims[0])).astype(np.uint8)
+    y = rng.integers(0, dims[-1], size=batch).astype(np.int32)
+    f_inh = rng.normal(-2.0, 0.1, size=pop).astype(np.float32)
+    f_tc, a_tc, c_tc = _eval_u8(gpu, dims, popv, levels, y, gpu.EVAL_TENSOR, f_inh, 0.3)
+    f_ref, cor_ref, logits = oracle_mod.evaluate(popv.astype(np.float64), dims, levels.astype(np.float64) / 255.0, y,
+                                                 want_logits=True)
+    assert_fitness_close(f_tc, f_ref, "tensor-core fitness")
+    assert_correct_close(c_tc, cor_ref, logits)
+    assert_fitness_close(a_tc, oracle_mod.inherit(float(np.float32(0.3)), f_inh, f_ref, first=False), "f_adj")
+    f_simt, _, _ = _eval_u8(gpu, dims, popv, levels, y, gpu.EVAL_SIMT)
+    assert_fitness_close(f_tc, f_simt.astype(np.float64), "tensor cores vs CUDA cores")
+
+
+def test_mlp_tensor_cores_fall_back_outside_the_piece_range(gpu, oracle_mod):
+    # A weight of 200 in W2, and an individual whose layer-1 activations exceed
+    # 128: both are recomputed in FP32; the others stay on the tensor cores.
+    dims = PAPER_DIMS
+    c = gpu.leea_num_params(dims)
+    popv = synthetic.random_population(6, c, seed=3, scale=0.1)
+    w2 = 196 * 256 + 256
+    popv[1, w2 + 77] = 200.0
+    popv[3, :196 * 256] *= 40.0
+    rng = np.random.default_rng(2)
+    levels = rng.integers(0, 256, size=(300, 196)).astype(np.uint8)
+    y = rng.integers(0, 10, size=300).astype(np.int32)
+    f_tc, _, c_tc = _eval_u8(gpu, dims, popv, levels, y, gpu.EVAL_AUTO)
+    f_ref, cor_ref, logits = oracle_mod.evaluate(popv.astype(np.float64), dims, levels.astype(np.float64) / 255.0, y,
+                                                 want_logits=True)
+    assert_fitness_close(f_tc, f_ref)
+    assert_correct_close(c_tc, cor_ref, logits)
+
+
 def test_mlp_rejects_tensor_path_and_wide_layers(gpu):
     torch = _torch()
-    dims = PAPER_DIMS
-    cp = gpu.leea_padded_params(dims)
-    pd = torch.zeros((2, cp), dtype=torch.float32, device="cuda")
-    x = torch.zeros((4, 196), dtype=torch.uint8, device="cuda")
     y = torch.zeros(4, dtype=torch.int32, device="cuda")
     f = torch.empty(2, dtype=torch.float32, device="cuda")
+    deep = [64, 32, 32, 32, 16, 4]  # four hidden layers: CUDA cores only
+    pdd = torch.zeros((2, gpu.leea_padded_params(deep)), dtype=torch.float32, device="cuda")
+    xd = torch.zeros((4, 64), dtype=torch.uint8, device="cuda")
     with pytest.raises(gpu.LeeaError):
-        gpu.leea_evaluate_u8(2, dims, pd, x, 255.0, y, 4, 1.0, None, f, eval_path=gpu.EVAL_TENSOR)
+        gpu.leea_evaluate_u8(2, deep, pdd, xd, 255.0, y, 4, 1.0, None, f, eval_path=gpu.EVAL_TENSOR)
     wide = [300, 16, 8, 4]
     pw = torch.zeros((2, gpu.leea_padded_params(wide)), dtype=torch.float32, device="cuda")
     xw = torch.zeros((4, 300), dtype=torch.uint8, device="cuda")
