@@ -108,6 +108,16 @@ def _peaks():
         return 6800.0, SM_MAX_MHZ_NOMINAL, "fallback"
 
 
+def _tensor_peak() -> tuple[float, str]:
+    """Dense FP16/BF16 tensor peak (TFLOP/s) for a kernel timed inside a long step."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return float(m["bf16_tflops_sustained"]), "measured (cuBLAS BF16, sustained; FP16 runs at the BF16 rate)"
+    except Exception:
+        return 1700.0, "fallback (BF16 sustained; FP16 runs at the BF16 rate)"
+
+
 def _src_sha(name: str) -> str:
     p = os.path.join(ROOT, "paper_1806_09819_gb300", "csrc", name)
     with open(p, "rb") as fh:
@@ -398,7 +408,8 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
         leea.leea_maxpool2x2(batch, 28, 28, xk, pooled, stream=stream)
         st.leea_generation_u8(pooled, yk, 255.0)
 
-    st = leea.LeeaState(pop, dims, leea.Params(**PAPER_PARAMS), seed=1000 + rank, stream=stream)
+    st = leea.LeeaState(pop, dims, leea.Params(**PAPER_PARAMS, eval_path=args.eval_path), seed=1000 + rank,
+                        stream=stream)
     for k in range(warmup + 1):  # the first call evaluates the initial population
         step(st, xs[k], ys[k])
     torch.cuda.synchronize(dev)
@@ -449,8 +460,11 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
     n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PAPER_PARAMS))
     c = leea.leea_num_params(dims)
     macs = sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
+    tensor = args.eval_path != leea.EVAL_SIMT  # 8-bit inputs, three hidden layers: tcgen05 FP16 pieces
+    t_peak, t_src = _tensor_peak()
     work = {"breed": ("hbm", 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) / 1e9, "GB/s", hbm_peak),
-            "evaluate": ("alu", 2.0 * pop * batch * macs / 1e12, "TFLOP/s", fp32_peak),
+            "evaluate": ("tensor" if tensor else "alu", 2.0 * pop * batch * macs / 1e12, "TFLOP/s",
+                         t_peak if tensor else fp32_peak),
             "select": ("latency", None, None, None)}
     kernels = {}
     for name in STAGES:
@@ -464,9 +478,15 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
             entry.update({"bound": bound, "achieved": ach, "unit": unit, "peak": peak, "frac": ach / peak})
         kernels[name] = entry
     kd = kernels["evaluate"]
-    roofline = {"kernel": "evaluate", "bound": "alu", "achieved": kd["achieved"], "peak": kd["peak"],
+    if tensor:  # MMA work issued: 128-sample tiles, K padded to 16, 2 pieces (layer 1) or 3 products (layers 2-3)
+        tiles = (batch + 127) // 128
+        k16 = [(d + 15) // 16 * 16 for d in dims]
+        issued = sum((2 if l == 0 else 3) * 2.0 * 128 * k16[l] * dims[l + 1] for l in range(3))
+        kd["tensor_tflops_issued"] = pop * tiles * issued / 1e12 / (kd["ms_per_launch"] / 1000.0)
+    roofline = {"kernel": "evaluate", "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": "TFLOP/s", "frac": kd["frac"], "traffic": None,
-                "peak_source": "derived: FP32 FFMA, 152 SM x 128 lanes x 2 x max SM clock (no measured FP32 peak)"}
+                "peak_source": t_src if tensor else
+                "derived: FP32 FFMA, 152 SM x 128 lanes x 2 x max SM clock (no measured FP32 peak)"}
     line = {"metric": "generations/sec and network·samples/sec, the paper's 92k-parameter network at lambda=2000, "
                       "batch 1024; % of roofline",
             "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
@@ -476,11 +496,14 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
                        "kernel_timing": f"CUDA events around each kernel of every {PROFILE_EVERY}th generation "
                                         "inside the timed region",
                        "input": "uint8 levels k of 28x28 images, x = k/255, pooled on the GPU each step",
-                       "eval_kernel": "CUDA-core FP32, layers chained in shared memory (32-sample tiles)",
+                       "eval_kernel": ("tcgen05, FP16 operand pieces (FP32-class), FP32 accumulation in TMEM; layer 4 "
+                                       "and the loss in FP32" if tensor else
+                                       "CUDA-core FP32, layers chained in shared memory (64-sample tiles)"),
                        "l2": f"inputs larger than L2 (2 population buffers of "
                              f"{pop * leea.leea_padded_params(dims) * 4 / 1e6:.0f} MB), no flush"},
             "network_samples_per_sec": gen_per_s * pop * batch, "e2e": e2e,
-            "gpu_launches": int(steps * (1 + sum(kernels_per_generation(pop, batch, 0).values()))),
+            # + the max-pool, + the FP32 recomputation launch of marked individuals after the tensor-core evaluation
+            "gpu_launches": int(steps * (1 + (1 if tensor else 0) + sum(kernels_per_generation(pop, batch, 0).values()))),
             "roofline": roofline, "kernels": kernels, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x_last = xtr[idx[warmup + steps]].astype(np.float64)
