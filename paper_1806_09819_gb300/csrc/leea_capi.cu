@@ -230,10 +230,11 @@ leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop
 {
     if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
     if (net.n_layers > 2) {  // several hidden layers
-        const bool tc = eval_mlp_tc_supported(net, pop_dev);
+        const bool tc = eval_mlp_tc_supported(net, pop_dev) && (reinterpret_cast<uintptr_t>(x) & 3u) == 0;
         if (path == LEEA_EVAL_TENSOR && !tc)
             return fail(LEEA_EINVAL, "tensor-core evaluation of deeper nets needs three hidden layers, widths multiples "
-                                     "of 16 in [16, 256] summing to <= 512, d_0 %% 4 == 0, d_0 <= 256, d_out <= 16");
+                                     "of 16 in [16, 256] summing to <= 512, d_0 %% 4 == 0, d_0 <= 256, d_out <= 16 "
+                                     "and 4-byte aligned inputs");
         if (tc && path != LEEA_EVAL_SIMT) {
             unsigned int* status = device_status_ptr();
             if (!status) return fail(LEEA_ECUDA, "device status word unavailable");

@@ -264,29 +264,40 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                             break;
                         }
                         sphase ^= 1u;
-                        for (int i = ct; i < N * 8; i += kConvThreads) {
-                            const int n = i >> 3, ch = i & 7;
-                            const int k = kb * 64 + 8 * ch;
-                            float v[8];
-                            if (k < K) {
-                                const float4* src = reinterpret_cast<const float4*>(W + static_cast<int64_t>(n) * K + k);
-                                const float4 v0 = __ldg(src);
-                                const float4 v1 = k + 4 < K ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-                                v[0] = v0.x; v[1] = v0.y; v[2] = v0.z; v[3] = v0.w;
-                                v[4] = v1.x; v[5] = v1.y; v[6] = v1.z; v[7] = v1.w;
-                            } else {
+                        // kBatch items at a time: their loads are all in flight
+                        // before the first conversion.
+                        constexpr int kBatch = 4;
+                        for (int i0 = ct; i0 < N * 8; i0 += kBatch * kConvThreads) {
+                            float4 v[kBatch][2];
 #pragma unroll
-                                for (int e = 0; e < 8; ++e) v[e] = 0.0f;
+                            for (int b = 0; b < kBatch; ++b) {
+                                const int i = i0 + b * kConvThreads;
+                                const int n = i >> 3, k = kb * 64 + 8 * (i & 7);
+                                v[b][0] = v[b][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (i < N * 8 && k < K) {
+                                    const float4* src =
+                                        reinterpret_cast<const float4*>(W + static_cast<int64_t>(n) * K + k);
+                                    v[b][0] = __ldg(src);
+                                    if (k + 4 < K) v[b][1] = __ldg(src + 1);
+                                }
                             }
-                            uint32_t hi[4], lo[4];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) {
-                                split2x2(v[2 * e], v[2 * e + 1], hi[e], lo[e]);
-                                bad |= fabsf(v[2 * e]) >= kPieceRange || fabsf(v[2 * e + 1]) >= kPieceRange;
+                            for (int b = 0; b < kBatch; ++b) {
+                                const int i = i0 + b * kConvThreads;
+                                if (i >= N * 8) break;
+                                const float w[8] = { v[b][0].x, v[b][0].y, v[b][0].z, v[b][0].w,
+                                                     v[b][1].x, v[b][1].y, v[b][1].z, v[b][1].w };
+                                uint32_t hi[4], lo[4];
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) {
+                                    split2x2(w[2 * e], w[2 * e + 1], hi[e], lo[e]);
+                                    bad |= fabsf(w[2 * e]) >= kPieceRange || fabsf(w[2 * e + 1]) >= kPieceRange;
+                                }
+                                const uint32_t off = swz(i >> 3, i & 7);
+                                *reinterpret_cast<uint4*>(s.slot + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                                *reinterpret_cast<uint4*>(s.slot + N * 128 + off) =
+                                    make_uint4(lo[0], lo[1], lo[2], lo[3]);
                             }
-                            const uint32_t off = swz(n, ch);
-                            *reinterpret_cast<uint4*>(s.slot + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                            *reinterpret_cast<uint4*>(s.slot + N * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                         }
                         ptx::fence_proxy_async_smem();
                         __syncwarp();
@@ -324,18 +335,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                 // (1) the tile's levels as FP16 into the hi part of the region
                 const int smp = t * kTile + row;
                 const bool live = smp < a.batch;
-                const uint8_t* xr = a.x + static_cast<int64_t>(live ? smp : 0) * a.dims[0];
-                for (int k0 = 0; k0 < a.k16[0]; k0 += 8) {
-                    uint32_t w[4];
+                // 4 levels per 32-bit load (d0 % 4 == 0), 8 chunks of 8 levels
+                // per batch of loads; a level k < 1024 is (1024 + k) - 1024 in
+                // FP16, and 1024 + k has the bit pattern 0x6400 | k.
+                const uint32_t* xr = reinterpret_cast<const uint32_t*>(a.x + static_cast<int64_t>(live ? smp : 0) *
+                                                                                 a.dims[0]);
+                const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
+                for (int k0 = 0; k0 < a.k16[0]; k0 += 64) {
+                    uint32_t wd[16];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int k = k0 + 2 * e;
-                        const float l0 = (live && k < a.dims[0]) ? static_cast<float>(__ldg(xr + k)) : 0.0f;
-                        const float l1 = (live && k + 1 < a.dims[0]) ? static_cast<float>(__ldg(xr + k + 1)) : 0.0f;
-                        w[e] = half2_bits(__floats2half2_rn(l0, l1));
+                    for (int e = 0; e < 16; ++e) {
+                        const int k = k0 + 4 * e;
+                        wd[e] = (live && k < a.dims[0]) ? __ldg(xr + (k >> 2)) : 0u;
                     }
-                    *reinterpret_cast<uint4*>(s.region + (k0 >> 6) * kBlockBytes + swz(row, (k0 & 63) >> 3)) =
-                        make_uint4(w[0], w[1], w[2], w[3]);
+#pragma unroll
+                    for (int ch = 0; ch < 8; ++ch) {
+                        if (k0 + 8 * ch >= a.k16[0]) break;
+                        uint32_t h[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const uint32_t biased =
+                                __byte_perm(wd[2 * ch + (e >> 1)], 0x64646464u, (e & 1) ? 0x4342u : 0x4140u);
+                            h[e] = half2_bits(__hsub2(*reinterpret_cast<const __half2*>(&biased), k1024));
+                        }
+                        *reinterpret_cast<uint4*>(s.region + (k0 >> 6) * kBlockBytes + swz(row, ch)) =
+                            make_uint4(h[0], h[1], h[2], h[3]);
+                    }
                 }
                 ptx::fence_proxy_async_smem();
                 ptx::tc_fence_before();
