@@ -271,8 +271,14 @@ leea_status leea_breed_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_d
  * so identical individuals get bitwise identical results.
  * n_dims == 3 (d_0-h-d_out with d_out <= 32), or n_dims > 3 with every layer
  * input and hidden width <= 256 and d_out <= 32 (the paper's 196-256-128-64-10,
- * Section 4.1): such nets evaluate in FP32 on the CUDA cores (eval_path AUTO
- * or SIMT), layer by layer with ReLU between layers.  f_adj_dev and
+ * Section 4.1), layer by layer with ReLU between layers.  Deeper nets take
+ * the CUDA cores in exact FP32 (SIMT; AUTO for float inputs), or, for 8-bit
+ * inputs and three hidden layers (widths multiples of 16 in [16, 256] summing
+ * to <= 512, d_0 % 4 == 0, d_0 <= 256, d_out <= 16, 4-byte aligned x), the
+ * tensor cores (AUTO or TENSOR): FP16 operand pieces of 2^8 w and 2^8 h
+ * (hi.hi + hi.lo + lo.hi; the levels are exact), FP32 accumulation, FP32
+ * bias, ReLU, last layer and loss; an individual with a weight or activation
+ * |v| >= 128 is recomputed in FP32 on the CUDA cores.  f_adj_dev and
  * correct_dev may be NULL; f_raw_dev may not.  eval_path: LEEA_EVAL_*. */
 leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
                           const float* pop_dev, const float* x_dev, const int32_t* y_dev,
@@ -390,7 +396,8 @@ typedef struct leea_state leea_state;
  * which every later call of this object uses.  *out receives the object.
  * Nets: n_dims == 3 with d_out <= 32, or n_dims > 3 (several hidden layers,
  * every layer input and hidden width <= 256, d_out <= 32; precision 0,
- * eval_path AUTO or SIMT: FP32 on the CUDA cores). */
+ * breeding and evaluation as separate kernels; evaluation as in
+ * leea_evaluate / leea_evaluate_u8). */
 leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims,
                         const leea_params* p, uint64_t seed, void* stream,
                         leea_state** out);

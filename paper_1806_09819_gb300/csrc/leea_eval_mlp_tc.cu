@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                         sphase ^= 1u;
                         // kBatch items at a time: their loads are all in flight
                         // before the first conversion.
-                        constexpr int kBatch = 4;
+                        constexpr int kBatch = 8;
                         for (int i0 = ct; i0 < N * 8; i0 += kBatch * kConvThreads) {
                             float4 v[kBatch][2];
 #pragma unroll
