@@ -21,13 +21,13 @@
 // their tiles in order):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
 //   warps 1-8   converters: each 64-input block of W1, W2, W3 into the two
-//               FP16 pieces, 128-byte swizzled, in a shared-memory slot
+//               FP16 pieces, 128-byte swizzled, in one of two weight buffers
 //   warps 9-12  the epilogue (TMEM lane = sample): the tile's levels as the
 //               layer-1 operand, the activations of layers 1 and 2 as the
 //               next operands, layer 4 and the loss
-// The phases of a unit run in sequence (one weight slot, one activation
-// region).  Every wait is bounded; on expiry the kernel sets
-// kStatusEvalTimeout and exits.
+// The layers of a unit run in sequence (one activation region), each
+// layer's weight blocks double-buffered.  Every wait is bounded; on expiry
+// the kernel sets kStatusEvalTimeout and exits.
 #include <cuda.h>
 
 #include <cuda_fp16.h>
@@ -82,7 +82,7 @@ struct TcSmem {
     uint8_t* region;  // activations: hi piece [0, 64 KB), lo piece [64 KB, 128 KB); the levels in the hi part
     uint8_t* slot;    // weights: hi piece then lo piece, N x 128 bytes each per 64-input block
     float *b1, *b2, *b3, *w4t, *b4;
-    uint64_t *slot_full, *slot_empty, *x_ready, *d_full, *h_ready, *drain;
+    uint64_t *buf_full, *buf_empty, *x_ready, *d_full, *h_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
@@ -97,7 +97,7 @@ __host__ __device__ inline size_t tc_param_floats(const int32_t* dims)
 
 __host__ __device__ inline size_t tc_smem_bytes(const int32_t* dims)
 {
-    return 1024 + kRegionBytes + kSlotBytes + sizeof(float) * tc_param_floats(dims) + 8 * 16 + 64;
+    return 1024 + kRegionBytes + kSlotBytes + sizeof(float) * tc_param_floats(dims) + 8 * 16 + 64;  // 11 barriers, 11 words
 }
 
 __device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
@@ -114,13 +114,13 @@ __device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
     uint8_t* p = reinterpret_cast<uint8_t*>(s.b4 + kMaxOutTc);
     p += (8u - (reinterpret_cast<uintptr_t>(p) & 7u)) & 7u;
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
-    s.slot_full = bars;
-    s.slot_empty = bars + 1;
-    s.x_ready = bars + 2;
-    s.d_full = bars + 3;   // [3]
-    s.h_ready = bars + 6;  // [2]
-    s.drain = bars + 8;
-    uint32_t* w = reinterpret_cast<uint32_t*>(bars + 9);
+    s.buf_full = bars;       // [2]
+    s.buf_empty = bars + 2;  // [2]
+    s.x_ready = bars + 4;
+    s.d_full = bars + 5;     // [3]
+    s.h_ready = bars + 8;    // [2]
+    s.drain = bars + 10;
+    uint32_t* w = reinterpret_cast<uint32_t*>(bars + 11);
     s.tmem_holder = w;
     s.abort_flag = reinterpret_cast<volatile int*>(w + 1);
     s.ep_go = reinterpret_cast<int*>(w + 2);
@@ -159,6 +159,23 @@ __device__ __forceinline__ uint32_t swz(int r, int ch)
 
 __device__ __forceinline__ int layer_blocks(const MlpTcArgs& a, int l) { return (a.k16[l] + 63) / 64; }
 
+// The weight blocks of a layer alternate between two buffers, so that one is
+// converted while the MMAs read the other.  Layer 1: the slot, and the lo half
+// of the activation region (it holds nothing while layer 1 runs: the levels
+// use the hi half).  Layers 2 and 3 with N <= 128 (blocks of <= 32 KB): the
+// slot's two halves; wider ones take the whole slot for every block.
+__device__ __forceinline__ int buffer_of(const MlpTcArgs& a, int l, int kb)
+{
+    return (l == 0 || a.dims[l + 1] <= 128) ? (kb & 1) : 0;
+}
+
+// Offset of weight buffer b of layer l from the start of the region.
+__device__ __forceinline__ uint32_t buffer_offset(int l, int b)
+{
+    if (b == 0) return kRegionBytes;
+    return l == 0 ? kHalfRegion : kRegionBytes + kSlotBytes / 2;
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -168,8 +185,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
     const uint32_t col[3] = { 0u, static_cast<uint32_t>(d1), static_cast<uint32_t>(d1 + d2) };
 
     if (threadIdx.x == 0) {
-        ptx::mbar_init(s.slot_full, kConvWarps);
-        ptx::mbar_init(s.slot_empty, 1);
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(&s.buf_full[i], kConvWarps);
+            ptx::mbar_init(&s.buf_empty[i], 1);
+        }
         ptx::mbar_init(s.x_ready, kEpiThreads);
         for (int i = 0; i < 3; ++i) ptx::mbar_init(&s.d_full[i], 1);
         for (int i = 0; i < 2; ++i) ptx::mbar_init(&s.h_ready[i], kEpiThreads);
@@ -187,8 +206,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
     if (warp == 0) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const uint32_t region = ptx::smem_u32(s.region), slot = ptx::smem_u32(s.slot);
-            uint32_t unit = 0, sphase = 0;
+            const uint32_t region = ptx::smem_u32(s.region);
+            uint32_t unit = 0, bphase = 0;  // bit b: phase of weight buffer b
             bool ok = true;
             for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
                 for (int t = 0; ok && t < a.n_tiles; ++t, ++unit) {
@@ -210,12 +229,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                         const uint32_t d_tmem = tmem_base + col[l];
                         const int blocks = layer_blocks(a, l);
                         for (int kb = 0; kb < blocks; ++kb) {
-                            if (!ptx::mbar_wait_bounded(s.slot_full, sphase, s.abort_flag, kWaitLimitNs)) {
+                            const int b = buffer_of(a, l, kb);
+                            if (!ptx::mbar_wait_bounded(&s.buf_full[b], (bphase >> b) & 1u, s.abort_flag,
+                                                        kWaitLimitNs)) {
                                 raise_abort(s, a);
                                 ok = false;
                                 break;
                             }
-                            sphase ^= 1u;
+                            bphase ^= 1u << b;
+                            const uint32_t slot = region + buffer_offset(l, b);
                             ptx::tc_fence_after();
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
@@ -233,7 +255,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                                     ptx::mma_f16(d_tmem, ptx::smem_desc_sw128(a_hi + kHalfRegion),
                                                  ptx::smem_desc_sw128(b_hi), idesc, 1u);
                             }
-                            ptx::mma_commit(s.slot_empty);
+                            ptx::mma_commit(&s.buf_empty[b]);
                         }
                         if (ok) ptx::mma_commit(&s.d_full[l]);
                     }
@@ -247,23 +269,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
         // ------------------------------------------------------------ converters
         // Item i of a block: row n = i / 8, inputs 8 (i % 8) .. + 7 of the block.
         const int ct = threadIdx.x - 32 * kFirstConvWarp;
-        uint32_t sphase = 0;
+        uint32_t bphase = 0, unit = 0;
         bool ok = true;
         for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
             const float* net = a.popv + static_cast<int64_t>(p) * a.c_pad;
             bool bad = false;
-            for (int t = 0; ok && t < a.n_tiles; ++t) {
+            for (int t = 0; ok && t < a.n_tiles; ++t, ++unit) {
+                // The buffers of this unit's layer 1 (the slot, the region's lo
+                // half) are free once the previous unit's last MMAs are done.
+                if (unit > 0 &&
+                    !ptx::mbar_wait_bounded(&s.d_full[2], (unit - 1) & 1u, s.abort_flag, kWaitLimitNs)) {
+                    raise_abort(s, a);
+                    ok = false;
+                    break;
+                }
                 for (int l = 0; ok && l < 3; ++l) {
                     const int K = a.dims[l], N = a.dims[l + 1];
                     const float* W = net + a.w_off[l];
                     const int blocks = layer_blocks(a, l);
                     for (int kb = 0; kb < blocks; ++kb) {
-                        if (!ptx::mbar_wait_bounded(s.slot_empty, sphase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+                        const int b = buffer_of(a, l, kb);
+                        if (!ptx::mbar_wait_bounded(&s.buf_empty[b], ((bphase >> b) & 1u) ^ 1u, s.abort_flag,
+                                                    kWaitLimitNs)) {
                             raise_abort(s, a);
                             ok = false;
                             break;
                         }
-                        sphase ^= 1u;
+                        bphase ^= 1u << b;
+                        uint8_t* buf = s.region + buffer_offset(l, b);
                         // kBatch items at a time: their loads are all in flight
                         // before the first conversion.
                         constexpr int kBatch = 8;
@@ -294,14 +327,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                                     bad |= fabsf(w[2 * e]) >= kPieceRange || fabsf(w[2 * e + 1]) >= kPieceRange;
                                 }
                                 const uint32_t off = swz(i >> 3, i & 7);
-                                *reinterpret_cast<uint4*>(s.slot + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                                *reinterpret_cast<uint4*>(s.slot + N * 128 + off) =
-                                    make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                                *reinterpret_cast<uint4*>(buf + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                                *reinterpret_cast<uint4*>(buf + N * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
                             }
                         }
                         ptx::fence_proxy_async_smem();
                         __syncwarp();
-                        if (lane == 0) ptx::mbar_arrive(s.slot_full);
+                        if (lane == 0) ptx::mbar_arrive(&s.buf_full[b]);
                     }
                 }
             }
