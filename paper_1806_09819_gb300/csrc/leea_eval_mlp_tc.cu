@@ -16,13 +16,16 @@
 // cross-entropy and the loss sums in FP32, tiles in order.  A weight or an
 // activation with |v| >= 128 (2^8 |v| could overflow its FP16 piece) marks the
 // individual; the CUDA-core kernel then recomputes its fitness in FP32.
+// The weights are split once per evaluation (split_weights_kernel), not once
+// per tile.
 //
 // Warp roles (persistent CTA, one per SM; individuals strided by gridDim.x,
 // their tiles in order):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
-//   warps 1-8   converters: each 64-input block of W1, W2, W3 into the two
-//               FP16 pieces, 128-byte swizzled, in one of two weight buffers
-//   warps 9-12  the epilogue (TMEM lane = sample): the tile's levels as the
+//   warp 1      producer: one bulk copy per 64-input block of W1, W2, W3,
+//               already split into FP16 pieces and swizzled by
+//               split_weights_kernel, into one of two weight buffers
+//   warps 2-5   the epilogue (TMEM lane = sample): the tile's levels as the
 //               layer-1 operand, the activations of layers 1 and 2 as the
 //               next operands, layer 4 and the loss
 // The layers of a unit run in sequence (one activation region), each
@@ -41,10 +44,7 @@ namespace leea {
 
 namespace {
 
-constexpr int kConvWarps = 8;
-constexpr int kFirstConvWarp = 1;
-constexpr int kFirstEpiWarp = kFirstConvWarp + kConvWarps;
-constexpr int kConvThreads = 32 * kConvWarps;
+constexpr int kFirstEpiWarp = 2;
 constexpr int kEpiThreads = 128;
 constexpr int kTcThreads = 32 * (kFirstEpiWarp + 4);
 constexpr int kTile = 128;                      // samples per unit (MMA M)
@@ -76,6 +76,12 @@ struct MlpTcArgs {
     int32_t* correct;
     int32_t* flagged;    // [pop], zeroed before the launch: 1 = recompute in FP32
     unsigned int* status;
+    // the weights of layers 1-3 as FP16 pieces, per individual (piece_stride
+    // bytes): layer l's 64-input blocks from byte layer_off[l], each block the
+    // hi piece (N rows of 128 bytes, swizzled) then the lo piece
+    const uint8_t* pieces;
+    int64_t piece_stride;
+    int64_t layer_off[3];
 };
 
 struct TcSmem {
@@ -186,7 +192,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
-            ptx::mbar_init(&s.buf_full[i], kConvWarps);
+            ptx::mbar_init(&s.buf_full[i], 1);
             ptx::mbar_init(&s.buf_empty[i], 1);
         }
         ptx::mbar_init(s.x_ready, kEpiThreads);
@@ -265,79 +271,53 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
             volatile int never = 0;
             ptx::mbar_wait_bounded(s.drain, 0u, &never, ok ? kWaitLimitNs : kDrainLimitNs);
         }
-    } else if (warp < kFirstEpiWarp) {
-        // ------------------------------------------------------------ converters
-        // Item i of a block: row n = i / 8, inputs 8 (i % 8) .. + 7 of the block.
-        const int ct = threadIdx.x - 32 * kFirstConvWarp;
-        uint32_t bphase = 0, unit = 0;
-        bool ok = true;
-        for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
-            const float* net = a.popv + static_cast<int64_t>(p) * a.c_pad;
-            bool bad = false;
-            for (int t = 0; ok && t < a.n_tiles; ++t, ++unit) {
-                // The buffers of this unit's layer 1 (the slot, the region's lo
-                // half) are free once the previous unit's last MMAs are done.
-                if (unit > 0 &&
-                    !ptx::mbar_wait_bounded(&s.d_full[2], (unit - 1) & 1u, s.abort_flag, kWaitLimitNs)) {
-                    raise_abort(s, a);
-                    ok = false;
-                    break;
-                }
-                for (int l = 0; ok && l < 3; ++l) {
-                    const int K = a.dims[l], N = a.dims[l + 1];
-                    const float* W = net + a.w_off[l];
-                    const int blocks = layer_blocks(a, l);
-                    for (int kb = 0; kb < blocks; ++kb) {
-                        const int b = buffer_of(a, l, kb);
-                        if (!ptx::mbar_wait_bounded(&s.buf_empty[b], ((bphase >> b) & 1u) ^ 1u, s.abort_flag,
-                                                    kWaitLimitNs)) {
-                            raise_abort(s, a);
-                            ok = false;
-                            break;
-                        }
-                        bphase ^= 1u << b;
-                        uint8_t* buf = s.region + buffer_offset(l, b);
-                        // kBatch items at a time: their loads are all in flight
-                        // before the first conversion.
-                        constexpr int kBatch = 8;
-                        for (int i0 = ct; i0 < N * 8; i0 += kBatch * kConvThreads) {
-                            float4 v[kBatch][2];
-#pragma unroll
-                            for (int b = 0; b < kBatch; ++b) {
-                                const int i = i0 + b * kConvThreads;
-                                const int n = i >> 3, k = kb * 64 + 8 * (i & 7);
-                                v[b][0] = v[b][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-                                if (i < N * 8 && k < K) {
-                                    const float4* src =
-                                        reinterpret_cast<const float4*>(W + static_cast<int64_t>(n) * K + k);
-                                    v[b][0] = __ldg(src);
-                                    if (k + 4 < K) v[b][1] = __ldg(src + 1);
-                                }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ producer
+        // One bulk copy per 64-input weight block: the pieces are already in
+        // the swizzled operand layout (split_weights_kernel).
+        if (lane == 0) {
+            uint32_t bphase = 0, unit = 0;
+            uint32_t issued = 0, parity = 0;  // per buffer: a copy was issued / the parity it completes
+            bool ok = true;
+            for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
+                const uint8_t* src_p = a.pieces + static_cast<int64_t>(p) * a.piece_stride;
+                for (int t = 0; ok && t < a.n_tiles; ++t, ++unit) {
+                    // The buffers of this unit's layer 1 (the slot, the region's lo
+                    // half) are free once the previous unit's last MMAs are done.
+                    if (unit > 0 &&
+                        !ptx::mbar_wait_bounded(&s.d_full[2], (unit - 1) & 1u, s.abort_flag, kWaitLimitNs)) {
+                        raise_abort(s, a);
+                        ok = false;
+                        break;
+                    }
+                    for (int l = 0; ok && l < 3; ++l) {
+                        const uint32_t bytes = static_cast<uint32_t>(a.dims[l + 1]) * 256u;
+                        const int blocks = layer_blocks(a, l);
+                        for (int kb = 0; kb < blocks; ++kb) {
+                            const int b = buffer_of(a, l, kb);
+                            if (!ptx::mbar_wait_bounded(&s.buf_empty[b], ((bphase >> b) & 1u) ^ 1u, s.abort_flag,
+                                                        kWaitLimitNs)) {
+                                raise_abort(s, a);
+                                ok = false;
+                                break;
                             }
-#pragma unroll
-                            for (int b = 0; b < kBatch; ++b) {
-                                const int i = i0 + b * kConvThreads;
-                                if (i >= N * 8) break;
-                                const float w[8] = { v[b][0].x, v[b][0].y, v[b][0].z, v[b][0].w,
-                                                     v[b][1].x, v[b][1].y, v[b][1].z, v[b][1].w };
-                                uint32_t hi[4], lo[4];
-#pragma unroll
-                                for (int e = 0; e < 4; ++e) {
-                                    split2x2(w[2 * e], w[2 * e + 1], hi[e], lo[e]);
-                                    bad |= fabsf(w[2 * e]) >= kPieceRange || fabsf(w[2 * e + 1]) >= kPieceRange;
-                                }
-                                const uint32_t off = swz(i >> 3, i & 7);
-                                *reinterpret_cast<uint4*>(buf + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                                *reinterpret_cast<uint4*>(buf + N * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                            }
+                            ptx::mbar_arrive_expect_tx(&s.buf_full[b], bytes);
+                            ptx::bulk_load(s.region + buffer_offset(l, b),
+                                           src_p + a.layer_off[l] + static_cast<int64_t>(kb) * bytes, bytes,
+                                           &s.buf_full[b]);
+                            issued |= 1u << b;
+                            parity = (parity & ~(1u << b)) | (((bphase >> b) & 1u) << b);
+                            bphase ^= 1u << b;
                         }
-                        ptx::fence_proxy_async_smem();
-                        __syncwarp();
-                        if (lane == 0) ptx::mbar_arrive(&s.buf_full[b]);
                     }
                 }
             }
-            if (bad) a.flagged[p] = 1;  // read by the FP32 recomputation after this kernel
+            if (!ok) {  // let copies in flight land before the CTA exits
+                volatile int never = 0;
+                for (int b = 0; b < 2; ++b)
+                    if (issued & (1u << b))
+                        ptx::mbar_wait_bounded(&s.buf_full[b], (parity >> b) & 1u, &never, kDrainLimitNs);
+            }
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -524,6 +504,47 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
     }
 }
 
+// Each individual's weights of layers 1-3 as FP16 pieces of 2^8 w in the
+// swizzled operand layout (individuals strided over blockIdx.y); a weight
+// |w| >= 128 marks the individual for the FP32 recomputation.
+__global__ void __launch_bounds__(256) split_weights_kernel(const MlpTcArgs a)
+{
+    for (int p = blockIdx.y; p < a.pop; p += gridDim.y) {
+        const float* net = a.popv + static_cast<int64_t>(p) * a.c_pad;
+        uint8_t* dst_p = const_cast<uint8_t*>(a.pieces) + static_cast<int64_t>(p) * a.piece_stride;
+        int n_items[3];
+        for (int l = 0; l < 3; ++l) n_items[l] = layer_blocks(a, l) * a.dims[l + 1] * 8;
+        const int total = n_items[0] + n_items[1] + n_items[2];
+        bool bad = false;
+        for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < total; it += gridDim.x * blockDim.x) {
+            int l = 0, r = it;
+            while (r >= n_items[l]) r -= n_items[l++];
+            const int K = a.dims[l], N = a.dims[l + 1];
+            const int kb = r / (N * 8), rem = r - kb * N * 8;
+            const int n = rem >> 3, ch = rem & 7;
+            const int k = kb * 64 + 8 * ch;
+            float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+            if (k < K) {
+                const float4* src = reinterpret_cast<const float4*>(net + a.w_off[l] + static_cast<int64_t>(n) * K + k);
+                v0 = __ldg(src);
+                if (k + 4 < K) v1 = __ldg(src + 1);
+            }
+            const float w[8] = { v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w };
+            uint32_t hi[4], lo[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                split2x2(w[2 * e], w[2 * e + 1], hi[e], lo[e]);
+                bad |= fabsf(w[2 * e]) >= kPieceRange || fabsf(w[2 * e + 1]) >= kPieceRange;
+            }
+            uint8_t* blk = dst_p + a.layer_off[l] + static_cast<int64_t>(kb) * N * 256;
+            const uint32_t off = swz(n, ch);
+            *reinterpret_cast<uint4*>(blk + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+            *reinterpret_cast<uint4*>(blk + N * 128 + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+        if (bad) a.flagged[p] = 1;
+    }
+}
+
 // Library-owned flag array for the recomputation, grown on demand.
 int32_t* flag_buffer(int32_t pop)
 {
@@ -537,6 +558,23 @@ int32_t* flag_buffer(int32_t pop)
         cap = 0;
         if (cudaMalloc(&buf, sizeof(int32_t) * static_cast<size_t>(pop)) != cudaSuccess) return nullptr;
         cap = pop;
+    }
+    return buf;
+}
+
+// Library-owned buffer of the weight pieces, grown on demand.
+uint8_t* piece_buffer(size_t bytes)
+{
+    static std::mutex mu;
+    static uint8_t* buf = nullptr;
+    static size_t cap = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (bytes > cap) {
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        cap = 0;
+        if (cudaMalloc(&buf, bytes) != cudaSuccess) return nullptr;
+        cap = bytes;
     }
     return buf;
 }
@@ -584,8 +622,22 @@ cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* p
     a.status = status;
     a.flagged = flag_buffer(pop);
     if (!a.flagged) return cudaErrorMemoryAllocation;
+    int64_t off = 0;
+    for (int l = 0; l < 3; ++l) {
+        a.layer_off[l] = off;
+        off += static_cast<int64_t>((a.k16[l] + 63) / 64) * net.dims[l + 1] * 256;
+    }
+    a.piece_stride = off;
+    a.pieces = piece_buffer(static_cast<size_t>(off) * static_cast<size_t>(pop));
+    if (!a.pieces) return cudaErrorMemoryAllocation;
     cudaError_t err = cudaMemsetAsync(a.flagged, 0, sizeof(int32_t) * static_cast<size_t>(pop), stream);
     if (err != cudaSuccess) return err;
+    {
+        int items = 0;
+        for (int l = 0; l < 3; ++l) items += ((a.k16[l] + 63) / 64) * net.dims[l + 1] * 8;
+        split_weights_kernel<<<dim3((items + 255) / 256, pop < 65535 ? pop : 65535), 256, 0, stream>>>(a);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    }
     const size_t smem = tc_smem_bytes(net.dims);
     err = cudaFuncSetAttribute(eval_mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
