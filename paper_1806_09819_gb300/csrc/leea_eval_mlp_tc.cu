@@ -25,9 +25,11 @@
 //   warp 1      producer: one bulk copy per 64-input block of W1, W2, W3,
 //               already split into FP16 pieces and swizzled by
 //               split_weights_kernel, into one of two weight buffers
-//   warps 2-5   the epilogue (TMEM lane = sample): the tile's levels as the
-//               layer-1 operand, the activations of layers 1 and 2 as the
-//               next operands, layer 4 and the loss
+//   warps 2-9   the epilogue (TMEM lane = sample, two warps per lane
+//               quarter, each with half of a layer's 16-column groups): the
+//               tile's levels as the layer-1 operand, the activations of
+//               layers 1 and 2 as the next operands, layer 4 (the halves'
+//               partial logits added through shared memory) and the loss
 // The layers of a unit run in sequence (one activation region), each
 // layer's weight blocks double-buffered.  Every wait is bounded; on expiry
 // the kernel sets kStatusEvalTimeout and exits.
@@ -45,8 +47,9 @@ namespace leea {
 namespace {
 
 constexpr int kFirstEpiWarp = 2;
-constexpr int kEpiThreads = 128;
-constexpr int kTcThreads = 32 * (kFirstEpiWarp + 4);
+constexpr int kEpiWarps = 8;  // two per TMEM lane quarter: half of a layer's columns each
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kTcThreads = 32 * (kFirstEpiWarp + kEpiWarps);
 constexpr int kTile = 128;                      // samples per unit (MMA M)
 constexpr uint32_t kBlockBytes = kTile * 128;   // one 64-input block of a 128-row operand
 constexpr uint32_t kHalfRegion = 4 * kBlockBytes;  // 64 KB: one piece of up to 256 inputs
@@ -88,6 +91,7 @@ struct TcSmem {
     uint8_t* region;  // activations: hi piece [0, 64 KB), lo piece [64 KB, 128 KB); the levels in the hi part
     uint8_t* slot;    // weights: hi piece then lo piece, N x 128 bytes each per 64-input block
     float *b1, *b2, *b3, *w4t, *b4;
+    float* plog;  // [128][16]: the second half's partial layer-4 logits
     uint64_t *buf_full, *buf_empty, *x_ready, *d_full, *h_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
@@ -98,7 +102,7 @@ struct TcSmem {
 
 __host__ __device__ inline size_t tc_param_floats(const int32_t* dims)
 {
-    return static_cast<size_t>(dims[1] + dims[2] + dims[3] + dims[3] * kMaxOutTc + kMaxOutTc);
+    return static_cast<size_t>(dims[1] + dims[2] + dims[3] + dims[3] * kMaxOutTc + kMaxOutTc + kTile * kMaxOutTc);
 }
 
 __host__ __device__ inline size_t tc_smem_bytes(const int32_t* dims)
@@ -117,7 +121,8 @@ __device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
     s.b3 = s.b2 + a.dims[2];
     s.w4t = s.b3 + a.dims[3];
     s.b4 = s.w4t + a.dims[3] * kMaxOutTc;
-    uint8_t* p = reinterpret_cast<uint8_t*>(s.b4 + kMaxOutTc);
+    s.plog = s.b4 + kMaxOutTc;
+    uint8_t* p = reinterpret_cast<uint8_t*>(s.plog + kTile * kMaxOutTc);
     p += (8u - (reinterpret_cast<uintptr_t>(p) & 7u)) & 7u;
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.buf_full = bars;       // [2]
@@ -323,6 +328,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
         // ------------------------------------------------------------ epilogue
         const int et = threadIdx.x - 32 * kFirstEpiWarp;
         const int q = warp & 3;
+        const int half = (warp - kFirstEpiWarp) >> 2;
         const int row = q * 32 + lane;
         const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
         uint32_t unit = 0;
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                 const uint32_t* xr = reinterpret_cast<const uint32_t*>(a.x + static_cast<int64_t>(live ? smp : 0) *
                                                                                  a.dims[0]);
                 const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
-                for (int k0 = 0; k0 < a.k16[0]; k0 += 64) {
+                for (int k0 = 64 * half; k0 < a.k16[0]; k0 += 128) {  // the halves take alternate blocks
                     uint32_t wd[16];
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
@@ -390,8 +396,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                     const int N = a.dims[l + 1];
                     const float* bias = l == 0 ? s.b1 : (l == 1 ? s.b2 : s.b3);
                     const float scale = l == 0 ? a.inv_div : 1.0f / (kPieceScale * kPieceScale);
+                    // this half's 16-column groups
+                    const int groups = N / 16, g0 = half ? groups / 2 : 0, g1 = half ? groups : groups / 2;
                     if (l < 2) {
-                        for (int c = 0; c < N; c += 16) {
+                        for (int c = 16 * g0; c < 16 * g1; c += 16) {
                             float v[16];
                             ptx::tmem_ld16(tmem_base + lane_addr + col[l] + static_cast<uint32_t>(c), v);
                             uint32_t hi[8], lo[8];
@@ -419,7 +427,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                         float logit[kMaxOutTc];
 #pragma unroll
                         for (int o = 0; o < kMaxOutTc; ++o) logit[o] = 0.0f;
-                        for (int c = 0; c < N; c += 16) {
+                        for (int c = 16 * g0; c < 16 * g1; c += 16) {
                             float v[16];
                             ptx::tmem_ld16(tmem_base + lane_addr + col[l] + static_cast<uint32_t>(c), v);
 #pragma unroll
@@ -439,12 +447,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                             }
                         }
                         ptx::tc_fence_before();
+                        if (half == 1) {
+#pragma unroll
+                            for (int o = 0; o < kMaxOutTc; ++o) s.plog[row * kMaxOutTc + o] = logit[o];
+                        }
+                        ptx::named_barrier_sync(1, kEpiThreads);  // the second half's partial logits are in
                         float loss = 0.0f;
                         int32_t good = 0;
-                        if (live) {
+                        if (live && half == 0) {
                             float z[kMaxOutTc];
 #pragma unroll
-                            for (int o = 0; o < kMaxOutTc; ++o) z[o] = o < d_out ? logit[o] + s.b4[o] : 0.0f;
+                            for (int o = 0; o < kMaxOutTc; ++o)
+                                z[o] = o < d_out ? (logit[o] + s.plog[row * kMaxOutTc + o]) + s.b4[o] : 0.0f;
                             float zmax = z[0];
                             int arg = 0;
 #pragma unroll
@@ -471,7 +485,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                             loss += __shfl_xor_sync(0xFFFFFFFFu, loss, off);
                             good += __shfl_xor_sync(0xFFFFFFFFu, good, off);
                         }
-                        if (lane == 0) {
+                        if (lane == 0 && half == 0) {
                             s.red_loss[q] = loss;
                             s.red_ok[q] = good;
                         }
