@@ -162,6 +162,14 @@ def test_mlp_rejects_tensor_path_and_wide_layers(gpu):
         gpu.leea_evaluate_u8(2, wide, pw, xw, 255.0, y, 4, 1.0, None, f)
 
 
+def test_paper_net_state_object_limits(gpu):
+    # Deeper nets: FP32 populations, breeding and evaluation as separate kernels.
+    for prm in (dict(eval_path=gpu.EVAL_FUSED), dict(precision=1)):
+        with pytest.raises(gpu.LeeaError) as e:
+            gpu.LeeaState(8, PAPER_DIMS, gpu.Params(**prm), 1)
+        assert e.value.status == gpu.EINVAL
+
+
 def _paper_lockstep(gpu, oracle_mod, pop, batch, seed=13, gen0=5, sample=None):
     """One generation of the paper's net from a common state: raw 28x28 levels
     pooled on the GPU, selection bit-exact, children and fitness within

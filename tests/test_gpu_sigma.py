@@ -140,6 +140,13 @@ def test_decay_lockstep_full_size_sampled(gpu, oracle_mod):
     _lockstep(gpu, oracle_mod, **FULL, prm=prm, sample=SAMPLE, gen0=123)
 
 
+def test_self_adaptive_paper_network(gpu, oracle_mod):
+    # The paper's 196-256-128-64-10 (tensor-core evaluation of three hidden
+    # layers) with sigma genes and its Section 4.5 operators.
+    prm = dict(p_c=0.75, sigma=0.001, alpha=1.0, init=1, sigma_ctl=gpu.SIGMA_SELF, tau=0.3)
+    _lockstep(gpu, oracle_mod, dims=[196, 256, 128, 64, 10], pop=40, batch=64, prm=prm)
+
+
 @pytest.mark.parametrize("ctl", ["self", "decay"])
 def test_sigma_control_fused_breed_evaluate(gpu, oracle_mod, ctl):
     # The fused breed + evaluate kernel reads each child's own strength too.
