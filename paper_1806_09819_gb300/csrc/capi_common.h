@@ -32,10 +32,13 @@ leea_status check_device_status(cudaStream_t stream, uint32_t* flags_out);
 int64_t shadow_stride_of(const NetLayout& net, int32_t precision);
 leea_status check_shadow_shape(const NetLayout& net, int32_t precision);
 
-// The evaluation kernel `path` selects (LEEA_EVAL_*) for 8-bit inputs x = k / x_div.
+// The evaluation kernel `path` selects (LEEA_EVAL_*) for 8-bit inputs x = k / x_div;
+// mlp_scratch: the caller's scratch of the tensor-core evaluation of deeper nets
+// (eval_mlp_tc_scratch_bytes), or NULL for the library's shared buffer.
 leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
                              const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
-                             float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream);
+                             float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream,
+                             void* mlp_scratch = nullptr);
 // The precision form's evaluation on W1 shadows (scratch: batch > 128).
 leea_status dispatch_eval_shadow(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
                                  const uint8_t* shadow, const int32_t* scale_exp, const uint8_t* x, float x_div,

@@ -226,7 +226,7 @@ leea_status dispatch_eval(const NetLayout& net, int32_t pop, const float* pop_de
 // The same for 8-bit inputs x = k / x_div.
 leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
                              const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
-                             float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream)
+                             float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream, void* mlp_scratch)
 {
     if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
     if (net.n_layers > 2) {  // several hidden layers
@@ -239,7 +239,7 @@ leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop
             unsigned int* status = device_status_ptr();
             if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
             LEEA_CUDA_TRY(launch_eval_mlp_tc(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
-                                             status, stream),
+                                             status, stream, mlp_scratch),
                           "evaluate kernel");
         } else {
             LEEA_CUDA_TRY(launch_eval_mlp_u8(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj,
@@ -734,6 +734,8 @@ struct leea_state {
     size_t scratch_bytes;
     // self-adaptive mutation strength (prm.sigma_ctl == LEEA_SIGMA_SELF)
     float* sigma[2];     // sigma genes, paired with popbuf[0] / popbuf[1]
+    // tensor-core evaluation of deeper nets: weight pieces and marks
+    void* mlp_scratch;
 };
 
 namespace {
@@ -761,6 +763,7 @@ void free_state(leea_state* s)
     cudaFree(s->scratch);
     cudaFree(s->sigma[0]);
     cudaFree(s->sigma[1]);
+    cudaFree(s->mlp_scratch);
     if (s->prof) {
         if (s->prof->created)
             for (int st = 0; st < LEEA_NUM_STAGES; ++st)
@@ -889,6 +892,9 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         for (int b = 0; b < 2 && err == cudaSuccess; ++b)  // zero padding of the tiled layout
             err = cudaMemsetAsync(s->shadow[b], 0, np * s->sh_stride, s->stream);
     }
+    if (s->net.n_layers > 2 && err == cudaSuccess && eval_mlp_tc_supported(s->net, s->popbuf[0]) &&
+        p->eval_path != LEEA_EVAL_SIMT)
+        err = cudaMalloc(&s->mlp_scratch, eval_mlp_tc_scratch_bytes(s->net, pop));
     if (p->sigma_ctl == LEEA_SIGMA_SELF) {
         for (int b = 0; b < 2 && err == cudaSuccess; ++b) err = cudaMalloc(&s->sigma[b], sizeof(float) * np);
         if (err == cudaSuccess) {  // every individual starts with the sigma gene p->sigma
@@ -1022,7 +1028,7 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         else if (u8)
             st = dispatch_eval_u8(s->net, s->pop, s->popbuf[s->cur], static_cast<const uint8_t*>(x_dev), x_div, y_dev,
                                   batch, s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,
-                                  s->prm.eval_path, s->stream);
+                                  s->prm.eval_path, s->stream, s->mlp_scratch);
         else
             st = dispatch_eval(s->net, s->pop, s->popbuf[s->cur], static_cast<const float*>(x_dev), y_dev, batch,
                                s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,

@@ -559,25 +559,9 @@ __global__ void __launch_bounds__(256) split_weights_kernel(const MlpTcArgs a)
     }
 }
 
-// Library-owned flag array for the recomputation, grown on demand.
-int32_t* flag_buffer(int32_t pop)
-{
-    static std::mutex mu;
-    static int32_t* buf = nullptr;
-    static int32_t cap = 0;
-    std::lock_guard<std::mutex> lock(mu);
-    if (pop > cap) {
-        if (buf) cudaFree(buf);
-        buf = nullptr;
-        cap = 0;
-        if (cudaMalloc(&buf, sizeof(int32_t) * static_cast<size_t>(pop)) != cudaSuccess) return nullptr;
-        cap = pop;
-    }
-    return buf;
-}
-
-// Library-owned buffer of the weight pieces, grown on demand.
-uint8_t* piece_buffer(size_t bytes)
+// Library-owned scratch (weight pieces, marks), grown on demand, for callers
+// that bring none.
+uint8_t* shared_scratch(size_t bytes)
 {
     static std::mutex mu;
     static uint8_t* buf = nullptr;
@@ -593,7 +577,26 @@ uint8_t* piece_buffer(size_t bytes)
     return buf;
 }
 
+// Bytes of one individual's weight pieces; byte offset of each layer's blocks.
+int64_t piece_layout(const NetLayout& net, int64_t* layer_off)
+{
+    int64_t off = 0;
+    for (int l = 0; l < 3; ++l) {
+        layer_off[l] = off;
+        const int64_t k16 = (net.dims[l] + 15) / 16 * 16;
+        off += (k16 + 63) / 64 * net.dims[l + 1] * 256;
+    }
+    return off;
+}
+
 }  // namespace
+
+size_t eval_mlp_tc_scratch_bytes(const NetLayout& net, int32_t pop)
+{
+    int64_t layer_off[3];
+    const size_t pieces = static_cast<size_t>(piece_layout(net, layer_off)) * static_cast<size_t>(pop);
+    return pieces + sizeof(int32_t) * static_cast<size_t>(pop);
+}
 
 bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev)
 {
@@ -611,7 +614,8 @@ bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev)
 
 cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
                                const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
-                               float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream)
+                               float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream,
+                               void* scratch)
 {
     MlpTcArgs a{};
     a.pop = pop;
@@ -634,16 +638,12 @@ cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* p
     a.f_adj = f_adj;
     a.correct = correct;
     a.status = status;
-    a.flagged = flag_buffer(pop);
-    if (!a.flagged) return cudaErrorMemoryAllocation;
-    int64_t off = 0;
-    for (int l = 0; l < 3; ++l) {
-        a.layer_off[l] = off;
-        off += static_cast<int64_t>((a.k16[l] + 63) / 64) * net.dims[l + 1] * 256;
-    }
-    a.piece_stride = off;
-    a.pieces = piece_buffer(static_cast<size_t>(off) * static_cast<size_t>(pop));
-    if (!a.pieces) return cudaErrorMemoryAllocation;
+    a.piece_stride = piece_layout(net, a.layer_off);
+    const size_t pieces = static_cast<size_t>(a.piece_stride) * static_cast<size_t>(pop);
+    uint8_t* base = scratch ? static_cast<uint8_t*>(scratch) : shared_scratch(eval_mlp_tc_scratch_bytes(net, pop));
+    if (!base) return cudaErrorMemoryAllocation;
+    a.pieces = base;
+    a.flagged = reinterpret_cast<int32_t*>(base + pieces);  // pieces: a multiple of 256 bytes
     cudaError_t err = cudaMemsetAsync(a.flagged, 0, sizeof(int32_t) * static_cast<size_t>(pop), stream);
     if (err != cudaSuccess) return err;
     {

@@ -246,9 +246,15 @@ cudaError_t launch_eval_mlp_u8_only(const NetLayout& net, int32_t pop, const flo
 // operand pieces), individuals with a weight or activation |v| >= 128
 // recomputed in FP32 on the CUDA cores.
 bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev);
+// Scratch of one evaluation: the weights as FP16 pieces and the marks.
+size_t eval_mlp_tc_scratch_bytes(const NetLayout& net, int32_t pop);
+// scratch: eval_mlp_tc_scratch_bytes(net, pop) bytes of device memory owned by
+// the caller, or NULL for a library-owned buffer shared by every such call
+// (which must then not overlap on the device).
 cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
                                const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
-                               float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream);
+                               float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream,
+                               void* scratch = nullptr);
 cudaError_t launch_maxpool2x2(int32_t batch, int32_t h, int32_t w, const float* x, float* out, cudaStream_t stream);
 cudaError_t launch_maxpool2x2_u8(int32_t batch, int32_t h, int32_t w, const uint8_t* x, uint8_t* out,
                                  cudaStream_t stream);
