@@ -109,6 +109,16 @@ def test_lockstep_full_size_sampled(gpu, oracle_mod, path):
     _lockstep(gpu, oracle_mod, CONFIG_FULL["dims"], CONFIG_FULL["pop"], CONFIG_FULL["batch"], prm, sample=sample)
 
 
+@pytest.mark.parametrize("pop,batch,path,u8", [(1, 1, 2, True), (2, 3, 3, True), (1, 2, 1, False), (2, 1, 2, False),
+                                               (3, 128, 3, True)])
+def test_lockstep_degenerate_sizes(gpu, oracle_mod, pop, batch, path, u8):
+    # A population of one or two (the lone individual is elite, crossover
+    # partner or mutation parent of itself) and batches of one sample; the
+    # largest batch the 8-bit tensor-core and fused paths take.
+    prm = dict(sigma=0.05, n_elite=-1, eval_path=path)
+    _lockstep(gpu, oracle_mod, [784, 32, 10], pop, batch, prm, u8=u8)
+
+
 def test_first_generation_evaluates_the_initial_population(gpu, oracle_mod):
     dims, pop, batch = [784, 32, 10], 8, 16
     prm = dict(init=1)
