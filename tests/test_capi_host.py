@@ -132,3 +132,19 @@ def test_autotune_candidates():
     assert autotune.effective_chunk(48, 112) == 48
     c = autotune.candidates(1, 784, 256)
     assert c[0] == 96 and all(16 <= x <= 112 and x % 16 == 0 for x in c) and len(set(c)) == len(c)
+
+
+def test_header_is_plain_c(tmp_path):
+    # The boundary is a C ABI: the header compiles as strict C99 and as C++.
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text('#include "leea.h"\nint main(void) { leea_params p; leea_status s = leea_default_params(&p);\n'
+                   '  return (int)s + (int)p.sigma_ctl; }\n')
+    inc = os.path.dirname(HEADER)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc, "-c", str(src), "-o",
+                    str(tmp_path / "c.o")], check=True)
+    subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-I", inc, "-x", "c++", "-c", str(src), "-o",
+                    str(tmp_path / "cc.o")], check=True)
