@@ -185,7 +185,7 @@ leea_status leea_counts(int32_t pop, const leea_params* p, int32_t* n_elite,
 /* Step entry points on caller-owned device buffers (stream-ordered)        */
 /* ---------------------------------------------------------------------- */
 
-/* Random initial population (Algorithm 1, first line; Section 4.1).
+/* Random initial population (Algorithm 1's initial population; Section 4.1).
  * init 0: W ~ N(0, 1/d_l) by Box-Muller on the INIT stream; init 1:
  * Glorot-uniform W ~ U(-a, a), a = sqrt(6 / (d_l + d_{l+1})).  Biases and the
  * padding are zero.  pop_dev: float[pop][c_pad], written. */

@@ -1,4 +1,4 @@
-// leea_rng.cu -- population initialisation (Algorithm 1, first line; Section
+// leea_rng.cu -- population initialisation (Algorithm 1's initial population; Section
 // 4.1) and the diagnostic stream dumps.
 #include "leea_internal.h"
 #include "philox.cuh"
