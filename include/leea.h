@@ -378,6 +378,14 @@ leea_status leea_evaluate_shadow_u8_noalloc(int32_t pop, const int32_t* dims, in
  * (leea_fitness, leea_best_params, ...) perform the same check. */
 leea_status leea_device_status(void* stream, uint32_t* flags_out);
 
+/* Diagnostic of the failure path: enqueues a one-warp kernel whose thread
+ * waits on a barrier that nothing completes, with the bounded wait the
+ * pipelines use, limited to limit_us microseconds (1 .. 10^6).  When the wait
+ * gives up it sets a status bit, so the next leea_device_status on that
+ * stream returns LEEA_ETIMEOUT (flag 8) and clears it; the context stays
+ * usable.  No fault is involved. */
+leea_status leea_selftest_wait_timeout(uint32_t limit_us, void* stream);
+
 /* Diagnostic: words n0 .. n0+count-1 of the Philox stream (tag, gen, ent),
  * written to out_dev (uint32[count]).  Lets a caller check the generator. */
 leea_status leea_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,

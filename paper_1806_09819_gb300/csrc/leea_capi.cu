@@ -193,6 +193,8 @@ leea_status check_device_status(cudaStream_t stream, uint32_t* flags_out)
         return fail(LEEA_ETIMEOUT, "a breed kernel wait timed out; the children are invalid");
     if (v & kStatusProbeTimeout)
         return fail(LEEA_ETIMEOUT, "a tensor-core probe wait timed out; the descriptors are invalid");
+    if (v & kStatusSelftestTimeout)
+        return fail(LEEA_ETIMEOUT, "the self-test's bounded wait gave up (as it is meant to)");
     return LEEA_OK;
 }
 
@@ -666,6 +668,17 @@ leea_status leea_evaluate_shadow_u8_noalloc(int32_t pop, const int32_t* dims, in
 leea_status leea_device_status(void* stream, uint32_t* flags_out)
 {
     return check_device_status(static_cast<cudaStream_t>(stream), flags_out);
+}
+
+leea_status leea_selftest_wait_timeout(uint32_t limit_us, void* stream)
+{
+    if (limit_us < 1 || limit_us > 1000000) return fail(LEEA_EINVAL, "limit_us must be in [1, 1000000]");
+    unsigned int* status = device_status_ptr();
+    if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+    LEEA_CUDA_TRY(launch_wait_timeout_probe(static_cast<uint64_t>(limit_us) * 1000u, status,
+                                            static_cast<cudaStream_t>(stream)),
+                  "self-test kernel");
+    return LEEA_OK;
 }
 
 leea_status leea_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent, uint32_t n0,

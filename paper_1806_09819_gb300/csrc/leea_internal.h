@@ -33,6 +33,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 constexpr unsigned int kStatusEvalTimeout = 1u;   // a bounded mbarrier wait of the tensor-core eval gave up
 constexpr unsigned int kStatusBreedTimeout = 2u;  // a bounded mbarrier wait of the breed kernel gave up
 constexpr unsigned int kStatusProbeTimeout = 4u;  // a bounded mbarrier wait of the tensor-core probe gave up
+constexpr unsigned int kStatusSelftestTimeout = 8u;  // the self-test's wait gave up, as it is meant to
 
 // Per-layer offsets of a net, computed on the host (logical gene order of
 // Section 3.2: W_l rows out x in, then b_l).
@@ -319,6 +320,11 @@ cudaError_t launch_surrogate_adam(int64_t n_params, float* theta, const float* g
 cudaError_t launch_surrogate_train_step(int32_t n, int32_t d_in, int32_t h1, int32_t h2, float* theta, const float* x,
                                         const float* t, float* loss, float* work, float* m, float* v, int64_t step,
                                         float lr, float beta1, float beta2, float eps, cudaStream_t stream);
+
+// The failure path of the bounded waits, exercised without a fault: one
+// thread waits on an mbarrier that nothing completes, gives up after limit_ns
+// and sets kStatusSelftestTimeout.
+cudaError_t launch_wait_timeout_probe(uint64_t limit_ns, unsigned int* status, cudaStream_t stream);
 
 cudaError_t launch_philox_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32_t ent,
                                uint32_t n0, int64_t count, uint32_t* out, cudaStream_t stream);

@@ -2,6 +2,7 @@
 // 4.1) and the diagnostic stream dumps.
 #include "leea_internal.h"
 #include "philox.cuh"
+#include "tc_ptx.cuh"
 
 namespace leea {
 
@@ -95,6 +96,29 @@ cudaError_t launch_normal_fill(uint64_t seed, uint32_t tag, uint32_t gen, uint32
     const int64_t blocks = (count + 255) / 256;
     normal_fill_kernel<<<static_cast<unsigned>(blocks < 4096 ? blocks : 4096), 256, 0, stream>>>(
         seed, tag, gen, ent, n0, count, out);
+    return cudaGetLastError();
+}
+
+// A bounded wait on an mbarrier that nothing completes (phase 0 of a fresh
+// barrier with one expected arrival): the same wait the pipelines use, run
+// to its limit, then the status bit the host reads.
+__global__ void wait_timeout_probe_kernel(uint64_t limit_ns, unsigned int* status)
+{
+    __shared__ uint64_t bar;
+    __shared__ int never;
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(&bar, 1);
+        never = 0;
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !ptx::mbar_wait_bounded(&bar, 0u, &never, limit_ns))
+        atomicOr(status, kStatusSelftestTimeout);
+}
+
+cudaError_t launch_wait_timeout_probe(uint64_t limit_ns, unsigned int* status, cudaStream_t stream)
+{
+    wait_timeout_probe_kernel<<<1, 32, 0, stream>>>(limit_ns, status);
     return cudaGetLastError();
 }
 

@@ -114,6 +114,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                    vp, vp, vp, vp, vp],
         "leea_evaluate": [i32, vp, i32, vp, vp, vp, i32, f32, vp, vp, vp, vp, i32, vp],
         "leea_device_status": [vp, P(u32)],
+        "leea_selftest_wait_timeout": [u32, vp],
         "leea_shadow_stride": ([vp, i32, i32], i64),
         "leea_make_shadow": [i32, vp, i32, i32, vp, vp, vp, vp, vp],
         "leea_shadow_scratch_bytes": ([i32, i32], i64),
@@ -213,7 +214,7 @@ def exported_symbols() -> list[str]:
             "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_breed_evaluate_u8",
             "leea_maxpool2x2", "leea_maxpool2x2_u8",
             "leea_evaluate",
-            "leea_device_status", "leea_evaluate_u8", "leea_generation_u8", "leea_generation_u8_host",
+            "leea_device_status", "leea_selftest_wait_timeout", "leea_evaluate_u8", "leea_generation_u8", "leea_generation_u8_host",
             "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
             "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
             "leea_get_population", "leea_set_population", "leea_set_fitness", "leea_set_generation",
@@ -401,6 +402,11 @@ def leea_device_status(stream=None) -> int:
     flags = ctypes.c_uint32()
     _check(load_library().leea_device_status(_stream(stream), ctypes.byref(flags)))
     return flags.value
+
+
+def leea_selftest_wait_timeout(limit_us: int, stream=None) -> None:
+    """Enqueues a bounded wait that runs out after limit_us (the failure path, no fault)."""
+    _check(load_library().leea_selftest_wait_timeout(int(limit_us), _stream(stream)))
 
 
 def leea_philox_fill(seed: int, tag: int, gen: int, ent: int, n0: int, count: int, out_dev, stream=None) -> None:

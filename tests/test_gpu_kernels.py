@@ -413,3 +413,29 @@ def test_u8_and_float_inputs_agree(gpu):
                          f_u8, eval_path=2)
     assert gpu.leea_device_status() == 0
     assert_fitness_close(f_u8.cpu().numpy(), f_float.cpu().numpy().astype(np.float64), "u8 vs float")
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(gpu):
+    # The failure path of every pipeline wait, without a fault: a wait that
+    # nothing completes runs to its limit, the kernel reports it through the
+    # status word, the host reads LEEA_ETIMEOUT, and the context keeps working.
+    import time
+    torch = _torch()
+    gpu.leea_device_status()  # start from a clear status word
+    t0 = time.perf_counter()
+    gpu.leea_selftest_wait_timeout(20000)  # 20 ms
+    with pytest.raises(gpu.LeeaError) as e:
+        gpu.leea_device_status()
+    assert e.value.status == gpu.ETIMEOUT
+    assert time.perf_counter() - t0 >= 0.02
+    assert gpu.leea_device_status() == 0  # read and cleared
+    dims, pop = [784, 32, 10], 3
+    pd = torch.zeros((pop, gpu.leea_padded_params(dims)), dtype=torch.float32, device="cuda")
+    x = torch.zeros((16, 784), dtype=torch.uint8, device="cuda")
+    y = torch.arange(16, dtype=torch.int32, device="cuda") % 10
+    f = torch.empty(pop, dtype=torch.float32, device="cuda")
+    gpu.leea_evaluate_u8(pop, dims, pd, x, 255.0, y, 16, 1.0, None, f)
+    np.testing.assert_allclose(f.cpu().numpy(), -np.log(10.0), rtol=1e-6)  # zero nets
+    assert gpu.leea_device_status() == 0
+    with pytest.raises(gpu.LeeaError):
+        gpu.leea_selftest_wait_timeout(0)
