@@ -273,8 +273,8 @@ leea_status leea_breed_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_d
  * input and hidden width <= 256 and d_out <= 32 (the paper's 196-256-128-64-10,
  * Section 4.1), layer by layer with ReLU between layers.  Deeper nets take
  * the CUDA cores in exact FP32 (SIMT; AUTO for float inputs), or, for 8-bit
- * inputs and three hidden layers (widths multiples of 16 in [16, 256] summing
- * to <= 512, d_0 % 4 == 0, d_0 <= 256, d_out <= 16, 4-byte aligned x), the
+ * inputs and three hidden layers (widths multiples of 16 in [16, 256],
+ * d_0 % 4 == 0, d_0 <= 256, d_out <= 16, 4-byte aligned x), the
  * tensor cores (AUTO or TENSOR): FP16 operand pieces of 2^8 w and 2^8 h
  * (hi.hi + hi.lo + lo.hi; the levels are exact), FP32 accumulation, FP32
  * bias, ReLU, last layer and loss; an individual with a weight or activation

@@ -235,7 +235,7 @@ leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop
         const bool tc = eval_mlp_tc_supported(net, pop_dev) && (reinterpret_cast<uintptr_t>(x) & 3u) == 0;
         if (path == LEEA_EVAL_TENSOR && !tc)
             return fail(LEEA_EINVAL, "tensor-core evaluation of deeper nets needs three hidden layers, widths multiples "
-                                     "of 16 in [16, 256] summing to <= 512, d_0 %% 4 == 0, d_0 <= 256, d_out <= 16 "
+                                     "of 16 in [16, 256], d_0 %% 4 == 0, d_0 <= 256, d_out <= 16 "
                                      "and 4-byte aligned inputs");
         if (tc && path != LEEA_EVAL_SIMT) {
             unsigned int* status = device_status_ptr();
@@ -747,8 +747,9 @@ struct leea_state {
     size_t scratch_bytes;
     // self-adaptive mutation strength (prm.sigma_ctl == LEEA_SIGMA_SELF)
     float* sigma[2];     // sigma genes, paired with popbuf[0] / popbuf[1]
-    // tensor-core evaluation of deeper nets: weight pieces and marks
+    // tensor-core evaluation of deeper nets: weight pieces, marks, level tiles
     void* mlp_scratch;
+    size_t mlp_scratch_bytes;
 };
 
 namespace {
@@ -906,8 +907,10 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
             err = cudaMemsetAsync(s->shadow[b], 0, np * s->sh_stride, s->stream);
     }
     if (s->net.n_layers > 2 && err == cudaSuccess && eval_mlp_tc_supported(s->net, s->popbuf[0]) &&
-        p->eval_path != LEEA_EVAL_SIMT)
-        err = cudaMalloc(&s->mlp_scratch, eval_mlp_tc_scratch_bytes(s->net, pop));
+        p->eval_path != LEEA_EVAL_SIMT) {
+        s->mlp_scratch_bytes = eval_mlp_tc_scratch_bytes(s->net, pop, 0);  // grown with the batch
+        err = cudaMalloc(&s->mlp_scratch, s->mlp_scratch_bytes);
+    }
     if (p->sigma_ctl == LEEA_SIGMA_SELF) {
         for (int b = 0; b < 2 && err == cudaSuccess; ++b) err = cudaMalloc(&s->sigma[b], sizeof(float) * np);
         if (err == cudaSuccess) {  // every individual starts with the sigma gene p->sigma
@@ -953,6 +956,17 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
             s->scratch_bytes = 0;
             LEEA_CUDA_TRY(cudaMalloc(&s->scratch, need), "scratch allocation");
             s->scratch_bytes = need;
+        }
+    }
+    if (u8 && s->mlp_scratch) {
+        const size_t need = eval_mlp_tc_scratch_bytes(s->net, s->pop, batch);
+        if (need > s->mlp_scratch_bytes) {
+            LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "scratch sync");
+            cudaFree(s->mlp_scratch);
+            s->mlp_scratch = nullptr;
+            s->mlp_scratch_bytes = 0;
+            LEEA_CUDA_TRY(cudaMalloc(&s->mlp_scratch, need), "scratch allocation");
+            s->mlp_scratch_bytes = need;
         }
     }
     const bool first = !s->evaluated;

@@ -3,36 +3,45 @@
 // with FP32-class accuracy, for minibatches of 8-bit levels x = k / x_div.
 //
 // A unit is one individual on one 128-sample tile.  Layers 1-3 are MMAs with
-// the samples as M = 128 and FP32 accumulation in tensor memory (columns
-// [0, d1), [d1, d1 + d2), [d1 + d2, d1 + d2 + d3)):
+// the samples as M = 128 and FP32 accumulation in tensor memory (layer 1 in
+// columns [0, d1), layers 2 and 3 both from column d1: layer 3 starts after
+// the epilogue has read layer 2):
 //   layer 1     A = the tile's levels k, exact in FP16; B = 2^8 W1 as two FP16
 //               pieces hi = fp16(2^8 w), lo = fp16(2^8 w - hi) (the remainder is
 //               exact in FP32): 2 MMAs per 16 inputs, only the accumulation rounds
 //   layers 2, 3 A = 2^8 h of the layer below and B = 2^8 W, both as two FP16
-//               pieces: hi.hi + hi.lo + lo.hi, 3 MMAs per 16 inputs; the dropped
-//               lo.lo term is below 2^-21 of the product
+//               pieces: hi.hi + hi.lo + lo.hi; the dropped lo.lo term is below
+//               2^-21 of the product.  For widths N <= 128 the two products of
+//               the hi activations are one MMA of width 2N against the stacked
+//               [W_hi; W_lo] block (its rows are contiguous), lo.hi adds onto
+//               the second half, and the epilogue sums the halves: 2 MMAs per
+//               16 inputs (an MMA costs about the same up to N = 256), else 3
 // The epilogue adds the bias and applies ReLU in FP32, splits the activations
 // for the next layer, and computes layer 4 (d3 -> d_out), the softmax
 // cross-entropy and the loss sums in FP32, tiles in order.  A weight or an
 // activation with |v| >= 128 (2^8 |v| could overflow its FP16 piece) marks the
 // individual; the CUDA-core kernel then recomputes its fitness in FP32.
-// The weights are split once per evaluation (split_weights_kernel), not once
-// per tile.
+// The weights are split once per evaluation (split_weights_kernel), and the
+// batch's levels are converted once per evaluation into FP16 operand tiles
+// (stage_levels_kernel), so a unit's layer-1 operands arrive by bulk copies and
+// its layer-1 MMAs run while the epilogue finishes the previous unit.
 //
 // Warp roles (persistent CTA, one per SM; individuals strided by gridDim.x,
 // their tiles in order):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
-//   warp 1      producer: one bulk copy per 64-input block of W1, W2, W3,
-//               already split into FP16 pieces and swizzled by
+//   warp 1      producer: per unit, the tile's levels (one bulk copy into the
+//               activation region), then one bulk copy per 64-input block of
+//               W1, W2, W3, already split into FP16 pieces and swizzled by
 //               split_weights_kernel, into one of two weight buffers
 //   warps 2-9   the epilogue (TMEM lane = sample, two warps per lane
 //               quarter, each with half of a layer's 16-column groups): the
-//               tile's levels as the layer-1 operand, the activations of
-//               layers 1 and 2 as the next operands, layer 4 (the halves'
-//               partial logits added through shared memory) and the loss
+//               activations of layers 1 and 2 as the next operands, layer 4
+//               (the halves' partial logits added through shared memory) and
+//               the loss
 // The layers of a unit run in sequence (one activation region), each
-// layer's weight blocks double-buffered.  Every wait is bounded; on expiry
-// the kernel sets kStatusEvalTimeout and exits.
+// layer's weight blocks double-buffered; the next unit's levels and layer-1
+// MMAs start as soon as this unit's layer-3 MMAs are done.  Every wait is
+// bounded; on expiry the kernel sets kStatusEvalTimeout and exits.
 #include <cuda.h>
 
 #include <cuda_fp16.h>
@@ -78,6 +87,10 @@ struct MlpTcArgs {
     float* f_adj;
     int32_t* correct;
     int32_t* flagged;    // [pop], zeroed before the launch: 1 = recompute in FP32
+    // the batch's levels as FP16 layer-1 operand tiles: tile t (128 samples)
+    // at byte t * x_bytes, its 64-input blocks of 128 swizzled 128-byte rows
+    const uint8_t* xtiles;
+    uint32_t x_bytes;
     unsigned int* status;
     // the weights of layers 1-3 as FP16 pieces, per individual (piece_stride
     // bytes): layer l's 64-input blocks from byte layer_off[l], each block the
@@ -92,7 +105,7 @@ struct TcSmem {
     uint8_t* slot;    // weights: hi piece then lo piece, N x 128 bytes each per 64-input block
     float *b1, *b2, *b3, *w4t, *b4;
     float* plog;  // [128][16]: the second half's partial layer-4 logits
-    uint64_t *buf_full, *buf_empty, *x_ready, *d_full, *h_ready, *drain;
+    uint64_t *buf_full, *buf_empty, *x_full, *d_full, *h_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
@@ -127,7 +140,7 @@ __device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.buf_full = bars;       // [2]
     s.buf_empty = bars + 2;  // [2]
-    s.x_ready = bars + 4;
+    s.x_full = bars + 4;
     s.d_full = bars + 5;     // [3]
     s.h_ready = bars + 8;    // [2]
     s.drain = bars + 10;
@@ -187,20 +200,51 @@ __device__ __forceinline__ uint32_t buffer_offset(int l, int b)
     return l == 0 ? kHalfRegion : kRegionBytes + kSlotBytes / 2;
 }
 
+// 16 accumulator columns of this thread's lane from TMEM address taddr; for a
+// merged layer the sum of the two halves (hi.hi + (hi.lo + lo.hi)).
+__device__ __forceinline__ void load_acc16(uint32_t taddr, uint32_t half_cols, bool merged, float (&v)[16])
+{
+    uint32_t r[16];
+    ptx::tmem_ld16_nowait(taddr, r);
+    if (merged) {
+        uint32_t r2[16];
+        ptx::tmem_ld16_nowait(taddr + half_cols, r2);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]) + __uint_as_float(r2[i]);
+    } else {
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    }
+}
+
+// Layers 2 and 3 (width n, layer 1 of width d1 in the columns below them) take
+// the hi activations' two products as one MMA of width 2n where 2n fits both
+// the MMA (N <= 256) and tensor memory.
+__host__ __device__ inline bool merged_layer(int32_t d1, int32_t n)
+{
+    return 2 * n <= 256 && d1 + 2 * n <= static_cast<int32_t>(kTmemCols);
+}
+
 __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcArgs a)
 {
     extern __shared__ uint8_t smem_raw[];
     const TcSmem s = carve(smem_raw, a);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int d1 = a.dims[1], d2 = a.dims[2], d3 = a.dims[3], d_out = a.dims[4];
-    const uint32_t col[3] = { 0u, static_cast<uint32_t>(d1), static_cast<uint32_t>(d1 + d2) };
+    // Layer 3 reuses layer 2's columns; a merged layer (2N columns: hi.hi, then
+    // hi.lo + lo.hi) where its width allows.
+    const bool merged2 = merged_layer(d1, d2), merged3 = merged_layer(d1, d3);
+    auto col = [&](int l) { return l == 0 ? 0u : static_cast<uint32_t>(d1); };
+    auto merged = [&](int l) { return l == 1 ? merged2 : (l == 2 && merged3); };
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
             ptx::mbar_init(&s.buf_full[i], 1);
             ptx::mbar_init(&s.buf_empty[i], 1);
         }
-        ptx::mbar_init(s.x_ready, kEpiThreads);
+        ptx::mbar_init(s.x_full, 1);
         for (int i = 0; i < 3; ++i) ptx::mbar_init(&s.d_full[i], 1);
         for (int i = 0; i < 2; ++i) ptx::mbar_init(&s.h_ready[i], kEpiThreads);
         ptx::mbar_init(s.drain, 1);
@@ -222,7 +266,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
             bool ok = true;
             for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
                 for (int t = 0; ok && t < a.n_tiles; ++t, ++unit) {
-                    if (!ptx::mbar_wait_bounded(s.x_ready, unit & 1u, s.abort_flag, kWaitLimitNs)) {
+                    if (!ptx::mbar_wait_bounded(s.x_full, unit & 1u, s.abort_flag, kWaitLimitNs)) {
                         raise_abort(s, a);
                         ok = false;
                         break;
@@ -237,7 +281,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                         ptx::tc_fence_after();
                         const uint32_t n = static_cast<uint32_t>(a.dims[l + 1]);
                         const uint32_t idesc = ptx::idesc_f16(kTile, n);
-                        const uint32_t d_tmem = tmem_base + col[l];
+                        const uint32_t idesc2 = ptx::idesc_f16(kTile, 2u * n);
+                        const uint32_t d_tmem = tmem_base + col(l);
                         const int blocks = layer_blocks(a, l);
                         for (int kb = 0; kb < blocks; ++kb) {
                             const int b = buffer_of(a, l, kb);
@@ -258,6 +303,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                                 const uint32_t b_hi = slot + kk * 32u;
                                 const uint32_t b_lo = slot + n * 128u + kk * 32u;
                                 const uint32_t first = (kb | kk) == 0 ? 0u : 1u;
+                                if (merged(l)) {
+                                    // [hi.hi | hi.lo] against the stacked block, then lo.hi onto the second half
+                                    ptx::mma_f16(d_tmem, ptx::smem_desc_sw128(a_hi), ptx::smem_desc_sw128(b_hi),
+                                                 idesc2, first);
+                                    ptx::mma_f16(d_tmem + n, ptx::smem_desc_sw128(a_hi + kHalfRegion),
+                                                 ptx::smem_desc_sw128(b_hi), idesc, 1u);
+                                    continue;
+                                }
                                 ptx::mma_f16(d_tmem, ptx::smem_desc_sw128(a_hi), ptx::smem_desc_sw128(b_hi), idesc,
                                              first);
                                 ptx::mma_f16(d_tmem, ptx::smem_desc_sw128(a_hi), ptx::smem_desc_sw128(b_lo), idesc,
@@ -283,18 +336,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
         if (lane == 0) {
             uint32_t bphase = 0, unit = 0;
             uint32_t issued = 0, parity = 0;  // per buffer: a copy was issued / the parity it completes
+            uint32_t x_issued = 0;            // level copies issued (at most the last one in flight)
             bool ok = true;
             for (int p = blockIdx.x; ok && p < a.pop; p += gridDim.x) {
                 const uint8_t* src_p = a.pieces + static_cast<int64_t>(p) * a.piece_stride;
                 for (int t = 0; ok && t < a.n_tiles; ++t, ++unit) {
-                    // The buffers of this unit's layer 1 (the slot, the region's lo
-                    // half) are free once the previous unit's last MMAs are done.
+                    // The activation region and the buffers of this unit's layer 1
+                    // (the slot, the region's lo half) are free once the previous
+                    // unit's last MMAs are done: the tile's levels into the hi half.
                     if (unit > 0 &&
                         !ptx::mbar_wait_bounded(&s.d_full[2], (unit - 1) & 1u, s.abort_flag, kWaitLimitNs)) {
                         raise_abort(s, a);
                         ok = false;
                         break;
                     }
+                    ptx::mbar_arrive_expect_tx(s.x_full, a.x_bytes);
+                    ptx::bulk_load(s.region, a.xtiles + static_cast<int64_t>(t) * a.x_bytes, a.x_bytes, s.x_full);
+                    ++x_issued;
                     for (int l = 0; ok && l < 3; ++l) {
                         const uint32_t bytes = static_cast<uint32_t>(a.dims[l + 1]) * 256u;
                         const int blocks = layer_blocks(a, l);
@@ -322,6 +380,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                 for (int b = 0; b < 2; ++b)
                     if (issued & (1u << b))
                         ptx::mbar_wait_bounded(&s.buf_full[b], (parity >> b) & 1u, &never, kDrainLimitNs);
+                if (x_issued) ptx::mbar_wait_bounded(s.x_full, (x_issued - 1) & 1u, &never, kDrainLimitNs);
             }
         }
     } else {
@@ -350,40 +409,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
             int32_t n_ok = 0;
             bool bad = false;
             for (int t = 0; t < a.n_tiles; ++t, ++unit) {
-                // (1) the tile's levels as FP16 into the hi part of the region
                 const int smp = t * kTile + row;
                 const bool live = smp < a.batch;
-                // 4 levels per 32-bit load (d0 % 4 == 0), 8 chunks of 8 levels
-                // per batch of loads; a level k < 1024 is (1024 + k) - 1024 in
-                // FP16, and 1024 + k has the bit pattern 0x6400 | k.
-                const uint32_t* xr = reinterpret_cast<const uint32_t*>(a.x + static_cast<int64_t>(live ? smp : 0) *
-                                                                                 a.dims[0]);
-                const __half2 k1024 = __floats2half2_rn(1024.0f, 1024.0f);
-                for (int k0 = 64 * half; k0 < a.k16[0]; k0 += 128) {  // the halves take alternate blocks
-                    uint32_t wd[16];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int k = k0 + 4 * e;
-                        wd[e] = (live && k < a.dims[0]) ? __ldg(xr + (k >> 2)) : 0u;
-                    }
-#pragma unroll
-                    for (int ch = 0; ch < 8; ++ch) {
-                        if (k0 + 8 * ch >= a.k16[0]) break;
-                        uint32_t h[4];
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const uint32_t biased =
-                                __byte_perm(wd[2 * ch + (e >> 1)], 0x64646464u, (e & 1) ? 0x4342u : 0x4140u);
-                            h[e] = half2_bits(__hsub2(*reinterpret_cast<const __half2*>(&biased), k1024));
-                        }
-                        *reinterpret_cast<uint4*>(s.region + (k0 >> 6) * kBlockBytes + swz(row, ch)) =
-                            make_uint4(h[0], h[1], h[2], h[3]);
-                    }
-                }
-                ptx::fence_proxy_async_smem();
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(s.x_ready);
-                // (2), (3) layers 1 and 2: bias, ReLU, split for the next layer
+                // layers 1 and 2: bias, ReLU, split for the next layer; layer 3: ReLU, layer 4, loss
                 for (int l = 0; l < 3; ++l) {
                     if (et == 0) {
                         const bool got = ptx::mbar_wait_bounded(&s.d_full[l], unit & 1u, s.abort_flag, kWaitLimitNs);
@@ -401,7 +429,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                     if (l < 2) {
                         for (int c = 16 * g0; c < 16 * g1; c += 16) {
                             float v[16];
-                            ptx::tmem_ld16(tmem_base + lane_addr + col[l] + static_cast<uint32_t>(c), v);
+                            load_acc16(tmem_base + lane_addr + col(l) + static_cast<uint32_t>(c),
+                                       static_cast<uint32_t>(N), merged(l), v);
                             uint32_t hi[8], lo[8];
 #pragma unroll
                             for (int e = 0; e < 8; ++e) {
@@ -429,7 +458,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                         for (int o = 0; o < kMaxOutTc; ++o) logit[o] = 0.0f;
                         for (int c = 16 * g0; c < 16 * g1; c += 16) {
                             float v[16];
-                            ptx::tmem_ld16(tmem_base + lane_addr + col[l] + static_cast<uint32_t>(c), v);
+                            load_acc16(tmem_base + lane_addr + col(l) + static_cast<uint32_t>(c),
+                                       static_cast<uint32_t>(N), merged(l), v);
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 const float h = fmaxf(fmaf(v[j], scale, bias[c + j]), 0.0f);
@@ -559,6 +589,33 @@ __global__ void __launch_bounds__(256) split_weights_kernel(const MlpTcArgs a)
     }
 }
 
+// The batch's levels as FP16 layer-1 operand tiles (exact: integers below 2048
+// are FP16 values).  Item = (tile t, 64-input block kb, row r, 16-byte chunk
+// ch): levels kb * 64 + 8 ch .. + 7 of sample t * 128 + r, swizzled like the
+// weight pieces; levels past d0 and samples past the batch are 0.
+__global__ void __launch_bounds__(256) stage_levels_kernel(const MlpTcArgs a, const uint8_t* __restrict__ x)
+{
+    const int blocks = layer_blocks(a, 0), d0 = a.dims[0];
+    const int items = a.n_tiles * blocks * kTile * 8;
+    uint8_t* out = const_cast<uint8_t*>(a.xtiles);
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < items; it += gridDim.x * blockDim.x) {
+        const int ch = it & 7, r = (it >> 3) % kTile, tb = (it >> 3) / kTile;
+        const int t = tb / blocks, kb = tb - t * blocks;
+        const int smp = t * kTile + r, k0 = kb * 64 + 8 * ch;
+        const uint8_t* xr = x + static_cast<int64_t>(smp) * d0;
+        uint32_t h[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int k = k0 + 2 * e;
+            const float v0 = (smp < a.batch && k < d0) ? static_cast<float>(xr[k]) : 0.0f;
+            const float v1 = (smp < a.batch && k + 1 < d0) ? static_cast<float>(xr[k + 1]) : 0.0f;
+            h[e] = half2_bits(__floats2half2_rn(v0, v1));
+        }
+        *reinterpret_cast<uint4*>(out + static_cast<int64_t>(t) * a.x_bytes + kb * kBlockBytes + swz(r, ch)) =
+            make_uint4(h[0], h[1], h[2], h[3]);
+    }
+}
+
 // Library-owned scratch (weight pieces, marks), grown on demand, for callers
 // that bring none.
 uint8_t* shared_scratch(size_t bytes)
@@ -589,13 +646,27 @@ int64_t piece_layout(const NetLayout& net, int64_t* layer_off)
     return off;
 }
 
+// Bytes of one tile's levels (64-input blocks of 128 rows of 128 bytes).
+uint32_t level_tile_bytes(const NetLayout& net)
+{
+    return static_cast<uint32_t>((net.dims[0] + 63) / 64) * kBlockBytes;
+}
+
+// Scratch layout: the pieces (a multiple of 256 bytes), the marks (rounded up
+// to 256 bytes), the level tiles.
+size_t marks_bytes(int32_t pop)
+{
+    return (sizeof(int32_t) * static_cast<size_t>(pop) + 255) / 256 * 256;
+}
+
 }  // namespace
 
-size_t eval_mlp_tc_scratch_bytes(const NetLayout& net, int32_t pop)
+size_t eval_mlp_tc_scratch_bytes(const NetLayout& net, int32_t pop, int32_t batch)
 {
     int64_t layer_off[3];
     const size_t pieces = static_cast<size_t>(piece_layout(net, layer_off)) * static_cast<size_t>(pop);
-    return pieces + sizeof(int32_t) * static_cast<size_t>(pop);
+    const size_t tiles = static_cast<size_t>((batch + kTile - 1) / kTile);
+    return pieces + marks_bytes(pop) + tiles * level_tile_bytes(net);
 }
 
 bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev)
@@ -605,7 +676,9 @@ bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev)
     if (d0 % 4 != 0 || d0 > 256 || d_out > kMaxOutTc) return false;
     for (int32_t n : { d1, d2, d3 })
         if (n % 16 != 0 || n < 16 || n > 256) return false;
-    if (d1 + d2 + d3 > static_cast<int32_t>(kTmemCols)) return false;
+    // layer 1 in [0, d1), layers 2 and 3 from column d1 (2n columns if merged)
+    for (int32_t n : { d2, d3 })
+        if (d1 + (merged_layer(d1, n) ? 2 * n : n) > static_cast<int32_t>(kTmemCols)) return false;
     for (int l = 0; l < 3; ++l)
         if (net.w_off[l] % 4 != 0) return false;
     if (reinterpret_cast<uintptr_t>(pop_dev) & 15u) return false;
@@ -640,16 +713,22 @@ cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* p
     a.status = status;
     a.piece_stride = piece_layout(net, a.layer_off);
     const size_t pieces = static_cast<size_t>(a.piece_stride) * static_cast<size_t>(pop);
-    uint8_t* base = scratch ? static_cast<uint8_t*>(scratch) : shared_scratch(eval_mlp_tc_scratch_bytes(net, pop));
+    uint8_t* base =
+        scratch ? static_cast<uint8_t*>(scratch) : shared_scratch(eval_mlp_tc_scratch_bytes(net, pop, batch));
     if (!base) return cudaErrorMemoryAllocation;
     a.pieces = base;
     a.flagged = reinterpret_cast<int32_t*>(base + pieces);  // pieces: a multiple of 256 bytes
+    a.x_bytes = level_tile_bytes(net);
+    a.xtiles = base + pieces + marks_bytes(pop);
     cudaError_t err = cudaMemsetAsync(a.flagged, 0, sizeof(int32_t) * static_cast<size_t>(pop), stream);
     if (err != cudaSuccess) return err;
     {
         int items = 0;
         for (int l = 0; l < 3; ++l) items += ((a.k16[l] + 63) / 64) * net.dims[l + 1] * 8;
         split_weights_kernel<<<dim3((items + 255) / 256, pop < 65535 ? pop : 65535), 256, 0, stream>>>(a);
+        if ((err = cudaGetLastError()) != cudaSuccess) return err;
+        const int level_items = a.n_tiles * ((a.dims[0] + 63) / 64) * kTile * 8;
+        stage_levels_kernel<<<(level_items + 255) / 256, 256, 0, stream>>>(a, x);
         if ((err = cudaGetLastError()) != cudaSuccess) return err;
     }
     const size_t smem = tc_smem_bytes(net.dims);

@@ -243,13 +243,14 @@ cudaError_t launch_eval_mlp_u8_only(const NetLayout& net, int32_t pop, const flo
                                     cudaStream_t stream);
 // Nets with three hidden layers (the paper's 196-256-128-64-10) on the tensor
 // cores for 8-bit inputs: d0 % 4 == 0, d0 <= 256, hidden widths multiples of 16
-// in [16, 256] summing to <= 512, d_out <= 16; FP32-class accuracy (FP16
+// in [16, 256], d_out <= 16; FP32-class accuracy (FP16
 // operand pieces), individuals with a weight or activation |v| >= 128
 // recomputed in FP32 on the CUDA cores.
 bool eval_mlp_tc_supported(const NetLayout& net, const float* pop_dev);
-// Scratch of one evaluation: the weights as FP16 pieces and the marks.
-size_t eval_mlp_tc_scratch_bytes(const NetLayout& net, int32_t pop);
-// scratch: eval_mlp_tc_scratch_bytes(net, pop) bytes of device memory owned by
+// Scratch of one evaluation: the weights as FP16 pieces, the marks and the
+// batch's levels as FP16 operand tiles.
+size_t eval_mlp_tc_scratch_bytes(const NetLayout& net, int32_t pop, int32_t batch);
+// scratch: eval_mlp_tc_scratch_bytes(net, pop, batch) bytes of device memory owned by
 // the caller, or NULL for a library-owned buffer shared by every such call
 // (which must then not overlap on the device).
 cudaError_t launch_eval_mlp_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
