@@ -38,10 +38,12 @@
 //               activations of layers 1 and 2 as the next operands, layer 4
 //               (the halves' partial logits added through shared memory) and
 //               the loss
-// The layers of a unit run in sequence (one activation region), each
-// layer's weight blocks double-buffered; the next unit's levels and layer-1
-// MMAs start as soon as this unit's layer-3 MMAs are done.  Every wait is
-// bounded; on expiry the kernel sets kStatusEvalTimeout and exits.
+// The layers of a unit share one activation region, each layer's weight
+// blocks double-buffered.  Layer 1's activations go to the layer-2 MMAs one
+// 64-column block at a time (the epilogue halves take two of each block's four
+// column groups); layer 3 starts after all of layer 2's; the next unit's
+// levels and layer-1 MMAs start as soon as this unit's layer-3 MMAs are done.
+// Every wait is bounded; on expiry the kernel sets kStatusEvalTimeout and exits.
 #include <cuda.h>
 
 #include <cuda_fp16.h>
@@ -105,7 +107,7 @@ struct TcSmem {
     uint8_t* slot;    // weights: hi piece then lo piece, N x 128 bytes each per 64-input block
     float *b1, *b2, *b3, *w4t, *b4;
     float* plog;  // [128][16]: the second half's partial layer-4 logits
-    uint64_t *buf_full, *buf_empty, *x_full, *d_full, *h_ready, *drain;
+    uint64_t *buf_full, *buf_empty, *x_full, *d_full, *h_blk, *h2_ready, *drain;
     uint32_t* tmem_holder;
     volatile int* abort_flag;
     int* ep_go;
@@ -120,7 +122,7 @@ __host__ __device__ inline size_t tc_param_floats(const int32_t* dims)
 
 __host__ __device__ inline size_t tc_smem_bytes(const int32_t* dims)
 {
-    return 1024 + kRegionBytes + kSlotBytes + sizeof(float) * tc_param_floats(dims) + 8 * 16 + 64;  // 11 barriers, 11 words
+    return 1024 + kRegionBytes + kSlotBytes + sizeof(float) * tc_param_floats(dims) + 8 * 16 + 64;  // 14 barriers, 11 words
 }
 
 __device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
@@ -142,9 +144,10 @@ __device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
     s.buf_empty = bars + 2;  // [2]
     s.x_full = bars + 4;
     s.d_full = bars + 5;     // [3]
-    s.h_ready = bars + 8;    // [2]
-    s.drain = bars + 10;
-    uint32_t* w = reinterpret_cast<uint32_t*>(bars + 11);
+    s.h_blk = bars + 8;      // [4]: a 64-column block of layer 1's activations is in
+    s.h2_ready = bars + 12;  // layer 2's activations are in
+    s.drain = bars + 13;
+    uint32_t* w = reinterpret_cast<uint32_t*>(bars + 14);
     s.tmem_holder = w;
     s.abort_flag = reinterpret_cast<volatile int*>(w + 1);
     s.ep_go = reinterpret_cast<int*>(w + 2);
@@ -246,7 +249,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
         }
         ptx::mbar_init(s.x_full, 1);
         for (int i = 0; i < 3; ++i) ptx::mbar_init(&s.d_full[i], 1);
-        for (int i = 0; i < 2; ++i) ptx::mbar_init(&s.h_ready[i], kEpiThreads);
+        for (int i = 0; i < 4; ++i) ptx::mbar_init(&s.h_blk[i], kEpiThreads);
+        ptx::mbar_init(s.h2_ready, kEpiThreads);
         ptx::mbar_init(s.drain, 1);
         *s.abort_flag = 0;
         *s.ep_go = 0;
@@ -272,8 +276,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                         break;
                     }
                     for (int l = 0; ok && l < 3; ++l) {
-                        if (l > 0 && !ptx::mbar_wait_bounded(&s.h_ready[l - 1], unit & 1u, s.abort_flag,
-                                                             kWaitLimitNs)) {
+                        // layer 3 after all of layer 2's activations (it reuses layer 2's
+                        // columns); layer 2 block by block below
+                        if (l == 2 && !ptx::mbar_wait_bounded(s.h2_ready, unit & 1u, s.abort_flag, kWaitLimitNs)) {
                             raise_abort(s, a);
                             ok = false;
                             break;
@@ -293,6 +298,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                                 break;
                             }
                             bphase ^= 1u << b;
+                            if (l == 1 &&
+                                !ptx::mbar_wait_bounded(&s.h_blk[kb], unit & 1u, s.abort_flag, kWaitLimitNs)) {
+                                raise_abort(s, a);
+                                ok = false;
+                                break;
+                            }
                             const uint32_t slot = region + buffer_offset(l, b);
                             ptx::tc_fence_after();
 #pragma unroll
@@ -427,30 +438,45 @@ __global__ void __launch_bounds__(kTcThreads, 1) eval_mlp_tc_kernel(const MlpTcA
                     // this half's 16-column groups
                     const int groups = N / 16, g0 = half ? groups / 2 : 0, g1 = half ? groups : groups / 2;
                     if (l < 2) {
-                        for (int c = 16 * g0; c < 16 * g1; c += 16) {
-                            float v[16];
-                            load_acc16(tmem_base + lane_addr + col(l) + static_cast<uint32_t>(c),
-                                       static_cast<uint32_t>(N), merged(l), v);
-                            uint32_t hi[8], lo[8];
+                        // 64-column blocks in order, two of each block's four groups per
+                        // half; layer 1's blocks go to the layer-2 MMAs one by one
+                        for (int gi = 0; gi < 2 * ((N + 63) / 64); ++gi) {
+                            const int kb = gi >> 1, g = 4 * kb + 2 * half + (gi & 1);
+                            const int c = 16 * g;
+                            if (g < groups) {
+                                float v[16];
+                                load_acc16(tmem_base + lane_addr + col(l) + static_cast<uint32_t>(c),
+                                           static_cast<uint32_t>(N), merged(l), v);
+                                uint32_t hi[8], lo[8];
 #pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                const float h0 = fmaxf(fmaf(v[2 * e], scale, bias[c + 2 * e]), 0.0f);
-                                const float h1 = fmaxf(fmaf(v[2 * e + 1], scale, bias[c + 2 * e + 1]), 0.0f);
-                                bad |= h0 >= kPieceRange || h1 >= kPieceRange;
-                                split2x2(h0, h1, hi[e], lo[e]);
+                                for (int e = 0; e < 8; ++e) {
+                                    const float h0 = fmaxf(fmaf(v[2 * e], scale, bias[c + 2 * e]), 0.0f);
+                                    const float h1 = fmaxf(fmaf(v[2 * e + 1], scale, bias[c + 2 * e + 1]), 0.0f);
+                                    bad |= h0 >= kPieceRange || h1 >= kPieceRange;
+                                    split2x2(h0, h1, hi[e], lo[e]);
+                                }
+                                uint8_t* dst = s.region + (c >> 6) * kBlockBytes;
+                                const int ch = (c & 63) >> 3;
+                                *reinterpret_cast<uint4*>(dst + swz(row, ch)) =
+                                    make_uint4(hi[0], hi[1], hi[2], hi[3]);
+                                *reinterpret_cast<uint4*>(dst + swz(row, ch + 1)) =
+                                    make_uint4(hi[4], hi[5], hi[6], hi[7]);
+                                *reinterpret_cast<uint4*>(dst + kHalfRegion + swz(row, ch)) =
+                                    make_uint4(lo[0], lo[1], lo[2], lo[3]);
+                                *reinterpret_cast<uint4*>(dst + kHalfRegion + swz(row, ch + 1)) =
+                                    make_uint4(lo[4], lo[5], lo[6], lo[7]);
                             }
-                            uint8_t* dst = s.region + (c >> 6) * kBlockBytes;
-                            const int ch = (c & 63) >> 3;
-                            *reinterpret_cast<uint4*>(dst + swz(row, ch)) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-                            *reinterpret_cast<uint4*>(dst + swz(row, ch + 1)) = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-                            *reinterpret_cast<uint4*>(dst + kHalfRegion + swz(row, ch)) =
-                                make_uint4(lo[0], lo[1], lo[2], lo[3]);
-                            *reinterpret_cast<uint4*>(dst + kHalfRegion + swz(row, ch + 1)) =
-                                make_uint4(lo[4], lo[5], lo[6], lo[7]);
+                            if (l == 0 && (gi & 1)) {
+                                ptx::fence_proxy_async_smem();
+                                ptx::tc_fence_before();
+                                ptx::mbar_arrive(&s.h_blk[kb]);
+                            }
                         }
-                        ptx::fence_proxy_async_smem();
-                        ptx::tc_fence_before();
-                        ptx::mbar_arrive(&s.h_ready[l]);
+                        if (l == 1) {
+                            ptx::fence_proxy_async_smem();
+                            ptx::tc_fence_before();
+                            ptx::mbar_arrive(s.h2_ready);
+                        }
                     } else {
                         // layer 3's ReLU, then layer 4 and the loss in FP32
                         float logit[kMaxOutTc];
