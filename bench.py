@@ -95,6 +95,10 @@ TRAFFIC = {
     "breed": {"bytes_per_launch": 707.47e6, "src_sha": "c8e7e85a0e65db99", "capture": "P=1000 plain workload"},
     "evaluate": {"bytes_per_launch": 359.45e6, "src_sha": "d972b174f2e01544", "capture": "P=1000 plain workload"},
     "breed_evaluate": {"bytes_per_launch": 738.19e6, "src_sha": "23e25d83744d9797", "capture": "P=1000 plain workload"},
+    # eval_mlp_tc_kernel alone (each individual's weight pieces read once from
+    # DRAM, the other tiles from L2); the stage also splits the weights
+    "evaluate_paper_net": {"bytes_per_launch": 869.37e6, "src_sha": "4d668950fd524059",
+                           "capture": "paper-net workload, eval_mlp_tc_kernel"},
 }
 
 
@@ -483,8 +487,12 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
         k16 = [(d + 15) // 16 * 16 for d in dims]
         issued = sum((2 if l == 0 else 3) * 2.0 * 128 * k16[l] * dims[l + 1] for l in range(3))
         kd["tensor_tflops_issued"] = pop * tiles * issued / 1e12 / (kd["ms_per_launch"] / 1000.0)
+    tr = TRAFFIC["evaluate_paper_net"]
+    traffic = (tr["bytes_per_launch"] if tensor and (pop, batch) == (PAPER_POP, PAPER_BATCH)
+               and tr["src_sha"] == _src_sha("leea_eval_mlp_tc.cu") else None)
     roofline = {"kernel": "evaluate", "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
-                "unit": "TFLOP/s", "frac": kd["frac"], "traffic": None,
+                "unit": "TFLOP/s", "frac": kd["frac"], "traffic": traffic,
+                "traffic_kernel": "eval_mlp_tc_kernel (DRAM bytes of the main kernel; not the weight split)",
                 "peak_source": t_src if tensor else
                 "derived: FP32 FFMA, 152 SM x 128 lanes x 2 x max SM clock (no measured FP32 peak)"}
     line = {"metric": "generations/sec and network·samples/sec, the paper's 92k-parameter network at lambda=2000, "

@@ -279,9 +279,10 @@ leea_status leea_breed_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_d
  * (hi.hi + hi.lo + lo.hi; the levels are exact), FP32 accumulation, FP32
  * bias, ReLU, last layer and loss; an individual with a weight or activation
  * |v| >= 128 is recomputed in FP32 on the CUDA cores.  That path splits the
- * weights into a library-owned scratch buffer (416 KB per individual for
- * 196-256-128-64-10) shared by these step calls, so such calls must not
- * overlap on the device; the state object owns its own.  f_adj_dev and
+ * weights and converts the batch into a library-owned scratch buffer (416 KB
+ * per individual for 196-256-128-64-10, plus 64 KB per 128 samples) shared by
+ * these step calls, so such calls must not overlap on the device; the state
+ * object owns its own.  f_adj_dev and
  * correct_dev may be NULL; f_raw_dev may not.  eval_path: LEEA_EVAL_*. */
 leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
                           const float* pop_dev, const float* x_dev, const int32_t* y_dev,
