@@ -245,3 +245,28 @@ def test_paper_net_learns(gpu):
         assert st.leea_fitness().max() > f0 + 0.1
     finally:
         st.close()
+
+
+def test_paper_net_state_object_across_batch_sizes(gpu, oracle_mod):
+    # One state object, batches growing and shrinking (its tensor-core scratch
+    # holds the batch's level tiles and grows with it): each generation's raw
+    # fitness matches the oracle's evaluation of that generation's children.
+    torch = _torch()
+    dims = PAPER_DIMS
+    pop = 24
+    st = gpu.LeeaState(pop, dims, gpu.Params(**PAPER_PRM), 21)
+    try:
+        for g, batch in enumerate((50, 300, 129, 1, 1024)):
+            rng = np.random.default_rng(100 + g)
+            levels = rng.integers(0, 256, size=(batch, 196)).astype(np.uint8)
+            y = rng.integers(0, 10, size=batch).astype(np.int32)
+            st.leea_generation_u8(torch.from_numpy(levels).cuda(), torch.from_numpy(y).cuda())
+            kids = st.leea_get_population()
+            f_raw = st.leea_raw_fitness()
+            _, cor = st.leea_fitness(with_correct=True)
+            f_ref, cor_ref, logits = oracle_mod.evaluate(kids.astype(np.float64), dims,
+                                                         levels.astype(np.float64) / 255.0, y, want_logits=True)
+            assert_fitness_close(f_raw, f_ref, f"batch {batch}")
+            assert_correct_close(cor, cor_ref, logits)
+    finally:
+        st.close()
