@@ -106,7 +106,11 @@ def _eval_u8(gpu, dims, popv, levels, y, path, f_inh=None, alpha=1.0):
 TC_CASES = [(PAPER_DIMS, 6, 1024), (PAPER_DIMS, 5, 129), (PAPER_DIMS, 3, 1), (PAPER_DIMS, 160, 100),
             ([64, 48, 32, 16, 4], 7, 200), ([256, 256, 128, 128, 16], 3, 77),
             # layers 2 and 3 wider than 128: three MMAs per 16 inputs, not the merged pair
-            ([128, 64, 256, 256, 10], 4, 150)]
+            ([128, 64, 256, 256, 10], 4, 150),
+            # d0 not a multiple of 64 (a partial last level block), a 48-wide merged layer
+            ([100, 32, 48, 16, 7], 5, 140),
+            # the smallest shape: one 16-input block, 16-wide layers
+            ([4, 16, 16, 16, 2], 3, 5)]
 
 
 @pytest.mark.parametrize("dims,pop,batch", TC_CASES, ids=lambda v: str(v))
