@@ -57,7 +57,11 @@ PAPER_PARAMS = dict(xo_op=0, xo_gene_p=0.5, sel_op=0, rho=0.5, n_elite=-1, p_e=0
 PAPER_WORKLOAD = ("the paper's network (Section 4.1): 2x2 max-pool of 28x28 synthetic images, then 196-256-128-64-10 "
                   "(92,042 params, FP32); lambda=2000, batch 1024, uniform crossover p_C=0.75, p_E=0.05, "
                   "rho=0.5, sigma=0.001 on every gene, alpha=1 (Section 4.5); the max-pool runs in every step")
+SMALL_POP, SMALL_DIMS, SMALL_BATCH = 32, [784, 32, 10], 16
+SMALL_WORKLOAD = ("P=32 MLPs 784-32-10 (25,450 params, FP32), batch 16 synthetic 28x28 images as 8-bit levels; "
+                  "operators as the plain workload")
 CONFIGS = {"plain": dict(pop=1000, batch=100, precision=0),
+           "small": dict(pop=SMALL_POP, batch=SMALL_BATCH, precision=0),
            "paper-net": dict(pop=PAPER_POP, batch=PAPER_BATCH, precision=0),
            "precision-bf16": dict(pop=4096, batch=256, precision=1),
            "precision-fp8": dict(pop=4096, batch=256, precision=2),
@@ -510,8 +514,9 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
                        "l2": f"inputs larger than L2 (2 population buffers of "
                              f"{pop * leea.leea_padded_params(dims) * 4 / 1e6:.0f} MB), no flush"},
             "network_samples_per_sec": gen_per_s * pop * batch, "e2e": e2e,
-            # + the max-pool, + the FP32 recomputation launch of marked individuals after the tensor-core evaluation
-            "gpu_launches": int(steps * (1 + (1 if tensor else 0) + sum(kernels_per_generation(pop, batch, 0).values()))),
+            # + the max-pool; the tensor-core evaluation is four launches: the weight split, the level
+            # tiles, the kernel and the FP32 recomputation of marked individuals
+            "gpu_launches": int(steps * (1 + (3 if tensor else 0) + sum(kernels_per_generation(pop, batch, 0).values()))),
             "roofline": roofline, "kernels": kernels, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x_last = xtr[idx[warmup + steps]].astype(np.float64)
@@ -520,6 +525,130 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
         pooled_h = oracle.maxpool2x2(x_last, 28, 28) / 255.0
         line["cpu_baseline"] = paper_cpu_baseline(st.leea_get_population(), st.leea_fitness(), pooled_h,
                                                   ytr[idx[warmup + steps]], n_children=min(args.cpu_children, 40))
+    st.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def small_cpu_baseline(parents, f_adj, x64, y) -> dict:
+    """The oracle on one host core: one whole generation of the small workload
+    (rank, select, breed and evaluate all P children, inheritance)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    prm = oracle.Params(**PARAMS)
+    p64, f64 = parents.astype(np.float64), f_adj.astype(np.float64)
+    t0 = time.perf_counter()
+    order = oracle.rank(f64)
+    p1, p2, kind, f_inh = oracle.select(prm, f64, order, 0, 1)
+    kids = oracle.breed(prm, SMALL_DIMS, 0, 1, p64, p1, p2, kind)
+    f, _ = oracle.evaluate(kids, SMALL_DIMS, x64, y)
+    oracle.inherit(float(prm.alpha), f_inh, f, first=False)
+    secs = time.perf_counter() - t0
+    return {"value": 1.0 / secs, "unit": "generations/s", "cores": 1, "kind": "oracle",
+            "sample": f"one whole generation: rank+select, breed and evaluate all {SMALL_POP} children, "
+                      f"batch {SMALL_BATCH}", "seconds": secs}
+
+
+def run_small(args, rank: int, world: int, local_rank: int):
+    """The small configuration (P=32, 784-32-10, batch 16): launch latency, not
+    bytes, bounds a generation, so each generation is timed on its own between
+    CUDA events with L2 flushed in between (the population is 3 MB)."""
+    import numpy as np
+    import torch
+    from paper_1806_09819_gb300 import build as B
+    from paper_1806_09819_gb300 import leea, synthetic
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = dist_init(world, True)
+    if rank == 0 or world == 1:
+        B.build()
+    barrier(dist, dev)
+    B.build()
+    leea.load_library()
+    steps, warmup = args.steps, args.warmup
+    pop, batch, dims = SMALL_POP, SMALL_BATCH, SMALL_DIMS
+    (xtr, ytr), _ = synthetic.dataset(n_train=60000, n_test=1)
+    xtr = synthetic.to_levels(xtr)
+    n_batches = warmup + 1 + steps
+    idx = synthetic.batch_indices(len(ytr), batch, n_batches, seed=synthetic.BATCH_SEED + rank)
+    xs = torch.from_numpy(xtr[idx]).to(dev)
+    ys = torch.from_numpy(ytr[idx]).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 126 MB L2
+    st = leea.LeeaState(pop, dims, leea.Params(**PARAMS, eval_path=args.eval_path), seed=1000 + rank, stream=stream)
+    for k in range(warmup + 1):  # the first call evaluates the initial population
+        st.leea_generation_u8(xs[k], ys[k], 255.0)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(_gpu_id_for(local_rank))
+    clocks.start()
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    mark = clocks.mark()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 255)  # outside the timed pair: the next generation starts from DRAM
+        evs[k][0].record(stream)
+        st.leea_generation_u8(xs[warmup + 1 + k], ys[warmup + 1 + k], 255.0)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(dist, dev)
+    clk = clocks.stop(mark)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms_max, gen_per_s = job_rate(world, steps, ms, dist, dev)
+    # back to back, no flush: the steady state with the population in L2
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(steps):
+        st.leea_generation_u8(xs[warmup + 1 + k], ys[warmup + 1 + k], 255.0)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    us_b2b = e0.elapsed_time(e1) * 1000.0 / steps
+
+    # end to end through the host-batch call: H2D of the batch, a generation, the fitness read back
+    e2e_steps = max(10, min(steps, 500))
+    sel = idx[np.arange(e2e_steps) % n_batches]
+    xh, yh = xtr[sel], ytr[sel]
+    f_host = None
+    barrier(dist, dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        st.leea_generation_u8_host(xh[k], yh[k], 255.0)
+        f_host = st.leea_fitness()
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
+    e2e = {"value": world * e2e_steps / t_e2e, "unit": "generations/s",
+           "h2d_bytes_per_step": int(xh[0].nbytes + yh[0].size * 4), "d2h_bytes_per_step": int(f_host.nbytes),
+           "steps": e2e_steps}
+
+    hbm_peak, _, peak_src = _peaks()
+    n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PARAMS))
+    c = leea.leea_num_params(dims)
+    gen_bytes = 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + 4.0 * c * pop  # breed, then the evaluation's weights
+    us = ms_max * 1000.0 / steps
+    roofline = {"kernel": "generation", "bound": "hbm", "achieved": gen_bytes / (us * 1e-6) / 1e9,
+                "peak": hbm_peak, "unit": "GB/s", "frac": gen_bytes / (us * 1e-6) / 1e9 / hbm_peak,
+                "traffic": None, "peak_source": f"{peak_src} (HBM copy)",
+                "note": "launch-latency bound: a generation's algorithmic bytes over its whole time"}
+    line = {"metric": "generations/sec and microseconds per generation at P=32, 784-32-10, batch 16; % of roofline",
+            "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+            "ms_per_step": ms_max / steps, "us_per_generation": us, "us_per_generation_back_to_back": us_b2b,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SMALL_WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
+                       "timing": "CUDA events around each generation, L2 flushed (256 MB write) between "
+                                 "generations outside the events; back to back: one event pair, no flush",
+                       "input": "uint8 levels k, x = k/255",
+                       "l2": "flushed between timed generations"},
+            "network_samples_per_sec": gen_per_s * pop * batch, "e2e": e2e,
+            "gpu_launches": int(steps * sum(kernels_per_generation(pop, batch, 0).values())),
+            "roofline": roofline, "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        x64 = xtr[idx[warmup + steps]].astype(np.float64) / 255.0
+        line["cpu_baseline"] = small_cpu_baseline(st.leea_get_population(), st.leea_fitness(), x64,
+                                                  ytr[idx[warmup + steps]])
     st.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -953,7 +1082,8 @@ def main():
                     help="0 auto (fused breed + evaluate where it applies), 1 CUDA-core FP32, 2 tensor cores as a "
                          "separate kernel, 3 fused")
     ap.add_argument("--config", choices=sorted(CONFIGS), default="plain",
-                    help="plain: the headline FP32 workload; precision-*: P=4096, batch 256, BF16/FP8 shadows; "
+                    help="plain: the headline FP32 workload; small: P=32, 784-32-10, batch 16 (launch latency); "
+                         "precision-*: P=4096, batch 256, BF16/FP8 shadows; "
                          "batching: 64 uneven runs together; paper-net: the paper's 196-256-128-64-10 behind 2x2 "
                          "max-pooling at lambda=2000, batch 1024")
     ap.add_argument("--pop", type=int, default=0, help="override the population size (small profiling cases)")
@@ -966,6 +1096,8 @@ def main():
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.config == "small":
+        run_small(args, rank, world, local_rank)
     elif args.config == "paper-net":
         run_paper_net(args, rank, world, local_rank)
     elif args.config == "batching":
