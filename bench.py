@@ -44,6 +44,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "generations/sec and network·samples/sec at P=1000, 89k MLP; % of roofline"
+PAPER_METRIC = ("generations/sec and network·samples/sec, the paper's 92k-parameter network at lambda=2000, "
+                "batch 1024; % of roofline")
+SMALL_METRIC = "generations/sec and microseconds per generation at P=32, 784-32-10, batch 16; % of roofline"
 POP, DIMS, BATCH = 1000, [784, 112, 10], 100
 PARAMS = dict(xo_op=0, xo_gene_p=0.5, sel_op=0, rho=0.5, n_elite=1, p_c=0.5, sigma=0.005, mut_rate=0.1,
               alpha=1.0, init=0)
@@ -336,49 +339,92 @@ def precision_report(st, levels, y, precision: int, n: int = 64) -> dict:
 # arms
 # --------------------------------------------------------------------------------
 def run_reference(args, rank: int, world: int):
-    """The oracle as the reference arm: each step a bounded sample of one generation."""
+    """The oracle as the reference arm, on the native arm's configuration: each
+    step a bounded sample of one generation (the whole generation for the
+    small configuration)."""
     if rank != 0:
         return
-    inputs = oracle_inputs()
+    import numpy as np
+    import oracle
+    from paper_1806_09819_gb300 import synthetic
+    oracle.build()
+    if args.config == "plain":
+        inputs = oracle_inputs()
+        pop, batch, workload, metric = POP, BATCH, WORKLOAD, METRIC
+
+        def step(n, gen):
+            return oracle_step_sample(*inputs, n_children=n, gen=gen)
+    elif args.config == "small":
+        pop, batch, workload, metric = SMALL_POP, SMALL_BATCH, SMALL_WORKLOAD, SMALL_METRIC
+        parents = synthetic.random_population(pop, oracle.num_params(SMALL_DIMS), seed=1, scale=0.05)
+        f_adj = np.random.default_rng(2).normal(-2.3, 0.05, size=pop).astype(np.float32)
+        x, y = synthetic.make_split(batch, seed=4)
+        x64 = synthetic.to_levels(x).astype(np.float64) / 255.0
+
+        def step(n, gen):
+            return small_cpu_baseline(parents, f_adj, x64, y)["seconds"]
+    elif args.config == "paper-net":
+        pop, batch, workload, metric = PAPER_POP, PAPER_BATCH, PAPER_WORKLOAD, PAPER_METRIC
+        par64 = synthetic.random_population(pop, oracle.num_params(PAPER_DIMS), seed=1, scale=0.05).astype(np.float64)
+        f64 = np.random.default_rng(2).normal(-2.3, 0.05, size=pop)
+        x, y = synthetic.make_split(batch, seed=4)
+        pooled64 = oracle.maxpool2x2(synthetic.to_levels(x).astype(np.float64), 28, 28) / 255.0
+
+        def step(n, gen):
+            return paper_step_sample(par64, f64, pooled64, y, n, gen)
+    else:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the plain, small and paper-net "
+                                                              f"configurations, not {args.config}"}), flush=True)
+        return
     per_step_budget = 60.0 / max(1, args.steps + args.warmup)
-    probe = oracle_step_sample(*inputs, n_children=2, gen=1) / 2.0
-    n_children = int(max(1, min(POP, round(per_step_budget / max(probe, 1e-6)))))
+    if args.config == "small":
+        n_children = pop  # a whole generation per step
+    else:
+        probe = step(2, 1) / 2.0
+        n_children = int(max(1, min(pop, round(per_step_budget / max(probe, 1e-6)))))
     for w in range(args.warmup):
-        oracle_step_sample(*inputs, n_children=n_children, gen=2 + w)
+        step(n_children, 2 + w)
     total = 0.0
     for k in range(args.steps):
-        total += oracle_step_sample(*inputs, n_children=n_children, gen=100 + k)
-    gen_per_s = args.steps * (n_children / POP) / total
-    sample = (f"per step: rank+select of {POP} nets, breed+evaluate of {n_children} of {POP} children, "
-              f"batch {BATCH}; value = steps*({n_children}/{POP}) / seconds")
-    line = {"impl": "reference", "metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * POP / n_children * total / args.steps,
+        total += step(n_children, 100 + k)
+    gen_per_s = args.steps * (n_children / pop) / total
+    sample = (f"per step: rank+select of {pop} nets, breed+evaluate of {n_children} of {pop} children, "
+              f"batch {batch}; value = steps*({n_children}/{pop}) / seconds")
+    line = {"impl": "reference", "metric": metric, "value": gen_per_s, "unit": "generations/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * pop / n_children * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "l2": "host CPU run"},
+            "config": {"workload": workload, "l2": "host CPU run"},
             "cpu_baseline": {"value": gen_per_s, "unit": "generations/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": gen_per_s, "unit": "generations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "network_samples_per_sec": gen_per_s * POP * BATCH}
+            "network_samples_per_sec": gen_per_s * pop * batch}
     print(json.dumps(line), flush=True)
 
 
-def paper_cpu_baseline(parents, f_adj, pooled64, y, n_children: int) -> dict:
+def paper_step_sample(par64, f64, pooled64, y, n_children: int, gen: int) -> float:
     """The oracle on one generation of the paper's network: rank + select all
-    lambda children, breed and evaluate n_children of them (strided)."""
+    lambda children, breed and evaluate n_children of them (strided); returns
+    the CPU seconds taken."""
     import numpy as np
     import oracle
-    oracle.build()
     prm = oracle.Params(**PAPER_PARAMS)
-    par64, f64 = parents.astype(np.float64), f_adj.astype(np.float64)
     t0 = time.perf_counter()
     order = oracle.rank(f64)
-    p1, p2, kind, f_inh = oracle.select(prm, f64, order, 0, 1)
+    p1, p2, kind, f_inh = oracle.select(prm, f64, order, 0, gen)
     rows = np.linspace(0, PAPER_POP - 1, n_children).round().astype(int)
-    kids = np.concatenate([oracle.breed(prm, PAPER_DIMS, 0, 1, par64, p1, p2, kind, j0=int(j), j1=int(j) + 1)
+    kids = np.concatenate([oracle.breed(prm, PAPER_DIMS, 0, gen, par64, p1, p2, kind, j0=int(j), j1=int(j) + 1)
                            for j in rows])
     f, _ = oracle.evaluate(kids, PAPER_DIMS, pooled64, y)
     oracle.inherit(float(prm.alpha), f_inh[rows], f, first=False)
-    secs = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def paper_cpu_baseline(parents, f_adj, pooled64, y, n_children: int) -> dict:
+    """The oracle on one generation of the paper's network (paper_step_sample)."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    secs = paper_step_sample(parents.astype(np.float64), f_adj.astype(np.float64), pooled64, y, n_children, 1)
     gen_per_s = (n_children / PAPER_POP) / secs
     return {"value": gen_per_s, "unit": "generations/s", "cores": 1, "kind": "oracle",
             "sample": f"one generation's rank+select over all {PAPER_POP} nets, breed+evaluate of {n_children} of "
@@ -499,9 +545,7 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
                 "traffic_kernel": "eval_mlp_tc_kernel (DRAM bytes of the main kernel; not the weight split)",
                 "peak_source": t_src if tensor else
                 "derived: FP32 FFMA, 152 SM x 128 lanes x 2 x max SM clock (no measured FP32 peak)"}
-    line = {"metric": "generations/sec and network·samples/sec, the paper's 92k-parameter network at lambda=2000, "
-                      "batch 1024; % of roofline",
-            "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+    line = {"metric": PAPER_METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
             "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": PAPER_WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
@@ -633,8 +677,7 @@ def run_small(args, rank: int, world: int, local_rank: int):
                 "peak": hbm_peak, "unit": "GB/s", "frac": gen_bytes / (us * 1e-6) / 1e9 / hbm_peak,
                 "traffic": None, "peak_source": f"{peak_src} (HBM copy)",
                 "note": "launch-latency bound: a generation's algorithmic bytes over its whole time"}
-    line = {"metric": "generations/sec and microseconds per generation at P=32, 784-32-10, batch 16; % of roofline",
-            "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
+    line = {"metric": SMALL_METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world, "steps": steps, "warmup": warmup,
             "ms_per_step": ms_max / steps, "us_per_generation": us, "us_per_generation_back_to_back": us_b2b,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": SMALL_WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
