@@ -8,7 +8,14 @@ breed, evaluate).  The population (2 x 356 MB) is larger than L2, so no flush
 is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
-                    [--config plain|precision-bf16|precision-fp8|batching|surrogate|paper-net]
+                    [--config plain|small|precision-bf16|precision-fp8|batching|surrogate|paper-net]
+
+--config small measures the small configuration (P = 32 nets 784-32-10,
+batch 16), which launch latency bounds: each generation is timed between CUDA
+events with L2 flushed in between, and the line adds microseconds per
+generation.  --config paper-net measures the paper's own network (Section
+4.1: 2x2 max-pooling, 196-256-128-64-10) at its Section 4.5 setting (lambda =
+2000, batch 1024) on the tensor cores.
 
 --config precision-* measures the precision form instead (P = 4096 nets
 784-112-10, batch 256, BF16 or FP8-e4m3 shadows of W1 with FP32 accumulation
@@ -27,6 +34,8 @@ time each needs to reach the accuracy both attain.
 N > 1 (under torch.distributed.run) runs N independent replicas, one per GPU
 (the generation's selection needs every parent, so a run does not shard);
 the value is all replicas' generations over the slowest replica's time.
+--impl reference times the FP64 oracle on the host cores for the plain, small
+and paper-net configurations (a bounded sample of each generation).
 """
 from __future__ import annotations
 
