@@ -113,7 +113,7 @@ TRAFFIC = {
     "breed_evaluate": {"bytes_per_launch": 738.19e6, "src_sha": "23e25d83744d9797", "capture": "P=1000 plain workload"},
     # eval_mlp_tc_kernel alone (each individual's weight pieces read once from
     # DRAM, the other tiles from L2); the stage also splits the weights
-    "evaluate_paper_net": {"bytes_per_launch": 869.37e6, "src_sha": "4d668950fd524059",
+    "evaluate_paper_net": {"bytes_per_launch": 869.37e6, "src_sha": "b394b877523b3071",
                            "capture": "paper-net workload, eval_mlp_tc_kernel"},
 }
 

@@ -15,7 +15,8 @@
 //               the hi activations are one MMA of width 2N against the stacked
 //               [W_hi; W_lo] block (its rows are contiguous), lo.hi adds onto
 //               the second half, and the epilogue sums the halves: 2 MMAs per
-//               16 inputs (an MMA costs about the same up to N = 256), else 3
+//               16 inputs (an MMA of N = 256 costs little more than one of
+//               N = 128), else 3
 // The epilogue adds the bias and applies ReLU in FP32, splits the activations
 // for the next layer, and computes layer 4 (d3 -> d_out), the softmax
 // cross-entropy and the loss sums in FP32, tiles in order.  A weight or an
@@ -122,7 +123,8 @@ __host__ __device__ inline size_t tc_param_floats(const int32_t* dims)
 
 __host__ __device__ inline size_t tc_smem_bytes(const int32_t* dims)
 {
-    return 1024 + kRegionBytes + kSlotBytes + sizeof(float) * tc_param_floats(dims) + 8 * 16 + 64;  // 14 barriers, 11 words
+    // room for 16 barriers (14 used) and 16 words (11 used)
+    return 1024 + kRegionBytes + kSlotBytes + sizeof(float) * tc_param_floats(dims) + 8 * 16 + 64;
 }
 
 __device__ __forceinline__ TcSmem carve(uint8_t* raw, const MlpTcArgs& a)
