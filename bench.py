@@ -664,7 +664,8 @@ def run_small(args, rank: int, world: int, local_rank: int):
     # end to end through the host-batch call: H2D of the batch, a generation, the fitness read back
     e2e_steps = max(10, min(steps, 500))
     sel = idx[np.arange(e2e_steps) % n_batches]
-    xh, yh = xtr[sel], ytr[sel]
+    xh = torch.from_numpy(xtr[sel]).pin_memory()  # the batches in pinned host memory
+    yh = torch.from_numpy(ytr[sel]).pin_memory()
     f_host = None
     barrier(dist, dev)
     torch.cuda.synchronize(dev)
@@ -674,7 +675,7 @@ def run_small(args, rank: int, world: int, local_rank: int):
         f_host = st.leea_fitness()
     t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
     e2e = {"value": world * e2e_steps / t_e2e, "unit": "generations/s",
-           "h2d_bytes_per_step": int(xh[0].nbytes + yh[0].size * 4), "d2h_bytes_per_step": int(f_host.nbytes),
+           "h2d_bytes_per_step": int(xh[0].numel() + yh[0].numel() * 4), "d2h_bytes_per_step": int(f_host.nbytes),
            "steps": e2e_steps}
 
     hbm_peak, _, peak_src = _peaks()
