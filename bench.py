@@ -521,7 +521,7 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
     hbm_peak, sm_max_mhz, peak_src = _peaks()
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
     n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PAPER_PARAMS))
-    c = leea.leea_num_params(dims)
+    c = leea.leea_layout_num_params(dims)
     macs = sum(dims[l] * dims[l + 1] for l in range(len(dims) - 1))
     tensor = args.eval_path != leea.EVAL_SIMT  # 8-bit inputs, three hidden layers: tcgen05 FP16 pieces
     t_peak, t_src = _tensor_peak()
@@ -680,7 +680,7 @@ def run_small(args, rank: int, world: int, local_rank: int):
 
     hbm_peak, _, peak_src = _peaks()
     n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PARAMS))
-    c = leea.leea_num_params(dims)
+    c = leea.leea_layout_num_params(dims)
     gen_bytes = 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + 4.0 * c * pop  # breed, then the evaluation's weights
     us = ms_max * 1000.0 / steps
     roofline = {"kernel": "generation", "bound": "hbm", "achieved": gen_bytes / (us * 1e-6) / 1e9,
@@ -795,7 +795,7 @@ def run_batching(args, rank: int, world: int, local_rank: int):
     breed_b = evaluate_b = 0.0
     for sp in specs:
         dims = [DIMS[0], sp.hidden, DIMS[2]]
-        c = leea.leea_num_params(dims)
+        c = leea.leea_layout_num_params(dims)
         n_e, n_c, n_m, _ = leea.leea_counts(sp.pop, leea.Params(**PARAMS))
         shadow = DIMS[0] * sp.hidden * 2
         breed_b += 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + shadow * sp.pop
@@ -1030,15 +1030,16 @@ def run_native(args, rank: int, world: int, local_rank: int):
     # ---- roofline of the dominant kernel ----
     hbm_peak, sm_max_mhz, peak_src = _peaks()
     n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PARAMS))
-    c = leea.leea_num_params(DIMS)
+    c = leea.leea_layout_num_params(DIMS)
     d0, h, d_out = DIMS
     tensor_eval = args.eval_path != leea.EVAL_SIMT
     elem = {0: 4, 1: 2, 2: 1}[precision]
     shadow_bytes = d0 * h * elem if precision else 0  # per child written by breed, read by evaluate
     work = {
-        # parents read once per use, children written (FP32 master, plus the shadow of W1)
-        "breed": ("hbm", (4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + shadow_bytes * (n_e + n_c + n_m)) / 1e9,
-                  "GB/s", hbm_peak),
+        # one read and one write per child gene (8c bytes per child in FP32; a
+        # crossover child's second parent is not counted: repeats hit L2), plus
+        # the shadow of W1 written in the precision form
+        "breed": ("hbm", (8.0 * c + shadow_bytes) * (n_e + n_c + n_m) / 1e9, "GB/s", hbm_peak),
         # tensor-core path: the per-individual weight stream (X stays in L2);
         # precision form: the shadow of W1 plus b1, W2, b2 from the master;
         # CUDA-core path: FP32 FFMA work
@@ -1072,6 +1073,16 @@ def run_native(args, rank: int, world: int, local_rank: int):
     roofline = {"kernel": dom, "bound": kd["bound"], "achieved": kd["achieved"], "peak": kd["peak"],
                 "unit": kd["unit"], "frac": kd["frac"], "traffic": traffic,
                 "peak_source": f"{peak_src} ({'HBM copy' if kd['unit'] == 'GB/s' else 'FP32 FFMA: 152 SM x 128 lanes x 2 x max SM clock'})"}
+    if traffic is not None and kd["unit"] == "GB/s":  # DRAM bytes the kernel really moved, at its measured time
+        roofline["dram_frac"] = traffic / (kd["ms_per_launch"] / 1000.0) / 1e9 / kd["peak"]
+    # the whole generation: breed and evaluation algorithmic bytes over the
+    # step time (the evaluation's weight stream is gone when the two are fused)
+    if fused or tensor_eval:
+        gen_alg = work["breed"][1] + (0.0 if fused else work["evaluate"][1])
+        roofline["generation"] = {"algorithmic_gb": gen_alg, "ms": ms_max / steps,
+                                  "achieved": gen_alg / (ms_max / steps / 1000.0),
+                                  "frac": gen_alg / (ms_max / steps / 1000.0) / hbm_peak,
+                                  "floor_ms": gen_alg / hbm_peak * 1000.0}
     if tensor_eval:  # tensor-core work issued (passes, M padded to 128-sample tiles, K to the MMA step)
         k_pad = {0: 784 if u8 else 800, 1: 784, 2: 800}[precision]
         passes = {0: 2 if u8 else 3, 1: 1, 2: 2}[precision]  # u8: two FP16 weight pieces; float: 3xTF32

@@ -168,8 +168,10 @@ leea_status leea_default_params(leea_params* out);
 /* Layout and operator counts                                              */
 /* ---------------------------------------------------------------------- */
 
-/* c, the number of genes of one individual (Section 3.2); -1 if dims invalid. */
-int64_t leea_num_params(const int32_t* dims, int32_t n_dims);
+/* c, the number of genes of one individual of the layout `dims` (Section
+ * 3.2: the direct encoding theta in R^c); -1 if dims is invalid.  The state
+ * object's own c is leea_num_params(s). */
+int64_t leea_layout_num_params(const int32_t* dims, int32_t n_dims);
 
 /* c_pad = round_up(c, 32), the device stride between individuals; -1 if invalid. */
 int64_t leea_padded_params(const int32_t* dims, int32_t n_dims);
@@ -280,9 +282,10 @@ leea_status leea_breed_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_d
  * bias, ReLU, last layer and loss; an individual with a weight or activation
  * |v| >= 128 is recomputed in FP32 on the CUDA cores.  That path splits the
  * weights and converts the batch into a library-owned scratch buffer (416 KB
- * per individual for 196-256-128-64-10, plus 64 KB per 128 samples) shared by
- * these step calls, so such calls must not overlap on the device; the state
- * object owns its own.  f_adj_dev and
+ * per individual for 196-256-128-64-10, plus 64 KB per 128 samples), one per
+ * device, shared by these step calls on that device, so such calls must not
+ * overlap on one device; growing it frees the old buffer (which synchronises
+ * the device).  The state object owns its own.  f_adj_dev and
  * correct_dev may be NULL; f_raw_dev may not.  eval_path: LEEA_EVAL_*. */
 leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
                           const float* pop_dev, const float* x_dev, const int32_t* y_dev,
@@ -359,9 +362,10 @@ leea_status leea_evaluate_shadow_u8(int32_t pop, const int32_t* dims, int32_t n_
  * the same call.  There is one array per device, so calls whose device work
  * can overlap (other streams, other host threads, without an ordering
  * between them) race on it; order them, e.g. on one stream.  The first call
- * on a device looks up the array's address (with that device current) and
- * sets the kernel's shared-memory attribute; make it before any stream
- * capture.  No claim is made about use inside CUDA graph capture.  Other
+ * on a device looks up the array's address (with that device current; the
+ * lookup is safe from several host threads); make that first call before
+ * any stream capture.  Every call sets the kernel's shared-memory size
+ * attribute.  No claim is made about use inside CUDA graph capture.  Other
  * arguments, requirements and results as in leea_evaluate_shadow_u8. */
 #define LEEA_NOALLOC_SCRATCH_BYTES (1 << 20)
 leea_status leea_evaluate_shadow_u8_noalloc(int32_t pop, const int32_t* dims, int32_t n_dims,
@@ -438,14 +442,23 @@ leea_status leea_generation_u8_host(leea_state* s, const uint8_t* x_u8_host, flo
                                     const int32_t* y_host, int32_t batch);
 
 /* Adjusted fitness f_adj (float[pop]) and, if correct_host is not NULL, the
- * correct-prediction counts of the last evaluation.  Synchronises. */
+ * correct-prediction counts of the last evaluation.  f_adj is the fitness
+ * Algorithm 1 sorts by: the blend (1 - alpha) f_inh + alpha f of Section 3.1
+ * (fitness inheritance), or the raw f of Eq. 1 after the first call.
+ * Caller-owned host buffers of pop elements.  Synchronises the object's
+ * stream and checks the device status word first (LEEA_ETIMEOUT if a kernel
+ * gave up a wait; the values are then invalid). */
 leea_status leea_fitness(leea_state* s, float* f_adj_host, int32_t* correct_host);
 
 /* Raw fitness f of the last evaluation, before inheritance.  Synchronises. */
 leea_status leea_raw_fitness(leea_state* s, float* f_raw_host);
 
 /* Genes (float[c], logical layout) of the individual with the highest f_adj
- * (ties to the lower index, NaN as -infinity).  Synchronises. */
+ * (ties to the lower index, NaN as -infinity): the head of Algorithm 1's
+ * sorted population, the net the algorithm returns.  c must equal
+ * leea_num_params(s) (LEEA_EINVAL otherwise), and LEEA_ESTATE before the
+ * first generation call; out_host is caller-owned.
+ * Synchronises. */
 leea_status leea_best_params(leea_state* s, float* out_host, int64_t c);
 
 /* Whole current population, float[pop][c] logical layout.  Synchronises. */
@@ -485,8 +498,10 @@ leea_status leea_get_sigma(leea_state* s, float* sigma_host);
  * unless the object runs LEEA_SIGMA_SELF. */
 leea_status leea_set_sigma(leea_state* s, const float* sigma_host);
 
-/* c of the object's nets, or -1 for NULL. */
-int64_t leea_state_num_params(const leea_state* s);
+/* c, the length of the genome theta in R^c of the object's nets (Section
+ * 3.2's direct encoding: every weight and bias of the net is one gene), or
+ * -1 for NULL. */
+int64_t leea_num_params(const leea_state* s);
 
 /* Per-stage timing with CUDA events recorded on the object's stream around
  * each kernel of leea_generation.  Stages: 0 ranking + selection (one fused
@@ -595,7 +610,10 @@ uint32_t leea_multi_generation_index(const leea_multi* m);
 leea_status leea_multi_profile_enable(leea_multi* m, int32_t enable);
 leea_status leea_multi_profile_read(leea_multi* m, double* ms_out, int64_t* launches_out);
 
-/* Frees the object and its device memory (synchronises its stream first). */
+/* Ends the run of Algorithm 1 held by the object: synchronises its stream,
+ * then frees the object and all device memory it owns (both population
+ * buffers and the per-individual arrays).  NULL is ignored.  Caller-owned
+ * buffers (minibatches, the stream) are not touched. */
 void leea_multi_destroy(leea_multi* m);
 
 /* Autotuner support: mean time in ms of `reps` shadow evaluations of a
@@ -772,7 +790,10 @@ void leea_surr_destroy(leea_surr* s);
 /* Thread-local message of the last failure on this thread ("" if none). */
 const char* leea_last_error(void);
 
-/* Frees the object and its device memory (synchronises its stream first). */
+/* Ends the run of Algorithm 1 held by the object: synchronises its stream,
+ * then frees the object and all device memory it owns (both population
+ * buffers and the per-individual arrays).  NULL is ignored.  Caller-owned
+ * buffers (minibatches, the stream) are not touched. */
 void leea_destroy(leea_state* s);
 
 #if defined(__GNUC__)

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -130,17 +131,21 @@ __device__ unsigned int g_device_status = 0;
 
 // Device address of g_device_status on the current device (looked up once per
 // device, with that device current).
+// Host threads may race on the first lookup; each stores the same address,
+// and the atomic entries make that race well defined.
 unsigned int* device_status_ptr()
 {
-    static unsigned int* cache[64] = { nullptr };
+    static std::atomic<unsigned int*> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    if (!cache[dev]) {
+    unsigned int* hit = cache[dev].load(std::memory_order_acquire);
+    if (!hit) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
-        cache[dev] = static_cast<unsigned int*>(p);
+        hit = static_cast<unsigned int*>(p);
+        cache[dev].store(hit, std::memory_order_release);
     }
-    return cache[dev];
+    return hit;
 }
 
 // Scratch of leea_evaluate_shadow_u8_noalloc: the per-tile partial sums of one
@@ -154,7 +159,7 @@ static __device__ __align__(256) float g_noalloc_scratch[LEEA_NOALLOC_SCRATCH_BY
 // per device, with that device current); NULL with the CUDA error in *err.
 float* noalloc_scratch_ptr(cudaError_t* err)
 {
-    static float* cache[64] = { nullptr };
+    static std::atomic<float*> cache[64];  // same-address stores only, as in device_status_ptr
     int dev = 0;
     *err = cudaGetDevice(&dev);
     if (*err != cudaSuccess) return nullptr;
@@ -162,13 +167,13 @@ float* noalloc_scratch_ptr(cudaError_t* err)
         *err = cudaErrorInvalidDevice;
         return nullptr;
     }
-    if (!cache[dev]) {
-        float* p = nullptr;
-        *err = cudaGetSymbolAddress(reinterpret_cast<void**>(&p), g_noalloc_scratch);
+    float* hit = cache[dev].load(std::memory_order_acquire);
+    if (!hit) {
+        *err = cudaGetSymbolAddress(reinterpret_cast<void**>(&hit), g_noalloc_scratch);
         if (*err != cudaSuccess) return nullptr;
-        cache[dev] = p;
+        cache[dev].store(hit, std::memory_order_release);
     }
-    return cache[dev];
+    return hit;
 }
 
 // Synchronises `stream`, reads and clears the status word.
@@ -381,7 +386,7 @@ leea_status leea_default_params(leea_params* out)
     return LEEA_OK;
 }
 
-int64_t leea_num_params(const int32_t* dims, int32_t n_dims)
+int64_t leea_layout_num_params(const int32_t* dims, int32_t n_dims)
 {
     NetLayout net;
     return make_layout(dims, n_dims, 0, &net) ? net.c : -1;
@@ -638,22 +643,24 @@ leea_status leea_evaluate_shadow_u8_noalloc(int32_t pop, const int32_t* dims, in
 {
     leea_status st = check_pop(pop);
     if (st) return st;
-    NetLayout net;
-    if (!make_layout(dims, n_dims, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
-    if ((st = check_shadow_shape(net, precision))) return st;
     if (batch <= 0) return fail(LEEA_EINVAL, "batch must be >= 1");
-    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
-    if (!pop_dev || !shadow_dev || !x_u8_dev || !y_dev || !f_raw_dev || (precision == 2 && !scale_exp_dev))
-        return fail(LEEA_EINVAL, "NULL device pointer");
-    if ((reinterpret_cast<uintptr_t>(pop_dev) & 15u) || (reinterpret_cast<uintptr_t>(shadow_dev) & 127u) ||
-        (reinterpret_cast<uintptr_t>(x_u8_dev) & 15u))
-        return fail(LEEA_EINVAL, "population, x (16-byte) and shadow (128-byte) must be aligned");
+    // The size limit depends on pop and batch alone, so it is checked before
+    // anything else about the request.
     const size_t need = eval_shadow_scratch_bytes(pop, batch);
     if (need > static_cast<size_t>(LEEA_NOALLOC_SCRATCH_BYTES))
         return fail(LEEA_EINVAL,
                     "pop %d with batch %d needs %zu scratch bytes, above the %d bytes the allocation-free entry "
                     "point holds; use leea_evaluate_shadow_u8 with caller scratch",
                     pop, batch, need, LEEA_NOALLOC_SCRATCH_BYTES);
+    NetLayout net;
+    if (!make_layout(dims, n_dims, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    if ((st = check_shadow_shape(net, precision))) return st;
+    if (!(alpha >= 0.0f && alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
+    if (!pop_dev || !shadow_dev || !x_u8_dev || !y_dev || !f_raw_dev || (precision == 2 && !scale_exp_dev))
+        return fail(LEEA_EINVAL, "NULL device pointer");
+    if ((reinterpret_cast<uintptr_t>(pop_dev) & 15u) || (reinterpret_cast<uintptr_t>(shadow_dev) & 127u) ||
+        (reinterpret_cast<uintptr_t>(x_u8_dev) & 15u))
+        return fail(LEEA_EINVAL, "population, x (16-byte) and shadow (128-byte) must be aligned");
     float* scratch = nullptr;
     if (need > 0) {
         cudaError_t err = cudaSuccess;
@@ -1296,7 +1303,7 @@ leea_status leea_set_sigma(leea_state* s, const float* sigma_host)
     return LEEA_OK;
 }
 
-int64_t leea_state_num_params(const leea_state* s) { return s ? s->net.c : -1; }
+int64_t leea_num_params(const leea_state* s) { return s ? s->net.c : -1; }
 
 leea_status leea_profile_enable(leea_state* s, int32_t enable)
 {

@@ -645,21 +645,28 @@ __global__ void __launch_bounds__(256) stage_levels_kernel(const MlpTcArgs a, co
 }
 
 // Library-owned scratch (weight pieces, marks), grown on demand, for callers
-// that bring none.
+// that bring none: one buffer per device, for the device current at the call
+// (a buffer of another device would be another GPU's memory).
 uint8_t* shared_scratch(size_t bytes)
 {
+    constexpr int kMaxDevices = 64;
     static std::mutex mu;
-    static uint8_t* buf = nullptr;
-    static size_t cap = 0;
+    static uint8_t* buf[kMaxDevices] = { nullptr };
+    static size_t cap[kMaxDevices] = { 0 };
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
     std::lock_guard<std::mutex> lock(mu);
-    if (bytes > cap) {
-        if (buf) cudaFree(buf);
-        buf = nullptr;
-        cap = 0;
-        if (cudaMalloc(&buf, bytes) != cudaSuccess) return nullptr;
-        cap = bytes;
+    if (bytes > cap[dev]) {
+        if (buf[dev]) cudaFree(buf[dev]);  // synchronises the device: earlier calls' kernels are done with it
+        buf[dev] = nullptr;
+        cap[dev] = 0;
+        if (cudaMalloc(&buf[dev], bytes) != cudaSuccess) {
+            buf[dev] = nullptr;
+            return nullptr;
+        }
+        cap[dev] = bytes;
     }
-    return buf;
+    return buf[dev];
 }
 
 // Bytes of one individual's weight pieces; byte offset of each layer's blocks.

@@ -101,7 +101,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     P = ctypes.POINTER
     sig = {
         "leea_default_params": [P(leea_params)],
-        "leea_num_params": ([vp, i32], i64),
+        "leea_layout_num_params": ([vp, i32], i64),
         "leea_padded_params": ([vp, i32], i64),
         "leea_counts": [i32, P(leea_params), P(i32), P(i32), P(i32), P(i32)],
         "leea_init_population": [i32, vp, i32, i32, u64, vp, vp],
@@ -142,7 +142,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_generation_index": ([vp], u32),
         "leea_get_sigma": [vp, vp],
         "leea_set_sigma": [vp, vp],
-        "leea_state_num_params": ([vp], i64),
+        "leea_num_params": ([vp], i64),
         "leea_profile_enable": [vp, i32],
         "leea_profile_read": [vp, vp, vp],
         "leea_multi_create": [i32, vp, i32, i32, P(leea_params), vp, P(vp)],
@@ -210,7 +210,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
 
 def exported_symbols() -> list[str]:
     """Names of the entry points the binding expects the library to export."""
-    return ["leea_default_params", "leea_num_params", "leea_padded_params", "leea_counts",
+    return ["leea_default_params", "leea_layout_num_params", "leea_padded_params", "leea_counts",
             "leea_init_population", "leea_rank", "leea_select", "leea_breed", "leea_breed_evaluate_u8",
             "leea_maxpool2x2", "leea_maxpool2x2_u8",
             "leea_evaluate",
@@ -218,7 +218,7 @@ def exported_symbols() -> list[str]:
             "leea_philox_fill", "leea_normal_fill", "leea_create", "leea_generation",
             "leea_generation_host", "leea_fitness", "leea_raw_fitness", "leea_best_params",
             "leea_get_population", "leea_set_population", "leea_set_fitness", "leea_set_generation",
-            "leea_get_selection", "leea_generation_index", "leea_state_num_params", "leea_get_sigma",
+            "leea_get_selection", "leea_generation_index", "leea_num_params", "leea_get_sigma",
             "leea_set_sigma",
             "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy",
             "leea_shadow_stride", "leea_make_shadow", "leea_shadow_scratch_bytes", "leea_evaluate_shadow_u8",
@@ -278,9 +278,9 @@ def leea_default_params() -> Params:
     return Params(**{f.name: getattr(s, f.name) for f in fields(Params)})
 
 
-def leea_num_params(dims) -> int:
+def leea_layout_num_params(dims) -> int:
     d = _dims(dims)
-    return int(load_library().leea_num_params(_hp(d), len(d)))
+    return int(load_library().leea_layout_num_params(_hp(d), len(d)))
 
 
 def leea_padded_params(dims) -> int:
@@ -430,7 +430,7 @@ class LeeaState:
         _check(self.lib.leea_create(pop, _hp(self.dims), len(self.dims), ctypes.byref(self._cp), seed,
                                     _stream(stream), ctypes.byref(h)))
         self._h = h
-        self.c = int(self.lib.leea_state_num_params(h))
+        self.c = int(self.lib.leea_num_params(h))
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
@@ -455,16 +455,42 @@ class LeeaState:
     def leea_generation_u8(self, x_u8_dev, y_dev, x_div: float = 255.0) -> None:
         _check(self.lib.leea_generation_u8(self._h, _dptr(x_u8_dev), float(x_div), _dptr(y_dev), int(y_dev.shape[0])))
 
+    def _host_batch(self, x_host, y_host, x_dtype: str):
+        """Host pointers and batch size of a host minibatch, after the checks the C call cannot make:
+        C-contiguous CPU buffers of the right dtypes, x holding batch * d_0 elements."""
+        bufs = []
+        for name, arr, want in (("x", x_host, x_dtype), ("y", y_host, "int32")):
+            if hasattr(arr, "data_ptr"):  # torch tensor
+                if arr.is_cuda:
+                    raise ValueError(f"{name} must be a host (CPU) tensor")
+                if str(arr.dtype).replace("torch.", "") != want:
+                    raise ValueError(f"{name} must be {want}, got {arr.dtype}")
+                if not arr.is_contiguous():
+                    raise ValueError(f"{name} must be contiguous")
+                bufs.append((arr.data_ptr(), int(arr.numel()), tuple(arr.shape)))
+            else:
+                a = np.asarray(arr)
+                if a.dtype != np.dtype(want):
+                    raise ValueError(f"{name} must be {want}, got {a.dtype}")
+                if not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError(f"{name} must be C-contiguous")
+                bufs.append((a.ctypes.data, int(a.size), a.shape))
+        (xp, xn, _), (yp, yn, yshape) = bufs
+        if len(yshape) != 1:
+            raise ValueError("y must be one-dimensional (one label per sample)")
+        if xn != yn * self.dims[0]:
+            raise ValueError(f"x holds {xn} elements; batch {yn} x d_0 {self.dims[0]} = {yn * self.dims[0]} expected")
+        return xp, yp, yn
+
     def leea_generation_u8_host(self, x_u8_host, y_host, x_div: float = 255.0) -> None:
-        xp = x_u8_host.data_ptr() if hasattr(x_u8_host, "data_ptr") else x_u8_host.ctypes.data
-        yp = y_host.data_ptr() if hasattr(y_host, "data_ptr") else y_host.ctypes.data
-        _check(self.lib.leea_generation_u8_host(self._h, xp, float(x_div), yp, int(y_host.shape[0])))
+        """x_u8_host uint8[batch][d_0], y_host int32[batch]: CPU torch tensors (ideally pinned) or numpy arrays."""
+        xp, yp, batch = self._host_batch(x_u8_host, y_host, "uint8")
+        _check(self.lib.leea_generation_u8_host(self._h, xp, float(x_div), yp, batch))
 
     def leea_generation_host(self, x_host, y_host) -> None:
-        """x_host / y_host: CPU torch tensors (ideally pinned) or numpy arrays."""
-        xp = x_host.data_ptr() if hasattr(x_host, "data_ptr") else x_host.ctypes.data
-        yp = y_host.data_ptr() if hasattr(y_host, "data_ptr") else y_host.ctypes.data
-        _check(self.lib.leea_generation_host(self._h, xp, yp, int(y_host.shape[0])))
+        """x_host float32[batch][d_0], y_host int32[batch]: CPU torch tensors (ideally pinned) or numpy arrays."""
+        xp, yp, batch = self._host_batch(x_host, y_host, "float32")
+        _check(self.lib.leea_generation_host(self._h, xp, yp, batch))
 
     def leea_fitness(self, with_correct: bool = False):
         f = np.empty(self.pop, dtype=np.float32)
@@ -624,7 +650,7 @@ class MultiRun:
         return slice(int(self.batch_off[run]), int(self.batch_off[run]) + self.specs[run].batch)
 
     def num_params(self, run: int) -> int:
-        return leea_num_params([self.d_in, self.specs[run].hidden, self.d_out])
+        return leea_layout_num_params([self.d_in, self.specs[run].hidden, self.d_out])
 
     def get_population(self, run: int) -> np.ndarray:
         out = np.empty((self.specs[run].pop, self.num_params(run)), dtype=np.float32)
@@ -785,7 +811,7 @@ class SurrState:
                                          ctypes.byref(self._sp), seed, _hp(self.probe), _stream(stream),
                                          ctypes.byref(h)))
         self._h = h
-        self.c = leea_num_params(self.dims)
+        self.c = leea_layout_num_params(self.dims)
         v = [ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()]
         _check(self.lib.leea_surr_layout(h, *[ctypes.byref(x) for x in v]))
         self.n_recipes, self.n_audit, self.width, self.n_theta = (x.value for x in v)

@@ -55,15 +55,15 @@ def test_default_params_are_the_papers(lib, oracle_mod):
 
 @pytest.mark.parametrize("dims", [[784, 112, 10], [784, 32, 10], [2, 2, 2], [196, 256, 128, 64, 10], [3, 1]])
 def test_layout_matches_oracle(lib, oracle_mod, dims):
-    c = leea.leea_num_params(dims)
+    c = leea.leea_layout_num_params(dims)
     assert c == oracle_mod.num_params(dims)
     cp = leea.leea_padded_params(dims)
     assert cp % 32 == 0 and c <= cp < c + 32
 
 
 def test_invalid_dims(lib):
-    assert leea.leea_num_params([784]) == -1
-    assert leea.leea_num_params([784, 0, 10]) == -1
+    assert leea.leea_layout_num_params([784]) == -1
+    assert leea.leea_layout_num_params([784, 0, 10]) == -1
 
 
 def test_counts_match_oracle(lib, oracle_mod):
@@ -148,3 +148,39 @@ def test_header_is_plain_c(tmp_path):
                     str(tmp_path / "c.o")], check=True)
     subprocess.run(["g++", "-std=c++17", "-Wall", "-Wextra", "-Werror", "-I", inc, "-x", "c++", "-c", str(src), "-o",
                     str(tmp_path / "cc.o")], check=True)
+
+
+def test_noalloc_rejects_oversize_before_touching_the_device(lib):
+    # pop x ceil(batch / 128) x 8 bytes above LEEA_NOALLOC_SCRATCH_BYTES: refused
+    # from pop and batch alone, with NULL for every buffer (no CUDA call is made).
+    dims = np.array([784, 32, 10], dtype=np.int32)
+    assert leea.leea_shadow_scratch_bytes(20000, 1024) > leea.NOALLOC_SCRATCH_BYTES
+    rc = lib.leea_evaluate_shadow_u8_noalloc(20000, dims.ctypes.data_as(ctypes.c_void_p), 3, None, 1, None, None,
+                                             None, ctypes.c_float(255.0), None, 1024, ctypes.c_float(1.0), None, None,
+                                             None, None, None)
+    assert rc == leea.EINVAL and b"scratch bytes" in lib.leea_last_error()
+
+
+def test_host_minibatch_checks():
+    # The host-buffer generation calls check what the C call cannot see: dtype,
+    # contiguity and x holding batch * d_0 elements (no object or device needed).
+    st = leea.LeeaState.__new__(leea.LeeaState)
+    st.dims = [784, 32, 10]
+    x = np.zeros((16, 784), dtype=np.uint8)
+    y = np.zeros(16, dtype=np.int32)
+    _, _, batch = st._host_batch(x, y, "uint8")
+    assert batch == 16
+    with pytest.raises(ValueError, match="uint8"):
+        st._host_batch(x.astype(np.float32), y, "uint8")
+    with pytest.raises(ValueError, match="int32"):
+        st._host_batch(x, y.astype(np.int64), "uint8")
+    with pytest.raises(ValueError, match="contiguous"):
+        st._host_batch(np.zeros((16, 1568), dtype=np.uint8)[:, ::2], y, "uint8")
+    with pytest.raises(ValueError, match="expected"):
+        st._host_batch(x[:15], y, "uint8")
+    import torch
+    _, _, batch = st._host_batch(torch.zeros((16, 784), dtype=torch.float32), torch.zeros(16, dtype=torch.int32),
+                                 "float32")
+    assert batch == 16
+    with pytest.raises(ValueError, match="float32"):
+        st._host_batch(torch.zeros((16, 784), dtype=torch.float64), torch.zeros(16, dtype=torch.int32), "float32")

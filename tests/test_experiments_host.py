@@ -1,10 +1,11 @@
 """Host logic of the experiment harness (Section 4's protocol): the settings
 grids carry the paper's stated values, scaling keeps the sample budget's
 shape, and significance is the one-sided Mann-Whitney U test."""
+import itertools
+
 import numpy as np
 import pytest
 
-pytest.importorskip("scipy")
 from paper_1806_09819_gb300 import experiments as E
 
 
@@ -36,3 +37,40 @@ def test_mann_whitney_is_one_sided():
     hi, lo = rng.normal(1.0, 0.1, 15), rng.normal(0.0, 0.1, 15)
     assert E.mann_whitney_greater(hi, lo) < 1e-4
     assert E.mann_whitney_greater(lo, hi) > 0.99
+
+
+def test_mann_whitney_exact_against_enumeration():
+    # no ties, small samples: the exact p-value equals the share of all
+    # C(m + n, m) equally likely rank sets whose U is at least the observed one
+    rng = np.random.default_rng(3)
+    for m, n in ((3, 4), (5, 2), (4, 6), (1, 7)):
+        v = rng.permutation(m + n).astype(float)
+        a, b = v[:m], v[m:]
+        u_obs = sum(float(x > y) for x in a for y in b)
+        us = []
+        for pos in itertools.combinations(range(m + n), m):
+            xs = [float(i) for i in pos]
+            ys = [float(i) for i in range(m + n) if i not in pos]
+            us.append(sum(float(x > y) for x in xs for y in ys))
+        want = np.mean(np.asarray(us) >= u_obs)
+        assert abs(E.mann_whitney_greater(a, b) - want) < 1e-12
+
+
+def test_mann_whitney_null_counts_are_binomial_totals():
+    for m, n in ((1, 1), (3, 5), (8, 8), (15, 15)):
+        c = E._u_null_counts(m, n)
+        assert len(c) == m * n + 1 and c.sum() == float(np.round(np.exp(
+            np.sum(np.log(np.arange(1, m + n + 1))) - np.sum(np.log(np.arange(1, m + 1)))
+            - np.sum(np.log(np.arange(1, n + 1))))))
+        np.testing.assert_array_equal(c, c[::-1])  # U and m n - U are equally likely
+
+
+def test_mann_whitney_matches_scipy_where_available():
+    stats = pytest.importorskip("scipy.stats")
+    rng = np.random.default_rng(11)
+    for m, n, ties in ((15, 15, False), (15, 15, True), (6, 9, False), (20, 7, True)):
+        a, b = rng.normal(0.2, 1.0, m), rng.normal(0.0, 1.0, n)
+        if ties:
+            a, b = np.round(a * 2) / 2, np.round(b * 2) / 2
+        want = stats.mannwhitneyu(a, b, alternative="greater").pvalue
+        assert abs(E.mann_whitney_greater(a, b) - want) < 1e-9, (m, n, ties)

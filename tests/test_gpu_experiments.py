@@ -8,7 +8,6 @@ pytestmark = pytest.mark.gpu
 
 
 def test_harness_runs_and_is_reproducible(gpu):
-    pytest.importorskip("scipy")
     import torch
     from paper_1806_09819_gb300 import experiments as E
     data = E.Data(torch.device("cuda", 0), n_train=4000, n_val=1000)

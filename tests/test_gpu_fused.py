@@ -25,7 +25,7 @@ def _i32(a):
 
 def _fused_vs_separate(gpu, oracle_mod, dims, pop, batch, prm, seed=7, gen=9, scale=0.2, plant=None):
     torch = _torch()
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     parents = synthetic.random_population(pop, c, seed=pop + c + batch, scale=scale)
     if plant is not None:
         plant(parents)
@@ -124,7 +124,7 @@ def test_fused_invalid_parent_gives_nan(gpu):
                                1.0, None, f)
     torch.cuda.synchronize()
     kids = kid_d.cpu().numpy()
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     assert np.isnan(kids[2, :c]).all() and (kids[2, c:] == 0).all()
     fv = f.cpu().numpy()
     assert np.isnan(fv[2]) and np.isfinite(fv[[0, 1, 3]]).all()

@@ -25,8 +25,10 @@ def _dev_batch(x, y):
 
 def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=11, gen0=3, sample=None, u8=False):
     """One generation from a common state; returns nothing, asserts parity.
-    With u8=True the minibatch goes in as 8-bit levels k (x = k / 255)."""
-    c = gpu.leea_num_params(dims)
+    With u8=True the minibatch goes in as 8-bit levels k (x = k / 255).  With
+    a sample, the oracle breeds only the sampled children, but evaluates every
+    child the GPU made (the fitness of the whole population is compared)."""
+    c = gpu.leea_layout_num_params(dims)
     st = gpu.LeeaState(pop, dims, gpu.Params(**prm), seed)
     pop0 = synthetic.random_population(pop, c, seed=seed + 1, scale=0.1)
     f0 = np.random.default_rng(seed).normal(-2.3, 0.05, size=pop).astype(np.float32)
@@ -65,12 +67,12 @@ def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=11, gen0=3, sample=No
     for j in rows:
         ref = oracle_mod.breed(o_prm, dims, seed, gen0 + 1, pop0d, o1, o2, ok, j0=int(j), j1=int(j) + 1)
         assert_genes_close(kids[j][None], ref, o_prm.sigma, what=f"child {j}")
-    f_ref, cor_ref, logits = oracle_mod.evaluate(kids[rows].astype(np.float64), dims, x.astype(np.float64), y,
+    f_ref, cor_ref, logits = oracle_mod.evaluate(kids.astype(np.float64), dims, x.astype(np.float64), y,
                                                  want_logits=True)
-    assert_fitness_close(f_raw[rows], f_ref)
-    assert_correct_close(cor[rows], cor_ref, logits)
-    adj = oracle_mod.inherit(float(np.float32(o_prm.alpha)), ofi[rows], f_ref, first=False)
-    assert_fitness_close(f_adj[rows], adj, "f_adj")
+    assert_fitness_close(f_raw, f_ref)
+    assert_correct_close(cor, cor_ref, logits)
+    adj = oracle_mod.inherit(float(np.float32(o_prm.alpha)), ofi, f_ref, first=False)
+    assert_fitness_close(f_adj, adj, "f_adj")
     st.close()
 
 

@@ -47,7 +47,7 @@ def test_normals_match(gpu, oracle_mod):
 def test_init_matches_oracle(gpu, oracle_mod, dims, init):
     torch = _torch()
     pop = 3
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     t = torch.full((pop, cp), 7.0, dtype=torch.float32, device="cuda")
     gpu.leea_init_population(pop, dims, init, 2024, t)
     torch.cuda.synchronize()
@@ -126,7 +126,7 @@ BREED_CASES = [
 def test_breed_matches_oracle(gpu, oracle_mod, case):
     torch = _torch()
     dims, pop = case["dims"], case["pop"]
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     parents = synthetic.random_population(pop, c, seed=pop + c, scale=0.2)
     f = np.random.default_rng(1).normal(-2.0, 0.2, size=pop)
     o_prm = oracle_mod.Params(**case["prm"])
@@ -194,7 +194,7 @@ def _eval_params():
 @pytest.mark.parametrize("dims,pop,batch,path", _eval_params())
 def test_evaluate_matches_oracle(gpu, oracle_mod, dims, pop, batch, path):
     torch = _torch()
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     popv = synthetic.random_population(pop, c, seed=c + batch, scale=0.15)
     if dims[0] == 784:
         x, y = synthetic.make_split(batch, seed=batch)
@@ -240,7 +240,7 @@ def test_tensor_path_rejects_unsupported_shapes(gpu):
 def test_evaluate_zero_weights_and_clones(gpu, oracle_mod, path):
     torch = _torch()
     dims, pop, batch = [784, 112, 10], 6, 100
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     x, y = synthetic.make_split(batch, seed=4)
     popv = np.zeros((pop, c), dtype=np.float32)
     popv[3:] = synthetic.random_population(1, c, seed=5)  # three identical clones
@@ -259,7 +259,7 @@ def test_evaluate_zero_weights_and_clones(gpu, oracle_mod, path):
 def test_tensor_and_simt_paths_agree_at_full_size(gpu):
     torch = _torch()
     dims, pop, batch = [784, 112, 10], 1000, 100
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     pd = torch.empty((pop, cp), dtype=torch.float32, device="cuda")
     gpu.leea_init_population(pop, dims, 0, 99, pd)
     x, y = synthetic.make_split(batch, seed=8)
@@ -316,7 +316,7 @@ def _u8_params():
 @pytest.mark.parametrize("dims,pop,batch,path", _u8_params())
 def test_evaluate_u8_matches_oracle(gpu, oracle_mod, dims, pop, batch, path):
     torch = _torch()
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     popv = synthetic.random_population(pop, c, seed=c + 7 * batch, scale=0.15)
     rng = np.random.default_rng(batch)
     levels = rng.integers(0, 256, size=(batch, dims[0])).astype(np.uint8)
@@ -355,7 +355,7 @@ def test_evaluate_u8_tensor_rejects_large_batches(gpu):
 def test_evaluate_u8_clones_and_zero_weights(gpu):
     torch = _torch()
     dims, pop, batch = [784, 112, 10], 7, 100
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     x, y = synthetic.make_split(batch, seed=4)
     popv = np.zeros((pop, c), dtype=np.float32)
     popv[3:] = synthetic.random_population(1, c, seed=5)
@@ -378,7 +378,7 @@ def test_evaluate_u8_tensor_weights_outside_the_piece_range(gpu, oracle_mod):
     # 127.5 (just inside the range), stay on the tensor path.
     torch = _torch()
     dims, pop, batch = [784, 112, 10], 400, 100
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     popv = synthetic.random_population(pop, c, seed=21, scale=0.05)
     for p_, w_ in ((3, 300.0), (155, -128.0), (307, 1.0e6), (160, 200.0), (9, 127.5), (161, -127.5)):
         popv[p_, (p_ * 37) % (dims[0] * dims[1])] = w_

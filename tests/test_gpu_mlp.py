@@ -58,7 +58,7 @@ MLP_CASES = [
 @pytest.mark.parametrize("dims,pop,batch,inp", MLP_CASES, ids=lambda v: str(v))
 def test_mlp_evaluate_matches_oracle(gpu, oracle_mod, dims, pop, batch, inp):
     torch = _torch()
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     popv = synthetic.random_population(pop, c, seed=c + batch, scale=0.15)
     popv[pop - 1] = popv[0]  # identical individuals: identical results
     rng = np.random.default_rng(batch)
@@ -117,7 +117,7 @@ TC_CASES = [(PAPER_DIMS, 6, 1024), (PAPER_DIMS, 5, 129), (PAPER_DIMS, 3, 1), (PA
 def test_mlp_tensor_cores_match_oracle(gpu, oracle_mod, dims, pop, batch):
     # Three hidden layers on tcgen05 (FP16 operand pieces, FP32 accumulation):
     # within the evaluation tolerance of the FP64 oracle, like the FP32 kernel.
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     popv = synthetic.random_population(pop, c, seed=c + batch + 1, scale=0.12)
     rng = np.random.default_rng(batch + 5)
     levels = rng.integers(0, 256, size=(batch, dims[0])).astype(np.uint8)
@@ -137,7 +137,7 @@ def test_mlp_tensor_cores_fall_back_outside_the_piece_range(gpu, oracle_mod):
     # A weight of 200 in W2, and an individual whose layer-1 activations exceed
     # 128: both are recomputed in FP32; the others stay on the tensor cores.
     dims = PAPER_DIMS
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     popv = synthetic.random_population(6, c, seed=3, scale=0.1)
     w2 = 196 * 256 + 256
     popv[1, w2 + 77] = 200.0
@@ -182,7 +182,7 @@ def _paper_lockstep(gpu, oracle_mod, pop, batch, seed=13, gen0=5, sample=None):
     tolerance."""
     torch = _torch()
     dims = PAPER_DIMS
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     st = gpu.LeeaState(pop, dims, gpu.Params(**PAPER_PRM), seed)
     try:
         pop0 = synthetic.random_population(pop, c, seed=seed + 1, scale=0.08)

@@ -104,7 +104,7 @@ def test_multi_generation_matches_oracle(gpu, oracle_mod, precision):
         parents, n_w1 = [], []
         for r, sp in enumerate(specs):
             dims = [D_IN, sp.hidden, D_OUT]
-            popv = synthetic.random_population(sp.pop, gpu.leea_num_params(dims), seed=30 + r, scale=0.1)
+            popv = synthetic.random_population(sp.pop, gpu.leea_layout_num_params(dims), seed=30 + r, scale=0.1)
             m.set_population(r, popv)
             parents.append(popv)
             n_w1.append(D_IN * sp.hidden)

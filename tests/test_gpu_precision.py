@@ -113,7 +113,7 @@ SHADOW_CASES = [
 @pytest.mark.parametrize("dims,pop,batch", SHADOW_CASES)
 def test_evaluate_shadow_matches_oracle(gpu, oracle_mod, dims, pop, batch, precision):
     torch = _torch()
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     popv = synthetic.random_population(pop, c, seed=c + batch, scale=0.15)
     rng = np.random.default_rng(batch + 1000 * precision)
     levels = rng.integers(0, 256, size=(batch, dims[0])).astype(np.uint8)
@@ -150,7 +150,7 @@ def test_evaluate_shadow_argument_errors(gpu):
     torch = _torch()
     dims = [784, 32, 10]
     pop, batch = 4, 200
-    popv = synthetic.random_population(pop, gpu.leea_num_params(dims), seed=1)
+    popv = synthetic.random_population(pop, gpu.leea_layout_num_params(dims), seed=1)
     pd, sh, se, _ = _make_shadow(gpu, popv, dims, 1)
     x = torch.zeros((batch, 784), dtype=torch.uint8, device="cuda")
     y = torch.zeros(batch, dtype=torch.int32, device="cuda")
@@ -189,7 +189,7 @@ def _bound_exp(oracle_mod, kind, par1, par2, amax_par, sigma):
 def _state_generation(gpu, oracle_mod, precision, dims, pop, batch, sigma, gens=2, sample=None):
     torch = _torch()
     prm = gpu.Params(sigma=sigma, mut_rate=0.1, n_elite=2, p_c=0.5, precision=precision, alpha=0.5)
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     n = _n_w1(dims)
     st = gpu.LeeaState(pop, dims, prm, seed=77)
     try:
@@ -279,7 +279,7 @@ def test_rank_agreement_reported(gpu, oracle_mod, precision, capsys):
     # FP64 evaluation of the master (Spearman and top-10% overlap).
     torch = _torch()
     dims, pop, batch = [784, 112, 10], 128, 256
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     popv = synthetic.random_population(pop, c, seed=21, scale=0.05)
     x, y = synthetic.make_split(batch, seed=4)
     levels = synthetic.to_levels(x)

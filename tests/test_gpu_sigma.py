@@ -23,7 +23,7 @@ def _dev(a):
 
 
 def _lockstep(gpu, oracle_mod, dims, pop, batch, prm, seed=21, gen0=40, sample=None, precision=0):
-    c = gpu.leea_num_params(dims)
+    c = gpu.leea_layout_num_params(dims)
     st = gpu.LeeaState(pop, dims, gpu.Params(**prm, precision=precision), seed)
     try:
         rng = np.random.default_rng(seed)

@@ -140,7 +140,7 @@ def test_breed_entities_matches_oracle(gpu, oracle_mod):
     dims = [64, 32, 10]
     pop, mult = 24, 2
     f, order, (p1, p2, kind, f_inh, ent) = _recipes(gpu, oracle_mod, pop, mult)
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     parents = np.random.default_rng(4).normal(0, 0.3, size=(pop, c)).astype(np.float32)
     n = kind.numel()
     kids = torch.zeros((n, cp), dtype=torch.float32, device="cuda")
@@ -175,7 +175,7 @@ def test_descriptors_match_oracle(gpu, oracle_mod, dims, n_probe, xo_op, precisi
     inh_h = np.concatenate([f_inh.cpu().numpy(), f[[3, 5]]]).astype(np.float32)
     ent_h = np.concatenate([ent.cpu().numpy().view(np.uint32), [11, 12]]).astype(np.uint32)
     n = kind_h.size
-    c, cp = gpu.leea_num_params(dims), gpu.leea_padded_params(dims)
+    c, cp = gpu.leea_layout_num_params(dims), gpu.leea_padded_params(dims)
     parents = np.random.default_rng(dims[1]).normal(0, 0.1, size=(pop, c)).astype(np.float32)
     probe = (np.random.default_rng(5).integers(0, 256, size=(n_probe, dims[0])) / 255.0).astype(np.float32)
     desc = torch.empty((n, 5 + n_probe * dims[-1]), dtype=torch.float32, device="cuda")
