@@ -173,13 +173,14 @@ def max_over_ranks(value: float, dist, device=None) -> float:
 PROFILE_EVERY = 8  # generations per profiled one inside the timed region
 
 
-def kernels_per_generation(pop: int, batch: int, precision: int, fused: bool = False) -> dict:
+def kernels_per_generation(pop: int, batch: int, precision: int, fused: bool = False, x16: bool = False) -> dict:
     """Kernel launches per stage of one state-object generation: ranking and
-    selection run as one kernel below 512 nets and as two above; breeding and
-    evaluation are one fused kernel on the 8-bit FP32 path, else two; the shadow
-    evaluation adds a combining kernel when the batch spans several 128-sample
-    tiles."""
-    sel = 2 if pop >= 512 else 1
+    selection run as one kernel below 512 nets and as two above (plus the
+    kernel that stages the batch as FP16 for the FP32 tensor-core evaluation
+    of 8-bit inputs, x16); breeding and evaluation are one fused kernel on the
+    8-bit FP32 path, else two; the shadow evaluation adds a combining kernel
+    when the batch spans several 128-sample tiles."""
+    sel = (2 if pop >= 512 else 1) + (1 if x16 else 0)
     if fused:
         return {"select": sel, "breed_evaluate": 1}
     return {"select": sel, "breed": 1, "evaluate": 1 + (1 if precision > 0 and batch > 128 else 0)}
@@ -681,7 +682,7 @@ def run_small(args, rank: int, world: int, local_rank: int):
     hbm_peak, _, peak_src = _peaks()
     n_e, n_c, n_m, _ = leea.leea_counts(pop, leea.Params(**PARAMS))
     c = leea.leea_layout_num_params(dims)
-    gen_bytes = 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + 4.0 * c * pop  # breed, then the evaluation's weights
+    gen_bytes = 8.0 * c * (n_e + n_c + n_m) + 4.0 * c * pop  # breed (one read, one write per gene), evaluation
     us = ms_max * 1000.0 / steps
     roofline = {"kernel": "generation", "bound": "hbm", "achieved": gen_bytes / (us * 1e-6) / 1e9,
                 "peak": hbm_peak, "unit": "GB/s", "frac": gen_bytes / (us * 1e-6) / 1e9 / hbm_peak,
@@ -696,7 +697,8 @@ def run_small(args, rank: int, world: int, local_rank: int):
                        "input": "uint8 levels k, x = k/255",
                        "l2": "flushed between timed generations"},
             "network_samples_per_sec": gen_per_s * pop * batch, "e2e": e2e,
-            "gpu_launches": int(steps * sum(kernels_per_generation(pop, batch, 0).values())),
+            "gpu_launches": int(steps * sum(kernels_per_generation(
+                pop, batch, 0, x16=args.eval_path in (0, 2)).values())),
             "roofline": roofline, "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x64 = xtr[idx[warmup + steps]].astype(np.float64) / 255.0
@@ -1097,8 +1099,9 @@ def run_native(args, rank: int, world: int, local_rank: int):
         workload = f"PROFILING OVERRIDE P={pop}, batch {batch} (not the benchmark workload): " + workload
     eval_kernel = ("tcgen05 " + {1: "kind::f16 on BF16 shadows", 2: "kind::f8f6f4 on FP8 shadows, 2 input pieces"}[
         precision] + ", batch in TMEM" if precision else
-                   (("tcgen05 FP16 two-piece weights, batch in TMEM" if u8 else "tcgen05 3xTF32") if tensor_eval
-                    else "CUDA-core FP32 FFMA"))
+                   (("tcgen05 kind::f16, two individuals per MMA (N = 2h), W1 as two FP16 pieces of 2^8 w "
+                     "(22-bit significands, exact products, FP32 accumulation)" if u8 else "tcgen05 3xTF32")
+                    if tensor_eval else "CUDA-core FP32 FFMA"))
     if fused:
         eval_kernel = "fused breed + evaluate (children made in shared memory, written once, fed to " + eval_kernel + ")"
     pop_mb = pop * leea.leea_padded_params(DIMS) * 4 / 1e6
@@ -1114,7 +1117,8 @@ def run_native(args, rank: int, world: int, local_rank: int):
                        "l2": f"inputs larger than L2 (2 population buffers of {pop_mb:.0f} MB), no flush"},
             "network_samples_per_sec": gen_per_s * pop * batch,
             "e2e": e2e,
-            "gpu_launches": int(steps * sum(kernels_per_generation(pop, batch, precision, fused).values())),
+            "gpu_launches": int(steps * sum(kernels_per_generation(
+                pop, batch, precision, fused, x16=u8 and tensor_eval and precision == 0 and not fused).values())),
             "roofline": roofline,
             "kernels": kernels, "clocks": clk}
     if precision and rank == 0:

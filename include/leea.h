@@ -296,15 +296,16 @@ leea_status leea_evaluate(int32_t pop, const int32_t* dims, int32_t n_dims,
 /* leea_evaluate for minibatches of 8-bit levels: x_u8_dev is uint8[batch][d_0]
  * and the input value is x = k / x_div (x_div = 255 for images stored as
  * bytes, as MNIST's are).  The tensor-core path needs batch <= 128,
- * d_0 % 4 == 0, h % 16 == 0, h <= 128, h + round_up(8 ceil(d_0 / 16), 16) <= 512
- * and d_out <= 16.  It forms layer 1 from exact products: the levels are exact
- * in FP16 and each weight, scaled by 2^8, is split into two FP16 pieces
- * (|2^8 w - w1 - w2| <= max(2^-22 2^8 |w|, 2^-25), a 22-bit significand),
- * so besides that split only the tensor core's FP32 accumulation rounds; an
- * individual with a weight |w| >= 128 gets its layer 1 in FP32 FFMA
- * instead.  Otherwise, or with
- * LEEA_EVAL_SIMT, the CUDA-core kernel computes x = k / x_div in FP32.
- * x_div must be finite and > 0. */
+ * d_0 % 4 == 0, h % 16 == 0, h <= 128 and d_out <= 16.  It forms layer 1 from
+ * exact products: the levels are exact in FP16 and each weight, scaled by
+ * 2^8, is split into two FP16 pieces (|2^8 w - w1 - w2| <= max(2^-22 2^8 |w|,
+ * 2^-25), a 22-bit significand), so besides that split only the tensor
+ * core's FP32 accumulation rounds; an individual with a weight |w| >= 128
+ * gets its layer 1 in FP32 FFMA instead.  That path first writes the batch
+ * as FP16 into a stream-ordered allocation of batch * round_up(d_0, 8) * 2
+ * bytes (cudaMallocAsync on `stream`, freed after the evaluation).
+ * Otherwise, or with LEEA_EVAL_SIMT, the CUDA-core kernel computes
+ * x = k / x_div in FP32.  x_div must be finite and > 0. */
 leea_status leea_evaluate_u8(int32_t pop, const int32_t* dims, int32_t n_dims,
                              const float* pop_dev, const uint8_t* x_u8_dev, float x_div,
                              const int32_t* y_dev, int32_t batch, float alpha,

@@ -35,10 +35,12 @@ leea_status check_shadow_shape(const NetLayout& net, int32_t precision);
 // The evaluation kernel `path` selects (LEEA_EVAL_*) for 8-bit inputs x = k / x_div;
 // mlp_scratch: the caller's scratch of the tensor-core evaluation of deeper nets
 // (eval_mlp_tc_scratch_bytes), or NULL for the library's shared buffer.
+// x16: the caller's buffer for the batch as FP16 (eval_u8_x16_bytes), already
+// filled when x16_staged; NULL takes a stream-ordered allocation for the call.
 leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
                              const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
                              float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream,
-                             void* mlp_scratch = nullptr);
+                             void* mlp_scratch = nullptr, void* x16 = nullptr, bool x16_staged = false);
 // The precision form's evaluation on W1 shadows (scratch: batch > 128).
 leea_status dispatch_eval_shadow(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
                                  const uint8_t* shadow, const int32_t* scale_exp, const uint8_t* x, float x_div,

@@ -5,14 +5,18 @@
 // (crossover) parent floats and writes one child float.  To keep HBM busy
 // while the generator arithmetic runs, the kernel is persistent (one CTA per
 // SM) and decoupled:
-//   warp 0 (one thread)  streams parent chunks (4096 genes = 16 KB per parent)
-//                        into a ring of shared-memory stages with
-//                        cp.async.bulk, tracked by transaction-count mbarriers;
-//   warps 1-16           take a stage, compute the child chunk and write it
+//   warp 0               streams parent chunks (6144 genes = 24 KB per parent
+//                        for one run, 4096 for many) into a ring of
+//                        shared-memory stages with cp.async.bulk, tracked by
+//                        transaction-count mbarriers;
+//   warps 1-24 (1-16)    take a stage, compute the child chunk and write it
 //                        with 128-bit stores, then release the stage.
 // Work items walk the children alternately from the front (elites, crossover
 // children) and the back (mutation children), so every SM mixes the
-// HBM-heavier crossover items with the arithmetic-heavier mutation items.
+// HBM-heavier crossover items with the arithmetic-heavier mutation items;
+// with one run they go chunk by chunk over all children, so that parents
+// shared by several children are read from HBM about once.  The producer
+// warp resolves 32 items' children and parents at a time.
 // With many runs each CTA takes a contiguous range of items, so that it
 // meets few run boundaries (each one reloads the run's arguments).
 // A consumer thread owns 8 consecutive genes of the chunk: one Philox block
@@ -35,11 +39,18 @@ namespace leea {
 
 namespace {
 
-constexpr int kConsumerWarps = 16;
-constexpr int kBreedThreads = 32 * (1 + kConsumerWarps);
-constexpr int kChunk = 4096;                // genes per work item
-constexpr int kStages = 6;                  // ring depth (2 x 16 KB per stage)
-constexpr uint32_t kChunkBytes = kChunk * 4;
+// Shape of the kernel: one run takes 24 consumer warps (about six per
+// scheduler, to hide the Philox and Box-Muller dependency chains) over
+// 6144-gene chunks in a 4-deep ring; many runs keep 16 warps over 4096-gene
+// chunks in a 6-deep ring (their per-run state needs more registers).
+template <bool MULTI>
+struct BreedShape {
+    static constexpr int kConsumerWarps = MULTI ? 16 : 24;
+    static constexpr int kThreads = 32 * (1 + kConsumerWarps);
+    static constexpr int kChunk = 8 * 32 * kConsumerWarps;  // genes per work item: 8 per consumer thread
+    static constexpr int kStages = MULTI ? 6 : 4;           // ring depth (2 parent chunks per stage)
+    static constexpr uint32_t kChunkBytes = kChunk * 4;
+};
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr uint64_t kDrainLimitNs = 200000000ull;
 constexpr int32_t kKindInvalid = -1;
@@ -57,24 +68,38 @@ struct StageMeta {
 
 constexpr int kJobSlots = 4 * 32;  // Box-Muller pairs of a warp's 32 units
 
+// An item's source as the producer warp resolves it, 32 items at a time.
+struct ItemSrc {
+    const float* p1;  // parent chunks (NULL for an invalid parent index)
+    const float* p2;
+    StageMeta m;
+};
+
 struct BreedSmem {
     uint8_t* base;   // stage i: parent 1 at base + 2i chunks, parent 2 at base + (2i+1) chunks
     StageMeta* meta;
-    float2* job_z;      // [kConsumerWarps][kJobSlots]: normals of a warp's job list
-    uint8_t* job_code;  // [kConsumerWarps][kJobSlots]: owner lane << 2 | pair slot
+    ItemSrc* batch;  // [32]: the producer warp's next 32 items
+    float2* job_z;      // [consumer warps][kJobSlots]: normals of a warp's job list
+    uint8_t* job_code;  // [consumer warps][kJobSlots]: owner lane << 2 | pair slot
     uint64_t* full;
     uint64_t* empty;
     volatile int* abort_flag;
 };
 
+template <bool MULTI>
 __device__ __forceinline__ BreedSmem carve(uint8_t* raw)
 {
+    using S = BreedShape<MULTI>;
+    constexpr int kStages = S::kStages, kConsumerWarps = S::kConsumerWarps;
+    constexpr uint32_t kChunkBytes = S::kChunkBytes;
     BreedSmem s;
     uint8_t* base = raw + ((128u - (ptx::smem_u32(raw) & 127u)) & 127u);
     s.base = base;
     uint8_t* p = base + 2 * kStages * kChunkBytes;
     s.meta = reinterpret_cast<StageMeta*>(p);
     p += sizeof(StageMeta) * kStages;
+    s.batch = reinterpret_cast<ItemSrc*>(p);
+    p += sizeof(ItemSrc) * 32;
     s.job_z = reinterpret_cast<float2*>(p);
     p += sizeof(float2) * kConsumerWarps * kJobSlots;
     s.job_code = p;
@@ -85,8 +110,15 @@ __device__ __forceinline__ BreedSmem carve(uint8_t* raw)
     return s;
 }
 
-constexpr size_t kBreedSmemBytes = 128 + 2 * kStages * kChunkBytes + sizeof(StageMeta) * kStages +
-                                   (sizeof(float2) + 1) * kConsumerWarps * kJobSlots + 16 * kStages + 16;
+template <bool MULTI>
+constexpr size_t breed_smem_bytes()
+{
+    using S = BreedShape<MULTI>;
+    return 128 + 2 * S::kStages * S::kChunkBytes + sizeof(StageMeta) * S::kStages + sizeof(ItemSrc) * 32 +
+           (sizeof(float2) + 1) * S::kConsumerWarps * kJobSlots + 16 * S::kStages + 16;
+}
+static_assert(breed_smem_bytes<false>() <= 227 * 1024 && breed_smem_bytes<true>() <= 227 * 1024,
+              "breed ring must fit in shared memory");
 
 // The shadow of 8 child genes i0 .. i0+7 of W1: 8 BF16 (16 bytes) or 8 FP8-e4m3
 // of w / 2^sexp with saturation (8 bytes).  Returns max |w| of the 8 genes.
@@ -131,14 +163,14 @@ __device__ __forceinline__ float write_shadow8(const BreedArgs& a, int32_t j, in
     return mx;
 }
 
-__device__ __forceinline__ float* stage_a(const BreedSmem& s, uint32_t stage)
+__device__ __forceinline__ float* stage_a(const BreedSmem& s, uint32_t stage, uint32_t chunk_bytes)
 {
-    return reinterpret_cast<float*>(s.base + (2u * stage) * kChunkBytes);
+    return reinterpret_cast<float*>(s.base + (2u * stage) * chunk_bytes);
 }
 
-__device__ __forceinline__ float* stage_b(const BreedSmem& s, uint32_t stage)
+__device__ __forceinline__ float* stage_b(const BreedSmem& s, uint32_t stage, uint32_t chunk_bytes)
 {
-    return reinterpret_cast<float*>(s.base + (2u * stage + 1u) * kChunkBytes);
+    return reinterpret_cast<float*>(s.base + (2u * stage + 1u) * chunk_bytes);
 }
 
 __device__ __forceinline__ void raise_abort(volatile int* abort_flag, unsigned int* status)
@@ -148,7 +180,9 @@ __device__ __forceinline__ void raise_abort(volatile int* abort_flag, unsigned i
 }
 
 constexpr int kGenesPerLane = 8;  // one Philox block of 16-bit mask draws per lane and chunk
-static_assert(kChunk == kGenesPerLane * 32 * kConsumerWarps, "consumers must tile a chunk exactly");
+static_assert(BreedShape<false>::kChunk == kGenesPerLane * 32 * BreedShape<false>::kConsumerWarps &&
+                  BreedShape<true>::kChunk == kGenesPerLane * 32 * BreedShape<true>::kConsumerWarps,
+              "consumers must tile a chunk exactly");
 
 // Zero the padding genes (>= c) among genes i0 .. i0+3.
 __device__ __forceinline__ float4 clear_padding(float4 v, int64_t i0, int64_t c)
@@ -176,14 +210,17 @@ __device__ __forceinline__ int32_t run_of_item(const BreedRun* runs, int32_t n_r
 // runs of a device table, whose work items are numbered consecutively, and
 // the generation read from gen_dev.
 template <bool MULTI>
-__global__ void __launch_bounds__(kBreedThreads, 1)
+__global__ void __launch_bounds__(BreedShape<MULTI>::kThreads, 1)
 breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__ runs, int32_t n_runs,
              int64_t n_items, const uint32_t* __restrict__ gen_dev, unsigned int* __restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
     ptx::grid_dep_launch();  // the evaluation that follows may stage its batch meanwhile
     ptx::grid_dep_wait();    // the selection comes from the previous kernel
-    const BreedSmem s = carve(smem_raw);
+    using S = BreedShape<MULTI>;
+    constexpr int kStages = S::kStages, kConsumerWarps = S::kConsumerWarps, kChunk = S::kChunk;
+    constexpr uint32_t kChunkBytes = S::kChunkBytes;
+    const BreedSmem s = carve<MULTI>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // Items of this CTA: many runs, a contiguous range; one run, every gridDim.x-th
     // (neighbouring CTAs then work on neighbouring children, which share parents in L2).
@@ -202,61 +239,89 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
-        if (lane == 0) {
-            uint32_t stage = 0, phase = 0;
-            uint32_t issued_mask = 0, parity_mask = 0;  // per stage: issued at all / parity of the last issue
-            int32_t cur_j = -1, cur_run = -1, cur_kind = 0, cur_p1 = 0, cur_p2 = 0, cur_sexp = 0;
-            float cur_sigma = 0.0f;
-            bool ok = true;
-            for (int64_t it = it_begin; it < it_end; it += it_step) {
-                if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
-                    raise_abort(s.abort_flag, status);
-                    ok = false;
-                    break;
-                }
-                const int32_t ri = MULTI ? run_of_item(runs, n_runs, it) : 0;
-                const BreedRun& R = MULTI ? runs[ri] : run0;
-                const BreedArgs& a = R.a;
-                const int64_t li = it - R.item0;
-                const int32_t ci = static_cast<int32_t>(li / R.chunks);
-                const int32_t ck = static_cast<int32_t>(li - static_cast<int64_t>(ci) * R.chunks);
-                const int32_t j = (ci & 1) ? a.pop - 1 - (ci >> 1) : (ci >> 1);
-                if (j != cur_j || ri != cur_run) {
-                    cur_j = j;
-                    cur_run = ri;
-                    cur_kind = R.kind[j];
-                    cur_p1 = R.par1[j];
-                    cur_p2 = R.par2[j];
-                    cur_sexp = (a.precision == 2) ? a.scale_exp[j] : 0;
-                    cur_sigma = a.sigma_child ? a.sigma_child[j] : a.sigma;
+        // The warp resolves 32 items at a time (lane l: the item's child,
+        // kind, parents, scale and sigma; loads of all lanes in flight
+        // together), then lane 0 streams their parent chunks into the ring.
+        uint32_t stage = 0, phase = 0;
+        uint32_t issued_mask = 0, parity_mask = 0;  // per stage: issued at all / parity of the last issue
+        bool ok = true;
+        for (int64_t base = it_begin; ok && base < it_end; base += 32 * it_step) {
+            {
+                const int64_t it = base + lane * it_step;
+                ItemSrc src{};
+                src.m.kind = kKindInvalid;
+                src.m.len = 0;
+                if (it < it_end) {
+                    const int32_t ri = MULTI ? run_of_item(runs, n_runs, it) : 0;
+                    const BreedRun& R = MULTI ? runs[ri] : run0;
+                    const BreedArgs& a = R.a;
+                    const int64_t li = it - R.item0;
+                    // One run: chunk-major (all children's chunk 0, then chunk
+                    // 1, ...), so the parents' chunk (pool x 16 KB) stays in L2
+                    // while every child that reads it is made: each parent
+                    // chunk comes from HBM about once however many children
+                    // share it.  Many runs: child-major within each CTA's
+                    // contiguous range.
+                    const int32_t ci = MULTI ? static_cast<int32_t>(li / R.chunks) : static_cast<int32_t>(li % a.pop);
+                    const int32_t ck = MULTI ? static_cast<int32_t>(li - static_cast<int64_t>(ci) * R.chunks)
+                                             : static_cast<int32_t>(li / a.pop);
+                    // Front (elites, crossover) and back (mutation) children
+                    // alternate along a CTA's items; with an even grid a CTA's
+                    // ci keep one parity, so alternate rounds swap ci with its
+                    // pair partner (a bijection on each chunk's children).
+                    int32_t x = ci;
+                    if (!MULTI && (gridDim.x & 1u) == 0u) {
+                        const int32_t y = ci ^ static_cast<int32_t>((static_cast<uint32_t>(ci) / gridDim.x) & 1u);
+                        if (y < a.pop) x = y;
+                    }
+                    const int32_t j = (x & 1) ? a.pop - 1 - (x >> 1) : (x >> 1);
+                    int32_t kind = R.kind[j];
+                    const int32_t p1 = R.par1[j], p2 = R.par2[j];
                     const int32_t n_par = a.n_parents > 0 ? a.n_parents : a.pop;
-                    if (cur_p1 < 0 || cur_p1 >= n_par || cur_p2 < 0 || cur_p2 >= n_par) cur_kind = kKindInvalid;
+                    if (p1 < 0 || p1 >= n_par || p2 < 0 || p2 >= n_par) kind = kKindInvalid;
+                    const int64_t g0 = static_cast<int64_t>(ck) * kChunk;
+                    const int32_t len = static_cast<int32_t>(a.c_pad - g0 < kChunk ? a.c_pad - g0 : kChunk);
+                    src.m = StageMeta{ j, kind, static_cast<int32_t>(g0), len,
+                                       (a.precision == 2) ? a.scale_exp[j] : 0, ri,
+                                       a.sigma_child ? a.sigma_child[j] : a.sigma, 0 };
+                    if (kind != kKindInvalid) {
+                        src.p1 = R.parents + static_cast<int64_t>(p1) * a.c_pad + g0;
+                        src.p2 = R.parents + static_cast<int64_t>(p2) * a.c_pad + g0;
+                    }
                 }
-                const int64_t g0 = static_cast<int64_t>(ck) * kChunk;
-                const int32_t len = static_cast<int32_t>(a.c_pad - g0 < kChunk ? a.c_pad - g0 : kChunk);
-                s.meta[stage] = StageMeta{ j, cur_kind, static_cast<int32_t>(g0), len, cur_sexp, ri, cur_sigma, 0 };
-                const uint32_t bytes = static_cast<uint32_t>(len) * 4u;
-                if (cur_kind == kKindInvalid) {
-                    ptx::mbar_arrive(&s.full[stage]);
-                } else {
-                    const bool two = (cur_kind == 1);
-                    ptx::mbar_arrive_expect_tx(&s.full[stage], two ? 2u * bytes : bytes);
-                    ptx::bulk_load(stage_a(s, stage), R.parents + static_cast<int64_t>(cur_p1) * a.c_pad + g0, bytes,
-                                   &s.full[stage]);
-                    if (two)
-                        ptx::bulk_load(stage_b(s, stage), R.parents + static_cast<int64_t>(cur_p2) * a.c_pad + g0, bytes,
-                                       &s.full[stage]);
+                s.batch[lane] = src;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                for (int l = 0; l < 32 && base + l * it_step < it_end; ++l) {
+                    if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
+                        raise_abort(s.abort_flag, status);
+                        ok = false;
+                        break;
+                    }
+                    const ItemSrc src = s.batch[l];
+                    s.meta[stage] = src.m;
+                    const uint32_t bytes = static_cast<uint32_t>(src.m.len) * 4u;
+                    if (src.m.kind == kKindInvalid) {
+                        ptx::mbar_arrive(&s.full[stage]);
+                    } else {
+                        const bool two = (src.m.kind == 1);
+                        ptx::mbar_arrive_expect_tx(&s.full[stage], two ? 2u * bytes : bytes);
+                        ptx::bulk_load(stage_a(s, stage, kChunkBytes), src.p1, bytes, &s.full[stage]);
+                        if (two) ptx::bulk_load(stage_b(s, stage, kChunkBytes), src.p2, bytes, &s.full[stage]);
+                    }
+                    issued_mask |= 1u << stage;
+                    parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
+                    if (++stage == kStages) { stage = 0; phase ^= 1u; }
                 }
-                issued_mask |= 1u << stage;
-                parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
-                if (++stage == kStages) { stage = 0; phase ^= 1u; }
             }
-            if (!ok) {  // let copies in flight land before the CTA exits
-                volatile int never = 0;
-                for (int i = 0; i < kStages; ++i)
-                    if (issued_mask & (1u << i))
-                        ptx::mbar_wait_bounded(&s.full[i], (parity_mask >> i) & 1u, &never, kDrainLimitNs);
-            }
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);  // also: lane 0 is done with the batch
+        }
+        if (!ok && lane == 0) {  // let copies in flight land before the CTA exits
+            volatile int never = 0;
+            for (int i = 0; i < kStages; ++i)
+                if (issued_mask & (1u << i))
+                    ptx::mbar_wait_bounded(&s.full[i], (parity_mask >> i) & 1u, &never, kDrainLimitNs);
         }
     } else {
         // ------------------------------------------------------------ consumers
@@ -282,8 +347,8 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
                 key = philox_keys(a.seed);
                 cur_run = m.run;
             }
-            const float4* A = reinterpret_cast<const float4*>(stage_a(s, stage));
-            const float4* B = reinterpret_cast<const float4*>(stage_b(s, stage));
+            const float4* A = reinterpret_cast<const float4*>(stage_a(s, stage, kChunkBytes));
+            const float4* B = reinterpret_cast<const float4*>(stage_b(s, stage, kChunkBytes));
             float4* O = reinterpret_cast<float4*>(children + static_cast<int64_t>(m.j) * a.c_pad + m.g0);
             const uint32_t j = a.entity ? a.entity[m.j] : static_cast<uint32_t>(m.j);  // Philox entity
             const bool live = ct * kGenesPerLane < m.len;
@@ -340,7 +405,10 @@ breed_kernel(const __grid_constant__ BreedRun run0, const BreedRun* __restrict__
 
 }  // namespace
 
-int32_t breed_chunks(int64_t c_pad) { return static_cast<int32_t>((c_pad + kChunk - 1) / kChunk); }
+int32_t breed_chunks(int64_t c_pad)
+{
+    return static_cast<int32_t>((c_pad + BreedShape<true>::kChunk - 1) / BreedShape<true>::kChunk);
+}
 
 namespace {
 
@@ -367,16 +435,17 @@ cudaError_t launch_breed(const BreedArgs& a, const float* parents, const int32_t
     r.par2 = par2;
     r.kind = kind;
     r.children = children;
-    r.chunks = breed_chunks(a.c_pad);
+    r.chunks = static_cast<int32_t>((a.c_pad + BreedShape<false>::kChunk - 1) / BreedShape<false>::kChunk);
     r.item0 = 0;
     const int64_t items = static_cast<int64_t>(a.pop) * r.chunks;
     int grid = 0;
     cudaError_t err = breed_grid(items, &grid);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(breed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(kBreedSmemBytes));
+                               static_cast<int>(breed_smem_bytes<false>()));
     if (err != cudaSuccess) return err;
-    return launch_pdl(breed_kernel<false>, dim3(grid), dim3(kBreedThreads), kBreedSmemBytes, stream, r,
+    return launch_pdl(breed_kernel<false>, dim3(grid), dim3(BreedShape<false>::kThreads), breed_smem_bytes<false>(),
+                      stream, r,
                       static_cast<const BreedRun*>(nullptr), 1, items, static_cast<const uint32_t*>(nullptr), status);
 }
 
@@ -387,11 +456,11 @@ cudaError_t launch_breed_runs(const BreedRun* runs_dev, int32_t n_runs, int64_t 
     cudaError_t err = breed_grid(n_items, &grid);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(breed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               static_cast<int>(kBreedSmemBytes));
+                               static_cast<int>(breed_smem_bytes<true>()));
     if (err != cudaSuccess) return err;
     const BreedRun none{};
-    breed_kernel<true><<<grid, kBreedThreads, kBreedSmemBytes, stream>>>(none, runs_dev, n_runs, n_items, gen_dev,
-                                                                       status);
+    breed_kernel<true><<<grid, BreedShape<true>::kThreads, breed_smem_bytes<true>(), stream>>>(
+        none, runs_dev, n_runs, n_items, gen_dev, status);
     return cudaGetLastError();
 }
 

@@ -233,7 +233,8 @@ leea_status dispatch_eval(const NetLayout& net, int32_t pop, const float* pop_de
 // The same for 8-bit inputs x = k / x_div.
 leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x, float x_div,
                              const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
-                             float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream, void* mlp_scratch)
+                             float* f_adj, int32_t* correct, int32_t path, cudaStream_t stream, void* mlp_scratch,
+                             void* x16, bool x16_staged)
 {
     if (!(x_div > 0.0f) || std::isinf(x_div)) return fail(LEEA_EINVAL, "x_div must be finite and > 0");
     if (net.n_layers > 2) {  // several hidden layers
@@ -258,14 +259,25 @@ leea_status dispatch_eval_u8(const NetLayout& net, int32_t pop, const float* pop
     const bool tc_ok = eval_u8_tc_supported(net, batch, pop_dev);
     if (path == LEEA_EVAL_TENSOR && !tc_ok)
         return fail(LEEA_EINVAL, "tensor-core evaluation of 8-bit inputs needs batch <= 128, d_0 %% 4 == 0, "
-                                 "h %% 16 == 0, h <= 128, h + round_up(8 ceil(d_0/16), 16) <= 512, d_out <= 16 and a "
-                                 "16-byte aligned population");
+                                 "h %% 16 == 0, h <= 128, d_out <= 16 and a 16-byte aligned population");
     cudaError_t err;
     if (tc_ok && path != LEEA_EVAL_SIMT) {
         unsigned int* status = device_status_ptr();
         if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
-        err = launch_eval_u8_tc(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct, status,
-                                stream);
+        void* own = nullptr;  // the call's own FP16 batch, freed in stream order after the evaluation
+        if (!x16) {
+            LEEA_CUDA_TRY(cudaMallocAsync(&own, eval_u8_x16_bytes(net, batch), stream), "batch staging allocation");
+            x16 = own;
+            x16_staged = false;
+        }
+        err = x16_staged ? cudaSuccess : launch_stage_x16(net, x, batch, x16, stream);
+        if (err == cudaSuccess)
+            err = launch_eval_u8_tc(net, pop, pop_dev, x, x16, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
+                                    status, stream);
+        if (own) {
+            const cudaError_t ferr = cudaFreeAsync(own, stream);
+            if (err == cudaSuccess) err = ferr;
+        }
     } else {
         err = launch_eval_simt_u8(net, pop, pop_dev, x, x_div, y, batch, alpha, f_inh, f_raw, f_adj, correct,
                                   stream);
@@ -757,6 +769,9 @@ struct leea_state {
     // tensor-core evaluation of deeper nets: weight pieces, marks, level tiles
     void* mlp_scratch;
     size_t mlp_scratch_bytes;
+    // tensor-core evaluation of d_0-h-d_out nets on 8-bit inputs: the batch as
+    // FP16 (at most 128 samples), staged once per generation
+    void* x16;
 };
 
 namespace {
@@ -785,6 +800,7 @@ void free_state(leea_state* s)
     cudaFree(s->sigma[0]);
     cudaFree(s->sigma[1]);
     cudaFree(s->mlp_scratch);
+    cudaFree(s->x16);
     if (s->prof) {
         if (s->prof->created)
             for (int st = 0; st < LEEA_NUM_STAGES; ++st)
@@ -918,6 +934,9 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         s->mlp_scratch_bytes = eval_mlp_tc_scratch_bytes(s->net, pop, 0);  // grown with the batch
         err = cudaMalloc(&s->mlp_scratch, s->mlp_scratch_bytes);
     }
+    if (s->net.n_layers == 2 && p->precision == 0 && err == cudaSuccess &&
+        eval_u8_tc_supported(s->net, 128, s->popbuf[0]))
+        err = cudaMalloc(&s->x16, eval_u8_x16_bytes(s->net, 128));
     if (p->sigma_ctl == LEEA_SIGMA_SELF) {
         for (int b = 0; b < 2 && err == cudaSuccess; ++b) err = cudaMalloc(&s->sigma[b], sizeof(float) * np);
         if (err == cudaSuccess) {  // every individual starts with the sigma gene p->sigma
@@ -987,6 +1006,10 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
                                  "d_out <= 16 and batch <= 128");
     if (!u8 && s->prm.eval_path == LEEA_EVAL_FUSED)
         return fail(LEEA_EINVAL, "the fused breed + evaluate path takes 8-bit inputs (leea_generation_u8*)");
+    // The tensor-core evaluation of 8-bit inputs reads the batch as FP16: a
+    // breeding generation stages it beside the selection.
+    const bool stage_early = !first && !fused && u8 && prec == 0 && s->x16 && s->prm.eval_path != LEEA_EVAL_SIMT &&
+                             s->net.n_layers == 2 && eval_u8_tc_supported(s->net, batch, s->popbuf[0]);
     if (!first) {
         const uint32_t g = s->gen + 1;
         const float sigma_g = sigma_of_breed(s->prm, g);
@@ -1008,6 +1031,9 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
             }
             LEEA_CUDA_TRY(launch_rank_select(a, s->f_adj, s->order, s->par1, s->par2, s->kind, s->f_inh, s->stream),
                           "rank/select kernel");
+            if (stage_early)  // runs beside the selection; the breed that follows waits for both
+                LEEA_CUDA_TRY(launch_stage_x16(s->net, static_cast<const uint8_t*>(x_dev), batch, s->x16, s->stream),
+                              "batch staging kernel");
             sc.done();
         }
         if (fused) {
@@ -1062,7 +1088,7 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         else if (u8)
             st = dispatch_eval_u8(s->net, s->pop, s->popbuf[s->cur], static_cast<const uint8_t*>(x_dev), x_div, y_dev,
                                   batch, s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,
-                                  s->prm.eval_path, s->stream, s->mlp_scratch);
+                                  s->prm.eval_path, s->stream, s->mlp_scratch, s->x16, stage_early);
         else
             st = dispatch_eval(s->net, s->pop, s->popbuf[s->cur], static_cast<const float*>(x_dev), y_dev, batch,
                                s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct,

@@ -216,15 +216,21 @@ cudaError_t launch_eval_tc(const NetLayout& net, int32_t pop, const float* pop_d
                            const int32_t* y, int32_t batch, float alpha, const float* f_inh, float* f_raw,
                            float* f_adj, int32_t* correct, unsigned int* status, cudaStream_t stream);
 // 8-bit inputs x = k / x_div: CUDA-core FP32 evaluation of any shape, and the
-// tensor-core evaluation (batch in TMEM, exact BF16 pieces) for batch <= 128,
-// d_0 % 4 == 0, h % 16 == 0, h + d_0/2 (rounded) <= 512 TMEM columns, d_out <= 16.
+// tensor-core evaluation (two individuals per MMA, exact FP16 pieces) for
+// batch <= 128, d_0 % 4 == 0, h % 16 == 0, h <= 128, d_out <= 16.  The
+// tensor-core path reads the batch as FP16 from x16 (eval_u8_x16_bytes(net,
+// batch) bytes, 16-byte aligned), which launch_stage_x16 fills from the levels
+// earlier on the same stream; the staging kernel lets its successor start at
+// once and waits for its own predecessor before it ends.
 cudaError_t launch_eval_simt_u8(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
                                 float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
                                 float* f_raw, float* f_adj, int32_t* correct, cudaStream_t stream);
 bool eval_u8_tc_supported(const NetLayout& net, int32_t batch, const float* pop_dev);
+size_t eval_u8_x16_bytes(const NetLayout& net, int32_t batch);
+cudaError_t launch_stage_x16(const NetLayout& net, const uint8_t* x, int32_t batch, void* x16, cudaStream_t stream);
 cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* pop_dev, const uint8_t* x,
-                              float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
-                              float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
+                              const void* x16, float x_div, const int32_t* y, int32_t batch, float alpha,
+                              const float* f_inh, float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
                               cudaStream_t stream);
 // Evaluation of nets with several hidden layers (n_dims >= 3; every layer
 // input and hidden width <= 256, d_out <= 32), FP32 on the CUDA cores; and the

@@ -318,3 +318,65 @@ __device__ __forceinline__ void mma_f8_tmem_a(uint32_t d_tmem, uint32_t a_tmem, 
 
 }  // namespace ptx
 }  // namespace leea
+
+namespace leea {
+namespace ptx {
+
+// Shared-memory matrix descriptor, K-major operand in the 64-byte swizzle
+// layout (8-row atoms of 64-byte rows, 512 bytes, the 16-byte chunk index
+// XORed with address bits 7-8); `sbo` = bytes between consecutive 8-row
+// groups (512 when dense, larger when other data is interleaved).
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t saddr, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= static_cast<uint64_t>(1u) << 16;                  // leading byte offset (unused in one atom)
+    d |= static_cast<uint64_t>(sbo >> 4) << 32;            // stride byte offset: next 8-row group
+    d |= static_cast<uint64_t>(1u) << 46;                  // descriptor version
+    d |= static_cast<uint64_t>(4u) << 61;                  // 64-byte swizzle
+    return d;
+}
+
+}  // namespace ptx
+}  // namespace leea
+
+namespace leea {
+namespace ptx {
+
+// Prefetches the tile at (x, y, z) of a 3-D tensor map into L2 (no shared
+// memory, no completion signal).
+__device__ __forceinline__ void tma_prefetch_3d(const void* map, int32_t x, int32_t y, int32_t z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+                 ::"l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
+}  // namespace ptx
+}  // namespace leea
+
+namespace leea {
+namespace ptx {
+
+// 16-byte asynchronous copy global -> shared through the load path (L2 only);
+// completion per thread by cp.async groups.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src))
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Waits until at most N of this thread's committed cp.async groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+}  // namespace ptx
+}  // namespace leea
