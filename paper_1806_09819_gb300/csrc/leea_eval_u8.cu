@@ -17,32 +17,32 @@
 // samples, the M side) is the A operand and the stacked W1 pieces of two
 // individuals (N = 2h) the B operand, and 2 x 49 MMAs evaluate a pair at
 // d_0 = 784.  The batch, staged once per evaluation as FP16 in global memory
-// (stage_x16_kernel; it stays in L2), arrives by TMA in 32-input tiles next to
-// the weights.
+// (stage_x16_kernel; it stays in L2), arrives by TMA in K-stage tiles next to
+// the weights.  A K stage is 64 inputs (128-byte swizzled FP16 rows, 256-byte
+// FP32 rows) when three such stages fit in shared memory (h <= 112), else 32
+// (64-byte swizzle): the wider slices stream HBM faster (measured with no
+// compute: 4.8 against 4.0-4.4 TB/s for the same 351 MB).
 //
 // Pipeline (persistent CTA, one per SM; each CTA takes a contiguous range of
 // individuals, as pairs, the last one alone when the range is odd):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
-//   warp 1      producer: per stage, one TMA of the batch tile (128 x 32
-//               FP16, 64-byte swizzle, from L2) and one TMA per individual of
-//               its FP32 W1 slice (h x 32); per unit, b1/W2/b2 by one bulk
-//               copy per individual
-//   warps 2-9   converters: each 8-row group of a raw FP32 slice (1 KB) is
-//               read by one warp and overwritten in place by its two FP16
-//               pieces in the 64-byte swizzled K-major layout (piece q at
-//               +512 bytes, so the pieces of all 2h rows form two operands
-//               with 8-row groups 1 KB apart); a warp reads all its groups of
-//               the stage before it writes any.  (Measured with no compute:
-//               tile loads of these 32-input slices stream the population at
-//               4.5 TB/s; 128-bit loads from many threads at 5.1-5.5 TB/s but
-//               only with 64-128 KB in flight per SM, more registers than this
-//               kernel has; cp.async into the ring at 4.1-4.8 TB/s.)
+//   warp 1      producer: per stage, one TMA of the batch tile (the batch's
+//               rows rounded up to 8, from L2) and one TMA per individual of
+//               its FP32 W1 slice.  A stage is [batch tile][slot 0][slot 1]:
+//               the MMA reads 128 rows of A, and rows past the tile fall on
+//               the slots' data, which only accumulator rows past the batch see
+//   warps 2-9   converters: each 8-row group of a raw FP32 slice is read by
+//               one warp and overwritten in place by its two FP16 pieces in
+//               the swizzled K-major layout (piece q in the group's q-th half,
+//               so the pieces of all 2h rows form two operands whose 8-row
+//               groups are one group apart); a warp reads the groups of a
+//               batch before it writes any of them
 //   warps 10-17 epilogue, 4 warps (one per TMEM lane quarter = 32 samples)
-//               per individual: bias, ReLU, layer 2 (W2 staged transposed in
-//               shared memory), softmax cross-entropy, fixed-order batch sum,
-//               inheritance blend; accumulators are double-buffered in TMEM
-//               (columns 0 and 256), so a pair's epilogue overlaps the next
-//               pair's MMAs
+//               per individual: while the unit's MMAs run, b1, W2 (transposed)
+//               and b2 are loaded into shared memory; then bias, ReLU, layer
+//               2, softmax cross-entropy, fixed-order batch sum, inheritance
+//               blend; accumulators are double-buffered in TMEM (columns 0
+//               and 256), so a pair's epilogue overlaps the next pair's MMAs
 // Every mbarrier wait is bounded in time; on expiry the kernel sets
 // kStatusEvalTimeout, lets its copies and MMAs in flight finish and exits.
 #include <cuda.h>
@@ -59,15 +59,13 @@ namespace {
 
 constexpr int kConvWarps = 8;
 constexpr int kFirstConvWarp = 2;
-constexpr int kGroupsPerWarp = 4;           // 8-row groups per converter warp and stage: 2 x 128 rows / 8 / 8
 constexpr int kFirstEpiWarp = kFirstConvWarp + kConvWarps;
 constexpr int kEpiWarps = 8;
 constexpr int kU8Threads = 32 * (kFirstEpiWarp + kEpiWarps);
-constexpr int kKStage = 32;             // K elements per stage: 128-byte FP32 rows, 64-byte FP16 rows
-constexpr uint32_t kATileBytes = 128u * 64u;  // batch tile: 128 samples x 32 levels as FP16
 constexpr int kMinStages = 3;
 constexpr int kMaxStages = 6;
 constexpr int kMaxOutU8 = 16;
+constexpr int kMaxGroups = 2 * 128 / 8;  // 8-row groups of the widest pair
 constexpr int kFlagSlots = 16;          // unit-tagged range flags; converters run at most a few units ahead
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kAccStride = 256;    // the two accumulators: columns 0 and 256
@@ -76,12 +74,24 @@ constexpr float kPieceRange = 128.0f;   // |w| below this: 2^8 |w| < 2^15, finit
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 constexpr uint64_t kDrainLimitNs = 200000000ull;
 
+// Layout of one K stage of KS inputs.
+template <int KS>
+struct StageShape {
+    static constexpr uint32_t kRawRow = 4u * KS;            // FP32 bytes per row
+    static constexpr uint32_t kPieceRow = 2u * KS;          // FP16 bytes per row: one swizzle atom row
+    static constexpr uint32_t kGroup = 8u * kRawRow;        // an 8-row group: raw, then both pieces
+    static constexpr uint32_t kPieceOff = 8u * kPieceRow;   // piece 1 within a group
+    static constexpr int kF4 = KS / 16;                     // float4 per lane and group
+    static constexpr int kBatch = KS == 64 ? 2 : 4;         // groups a converter warp reads before it writes
+    static constexpr uint32_t kSwizzle = KS == 64 ? 2u : 4u;  // descriptor swizzle code: 128 or 64 bytes
+};
+
 struct EvalU8Args {
     int32_t pop, k, h, d_out, dpad, batch, k16, k_stages, n_stages;
     int32_t per_cta, extra;  // individuals per CTA: per_cta, one more for the first `extra` CTAs
-    uint32_t prm_bytes;      // b1, W2, b2 of one individual, rounded up to 16 bytes
-    uint32_t slot_bytes;     // one individual's slice of a stage: h rows x 128 bytes (FP32, then its two FP16 pieces)
-    uint32_t stage_bytes;    // two slots and the batch tile
+    uint32_t slot_bytes;     // one individual's slice of a stage: h raw rows
+    uint32_t a_bytes;        // the batch tile: round_up(batch, 8) rows of FP16 levels
+    uint32_t stage_bytes;    // the batch tile and two slots, rounded up to 1 KB
     int64_t c_pad;
     float inv_div, alpha;
     const float* popv;
@@ -95,8 +105,7 @@ struct EvalU8Args {
 };
 
 struct U8Smem {
-    uint8_t* ring;       // n_stages x stage_bytes, 1024-aligned: W1 slices (raw, then pieces), then the batch tile
-    uint8_t* prm_raw;    // [2 buffers][2 slots] x prm_bytes: b1, W2 (row-major), b2 as stored
+    uint8_t* ring;       // n_stages x stage_bytes, 1024-aligned: the batch tile, then W1 slices (raw, then pieces)
     float* w2t;          // [2 slots][h][dpad]
     float* b1;           // [2 slots][h]
     float* b2;           // [2 slots][16]
@@ -104,17 +113,18 @@ struct U8Smem {
     int32_t* red_ok;     // [2 slots][4 quarters]
     uint32_t* flag;      // [kFlagSlots][2]: u + 1 if unit u's individual in that slot has |w| >= 128
     uint32_t* accflag;   // [2]: the flags of the unit in that accumulator, for the epilogue
-    int* ep_go;          // [2 slots][2]: the epilogue groups' go words (parameters, accumulator)
+    int* ep_go;          // [2 slots]: the epilogue groups' go words
     uint32_t* tmem_holder;
     volatile int* abort_flag;
-    uint64_t *full, *a_full, *empty, *prm_full, *prm_empty, *acc_full, *acc_empty, *drain;
+    uint64_t *full, *a_full, *empty, *acc_full, *acc_empty, *drain;
 };
 
-__host__ __device__ inline size_t u8_tail_bytes(int32_t h, int32_t dpad, uint32_t prm_bytes, int32_t n_stages)
+constexpr size_t kTailFixed = sizeof(float) * 8 + sizeof(int32_t) * 8 + sizeof(uint32_t) * (2 * kFlagSlots + 2) +
+                              sizeof(int) * 2 + 16 + 16;
+
+size_t u8_tail_bytes(int32_t h, int32_t dpad, int32_t n_stages)
 {
-    return 4u * static_cast<size_t>(prm_bytes) + sizeof(float) * (2u * h * dpad + 2u * h + 32u + 8u) +
-           sizeof(int32_t) * 8u + sizeof(uint32_t) * (2u * kFlagSlots + 2u) + sizeof(int) * 4u + 16u +
-           8u * (3u * n_stages + 9u) + 64u;
+    return sizeof(float) * (2u * h * dpad + 2u * h + 32u) + kTailFixed + 8u * (3u * n_stages + 5u);
 }
 
 __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
@@ -122,8 +132,6 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     U8Smem s;
     s.ring = raw + ((1024u - (ptx::smem_u32(raw) & 1023u)) & 1023u);
     uint8_t* p = s.ring + static_cast<size_t>(a.n_stages) * a.stage_bytes;
-    s.prm_raw = p;
-    p += 4u * a.prm_bytes;
     s.w2t = reinterpret_cast<float*>(p);
     p += sizeof(float) * 2 * a.h * a.dpad;
     s.b1 = reinterpret_cast<float*>(p);
@@ -139,46 +147,53 @@ __device__ __forceinline__ U8Smem carve(uint8_t* raw, const EvalU8Args& a)
     s.accflag = reinterpret_cast<uint32_t*>(p);
     p += sizeof(uint32_t) * 2;
     s.ep_go = reinterpret_cast<int*>(p);
-    p += sizeof(int) * 4;
+    p += sizeof(int) * 2;
     s.tmem_holder = reinterpret_cast<uint32_t*>(p);
     s.abort_flag = reinterpret_cast<volatile int*>(p + 4);
     p += 16;
-    p = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 7u) & ~uintptr_t(7));
+    p = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 15u) & ~uintptr_t(15));
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.full = bars;
     s.a_full = bars + a.n_stages;
     s.empty = bars + 2 * a.n_stages;
-    s.prm_full = bars + 3 * a.n_stages;
-    s.prm_empty = s.prm_full + 2;
-    s.acc_full = s.prm_empty + 2;
+    s.acc_full = bars + 3 * a.n_stages;
     s.acc_empty = s.acc_full + 2;
     s.drain = s.acc_empty + 2;
     return s;
 }
 
-uint32_t u8_prm_bytes(int32_t h, int32_t d_out)
+uint32_t u8_a_bytes(int32_t batch, int32_t ks)
 {
-    return (static_cast<uint32_t>(h + d_out * h + d_out) * 4u + 15u) & ~15u;
+    return static_cast<uint32_t>((batch + 7) / 8 * 8) * 2u * static_cast<uint32_t>(ks);
 }
 
-uint32_t u8_stage_bytes(int32_t h)
+// A stage holds the batch tile and two slots, and at least the 128 rows of A
+// the MMA reads from its start.
+uint32_t u8_stage_bytes(int32_t h, int32_t batch, int32_t ks)
 {
-    return 2u * static_cast<uint32_t>(h) * 128u + kATileBytes;
+    const uint32_t b = u8_a_bytes(batch, ks) + 2u * static_cast<uint32_t>(h) * 4u * static_cast<uint32_t>(ks);
+    return std::max((b + 1023u) & ~1023u, 128u * 2u * static_cast<uint32_t>(ks));
 }
 
-size_t u8_smem_bytes(int32_t h, int32_t d_out, int32_t n_stages)
+size_t u8_smem_bytes(int32_t h, int32_t d_out, int32_t batch, int32_t ks, int32_t n_stages)
 {
     const int32_t dpad = (d_out + 3) / 4 * 4;
-    return 1024 + static_cast<size_t>(n_stages) * u8_stage_bytes(h) +
-           u8_tail_bytes(h, dpad, u8_prm_bytes(h, d_out), n_stages);
+    return 1024 + static_cast<size_t>(n_stages) * u8_stage_bytes(h, batch, ks) + u8_tail_bytes(h, dpad, n_stages);
 }
 
-// The deepest ring that fits in 227 KB of shared memory; 0 if not even kMinStages do.
-int32_t u8_stages(int32_t h, int32_t d_out)
+// The deepest ring of K stage `ks` that fits in 227 KB of shared memory; 0 if
+// not even kMinStages do.
+int32_t u8_stages(int32_t h, int32_t d_out, int32_t batch, int32_t ks)
 {
     for (int32_t ns = kMaxStages; ns >= kMinStages; --ns)
-        if (u8_smem_bytes(h, d_out, ns) <= 227u * 1024u) return ns;
+        if (u8_smem_bytes(h, d_out, batch, ks, ns) <= 227u * 1024u) return ns;
     return 0;
+}
+
+// K stage of a net: 64 inputs when kMinStages of them fit, else 32 (0: neither).
+int32_t u8_kstage(int32_t h, int32_t d_out, int32_t batch)
+{
+    return u8_stages(h, d_out, batch, 64) > 0 ? 64 : (u8_stages(h, d_out, batch, 32) > 0 ? 32 : 0);
 }
 
 __device__ __forceinline__ void raise_abort(const U8Smem& s, const EvalU8Args& a)
@@ -210,19 +225,21 @@ __device__ __forceinline__ bool out_of_piece_range(const float4& v)
            fabsf(v.w) >= kPieceRange;
 }
 
-// Four weights of row r (0..7) of an 8-row group, K offset 4 c8 within the
-// stage, as FP16 pieces at their 64-byte-swizzle positions: piece q of the
-// group occupies bytes 512 q .. 512 q + 511 of the group.
-__device__ __forceinline__ void put_pieces(uint8_t* group, int r, int c8, const float4& f)
+// Four weights of row r (0..7) of an 8-row group, inputs 4 c4 .. 4 c4 + 3 of
+// the stage, as FP16 pieces at their swizzled positions (the 16-byte chunk
+// index XORed with r for the 128-byte swizzle, with r / 2 for the 64-byte one).
+template <int KS>
+__device__ __forceinline__ void put_pieces(uint8_t* group, int r, int c4, const float4& f)
 {
+    using S = StageShape<KS>;
     uint32_t lo[2], hi[2];
     split2x2(f.x, f.y, lo[0], lo[1]);
     split2x2(f.z, f.w, hi[0], hi[1]);
-    const uint32_t off = static_cast<uint32_t>(r) * 64u +
-                         ((static_cast<uint32_t>(c8 >> 1) ^ (static_cast<uint32_t>(r >> 1) & 3u)) << 4) +
-                         (static_cast<uint32_t>(c8 & 1) << 3);
+    const uint32_t chunk = static_cast<uint32_t>(c4 >> 1) ^
+                           (KS == 64 ? static_cast<uint32_t>(r & 7) : (static_cast<uint32_t>(r >> 1) & 3u));
+    const uint32_t off = static_cast<uint32_t>(r) * S::kPieceRow + (chunk << 4) + (static_cast<uint32_t>(c4 & 1) << 3);
     *reinterpret_cast<uint2*>(group + off) = make_uint2(lo[0], hi[0]);
-    *reinterpret_cast<uint2*>(group + 512 + off) = make_uint2(lo[1], hi[1]);
+    *reinterpret_cast<uint2*>(group + S::kPieceOff + off) = make_uint2(lo[1], hi[1]);
 }
 
 // This CTA's individuals: [first, first + count).
@@ -233,16 +250,17 @@ __device__ __forceinline__ void cta_range(const EvalU8Args& a, int& first, int& 
     count = a.per_cta + (b < a.extra ? 1 : 0);
 }
 
+template <int KS>
 __global__ void __launch_bounds__(kU8Threads, 1)
 eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant__ CUtensorMap tmap_x,
                const EvalU8Args a)
 {
+    using S = StageShape<KS>;
     extern __shared__ uint8_t smem_raw[];
     const U8Smem s = carve(smem_raw, a);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int first = 0, count = 0;
     cta_range(a, first, count);
-    const uint32_t a_off = 2u * a.slot_bytes;  // batch tile within a stage
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < a.n_stages; ++i) {
@@ -251,8 +269,6 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
             ptx::mbar_init(&s.empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
-            ptx::mbar_init(&s.prm_full[i], 1);
-            ptx::mbar_init(&s.prm_empty[i], kEpiWarps);
             ptx::mbar_init(&s.acc_full[i], 2);  // the MMAs' commit and the issuer's flag hand-over
             ptx::mbar_init(&s.acc_empty[i], kEpiWarps);
         }
@@ -261,7 +277,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
         ptx::tma_prefetch_map(&tmap_x);
         for (int i = 0; i < 2 * kFlagSlots; ++i) s.flag[i] = 0u;
         s.accflag[0] = s.accflag[1] = 0u;
-        for (int i = 0; i < 4; ++i) s.ep_go[i] = 0;
+        s.ep_go[0] = s.ep_go[1] = 0;
         *s.abort_flag = 0;
         ptx::fence_mbar_init();
     }
@@ -300,12 +316,13 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
                     ptx::tc_fence_after();
                     const uint32_t sb = ring + stage * a.stage_bytes;
 #pragma unroll
-                    for (int kk = 0; kk < kKStage / 16; ++kk) {
-                        if (kc * kKStage + kk * 16 >= a.k16) break;
-                        const uint64_t ad = ptx::smem_desc_sw64(sb + a_off + 32u * kk, 512u);
+                    for (int kk = 0; kk < KS / 16; ++kk) {
+                        if (kc * KS + kk * 16 >= a.k16) break;
+                        const uint64_t ad = ptx::smem_desc(sb + 32u * kk, 8u * S::kPieceRow, S::kSwizzle);
 #pragma unroll
                         for (int q = 0; q < 2; ++q) {
-                            const uint64_t bd = ptx::smem_desc_sw64(sb + 512u * q + 32u * kk, 1024u);
+                            const uint64_t bd =
+                                ptx::smem_desc(sb + a.a_bytes + S::kPieceOff * q + 32u * kk, S::kGroup, S::kSwizzle);
                             ptx::mma_f16(d, ad, bd, idesc, (kc | kk | q) != 0 ? 1u : 0u);
                         }
                     }
@@ -330,22 +347,10 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             ptx::grid_dep_wait();  // the population (breeding) and the staged batch come from earlier kernels
-            uint32_t stage = 0, phase = 0, issued_mask = 0, parity_mask = 0, prm_issued = 0;
+            uint32_t stage = 0, phase = 0, issued_mask = 0, parity_mask = 0;
             bool ok = true;
             for (int u = 0; ok && 2 * u < count; ++u) {
                 const int n = min(2, count - 2 * u), p0 = first + 2 * u;
-                const uint32_t pb = static_cast<uint32_t>(u) & 1u, pph = (static_cast<uint32_t>(u) >> 1) & 1u;
-                if (!ptx::mbar_wait_bounded(&s.prm_empty[pb], pph ^ 1u, s.abort_flag, kWaitLimitNs)) {
-                    raise_abort(s, a);
-                    ok = false;
-                    break;
-                }
-                ptx::mbar_arrive_expect_tx(&s.prm_full[pb], static_cast<uint32_t>(n) * a.prm_bytes);
-                for (int j = 0; j < n; ++j)
-                    ptx::bulk_load(s.prm_raw + (2 * pb + j) * a.prm_bytes,
-                                   a.popv + static_cast<int64_t>(p0 + j) * a.c_pad + static_cast<int64_t>(a.h) * a.k,
-                                   a.prm_bytes, &s.prm_full[pb]);
-                ++prm_issued;
                 for (int kc = 0; kc < a.k_stages; ++kc) {
                     if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
                         raise_abort(s, a);
@@ -353,10 +358,11 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
                         break;
                     }
                     uint8_t* sb = s.ring + stage * a.stage_bytes;
-                    ptx::mbar_arrive_expect_tx(&s.a_full[stage], kATileBytes + static_cast<uint32_t>(n) * a.slot_bytes);
-                    ptx::tma_load_2d(sb + a_off, &tmap_x, &s.a_full[stage], kc * kKStage, 0);
+                    ptx::mbar_arrive_expect_tx(&s.a_full[stage], a.a_bytes + static_cast<uint32_t>(n) * a.slot_bytes);
+                    ptx::tma_load_2d(sb, &tmap_x, &s.a_full[stage], kc * KS, 0);
                     for (int j = 0; j < n; ++j)
-                        ptx::tma_load_3d(sb + j * a.slot_bytes, &tmap_w, &s.a_full[stage], kc * kKStage, 0, p0 + j);
+                        ptx::tma_load_3d(sb + a.a_bytes + j * a.slot_bytes, &tmap_w, &s.a_full[stage], kc * KS, 0,
+                                         p0 + j);
                     issued_mask |= 1u << stage;
                     parity_mask = (parity_mask & ~(1u << stage)) | (phase << stage);
                     if (++stage == static_cast<uint32_t>(a.n_stages)) { stage = 0; phase ^= 1u; }
@@ -367,12 +373,12 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
                 for (int i = 0; i < a.n_stages; ++i)
                     if (issued_mask & (1u << i))
                         ptx::mbar_wait_bounded(&s.a_full[i], (parity_mask >> i) & 1u, &never, kDrainLimitNs);
-                for (uint32_t u = prm_issued > 2 ? prm_issued - 2 : 0; u < prm_issued; ++u)
-                    ptx::mbar_wait_bounded(&s.prm_full[u & 1u], (u >> 1) & 1u, &never, kDrainLimitNs);
             }
         }
     } else if (warp < kFirstEpiWarp) {
         // ------------------------------------------------------------ converters (in place)
+        // Lane l handles float4 f = l + 32 m (m < kF4) of each of its groups:
+        // row f / (KS / 4), inputs 4 (f % (KS / 4)) .. + 3.
         const int cw = warp - kFirstConvWarp;
         const int gps = a.h >> 3;  // 8-row groups per individual
         uint32_t stage = 0, phase = 0;
@@ -386,32 +392,37 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
                     ok = false;
                     break;
                 }
-                uint8_t* sb = s.ring + stage * a.stage_bytes;
+                uint8_t* sb = s.ring + stage * a.stage_bytes + a.a_bytes;  // the slots
                 bool bad0 = false, bad1 = false;
-                // All of this warp's groups are read first (their loads in
-                // flight together), then overwritten: lane l holds rows l/8
-                // and 4 + l/8 of each group, K-elements 4 (l % 8) .. + 3.
-                float4 f0[kGroupsPerWarp], f1[kGroupsPerWarp];
 #pragma unroll
-                for (int j = 0; j < kGroupsPerWarp; ++j) {
-                    const int g = cw + kConvWarps * j;
-                    if (g < groups) {
-                        const uint8_t* gp = sb + g * 1024;
-                        f0[j] = *reinterpret_cast<const float4*>(gp + lane * 16);
-                        f1[j] = *reinterpret_cast<const float4*>(gp + 512 + lane * 16);
-                    }
-                }
-                __syncwarp();  // every group is read before any of it is overwritten
+                for (int g0 = 0; g0 < kMaxGroups / kConvWarps; g0 += S::kBatch) {
+                    // Read a batch of this warp's groups, then overwrite them.
+                    float4 f[S::kBatch][S::kF4];
 #pragma unroll
-                for (int j = 0; j < kGroupsPerWarp; ++j) {
-                    const int g = cw + kConvWarps * j;
-                    if (g < groups) {
-                        uint8_t* gp = sb + g * 1024;
-                        put_pieces(gp, lane >> 3, lane & 7, f0[j]);
-                        put_pieces(gp, 4 + (lane >> 3), lane & 7, f1[j]);
-                        const bool b = out_of_piece_range(f0[j]) || out_of_piece_range(f1[j]);
-                        if (g < gps) bad0 |= b; else bad1 |= b;
+                    for (int b = 0; b < S::kBatch; ++b) {
+                        const int g = cw + kConvWarps * (g0 + b);
+                        if (g < groups) {
+#pragma unroll
+                            for (int m = 0; m < S::kF4; ++m)
+                                f[b][m] = *reinterpret_cast<const float4*>(sb + g * S::kGroup + (lane + 32 * m) * 16);
+                        }
                     }
+                    __syncwarp();  // the batch is read before any of it is overwritten
+#pragma unroll
+                    for (int b = 0; b < S::kBatch; ++b) {
+                        const int g = cw + kConvWarps * (g0 + b);
+                        if (g < groups) {
+                            bool bad = false;
+#pragma unroll
+                            for (int m = 0; m < S::kF4; ++m) {
+                                const int fi = lane + 32 * m;
+                                put_pieces<KS>(sb + g * S::kGroup, fi / (KS / 4), fi % (KS / 4), f[b][m]);
+                                bad |= out_of_piece_range(f[b][m]);
+                            }
+                            if (g < gps) bad0 |= bad; else bad1 |= bad;
+                        }
+                    }
+                    __syncwarp();
                 }
                 const bool any0 = __any_sync(0xFFFFFFFFu, bad0), any1 = __any_sync(0xFFFFFFFFu, bad1);
                 if (lane == 0) {
@@ -435,45 +446,38 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
         const uint32_t lane_addr = static_cast<uint32_t>(q * 32) << 16;
         const uint32_t bar_id = 1u + static_cast<uint32_t>(g);
         const int32_t label = row < a.batch ? a.y[row] : 0;
-        float* b1 = s.b1 + g * a.h;
-        float* b2 = s.b2 + g * 16;
+        float* b1s = s.b1 + g * a.h;
+        float* b2s = s.b2 + g * 16;
         float* w2t = s.w2t + g * a.h * a.dpad;
-        int* go_prm = s.ep_go + 2 * g;
-        int* go_acc = s.ep_go + 2 * g + 1;
+        int* go = s.ep_go + g;
+        ptx::grid_dep_wait();  // b1, W2, b2 come from the previous kernel (breeding)
         for (int u = 0; 2 * u < count; ++u) {
             const int n = min(2, count - 2 * u);
             const int p = first + 2 * u + g;
             const uint32_t buf = static_cast<uint32_t>(u) & 1u, bph = (static_cast<uint32_t>(u) >> 1) & 1u;
-            // Parameters of this slot's individual: wait for the bulk copy,
-            // then stage b1, W2 transposed (rows padded to dpad) and b2.
-            if (et == 0) {
-                const bool got = ptx::mbar_wait_bounded(&s.prm_full[buf], bph, s.abort_flag, kWaitLimitNs);
-                if (!got) raise_abort(s, a);
-                *go_prm = got ? 1 : 0;
-            }
-            ptx::named_barrier_sync(bar_id, 128);  // A1: parameters landed (or abort)
-            if (!*go_prm) break;
             if (g < n) {
-                const float* src = reinterpret_cast<const float*>(s.prm_raw + (2 * buf + g) * a.prm_bytes);
-                for (int i = et; i < a.h; i += 128) b1[i] = src[i];
+                // While this unit's MMAs run: b1, W2 transposed (rows padded to
+                // dpad with zeros) and b2 of this slot's individual, as stored
+                // after W1, into shared memory.  The group finished reading the
+                // previous ones at its barrier B.
+                const float* src = a.popv + static_cast<int64_t>(p) * a.c_pad + static_cast<int64_t>(a.h) * a.k;
+                for (int i = et; i < a.h; i += 128) b1s[i] = __ldg(src + i);
                 for (int i = et; i < a.d_out * a.h; i += 128) {
                     const int o = i / a.h, col = i - o * a.h;
-                    w2t[col * a.dpad + o] = src[a.h + i];
+                    w2t[col * a.dpad + o] = __ldg(src + a.h + i);
                 }
                 const int pad = a.dpad - a.d_out;
                 for (int i = et; i < a.h * pad; i += 128) w2t[(i / pad) * a.dpad + a.d_out + i % pad] = 0.0f;
-                if (et < 16) b2[et] = et < a.d_out ? src[a.h + a.d_out * a.h + et] : 0.0f;
+                if (et < 16) b2s[et] = et < a.d_out ? __ldg(src + a.h + a.d_out * a.h + et) : 0.0f;
             }
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&s.prm_empty[buf]);
             if (et == 0) {
                 const bool got = ptx::mbar_wait_bounded(&s.acc_full[buf], bph, s.abort_flag, kWaitLimitNs);
                 if (!got) raise_abort(s, a);
-                *go_acc = !got ? 0 : (((s.accflag[buf] >> g) & 1u) ? 2 : 1);
+                *go = !got ? 0 : (((s.accflag[buf] >> g) & 1u) ? 2 : 1);
             }
-            ptx::named_barrier_sync(bar_id, 128);  // A2: accumulator ready (or abort); parameters staged
-            const int go = *go_acc;
-            if (!go) break;
+            ptx::named_barrier_sync(bar_id, 128);  // A: accumulator ready (or abort); parameters staged
+            const int gov = *go;
+            if (!gov) break;
             ptx::tc_fence_after();
 
             float loss = 0.0f;
@@ -491,8 +495,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
                     float v[16];
                     ptx::tmem_ld16(col0 + static_cast<uint32_t>(c), v);
                     if (row < a.batch) {
-                        if (go == 2) {
-                            ptx::grid_dep_wait();
+                        if (gov == 2) {
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
                                 const float* wr = w1p + static_cast<int64_t>(c + j) * a.k;
@@ -504,7 +507,7 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int col = c + j;
-                            const float hv = fmaxf(fmaf(v[j], a.inv_div, b1[col]), 0.0f);
+                            const float hv = fmaxf(fmaf(v[j], a.inv_div, b1s[col]), 0.0f);
                             const float4* wr = reinterpret_cast<const float4*>(w2t + col * a.dpad);
 #pragma unroll
                             for (int o4 = 0; o4 < kMaxOutU8 / 4; ++o4) {
@@ -520,24 +523,27 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
                     }
                 }
                 if (row < a.batch) {
-                    float zmax = logit[0] + b2[0];
+                    float bo[kMaxOutU8];
+#pragma unroll
+                    for (int o = 0; o < kMaxOutU8; ++o) bo[o] = b2s[o];
+                    float zmax = logit[0] + bo[0];
                     int arg = 0;
 #pragma unroll
                     for (int o = 1; o < kMaxOutU8; ++o) {
                         if (o < a.d_out) {
-                            const float z = logit[o] + b2[o];
+                            const float z = logit[o] + bo[o];
                             if (z > zmax) { zmax = z; arg = o; }
                         }
                     }
                     float se = 0.0f;
 #pragma unroll
                     for (int o = 0; o < kMaxOutU8; ++o)
-                        if (o < a.d_out) se += expf(logit[o] + b2[o] - zmax);
+                        if (o < a.d_out) se += expf(logit[o] + bo[o] - zmax);
                     if (label >= 0 && label < a.d_out) {
                         float zl = 0.0f;
 #pragma unroll
                         for (int o = 0; o < kMaxOutU8; ++o)
-                            if (o == label) zl = logit[o] + b2[o];
+                            if (o == label) zl = logit[o] + bo[o];
                         loss = logf(se) + zmax - zl;
                         good = (arg == label) ? 1 : 0;
                     } else {
@@ -633,7 +639,7 @@ bool eval_u8_tc_supported(const NetLayout& net, int32_t batch, const float* pop_
     const int32_t k = net.dims[0], h = net.dims[1], d_out = net.dims[2];
     if (k % 4 != 0 || h % 16 != 0 || h > 128 || d_out > kMaxOutU8 || batch < 1 || batch > 128) return false;
     if (reinterpret_cast<uintptr_t>(pop_dev) & 15u) return false;
-    return u8_stages(h, d_out) > 0 && u8_encode_fn() != nullptr;
+    return u8_kstage(h, d_out, batch) > 0 && u8_encode_fn() != nullptr;
 }
 
 size_t eval_u8_x16_bytes(const NetLayout& net, int32_t batch)
@@ -669,12 +675,13 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     a.k = net.dims[0];
     a.h = net.dims[1];
     a.d_out = net.dims[2];
-    a.dpad = (a.d_out + 3) / 4 * 4;
     a.batch = batch;
     a.k16 = (a.k + 15) / 16 * 16;
-    a.k_stages = (a.k + kKStage - 1) / kKStage;
-    a.n_stages = u8_stages(a.h, a.d_out);
-    if (a.n_stages == 0) return cudaErrorInvalidValue;
+    a.dpad = (a.d_out + 3) / 4 * 4;
+    const int32_t ks = u8_kstage(a.h, a.d_out, batch);
+    if (ks == 0) return cudaErrorInvalidValue;
+    a.k_stages = (a.k + ks - 1) / ks;
+    a.n_stages = u8_stages(a.h, a.d_out, batch, ks);
     a.c_pad = net.c_pad;
     a.inv_div = static_cast<float>(1.0 / (static_cast<double>(x_div) * kPieceScale));
     a.alpha = alpha;
@@ -686,10 +693,10 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     a.f_adj = f_adj;
     a.correct = correct;
     a.status = status;
-    a.prm_bytes = u8_prm_bytes(a.h, a.d_out);
-    a.slot_bytes = static_cast<uint32_t>(a.h) * 128u;
-    a.stage_bytes = u8_stage_bytes(a.h);
-    const size_t smem = u8_smem_bytes(a.h, a.d_out, a.n_stages);
+    a.slot_bytes = static_cast<uint32_t>(a.h) * 4u * static_cast<uint32_t>(ks);
+    a.a_bytes = u8_a_bytes(batch, ks);
+    a.stage_bytes = u8_stage_bytes(a.h, batch, ks);
+    const size_t smem = u8_smem_bytes(a.h, a.d_out, batch, ks, a.n_stages);
     U8EncodeTiledFn enc = u8_encode_fn();
     if (!enc) return cudaErrorNotSupported;
     CUtensorMap tw, tx;
@@ -698,7 +705,7 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
         const cuuint64_t dims[3] = { static_cast<cuuint64_t>(a.k), static_cast<cuuint64_t>(a.h),
                                      static_cast<cuuint64_t>(pop) };
         const cuuint64_t strides[2] = { static_cast<cuuint64_t>(a.k) * 4u, static_cast<cuuint64_t>(net.c_pad) * 4u };
-        const cuuint32_t box[3] = { static_cast<cuuint32_t>(kKStage), static_cast<cuuint32_t>(a.h), 1 };
+        const cuuint32_t box[3] = { static_cast<cuuint32_t>(ks), static_cast<cuuint32_t>(a.h), 1 };
         const cuuint32_t es[3] = { 1, 1, 1 };
         if (enc(&tw, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(pop_dev), dims, strides, box, es,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -706,16 +713,16 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
             return cudaErrorInvalidValue;
     }
     {
-        // The staged batch: [batch][kp] FP16; rows past the batch and levels
-        // past k read as zero.
+        // The staged batch: [batch][kp] FP16, tiles of round_up(batch, 8)
+        // rows; rows past the batch and levels past k read as zero.
         const int32_t kp = (a.k + 7) / 8 * 8;
         const cuuint64_t dims[2] = { static_cast<cuuint64_t>(a.k), static_cast<cuuint64_t>(batch) };
         const cuuint64_t strides[1] = { static_cast<cuuint64_t>(kp) * 2u };
-        const cuuint32_t box[2] = { static_cast<cuuint32_t>(kKStage), 128 };
+        const cuuint32_t box[2] = { static_cast<cuuint32_t>(ks), static_cast<cuuint32_t>((batch + 7) / 8 * 8) };
         const cuuint32_t es[2] = { 1, 1 };
         if (enc(&tx, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void*>(x16), dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                CU_TENSOR_MAP_INTERLEAVE_NONE, ks == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaErrorInvalidValue;
     }
     int dev = 0, sms = 0;
@@ -723,14 +730,16 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     if (err != cudaSuccess) return err;
     err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(eval_u8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    const void* kern = ks == 64 ? reinterpret_cast<const void*>(eval_u8_kernel<64>)
+                                : reinterpret_cast<const void*>(eval_u8_kernel<32>);
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     const int grid = pop < sms ? pop : sms;
     a.per_cta = pop / grid;
     a.extra = pop % grid;
     // Programmatic stream serialisation: CTAs may start (barriers, TMEM) while
-    // the previous kernel finishes; the producer waits for it before it reads
-    // the population or the staged batch.
+    // the previous kernel finishes; the producer and the epilogue wait for it
+    // before they read the population or the staged batch.
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kU8Threads);
@@ -741,7 +750,8 @@ cudaError_t launch_eval_u8_tc(const NetLayout& net, int32_t pop, const float* po
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, eval_u8_kernel, tw, tx, a);
+    return ks == 64 ? cudaLaunchKernelEx(&cfg, eval_u8_kernel<64>, tw, tx, a)
+                    : cudaLaunchKernelEx(&cfg, eval_u8_kernel<32>, tw, tx, a);
 }
 
 }  // namespace leea

@@ -380,3 +380,22 @@ __device__ __forceinline__ void cp_async_wait_group()
 
 }  // namespace ptx
 }  // namespace leea
+
+namespace leea {
+namespace ptx {
+
+// Shared-memory matrix descriptor of a K-major operand: 8-row groups `sbo`
+// bytes apart, swizzle code 2 (128-byte), 4 (64-byte) or 6 (32-byte).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo, uint32_t swizzle)
+{
+    uint64_t d = 0;
+    d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= static_cast<uint64_t>(1u) << 16;                  // leading byte offset (unused within one atom)
+    d |= static_cast<uint64_t>(sbo >> 4) << 32;            // stride byte offset: next 8-row group
+    d |= static_cast<uint64_t>(1u) << 46;                  // descriptor version
+    d |= static_cast<uint64_t>(swizzle) << 61;
+    return d;
+}
+
+}  // namespace ptx
+}  // namespace leea
