@@ -274,8 +274,8 @@ def _gpu_id_for(dev: int) -> str | None:
 # --------------------------------------------------------------------------------
 def oracle_step_sample(parents64, f_adj64, x64, y, n_children: int, gen: int, seed: int = 0) -> float:
     """Rank + select all P children, then breed and evaluate `n_children` of
-    them (strided over elite, crossover and mutation children); returns the
-    CPU seconds taken."""
+    them (strided over elite, crossover and mutation children) in this
+    process; returns the CPU seconds taken."""
     import numpy as np
     import oracle
     prm = oracle.Params(**PARAMS)
@@ -288,6 +288,74 @@ def oracle_step_sample(parents64, f_adj64, x64, y, n_children: int, gen: int, se
     f, _ = oracle.evaluate(kids, DIMS, x64, y)
     oracle.inherit(float(prm.alpha), f_inh[rows], f, first=False)
     return time.perf_counter() - t0
+
+
+# The oracle on every host core: worker processes (started with spawn) each
+# breed and evaluate ranges of children with the unchanged oracle; the parents
+# sit in one shared-memory block, the minibatch and the operators are sent once.
+_ORACLE_POOL_STATE: dict = {}
+
+
+def _oracle_worker_init(shm_name, shape, dims, params, x64, y):
+    import numpy as np
+    from multiprocessing import shared_memory
+    import oracle
+    oracle.build()
+    # The creating process owns the block (and unlinks it); workers share its
+    # resource tracker, so mapping the block here registers nothing new.
+    shm = shared_memory.SharedMemory(name=shm_name)
+    _ORACLE_POOL_STATE.update(shm=shm, parents=np.ndarray(shape, dtype=np.float64, buffer=shm.buf), dims=dims,
+                              prm=oracle.Params(**params), x=x64, y=y)
+
+
+def _oracle_worker_task(task):
+    import oracle
+    j0, j1, seed, gen, p1, p2, kind = task
+    st = _ORACLE_POOL_STATE
+    kids = oracle.breed(st["prm"], st["dims"], seed, gen, st["parents"], p1, p2, kind, j0=j0, j1=j1)
+    f, _ = oracle.evaluate(kids, st["dims"], st["x"], st["y"])
+    return j0, f
+
+
+class OraclePool:
+    """Whole generations of the oracle spread over `workers` processes."""
+
+    def __init__(self, parents64, dims, params: dict, x64, y, workers: int | None = None):
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        import numpy as np
+        self.workers = workers or (len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count())
+        self.dims, self.params = list(dims), dict(params)
+        self.shm = shared_memory.SharedMemory(create=True, size=parents64.nbytes)
+        self.parents = np.ndarray(parents64.shape, dtype=np.float64, buffer=self.shm.buf)
+        self.parents[:] = parents64
+        self.pool = mp.get_context("spawn").Pool(
+            self.workers, initializer=_oracle_worker_init,
+            initargs=(self.shm.name, parents64.shape, self.dims, self.params, x64, y))
+
+    def generation(self, f_adj64, gen: int, seed: int = 0, chunk: int = 4) -> float:
+        """Rank + select in this process, then breed + evaluate every child on
+        the workers (tasks of `chunk` children, handed out as workers free up);
+        returns the wall-clock seconds of the generation."""
+        import numpy as np
+        import oracle
+        prm = oracle.Params(**self.params)
+        pop = len(f_adj64)
+        t0 = time.perf_counter()
+        order = oracle.rank(f_adj64)
+        p1, p2, kind, f_inh = oracle.select(prm, f_adj64, order, seed, gen)
+        tasks = [(j, min(pop, j + chunk), seed, gen, p1, p2, kind) for j in range(0, pop, chunk)]
+        f = np.empty(pop)
+        for j0, fj in self.pool.imap_unordered(_oracle_worker_task, tasks):
+            f[j0:j0 + len(fj)] = fj
+        self.last_f_adj = oracle.inherit(float(prm.alpha), f_inh, f, first=False)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        self.shm.close()
+        self.shm.unlink()
 
 
 def oracle_inputs(parents=None, f_adj=None):
@@ -304,14 +372,40 @@ def oracle_inputs(parents=None, f_adj=None):
     return parents.astype(np.float64), f_adj.astype(np.float64), x.astype(np.float64), y
 
 
-def cpu_baseline(parents=None, f_adj=None, n_children: int = 1000):
-    args = oracle_inputs(parents, f_adj)
-    secs = oracle_step_sample(*args, n_children=n_children, gen=1)
-    gen_per_s = (n_children / POP) / secs
-    return {"value": gen_per_s, "unit": "generations/s", "cores": 1, "kind": "oracle",
-            "sample": f"one generation's rank+select over all {POP} nets, breed+evaluate of {n_children} of the "
-                      f"{POP} children (strided), batch {BATCH}; value = ({n_children}/{POP}) / seconds",
-            "seconds": secs, "network_samples_per_sec": gen_per_s * POP * BATCH}
+def cpu_baseline(parents=None, f_adj=None, generations: int = 2) -> dict:
+    """The oracle (unchanged, FP64) on every host core: whole generations of
+    the benchmark workload, the workers started outside the timing."""
+    parents64, f_adj64, x64, y = oracle_inputs(parents, f_adj)
+    pool = OraclePool(parents64, DIMS, PARAMS, x64, y)
+    try:
+        pool.generation(f_adj64, gen=1)  # workers load the oracle
+        secs = [pool.generation(f_adj64, gen=2 + g) for g in range(generations)]
+    finally:
+        pool.close()
+    s = min(secs)
+    return {"value": 1.0 / s, "unit": "generations/s", "cores": pool.workers, "kind": "oracle",
+            "sample": f"whole generations ({POP} children bred and evaluated, batch {BATCH}) of the unchanged FP64 "
+                      f"oracle, children spread over {pool.workers} worker processes; best of {generations}",
+            "seconds": s, "network_samples_per_sec": POP * BATCH / s}
+
+
+def cpu_baseline_fp32(parents=None, f_adj=None, generations: int = 3) -> dict:
+    """The FP32 multi-core variant of the oracle (oracle/leea_cpu_fp32.c,
+    OpenMP over children and individuals): whole generations."""
+    import oracle
+    parents64, f_adj64, x64, y = oracle_inputs(parents, f_adj)
+    prm = oracle.Params(**PARAMS)
+    p32, f32, x32 = parents64.astype("float32"), f_adj64.astype("float32"), x64.astype("float32")
+    oracle.cpu32_generation(prm, DIMS, 0, 1, p32, f32, x32, y)  # warm-up (pages, threads)
+    secs, threads = [], 1
+    for g in range(generations):
+        t0 = time.perf_counter()
+        _, _, _, _, threads = oracle.cpu32_generation(prm, DIMS, 0, 2 + g, p32, f32, x32, y)
+        secs.append(time.perf_counter() - t0)
+    s = min(secs)
+    return {"value": 1.0 / s, "unit": "generations/s", "cores": threads, "kind": "fp32 OpenMP variant of the oracle",
+            "sample": f"whole generations ({POP} children, batch {BATCH}) in FP32 on {threads} threads; "
+                      f"best of {generations}", "seconds": s, "network_samples_per_sec": POP * BATCH / s}
 
 
 def precision_report(st, levels, y, precision: int, n: int = 64) -> dict:
@@ -359,11 +453,30 @@ def run_reference(args, rank: int, world: int):
     from paper_1806_09819_gb300 import synthetic
     oracle.build()
     if args.config == "plain":
-        inputs = oracle_inputs()
-        pop, batch, workload, metric = POP, BATCH, WORKLOAD, METRIC
-
-        def step(n, gen):
-            return oracle_step_sample(*inputs, n_children=n, gen=gen)
+        parents64, f_adj64, x64, y = oracle_inputs()
+        pool = OraclePool(parents64, DIMS, PARAMS, x64, y)
+        pool.generation(f_adj64, gen=1)  # the workers load the oracle outside the timing
+        try:
+            for w in range(args.warmup):
+                pool.generation(f_adj64, gen=2 + w)
+            secs = [pool.generation(f_adj64, gen=100 + k) for k in range(args.steps)]
+        finally:
+            pool.close()
+        total = sum(secs)
+        gen_per_s = args.steps / total
+        sample = (f"whole generations: rank+select of {POP} nets, breed+evaluate of all {POP} children (batch "
+                  f"{BATCH}) with the unchanged FP64 oracle over {pool.workers} worker processes")
+        line = {"impl": "reference", "metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "host CPU run"},
+                "cpu_baseline": {"value": gen_per_s, "unit": "generations/s", "cores": pool.workers, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": gen_per_s, "unit": "generations/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0},
+                "network_samples_per_sec": gen_per_s * POP * BATCH}
+        print(json.dumps(line), flush=True)
+        return
     elif args.config == "small":
         pop, batch, workload, metric = SMALL_POP, SMALL_BATCH, SMALL_WORKLOAD, SMALL_METRIC
         parents = synthetic.random_population(pop, oracle.num_params(SMALL_DIMS), seed=1, scale=0.05)
@@ -578,7 +691,7 @@ def run_paper_net(args, rank: int, world: int, local_rank: int):
         oracle.build()
         pooled_h = oracle.maxpool2x2(x_last, 28, 28) / 255.0
         line["cpu_baseline"] = paper_cpu_baseline(st.leea_get_population(), st.leea_fitness(), pooled_h,
-                                                  ytr[idx[warmup + steps]], n_children=min(args.cpu_children, 40))
+                                                  ytr[idx[warmup + steps]], n_children=40)
     st.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1130,7 +1243,8 @@ def run_native(args, rank: int, world: int, local_rank: int):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not precision:
         pop_now = st.leea_get_population()
         f_now = st.leea_fitness()
-        line["cpu_baseline"] = cpu_baseline(pop_now, f_now, n_children=args.cpu_children)
+        line["cpu_baseline"] = cpu_baseline(pop_now, f_now)
+        line["cpu_baseline_fp32"] = cpu_baseline_fp32(pop_now, f_now)
     st.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1144,7 +1258,6 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--cpu-children", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--eval-path", type=int, default=0,
                     help="0 auto (fused breed + evaluate where it applies), 1 CUDA-core FP32, 2 tensor cores as a "

@@ -575,3 +575,78 @@ def descriptors(prm: Params, dims, seed: int, gen: int, parents, f_adj, par1, pa
                                       _ptr(_f64(f_inh)), _ptr(_u32(entity)), n, _ptr(px), px.shape[0], _ptr(out)),
            "descriptors")
     return out
+
+
+# ---- the FP32 multi-core CPU baseline (leea_cpu_fp32.c) ----------------------
+_SRC32 = os.path.join(_HERE, "leea_cpu_fp32.c")
+_OUT32 = os.path.join(_HERE, "_build", "libleea_cpu32.so")
+_lib32 = None
+
+
+def build32(force: bool = False) -> str:
+    """Compile the FP32 baseline (OpenMP where gcc has it) with the oracle
+    linked in (its ranking, selection and Philox block).  The baseline's file
+    alone is compiled for speed; the oracle's keeps its own flags."""
+    os.makedirs(os.path.dirname(_OUT32), exist_ok=True)
+    newest = max(os.path.getmtime(_SRC32), os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    stamp_path = os.path.join(os.path.dirname(_OUT32), "STAMP32")
+    try:
+        with open(stamp_path) as fh:
+            same_host = fh.read() == platform.machine()
+    except OSError:
+        same_host = False
+    if force or not same_host or not os.path.exists(_OUT32) or os.path.getmtime(_OUT32) < newest:
+        bdir = os.path.dirname(_OUT32)
+        o_oracle = os.path.join(bdir, f"oracle32_{os.getpid()}.o")
+        o_fp32 = os.path.join(bdir, f"fp32_{os.getpid()}.o")
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fPIC", "-c", "-o", o_oracle, _SRC])
+        fast = ["-O3", "-fno-math-errno", "-fno-trapping-math", "-fno-signed-zeros", "-fassociative-math"]
+        omp = ["-fopenmp"]
+        try:
+            subprocess.check_call(["gcc", "-std=gnu99", *fast, *omp, "-fPIC", "-c", "-o", o_fp32, _SRC32])
+        except subprocess.CalledProcessError:
+            omp = []
+            subprocess.check_call(["gcc", "-std=gnu99", *fast, "-fPIC", "-c", "-o", o_fp32, _SRC32])
+        tmp = _OUT32 + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-shared", *omp, "-o", tmp, o_oracle, o_fp32, "-lm"])
+        os.replace(tmp, _OUT32)
+        for f in (o_oracle, o_fp32):
+            os.remove(f)
+        with open(stamp_path, "w") as fh:
+            fh.write(platform.machine())
+    return _OUT32
+
+
+def lib32() -> ctypes.CDLL:
+    global _lib32
+    if _lib32 is None:
+        L = ctypes.CDLL(build32())
+        vp, i32, u32, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64
+        L.leea_cpu32_threads.argtypes = []
+        L.leea_cpu32_threads.restype = ctypes.c_int
+        L.leea_cpu32_generation.argtypes = [i32, vp, i32, ctypes.POINTER(_CParams), u64, u32, vp, vp, vp, vp, i32,
+                                            vp, vp, vp, vp, vp]
+        L.leea_cpu32_generation.restype = ctypes.c_int
+        _lib32 = L
+    return _lib32
+
+
+def cpu32_generation(prm: Params, dims, seed: int, gen: int, parents, f_adj, x, y):
+    """One generation on every host core in FP32 (the CPU baseline): returns
+    (children float32[pop, c], f_raw, f_adj, correct, threads used)."""
+    d = _dims(dims)
+    pv = np.ascontiguousarray(np.asarray(parents, dtype=np.float32))
+    pop = pv.shape[0]
+    fa = np.ascontiguousarray(np.asarray(f_adj, dtype=np.float32))
+    xv = np.ascontiguousarray(np.asarray(x, dtype=np.float32)).reshape(-1, int(d[0]))
+    yv = _i32(y)
+    kids = np.empty_like(pv)
+    f_raw = np.empty(pop, dtype=np.float32)
+    f_out = np.empty(pop, dtype=np.float32)
+    cor = np.empty(pop, dtype=np.int32)
+    thr = ctypes.c_int32(0)
+    cp = _cparams(prm)
+    _check(lib32().leea_cpu32_generation(pop, _ptr(d), len(d), ctypes.byref(cp), seed, gen, _ptr(pv), _ptr(fa),
+                                         _ptr(xv), _ptr(yv), xv.shape[0], _ptr(kids), _ptr(f_raw), _ptr(f_out),
+                                         _ptr(cor), ctypes.byref(thr)), "cpu32_generation")
+    return kids, f_raw, f_out, cor, int(thr.value)

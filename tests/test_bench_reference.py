@@ -31,3 +31,33 @@ def test_reference_arm_small_configuration():
 def test_reference_arm_names_what_it_does_not_cover():
     line = _run("--config", "batching", "--steps", "3", "--warmup", "3")
     assert line["impl"] == "reference" and "batching" in line["unavailable"]
+
+
+def test_oracle_pool_generation_equals_the_serial_oracle(oracle_mod):
+    # The oracle spread over worker processes computes exactly what one
+    # process computes: the same FP64 code on the same children.
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1806_09819_gb300 import synthetic
+    dims, pop, batch = [40, 16, 10], 30, 12
+    params = dict(bench.PARAMS, alpha=0.5)
+    c = oracle_mod.num_params(dims)
+    parents = synthetic.random_population(pop, c, seed=8, scale=0.2).astype(np.float64)
+    f_adj = np.random.default_rng(9).normal(-2.3, 0.1, size=pop)
+    rng = np.random.default_rng(10)
+    x = rng.uniform(0, 1, size=(batch, dims[0]))
+    y = rng.integers(0, dims[-1], size=batch).astype(np.int32)
+    pool = bench.OraclePool(parents, dims, params, x, y, workers=2)
+    try:
+        secs = pool.generation(f_adj, gen=5, seed=3, chunk=4)
+    finally:
+        pool.close()
+    assert secs > 0
+    prm = oracle_mod.Params(**params)
+    order = oracle_mod.rank(f_adj)
+    p1, p2, kind, f_inh = oracle_mod.select(prm, f_adj, order, 3, 5)
+    kids = oracle_mod.breed(prm, dims, 3, 5, parents, p1, p2, kind)
+    f, _ = oracle_mod.evaluate(kids, dims, x, y)
+    want = oracle_mod.inherit(float(prm.alpha), f_inh, f, first=False)
+    np.testing.assert_array_equal(pool.last_f_adj, want)
