@@ -108,8 +108,8 @@ STAGES = ("select", "breed", "evaluate")
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 TRAFFIC = {
-    "breed": {"bytes_per_launch": 707.47e6, "src_sha": "c8e7e85a0e65db99", "capture": "P=1000 plain workload"},
-    "evaluate": {"bytes_per_launch": 359.45e6, "src_sha": "d972b174f2e01544", "capture": "P=1000 plain workload"},
+    "breed": {"bytes_per_launch": 472.52e6, "src_sha": "641fc663c50d3438", "capture": "P=1000 plain workload"},
+    "evaluate": {"bytes_per_launch": 369.34e6, "src_sha": "3a95c7a5d4372dc7", "capture": "P=1000 plain workload"},
     "breed_evaluate": {"bytes_per_launch": 738.19e6, "src_sha": "23e25d83744d9797", "capture": "P=1000 plain workload"},
     # eval_mlp_tc_kernel alone (each individual's weight pieces read once from
     # DRAM, the other tiles from L2); the stage also splits the weights
