@@ -176,8 +176,8 @@ PROFILE_EVERY = 8  # generations per profiled one inside the timed region
 def kernels_per_generation(pop: int, batch: int, precision: int, fused: bool = False, x16: bool = False) -> dict:
     """Kernel launches per stage of one state-object generation: ranking and
     selection run as one kernel below 512 nets and as two above (plus the
-    kernel that stages the batch as FP16 for the FP32 tensor-core evaluation
-    of 8-bit inputs, x16); breeding and evaluation are one fused kernel on the
+    kernel that stages the batch as operand tiles for the tensor-core
+    evaluations of 8-bit inputs, x16); breeding and evaluation are one fused kernel on the
     8-bit FP32 path, else two; the shadow evaluation adds a combining kernel
     when the batch spans several 128-sample tiles."""
     sel = (2 if pop >= 512 else 1) + (1 if x16 else 0)
@@ -1211,7 +1211,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
     if (pop, batch) != (cfg["pop"], cfg["batch"]):
         workload = f"PROFILING OVERRIDE P={pop}, batch {batch} (not the benchmark workload): " + workload
     eval_kernel = ("tcgen05 " + {1: "kind::f16 on BF16 shadows", 2: "kind::f8f6f4 on FP8 shadows, 2 input pieces"}[
-        precision] + ", batch in TMEM" if precision else
+        precision] + ", two individuals per MMA (N = 2h), batch tile from shared memory" if precision else
                    (("tcgen05 kind::f16, two individuals per MMA (N = 2h), W1 as two FP16 pieces of 2^8 w "
                      "(22-bit significands, exact products, FP32 accumulation)" if u8 else "tcgen05 3xTF32")
                     if tensor_eval else "CUDA-core FP32 FFMA"))
@@ -1231,7 +1231,7 @@ def run_native(args, rank: int, world: int, local_rank: int):
             "network_samples_per_sec": gen_per_s * pop * batch,
             "e2e": e2e,
             "gpu_launches": int(steps * sum(kernels_per_generation(
-                pop, batch, precision, fused, x16=u8 and tensor_eval and precision == 0 and not fused).values())),
+                pop, batch, precision, fused, x16=(u8 and tensor_eval and not fused) or precision > 0).values())),
             "roofline": roofline,
             "kernels": kernels, "clocks": clk}
     if precision and rank == 0:

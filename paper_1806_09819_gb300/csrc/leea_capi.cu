@@ -772,6 +772,9 @@ struct leea_state {
     // tensor-core evaluation of d_0-h-d_out nets on 8-bit inputs: the batch as
     // FP16 (at most 128 samples), staged once per generation
     void* x16;
+    // precision form: the batch as the pair kernel's operand tiles (grown with the batch)
+    void* xop;
+    size_t xop_bytes;
 };
 
 namespace {
@@ -801,6 +804,7 @@ void free_state(leea_state* s)
     cudaFree(s->sigma[1]);
     cudaFree(s->mlp_scratch);
     cudaFree(s->x16);
+    cudaFree(s->xop);
     if (s->prof) {
         if (s->prof->created)
             for (int st = 0; st < LEEA_NUM_STAGES; ++st)
@@ -984,6 +988,20 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
             s->scratch_bytes = need;
         }
     }
+    // The precision form's evaluation: two individuals per MMA where the
+    // shape allows, on the batch staged as operand tiles.
+    const bool shadow_pair = prec != 0 && eval_shadow_pair_supported(s->net, prec, batch);
+    if (shadow_pair) {
+        const size_t need = eval_shadow_pair_xop_bytes(s->net, prec, batch);
+        if (need > s->xop_bytes) {
+            LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "staging sync");
+            cudaFree(s->xop);
+            s->xop = nullptr;
+            s->xop_bytes = 0;
+            LEEA_CUDA_TRY(cudaMalloc(&s->xop, need), "batch staging allocation");
+            s->xop_bytes = need;
+        }
+    }
     if (u8 && s->mlp_scratch) {
         const size_t need = eval_mlp_tc_scratch_bytes(s->net, s->pop, batch);
         if (need > s->mlp_scratch_bytes) {
@@ -1034,6 +1052,10 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
             if (stage_early)  // runs beside the selection; the breed that follows waits for both
                 LEEA_CUDA_TRY(launch_stage_x16(s->net, static_cast<const uint8_t*>(x_dev), batch, s->x16, s->stream),
                               "batch staging kernel");
+            if (shadow_pair && !fused)
+                LEEA_CUDA_TRY(launch_stage_xop(s->net, prec, static_cast<const uint8_t*>(x_dev), batch, s->xop,
+                                               s->stream),
+                              "batch staging kernel");
             sc.done();
         }
         if (fused) {
@@ -1080,7 +1102,19 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
     }
     {
         StageScope sc(s, 2);
-        if (prec != 0)
+        if (shadow_pair) {
+            unsigned int* status = device_status_ptr();
+            if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+            if (first)
+                LEEA_CUDA_TRY(launch_stage_xop(s->net, prec, static_cast<const uint8_t*>(x_dev), batch, s->xop,
+                                               s->stream),
+                              "batch staging kernel");
+            LEEA_CUDA_TRY(launch_eval_shadow_pair(s->net, s->pop, s->popbuf[s->cur], prec, s->shadow[s->cur],
+                                                  s->sh_stride, s->scale_exp, s->xop, x_div, y_dev, batch,
+                                                  s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj,
+                                                  s->correct, s->scratch, status, s->stream),
+                          "shadow evaluation kernel");
+        } else if (prec != 0)
             st = dispatch_eval_shadow(s->net, s->pop, s->popbuf[s->cur], prec, s->shadow[s->cur], s->scale_exp,
                                       static_cast<const uint8_t*>(x_dev), x_div, y_dev, batch, s->prm.alpha,
                                       first ? nullptr : s->f_inh, s->f_raw, s->f_adj, s->correct, s->scratch,

@@ -459,16 +459,19 @@ eval_u8_kernel(const __grid_constant__ CUtensorMap tmap_w, const __grid_constant
                 // While this unit's MMAs run: b1, W2 transposed (rows padded to
                 // dpad with zeros) and b2 of this slot's individual, as stored
                 // after W1, into shared memory.  The group finished reading the
-                // previous ones at its barrier B.
+                // previous ones at its barrier B.  Loads go through L2
+                // (ld.global.cg), not the read-only path: this grid starts while
+                // the breeding kernel that writes the masters still runs, and the
+                // read-only path assumes data no grid changes during the kernel.
                 const float* src = a.popv + static_cast<int64_t>(p) * a.c_pad + static_cast<int64_t>(a.h) * a.k;
-                for (int i = et; i < a.h; i += 128) b1s[i] = __ldg(src + i);
+                for (int i = et; i < a.h; i += 128) b1s[i] = __ldcg(src + i);
                 for (int i = et; i < a.d_out * a.h; i += 128) {
                     const int o = i / a.h, col = i - o * a.h;
-                    w2t[col * a.dpad + o] = __ldg(src + a.h + i);
+                    w2t[col * a.dpad + o] = __ldcg(src + a.h + i);
                 }
                 const int pad = a.dpad - a.d_out;
                 for (int i = et; i < a.h * pad; i += 128) w2t[(i / pad) * a.dpad + a.d_out + i % pad] = 0.0f;
-                if (et < 16) b2s[et] = et < a.d_out ? __ldg(src + a.h + a.d_out * a.h + et) : 0.0f;
+                if (et < 16) b2s[et] = et < a.d_out ? __ldcg(src + a.h + a.d_out * a.h + et) : 0.0f;
             }
             if (et == 0) {
                 const bool got = ptx::mbar_wait_bounded(&s.acc_full[buf], bph, s.abort_flag, kWaitLimitNs);

@@ -185,6 +185,20 @@ struct ShadowSeg {
     int32_t run, mt, p0, p1;
 };
 bool eval_shadow_supported(const NetLayout& net, int32_t precision, int32_t batch);
+// The state object's shadow evaluation, two individuals per MMA (h <= 128,
+// d_0 % 16 == 0, d_out <= 16): the batch staged by launch_stage_xop into
+// xop (eval_shadow_pair_xop_bytes, 16-byte aligned) earlier on the stream;
+// scratch as eval_shadow_scratch_bytes when the batch spans several
+// 128-sample tiles.
+bool eval_shadow_pair_supported(const NetLayout& net, int32_t precision, int32_t batch);
+size_t eval_shadow_pair_xop_bytes(const NetLayout& net, int32_t precision, int32_t batch);
+cudaError_t launch_stage_xop(const NetLayout& net, int32_t precision, const uint8_t* x, int32_t batch, void* xop,
+                             cudaStream_t stream);
+cudaError_t launch_eval_shadow_pair(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
+                                    const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp,
+                                    const void* xop, float x_div, const int32_t* y, int32_t batch, float alpha,
+                                    const float* f_inh, float* f_raw, float* f_adj, int32_t* correct, float* scratch,
+                                    unsigned int* status, cudaStream_t stream);
 size_t eval_shadow_scratch_bytes(int32_t pop, int32_t batch);
 // Widest hidden chunk the tensor memory leaves room for next to the batch tile.
 int32_t eval_shadow_max_chunk(int32_t precision, int32_t k);

@@ -399,3 +399,21 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t sbo, uint
 
 }  // namespace ptx
 }  // namespace leea
+
+namespace leea {
+namespace ptx {
+
+// tcgen05.mma kind::f8f6f4 with both operands in shared memory.
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+}  // namespace ptx
+}  // namespace leea
