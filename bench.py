@@ -889,6 +889,7 @@ def run_batching(args, rank: int, world: int, local_rank: int):
         m.generation_u8(xd[k % n_pool], yd[k % n_pool])
     prof = m.profile_read()
     m.profile_enable(False)
+    eval_launches = m.eval_launches()
 
     # end to end: packed host minibatch in, packed fitness out
     e2e_steps = max(10, min(steps, 500))
@@ -913,7 +914,7 @@ def run_batching(args, rank: int, world: int, local_rank: int):
         c = leea.leea_layout_num_params(dims)
         n_e, n_c, n_m, _ = leea.leea_counts(sp.pop, leea.Params(**PARAMS))
         shadow = DIMS[0] * sp.hidden * 2
-        breed_b += 4.0 * c * (2 * n_e + 3 * n_c + 2 * n_m) + shadow * sp.pop
+        breed_b += (8.0 * c + shadow) * (n_e + n_c + n_m)  # one read and one write per gene, the shadow written
         evaluate_b += (shadow + 4.0 * (c - DIMS[0] * sp.hidden)) * sp.pop
     work = {"breed": breed_b / 1e9, "evaluate": evaluate_b / 1e9}
     kernels = {}
@@ -937,7 +938,7 @@ def run_batching(args, rank: int, world: int, local_rank: int):
                                 for sp in specs],
                        "l2": "inputs larger than L2 (populations of all runs, 2 buffers), no flush"},
             "network_samples_per_sec": gen_per_s / n_runs * samples_per_gen,
-            "e2e": e2e, "gpu_launches": int(sum(v[1] for v in prof.values()) + prof_steps),
+            "e2e": e2e, "gpu_launches": int(steps * (3 + eval_launches)),  # generation bump, select, breed, evaluation
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": kd["achieved"], "peak": kd["peak"],
                          "unit": "GB/s", "frac": kd["frac"], "traffic": None,
                          "peak_source": f"{peak_src} (HBM copy)"},

@@ -552,6 +552,13 @@ leea_status leea_multi_layout(const leea_multi* m, int64_t* batch_off, int64_t* 
 leea_status leea_multi_run_shape(const leea_multi* m, int32_t run, int32_t* chunk, int32_t* n_chunks,
                                  int32_t* m_tiles);
 
+/* Kernels one evaluation of all runs launches (a stage of
+ * leea_multi_profile_read): 2 when every run takes the group evaluation
+ * (several individuals per MMA: the batch staging, then the evaluation), 1
+ * when the chunked evaluation is used; plus 1 (the combine of per-tile sums)
+ * when some run's batch spans several 128-sample tiles. */
+leea_status leea_multi_eval_launches(const leea_multi* m, int32_t* launches);
+
 /* The object's own packed minibatch buffers.  A caller that writes the next
  * minibatch there (on the object's stream) saves the copy of
  * leea_multi_generation_u8. */

@@ -751,6 +751,15 @@ cudaError_t launch_eval_shadow(const NetLayout& net, int32_t pop, const float* p
     return launch(a, precision, r.h, r.cw, groups * r.m_tiles, 1, pop, r.m_tiles > 1, stream);
 }
 
+cudaError_t launch_combine_shadow_tiles(const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max,
+                                        cudaStream_t stream)
+{
+    EvalShArgs a{};
+    a.runs = runs_dev;
+    combine_tiles_kernel<<<dim3((pop_max + 255) / 256, n_runs), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eval_shadow_runs(int32_t k, int32_t d_out, int32_t precision, int32_t h_max, int32_t cw_max,
                                     int32_t n_runs, int32_t pop_max, bool any_tiles, const ShadowRun* runs_dev,
                                     const ShadowSeg* segs_dev, const int32_t* seg_off_dev, int32_t grid,

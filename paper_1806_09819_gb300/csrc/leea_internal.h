@@ -179,6 +179,10 @@ struct ShadowRun {
     float* f_adj;
     int32_t* correct;
     float* scratch;  // m_tiles > 1: 2 m_tiles pop floats of per-tile partial sums
+    // The group evaluation (batching form): the batch staged as operand tiles,
+    // [m_tiles][k_blocks][pieces][128 rows][128 B], and individuals per MMA.
+    const uint8_t* xop;
+    int32_t group;
 };
 // Individuals [p0, p1) of run `run` on its 128-sample tile mt.
 struct ShadowSeg {
@@ -200,6 +204,27 @@ cudaError_t launch_eval_shadow_pair(const NetLayout& net, int32_t pop, const flo
                                     const float* f_inh, float* f_raw, float* f_adj, int32_t* correct, float* scratch,
                                     unsigned int* status, cudaStream_t stream);
 size_t eval_shadow_scratch_bytes(int32_t pop, int32_t batch);
+// Sums each run's per-tile partial losses (runs with m_tiles > 1) in tile order.
+cudaError_t launch_combine_shadow_tiles(const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max,
+                                        cudaStream_t stream);
+// The batching form's evaluation over a table of runs (h <= 256, h % 16 == 0,
+// d_0 % 16 == 0, d_out <= 16): group = eval_shadow_group_size(h) individuals
+// share every MMA (N = group h <= 256); each run's batch staged into its xop
+// by launch_stage_xop_tiles earlier on the stream.
+struct XopTile {
+    const uint8_t* x;  // the tile's first sample (8-bit levels, d_0 per sample)
+    int32_t rows;      // samples of the tile (1 .. 128); the rest are zero
+    uint8_t* dst;      // [k_blocks][pieces][128 rows][128 B]
+};
+int32_t eval_shadow_group_size(int32_t h);
+bool eval_shadow_group_supported(int32_t k, int32_t d_out, int32_t precision, int32_t h, int32_t n_max);
+size_t eval_shadow_group_xop_bytes(int32_t k, int32_t precision, int32_t batch);
+cudaError_t launch_stage_xop_tiles(const XopTile* tiles_dev, int32_t n_tiles, int32_t k, int32_t precision,
+                                   cudaStream_t stream);
+cudaError_t launch_eval_shadow_group(int32_t k, int32_t d_out, int32_t precision, int32_t n_max,
+                                     const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max, bool any_tiles,
+                                     const ShadowSeg* segs_dev, const int32_t* seg_off_dev, int32_t grid,
+                                     unsigned int* status, cudaStream_t stream);
 // Widest hidden chunk the tensor memory leaves room for next to the batch tile.
 int32_t eval_shadow_max_chunk(int32_t precision, int32_t k);
 // chunk: hidden units per chunk (multiple of 16), 0 for the widest.

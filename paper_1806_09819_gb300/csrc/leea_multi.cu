@@ -9,6 +9,7 @@
 // advances, so a replay needs no new arguments.
 #include "capi_common.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -24,6 +25,8 @@ struct RunBuf {
     uint64_t seed = 0;
     NetLayout net{};
     int32_t m_tiles = 1, cw = 0, n_chunks = 1;
+    int32_t group = 1;      // individuals per MMA in the group evaluation
+    int64_t xop_off = 0;    // its staged batch tiles within leea_multi::xop
     int64_t batch_off = 0, pop_off = 0, sh_stride = 0;
     float* popbuf[2] = { nullptr, nullptr };
     uint8_t* shadow[2] = { nullptr, nullptr };
@@ -47,6 +50,13 @@ struct leea_multi {
     int64_t total_rows = 0, total_pop = 0, breed_items = 0;
     int32_t h_max = 0, cw_max = 0, pop_max = 0, eval_grid = 0;
     bool any_tiles = false;
+    // The group evaluation (several individuals per MMA) when every run fits
+    // it, else the chunked kernel; its batch tiles, restaged every evaluation.
+    bool grouped = false;
+    int32_t n_max = 0;  // widest unit: max over runs of group h
+    uint8_t* xop = nullptr;
+    XopTile* xtiles = nullptr;
+    int32_t n_xtiles = 0;
     float *f_adj = nullptr, *f_raw = nullptr, *f_inh = nullptr;  // packed over the runs
     int32_t* correct = nullptr;
     uint8_t* x = nullptr;  // packed minibatch: the graph's fixed inputs
@@ -95,6 +105,8 @@ void free_multi(leea_multi* m)
     cudaFree(m->correct);
     cudaFree(m->x);
     cudaFree(m->y);
+    cudaFree(m->xop);
+    cudaFree(m->xtiles);
     cudaFree(m->gen_dev);
     for (int c = 0; c < 2; ++c) {
         cudaFree(m->sel_tab[c]);
@@ -137,6 +149,8 @@ cudaError_t build_eval_table(leea_multi* m, int which, float x_div)
                             m->x + r.batch_off * m->d_in, x_div, m->y + r.batch_off, r.batch, m->prm.alpha,
                             which == 0 ? nullptr : m->f_inh + r.pop_off, m->f_raw + r.pop_off,
                             m->f_adj + r.pop_off, m->correct + r.pop_off, r.scratch, r.cw);
+        tab[i].xop = m->grouped ? m->xop + r.xop_off : nullptr;
+        tab[i].group = r.group;
     }
     return upload(&m->eval_tab[which], tab);
 }
@@ -190,8 +204,9 @@ cudaError_t build_step_tables(leea_multi* m, int c)
 }
 
 // Splits the evaluation work -- (run, tile, individual) units in that order,
-// each costing about its number of hidden chunks -- into `grid` contiguous
-// ranges of equal cost, one per CTA, cut into segments at run and tile edges.
+// each costing about its number of hidden chunks (chunked kernel) or 1/group
+// of a pass over K (group kernel) -- into `grid` contiguous ranges of equal
+// cost, one per CTA, cut into segments at run and tile edges.
 cudaError_t build_segments(leea_multi* m, int grid)
 {
     struct Block { int32_t run, mt, pop; double cost; };
@@ -200,8 +215,9 @@ cudaError_t build_segments(leea_multi* m, int grid)
     for (int32_t i = 0; i < m->n_runs; ++i) {
         const RunBuf& r = m->runs[i];
         for (int32_t mt = 0; mt < r.m_tiles; ++mt) {
-            blocks.push_back(Block{ i, mt, r.pop, r.n_chunks + 0.25 });
-            total += r.pop * (r.n_chunks + 0.25);
+            const double cost = m->grouped ? 1.0 / r.group : r.n_chunks + 0.25;
+            blocks.push_back(Block{ i, mt, r.pop, cost });
+            total += r.pop * cost;
         }
     }
     std::vector<ShadowSeg> segs;
@@ -250,6 +266,12 @@ leea_status set_x_div(leea_multi* m, float x_div)
 
 cudaError_t launch_eval(leea_multi* m, int which, unsigned int* status, cudaStream_t stream)
 {
+    if (m->grouped) {
+        cudaError_t err = launch_stage_xop_tiles(m->xtiles, m->n_xtiles, m->d_in, m->prm.precision, stream);
+        if (err != cudaSuccess) return err;
+        return launch_eval_shadow_group(m->d_in, m->d_out, m->prm.precision, m->n_max, m->eval_tab[which], m->n_runs,
+                                        m->pop_max, m->any_tiles, m->segs, m->seg_off, m->eval_grid, status, stream);
+    }
     return launch_eval_shadow_runs(m->d_in, m->d_out, m->prm.precision, m->h_max, m->cw_max, m->n_runs, m->pop_max,
                                    m->any_tiles, m->eval_tab[which], m->segs, m->seg_off, m->eval_grid, status,
                                    stream);
@@ -420,6 +442,19 @@ leea_status leea_multi_create(int32_t n_runs, const leea_run_spec* specs, int32_
         m->cw_max = r.cw > m->cw_max ? r.cw : m->cw_max;
         m->pop_max = r.pop > m->pop_max ? r.pop : m->pop_max;
         m->any_tiles = m->any_tiles || r.m_tiles > 1;
+        r.group = eval_shadow_group_size(r.h);
+        m->n_max = r.group * r.h > m->n_max ? r.group * r.h : m->n_max;
+    }
+    m->grouped = true;
+    for (int32_t i = 0; i < n_runs; ++i)
+        m->grouped = m->grouped && eval_shadow_group_supported(d_in, d_out, p->precision, m->runs[i].h, m->n_max);
+    int64_t xop_bytes = 0;
+    if (m->grouped) {
+        for (int32_t i = 0; i < n_runs; ++i) {
+            RunBuf& r = m->runs[i];
+            r.xop_off = xop_bytes;
+            xop_bytes += static_cast<int64_t>(eval_shadow_group_xop_bytes(d_in, p->precision, r.batch));
+        }
     }
     cudaError_t err = cudaSuccess;
     for (int32_t i = 0; i < n_runs && err == cudaSuccess; ++i) {
@@ -443,6 +478,20 @@ leea_status leea_multi_create(int32_t n_runs, const leea_run_spec* specs, int32_
     if (err == cudaSuccess) err = alloc(&m->x, static_cast<size_t>(m->total_rows) * d_in);
     if (err == cudaSuccess) err = alloc(&m->y, m->total_rows);
     if (err == cudaSuccess) err = alloc(&m->gen_dev, 1);
+    if (err == cudaSuccess && m->grouped) {
+        err = alloc(&m->xop, static_cast<size_t>(xop_bytes));
+        // one staging tile per (run, 128-sample tile)
+        const int64_t tile_bytes = static_cast<int64_t>(eval_shadow_group_xop_bytes(d_in, p->precision, 1));
+        std::vector<XopTile> xt;
+        for (int32_t i = 0; i < n_runs; ++i) {
+            const RunBuf& r = m->runs[i];
+            for (int32_t mt = 0; mt < r.m_tiles; ++mt)
+                xt.push_back(XopTile{ m->x + (r.batch_off + 128 * mt) * d_in, std::min(128, r.batch - 128 * mt),
+                                      m->xop + r.xop_off + mt * tile_bytes });
+        }
+        m->n_xtiles = static_cast<int32_t>(xt.size());
+        if (err == cudaSuccess) err = upload(&m->xtiles, xt);
+    }
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking);
     if (err != cudaSuccess) {
         free_multi(m);
@@ -499,6 +548,15 @@ leea_status leea_multi_run_shape(const leea_multi* m, int32_t run, int32_t* chun
     if (chunk) *chunk = m->runs[run].cw;
     if (n_chunks) *n_chunks = m->runs[run].n_chunks;
     if (m_tiles) *m_tiles = m->runs[run].m_tiles;
+    return LEEA_OK;
+}
+
+leea_status leea_multi_eval_launches(const leea_multi* m, int32_t* launches)
+{
+    leea_status st = check_multi(m);
+    if (st) return st;
+    if (!launches) return fail(LEEA_EINVAL, "launches is NULL");
+    *launches = (m->grouped ? 2 : 1) + (m->any_tiles ? 1 : 0);
     return LEEA_OK;
 }
 

@@ -148,6 +148,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_multi_create": [i32, vp, i32, i32, P(leea_params), vp, P(vp)],
         "leea_multi_layout": [vp, vp, vp, vp, vp],
         "leea_multi_run_shape": [vp, i32, vp, vp, vp],
+        "leea_multi_eval_launches": [vp, vp],
         "leea_multi_batch_buffers": [vp, P(vp), P(vp)],
         "leea_multi_generation_u8": [vp, vp, f32, vp],
         "leea_multi_generation_u8_host": [vp, vp, f32, vp],
@@ -223,7 +224,8 @@ def exported_symbols() -> list[str]:
             "leea_profile_enable", "leea_profile_read", "leea_last_error", "leea_destroy",
             "leea_shadow_stride", "leea_make_shadow", "leea_shadow_scratch_bytes", "leea_evaluate_shadow_u8",
             "leea_get_shadow", "leea_evaluate_shadow_u8_noalloc",
-            "leea_multi_create", "leea_multi_layout", "leea_multi_run_shape", "leea_multi_batch_buffers",
+            "leea_multi_create", "leea_multi_layout", "leea_multi_run_shape", "leea_multi_eval_launches",
+            "leea_multi_batch_buffers",
             "leea_multi_generation_u8", "leea_multi_generation_u8_host", "leea_multi_fitness",
             "leea_multi_raw_fitness", "leea_multi_get_population", "leea_multi_set_population",
             "leea_multi_set_fitness", "leea_multi_set_generation", "leea_multi_get_selection",
@@ -616,6 +618,12 @@ class MultiRun:
         v = [ctypes.c_int32() for _ in range(3)]
         _check(self.lib.leea_multi_run_shape(self._h, run, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
+
+    def eval_launches(self) -> int:
+        """Kernels one evaluation of all runs launches."""
+        v = ctypes.c_int32()
+        _check(self.lib.leea_multi_eval_launches(self._h, ctypes.byref(v)))
+        return int(v.value)
 
     def batch_buffers(self):
         x, y = ctypes.c_void_p(), ctypes.c_void_p()
