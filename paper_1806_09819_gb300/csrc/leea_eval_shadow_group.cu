@@ -12,8 +12,13 @@
 // L2.  An individual of h up to 256 thus needs one pass over K (the chunked
 // kernel, whose batch tile sits in TMEM, needs up to three).
 //
-// Work: one launch over a table of runs; CTA b walks its segments (run,
-// sample tile, individuals [p0, p1)) in units of at most `group` individuals.
+// Work: one launch over a table of runs and a table of units (at most
+// `group` individuals of a run on one sample tile, the tiles of a group
+// next to each other so that the second tile finds the shadows in L2).
+// CTAs take units dynamically: the shadow producer's lane 0 claims the next
+// unit index with an atomic add, one unit ahead of its own work, and hands
+// it to the CTA's other roles through a ring of unit slots in shared memory
+// (each slot with a full and an empty mbarrier).
 // Warp roles (one CTA per SM):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
 //   warp 1      shadow producer: lane j copies individual j's block of each
@@ -62,6 +67,8 @@ constexpr int kMaxGroup = 16;  // individuals of one unit (h >= 16)
 constexpr int kMaxSplit = 2;   // units of at most this many individuals split each one's chains
 constexpr int kPrmRegs = 9;    // b1, W2, b2 floats per epilogue thread: ceil((256 (1 + 16) + 16 16) / 512)
 constexpr int kFullArrivals = 33;  // the shadow producer's 32 lanes and the batch producer
+constexpr int kURing = 8;          // unit slots
+constexpr int kUnitReaders = 3;    // the MMA thread, the batch producer, the epilogue
 constexpr int kMinStages = 2;
 constexpr int kMaxStages = 6;
 constexpr uint32_t kBlockBytes = 128u * 128u;  // a 128-row operand block of 128-byte rows
@@ -74,8 +81,9 @@ struct GroupArgs {
     int32_t k, d_out, dpad, k_blocks, k_mma, n_stages;
     uint32_t a_bytes, stage_bytes;
     const ShadowRun* runs;
-    const ShadowSeg* segs;     // CTA b walks segs[seg_off[b] .. seg_off[b + 1])
-    const int32_t* seg_off;
+    const GroupUnit* units;
+    int32_t n_units;
+    int32_t* sched;  // [0] next unit, [1] CTAs that found no more
     unsigned int* status;
 };
 
@@ -88,16 +96,19 @@ struct GroupSmem {
     float* red_loss;     // [kMaxGroup][4]
     int32_t* red_ok;     // [kMaxGroup][4]
     int* ep_go;
+    int32_t* ep_next;    // [2]: the epilogue's unit indices, slot = unit parity
+    int32_t* uidx;       // [kURing] unit slots
     uint32_t* tmem_holder;
     volatile int* abort_flag;
-    uint64_t *full, *empty, *acc_full, *acc_empty, *drain;
+    uint64_t *full, *empty, *acc_full, *acc_empty, *drain, *ufull, *uempty;
 };
 
 size_t group_tail_bytes(int32_t dpad, int32_t n_stages)
 {
     return sizeof(float) * (static_cast<size_t>(kMaxN) * dpad + kMaxN + kMaxGroup * 16 +
                             static_cast<size_t>(kMaxSplit) * 128 * 2 * dpad + kMaxGroup * 4) +
-           sizeof(int32_t) * kMaxGroup * 4 + 32u + 8u * (2u * n_stages + 5u) + 64u;
+           sizeof(int32_t) * kMaxGroup * 4 + 48u + sizeof(int32_t) * kURing + 8u * (2u * n_stages + 5u + 2u * kURing) +
+           64u;
 }
 
 uint32_t group_stage_bytes(int32_t precision, int32_t n_max)
@@ -140,7 +151,10 @@ __device__ __forceinline__ GroupSmem carve(uint8_t* raw, const GroupArgs& a)
     s.ep_go = reinterpret_cast<int*>(p);
     s.tmem_holder = reinterpret_cast<uint32_t*>(p + 4);
     s.abort_flag = reinterpret_cast<volatile int*>(p + 8);
-    p += 16;
+    s.ep_next = reinterpret_cast<int32_t*>(p + 12);
+    p += 32;
+    s.uidx = reinterpret_cast<int32_t*>(p);
+    p += sizeof(int32_t) * kURing;
     p = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 7u) & ~uintptr_t(7));
     uint64_t* bars = reinterpret_cast<uint64_t*>(p);
     s.full = bars;
@@ -148,6 +162,8 @@ __device__ __forceinline__ GroupSmem carve(uint8_t* raw, const GroupArgs& a)
     s.acc_full = bars + 2 * a.n_stages;
     s.acc_empty = s.acc_full + 2;
     s.drain = s.acc_empty + 2;
+    s.ufull = s.drain + 1;
+    s.uempty = s.ufull + kURing;
     return s;
 }
 
@@ -157,37 +173,34 @@ __device__ __forceinline__ void raise_abort(const GroupSmem& s, const GroupArgs&
     atomicOr(a.status, kStatusEvalTimeout);
 }
 
-// One unit: individuals [p, p + n) of run `run` on its sample tile mt.
-struct Unit {
-    int32_t run, mt, p, n;
-};
-struct Cursor {
-    int32_t s, s_end, p;  // segment, end of this CTA's segments, next individual (-1: segment start)
-};
-
-__device__ __forceinline__ Cursor first_cursor(const GroupArgs& a)
+// The index of unit ui of this CTA (-1: no more), from the ring; false when
+// the wait gives up.  Each reader releases the slot once it has the index.
+__device__ __forceinline__ bool take_unit(const GroupSmem& s, uint32_t ui, int32_t& idx)
 {
-    return Cursor{ a.seg_off[blockIdx.x], a.seg_off[blockIdx.x + 1], -1 };
+    const uint32_t slot = ui % kURing;
+    if (!ptx::mbar_wait_bounded(&s.ufull[slot], (ui / kURing) & 1u, s.abort_flag, kWaitLimitNs)) return false;
+    idx = s.uidx[slot];
+    ptx::mbar_arrive(&s.uempty[slot]);
+    return true;
 }
 
-// The same sequence for every role of the CTA.
-__device__ __forceinline__ bool next_unit(const GroupArgs& a, Cursor& c, Unit& u)
+// Claims the CTA's unit ui and publishes its index; the CTA that is last to
+// find the table exhausted leaves the counters at zero for the next launch.
+__device__ __forceinline__ bool publish_unit(const GroupSmem& s, const GroupArgs& a, uint32_t ui, int32_t& idx)
 {
-    while (c.s < c.s_end) {
-        const ShadowSeg sg = a.segs[c.s];
-        if (c.p < 0) c.p = sg.p0;
-        if (c.p < sg.p1) {
-            u.run = sg.run;
-            u.mt = sg.mt;
-            u.p = c.p;
-            u.n = min(a.runs[sg.run].group, sg.p1 - c.p);
-            c.p += u.n;
-            return true;
+    const uint32_t slot = ui % kURing;
+    if (!ptx::mbar_wait_bounded(&s.uempty[slot], ((ui / kURing) & 1u) ^ 1u, s.abort_flag, kWaitLimitNs)) return false;
+    idx = atomicAdd(&a.sched[0], 1);
+    if (idx >= a.n_units) {
+        idx = -1;
+        if (atomicAdd(&a.sched[1], 1) == static_cast<int>(gridDim.x) - 1) {
+            atomicExch(&a.sched[0], 0);
+            atomicExch(&a.sched[1], 0);
         }
-        ++c.s;
-        c.p = -1;
     }
-    return false;
+    s.uidx[slot] = idx;
+    ptx::mbar_arrive(&s.ufull[slot]);
+    return true;
 }
 
 template <int PREC, int DOUT>  // DOUT: d_out when fixed at compile time (10), else 0
@@ -209,6 +222,10 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             ptx::mbar_init(&s.acc_empty[i], kEpiWarps);
         }
         ptx::mbar_init(s.drain, 1);
+        for (int i = 0; i < kURing; ++i) {
+            ptx::mbar_init(&s.ufull[i], 1);
+            ptx::mbar_init(&s.uempty[i], kUnitReaders);
+        }
         *s.ep_go = 0;
         *s.abort_flag = 0;
         ptx::fence_mbar_init();
@@ -231,9 +248,15 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             const uint32_t ring = ptx::smem_u32(s.ring);
             uint32_t stage = 0, phase = 0;
             bool ok = true;
-            Cursor c = first_cursor(a);
-            Unit u;
-            for (uint32_t ui = 0; ok && next_unit(a, c, u); ++ui) {
+            for (uint32_t ui = 0; ok; ++ui) {
+                int32_t idx = -1;
+                if (!take_unit(s, ui, idx)) {
+                    raise_abort(s, a);
+                    ok = false;
+                    break;
+                }
+                if (idx < 0) break;
+                const GroupUnit u = a.units[idx];
                 const uint32_t n_cols = static_cast<uint32_t>(u.n * a.runs[u.run].h);
                 const uint32_t buf = ui & 1u;
                 const uint32_t idesc = PREC == 1 ? ptx::idesc_bf16(128, n_cols) : ptx::idesc_e4m3(128, n_cols);
@@ -283,9 +306,15 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
         ptx::grid_dep_wait();  // shadows and masters come from the previous kernel (breeding)
         uint32_t stage = 0, phase = 0, issued_mask = 0, parity_mask = 0;
         bool ok = true;
-        Cursor c = first_cursor(a);
-        Unit u;
-        while (ok && next_unit(a, c, u)) {
+        int32_t idx = -1;
+        if (lane == 0) ok = publish_unit(s, a, 0, idx);
+        for (uint32_t ui = 0; ; ++ui) {
+            ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+            idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
+            if (!ok || idx < 0) break;
+            const GroupUnit u = a.units[idx];
+            if (lane == 0) ok = publish_unit(s, a, ui + 1, idx);  // one unit ahead
+            if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) break;
             const ShadowRun& r = a.runs[u.run];
             const uint32_t slot = static_cast<uint32_t>(r.h) * 128u;
             const uint8_t* src = r.shadow + static_cast<int64_t>(u.p + (lane < u.n ? lane : 0)) * r.sh_stride;
@@ -312,6 +341,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             }
         }
         if (!ok && lane == 0) {  // let copies in flight land before the CTA exits
+            raise_abort(s, a);
             volatile int never = 0;
             for (int i = 0; i < a.n_stages; ++i)
                 if (issued_mask & (1u << i))
@@ -323,9 +353,15 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             ptx::grid_dep_wait();  // the staged batch comes from an earlier kernel
             uint32_t stage = 0, phase = 0, issued_mask = 0, parity_mask = 0;
             bool ok = true;
-            Cursor c = first_cursor(a);
-            Unit u;
-            while (ok && next_unit(a, c, u)) {
+            for (uint32_t ui = 0; ok; ++ui) {
+                int32_t idx = -1;
+                if (!take_unit(s, ui, idx)) {
+                    raise_abort(s, a);
+                    ok = false;
+                    break;
+                }
+                if (idx < 0) break;
+                const GroupUnit u = a.units[idx];
                 const uint8_t* xt = a.runs[u.run].xop + static_cast<int64_t>(u.mt) * a.k_blocks * a.a_bytes;
                 for (int kb = 0; kb < a.k_blocks; ++kb) {
                     if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
@@ -370,7 +406,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
         // (ld.global.cg), not the read-only path: this grid starts while the
         // breeding kernel that writes them still runs.
         float prm[kPrmRegs];
-        auto load_prm = [&](const Unit& u) {
+        auto load_prm = [&](const GroupUnit& u) {
             const ShadowRun& r = a.runs[u.run];
             const int n_prm = r.h + d_out * r.h + d_out;
             const int total = u.n * n_prm;
@@ -386,7 +422,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
                 prm[j] = v;
             }
         };
-        auto stage_prm = [&](const Unit& u) {
+        auto stage_prm = [&](const GroupUnit& u) {
             const int h = a.runs[u.run].h;
             const int n_prm = h + d_out * h + d_out;
             const int total = u.n * n_prm;
@@ -507,24 +543,43 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             }
         };
 
-        Cursor cn = first_cursor(a);
-        Unit u, un;
-        bool have = next_unit(a, cn, u);
-        if (have) load_prm(u);
+        GroupUnit u{}, un{};
+        if (et == 0) {
+            int32_t idx = -1;
+            if (!take_unit(s, 0, idx)) {
+                raise_abort(s, a);
+                idx = -1;
+            }
+            s.ep_next[0] = idx;
+        }
+        ptx::named_barrier_sync(kBar, kEpiThreads);
+        const int32_t idx0 = s.ep_next[0];
+        bool have = idx0 >= 0;
+        if (have) {
+            u = a.units[idx0];
+            load_prm(u);
+        }
         int32_t cur_run = -1, cur_mt = -1, label = 0;
         for (uint32_t ui = 0; have; ++ui) {
             // The previous unit's readers finished with the staged parameters at barrier B.
             stage_prm(u);
-            const bool have_n = next_unit(a, cn, un);
-            if (have_n) load_prm(un);  // in flight while this unit is evaluated
             const uint32_t buf = ui & 1u, bph = (ui >> 1) & 1u;
             if (et == 0) {
-                const bool got = ptx::mbar_wait_bounded(&s.acc_full[buf], bph, s.abort_flag, kWaitLimitNs);
+                bool got = ptx::mbar_wait_bounded(&s.acc_full[buf], bph, s.abort_flag, kWaitLimitNs);
+                int32_t nx = -1;
+                if (got) got = take_unit(s, ui + 1, nx);
                 if (!got) raise_abort(s, a);
                 *s.ep_go = got ? 1 : 0;
+                s.ep_next[(ui + 1) & 1u] = nx;  // its previous value was read after barrier A of unit ui - 2
             }
             ptx::named_barrier_sync(kBar, kEpiThreads);  // A: accumulator ready (or abort); parameters staged
             if (!*s.ep_go) break;
+            const int32_t idx_n = s.ep_next[(ui + 1) & 1u];
+            const bool have_n = idx_n >= 0;
+            if (have_n) {
+                un = a.units[idx_n];
+                load_prm(un);  // in flight while this unit is evaluated
+            }
             ptx::tc_fence_after();
 
             const ShadowRun& r = a.runs[u.run];
@@ -746,7 +801,7 @@ cudaError_t launch_stage_xop_tiles(const XopTile* tiles_dev, int32_t n_tiles, in
 
 cudaError_t launch_eval_shadow_group(int32_t k, int32_t d_out, int32_t precision, int32_t n_max,
                                      const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max, bool any_tiles,
-                                     const ShadowSeg* segs_dev, const int32_t* seg_off_dev, int32_t grid,
+                                     const GroupUnit* units_dev, int32_t n_units, int32_t* sched_dev, int32_t grid,
                                      unsigned int* status, cudaStream_t stream)
 {
     if (precision != 1 && precision != 2) return cudaErrorInvalidValue;
@@ -761,8 +816,9 @@ cudaError_t launch_eval_shadow_group(int32_t k, int32_t d_out, int32_t precision
     a.a_bytes = (precision == 1 ? 1u : 2u) * kBlockBytes;
     a.stage_bytes = group_stage_bytes(precision, n_max);
     a.runs = runs_dev;
-    a.segs = segs_dev;
-    a.seg_off = seg_off_dev;
+    a.units = units_dev;
+    a.n_units = n_units;
+    a.sched = sched_dev;
     a.status = status;
     const size_t smem = group_smem_bytes(precision, n_max, a.dpad, a.n_stages);
     const bool ten = d_out == 10;

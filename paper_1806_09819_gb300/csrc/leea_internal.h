@@ -216,6 +216,13 @@ struct XopTile {
     int32_t rows;      // samples of the tile (1 .. 128); the rest are zero
     uint8_t* dst;      // [k_blocks][pieces][128 rows][128 B]
 };
+// One unit of the group evaluation: individuals [p, p + n) of run `run` on
+// its 128-sample tile mt.  CTAs take units from the table in order through
+// a device counter pair sched[2] (zero before the first launch; each launch
+// leaves it at zero).
+struct GroupUnit {
+    int32_t run, mt, p, n;
+};
 int32_t eval_shadow_group_size(int32_t h);
 bool eval_shadow_group_supported(int32_t k, int32_t d_out, int32_t precision, int32_t h, int32_t n_max);
 size_t eval_shadow_group_xop_bytes(int32_t k, int32_t precision, int32_t batch);
@@ -223,7 +230,7 @@ cudaError_t launch_stage_xop_tiles(const XopTile* tiles_dev, int32_t n_tiles, in
                                    cudaStream_t stream);
 cudaError_t launch_eval_shadow_group(int32_t k, int32_t d_out, int32_t precision, int32_t n_max,
                                      const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max, bool any_tiles,
-                                     const ShadowSeg* segs_dev, const int32_t* seg_off_dev, int32_t grid,
+                                     const GroupUnit* units_dev, int32_t n_units, int32_t* sched_dev, int32_t grid,
                                      unsigned int* status, cudaStream_t stream);
 // Widest hidden chunk the tensor memory leaves room for next to the batch tile.
 int32_t eval_shadow_max_chunk(int32_t precision, int32_t k);

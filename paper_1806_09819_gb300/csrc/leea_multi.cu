@@ -57,6 +57,9 @@ struct leea_multi {
     uint8_t* xop = nullptr;
     XopTile* xtiles = nullptr;
     int32_t n_xtiles = 0;
+    GroupUnit* units = nullptr;  // the group evaluation's work, taken by CTAs in order
+    int32_t n_units = 0;
+    int32_t* sched = nullptr;    // its counters
     float *f_adj = nullptr, *f_raw = nullptr, *f_inh = nullptr;  // packed over the runs
     int32_t* correct = nullptr;
     uint8_t* x = nullptr;  // packed minibatch: the graph's fixed inputs
@@ -107,6 +110,8 @@ void free_multi(leea_multi* m)
     cudaFree(m->y);
     cudaFree(m->xop);
     cudaFree(m->xtiles);
+    cudaFree(m->units);
+    cudaFree(m->sched);
     cudaFree(m->gen_dev);
     for (int c = 0; c < 2; ++c) {
         cudaFree(m->sel_tab[c]);
@@ -270,7 +275,8 @@ cudaError_t launch_eval(leea_multi* m, int which, unsigned int* status, cudaStre
         cudaError_t err = launch_stage_xop_tiles(m->xtiles, m->n_xtiles, m->d_in, m->prm.precision, stream);
         if (err != cudaSuccess) return err;
         return launch_eval_shadow_group(m->d_in, m->d_out, m->prm.precision, m->n_max, m->eval_tab[which], m->n_runs,
-                                        m->pop_max, m->any_tiles, m->segs, m->seg_off, m->eval_grid, status, stream);
+                                        m->pop_max, m->any_tiles, m->units, m->n_units, m->sched, m->eval_grid, status,
+                                        stream);
     }
     return launch_eval_shadow_runs(m->d_in, m->d_out, m->prm.precision, m->h_max, m->cw_max, m->n_runs, m->pop_max,
                                    m->any_tiles, m->eval_tab[which], m->segs, m->seg_off, m->eval_grid, status,
@@ -491,6 +497,18 @@ leea_status leea_multi_create(int32_t n_runs, const leea_run_spec* specs, int32_
         }
         m->n_xtiles = static_cast<int32_t>(xt.size());
         if (err == cudaSuccess) err = upload(&m->xtiles, xt);
+        // units: each group of individuals on all its sample tiles in turn
+        std::vector<GroupUnit> units;
+        for (int32_t i = 0; i < n_runs; ++i) {
+            const RunBuf& r = m->runs[i];
+            for (int32_t p0 = 0; p0 < r.pop; p0 += r.group)
+                for (int32_t mt = 0; mt < r.m_tiles; ++mt)
+                    units.push_back(GroupUnit{ i, mt, p0, std::min(r.group, r.pop - p0) });
+        }
+        m->n_units = static_cast<int32_t>(units.size());
+        if (err == cudaSuccess) err = upload(&m->units, units);
+        if (err == cudaSuccess) err = alloc(&m->sched, 2);
+        if (err == cudaSuccess) err = cudaMemset(m->sched, 0, 2 * sizeof(int32_t));
     }
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&m->capture, cudaStreamNonBlocking);
     if (err != cudaSuccess) {
