@@ -85,7 +85,7 @@ SURROGATE_WORKLOAD = ("surrogate form: population 2048 MLPs 784-112-10, 4 recipe
                       "operators and batches in FP32")
 BATCHING_WORKLOAD = ("64 independent LEEA runs of 784-h-10 MLPs, P in [50,2000], h in [16,256] (multiple of 16), "
                      "batch in [8,512], log-uniform (seed 4242); BF16 shadows of W1, FP32 masters; operators as the "
-                     "plain workload; one CUDA graph per generation, hidden chunks from the autotuner")
+                     "plain workload; one CUDA graph per generation, individuals per MMA from the autotuner")
 
 
 def batching_specs(cfg: dict):
@@ -934,7 +934,8 @@ def run_batching(args, rank: int, world: int, local_rank: int):
             "ms_per_step": ms_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 (f32 accumulate)", "data": "synthetic",
             "config": {"workload": BATCHING_WORKLOAD, "parallelism": "replicas" if world > 1 else "single GPU",
-                       "runs": [{"pop": sp.pop, "hidden": sp.hidden, "batch": sp.batch, "chunk": sp.chunk}
+                       "runs": [{"pop": sp.pop, "hidden": sp.hidden, "batch": sp.batch, "chunk": sp.chunk,
+                                 "group": sp.group}
                                 for sp in specs],
                        "l2": "inputs larger than L2 (populations of all runs, 2 buffers), no flush"},
             "network_samples_per_sec": gen_per_s / n_runs * samples_per_gen,

@@ -521,11 +521,15 @@ leea_status leea_profile_read(leea_state* s, double* ms_out, int64_t* launches_o
 
 /* One run of the batching form: `pop` nets d_in-hidden-d_out (pop <= 4096),
  * minibatches of `batch` samples, its own seed (streams as in leea_create),
- * and `chunk`, the hidden units per tensor-core pass of its evaluation (a
- * multiple of 16; 0 = the widest the tensor memory allows) -- the tile shape
- * an autotuner chooses. */
+ * and the evaluation's tile, as an autotuner chooses it:
+ *   chunk  hidden units per chunk of the layer-2 summation order (and, in the
+ *          chunked evaluation, per tensor-core pass): a multiple of 16; 0 =
+ *          the widest the tensor memory allows, the order the state object
+ *          uses;
+ *   group  individuals of the run sharing each MMA in the group evaluation
+ *          (the tile's N = group hidden <= 256): 0 = the most that fit. */
 typedef struct {
-    int32_t pop, hidden, batch, chunk;
+    int32_t pop, hidden, batch, chunk, group;
     uint64_t seed;
 } leea_run_spec;
 
@@ -548,9 +552,10 @@ leea_status leea_multi_layout(const leea_multi* m, int64_t* batch_off, int64_t* 
                               int64_t* total_rows, int64_t* total_pop);
 
 /* The evaluation shape run `run` uses: hidden units per chunk, chunks per
- * individual and 128-sample tiles per batch (any pointer may be NULL). */
+ * individual, 128-sample tiles per batch and individuals per MMA of the
+ * group evaluation (any pointer may be NULL). */
 leea_status leea_multi_run_shape(const leea_multi* m, int32_t run, int32_t* chunk, int32_t* n_chunks,
-                                 int32_t* m_tiles);
+                                 int32_t* m_tiles, int32_t* group);
 
 /* Kernels one evaluation of all runs launches (a stage of
  * leea_multi_profile_read): 2 when every run takes the group evaluation
@@ -630,6 +635,15 @@ void leea_multi_destroy(leea_multi* m);
  * the legacy default stream.  Allocates and frees its own buffers. */
 leea_status leea_tune_shadow_eval(int32_t precision, int32_t d_in, int32_t hidden, int32_t d_out, int32_t batch,
                                   int32_t pop, int32_t chunk, int32_t reps, float* ms_out);
+
+/* Autotuner support: mean time in ms of `reps` group evaluations (batch
+ * staging included) of `pop` random nets d_in-hidden-d_out on `batch`
+ * samples with `group` individuals per MMA (1 .. min(16, 256 / hidden)), on
+ * the current device and the legacy default stream.  LEEA_EINVAL when the
+ * group evaluation does not take the shape.  Allocates and frees its own
+ * buffers. */
+leea_status leea_tune_group_eval(int32_t precision, int32_t d_in, int32_t hidden, int32_t d_out, int32_t batch,
+                                 int32_t pop, int32_t group, int32_t reps, float* ms_out);
 
 /* ---------------------------------------------------------------------- */
 /* Surrogate form: the learned pre-screen of offspring (no counterpart in   */

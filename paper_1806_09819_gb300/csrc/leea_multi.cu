@@ -427,6 +427,10 @@ leea_status leea_multi_create(int32_t n_runs, const leea_run_spec* specs, int32_
             free_multi(m);
             return fail(LEEA_EINVAL, "run %d: chunk must be 0 or a multiple of 16 up to %d", i, cw_max);
         }
+        if (sp.group < 0 || sp.group > eval_shadow_group_size(sp.hidden)) {
+            free_multi(m);
+            return fail(LEEA_EINVAL, "run %d: group must be 0 or in [1, %d]", i, eval_shadow_group_size(sp.hidden));
+        }
         r.pop = sp.pop;
         r.h = sp.hidden;
         r.batch = sp.batch;
@@ -448,7 +452,7 @@ leea_status leea_multi_create(int32_t n_runs, const leea_run_spec* specs, int32_
         m->cw_max = r.cw > m->cw_max ? r.cw : m->cw_max;
         m->pop_max = r.pop > m->pop_max ? r.pop : m->pop_max;
         m->any_tiles = m->any_tiles || r.m_tiles > 1;
-        r.group = eval_shadow_group_size(r.h);
+        r.group = sp.group > 0 ? sp.group : eval_shadow_group_size(r.h);
         m->n_max = r.group * r.h > m->n_max ? r.group * r.h : m->n_max;
     }
     m->grouped = true;
@@ -559,13 +563,14 @@ leea_status leea_multi_layout(const leea_multi* m, int64_t* batch_off, int64_t* 
 }
 
 leea_status leea_multi_run_shape(const leea_multi* m, int32_t run, int32_t* chunk, int32_t* n_chunks,
-                                 int32_t* m_tiles)
+                                 int32_t* m_tiles, int32_t* group)
 {
     leea_status st = check_run(m, run);
     if (st) return st;
     if (chunk) *chunk = m->runs[run].cw;
     if (n_chunks) *n_chunks = m->runs[run].n_chunks;
     if (m_tiles) *m_tiles = m->runs[run].m_tiles;
+    if (group) *group = m->runs[run].group;
     return LEEA_OK;
 }
 
@@ -836,6 +841,105 @@ leea_status leea_tune_shadow_eval(int32_t precision, int32_t d_in, int32_t hidde
     if (err != cudaSuccess) return cuda_fail(err, "tuning run");
     *ms_out = ms / static_cast<float>(reps);
     return check_device_status(nullptr, nullptr);
+}
+
+leea_status leea_tune_group_eval(int32_t precision, int32_t d_in, int32_t hidden, int32_t d_out, int32_t batch,
+                                 int32_t pop, int32_t group, int32_t reps, float* ms_out)
+{
+    if (!ms_out || reps < 1 || pop < 1 || batch < 1) return fail(LEEA_EINVAL, "bad tuning arguments");
+    const int32_t dims[3] = { d_in, hidden, d_out };
+    NetLayout net;
+    if (!make_layout(dims, 3, 0, &net)) return fail(LEEA_EINVAL, "invalid dims");
+    leea_status st = check_shadow_shape(net, precision);
+    if (st) return st;
+    const int32_t g_max = eval_shadow_group_size(hidden);
+    if (group < 1 || group > g_max) return fail(LEEA_EINVAL, "group must be in [1, %d]", g_max);
+    if (!eval_shadow_group_supported(d_in, d_out, precision, hidden, group * hidden))
+        return fail(LEEA_EINVAL, "the group evaluation does not take %d-%d-%d", d_in, hidden, d_out);
+    unsigned int* status = device_status_ptr();
+    if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+    const int64_t stride = shadow_stride_of(net, precision);
+    const int32_t m_tiles = (batch + 127) / 128;
+    const int64_t tile_bytes = static_cast<int64_t>(eval_shadow_group_xop_bytes(d_in, precision, 1));
+    float *popv = nullptr, *f = nullptr, *amax = nullptr, *scratch = nullptr;
+    uint8_t *shadow = nullptr, *x = nullptr, *xop = nullptr;
+    int32_t *y = nullptr, *se = nullptr, *sched = nullptr;
+    ShadowRun* run_dev = nullptr;
+    XopTile* tiles_dev = nullptr;
+    GroupUnit* units_dev = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int dev = 0, sms = 0;
+    cudaError_t err = alloc(&popv, static_cast<size_t>(pop) * net.c_pad);
+    if (err == cudaSuccess) err = alloc(&shadow, static_cast<size_t>(pop) * stride);
+    if (err == cudaSuccess) err = alloc(&f, static_cast<size_t>(pop));
+    if (err == cudaSuccess) err = alloc(&amax, static_cast<size_t>(pop));
+    if (err == cudaSuccess) err = alloc(&se, static_cast<size_t>(pop));
+    if (err == cudaSuccess) err = alloc(&x, static_cast<size_t>(batch) * d_in);
+    if (err == cudaSuccess) err = alloc(&y, static_cast<size_t>(batch));
+    if (err == cudaSuccess) err = alloc(&xop, static_cast<size_t>(m_tiles * tile_bytes));
+    if (err == cudaSuccess) err = alloc(&sched, 2);
+    if (err == cudaSuccess && eval_shadow_scratch_bytes(pop, batch) > 0)
+        err = alloc(&scratch, eval_shadow_scratch_bytes(pop, batch) / sizeof(float));
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = cudaMemset(x, 0x5A, static_cast<size_t>(batch) * d_in);
+    if (err == cudaSuccess) err = cudaMemset(y, 0, sizeof(int32_t) * batch);
+    if (err == cudaSuccess) err = cudaMemset(sched, 0, 2 * sizeof(int32_t));
+    if (err == cudaSuccess) err = cudaMemset(shadow, 0, static_cast<size_t>(pop) * stride);
+    if (err == cudaSuccess) err = launch_init(net, pop, 0, 12345u, popv, nullptr);
+    if (err == cudaSuccess)
+        err = launch_make_shadow(pop, d_in, hidden, net.c_pad, popv, precision, shadow, stride, se, amax, nullptr);
+    if (err == cudaSuccess) {
+        ShadowRun r = shadow_run(net, pop, popv, precision, shadow, stride, se, x, 255.0f, y, batch, 1.0f, nullptr,
+                                 f, nullptr, nullptr, scratch, 0);
+        r.xop = xop;
+        r.group = group;
+        std::vector<ShadowRun> runs(1, r);
+        std::vector<XopTile> tiles;
+        for (int32_t mt = 0; mt < m_tiles; ++mt)
+            tiles.push_back(XopTile{ x + static_cast<int64_t>(128) * mt * d_in, std::min(128, batch - 128 * mt),
+                                     xop + mt * tile_bytes });
+        std::vector<GroupUnit> units;
+        for (int32_t p0 = 0; p0 < pop; p0 += group)
+            for (int32_t mt = 0; mt < m_tiles; ++mt) units.push_back(GroupUnit{ 0, mt, p0, std::min(group, pop - p0) });
+        err = upload(&run_dev, runs);
+        if (err == cudaSuccess) err = upload(&tiles_dev, tiles);
+        if (err == cudaSuccess) err = upload(&units_dev, units);
+        if (err == cudaSuccess) err = cudaGetDevice(&dev);
+        if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        auto once = [&]() {
+            cudaError_t e = launch_stage_xop_tiles(tiles_dev, m_tiles, d_in, precision, nullptr);
+            if (e != cudaSuccess) return e;
+            return launch_eval_shadow_group(d_in, d_out, precision, group * hidden, run_dev, 1, pop, m_tiles > 1,
+                                            units_dev, static_cast<int32_t>(units.size()), sched, sms, status,
+                                            nullptr);
+        };
+        if (err == cudaSuccess) err = once();  // warm-up
+        if (err == cudaSuccess) err = cudaEventRecord(e0, nullptr);
+        for (int32_t i = 0; i < reps && err == cudaSuccess; ++i) err = once();
+        if (err == cudaSuccess) err = cudaEventRecord(e1, nullptr);
+        if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    }
+    float ms = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    cudaFree(popv);
+    cudaFree(shadow);
+    cudaFree(f);
+    cudaFree(amax);
+    cudaFree(se);
+    cudaFree(x);
+    cudaFree(y);
+    cudaFree(xop);
+    cudaFree(sched);
+    cudaFree(scratch);
+    cudaFree(run_dev);
+    cudaFree(tiles_dev);
+    cudaFree(units_dev);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (err != cudaSuccess) return cuda_fail(err, "tuning run");
+    *ms_out = ms / static_cast<float>(reps);
+    return LEEA_OK;
 }
 
 }  // extern "C"

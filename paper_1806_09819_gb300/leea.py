@@ -36,7 +36,7 @@ class LeeaError(RuntimeError):
 
 class leea_run_spec(ctypes.Structure):
     _fields_ = [("pop", ctypes.c_int32), ("hidden", ctypes.c_int32), ("batch", ctypes.c_int32),
-                ("chunk", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+                ("chunk", ctypes.c_int32), ("group", ctypes.c_int32), ("seed", ctypes.c_uint64)]
 
 
 class leea_surrogate_params(ctypes.Structure):
@@ -147,7 +147,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_profile_read": [vp, vp, vp],
         "leea_multi_create": [i32, vp, i32, i32, P(leea_params), vp, P(vp)],
         "leea_multi_layout": [vp, vp, vp, vp, vp],
-        "leea_multi_run_shape": [vp, i32, vp, vp, vp],
+        "leea_multi_run_shape": [vp, i32, vp, vp, vp, vp],
         "leea_multi_eval_launches": [vp, vp],
         "leea_multi_batch_buffers": [vp, P(vp), P(vp)],
         "leea_multi_generation_u8": [vp, vp, f32, vp],
@@ -165,6 +165,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "leea_multi_profile_read": [vp, vp, vp],
         "leea_multi_destroy": ([vp], None),
         "leea_tune_shadow_eval": [i32, i32, i32, i32, i32, i32, i32, i32, P(f32)],
+        "leea_tune_group_eval": [i32, i32, i32, i32, i32, i32, i32, i32, P(f32)],
         "leea_num_recipes": ([i32, P(leea_params), i32], i32),
         "leea_select_recipes": [i32, P(leea_params), vp, vp, u64, u32, i32, vp, vp, vp, vp, vp, vp],
         "leea_breed_entities": [i32, vp, i32, P(leea_params), u64, u32, vp, vp, vp, vp, vp, i32, vp, vp],
@@ -230,7 +231,7 @@ def exported_symbols() -> list[str]:
             "leea_multi_raw_fitness", "leea_multi_get_population", "leea_multi_set_population",
             "leea_multi_set_fitness", "leea_multi_set_generation", "leea_multi_get_selection",
             "leea_multi_get_shadow", "leea_multi_generation_index", "leea_multi_profile_enable",
-            "leea_multi_profile_read", "leea_multi_destroy", "leea_tune_shadow_eval",
+            "leea_multi_profile_read", "leea_multi_destroy", "leea_tune_shadow_eval", "leea_tune_group_eval",
             "leea_surrogate_num_params", "leea_surrogate_init", "leea_surrogate_forward",
             "leea_surrogate_work_floats", "leea_surrogate_loss_grad", "leea_surrogate_adam",
             "leea_num_recipes", "leea_select_recipes", "leea_breed_entities", "leea_descriptors",
@@ -577,6 +578,7 @@ class RunSpec:
     batch: int
     chunk: int = 0
     seed: int = 0
+    group: int = 0
 
 
 class MultiRun:
@@ -588,7 +590,7 @@ class MultiRun:
         self.specs = list(specs)
         self.n_runs = len(self.specs)
         self.d_in, self.d_out = d_in, d_out
-        arr = (leea_run_spec * self.n_runs)(*[leea_run_spec(sp.pop, sp.hidden, sp.batch, sp.chunk, sp.seed)
+        arr = (leea_run_spec * self.n_runs)(*[leea_run_spec(sp.pop, sp.hidden, sp.batch, sp.chunk, sp.group, sp.seed)
                                                for sp in self.specs])
         self._cp = prm.c_struct()
         h = ctypes.c_void_p()
@@ -614,8 +616,8 @@ class MultiRun:
             pass
 
     def run_shape(self, run: int):
-        """(chunk, n_chunks, m_tiles) of run `run`'s evaluation."""
-        v = [ctypes.c_int32() for _ in range(3)]
+        """(chunk, n_chunks, m_tiles, group) of run `run`'s evaluation."""
+        v = [ctypes.c_int32() for _ in range(4)]
         _check(self.lib.leea_multi_run_shape(self._h, run, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
 
@@ -712,6 +714,14 @@ def leea_tune_shadow_eval(precision: int, d_in: int, hidden: int, d_out: int, ba
     ms = ctypes.c_float()
     _check(load_library().leea_tune_shadow_eval(precision, d_in, hidden, d_out, batch, pop, chunk, reps,
                                                 ctypes.byref(ms)))
+    return float(ms.value)
+
+
+def leea_tune_group_eval(precision: int, d_in: int, hidden: int, d_out: int, batch: int, pop: int, group: int,
+                         reps: int = 5) -> float:
+    ms = ctypes.c_float()
+    _check(load_library().leea_tune_group_eval(precision, d_in, hidden, d_out, batch, pop, group, reps,
+                                               ctypes.byref(ms)))
     return float(ms.value)
 
 

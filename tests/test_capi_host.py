@@ -132,6 +132,10 @@ def test_autotune_candidates():
     assert autotune.effective_chunk(48, 112) == 48
     c = autotune.candidates(1, 784, 256)
     assert c[0] == 96 and all(16 <= x <= 112 and x % 16 == 0 for x in c) and len(set(c)) == len(c)
+    # group evaluation: N = group * hidden <= 256, at most 16 individuals per MMA
+    assert autotune.max_group(16) == 16 and autotune.max_group(112) == 2 and autotune.max_group(256) == 1
+    assert autotune.group_candidates(16) == [16, 8, 4] and autotune.group_candidates(112) == [2, 1]
+    assert autotune.group_candidates(256) == [1] and autotune.group_candidates(80) == [3, 1]
 
 
 def test_header_is_plain_c(tmp_path):

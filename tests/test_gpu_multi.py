@@ -165,14 +165,18 @@ def test_autotune_picks_a_candidate_and_caches(gpu, tmp_path):
     cache = str(tmp_path / "tune.json")
     tuned, timings = autotune.tune(specs, D_IN, D_OUT, 1, cache_path=cache, pop=160, reps=2)
     assert len(timings) == 2
-    for sp, t in zip(tuned, tuned):
-        assert sp.chunk in autotune.candidates(1, D_IN, sp.hidden)
+    for sp in tuned:  # both classes take the group evaluation: the tuner picks the group
+        assert sp.chunk == 0 and sp.group in autotune.group_candidates(sp.hidden)
+    assert all(len(t) == len(autotune.group_candidates(h)) for t, h in zip(timings.values(), (256, 48)))
     tuned2, timings2 = autotune.tune(specs, D_IN, D_OUT, 1, cache_path=cache)
-    assert timings2 == {} and [s.chunk for s in tuned2] == [s.chunk for s in tuned]
-    # a tuned multi-run object uses the chosen chunks
+    assert timings2 == {} and [s.group for s in tuned2] == [s.group for s in tuned]
+    # a tuned multi-run object uses the chosen groups
     m = gpu.MultiRun(tuned, D_IN, D_OUT, gpu.Params(**PRM, precision=1))
     try:
         for r, sp in enumerate(tuned):
-            assert m.run_shape(r)[0] == sp.chunk
+            assert m.run_shape(r)[3] == sp.group
     finally:
         m.close()
+    # a group wider than N = 256 allows is refused
+    with pytest.raises(gpu.LeeaError, match="group"):
+        gpu.MultiRun([gpu.RunSpec(pop=5, hidden=128, batch=8, group=3)], D_IN, D_OUT, gpu.Params(**PRM, precision=1))
