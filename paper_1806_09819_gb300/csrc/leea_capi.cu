@@ -775,6 +775,7 @@ struct leea_state {
     // precision form: the batch as the pair kernel's operand tiles (grown with the batch)
     void* xop;
     size_t xop_bytes;
+    int32_t* sched;  // the group evaluation's two unit counters (zero between launches)
 };
 
 namespace {
@@ -805,6 +806,7 @@ void free_state(leea_state* s)
     cudaFree(s->mlp_scratch);
     cudaFree(s->x16);
     cudaFree(s->xop);
+    cudaFree(s->sched);
     if (s->prof) {
         if (s->prof->created)
             for (int st = 0; st < LEEA_NUM_STAGES; ++st)
@@ -989,9 +991,18 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         }
     }
     // The precision form's evaluation: two individuals per MMA where the
-    // shape allows, on the batch staged as operand tiles.
+    // shape allows (h <= 128), else one individual of width up to 256 per MMA
+    // (the group evaluation), on the batch staged as operand tiles.
     const bool shadow_pair = prec != 0 && eval_shadow_pair_supported(s->net, prec, batch);
-    if (shadow_pair) {
+    const bool shadow_group =
+        prec != 0 && !shadow_pair && s->net.n_layers == 2 &&
+        eval_shadow_group_supported(s->net.dims[0], s->net.dims[2], prec, s->net.dims[1],
+                                    eval_shadow_group_size(s->net.dims[1]) * s->net.dims[1]);
+    if (shadow_group && !s->sched) {
+        LEEA_CUDA_TRY(cudaMalloc(&s->sched, 2 * sizeof(int32_t)), "unit counter allocation");
+        LEEA_CUDA_TRY(cudaMemsetAsync(s->sched, 0, 2 * sizeof(int32_t), s->stream), "unit counter clear");
+    }
+    if (shadow_pair || shadow_group) {
         const size_t need = eval_shadow_pair_xop_bytes(s->net, prec, batch);
         if (need > s->xop_bytes) {
             LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "staging sync");
@@ -1052,7 +1063,7 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
             if (stage_early)  // runs beside the selection; the breed that follows waits for both
                 LEEA_CUDA_TRY(launch_stage_x16(s->net, static_cast<const uint8_t*>(x_dev), batch, s->x16, s->stream),
                               "batch staging kernel");
-            if (shadow_pair && !fused)
+            if ((shadow_pair || shadow_group) && !fused)
                 LEEA_CUDA_TRY(launch_stage_xop(s->net, prec, static_cast<const uint8_t*>(x_dev), batch, s->xop,
                                                s->stream),
                               "batch staging kernel");
@@ -1114,6 +1125,18 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
                                                   s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj,
                                                   s->correct, s->scratch, status, s->stream),
                           "shadow evaluation kernel");
+        } else if (shadow_group) {
+            unsigned int* status = device_status_ptr();
+            if (!status) return fail(LEEA_ECUDA, "device status word unavailable");
+            if (first)
+                LEEA_CUDA_TRY(launch_stage_xop(s->net, prec, static_cast<const uint8_t*>(x_dev), batch, s->xop,
+                                               s->stream),
+                              "batch staging kernel");
+            LEEA_CUDA_TRY(launch_eval_shadow_group_run(s->net, s->pop, s->popbuf[s->cur], prec, s->shadow[s->cur],
+                                                       s->sh_stride, s->scale_exp, s->xop, x_div, y_dev, batch,
+                                                       s->prm.alpha, first ? nullptr : s->f_inh, s->f_raw, s->f_adj,
+                                                       s->correct, s->scratch, s->sched, status, s->stream),
+                          "shadow group evaluation kernel");
         } else if (prec != 0)
             st = dispatch_eval_shadow(s->net, s->pop, s->popbuf[s->cur], prec, s->shadow[s->cur], s->scale_exp,
                                       static_cast<const uint8_t*>(x_dev), x_div, y_dev, batch, s->prm.alpha,

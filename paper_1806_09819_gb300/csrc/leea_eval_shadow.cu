@@ -760,6 +760,14 @@ cudaError_t launch_combine_shadow_tiles(const ShadowRun* runs_dev, int32_t n_run
     return cudaGetLastError();
 }
 
+cudaError_t launch_combine_shadow_run_tiles(const ShadowRun& run, cudaStream_t stream)
+{
+    EvalShArgs a{};
+    a.run0 = run;
+    combine_tiles_kernel<<<dim3((run.pop + 255) / 256, 1), 256, 0, stream>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_eval_shadow_runs(int32_t k, int32_t d_out, int32_t precision, int32_t h_max, int32_t cw_max,
                                     int32_t n_runs, int32_t pop_max, bool any_tiles, const ShadowRun* runs_dev,
                                     const ShadowSeg* segs_dev, const int32_t* seg_off_dev, int32_t grid,

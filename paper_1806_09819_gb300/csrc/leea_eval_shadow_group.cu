@@ -18,7 +18,9 @@
 // CTAs take units dynamically: the shadow producer's lane 0 claims the next
 // unit index with an atomic add, one unit ahead of its own work, and hands
 // it to the CTA's other roles through a ring of unit slots in shared memory
-// (each slot with a full and an empty mbarrier).
+// (each slot with a full and an empty mbarrier).  A single run (the state
+// object's precision form for h above 128) comes by value, its units
+// computed from their index.
 // Warp roles (one CTA per SM):
 //   warp 0      TMEM allocation and the single MMA-issuing thread
 //   warp 1      shadow producer: lane j copies individual j's block of each
@@ -80,8 +82,9 @@ constexpr uint64_t kDrainLimitNs = 200000000ull;
 struct GroupArgs {
     int32_t k, d_out, dpad, k_blocks, k_mma, n_stages;
     uint32_t a_bytes, stage_bytes;
-    const ShadowRun* runs;
-    const GroupUnit* units;
+    const ShadowRun* runs;    // many runs: device table; NULL: the single run run0
+    ShadowRun run0;
+    const GroupUnit* units;   // many runs: device table; NULL: unit i of run0 is (i / m_tiles, i % m_tiles)
     int32_t n_units;
     int32_t* sched;  // [0] next unit, [1] CTAs that found no more
     unsigned int* status;
@@ -173,6 +176,19 @@ __device__ __forceinline__ void raise_abort(const GroupSmem& s, const GroupArgs&
     atomicOr(a.status, kStatusEvalTimeout);
 }
 
+__device__ __forceinline__ const ShadowRun& run_of(const GroupArgs& a, int32_t r)
+{
+    return a.runs ? a.runs[r] : a.run0;
+}
+
+// Unit idx of the table, or of run0's groups in order, each on all its tiles.
+__device__ __forceinline__ GroupUnit unit_at(const GroupArgs& a, int32_t idx)
+{
+    if (a.units) return a.units[idx];
+    const int32_t p0 = (idx / a.run0.m_tiles) * a.run0.group;
+    return GroupUnit{ 0, idx % a.run0.m_tiles, p0, min(a.run0.group, a.run0.pop - p0) };
+}
+
 // The index of unit ui of this CTA (-1: no more), from the ring; false when
 // the wait gives up.  Each reader releases the slot once it has the index.
 __device__ __forceinline__ bool take_unit(const GroupSmem& s, uint32_t ui, int32_t& idx)
@@ -256,8 +272,8 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
                     break;
                 }
                 if (idx < 0) break;
-                const GroupUnit u = a.units[idx];
-                const uint32_t n_cols = static_cast<uint32_t>(u.n * a.runs[u.run].h);
+                const GroupUnit u = unit_at(a, idx);
+                const uint32_t n_cols = static_cast<uint32_t>(u.n * run_of(a, u.run).h);
                 const uint32_t buf = ui & 1u;
                 const uint32_t idesc = PREC == 1 ? ptx::idesc_bf16(128, n_cols) : ptx::idesc_e4m3(128, n_cols);
                 if (!ptx::mbar_wait_bounded(&s.acc_empty[buf], ((ui >> 1) & 1u) ^ 1u, s.abort_flag, kWaitLimitNs)) {
@@ -312,10 +328,10 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
             idx = __shfl_sync(0xFFFFFFFFu, idx, 0);
             if (!ok || idx < 0) break;
-            const GroupUnit u = a.units[idx];
+            const GroupUnit u = unit_at(a, idx);
             if (lane == 0) ok = publish_unit(s, a, ui + 1, idx);  // one unit ahead
             if (!__shfl_sync(0xFFFFFFFFu, ok, 0)) break;
-            const ShadowRun& r = a.runs[u.run];
+            const ShadowRun& r = run_of(a, u.run);
             const uint32_t slot = static_cast<uint32_t>(r.h) * 128u;
             const uint8_t* src = r.shadow + static_cast<int64_t>(u.p + (lane < u.n ? lane : 0)) * r.sh_stride;
             for (int kb = 0; kb < a.k_blocks; ++kb) {
@@ -361,8 +377,8 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
                     break;
                 }
                 if (idx < 0) break;
-                const GroupUnit u = a.units[idx];
-                const uint8_t* xt = a.runs[u.run].xop + static_cast<int64_t>(u.mt) * a.k_blocks * a.a_bytes;
+                const GroupUnit u = unit_at(a, idx);
+                const uint8_t* xt = run_of(a, u.run).xop + static_cast<int64_t>(u.mt) * a.k_blocks * a.a_bytes;
                 for (int kb = 0; kb < a.k_blocks; ++kb) {
                     if (!ptx::mbar_wait_bounded(&s.empty[stage], phase ^ 1u, s.abort_flag, kWaitLimitNs)) {
                         raise_abort(s, a);
@@ -407,7 +423,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
         // breeding kernel that writes them still runs.
         float prm[kPrmRegs];
         auto load_prm = [&](const GroupUnit& u) {
-            const ShadowRun& r = a.runs[u.run];
+            const ShadowRun& r = run_of(a, u.run);
             const int n_prm = r.h + d_out * r.h + d_out;
             const int total = u.n * n_prm;
 #pragma unroll
@@ -423,7 +439,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             }
         };
         auto stage_prm = [&](const GroupUnit& u) {
-            const int h = a.runs[u.run].h;
+            const int h = run_of(a, u.run).h;
             const int n_prm = h + d_out * h + d_out;
             const int total = u.n * n_prm;
 #pragma unroll
@@ -556,7 +572,7 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
         const int32_t idx0 = s.ep_next[0];
         bool have = idx0 >= 0;
         if (have) {
-            u = a.units[idx0];
+            u = unit_at(a, idx0);
             load_prm(u);
         }
         int32_t cur_run = -1, cur_mt = -1, label = 0;
@@ -577,12 +593,12 @@ __global__ void __launch_bounds__(kGroupThreads, 1) eval_shadow_group_kernel(con
             const int32_t idx_n = s.ep_next[(ui + 1) & 1u];
             const bool have_n = idx_n >= 0;
             if (have_n) {
-                un = a.units[idx_n];
+                un = unit_at(a, idx_n);
                 load_prm(un);  // in flight while this unit is evaluated
             }
             ptx::tc_fence_after();
 
-            const ShadowRun& r = a.runs[u.run];
+            const ShadowRun& r = run_of(a, u.run);
             const int h = r.h, cw = r.cw, n_chunks = r.n_chunks, n = u.n;
             const int srow = u.mt * 128 + row;  // the sample of this TMEM lane
             const bool live = srow < r.batch;
@@ -799,29 +815,19 @@ cudaError_t launch_stage_xop_tiles(const XopTile* tiles_dev, int32_t n_tiles, in
                           : cudaLaunchKernelEx(&cfg, stage_xop_tiles_kernel<2>, tiles_dev, n_tiles, k, k_blocks);
 }
 
-cudaError_t launch_eval_shadow_group(int32_t k, int32_t d_out, int32_t precision, int32_t n_max,
-                                     const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max, bool any_tiles,
-                                     const GroupUnit* units_dev, int32_t n_units, int32_t* sched_dev, int32_t grid,
-                                     unsigned int* status, cudaStream_t stream)
+namespace {
+
+cudaError_t launch_group(GroupArgs& a, int32_t precision, int32_t n_max, int32_t grid, cudaStream_t stream)
 {
-    if (precision != 1 && precision != 2) return cudaErrorInvalidValue;
-    GroupArgs a{};
-    a.k = k;
-    a.d_out = d_out;
-    a.dpad = group_dpad(d_out);
-    a.k_blocks = (k + (precision == 1 ? 63 : 127)) / (precision == 1 ? 64 : 128);
-    a.k_mma = precision == 1 ? (k + 15) / 16 * 16 : (k + 31) / 32 * 32;
-    a.n_stages = group_stages(precision, n_max, d_out);
+    a.dpad = group_dpad(a.d_out);
+    a.k_blocks = (a.k + (precision == 1 ? 63 : 127)) / (precision == 1 ? 64 : 128);
+    a.k_mma = precision == 1 ? (a.k + 15) / 16 * 16 : (a.k + 31) / 32 * 32;
+    a.n_stages = group_stages(precision, n_max, a.d_out);
     if (a.n_stages == 0 || grid < 1) return cudaErrorInvalidValue;
     a.a_bytes = (precision == 1 ? 1u : 2u) * kBlockBytes;
     a.stage_bytes = group_stage_bytes(precision, n_max);
-    a.runs = runs_dev;
-    a.units = units_dev;
-    a.n_units = n_units;
-    a.sched = sched_dev;
-    a.status = status;
     const size_t smem = group_smem_bytes(precision, n_max, a.dpad, a.n_stages);
-    const bool ten = d_out == 10;
+    const bool ten = a.d_out == 10;
     const void* kern = precision == 1 ? (ten ? reinterpret_cast<const void*>(eval_shadow_group_kernel<1, 10>)
                                              : reinterpret_cast<const void*>(eval_shadow_group_kernel<1, 0>))
                                       : (ten ? reinterpret_cast<const void*>(eval_shadow_group_kernel<2, 10>)
@@ -842,11 +848,55 @@ cudaError_t launch_eval_shadow_group(int32_t k, int32_t d_out, int32_t precision
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     if (precision == 1)
-        err = ten ? cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<1, 10>, a)
-                  : cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<1, 0>, a);
-    else
-        err = ten ? cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<2, 10>, a)
-                  : cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<2, 0>, a);
+        return ten ? cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<1, 10>, a)
+                   : cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<1, 0>, a);
+    return ten ? cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<2, 10>, a)
+               : cudaLaunchKernelEx(&cfg, eval_shadow_group_kernel<2, 0>, a);
+}
+
+}  // namespace
+
+cudaError_t launch_eval_shadow_group_run(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
+                                         const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp,
+                                         const void* xop, float x_div, const int32_t* y, int32_t batch, float alpha,
+                                         const float* f_inh, float* f_raw, float* f_adj, int32_t* correct,
+                                         float* scratch, int32_t* sched, unsigned int* status, cudaStream_t stream)
+{
+    if (precision != 1 && precision != 2) return cudaErrorInvalidValue;
+    GroupArgs a{};
+    a.k = net.dims[0];
+    a.d_out = net.dims[2];
+    a.run0 = shadow_run(net, pop, pop_dev, precision, shadow, sh_stride, scale_exp, nullptr, x_div, y, batch, alpha,
+                        f_inh, f_raw, f_adj, correct, scratch, 0);
+    a.run0.xop = static_cast<const uint8_t*>(xop);
+    a.run0.group = eval_shadow_group_size(net.dims[1]);
+    if (a.run0.m_tiles > 1 && !scratch) return cudaErrorInvalidValue;
+    a.n_units = (pop + a.run0.group - 1) / a.run0.group * a.run0.m_tiles;
+    a.sched = sched;
+    a.status = status;
+    int dev = 0, sms = 0;
+    cudaError_t err = cudaGetDevice(&dev);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (err == cudaSuccess) err = launch_group(a, precision, a.run0.group * net.dims[1], sms, stream);
+    if (err != cudaSuccess || a.run0.m_tiles == 1) return err;
+    return launch_combine_shadow_run_tiles(a.run0, stream);
+}
+
+cudaError_t launch_eval_shadow_group(int32_t k, int32_t d_out, int32_t precision, int32_t n_max,
+                                     const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max, bool any_tiles,
+                                     const GroupUnit* units_dev, int32_t n_units, int32_t* sched_dev, int32_t grid,
+                                     unsigned int* status, cudaStream_t stream)
+{
+    if (precision != 1 && precision != 2) return cudaErrorInvalidValue;
+    GroupArgs a{};
+    a.k = k;
+    a.d_out = d_out;
+    a.runs = runs_dev;
+    a.units = units_dev;
+    a.n_units = n_units;
+    a.sched = sched_dev;
+    a.status = status;
+    cudaError_t err = launch_group(a, precision, n_max, grid, stream);
     if (err != cudaSuccess || !any_tiles) return err;
     return launch_combine_shadow_tiles(runs_dev, n_runs, pop_max, stream);
 }

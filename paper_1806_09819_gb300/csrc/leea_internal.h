@@ -207,6 +207,7 @@ size_t eval_shadow_scratch_bytes(int32_t pop, int32_t batch);
 // Sums each run's per-tile partial losses (runs with m_tiles > 1) in tile order.
 cudaError_t launch_combine_shadow_tiles(const ShadowRun* runs_dev, int32_t n_runs, int32_t pop_max,
                                         cudaStream_t stream);
+cudaError_t launch_combine_shadow_run_tiles(const ShadowRun& run, cudaStream_t stream);
 // The batching form's evaluation over a table of runs (h <= 256, h % 16 == 0,
 // d_0 % 16 == 0, d_out <= 16): group = eval_shadow_group_size(h) individuals
 // share every MMA (N = group h <= 256); each run's batch staged into its xop
@@ -224,6 +225,15 @@ struct GroupUnit {
     int32_t run, mt, p, n;
 };
 int32_t eval_shadow_group_size(int32_t h);
+// The group evaluation of one run (the state object, h > 128): the batch
+// staged by launch_stage_xop into xop; sched: two int32 counters, zero before
+// the first launch (each launch leaves them at zero); scratch as
+// eval_shadow_scratch_bytes when the batch spans several 128-sample tiles.
+cudaError_t launch_eval_shadow_group_run(const NetLayout& net, int32_t pop, const float* pop_dev, int32_t precision,
+                                         const uint8_t* shadow, int64_t sh_stride, const int32_t* scale_exp,
+                                         const void* xop, float x_div, const int32_t* y, int32_t batch, float alpha,
+                                         const float* f_inh, float* f_raw, float* f_adj, int32_t* correct,
+                                         float* scratch, int32_t* sched, unsigned int* status, cudaStream_t stream);
 bool eval_shadow_group_supported(int32_t k, int32_t d_out, int32_t precision, int32_t h, int32_t n_max);
 size_t eval_shadow_group_xop_bytes(int32_t k, int32_t precision, int32_t batch);
 cudaError_t launch_stage_xop_tiles(const XopTile* tiles_dev, int32_t n_tiles, int32_t k, int32_t precision,

@@ -235,6 +235,15 @@ def test_state_breeds_shadows_and_scales(gpu, oracle_mod, precision):
 
 
 @pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("dims,pop,batch", [([784, 160, 10], 40, 200), ([784, 256, 10], 19, 100)])
+def test_state_wide_hidden_generations(gpu, oracle_mod, precision, dims, pop, batch):
+    # h above 128: the state object evaluates one individual per MMA of N = h
+    # (one pass over K), its fitness against the oracle's evaluation of the
+    # same shadows, generation by generation.
+    _state_generation(gpu, oracle_mod, precision, dims, pop, batch, sigma=0.02, gens=2)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
 def test_state_full_size_sampled(gpu, oracle_mod, precision):
     # 4096 MLPs 784-112-10 on batches of 256: every shadow exponent checked, 10 individuals in full.
     sample = [0, 1, 2, 3, 1000, 2047, 2048, 3001, 4094, 4095]
