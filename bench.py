@@ -109,11 +109,11 @@ STAGES = ("select", "breed", "evaluate")
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 TRAFFIC = {
     "breed": {"bytes_per_launch": 472.52e6, "src_sha": "641fc663c50d3438", "capture": "P=1000 plain workload"},
-    "evaluate": {"bytes_per_launch": 369.34e6, "src_sha": "3a95c7a5d4372dc7", "capture": "P=1000 plain workload"},
+    "evaluate": {"bytes_per_launch": 368.68e6, "src_sha": "921b0e7934e40403", "capture": "P=1000 plain workload"},
     "breed_evaluate": {"bytes_per_launch": 738.19e6, "src_sha": "23e25d83744d9797", "capture": "P=1000 plain workload"},
     # eval_mlp_tc_kernel alone (each individual's weight pieces read once from
     # DRAM, the other tiles from L2); the stage also splits the weights
-    "evaluate_paper_net": {"bytes_per_launch": 869.37e6, "src_sha": "b394b877523b3071",
+    "evaluate_paper_net": {"bytes_per_launch": 869.79e6, "src_sha": "407558790a9f32f1",
                            "capture": "paper-net workload, eval_mlp_tc_kernel"},
 }
 
