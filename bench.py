@@ -42,6 +42,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -333,9 +334,10 @@ class OraclePool:
             self.workers, initializer=_oracle_worker_init,
             initargs=(self.shm.name, parents64.shape, self.dims, self.params, x64, y))
 
-    def generation(self, f_adj64, gen: int, seed: int = 0, chunk: int = 4) -> float:
-        """Rank + select in this process, then breed + evaluate every child on
-        the workers (tasks of `chunk` children, handed out as workers free up);
+    def generation(self, f_adj64, gen: int, seed: int = 0, chunk: int = 4, stride: int = 1) -> float:
+        """Rank + select in this process, then breed + evaluate every child
+        (every `stride`-th child when stride > 1: a bounded sample) on the
+        workers (tasks of `chunk` children, handed out as workers free up);
         returns the wall-clock seconds of the generation."""
         import numpy as np
         import oracle
@@ -344,11 +346,15 @@ class OraclePool:
         t0 = time.perf_counter()
         order = oracle.rank(f_adj64)
         p1, p2, kind, f_inh = oracle.select(prm, f_adj64, order, seed, gen)
-        tasks = [(j, min(pop, j + chunk), seed, gen, p1, p2, kind) for j in range(0, pop, chunk)]
-        f = np.empty(pop)
+        if stride > 1:  # the sample: single-child tasks of every stride-th child
+            tasks = [(j, j + 1, seed, gen, p1, p2, kind) for j in range(0, pop, stride)]
+        else:
+            tasks = [(j, min(pop, j + chunk), seed, gen, p1, p2, kind) for j in range(0, pop, chunk)]
+        f = np.full(pop, np.nan)
         for j0, fj in self.pool.imap_unordered(_oracle_worker_task, tasks):
             f[j0:j0 + len(fj)] = fj
-        self.last_f_adj = oracle.inherit(float(prm.alpha), f_inh, f, first=False)
+        if stride == 1:
+            self.last_f_adj = oracle.inherit(float(prm.alpha), f_inh, f, first=False)
         return time.perf_counter() - t0
 
     def close(self):
@@ -457,15 +463,26 @@ def run_reference(args, rank: int, world: int):
         pool = OraclePool(parents64, DIMS, PARAMS, x64, y)
         pool.generation(f_adj64, gen=1)  # the workers load the oracle outside the timing
         try:
+            # Whole generations while the K + W steps fit about two minutes;
+            # else each step a bounded sample (every stride-th child) sized so
+            # that they do.
+            t_full = pool.generation(f_adj64, gen=2)
+            budget = 120.0
+            stride = max(1, math.ceil((args.steps + args.warmup) * t_full / budget))
+            n_children = len(range(0, POP, stride))
             for w in range(args.warmup):
-                pool.generation(f_adj64, gen=2 + w)
-            secs = [pool.generation(f_adj64, gen=100 + k) for k in range(args.steps)]
+                pool.generation(f_adj64, gen=3 + w, stride=stride)
+            secs = [pool.generation(f_adj64, gen=100 + k, stride=stride) for k in range(args.steps)]
         finally:
             pool.close()
         total = sum(secs)
-        gen_per_s = args.steps / total
+        gen_per_s = args.steps * (n_children / POP) / total
         sample = (f"whole generations: rank+select of {POP} nets, breed+evaluate of all {POP} children (batch "
-                  f"{BATCH}) with the unchanged FP64 oracle over {pool.workers} worker processes")
+                  f"{BATCH}) with the unchanged FP64 oracle over {pool.workers} worker processes" if stride == 1 else
+                  f"per step rank+select of {POP} nets and breed+evaluate of {n_children} of the {POP} children "
+                  f"(every {stride}th; batch {BATCH}) with the unchanged FP64 oracle over {pool.workers} worker "
+                  f"processes; value = ({n_children}/{POP}) generations per measured step (a whole generation "
+                  f"took {t_full:.2f} s, too long for {args.steps + args.warmup} steps in a few minutes)")
         line = {"impl": "reference", "metric": METRIC, "value": gen_per_s, "unit": "generations/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
