@@ -57,6 +57,35 @@ def test_multi_matches_single_run_objects(gpu, precision):
             st.close()
 
 
+def test_multi_other_outputs_matches_single_run_objects(gpu):
+    # 16 and 3 outputs (not the usual 10): the group evaluation's general
+    # layer-2 code, one-, two- and many-individual units, one and several tiles.
+    import torch
+    for d_out, specs in ((16, [(40, 144, 150, 21), (70, 32, 40, 22), (25, 96, 260, 23)]),
+                         (3, [(30, 16, 20, 24), (17, 208, 129, 25)])):
+        prm = gpu.Params(**PRM, precision=1)
+        m = gpu.MultiRun([gpu.RunSpec(pop=p, hidden=h, batch=b, seed=s) for p, h, b, s in specs], D_IN, d_out, prm)
+        singles = [gpu.LeeaState(p, [D_IN, h, d_out], prm, seed=s) for p, h, b, s in specs]
+        try:
+            rng = np.random.default_rng(d_out)
+            for g in range(3):
+                xs = rng.integers(0, 256, size=(m.total_rows, D_IN)).astype(np.uint8)
+                ys = rng.integers(0, d_out, size=m.total_rows).astype(np.int32)
+                m.generation_u8(torch.from_numpy(xs).cuda(), torch.from_numpy(ys).cuda())
+                for r, st in enumerate(singles):
+                    rows = m.rows_slice(r)
+                    st.leea_generation_u8(torch.from_numpy(np.ascontiguousarray(xs[rows])).cuda(),
+                                          torch.from_numpy(np.ascontiguousarray(ys[rows])).cuda())
+                f_multi = m.raw_fitness()
+                for r, st in enumerate(singles):
+                    np.testing.assert_array_equal(f_multi[m.run_slice(r)], st.leea_raw_fitness(),
+                                                  err_msg=f"d_out {d_out} run {r} generation {g}")
+        finally:
+            m.close()
+            for st in singles:
+                st.close()
+
+
 def test_graph_replay_equals_direct_launches(gpu):
     import torch
     prm = gpu.Params(**PRM, precision=1)

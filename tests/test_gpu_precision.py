@@ -235,11 +235,13 @@ def test_state_breeds_shadows_and_scales(gpu, oracle_mod, precision):
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("dims,pop,batch", [([784, 160, 10], 40, 200), ([784, 256, 10], 19, 100)])
+@pytest.mark.parametrize("dims,pop,batch", [([784, 160, 10], 40, 200), ([784, 256, 10], 19, 100),
+                                            ([96, 48, 16], 33, 130), ([64, 160, 4], 20, 50)])
 def test_state_wide_hidden_generations(gpu, oracle_mod, precision, dims, pop, batch):
     # h above 128: the state object evaluates one individual per MMA of N = h
-    # (one pass over K), its fitness against the oracle's evaluation of the
-    # same shadows, generation by generation.
+    # (one pass over K); h = 48 with 16 outputs: two individuals per MMA and
+    # the layer-2 code for outputs other than 10.  Fitness against the
+    # oracle's evaluation of the same shadows, generation by generation.
     _state_generation(gpu, oracle_mod, precision, dims, pop, batch, sigma=0.02, gens=2)
 
 
