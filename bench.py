@@ -860,6 +860,8 @@ def run_batching(args, rank: int, world: int, local_rank: int):
     cfg = CONFIGS["batching"]
     steps, warmup = args.steps, args.warmup
     runs = batching_specs(cfg)
+    if args.runs:  # profiling override: the first runs only
+        runs = runs[:args.runs]
     specs = [leea.RunSpec(pop=p, hidden=h, batch=b, seed=s + 100 * rank) for p, h, b, s in runs]
     specs, _ = autotune.tune(specs, DIMS[0], DIMS[2], cfg["precision"])
     prm = leea.Params(**PARAMS, precision=cfg["precision"])
@@ -1288,6 +1290,8 @@ def main():
                          "max-pooling at lambda=2000, batch 1024")
     ap.add_argument("--pop", type=int, default=0, help="override the population size (small profiling cases)")
     ap.add_argument("--batch", type=int, default=0, help="override the batch size (small profiling cases)")
+    ap.add_argument("--runs", type=int, default=0,
+                    help="batching form: only the first N runs (small profiling cases, not the workload)")
     ap.add_argument("--input", choices=["u8", "f32"], default="u8",
                     help="minibatch as 8-bit levels (x = k/255, the images' own encoding) or as float32")
     args = ap.parse_args()
