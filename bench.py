@@ -764,7 +764,12 @@ def run_small(args, rank: int, world: int, local_rank: int):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # larger than the 126 MB L2
     st = leea.LeeaState(pop, dims, leea.Params(**PARAMS, eval_path=args.eval_path), seed=1000 + rank, stream=stream)
     for k in range(warmup + 1):  # the first call evaluates the initial population
+        if k == warmup:  # which kernels a breeding generation launches
+            st.leea_profile_enable(True)
         st.leea_generation_u8(xs[k], ys[k], 255.0)
+    stage_launches = {s: n for s, (_, n) in st.leea_profile_read().items()}
+    st.leea_profile_enable(False)
+    single_launch = stage_launches == {"select": 0, "breed": 1, "evaluate": 0}
     torch.cuda.synchronize(dev)
     clocks = ClockSampler(_gpu_id_for(local_rank))
     clocks.start()
@@ -827,9 +832,11 @@ def run_small(args, rank: int, world: int, local_rank: int):
                        "input": "uint8 levels k, x = k/255",
                        "l2": "flushed between timed generations"},
             "network_samples_per_sec": gen_per_s * pop * batch, "e2e": e2e,
-            "gpu_launches": int(steps * sum(kernels_per_generation(
-                pop, batch, 0, x16=args.eval_path in (0, 2)).values())),
+            "gpu_launches": int(steps * (1 if single_launch else sum(kernels_per_generation(
+                pop, batch, 0, x16=args.eval_path in (0, 2)).values()))),
             "roofline": roofline, "clocks": clk}
+    line["config"]["generation"] = ("one kernel: ranking, selection, breeding and evaluation (one CTA per child "
+                                    "and 8 hidden units)" if single_launch else "a chain of kernels")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x64 = xtr[idx[warmup + steps]].astype(np.float64) / 255.0
         line["cpu_baseline"] = small_cpu_baseline(st.leea_get_population(), st.leea_fitness(), x64,

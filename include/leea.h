@@ -132,8 +132,18 @@ enum { LEEA_SIGMA_CONST = 0, LEEA_SIGMA_DECAY = 1, LEEA_SIGMA_SELF = 2 };
  * population back from memory; the children are bit-identical to
  * leea_breed's.  It needs d_0 % 16 == 0, h % 16 == 0, h <= 128, d_out <= 16,
  * batch <= 128 (LEEA_EINVAL otherwise); the first evaluation uses the
- * tensor-core kernel.  AUTO keeps breeding and evaluation as two kernels. */
-enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2, LEEA_EVAL_FUSED = 3 };
+ * tensor-core kernel.  AUTO keeps breeding and evaluation as two kernels.
+ * SMALL (state object, 8-bit generation calls, precision 0): the whole
+ * generation -- ranking, selection, breeding, evaluation (Algorithm 1) -- in
+ * one launch of one CTA per (child, 8 hidden units), each CTA ranking the
+ * previous population itself and evaluating the slice it bred; the children
+ * are bit-identical to leea_breed's and the fitness to the SIMT kernel's.  It
+ * needs one hidden layer, h % 8 == 0, h <= 256, d_0 % 4 == 0, d_0 <= 2048,
+ * d_out <= 32, batch <= 128, pop <= 1024, a 4-byte aligned batch and the
+ * batch in shared memory (LEEA_EINVAL otherwise).  AUTO takes it for such
+ * generations when pop * h / 8 is at most twice the number of SMs, where the
+ * chain of kernels would be bound by launch and dependency latency. */
+enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2, LEEA_EVAL_FUSED = 3, LEEA_EVAL_SMALL = 4 };
 
 /* Precision form (a throughput variant of Eq. 1; the paper itself computes in
  * FP32).  With precision 1 or 2 the population keeps its FP32 master, which
@@ -507,7 +517,9 @@ int64_t leea_num_params(const leea_state* s);
 /* Per-stage timing with CUDA events recorded on the object's stream around
  * each kernel of leea_generation.  Stages: 0 ranking + selection (one fused
  * launch for pop <= 4096), 1 breeding (with the evaluation under
- * LEEA_EVAL_FUSED), 2 evaluation (no launch after a fused breed). */
+ * LEEA_EVAL_FUSED; the whole generation under the single-launch path, which
+ * records nothing in stages 0 and 2 after the first evaluation), 2
+ * evaluation (no launch after a fused breed). */
 #define LEEA_NUM_STAGES 3
 leea_status leea_profile_enable(leea_state* s, int32_t enable);
 

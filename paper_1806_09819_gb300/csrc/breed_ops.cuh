@@ -39,6 +39,16 @@ __device__ __forceinline__ float4 mean4(float4 a, float4 b)
     return make_float4(0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z), 0.5f * (a.w + b.w));
 }
 
+// Zero the padding genes (>= c) among genes i0 .. i0+3.
+__device__ __forceinline__ float4 clear_padding(float4 v, int64_t i0, int64_t c)
+{
+    if (i0 + 0 >= c) v.x = 0.0f;
+    if (i0 + 1 >= c) v.y = 0.0f;
+    if (i0 + 2 >= c) v.z = 0.0f;
+    if (i0 + 3 >= c) v.w = 0.0f;
+    return v;
+}
+
 // Mutation of one lane's unit (8 genes in v) whose mask bits are `hit`.  Slot
 // s = 0..3 names the Box-Muller pair of genes 8u + 2s, 8u + 2s + 1, i.e. pair
 // s & 1 of NORMAL block 2u + (s >> 1).  The warp lists the slots that hold a

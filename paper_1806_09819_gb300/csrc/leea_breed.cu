@@ -184,16 +184,6 @@ static_assert(BreedShape<false>::kChunk == kGenesPerLane * 32 * BreedShape<false
                   BreedShape<true>::kChunk == kGenesPerLane * 32 * BreedShape<true>::kConsumerWarps,
               "consumers must tile a chunk exactly");
 
-// Zero the padding genes (>= c) among genes i0 .. i0+3.
-__device__ __forceinline__ float4 clear_padding(float4 v, int64_t i0, int64_t c)
-{
-    if (i0 + 0 >= c) v.x = 0.0f;
-    if (i0 + 1 >= c) v.y = 0.0f;
-    if (i0 + 2 >= c) v.z = 0.0f;
-    if (i0 + 3 >= c) v.w = 0.0f;
-    return v;
-}
-
 // The run owning global work item `it`: the last one whose first item is <= it.
 __device__ __forceinline__ int32_t run_of_item(const BreedRun* runs, int32_t n_runs, int64_t it)
 {

@@ -12,6 +12,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 #include <vector>
 
 using namespace leea;
@@ -87,10 +88,12 @@ leea_status check_params(const leea_params* p)
     if (!(p->alpha >= 0.0f && p->alpha <= 1.0f)) return fail(LEEA_EINVAL, "alpha not in [0,1]");
     if (p->init != 0 && p->init != 1) return fail(LEEA_EINVAL, "init must be 0 or 1");
     if (p->precision < 0 || p->precision > 2) return fail(LEEA_EINVAL, "precision must be 0, 1 or 2");
-    if (p->eval_path < LEEA_EVAL_AUTO || p->eval_path > LEEA_EVAL_FUSED)
-        return fail(LEEA_EINVAL, "eval_path must be LEEA_EVAL_AUTO, _SIMT, _TENSOR or _FUSED");
+    if (p->eval_path < LEEA_EVAL_AUTO || p->eval_path > LEEA_EVAL_SMALL)
+        return fail(LEEA_EINVAL, "eval_path must be LEEA_EVAL_AUTO, _SIMT, _TENSOR, _FUSED or _SMALL");
     if (p->eval_path == LEEA_EVAL_FUSED && p->precision != 0)
         return fail(LEEA_EINVAL, "the fused breed + evaluate path takes precision 0");
+    if (p->eval_path == LEEA_EVAL_SMALL && p->precision != 0)
+        return fail(LEEA_EINVAL, "the single-launch generation takes precision 0");
     if (p->sigma_ctl < LEEA_SIGMA_CONST || p->sigma_ctl > LEEA_SIGMA_SELF)
         return fail(LEEA_EINVAL, "sigma_ctl must be LEEA_SIGMA_CONST, _DECAY or _SELF");
     if (p->sigma_ctl == LEEA_SIGMA_DECAY && !(p->sigma_k > 0.0f && !std::isinf(p->sigma_k)))
@@ -776,6 +779,11 @@ struct leea_state {
     void* xop;
     size_t xop_bytes;
     int32_t* sched;  // the group evaluation's two unit counters (zero between launches)
+    // single-launch generation of small populations (eval_path SMALL, or AUTO)
+    float* f_adj_alt;    // the other fitness buffer: a generation reads one and writes the other
+    float* hid;          // layer-1 activations [pop][batch][h] (grown with the batch)
+    size_t hid_bytes;
+    uint32_t* count;     // arrivals per child (zero between launches)
 };
 
 namespace {
@@ -807,6 +815,9 @@ void free_state(leea_state* s)
     cudaFree(s->x16);
     cudaFree(s->xop);
     cudaFree(s->sched);
+    cudaFree(s->f_adj_alt);
+    cudaFree(s->hid);
+    cudaFree(s->count);
     if (s->prof) {
         if (s->prof->created)
             for (int st = 0; st < LEEA_NUM_STAGES; ++st)
@@ -901,7 +912,8 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         return fail(LEEA_EINVAL, "the state object evaluates nets with hidden layers (n_dims >= 3), d_out <= 32, and "
                                  "with several hidden layers every layer input and hidden width <= 256");
     }
-    if (s->net.n_layers > 2 && (p->precision != 0 || p->eval_path == LEEA_EVAL_FUSED)) {
+    if (s->net.n_layers > 2 &&
+        (p->precision != 0 || p->eval_path == LEEA_EVAL_FUSED || p->eval_path == LEEA_EVAL_SMALL)) {
         delete s;
         return fail(LEEA_EINVAL, "nets with several hidden layers evaluate FP32 populations, breeding and evaluation "
                                  "as separate kernels");
@@ -963,6 +975,90 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
         return cuda_fail(err, "leea_create init");
     }
     *out = s;
+    return LEEA_OK;
+}
+
+// One generation of a small population in a single launch (launch_small_gen):
+// the first call evaluates the initial population, later calls rank, select,
+// breed and evaluate.  The kernel reads the previous fitness from one buffer
+// and writes the new one to the other; the buffers then swap.
+static leea_status run_small_generation(leea_state* s, const uint8_t* x_dev, float x_div, const int32_t* y_dev,
+                                        int32_t batch)
+{
+    const size_t np = static_cast<size_t>(s->pop);
+    if (!s->count) {
+        LEEA_CUDA_TRY(cudaMalloc(&s->count, sizeof(uint32_t) * np), "arrival counter allocation");
+        LEEA_CUDA_TRY(cudaMemsetAsync(s->count, 0, sizeof(uint32_t) * np, s->stream), "arrival counter clear");
+    }
+    if (!s->f_adj_alt) LEEA_CUDA_TRY(cudaMalloc(&s->f_adj_alt, sizeof(float) * np), "fitness buffer allocation");
+    const size_t need = sizeof(float) * np * static_cast<size_t>(batch) * static_cast<size_t>(s->net.dims[1]);
+    if (need > s->hid_bytes) {
+        LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "scratch sync");
+        cudaFree(s->hid);
+        s->hid = nullptr;
+        s->hid_bytes = 0;
+        LEEA_CUDA_TRY(cudaMalloc(&s->hid, need), "activation scratch allocation");
+        s->hid_bytes = need;
+    }
+    const bool first = !s->evaluated;
+    SmallGenArgs ga{};
+    ga.pop = s->pop;
+    ga.d_in = s->net.dims[0];
+    ga.h = s->net.dims[1];
+    ga.d_out = s->net.dims[2];
+    ga.batch = batch;
+    ga.c = s->net.c;
+    ga.c_pad = s->net.c_pad;
+    ga.b1_off = s->net.b_off[0];
+    ga.w2_off = s->net.w_off[1];
+    ga.b2_off = s->net.b_off[1];
+    ga.x_div = x_div;
+    ga.alpha = s->prm.alpha;
+    ga.order = s->order;
+    ga.par1 = s->par1;
+    ga.par2 = s->par2;
+    ga.kind = s->kind;
+    ga.f_inh = s->f_inh;
+    ga.f_raw = s->f_raw;
+    ga.correct = s->correct;
+    ga.hid = s->hid;
+    ga.count = s->count;
+    ga.x = x_dev;
+    ga.y = y_dev;
+    if (first) {
+        ga.breed = 0;
+        ga.popv = s->popbuf[s->cur];
+        ga.f_adj = s->f_adj;
+        StageScope sc(s, 2);
+        LEEA_CUDA_TRY(launch_small_gen(ga, s->stream), "single-launch generation kernel");
+        sc.done();
+        s->evaluated = true;
+        return LEEA_OK;
+    }
+    const uint32_t g = s->gen + 1;
+    const float sigma_g = sigma_of_breed(s->prm, g);
+    ga.breed = 1;
+    ga.sel = select_args(s->pop, &s->prm, s->seed, g);
+    ga.sel.sigma = sigma_g;
+    if (s->prm.sigma_ctl == LEEA_SIGMA_SELF) {
+        ga.sel.tau = s->prm.tau;
+        ga.sel.sigma_in = s->sigma[s->cur];
+        ga.sel.sigma_out = s->sigma[s->cur ^ 1];
+    }
+    ga.br = breed_args(s->pop, s->net, &s->prm, s->seed, g);
+    ga.br.sigma = sigma_g;
+    ga.parents = s->popbuf[s->cur];
+    ga.popv = s->popbuf[s->cur ^ 1];
+    ga.f_adj_in = s->f_adj;
+    ga.f_adj = s->f_adj_alt;
+    {
+        StageScope sc(s, 1);
+        LEEA_CUDA_TRY(launch_small_gen(ga, s->stream), "single-launch generation kernel");
+        sc.done();
+    }
+    std::swap(s->f_adj, s->f_adj_alt);
+    s->cur ^= 1;
+    s->gen = g;
     return LEEA_OK;
 }
 
@@ -1035,6 +1131,24 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
                                  "d_out <= 16 and batch <= 128");
     if (!u8 && s->prm.eval_path == LEEA_EVAL_FUSED)
         return fail(LEEA_EINVAL, "the fused breed + evaluate path takes 8-bit inputs (leea_generation_u8*)");
+    // Small populations: the whole generation in one launch (SMALL, or AUTO
+    // when its CTAs, one per child and 8 hidden units, fit twice on the GPU).
+    const bool small_ok = u8 && prec == 0 && small_gen_supported(s->net, s->pop, batch) &&
+                          (reinterpret_cast<uintptr_t>(x_dev) & 3u) == 0;
+    bool small = false;
+    if (s->prm.eval_path == LEEA_EVAL_SMALL) {
+        if (!small_ok)
+            return fail(LEEA_EINVAL, "the single-launch generation needs 8-bit inputs (4-byte aligned), one hidden "
+                                     "layer with h %% 8 == 0 and h <= 256, d_0 %% 4 == 0 and d_0 <= 2048, "
+                                     "d_out <= 32, batch <= 128, pop <= 1024 and the batch in 200 KB of shared memory");
+        small = true;
+    } else if (s->prm.eval_path == LEEA_EVAL_AUTO && small_ok) {
+        int dev = 0, sms = 0;
+        LEEA_CUDA_TRY(cudaGetDevice(&dev), "device query");
+        LEEA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
+        small = small_gen_ctas(s->net, s->pop) <= 2 * sms;
+    }
+    if (small) return run_small_generation(s, static_cast<const uint8_t*>(x_dev), x_div, y_dev, batch);
     // The tensor-core evaluation of 8-bit inputs reads the batch as FP16: a
     // breeding generation stages it beside the selection.
     const bool stage_early = !first && !fused && u8 && prec == 0 && s->x16 && s->prm.eval_path != LEEA_EVAL_SIMT &&

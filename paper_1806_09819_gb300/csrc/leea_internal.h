@@ -332,6 +332,37 @@ cudaError_t launch_breed_eval_u8(const BreedArgs& b, const NetLayout& net, const
                                  float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
                                  float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
                                  cudaStream_t stream);
+// One generation (ranking, selection, breeding, evaluation of 8-bit inputs)
+// in a single launch for small FP32 populations of d_0-h-d_out nets: one CTA
+// per (child, 8 hidden units).  Children bit-identical to breed_kernel's,
+// fitness bit-identical to eval_simt_kernel's.  f_adj_in and f_adj must not
+// alias (every CTA ranks the whole previous population); count holds pop
+// zeros between launches; hid has room for pop x batch x h floats.
+struct SmallGenArgs {
+    SelectArgs sel;          // breed: the selection (sigma as the breed's)
+    BreedArgs br;            // breed: the operators and streams
+    int32_t breed;           // 0: evaluate the population in popv (the first evaluation)
+    int32_t pop, d_in, h, d_out, batch;
+    int32_t n_slices, n_pow2;  // set by the launcher
+    int64_t region_floats;     // set by the launcher
+    int64_t c, c_pad, b1_off, w2_off, b2_off;
+    float x_div, alpha;
+    const float* parents;    // breed: the previous population
+    float* popv;             // the children (breed) or the population evaluated
+    const float* f_adj_in;   // breed: the previous adjusted fitness
+    int32_t *order, *par1, *par2, *kind;
+    float* f_inh;
+    float *f_raw, *f_adj;
+    int32_t* correct;        // nullable
+    float* hid;              // [pop][batch][h] activations of layer 1
+    uint32_t* count;         // [pop] arrivals per child
+    const uint8_t* x;        // [batch][d_0] levels, 4-byte aligned
+    const int32_t* y;
+};
+bool small_gen_supported(const NetLayout& net, int32_t pop, int32_t batch);
+int32_t small_gen_ctas(const NetLayout& net, int32_t pop);
+size_t small_gen_smem_bytes(int32_t d_in, int32_t h, int32_t d_out, int32_t batch, int32_t pop);
+cudaError_t launch_small_gen(SmallGenArgs a, cudaStream_t stream);
 // Surrogate form: recipes (virtual offspring) and their descriptors.
 constexpr uint32_t kRecipeEntity0 = 0x40000000u;  // Philox entity of recipe r: kRecipeEntity0 + r
 // Recipes r < mult n_cross are crossovers, the rest mutations; parents as

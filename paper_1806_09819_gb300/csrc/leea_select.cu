@@ -3,25 +3,10 @@
 // inheritance values) plus the tournament alternative.
 #include "leea_internal.h"
 #include "philox.cuh"
+#include "select_ops.cuh"
 #include "tc_ptx.cuh"
 
 namespace leea {
-
-constexpr uint32_t kTagSel = 2;
-constexpr uint32_t kTagSigma = 7;
-constexpr int32_t kKindElite = 0, kKindCross = 1, kKindMut = 2;
-
-// A 64-bit key whose ascending order is: fitness descending (NaN as -inf,
-// -0 as +0), then index ascending.  Comparing keys is exact, so the order is
-// the same total order any correct sort of the same FP32 vector produces.
-__device__ __forceinline__ uint64_t rank_key(float f, int32_t idx)
-{
-    uint32_t b = __float_as_uint(f);
-    if (f != f) b = 0xFF800000u;       // NaN -> -inf
-    if (b == 0x80000000u) b = 0u;      // -0 -> +0
-    const uint32_t asc = (b & 0x80000000u) ? ~b : (b | 0x80000000u);  // grows with f
-    return (static_cast<uint64_t>(~asc) << 32) | static_cast<uint32_t>(idx);
-}
 
 // Rank by counting: the rank of i is the number of keys below its own.  A
 // warp owns one individual: its lanes scan the keys of a shared tile (the
@@ -58,92 +43,6 @@ cudaError_t launch_rank(int32_t pop, const float* f_adj, int32_t* order, cudaStr
 {
     return launch_pdl(rank_kernel, dim3((pop + kRankWarps - 1) / kRankWarps), dim3(32 * kRankWarps), 0, stream, pop,
                       f_adj, order);
-}
-
-// Draw n of child j's SEL stream, caching the current Philox block.
-struct SelStream {
-    uint64_t seed;
-    uint32_t gen, ent, blk;
-    uint4 w;
-    __device__ SelStream(uint64_t s, uint32_t g, uint32_t e) : seed(s), gen(g), ent(e), blk(0xFFFFFFFFu) {}
-    __device__ uint32_t draw(uint32_t n)
-    {
-        if ((n >> 2) != blk) {
-            blk = n >> 2;
-            w = stream_block(seed, kTagSel, gen, ent, blk);
-        }
-        return word_of(w, n & 3u);
-    }
-};
-
-__device__ __forceinline__ int32_t pick_parent(const SelectArgs& a, const float* f_adj,
-                                               const int32_t* order, SelStream& st, uint32_t first)
-{
-    if (a.sel_op == 0)
-        return order[index_of(st.draw(first), static_cast<uint32_t>(a.pool))];
-    int32_t best = -1;
-    uint64_t best_key = 0;
-    for (int32_t t = 0; t < a.tour_k; ++t) {
-        const int32_t cand = static_cast<int32_t>(index_of(st.draw(first + t), static_cast<uint32_t>(a.pop)));
-        const uint64_t k = rank_key(f_adj[cand], cand);
-        if (best < 0 || k < best_key) { best = cand; best_key = k; }
-    }
-    return best;
-}
-
-// Kind, parents and inherited fitness of child j (Algorithm 1; Section 3.1).
-__device__ __forceinline__ void select_child(const SelectArgs& a, const float* f_adj, const int32_t* order, int32_t j,
-                                             int32_t* par1, int32_t* par2, int32_t* kind, float* f_inh)
-{
-    SelStream st(a.seed, a.gen, static_cast<uint32_t>(j));
-    int32_t k, p1, p2;
-    float fi;
-    if (j < a.n_elite) {
-        k = kKindElite;
-        p1 = p2 = order[j];
-        fi = f_adj[p1];
-    } else if (j < a.n_elite + a.n_cross) {
-        k = kKindCross;
-        const uint32_t draws = a.sel_op == 0 ? 1u : static_cast<uint32_t>(a.tour_k);
-        p1 = pick_parent(a, f_adj, order, st, 0u);
-        p2 = pick_parent(a, f_adj, order, st, draws);
-        fi = 0.5f * (f_adj[p1] + f_adj[p2]);
-    } else {
-        k = kKindMut;
-        p1 = p2 = pick_parent(a, f_adj, order, st, 0u);
-        fi = f_adj[p1];
-    }
-    kind[j] = k;
-    par1[j] = p1;
-    par2[j] = p2;
-    f_inh[j] = fi;
-    // Mutation strength of the child (Section 3.2): constant or scheduled, or
-    // under self-adaptation its sigma gene -- the elite's own, the mean of the
-    // crossover parents', or the mutation parent's times exp(tau z), z from
-    // draw 0 of the child's SIGMA stream.
-    float sigma = a.sigma;
-    if (a.sigma_out) {
-        sigma = a.sigma_in[p1];
-        if (k == kKindCross) {
-            sigma = 0.5f * (sigma + a.sigma_in[p2]);
-        } else if (k == kKindMut) {
-            const uint4 w = stream_block(a.seed, kTagSigma, a.gen, static_cast<uint32_t>(j), 0u);
-            sigma *= expf(a.tau * box_muller(w.x, w.y).x);
-        }
-        a.sigma_out[j] = sigma;
-    }
-    if (a.precision > 0) {
-        a.amax_out[j] = 0.0f;
-        if (a.precision == 2) {
-            // Upper bound on the child's max |W1|: a crossover gene (either
-            // parent's, or their mean) is bounded by the larger parent bound; a
-            // mutation adds at most sigma * kNormalBound.
-            float bound = a.amax_in[p1];
-            if (k == kKindCross) bound = fmaxf(bound, a.amax_in[p2]);
-            else if (k == kKindMut) bound = fmaf(sigma, kNormalBound, bound);
-            a.scale_exp_out[j] = fp8_scale_exp(bound);
-        }
-    }
 }
 
 // Recipe r of the surrogate form: a crossover (r < mult n_cross) or a

@@ -22,7 +22,7 @@ TAG_INIT, TAG_SEL, TAG_XO, TAG_MUTMASK, TAG_NORMAL = 1, 2, 3, 4, 5
 TAG_SIGMA = 7
 SIGMA_CONST, SIGMA_DECAY, SIGMA_SELF = 0, 1, 2
 KIND_ELITE, KIND_CROSSOVER, KIND_MUTATION = 0, 1, 2
-EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR, EVAL_FUSED = 0, 1, 2, 3
+EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR, EVAL_FUSED, EVAL_SMALL = 0, 1, 2, 3, 4
 PRECISION_FP32, PRECISION_BF16, PRECISION_FP8 = 0, 1, 2
 NUM_STAGES = 3
 STAGES = ("select", "breed", "evaluate")  # select = ranking + selection
@@ -75,7 +75,7 @@ class Params:
     alpha: float = 1.0
     init: int = 0
     precision: int = 0  # PRECISION_FP32, PRECISION_BF16 or PRECISION_FP8
-    eval_path: int = 0  # EVAL_AUTO, EVAL_SIMT or EVAL_TENSOR
+    eval_path: int = 0  # EVAL_AUTO, EVAL_SIMT, EVAL_TENSOR, EVAL_FUSED or EVAL_SMALL
     sigma_ctl: int = 0  # SIGMA_CONST, SIGMA_DECAY or SIGMA_SELF (Section 3.2)
     sigma_k: float = 1.0
     tau: float = 0.1

@@ -1,0 +1,168 @@
+"""The single-launch generation of small populations (eval_path SMALL; AUTO at
+the small configuration): one kernel ranks, selects, breeds and evaluates
+(Algorithm 1; Sections 3.1-3.3).  Against two independent checks:
+
+* the two-kernel path with the CUDA-core evaluation (eval_path SIMT) from the
+  same state, generation after generation: selection, children, sigma genes
+  and fitness bit-identical (the same operators and streams, the same FMA
+  order in both layers and the same batch reduction);
+* the FP64 oracle in lock step: selection exact, children and fitness within
+  the stated tolerances (tests/test_gpu_generation.py's _lockstep).
+Also AUTO's choice of the path, the batch scratch growing between calls and
+the shape limits."""
+import numpy as np
+import pytest
+
+from paper_1806_09819_gb300 import synthetic
+
+pytestmark = pytest.mark.gpu
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _batch(dims, batch, seed):
+    torch = _torch()
+    if dims[0] == 784:
+        x, y = synthetic.make_split(batch, seed=seed)
+        lv = synthetic.to_levels(x)
+    else:
+        rng = np.random.default_rng(seed)
+        lv = rng.integers(0, 256, size=(batch, dims[0])).astype(np.uint8)
+        y = rng.integers(0, dims[-1], size=batch).astype(np.int32)
+    return torch.from_numpy(np.ascontiguousarray(lv)).cuda(), torch.from_numpy(np.ascontiguousarray(y)).cuda()
+
+
+def _snapshot(st, sigma: bool):
+    f_adj, cor = st.leea_fitness(with_correct=True)
+    out = dict(pop=st.leea_get_population(), f_adj=f_adj, correct=cor, f_raw=st.leea_raw_fitness())
+    if st.gen > 0:
+        out["selection"] = st.leea_get_selection()
+    if sigma:
+        out["sigma"] = st.leea_get_sigma()
+    return out
+
+
+def _bits(a):
+    a = np.asarray(a)
+    return a.view(np.uint32) if a.dtype == np.float32 else a
+
+
+SMALL_CASES = [
+    # the small benchmark configuration: P 32, 784-32-10, batch 16
+    dict(dims=[784, 32, 10], pop=32, batches=[16] * 4, prm=dict(n_elite=1, p_c=0.5, sigma=0.005, mut_rate=0.1)),
+    # tournament, arithmetic crossover, inheritance blend, every gene mutated
+    dict(dims=[784, 16, 10], pop=20, batches=[1, 7, 16],
+         prm=dict(sel_op=1, tour_k=3, xo_op=1, alpha=0.3, sigma=0.02, mut_rate=1.0)),
+    # odd shapes: d_0 = 100, h = 24 (three slices), d_out = 3; batches up to the limit (tiles of 32, 64, 128)
+    dict(dims=[100, 24, 3], pop=9, batches=[33, 128, 64, 5], prm=dict(n_elite=2, xo_gene_p=0.2, sigma=0.1)),
+    # one slice per child, 16 outputs, decaying sigma; a population of one
+    dict(dims=[64, 8, 16], pop=1, batches=[3, 3], prm=dict(n_elite=0, sigma=0.05, sigma_ctl=1, sigma_k=2.0)),
+    # self-adaptive sigma genes; populations of two and 64
+    dict(dims=[784, 32, 10], pop=2, batches=[16, 2], prm=dict(sigma=0.01, sigma_ctl=2, tau=0.3, n_elite=0)),
+    dict(dims=[196, 48, 10], pop=64, batches=[24, 24, 100],
+         prm=dict(sigma=0.01, sigma_ctl=2, tau=0.1, p_c=0.75, n_elite=-1, p_e=0.05)),
+]
+
+
+@pytest.mark.parametrize("case", SMALL_CASES, ids=lambda c: f"{c['dims']}-P{c['pop']}-B{c['batches']}")
+def test_small_generation_bitwise_equals_two_kernel_simt_path(gpu, case):
+    from paper_1806_09819_gb300 import leea
+    dims, pop, prm = case["dims"], case["pop"], case["prm"]
+    sigma = prm.get("sigma_ctl", 0) == 2
+    runs = {}
+    for path in (leea.EVAL_SIMT, leea.EVAL_SMALL):
+        st = gpu.LeeaState(pop, dims, gpu.Params(**prm, eval_path=path), seed=123)
+        try:
+            snaps = []
+            for g, b in enumerate(case["batches"]):
+                st.leea_generation_u8(*_batch(dims, b, seed=1000 + g), 255.0)
+                snaps.append(_snapshot(st, sigma))
+            runs[path] = snaps
+        finally:
+            st.close()
+    for g, (a, b) in enumerate(zip(runs[leea.EVAL_SIMT], runs[leea.EVAL_SMALL])):
+        assert set(a) == set(b)
+        for key in a:
+            if key == "selection":
+                for x, y in zip(a[key], b[key]):
+                    np.testing.assert_array_equal(_bits(x), _bits(y), err_msg=f"generation {g}: {key}")
+            else:
+                np.testing.assert_array_equal(_bits(a[key]), _bits(b[key]), err_msg=f"generation {g}: {key}")
+
+
+def test_small_generation_lockstep_with_oracle(gpu, oracle_mod):
+    from test_gpu_generation import CONFIG_SMALL, _lockstep
+    from paper_1806_09819_gb300 import leea
+    prm = dict(CONFIG_SMALL["prm"], eval_path=leea.EVAL_SMALL)
+    _lockstep(gpu, oracle_mod, CONFIG_SMALL["dims"], CONFIG_SMALL["pop"], CONFIG_SMALL["batch"], prm, u8=True)
+    # the benchmark's operators; odd shapes; the degenerate population of one
+    _lockstep(gpu, oracle_mod, [784, 32, 10], 32, 16,
+              dict(n_elite=1, p_c=0.5, sigma=0.005, mut_rate=0.1, eval_path=leea.EVAL_SMALL), u8=True)
+    _lockstep(gpu, oracle_mod, [784, 24, 10], 7, 57, dict(sigma=0.05, xo_op=1, eval_path=leea.EVAL_SMALL), u8=True)
+    _lockstep(gpu, oracle_mod, [784, 8, 10], 1, 1, dict(sigma=0.05, n_elite=-1, eval_path=leea.EVAL_SMALL), u8=True)
+
+
+def test_auto_takes_the_single_launch_generation_when_small(gpu):
+    from paper_1806_09819_gb300 import leea
+    xd, yd = _batch([784, 32, 10], 16, seed=3)
+    st = gpu.LeeaState(32, [784, 32, 10], gpu.Params(sigma=0.005, mut_rate=0.1), seed=9)
+    try:
+        st.leea_generation_u8(xd, yd, 255.0)
+        st.leea_profile_enable(True)
+        for _ in range(5):
+            st.leea_generation_u8(xd, yd, 255.0)
+        prof = st.leea_profile_read()
+        launches = [prof[s][1] for s in leea.STAGES]
+        assert launches == [0, 5, 0], prof
+        # the same children and fitness as the explicit path
+        ref = gpu.LeeaState(32, [784, 32, 10], gpu.Params(sigma=0.005, mut_rate=0.1, eval_path=leea.EVAL_SMALL),
+                            seed=9)
+        try:
+            for _ in range(6):
+                ref.leea_generation_u8(xd, yd, 255.0)
+            np.testing.assert_array_equal(_bits(st.leea_get_population()), _bits(ref.leea_get_population()))
+            np.testing.assert_array_equal(_bits(st.leea_fitness()), _bits(ref.leea_fitness()))
+        finally:
+            ref.close()
+    finally:
+        st.close()
+    # a population too large for it: AUTO keeps the chain of kernels
+    big = gpu.LeeaState(1000, [784, 32, 10], gpu.Params(), seed=9)
+    try:
+        big.leea_generation_u8(xd, yd, 255.0)
+        big.leea_profile_enable(True)
+        big.leea_generation_u8(xd, yd, 255.0)
+        prof = big.leea_profile_read()
+        assert prof[leea.STAGES[0]][1] == 1 and prof[leea.STAGES[2]][1] == 1, prof
+    finally:
+        big.close()
+
+
+def test_small_generation_limits(gpu):
+    from paper_1806_09819_gb300 import leea
+    torch = _torch()
+    with pytest.raises(gpu.LeeaError):  # FP32 populations only
+        gpu.LeeaState(8, [784, 32, 10], gpu.Params(precision=1, eval_path=leea.EVAL_SMALL), 1)
+    with pytest.raises(gpu.LeeaError):  # one hidden layer
+        gpu.LeeaState(8, [196, 32, 16, 10], gpu.Params(eval_path=leea.EVAL_SMALL), 1)
+    for dims, batch in (([784, 12, 10], 8), ([784, 32, 10], 129), ([30, 16, 10], 8)):  # h % 8, batch, d_0 % 4
+        st = gpu.LeeaState(8, dims, gpu.Params(eval_path=leea.EVAL_SMALL), 1)
+        try:
+            x = torch.zeros((batch, dims[0]), dtype=torch.uint8, device="cuda")
+            y = torch.zeros(batch, dtype=torch.int32, device="cuda")
+            with pytest.raises(gpu.LeeaError) as e:
+                st.leea_generation_u8(x, y, 255.0)
+            assert e.value.status == gpu.EINVAL
+        finally:
+            st.close()
+    st = gpu.LeeaState(8, [784, 32, 10], gpu.Params(eval_path=leea.EVAL_SMALL), 1)
+    try:  # 8-bit inputs only
+        xf = torch.zeros((8, 784), dtype=torch.float32, device="cuda")
+        y = torch.zeros(8, dtype=torch.int32, device="cuda")
+        with pytest.raises(gpu.LeeaError):
+            st.leea_generation(xf, y)
+    finally:
+        st.close()
