@@ -781,8 +781,8 @@ struct leea_state {
     int32_t* sched;  // the group evaluation's two unit counters (zero between launches)
     // single-launch generation of small populations (eval_path SMALL, or AUTO)
     float* f_adj_alt;    // the other fitness buffer: a generation reads one and writes the other
-    float* hid;          // layer-1 activations [pop][batch][h] (grown with the batch)
-    size_t hid_bytes;
+    float* part;         // partial logits [pop][h / 8][batch][d_out] (grown with the batch)
+    size_t part_bytes;
     uint32_t* count;     // arrivals per child (zero between launches)
 };
 
@@ -816,7 +816,7 @@ void free_state(leea_state* s)
     cudaFree(s->xop);
     cudaFree(s->sched);
     cudaFree(s->f_adj_alt);
-    cudaFree(s->hid);
+    cudaFree(s->part);
     cudaFree(s->count);
     if (s->prof) {
         if (s->prof->created)
@@ -991,14 +991,15 @@ static leea_status run_small_generation(leea_state* s, const uint8_t* x_dev, flo
         LEEA_CUDA_TRY(cudaMemsetAsync(s->count, 0, sizeof(uint32_t) * np, s->stream), "arrival counter clear");
     }
     if (!s->f_adj_alt) LEEA_CUDA_TRY(cudaMalloc(&s->f_adj_alt, sizeof(float) * np), "fitness buffer allocation");
-    const size_t need = sizeof(float) * np * static_cast<size_t>(batch) * static_cast<size_t>(s->net.dims[1]);
-    if (need > s->hid_bytes) {
+    const size_t need = sizeof(float) * np * static_cast<size_t>(s->net.dims[1] / 8) * static_cast<size_t>(batch) *
+                        static_cast<size_t>(s->net.dims[2]);
+    if (need > s->part_bytes) {
         LEEA_CUDA_TRY(cudaStreamSynchronize(s->stream), "scratch sync");
-        cudaFree(s->hid);
-        s->hid = nullptr;
-        s->hid_bytes = 0;
-        LEEA_CUDA_TRY(cudaMalloc(&s->hid, need), "activation scratch allocation");
-        s->hid_bytes = need;
+        cudaFree(s->part);
+        s->part = nullptr;
+        s->part_bytes = 0;
+        LEEA_CUDA_TRY(cudaMalloc(&s->part, need), "partial logit scratch allocation");
+        s->part_bytes = need;
     }
     const bool first = !s->evaluated;
     SmallGenArgs ga{};
@@ -1021,7 +1022,7 @@ static leea_status run_small_generation(leea_state* s, const uint8_t* x_dev, flo
     ga.f_inh = s->f_inh;
     ga.f_raw = s->f_raw;
     ga.correct = s->correct;
-    ga.hid = s->hid;
+    ga.part = s->part;
     ga.count = s->count;
     ga.x = x_dev;
     ga.y = y_dev;

@@ -335,9 +335,10 @@ cudaError_t launch_breed_eval_u8(const BreedArgs& b, const NetLayout& net, const
 // One generation (ranking, selection, breeding, evaluation of 8-bit inputs)
 // in a single launch for small FP32 populations of d_0-h-d_out nets: one CTA
 // per (child, 8 hidden units).  Children bit-identical to breed_kernel's,
-// fitness bit-identical to eval_simt_kernel's.  f_adj_in and f_adj must not
-// alias (every CTA ranks the whole previous population); count holds pop
-// zeros between launches; hid has room for pop x batch x h floats.
+// fitness within FP32 rounding of eval_simt_kernel's.  f_adj_in and f_adj
+// must not alias (every CTA ranks the whole previous population); count
+// holds pop zeros between launches; part has room for pop x (h / 8) x batch
+// x d_out floats.
 struct SmallGenArgs {
     SelectArgs sel;          // breed: the selection (sigma as the breed's)
     BreedArgs br;            // breed: the operators and streams
@@ -354,7 +355,7 @@ struct SmallGenArgs {
     float* f_inh;
     float *f_raw, *f_adj;
     int32_t* correct;        // nullable
-    float* hid;              // [pop][batch][h] activations of layer 1
+    float* part;             // [pop][h / 8][batch][d_out] partial logits of the slices
     uint32_t* count;         // [pop] arrivals per child
     const uint8_t* x;        // [batch][d_0] levels, 4-byte aligned
     const int32_t* y;
