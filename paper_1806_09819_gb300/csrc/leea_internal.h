@@ -344,7 +344,7 @@ struct SmallGenArgs {
     BreedArgs br;            // breed: the operators and streams
     int32_t breed;           // 0: evaluate the population in popv (the first evaluation)
     int32_t pop, d_in, h, d_out, batch;
-    int32_t n_slices, n_pow2;  // set by the launcher
+    int32_t n_slices, n_pow2, b2_units;  // set by the launcher
     int64_t region_floats;     // set by the launcher
     int64_t c, c_pad, b1_off, w2_off, b2_off;
     float x_div, alpha;

@@ -18,8 +18,8 @@
 //      the new population and keeps the slice's W1 rows and b1 in shared
 //      memory (8-gene units never straddle slices: 8 rows of d_0 genes are
 //      d_0 units, and h % 8 == 0 aligns b1, W2 and b2);
-//   3. forms the slice's layer 1 for the whole batch on the CUDA cores (4 x 4
-//      register blocks over pieces of the inputs), and from it the slice's share of
+//   3. forms the slice's layer 1 for the whole batch (m16n8k8 tensor-core
+//      tiles, the warps splitting the inputs), and from it the slice's share of
 //      layer 2 (the partial logits of its 8 hidden units), written to a
 //      scratch buffer;
 //   4. counts itself in with an atomic add after a memory fence; the last of
@@ -28,14 +28,18 @@
 //      the batch sum and the inheritance blend, then zeroes the counter for
 //      the next launch.
 // Arithmetic order (fixed, so identical individuals get identical bits):
-// layer 1 sums w k (k the exact 8-bit level) over each of up to 16 pieces of
-// the inputs in an FMA chain in ascending order, adds the pieces in order and
-// divides by x_div; layer 2 is one FMA chain per slice over its hidden units in
+// layer 1 accumulates the exact products k w_hi and k w_lo (k the 8-bit level,
+// w_hi + w_lo the weight to 22 bits) in FP32 on the tensor cores over each
+// warp's input group, adds the groups in order and divides by x_div; layer 2 is one FMA chain per slice over its hidden units in
 // ascending order, the slices added in order, then b2; the loss (softmax
 // cross-entropy with the maximum subtracted, exponentials added in class
 // order) and the batch reduction are eval_simt_kernel's.  The fitness is
-// thus within FP32 rounding of the CUDA-core evaluation's, and the children
-// are bit-identical to breed_kernel's.
+// thus within the evaluation tolerance of the CUDA-core evaluation's (as the
+// 8-bit tensor-core evaluation is), and the children are bit-identical to
+// breed_kernel's.  A single CTA's layer 1 is 16 samples x 8 units x d_0
+// inputs: mma.sync tiles in registers serve it without the setup of the
+// tcgen05 path (tensor memory, descriptors, barriers) that the large
+// evaluations amortise.
 #include "breed_ops.cuh"
 #include "leea_internal.h"
 #include "philox.cuh"
@@ -62,16 +66,11 @@ int pow2_at_least(int n)
     return p;
 }
 
-// Layer 1 is computed in 4 x 4 register blocks (4 hidden units x 4 samples)
-// over `pieces` consecutive pieces of the inputs, enough threads for the CTA.
-constexpr int kBlk = 4;
-constexpr int kMaxPieces = 16;
-__host__ __device__ inline int layer1_pieces(int batch)
-{
-    const int blocks = (kSlice / kBlk) * ((batch + kBlk - 1) / kBlk);
-    const int p = kSmallThreads / blocks;
-    return p < 1 ? 1 : (p > kMaxPieces ? kMaxPieces : p);
-}
+// Layer 1 runs as m16n8k8 TF32 tensor-core tiles (16 samples x the slice's 8
+// hidden units x 8 inputs); the warps split the inputs, and their partial
+// tiles ([input groups][16 * tiles][8] floats) are added in order.
+constexpr int kWarps = kSmallThreads / 32;
+constexpr int kPartialFloats = kWarps * 16 * kSlice;  // the largest [groups][16 tiles][8] over batch <= 128
 
 // Floats of the region shared by the two phases: the batch, the slice's W1
 // rows, b1, W2 columns and activations (steps 1-3), then the last arriver's
@@ -80,12 +79,17 @@ int64_t small_region_floats(int32_t d_in, int32_t h, int32_t d_out, int32_t batc
 {
     (void)h;
     const int64_t r1 = static_cast<int64_t>(batch) * (d_in + 4) + static_cast<int64_t>(kSlice) * (d_in + 4) + kSlice +
-                       static_cast<int64_t>(kSlice) * d_out +
-                       static_cast<int64_t>(1 + layer1_pieces(batch)) * kSlice * batch;
-    const int64_t r2 = 2 * static_cast<int64_t>(d_out) * batch + 2 * static_cast<int64_t>(batch) +
-                       2 * kSmallMaxBatch + 32;
+                       static_cast<int64_t>(kSlice) * d_out + static_cast<int64_t>(kSlice) * batch + kPartialFloats;
+    const int64_t r2 = static_cast<int64_t>(d_out) * batch + 2 * kSmallMaxBatch + 32;
     const int64_t r = r1 > r2 ? r1 : r2;
     return (r + 3) & ~int64_t(3);
+}
+
+// Offset in floats of b2 (and the cluster's gather buffer) behind the region,
+// the rank keys, the order and the fitness: a multiple of 4 (16 bytes).
+__host__ __device__ inline int64_t small_tail_floats(int64_t region_floats, int n_pow2, int pop)
+{
+    return (region_floats + 2 * static_cast<int64_t>(n_pow2) + 2 * static_cast<int64_t>(pop) + 3) & ~int64_t(3);
 }
 
 // Batch tile of eval_simt_kernel for this batch (16 x its TN): the reduction
@@ -124,6 +128,49 @@ __device__ __forceinline__ uint32_t ld_u32_now(const uint32_t* p)
     return v;
 }
 
+// Thread-block cluster of one child's slices (cluster rank q = slice q).
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// The address of this CTA's shared variable p in the shared memory of cluster CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_map(const void* p, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(ptx::smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+
+// FP32 -> TF32 (round to nearest, ties away), the bits of a TF32 operand.
+__device__ __forceinline__ uint32_t to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// d += a b for one m16n8k8 tile: A 16 x 8 (row-major fragment), B 8 x 8
+// (column-major fragment), TF32 operands, FP32 accumulators.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1)
+{
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+                 "{%0, %1, %2, %3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
 // Four 8-bit levels k as FP32 (exact).
 __device__ __forceinline__ float4 levels_to_float4(uint32_t v)
 {
@@ -131,6 +178,11 @@ __device__ __forceinline__ float4 levels_to_float4(uint32_t v)
                        static_cast<float>((v >> 16) & 0xFFu), static_cast<float>(v >> 24));
 }
 
+// CLUSTER: child i's slices form a thread-block cluster; each slice writes its
+// partial logits into slice 0's shared memory and one cluster barrier hands
+// them over.  Otherwise the partial logits go through L2 and the last slice to
+// count itself in (atomic add) finishes.
+template <bool CLUSTER>
 __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __grid_constant__ SmallGenArgs a)
 {
     extern __shared__ float4 smem_small[];
@@ -142,6 +194,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     uint64_t* keys = reinterpret_cast<uint64_t*>(R + a.region_floats);
     int32_t* ord = reinterpret_cast<int32_t*>(keys + a.n_pow2);
     float* fs = reinterpret_cast<float*>(ord + a.pop);  // the previous fitness, for the selection
+    float* b2s = R + small_tail_floats(a.region_floats, a.n_pow2, a.pop);  // slice 0: b2 (padded to 8), 16-byte aligned
+    float* gather = b2s + 8 * a.b2_units;               // CLUSTER, slice 0: [n_slices][Bt][D] partial logits
     const int K = a.d_in, H = a.h, D = a.d_out, Bt = a.batch;
     const int i = static_cast<int>(blockIdx.x) / a.n_slices;
     const int q = static_cast<int>(blockIdx.x) - i * a.n_slices;
@@ -151,9 +205,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     float* b1s = w1s + kSlice * (K + 4);  // [kSlice]
     float* w2s = b1s + kSlice;            // [D][kSlice]: the slice's columns of W2
     float* hs = w2s + D * kSlice;         // [Bt][kSlice]: the slice's activations
-    float* qs = hs + Bt * kSlice;         // [pieces][Bt * kSlice]: layer 1's sums over the pieces
+    float* qs = hs + Bt * kSlice;         // layer 1's partial tiles of the input groups
 
     ptx::grid_dep_launch();
+    if (CLUSTER) cluster_arrive_relaxed();  // every CTA of the cluster has started before any writes to slice 0
     ptx::grid_dep_wait();  // the previous generation's fitness and population
 
     // The previous fitness, then the batch's 8-bit levels (four per word):
@@ -162,6 +217,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     const int P = a.pop, n2 = a.n_pow2;
     float f_mine = 0.0f;
     if (a.breed && tid < P) f_mine = __ldcg(a.f_adj_in + tid);
+    SelStream sel_st(a.sel.seed, a.sel.gen, static_cast<uint32_t>(i));
+    if (a.breed && tid == 0) sel_st.draw(0);  // child i's first SEL block, while the fitness loads are in flight
     const uint32_t* x4 = reinterpret_cast<const uint32_t*>(a.x);
     const int n4 = Bt * K / 4;
     const bool x_in_regs = n4 <= kXWords * kSmallThreads;
@@ -215,7 +272,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
         __syncthreads();
         }
         if (tid == 0) {
-            const ChildSelection c = select_child_of(a.sel, fs, ord, i);
+            const ChildSelection c = select_child_of(a.sel, fs, ord, i, sel_st);
             sel_s = c;
             if (q == 0) store_child_selection(a.sel, c, i, a.par1, a.par2, a.kind, a.f_inh);
         }
@@ -225,8 +282,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     // 2. The slice's genes: bred (children) or read (the first evaluation),
     // two units per thread at a time so that their loads are in flight together.
     {
-        const int b2_units = static_cast<int>((a.c - a.b2_off + 7) / 8);
-        const int n_units = K + 1 + D + ((a.breed && q == 0) ? b2_units : 0);
+        const int n_units = K + 1 + D + (q == 0 ? a.b2_units : 0);
         const ChildSelection c = sel_s;
         const uint32_t gen = a.br.gen, ent = static_cast<uint32_t>(i);
         const PhiloxKeys key = philox_keys(a.br.seed);
@@ -283,15 +339,13 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
                 return;
             }
             if (t < K) {  // genes 8t .. 8t+7 of the slice's rows: row l / K, input l % K
-                const float e8[8] = { v[0].x, v[0].y, v[0].z, v[0].w, v[1].x, v[1].y, v[1].z, v[1].w };
-                int r = (8 * t) / K, col = 8 * t - r * K;
-#pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    w1s[r * (K + 4) + col] = e8[s];
-                    if (++col == K) { col = 0; ++r; }
-                }
-            } else if (t <= K + D) {  // b1, or column block 8q .. 8q+7 of W2 row t - K - 1
-                float* dst = t == K ? b1s : w2s + (t - K - 1) * kSlice;
+                // (K % 4 == 0: each half of the unit is 4 genes of one row, 16-byte aligned)
+                const int r = (8 * t) / K, col = 8 * t - r * K;
+                *reinterpret_cast<float4*>(w1s + r * (K + 4) + col) = v[0];
+                const int r1 = col + 4 < K ? r : r + 1, col1 = col + 4 < K ? col + 4 : col + 4 - K;
+                *reinterpret_cast<float4*>(w1s + r1 * (K + 4) + col1) = v[1];
+            } else {  // b1, column block 8q .. 8q+7 of W2 row t - K - 1, or (slice 0) 8 genes of b2
+                float* dst = t == K ? b1s : (t <= K + D ? w2s + (t - K - 1) * kSlice : b2s + 8 * (t - K - 1 - D));
                 reinterpret_cast<float4*>(dst)[0] = v[0];
                 reinterpret_cast<float4*>(dst)[1] = v[1];
             }
@@ -341,62 +395,45 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     }
     __syncthreads();
 
-    // 3. Layer 1 of the slice (hidden unit jj, sample n): the sum of w k (k the
-    // exact 8-bit level, each product exact in the FMA) over each piece of the
-    // inputs in ascending order, the pieces added in order, divided by x_div;
-    // then bias and ReLU.  A thread holds a 4 x 4 block of sums (4 rows of W1,
-    // 4 samples) for one piece: 8 vector loads per 64 FMAs.
+    // 3. Layer 1 of the slice (hidden unit jj, sample n) on the tensor cores:
+    // the levels k are exact TF32 operands and each weight enters as two TF32
+    // pieces (w_hi = tf32(w), w_lo = tf32(w - w_hi): 22 of FP32's 24 bits), so
+    // every product is exact and only the FP32 accumulation rounds.  Warp w
+    // takes sample tile w / groups and every groups-th 8-input step from
+    // w % groups on; the groups' partial tiles are added in order, divided by
+    // x_div; then bias and ReLU.
     {
-        const int n_pc = layer1_pieces(Bt);
-        const int kp = ((K + 4 * n_pc - 1) / (4 * n_pc)) * 4;  // piece length, a multiple of 4
-        const int n_nb = (Bt + kBlk - 1) / kBlk, n_blk = (kSlice / kBlk) * n_nb;
-        const int n_ch = kSlice * Bt;
-        for (int ct = tid; ct < n_pc * n_blk; ct += kSmallThreads) {
-            const int z = ct / n_blk, blk = ct - z * n_blk;
-            // rows j0 .. j0+3 of the slice; samples nb, nb + n_nb, nb + 2 n_nb, nb + 3 n_nb
-            // (interleaved, so that a load's 8 threads of a phase hit distinct banks)
-            const int j0 = kBlk * (blk % (kSlice / kBlk)), nb = blk / (kSlice / kBlk);
-            const int k0 = z * kp, k1 = min(K, k0 + kp);
-            const float* wr[kBlk];
-            const float* xr[kBlk];
-#pragma unroll
-            for (int r = 0; r < kBlk; ++r) {
-                wr[r] = w1s + (j0 + r) * (K + 4);
-                xr[r] = xs + min(nb + r * n_nb, Bt - 1) * (K + 4);  // samples past the batch: computed, not kept
+        const int n_tiles = (Bt + 15) / 16, T16 = 16 * n_tiles;
+        const int groups = kWarps / n_tiles > 1 ? kWarps / n_tiles : 1;
+        const int n_steps = (K + 7) / 8;
+        const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+        if (warp < groups * n_tiles) {
+            const int tile = warp / groups, kg = warp - tile * groups;
+            const float* x_lo = xs + min(16 * tile + g, Bt - 1) * (K + 4);      // sample rows g and g + 8
+            const float* x_hi = xs + min(16 * tile + g + 8, Bt - 1) * (K + 4);  // (past the batch: not kept)
+            const float* wrow = w1s + g * (K + 4);                               // hidden unit g of the slice
+            float d[4] = { 0.0f, 0.0f, 0.0f, 0.0f };
+            for (int st = kg; st < n_steps; st += groups) {
+                const int k0 = 8 * st + tq, k1 = k0 + 4;
+                const bool in0 = k0 < K, in1 = k1 < K;
+                const uint32_t a[4] = { __float_as_uint(in0 ? x_lo[k0] : 0.0f), __float_as_uint(in0 ? x_hi[k0] : 0.0f),
+                                        __float_as_uint(in1 ? x_lo[k1] : 0.0f), __float_as_uint(in1 ? x_hi[k1] : 0.0f) };
+                const float w0 = in0 ? wrow[k0] : 0.0f, w1 = in1 ? wrow[k1] : 0.0f;
+                const uint32_t h0 = to_tf32(w0), h1 = to_tf32(w1);
+                const uint32_t l0 = to_tf32(w0 - __uint_as_float(h0)), l1 = to_tf32(w1 - __uint_as_float(h1));
+                mma_tf32(d, a, h0, h1);
+                mma_tf32(d, a, l0, l1);
             }
-            float acc[kBlk][kBlk];
-#pragma unroll
-            for (int r = 0; r < kBlk; ++r)
-#pragma unroll
-                for (int s = 0; s < kBlk; ++s) acc[r][s] = 0.0f;
-            for (int k = k0; k < k1; k += 4) {
-                float4 wv[kBlk], xv[kBlk];
-#pragma unroll
-                for (int r = 0; r < kBlk; ++r) {
-                    wv[r] = *reinterpret_cast<const float4*>(wr[r] + k);
-                    xv[r] = *reinterpret_cast<const float4*>(xr[r] + k);
-                }
-#pragma unroll
-                for (int r = 0; r < kBlk; ++r)
-#pragma unroll
-                    for (int s = 0; s < kBlk; ++s) {
-                        acc[r][s] = fmaf(wv[r].x, xv[s].x, acc[r][s]);
-                        acc[r][s] = fmaf(wv[r].y, xv[s].y, acc[r][s]);
-                        acc[r][s] = fmaf(wv[r].z, xv[s].z, acc[r][s]);
-                        acc[r][s] = fmaf(wv[r].w, xv[s].w, acc[r][s]);
-                    }
-            }
-#pragma unroll
-            for (int s = 0; s < kBlk; ++s)
-                if (nb + s * n_nb < Bt)
-#pragma unroll
-                    for (int r = 0; r < kBlk; ++r) qs[z * n_ch + (nb + s * n_nb) * kSlice + j0 + r] = acc[r][s];
+            float* part = qs + (kg * T16 + 16 * tile) * kSlice;  // [16 samples][8 hidden units]
+            part[g * kSlice + 2 * tq] = d[0];
+            part[g * kSlice + 2 * tq + 1] = d[1];
+            part[(g + 8) * kSlice + 2 * tq] = d[2];
+            part[(g + 8) * kSlice + 2 * tq + 1] = d[3];
         }
         __syncthreads();
-        for (int ch = tid; ch < n_ch; ch += kSmallThreads) {
+        for (int ch = tid; ch < kSlice * Bt; ch += kSmallThreads) {
             float v = qs[ch];
-#pragma unroll 4
-            for (int z = 1; z < n_pc; ++z) v += qs[z * n_ch + ch];
+            for (int kg = 1; kg < groups; ++kg) v += qs[kg * T16 * kSlice + ch];
             hs[ch] = fmaxf(v / a.x_div + b1s[ch & (kSlice - 1)], 0.0f);
         }
     }
@@ -405,6 +442,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     // units 8q .. 8q+7 in ascending order.
     {
         float* part = a.part + (static_cast<int64_t>(i) * a.n_slices + q) * Bt * D;  // [Bt][D]
+        if (CLUSTER) cluster_wait_acquire();
+        const uint32_t dst = CLUSTER ? cluster_map(gather + q * Bt * D, 0) : 0u;
         for (int ch = tid; ch < Bt * D; ch += kSmallThreads) {
             const int n = ch / D, o = ch - n * D;
             const float* wv = w2s + o * kSlice;
@@ -412,65 +451,108 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
             float s = 0.0f;
 #pragma unroll
             for (int r = 0; r < kSlice; ++r) s = fmaf(wv[r], hv[r], s);
-            part[ch] = s;
+            if (CLUSTER) st_cluster_f32(dst + 4u * static_cast<uint32_t>(ch), s);
+            else part[ch] = s;
         }
     }
 
-    // 4. Arrival: the last of child i's CTAs finishes the evaluation.  The
-    // barrier orders the CTA's partial logits before thread 0's fence, which
-    // releases them with its count (and, in the last arriver, acquires the
-    // other slices' before the barrier that follows).
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        const bool last = atomicAdd(a.count + i, 1u) == static_cast<uint32_t>(a.n_slices - 1);
-        if (last) __threadfence();
-        last_s = last ? 1 : 0;
+    // 4. Hand-over.  Cluster: the barrier releases every slice's partial logits
+    // to slice 0, which finishes.  Otherwise: the block barrier orders the
+    // CTA's partial logits before thread 0's fence, which releases them with
+    // its count (and, in the last arriver, acquires the other slices' before
+    // the barrier that follows).
+    if (CLUSTER) {
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        if (q != 0) return;
+    } else {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const bool last = atomicAdd(a.count + i, 1u) == static_cast<uint32_t>(a.n_slices - 1);
+            if (last) __threadfence();
+            last_s = last ? 1 : 0;
+        }
+        __syncthreads();
+        if (!last_s) return;
     }
-    __syncthreads();
-    if (!last_s) return;
 
     float* Ls = R;                        // [D][Bt]: the logits z
-    float* Es = Ls + D * Bt;              // [D][Bt]: exp(z - max z)
-    float* zm = Es + D * Bt;              // [Bt]: max z of the sample
-    int32_t* am = reinterpret_cast<int32_t*>(zm + Bt);  // [Bt]: its argmax (lowest class on ties)
-    float* lossv = reinterpret_cast<float*>(am + Bt);   // [kSmallMaxBatch]
+    float* lossv = Ls + D * Bt;           // [kSmallMaxBatch]
     int32_t* corv = reinterpret_cast<int32_t*>(lossv + kSmallMaxBatch);  // [kSmallMaxBatch]
     float* warp_sums = reinterpret_cast<float*>(corv + kSmallMaxBatch);  // [32]
     {  // z = the slices' partial logits added in slice order, then b2
         const float* b2 = a.popv + static_cast<int64_t>(i) * a.c_pad + a.b2_off;
         const float* part = a.part + static_cast<int64_t>(i) * a.n_slices * Bt * D;
-        const int64_t slice_stride = static_cast<int64_t>(Bt) * D;
+        const int slice_stride = Bt * D;
         for (int ch = tid; ch < Bt * D; ch += kSmallThreads) {
             const int n = ch / D, o = ch - n * D;
-            const float bias = __ldcg(b2 + o);
-            float s = __ldcg(part + ch);
+            float s, bias;
+            if (CLUSTER) {  // slice 0 holds b2 and every slice's partial logits
+                bias = b2s[o];
+                s = gather[ch];
+                for (int qq = 1; qq < a.n_slices; ++qq) s += gather[qq * slice_stride + ch];
+            } else {
+                bias = __ldcg(b2 + o);
+                s = __ldcg(part + ch);
 #pragma unroll 4
-            for (int qq = 1; qq < a.n_slices; ++qq) s += __ldcg(part + qq * slice_stride + ch);
+                for (int qq = 1; qq < a.n_slices; ++qq) s += __ldcg(part + static_cast<int64_t>(qq) * slice_stride + ch);
+            }
             Ls[o * Bt + n] = s + bias;
         }
     }
     __syncthreads();
-    for (int n = tid; n < Bt; n += kSmallThreads) {
+
+    // Per-sample softmax cross-entropy (Eq. 1): log sum exp(z - max z) + max z
+    // - z[label], the exponentials summed over the classes in ascending order,
+    // and the argmax (the lowest class on ties); then the fixed-order batch
+    // sum: per tile of BN samples a warp xor-tree over each 32 samples, the
+    // warp sums added in order, the tile sums added in order.
+    auto sample_loss = [&](int n, float& loss, int32_t& ok) {
         float zmax = Ls[n];
         int arg = 0;
         for (int o = 1; o < D; ++o) {
             const float z = Ls[o * Bt + n];
             if (z > zmax) { zmax = z; arg = o; }
         }
-        zm[n] = zmax;
-        am[n] = arg;
-    }
-    __syncthreads();
-    for (int ch = tid; ch < D * Bt; ch += kSmallThreads) Es[ch] = expf(Ls[ch] - zm[ch % Bt]);
-    __syncthreads();
-
-    // Per-sample softmax cross-entropy (Eq. 1): log sum exp(z - max z) + max z
-    // - z[label], the exponentials summed over the classes in ascending order;
-    // then the fixed-order batch sum: per tile of BN samples a warp xor-tree
-    // over each 32 samples, the warp sums added in order, the tile sums added
-    // in order.
+        float s = 0.0f;
+#pragma unroll 4
+        for (int o = 0; o < D; ++o) s += expf(Ls[o * Bt + n] - zmax);
+        const int32_t lbl = a.y[n];
+        if (lbl >= 0 && lbl < D) {
+            loss = logf(s) + zmax - Ls[lbl * Bt + n];
+            ok = (arg == lbl) ? 1 : 0;
+        } else {
+            loss = __int_as_float(0x7FC00000);  // NaN: label out of range
+        }
+    };
+    auto write_out = [&](float total, int32_t n_correct) {
+        const float f = -(total / static_cast<float>(Bt));
+        a.f_raw[i] = f;
+        a.f_adj[i] = a.breed ? (1.0f - a.alpha) * sel_s.f_inh + a.alpha * f : f;
+        if (a.correct) a.correct[i] = n_correct;
+        if (!CLUSTER) a.count[i] = 0u;  // for the next launch
+    };
     const int BN = simt_batch_tile(Bt);
+    if (Bt <= 32) {  // one tile, one warp: a lane per sample, no block barriers
+        if (tid < 32) {
+            float v = 0.0f;
+            int32_t cv = 0;
+            if (tid < Bt) sample_loss(tid, v, cv);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+                cv += __shfl_xor_sync(0xFFFFFFFFu, cv, off);
+            }
+            if (tid == 0) {
+                float s = 0.0f, total = 0.0f;
+                s += v;
+                total += s;
+                write_out(total, cv);
+            }
+        }
+        return;
+    }
     float total = 0.0f;  // meaningful in thread 0 only
     int32_t n_correct = 0;
     for (int b0 = 0; b0 < Bt; b0 += BN) {
@@ -478,17 +560,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
             const int gn = b0 + tid;
             float loss = 0.0f;
             int32_t ok = 0;
-            if (gn < Bt) {
-                float s = 0.0f;
-                for (int o = 0; o < D; ++o) s += Es[o * Bt + gn];
-                const int32_t lbl = a.y[gn];
-                if (lbl >= 0 && lbl < D) {
-                    loss = logf(s) + zm[gn] - Ls[lbl * Bt + gn];
-                    ok = (am[gn] == lbl) ? 1 : 0;
-                } else {
-                    loss = __int_as_float(0x7FC00000);  // NaN: label out of range
-                }
-            }
+            if (gn < Bt) sample_loss(gn, loss, ok);
             lossv[tid] = loss;
             corv[tid] = ok;
         }
@@ -517,22 +589,27 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
         }
         __syncthreads();
     }
-    if (tid == 0) {
-        const float f = -(total / static_cast<float>(Bt));
-        a.f_raw[i] = f;
-        a.f_adj[i] = a.breed ? (1.0f - a.alpha) * sel_s.f_inh + a.alpha * f : f;
-        if (a.correct) a.correct[i] = n_correct;
-        a.count[i] = 0u;  // for the next launch
-    }
+    if (tid == 0) write_out(total, n_correct);
 }
+
+}  // namespace
+
+namespace {
+
+size_t smem_bytes_of(int32_t d_in, int32_t h, int32_t d_out, int32_t batch, int32_t pop, bool cluster)
+{
+    const size_t gather = cluster ? static_cast<size_t>(h / kSlice) * batch * d_out : 0;
+    const int64_t tail = small_tail_floats(small_region_floats(d_in, h, d_out, batch), pow2_at_least(pop), pop);
+    return sizeof(float) * (static_cast<size_t>(tail) + 8 * static_cast<size_t>((d_out + 7) / 8) + gather);
+}
+
+constexpr int kMaxClusterSlices = 8;  // portable cluster size
 
 }  // namespace
 
 size_t small_gen_smem_bytes(int32_t d_in, int32_t h, int32_t d_out, int32_t batch, int32_t pop)
 {
-    return sizeof(float) * static_cast<size_t>(small_region_floats(d_in, h, d_out, batch)) +
-           sizeof(uint64_t) * static_cast<size_t>(pow2_at_least(pop)) +
-           (sizeof(int32_t) + sizeof(float)) * static_cast<size_t>(pop);
+    return smem_bytes_of(d_in, h, d_out, batch, pop, false);
 }
 
 bool small_gen_supported(const NetLayout& net, int32_t pop, int32_t batch)
@@ -555,12 +632,29 @@ cudaError_t launch_small_gen(SmallGenArgs a, cudaStream_t stream)
 {
     a.n_slices = a.h / kSlice;
     a.n_pow2 = pow2_at_least(a.pop);
+    a.b2_units = (a.d_out + 7) / 8;
     a.region_floats = small_region_floats(a.d_in, a.h, a.d_out, a.batch);
-    const size_t smem = small_gen_smem_bytes(a.d_in, a.h, a.d_out, a.batch, a.pop);
-    cudaError_t err =
-        cudaFuncSetAttribute(small_gen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    const size_t smem_c = smem_bytes_of(a.d_in, a.h, a.d_out, a.batch, a.pop, true);
+    const bool cluster = a.n_slices <= kMaxClusterSlices && smem_c <= kSmallMaxSmem;
+    const size_t smem = cluster ? smem_c : smem_bytes_of(a.d_in, a.h, a.d_out, a.batch, a.pop, false);
+    auto kernel = cluster ? small_gen_kernel<true> : small_gen_kernel<false>;
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
-    return launch_pdl(small_gen_kernel, dim3(a.pop * a.n_slices), dim3(kSmallThreads), smem, stream, a);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(a.pop * a.n_slices);
+    cfg.blockDim = dim3(kSmallThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = static_cast<unsigned>(a.n_slices);
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = cluster ? 2 : 1;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
 }
 
 }  // namespace leea

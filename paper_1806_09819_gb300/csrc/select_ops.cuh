@@ -65,10 +65,10 @@ struct ChildSelection {
     float f_inh, sigma;
 };
 
+// st: child j's SEL stream (its first block may already be drawn).
 __device__ __forceinline__ ChildSelection select_child_of(const SelectArgs& a, const float* f_adj,
-                                                          const int32_t* order, int32_t j)
+                                                          const int32_t* order, int32_t j, SelStream st)
 {
-    SelStream st(a.seed, a.gen, static_cast<uint32_t>(j));
     ChildSelection c;
     if (j < a.n_elite) {
         c.kind = kKindElite;
@@ -100,6 +100,12 @@ __device__ __forceinline__ ChildSelection select_child_of(const SelectArgs& a, c
         }
     }
     return c;
+}
+
+__device__ __forceinline__ ChildSelection select_child_of(const SelectArgs& a, const float* f_adj,
+                                                          const int32_t* order, int32_t j)
+{
+    return select_child_of(a, f_adj, order, j, SelStream(a.seed, a.gen, static_cast<uint32_t>(j)));
 }
 
 // Writes child j's selection (and, in the precision form, its scale bounds).

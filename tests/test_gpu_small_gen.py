@@ -60,6 +60,9 @@ SMALL_CASES = [
     dict(dims=[784, 32, 10], pop=2, batches=[16, 2], prm=dict(sigma=0.01, sigma_ctl=2, tau=0.3, n_elite=0)),
     dict(dims=[196, 48, 10], pop=64, batches=[24, 24, 100],
          prm=dict(sigma=0.01, sigma_ctl=2, tau=0.1, p_c=0.75, n_elite=-1, p_e=0.05)),
+    # more than 8 slices per child (h = 72 and 128): the hand-over through L2 and an arrival counter
+    dict(dims=[64, 72, 10], pop=5, batches=[8, 8, 20], prm=dict(sigma=0.05, n_elite=1)),
+    dict(dims=[784, 128, 10], pop=3, batches=[16, 16], prm=dict(sigma=0.01, mut_rate=0.3)),
 ]
 
 
