@@ -49,15 +49,17 @@ __device__ __forceinline__ float4 clear_padding(float4 v, int64_t i0, int64_t c)
     return v;
 }
 
-// Mutation of one lane's unit (8 genes in v) whose mask bits are `hit`.  Slot
+// Normals of one lane's unit (8 genes) whose mask bits are `hit`.  Slot
 // s = 0..3 names the Box-Muller pair of genes 8u + 2s, 8u + 2s + 1, i.e. pair
 // s & 1 of NORMAL block 2u + (s >> 1).  The warp lists the slots that hold a
 // masked gene, slot by slot (one ballot each), in its shared-memory job list
 // (kJobs = 4 x 32 entries); consecutive lanes compute the listed normals and
-// every lane reads its own back.  unit_of(o) is the unit owned by lane o.
+// every lane reads its own back into z (zero for slots without a masked
+// gene).  unit_of(o) is the unit owned by lane o.  Every lane of the warp
+// calls it (hit = 0 for a lane without a unit).
 template <typename UnitOf>
-__device__ __forceinline__ void mutate8(float sigma, uint32_t gen, const PhiloxKeys& key, uint32_t ent, uint32_t hit,
-                                        float4 (&v)[2], int lane, float2* job_z, uint8_t* job_code, UnitOf unit_of)
+__device__ __forceinline__ void normals8(uint32_t gen, const PhiloxKeys& key, uint32_t ent, uint32_t hit,
+                                         float2 (&z)[4], int lane, float2* job_z, uint8_t* job_code, UnitOf unit_of)
 {
     constexpr int kSlots = 4;
     const uint32_t lt = (1u << lane) - 1u;
@@ -79,10 +81,15 @@ __device__ __forceinline__ void mutate8(float sigma, uint32_t gen, const PhiloxK
         job_z[job] = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
     }
     __syncwarp();
-    float2 z[kSlots];
 #pragma unroll
     for (int sl = 0; sl < kSlots; ++sl)
         z[sl] = ((hit >> (2 * sl)) & 3u) ? job_z[idx[sl]] : make_float2(0.f, 0.f);
+    __syncwarp();  // the list is reused by the next unit
+}
+
+// The mutation step of the masked genes: v += sigma z.
+__device__ __forceinline__ void apply_mutation8(float sigma, uint32_t hit, const float2 (&z)[4], float4 (&v)[2])
+{
     if (hit & 0x01u) v[0].x = fmaf(sigma, z[0].x, v[0].x);
     if (hit & 0x02u) v[0].y = fmaf(sigma, z[0].y, v[0].y);
     if (hit & 0x04u) v[0].z = fmaf(sigma, z[1].x, v[0].z);
@@ -91,7 +98,17 @@ __device__ __forceinline__ void mutate8(float sigma, uint32_t gen, const PhiloxK
     if (hit & 0x20u) v[1].y = fmaf(sigma, z[2].y, v[1].y);
     if (hit & 0x40u) v[1].z = fmaf(sigma, z[3].x, v[1].z);
     if (hit & 0x80u) v[1].w = fmaf(sigma, z[3].y, v[1].w);
-    __syncwarp();  // the list is reused by the next unit
+}
+
+// Mutation of one lane's unit (8 genes in v) whose mask bits are `hit`: its
+// normals through the warp's job list (normals8), then the step.
+template <typename UnitOf>
+__device__ __forceinline__ void mutate8(float sigma, uint32_t gen, const PhiloxKeys& key, uint32_t ent, uint32_t hit,
+                                        float4 (&v)[2], int lane, float2* job_z, uint8_t* job_code, UnitOf unit_of)
+{
+    float2 z[4];
+    normals8(gen, key, ent, hit, z, lane, job_z, job_code, unit_of);
+    apply_mutation8(sigma, hit, z, v);
 }
 
 // The same mutation of one unit by a single thread (no job list): each masked
@@ -109,14 +126,7 @@ __device__ __forceinline__ void mutate8_direct(float sigma, uint32_t gen, const 
             z[sl] = (sl & 1) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
         }
     }
-    if (hit & 0x01u) v[0].x = fmaf(sigma, z[0].x, v[0].x);
-    if (hit & 0x02u) v[0].y = fmaf(sigma, z[0].y, v[0].y);
-    if (hit & 0x04u) v[0].z = fmaf(sigma, z[1].x, v[0].z);
-    if (hit & 0x08u) v[0].w = fmaf(sigma, z[1].y, v[0].w);
-    if (hit & 0x10u) v[1].x = fmaf(sigma, z[2].x, v[1].x);
-    if (hit & 0x20u) v[1].y = fmaf(sigma, z[2].y, v[1].y);
-    if (hit & 0x40u) v[1].z = fmaf(sigma, z[3].x, v[1].z);
-    if (hit & 0x80u) v[1].w = fmaf(sigma, z[3].y, v[1].w);
+    apply_mutation8(sigma, hit, z, v);
 }
 
 }  // namespace leea

@@ -7,9 +7,10 @@
 //
 // Grid: one CTA per (child i, slice q of kSlice = 8 hidden units), no waiting
 // between CTAs.  Each CTA
-//   1. ranks the whole previous population itself (a bitonic sort of the
-//      64-bit rank keys: in one warp's registers up to 32 keys, else in
-//      shared memory) and selects child i with the
+//   1. ranks the whole previous population itself (up to 32 individuals one
+//      warp counts, for each, the rank keys below its own while the other
+//      warps draw; beyond, a bitonic sort in shared memory) and selects child
+//      i with the
 //      selection kernels' code (select_ops.cuh), so that no CTA depends on
 //      another's selection;
 //   2. breeds the genes its slice owns -- W1 rows 8q .. 8q+7, b1[8q .. 8q+7],
@@ -51,6 +52,7 @@ namespace leea {
 namespace {
 
 constexpr int kSmallThreads = 512;
+constexpr int kUnitThreads = kSmallThreads - 32;  // warps 0-14 breed; warp 15 selects (populations up to 32)
 constexpr int kSlice = 8;  // hidden units per CTA
 constexpr int kSmallMaxPop = 1024;
 constexpr int kSmallMaxBatch = 128;
@@ -79,7 +81,8 @@ int64_t small_region_floats(int32_t d_in, int32_t h, int32_t d_out, int32_t batc
 {
     (void)h;
     const int64_t r1 = static_cast<int64_t>(batch) * (d_in + 4) + static_cast<int64_t>(kSlice) * (d_in + 4) + kSlice +
-                       static_cast<int64_t>(kSlice) * d_out + static_cast<int64_t>(kSlice) * batch + kPartialFloats;
+                       static_cast<int64_t>(kSlice) * d_out + static_cast<int64_t>(kSlice) * batch + kPartialFloats +
+                       static_cast<int64_t>(batch) * d_in / 4;
     const int64_t r2 = static_cast<int64_t>(d_out) * batch + 2 * kSmallMaxBatch + 32;
     const int64_t r = r1 > r2 ? r1 : r2;
     return (r + 3) & ~int64_t(3);
@@ -99,33 +102,12 @@ __device__ __forceinline__ int simt_batch_tile(int batch)
     return 16 * (batch <= 32 ? 2 : batch <= 64 ? 4 : 8);
 }
 
-// Bitonic sort of one key per lane (n2 <= 32 keys, padding keys ~0 sort
-// last): afterwards lane r holds the r-th smallest key.
-__device__ __forceinline__ uint64_t warp_sort_keys(uint64_t key, int lane, int n2)
-{
-    for (int size = 2; size <= n2; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            const uint64_t other = __shfl_xor_sync(0xFFFFFFFFu, key, stride);
-            const bool ascending = (lane & size) == 0;
-            const bool lower = (lane & stride) == 0;
-            const uint64_t lo = key < other ? key : other, hi = key < other ? other : key;
-            key = (lower == ascending) ? lo : hi;
-        }
-    }
-    return key;
-}
-
 constexpr int kSmallJobs = 4 * 32;  // Box-Muller pairs of a warp's 32 units
-constexpr int kXWords = 8;  // words of the batch a thread holds in registers while it selects and breeds
 
-// A read-only load issued where it stands in the program (the memory clobber
-// keeps the compiler from sinking it to its first use), so that its latency
-// overlaps the work in between.
-__device__ __forceinline__ uint32_t ld_u32_now(const uint32_t* p)
+// 4-byte asynchronous copy global -> shared (completion per thread by cp.async groups).
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
 {
-    uint32_t v;
-    asm volatile("ld.global.nc.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(ptx::smem_u32(dst)), "l"(src) : "memory");
 }
 
 // Thread-block cluster of one child's slices (cluster rank q = slice q).
@@ -206,45 +188,109 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     float* w2s = b1s + kSlice;            // [D][kSlice]: the slice's columns of W2
     float* hs = w2s + D * kSlice;         // [Bt][kSlice]: the slice's activations
     float* qs = hs + Bt * kSlice;         // layer 1's partial tiles of the input groups
+    uint32_t* xraw = reinterpret_cast<uint32_t*>(qs + kPartialFloats);  // [Bt * K / 4]: the batch's levels as copied
 
     ptx::grid_dep_launch();
     if (CLUSTER) cluster_arrive_relaxed();  // every CTA of the cluster has started before any writes to slice 0
     ptx::grid_dep_wait();  // the previous generation's fitness and population
 
-    // The previous fitness, then the batch's 8-bit levels (four per word):
-    // a small batch is held in registers until layer 1 needs it, so that its
-    // loads overlap the selection and the breed.
+    // The batch's 8-bit levels are copied to shared memory four at a time
+    // (cp.async) by the unit threads while the work below proceeds.  For
+    // populations up to 32 the last warp ranks the previous population and
+    // selects child i meanwhile (step 1); larger ones are ranked by the whole
+    // CTA after the draws.
     const int P = a.pop, n2 = a.n_pow2;
-    float f_mine = 0.0f;
-    if (a.breed && tid < P) f_mine = __ldcg(a.f_adj_in + tid);
-    SelStream sel_st(a.sel.seed, a.sel.gen, static_cast<uint32_t>(i));
-    if (a.breed && tid == 0) sel_st.draw(0);  // child i's first SEL block, while the fitness loads are in flight
+    const bool sel_warp = a.breed && P <= 32;
     const uint32_t* x4 = reinterpret_cast<const uint32_t*>(a.x);
     const int n4 = Bt * K / 4;
-    const bool x_in_regs = n4 <= kXWords * kSmallThreads;
-    uint32_t xw[kXWords];
-#pragma unroll
-    for (int j = 0; j < kXWords; ++j) {
-        const int t = tid + j * kSmallThreads;
-        xw[j] = (x_in_regs && t < n4) ? ld_u32_now(x4 + t) : 0u;
+    if (tid < kUnitThreads) {
+        for (int t = tid; t < n4; t += kUnitThreads) cp_async4(xraw + t, x4 + t);
+        ptx::cp_async_commit();
     }
 
-    // 1. Ranking of the previous population and child i's selection.
-    if (a.breed) {
-        if (n2 <= 32) {  // one warp sorts the keys in registers
-            if (tid < 32) {
-                if (tid < P) fs[tid] = f_mine;
-                const uint64_t k = warp_sort_keys(tid < P ? rank_key(f_mine, tid) : ~0ull, tid, n2);
-                if (tid < P) {
-                    const int32_t idx = static_cast<int32_t>(k & 0xFFFFFFFFu);
-                    ord[tid] = idx;
-                    if (blockIdx.x == 0) a.order[tid] = idx;
-                }
-            }
-            __syncthreads();
-        } else {
+    // 1a. Ranking and selection by the last warp: the rank of individual l is
+    // the number of rank keys below its own (the keys are distinct).
+    if (sel_warp && tid >= kUnitThreads) {
+        const int l = tid - kUnitThreads;
+        SelStream sel_st(a.sel.seed, a.sel.gen, static_cast<uint32_t>(i));
+        if (l == 0) sel_st.draw(0);  // child i's first SEL block, while the fitness loads are in flight
+        const float f = l < P ? __ldcg(a.f_adj_in + l) : 0.0f;
+        const uint64_t mine = l < P ? rank_key(f, l) : ~0ull;
+        if (l < P) {
+            fs[l] = f;
+            keys[l] = mine;
+        }
+        __syncwarp();
+        int r = 0;
+        for (int m = 0; m < P; ++m) r += keys[m] < mine ? 1 : 0;
+        if (l < P) {
+            ord[r] = l;
+            if (blockIdx.x == 0) a.order[r] = l;
+        }
+        __syncwarp();
+        if (l == 0) {
+            const ChildSelection c = select_child_of(a.sel, fs, ord, i, sel_st);
+            sel_s = c;
+            if (q == 0) store_child_selection(a.sel, c, i, a.par1, a.par2, a.kind, a.f_inh);
+        }
+    }
+
+    // The slice's units (8 genes each) and, ahead of the selection, their
+    // random numbers: the crossover and mutation masks and the mutation
+    // normals depend on the child's index (its kind too), not on its parents.
+    const int n_units = K + 1 + D + (q == 0 ? a.b2_units : 0);
+    const int kind = i < a.sel.n_elite ? kKindElite : (i < a.sel.n_elite + a.sel.n_cross ? kKindCross : kKindMut);
+    const uint32_t gen = a.br.gen, ent = static_cast<uint32_t>(i);
+    const PhiloxKeys key = philox_keys(a.br.seed);
+    const int lane = tid & 31;
+    auto first_gene = [&](int t) -> int64_t {
+        if (t < K) return static_cast<int64_t>(q) * kSlice * K + 8 * t;  // W1 rows 8q .. 8q+7
+        if (t == K) return a.b1_off + kSlice * q;
+        if (t < K + 1 + D) return a.w2_off + static_cast<int64_t>(t - K - 1) * H + kSlice * q;
+        return a.b2_off + 8 * (t - K - 1 - D);
+    };
+    // The mask of unit t (mutation or crossover); for a mutation child also its
+    // normals, through the warp's job list (every lane of the warp calls it).
+    auto draw_unit = [&](int t, bool ok, uint32_t& msk, float2 (&z)[4]) {
+        const uint32_t u = ok ? static_cast<uint32_t>(first_gene(t) >> 3) : 0u;
+        if (kind == kKindMut) {
+            msk = ok ? mask8(philox_keyed(make_uint4(u, ent, gen, kTagMutMask), key), a.br.thr_mut) : 0u;
+            const int t0 = t - lane;
+            normals8(gen, key, ent, msk, z, lane, job_z + (tid >> 5) * kSmallJobs, job_code + (tid >> 5) * kSmallJobs,
+                     [&](uint32_t o) { return static_cast<uint32_t>(first_gene(t0 + static_cast<int>(o)) >> 3); });
+        } else if (kind == kKindCross && a.br.xo_op == 0) {
+            msk = ok ? mask8(philox_keyed(make_uint4(u, ent, gen, kTagXo), key), a.br.thr_xo) : 0u;
+        }
+    };
+    // Unit round r of a thread: units t = r * 2 * kUnitThreads + tid (A) and
+    // + kUnitThreads (B); the first round's numbers are drawn here.
+    const bool drawn = a.breed && n_units <= 2 * kUnitThreads;
+    uint32_t mskA = 0u, mskB = 0u;
+    float2 zA[4], zB[4];
+    if (tid < kUnitThreads) {
+        if (drawn && kind != kKindElite) {
+            if ((tid & ~31) < n_units) draw_unit(tid, tid < n_units, mskA, zA);
+            if (kUnitThreads + (tid & ~31) < n_units)
+                draw_unit(kUnitThreads + tid, kUnitThreads + tid < n_units, mskB, zB);
+        }
+    }
+    // The batch's levels as FP32 in the padded layout (word t holds inputs
+    // 4t .. 4t+3 of the row-major batch); a unit thread converts the words it
+    // copied, while the first units' parent loads are in flight (step 2).
+    auto convert_batch = [&]() {
+        ptx::cp_async_wait_group<0>();
+        const int kw = K / 4;
+        for (int t = tid; t < n4; t += kUnitThreads) {
+            const int n = t / kw;
+            *reinterpret_cast<float4*>(xs + n * (K + 4) + 4 * (t - n * kw)) = levels_to_float4(xraw[t]);
+        }
+    };
+
+    // 1b. Larger populations: the whole CTA ranks (a bitonic sort of the keys
+    // in shared memory, padding keys last), then thread 0 selects.
+    if (a.breed && !sel_warp) {
         for (int t = tid; t < n2; t += kSmallThreads) {
-            const float f = t < P ? (t < kSmallThreads ? f_mine : __ldcg(a.f_adj_in + t)) : 0.0f;
+            const float f = t < P ? __ldcg(a.f_adj_in + t) : 0.0f;
             if (t < P) fs[t] = f;
             keys[t] = t < P ? rank_key(f, t) : ~0ull;
         }
@@ -270,9 +316,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
             if (blockIdx.x == 0) a.order[r] = idx;
         }
         __syncthreads();
-        }
         if (tid == 0) {
-            const ChildSelection c = select_child_of(a.sel, fs, ord, i, sel_st);
+            const ChildSelection c = select_child_of(a.sel, fs, ord, i);
             sel_s = c;
             if (q == 0) store_child_selection(a.sel, c, i, a.par1, a.par2, a.kind, a.f_inh);
         }
@@ -282,19 +327,10 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     // 2. The slice's genes: bred (children) or read (the first evaluation),
     // two units per thread at a time so that their loads are in flight together.
     {
-        const int n_units = K + 1 + D + (q == 0 ? a.b2_units : 0);
         const ChildSelection c = sel_s;
-        const uint32_t gen = a.br.gen, ent = static_cast<uint32_t>(i);
-        const PhiloxKeys key = philox_keys(a.br.seed);
         float* child = a.popv + static_cast<int64_t>(i) * a.c_pad;
         const float* par1 = a.parents + static_cast<int64_t>(c.p1) * a.c_pad;
         const float* par2 = a.parents + static_cast<int64_t>(c.p2) * a.c_pad;
-        auto first_gene = [&](int t) -> int64_t {
-            if (t < K) return static_cast<int64_t>(q) * kSlice * K + 8 * t;  // W1 rows 8q .. 8q+7
-            if (t == K) return a.b1_off + kSlice * q;
-            if (t < K + 1 + D) return a.w2_off + static_cast<int64_t>(t - K - 1) * H + kSlice * q;
-            return a.b2_off + 8 * (t - K - 1 - D);
-        };
         // Parent genes of a unit (a.breed), or the individual's own (the first evaluation).
         auto load = [&](int64_t g0, float4 (&v)[2], float4 (&w)[2]) {
             const float4* src = reinterpret_cast<const float4*>((a.breed ? par1 : child) + g0);
@@ -306,21 +342,16 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
                 w[1] = __ldcg(src2 + 1);
             }
         };
-        // Called by every lane of a warp that holds a unit (ok: this lane's
-        // unit exists): the mutation normals go through the warp's job list.
-        auto finish = [&](int t, bool ok, int64_t g0, float4 (&v)[2], const float4 (&w)[2]) {
+        // The unit's genes from its parents' and its drawn numbers; then stored
+        // (children) and kept in shared memory.  ok: this lane's unit exists.
+        auto finish = [&](int t, bool ok, int64_t g0, float4 (&v)[2], const float4 (&w)[2], uint32_t msk,
+                          const float2 (&z)[4]) {
+            if (!ok) return;
             if (a.breed) {
-                const uint32_t u = static_cast<uint32_t>(g0 >> 3);
-                if (c.kind == kKindMut) {  // the same for the whole CTA
-                    const int lane = tid & 31, t0 = t - lane;
-                    const uint32_t hit =
-                        ok ? mask8(philox_keyed(make_uint4(u, ent, gen, kTagMutMask), key), a.br.thr_mut) : 0u;
-                    mutate8(c.sigma, gen, key, ent, hit, v, lane, job_z + (tid >> 5) * kSmallJobs,
-                            job_code + (tid >> 5) * kSmallJobs,
-                            [&](uint32_t o) { return static_cast<uint32_t>(first_gene(t0 + static_cast<int>(o)) >> 3); });
-                } else if (ok && c.kind == kKindCross) {
+                if (c.kind == kKindMut) {
+                    apply_mutation8(c.sigma, msk, z, v);
+                } else if (c.kind == kKindCross) {
                     if (a.br.xo_op == 0) {
-                        const uint32_t msk = mask8(philox_keyed(make_uint4(u, ent, gen, kTagXo), key), a.br.thr_xo);
                         v[0] = select4(msk, v[0], w[0]);
                         v[1] = select4(msk >> 4, v[1], w[1]);
                     } else {
@@ -332,11 +363,8 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
                     v[0] = clear_padding(v[0], g0, a.c);
                     v[1] = clear_padding(v[1], g0 + 4, a.c);
                 }
-                if (!ok) return;
                 reinterpret_cast<float4*>(child + g0)[0] = v[0];
                 reinterpret_cast<float4*>(child + g0)[1] = v[1];
-            } else if (!ok) {
-                return;
             }
             if (t < K) {  // genes 8t .. 8t+7 of the slice's rows: row l / K, input l % K
                 // (K % 4 == 0: each half of the unit is 4 genes of one row, 16-byte aligned)
@@ -350,47 +378,21 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
                 reinterpret_cast<float4*>(dst)[1] = v[1];
             }
         };
-        // The batch's levels as FP32, while the first units' parent loads are
-        // in flight (word t holds inputs 4t .. 4t+3 of the row-major batch).
-        auto convert_batch = [&]() {
-            const int kw = K / 4;
-            auto dst = [&](int t) {
-                const int n = t / kw;
-                return reinterpret_cast<float4*>(xs + n * (K + 4) + 4 * (t - n * kw));
-            };
-            if (x_in_regs) {
-#pragma unroll
-                for (int j = 0; j < kXWords; ++j) {
-                    const int t = tid + j * kSmallThreads;
-                    if (t < n4) *dst(t) = levels_to_float4(xw[j]);
-                }
-            } else {
-                for (int t0 = tid; t0 < n4; t0 += 4 * kSmallThreads) {
-                    uint32_t w4[4];
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int t = t0 + j * kSmallThreads;
-                        w4[j] = t < n4 ? __ldg(x4 + t) : 0u;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const int t = t0 + j * kSmallThreads;
-                        if (t < n4) *dst(t) = levels_to_float4(w4[j]);
-                    }
-                }
-            }
-        };
-        for (int base = 0; base < n_units; base += 2 * kSmallThreads) {
-            const int tA = base + tid, tB = tA + kSmallThreads;
+        for (int base = 0; tid < kUnitThreads && base < n_units; base += 2 * kUnitThreads) {
+            const int tA = base + tid, tB = tA + kUnitThreads;
             const bool okA = tA < n_units, okB = tB < n_units;
             const int64_t gA = okA ? first_gene(tA) : 0, gB = okB ? first_gene(tB) : 0;
             float4 vA[2], wA[2], vB[2], wB[2];
             if (okA) load(gA, vA, wA);
             if (okB) load(gB, vB, wB);
             if (base == 0) convert_batch();
-            const int wbase = base + (tid & ~31);  // the warp's first unit of this round
-            if (wbase < n_units) finish(tA, okA, gA, vA, wA);
-            if (wbase + kSmallThreads < n_units) finish(tB, okB, gB, vB, wB);
+            if (a.breed && !(drawn && base == 0) && kind != kKindElite) {  // later rounds draw here
+                const int wbase = base + (tid & ~31);
+                if (wbase < n_units) draw_unit(tA, okA, mskA, zA);
+                if (wbase + kUnitThreads < n_units) draw_unit(tB, okB, mskB, zB);
+            }
+            finish(tA, okA, gA, vA, wA, mskA, zA);
+            finish(tB, okB, gB, vB, wB, mskB, zB);
         }
     }
     __syncthreads();
