@@ -100,15 +100,39 @@ __device__ __forceinline__ void apply_mutation8(float sigma, uint32_t hit, const
     if (hit & 0x80u) v[1].w = fmaf(sigma, z[3].y, v[1].w);
 }
 
-// Mutation of one lane's unit (8 genes in v) whose mask bits are `hit`: its
-// normals through the warp's job list (normals8), then the step.
+// Mutation of one lane's unit (8 genes in v) whose mask bits are `hit`: the
+// normals of normals8 (the same job list, the same draws), the step applied
+// before the warp lets the list go.
 template <typename UnitOf>
 __device__ __forceinline__ void mutate8(float sigma, uint32_t gen, const PhiloxKeys& key, uint32_t ent, uint32_t hit,
                                         float4 (&v)[2], int lane, float2* job_z, uint8_t* job_code, UnitOf unit_of)
 {
-    float2 z[4];
-    normals8(gen, key, ent, hit, z, lane, job_z, job_code, unit_of);
+    constexpr int kSlots = 4;
+    const uint32_t lt = (1u << lane) - 1u;
+    uint32_t idx[kSlots], total = 0;
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+        const bool need = ((hit >> (2 * sl)) & 3u) != 0u;
+        const uint32_t b = __ballot_sync(0xFFFFFFFFu, need);
+        idx[sl] = total + __popc(b & lt);
+        if (need) job_code[idx[sl]] = static_cast<uint8_t>((lane << 2) | sl);
+        total += __popc(b);
+    }
+    __syncwarp();
+    for (uint32_t job = static_cast<uint32_t>(lane); job < total; job += 32) {
+        const uint32_t code = job_code[job];
+        const uint32_t o = code >> 2, slot = code & 3u;
+        const uint32_t uo = unit_of(o);
+        const uint4 n = philox_keyed(make_uint4(2u * uo + (slot >> 1), ent, gen, kTagNormal), key);
+        job_z[job] = (slot & 1u) ? box_muller(n.z, n.w) : box_muller(n.x, n.y);
+    }
+    __syncwarp();
+    float2 z[kSlots];
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl)
+        z[sl] = ((hit >> (2 * sl)) & 3u) ? job_z[idx[sl]] : make_float2(0.f, 0.f);
     apply_mutation8(sigma, hit, z, v);
+    __syncwarp();  // the list is reused by the next unit
 }
 
 // The same mutation of one unit by a single thread (no job list): each masked
