@@ -109,7 +109,7 @@ STAGES = ("select", "breed", "evaluate")
 # DRAM traffic per launch from one ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum), valid only while the kernel source is unchanged.
 TRAFFIC = {
-    "breed": {"bytes_per_launch": 472.52e6, "src_sha": "641fc663c50d3438", "capture": "P=1000 plain workload"},
+    "breed": {"bytes_per_launch": 472.53e6, "src_sha": "3ba6876d0f989830", "capture": "P=1000 plain workload"},
     "evaluate": {"bytes_per_launch": 368.68e6, "src_sha": "921b0e7934e40403", "capture": "P=1000 plain workload"},
     "breed_evaluate": {"bytes_per_launch": 738.19e6, "src_sha": "23e25d83744d9797", "capture": "P=1000 plain workload"},
     # eval_mlp_tc_kernel alone (each individual's weight pieces read once from
