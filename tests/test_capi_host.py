@@ -109,6 +109,18 @@ def test_argument_errors_are_reported_before_any_work(lib):
     bf16 = leea.Params(precision=1).c_struct()
     rc = lib.leea_create(10, d4.ctypes.data_as(ctypes.c_void_p), 5, ctypes.byref(bf16), 1, None, ctypes.byref(h))
     assert rc == leea.EINVAL
+    # The evaluation paths: SMALL (the single-launch generation) is the last one; it takes FP32
+    # populations of nets with one hidden layer.
+    assert leea.leea_counts(10, leea.Params(eval_path=leea.EVAL_SMALL))[0] >= 0
+    with pytest.raises(leea.LeeaError) as e:
+        leea.leea_counts(10, leea.Params(eval_path=leea.EVAL_SMALL + 1))
+    assert "eval_path" in str(e.value)
+    with pytest.raises(leea.LeeaError) as e:
+        leea.leea_counts(10, leea.Params(eval_path=leea.EVAL_SMALL, precision=1))
+    assert "single-launch" in str(e.value)
+    small_deep = leea.Params(eval_path=leea.EVAL_SMALL).c_struct()
+    rc = lib.leea_create(10, d4.ctypes.data_as(ctypes.c_void_p), 5, ctypes.byref(small_deep), 1, None, ctypes.byref(h))
+    assert rc == leea.EINVAL and h.value is None
 
 
 def test_oracle_and_library_share_no_code():
