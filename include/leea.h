@@ -136,8 +136,10 @@ enum { LEEA_SIGMA_CONST = 0, LEEA_SIGMA_DECAY = 1, LEEA_SIGMA_SELF = 2 };
  * SMALL (state object, 8-bit generation calls, precision 0): the whole
  * generation -- ranking, selection, breeding, evaluation (Algorithm 1) -- in
  * one launch of one CTA per (child, 8 hidden units), each CTA ranking the
- * previous population itself and evaluating the slice it bred; the children
- * are bit-identical to leea_breed's and the fitness to the SIMT kernel's.  It
+ * previous population itself and evaluating the slice it bred (layer 1 on
+ * tensor-core tiles, levels exact, weights to 22 bits as in the TENSOR path);
+ * the children are bit-identical to leea_breed's, the fitness within the
+ * evaluation tolerance of the SIMT kernel's.  It
  * needs one hidden layer, h % 8 == 0, h <= 256, d_0 % 4 == 0, d_0 <= 2048,
  * d_out <= 32, batch <= 128, pop <= 1024, a 4-byte aligned batch and the
  * batch in shared memory (LEEA_EINVAL otherwise).  AUTO takes it for such

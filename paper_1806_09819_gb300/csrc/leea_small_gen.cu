@@ -5,38 +5,44 @@
 // dependency latency rather than in moving bytes (P = 32 nets of 784-32-10 on
 // 16 samples are 3 MB).
 //
-// Grid: one CTA per (child i, slice q of kSlice = 8 hidden units), no waiting
-// between CTAs.  Each CTA
-//   1. ranks the whole previous population itself (up to 32 individuals one
-//      warp counts, for each, the rank keys below its own while the other
-//      warps draw; beyond, a bitonic sort in shared memory) and selects child
-//      i with the
-//      selection kernels' code (select_ops.cuh), so that no CTA depends on
-//      another's selection;
-//   2. breeds the genes its slice owns -- W1 rows 8q .. 8q+7, b1[8q .. 8q+7],
-//      the column block 8q .. 8q+7 of every W2 row and (slice 0) b2 -- with
-//      the breeding kernel's per-unit code (breed_ops.cuh), writes them to
-//      the new population and keeps the slice's W1 rows and b1 in shared
-//      memory (8-gene units never straddle slices: 8 rows of d_0 genes are
-//      d_0 units, and h % 8 == 0 aligns b1, W2 and b2);
+// Grid: one CTA per (child i, slice q of kSlice = 8 hidden units); a child's
+// slices form a thread-block cluster (up to 8 of them), no other CTA waits for
+// another.  Each CTA
+//   0. draws the random numbers of the genes its slice owns -- the crossover
+//      or mutation masks and the mutation normals (through the warps' job
+//      lists) -- which depend on the child's index and kind, not on its
+//      parents, while the batch is copied to shared memory;
+//   1. meanwhile ranks the whole previous population itself and selects child
+//      i with the selection kernels' code (select_ops.cuh): up to 32
+//      individuals the last warp counts, for each, the rank keys below its
+//      own; beyond, the whole CTA sorts the keys in shared memory after the
+//      draws;
+//   2. breeds the slice's genes -- W1 rows 8q .. 8q+7, b1[8q .. 8q+7], the
+//      column block 8q .. 8q+7 of every W2 row and (slice 0) b2 -- from the
+//      parents' genes and the drawn numbers with the breeding kernel's
+//      per-unit operators (breed_ops.cuh), writes them to the new population
+//      and keeps the slice in shared memory (8-gene units never straddle
+//      slices: 8 rows of d_0 genes are d_0 units, and h % 8 == 0 aligns b1,
+//      W2 and b2);
 //   3. forms the slice's layer 1 for the whole batch (m16n8k8 tensor-core
-//      tiles, the warps splitting the inputs), and from it the slice's share of
-//      layer 2 (the partial logits of its 8 hidden units), written to a
-//      scratch buffer;
-//   4. counts itself in with an atomic add after a memory fence; the last of
-//      child i's CTAs to arrive (the others simply exit) adds the slices'
-//      partial logits and b2, and forms the softmax cross-entropy (Eq. 1),
-//      the batch sum and the inheritance blend, then zeroes the counter for
-//      the next launch.
+//      tiles, the warps splitting the inputs) and from it the slice's share
+//      of layer 2, the partial logits of its 8 hidden units;
+//   4. hands them to slice 0: in a cluster by writing them into slice 0's
+//      shared memory before a cluster barrier, otherwise through L2 with an
+//      arrival counter (the last slice to count itself in finishes and zeroes
+//      the counter for the next launch).  The finishing CTA adds the partial
+//      logits and b2 and forms the softmax cross-entropy (Eq. 1), the batch
+//      sum and the inheritance blend.
 // Arithmetic order (fixed, so identical individuals get identical bits):
-// layer 1 accumulates the exact products k w_hi and k w_lo (k the 8-bit level,
-// w_hi + w_lo the weight to 22 bits) in FP32 on the tensor cores over each
-// warp's input group, adds the groups in order and divides by x_div; layer 2 is one FMA chain per slice over its hidden units in
-// ascending order, the slices added in order, then b2; the loss (softmax
-// cross-entropy with the maximum subtracted, exponentials added in class
-// order) and the batch reduction are eval_simt_kernel's.  The fitness is
-// thus within the evaluation tolerance of the CUDA-core evaluation's (as the
-// 8-bit tensor-core evaluation is), and the children are bit-identical to
+// layer 1 accumulates the exact products k w_hi and k w_lo (k the 8-bit
+// level, w_hi + w_lo the weight to 22 bits) in FP32 on the tensor cores over
+// each warp's input group, adds the groups in order and divides by x_div;
+// layer 2 is one FMA chain per slice over its hidden units in ascending
+// order, the slices added in order, then b2; the loss (softmax cross-entropy
+// with the maximum subtracted, exponentials added in class order) and the
+// batch reduction are eval_simt_kernel's.  The fitness is thus within the
+// evaluation tolerance of the CUDA-core evaluation's (as the 8-bit
+// tensor-core evaluation is), and the children are bit-identical to
 // breed_kernel's.  A single CTA's layer 1 is 16 samples x 8 units x d_0
 // inputs: mma.sync tiles in registers serve it without the setup of the
 // tcgen05 path (tensor memory, descriptors, barriers) that the large
