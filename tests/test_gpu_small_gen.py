@@ -189,3 +189,37 @@ def test_small_generation_limits(gpu):
             st.leea_generation(xf, y)
     finally:
         st.close()
+
+
+def test_auto_switches_between_the_paths_with_the_batch(gpu, oracle_mod):
+    # Batches inside the single-launch limits take it, a batch past them the
+    # chain of kernels; the object's fitness buffers stay consistent across the
+    # switches (children bit-identical to the two-kernel CUDA-core path's,
+    # fitness within tolerance, the oracle's near-ties allowed).
+    from paper_1806_09819_gb300 import leea
+    dims, pop = [784, 32, 10], 32
+    prm = dict(sigma=0.01, mut_rate=0.1, n_elite=1)
+    ref = gpu.LeeaState(pop, dims, gpu.Params(**prm, eval_path=leea.EVAL_SIMT), seed=77)
+    auto = gpu.LeeaState(pop, dims, gpu.Params(**prm), seed=77)
+    try:
+        for g, b in enumerate([16, 200, 16, 16, 150, 8]):
+            xd, yd = _batch(dims, b, seed=500 + g)
+            auto.leea_profile_enable(True)
+            for st in (ref, auto):
+                st.leea_generation_u8(xd, yd, 255.0)
+            prof = auto.leea_profile_read()
+            single = b <= 128
+            if g > 0:
+                assert (prof[leea.STAGES[0]][1] == 0) == single, (b, prof)
+            kids = ref.leea_get_population()
+            np.testing.assert_array_equal(_bits(auto.leea_get_population()), _bits(kids), err_msg=f"batch {b}")
+            f_ref, cor_ref = ref.leea_fitness(with_correct=True)
+            f_auto, cor_auto = auto.leea_fitness(with_correct=True)
+            assert_fitness_close(f_auto, f_ref, f"batch {b}: f_adj")
+            x64 = xd.cpu().numpy().astype(np.float64) / 255.0
+            _, _, logits = oracle_mod.evaluate(kids.astype(np.float64), dims, x64, yd.cpu().numpy(), want_logits=True)
+            assert_correct_close(cor_auto, cor_ref, logits)
+            auto.leea_set_fitness(f_ref)
+    finally:
+        ref.close()
+        auto.close()
