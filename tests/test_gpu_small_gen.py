@@ -62,6 +62,8 @@ SMALL_CASES = [
          prm=dict(sigma=0.01, sigma_ctl=2, tau=0.1, p_c=0.75, n_elite=-1, p_e=0.05)),
     # the largest cluster: 8 slices per child (h = 64), tournament selection, 40 individuals (bitonic ranking)
     dict(dims=[256, 64, 10], pop=40, batches=[30, 12], prm=dict(sel_op=1, tour_k=2, sigma=0.03, p_c=0.6)),
+    # a large population: 1024 rank keys sorted in shared memory, 600 clusters of one slice
+    dict(dims=[16, 8, 4], pop=600, batches=[4, 9, 4], prm=dict(sigma=0.05, p_c=0.3, n_elite=-1, p_e=0.1)),
     # more than 8 slices per child (h = 72 and 128): the hand-over through L2 and an arrival counter
     dict(dims=[64, 72, 10], pop=5, batches=[8, 8, 20], prm=dict(sigma=0.05, n_elite=1)),
     dict(dims=[784, 128, 10], pop=3, batches=[16, 16], prm=dict(sigma=0.01, mut_rate=0.3)),
