@@ -133,7 +133,7 @@ enum { LEEA_SIGMA_CONST = 0, LEEA_SIGMA_DECAY = 1, LEEA_SIGMA_SELF = 2 };
  * leea_breed's.  It needs d_0 % 16 == 0, h % 16 == 0, h <= 128, d_out <= 16,
  * batch <= 128 (LEEA_EINVAL otherwise); the first evaluation uses the
  * tensor-core kernel.  AUTO keeps breeding and evaluation as two kernels.
- * SMALL (state object, 8-bit generation calls, precision 0): the whole
+ * SMALL (state object, 8-bit or FP32 generation calls, precision 0): the whole
  * generation -- ranking, selection, breeding, evaluation (Algorithm 1) -- in
  * one launch of one CTA per (child, 8 hidden units), each CTA ranking the
  * previous population itself and evaluating the slice it bred (layer 1 on
@@ -141,8 +141,9 @@ enum { LEEA_SIGMA_CONST = 0, LEEA_SIGMA_DECAY = 1, LEEA_SIGMA_SELF = 2 };
  * the children are bit-identical to leea_breed's, the fitness within the
  * evaluation tolerance of the SIMT kernel's.  It
  * needs one hidden layer, h % 8 == 0, h <= 256, d_0 % 4 == 0, d_0 <= 2048,
- * d_out <= 32, batch <= 128, pop <= 1024, a 4-byte aligned batch and the
- * batch in shared memory (LEEA_EINVAL otherwise).  AUTO takes it for such
+ * d_out <= 32, batch <= 128, pop <= 1024, a 4-byte aligned 8-bit or 16-byte
+ * aligned FP32 batch and the batch in shared memory (LEEA_EINVAL otherwise);
+ * FP32 inputs enter layer 1 as two TF32 pieces as well.  AUTO takes it for such
  * generations when pop * h / 8 is at most twice the number of SMs, where the
  * chain of kernels would be bound by launch and dependency latency. */
 enum { LEEA_EVAL_AUTO = 0, LEEA_EVAL_SIMT = 1, LEEA_EVAL_TENSOR = 2, LEEA_EVAL_FUSED = 3, LEEA_EVAL_SMALL = 4 };

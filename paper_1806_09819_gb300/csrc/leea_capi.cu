@@ -982,8 +982,8 @@ leea_status leea_create(int32_t pop, const int32_t* dims, int32_t n_dims, const 
 // the first call evaluates the initial population, later calls rank, select,
 // breed and evaluate.  The kernel reads the previous fitness from one buffer
 // and writes the new one to the other; the buffers then swap.
-static leea_status run_small_generation(leea_state* s, const uint8_t* x_dev, float x_div, const int32_t* y_dev,
-                                        int32_t batch)
+static leea_status run_small_generation(leea_state* s, const uint8_t* x_dev, const float* xf_dev, float x_div,
+                                        const int32_t* y_dev, int32_t batch)
 {
     const size_t np = static_cast<size_t>(s->pop);
     if (!s->count) {
@@ -1025,6 +1025,7 @@ static leea_status run_small_generation(leea_state* s, const uint8_t* x_dev, flo
     ga.part = s->part;
     ga.count = s->count;
     ga.x = x_dev;
+    ga.xf = xf_dev;
     ga.y = y_dev;
     if (first) {
         ga.breed = 0;
@@ -1134,12 +1135,13 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         return fail(LEEA_EINVAL, "the fused breed + evaluate path takes 8-bit inputs (leea_generation_u8*)");
     // Small populations: the whole generation in one launch (SMALL, or AUTO
     // when its CTAs, one per child and 8 hidden units, fit twice on the GPU).
-    const bool small_ok = u8 && prec == 0 && small_gen_supported(s->net, s->pop, batch) &&
-                          (reinterpret_cast<uintptr_t>(x_dev) & 3u) == 0;
+    const bool small_ok = prec == 0 && small_gen_supported(s->net, s->pop, batch) &&
+                          (reinterpret_cast<uintptr_t>(x_dev) & (u8 ? 3u : 15u)) == 0;
     bool small = false;
     if (s->prm.eval_path == LEEA_EVAL_SMALL) {
         if (!small_ok)
-            return fail(LEEA_EINVAL, "the single-launch generation needs 8-bit inputs (4-byte aligned), one hidden "
+            return fail(LEEA_EINVAL, "the single-launch generation needs a 4-byte aligned 8-bit or 16-byte aligned "
+                                     "FP32 batch, one hidden "
                                      "layer with h %% 8 == 0 and h <= 256, d_0 %% 4 == 0 and d_0 <= 2048, "
                                      "d_out <= 32, batch <= 128, pop <= 1024 and the batch in 200 KB of shared memory");
         small = true;
@@ -1149,7 +1151,9 @@ static leea_status run_generation(leea_state* s, const void* x_dev, bool u8, flo
         LEEA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
         small = small_gen_ctas(s->net, s->pop) <= 2 * sms;
     }
-    if (small) return run_small_generation(s, static_cast<const uint8_t*>(x_dev), x_div, y_dev, batch);
+    if (small)
+        return run_small_generation(s, u8 ? static_cast<const uint8_t*>(x_dev) : nullptr,
+                                    u8 ? nullptr : static_cast<const float*>(x_dev), u8 ? x_div : 1.0f, y_dev, batch);
     // The tensor-core evaluation of 8-bit inputs reads the batch as FP16: a
     // breeding generation stages it beside the selection.
     const bool stage_early = !first && !fused && u8 && prec == 0 && s->x16 && s->prm.eval_path != LEEA_EVAL_SIMT &&

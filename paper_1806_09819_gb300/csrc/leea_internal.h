@@ -332,8 +332,8 @@ cudaError_t launch_breed_eval_u8(const BreedArgs& b, const NetLayout& net, const
                                  float x_div, const int32_t* y, int32_t batch, float alpha, const float* f_inh,
                                  float* f_raw, float* f_adj, int32_t* correct, unsigned int* status,
                                  cudaStream_t stream);
-// One generation (ranking, selection, breeding, evaluation of 8-bit inputs)
-// in a single launch for small FP32 populations of d_0-h-d_out nets: one CTA
+// One generation (ranking, selection, breeding, evaluation of 8-bit or FP32
+// inputs) in a single launch for small FP32 populations of d_0-h-d_out nets: one CTA
 // per (child, 8 hidden units).  Children bit-identical to breed_kernel's,
 // fitness within FP32 rounding of eval_simt_kernel's.  f_adj_in and f_adj
 // must not alias (every CTA ranks the whole previous population); count
@@ -357,7 +357,8 @@ struct SmallGenArgs {
     int32_t* correct;        // nullable
     float* part;             // [pop][h / 8][batch][d_out] partial logits of the slices
     uint32_t* count;         // [pop] arrivals per child
-    const uint8_t* x;        // [batch][d_0] levels, 4-byte aligned
+    const uint8_t* x;        // [batch][d_0] levels, 4-byte aligned (when xf is NULL)
+    const float* xf;         // [batch][d_0] FP32 inputs, 16-byte aligned, or NULL
     const int32_t* y;
 };
 bool small_gen_supported(const NetLayout& net, int32_t pop, int32_t batch);

@@ -207,10 +207,18 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     // CTA after the draws.
     const int P = a.pop, n2 = a.n_pow2;
     const bool sel_warp = a.breed && P <= 32;
-    const uint32_t* x4 = reinterpret_cast<const uint32_t*>(a.x);
-    const int n4 = Bt * K / 4;
+    const int n4 = Bt * K / 4;  // 4-input groups of the batch
     if (tid < kUnitThreads) {
-        for (int t = tid; t < n4; t += kUnitThreads) cp_async4(xraw + t, x4 + t);
+        if (a.xf) {  // FP32 inputs: 16-byte copies straight into the padded rows
+            const int kw = K / 4;
+            for (int t = tid; t < n4; t += kUnitThreads) {
+                const int n = t / kw;
+                ptx::cp_async16(xs + n * (K + 4) + 4 * (t - n * kw), a.xf + 4 * static_cast<int64_t>(t));
+            }
+        } else {
+            const uint32_t* x4 = reinterpret_cast<const uint32_t*>(a.x);
+            for (int t = tid; t < n4; t += kUnitThreads) cp_async4(xraw + t, x4 + t);
+        }
         ptx::cp_async_commit();
     }
 
@@ -285,6 +293,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     // copied, while the first units' parent loads are in flight (step 2).
     auto convert_batch = [&]() {
         ptx::cp_async_wait_group<0>();
+        if (a.xf) return;  // FP32 inputs arrive in place
         const int kw = K / 4;
         for (int t = tid; t < n4; t += kUnitThreads) {
             const int n = t / kw;
@@ -406,7 +415,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
     // 3. Layer 1 of the slice (hidden unit jj, sample n) on the tensor cores:
     // the levels k are exact TF32 operands and each weight enters as two TF32
     // pieces (w_hi = tf32(w), w_lo = tf32(w - w_hi): 22 of FP32's 24 bits), so
-    // every product is exact and only the FP32 accumulation rounds.  Warp w
+    // every product is exact and only the FP32 accumulation rounds; FP32
+    // inputs are split the same way and enter as x_hi w_hi + x_hi w_lo +
+    // x_lo w_hi (x_div = 1).  Warp w
     // takes sample tile w / groups and every groups-th 8-input step from
     // w % groups on; the groups' partial tiles are added in order, divided by
     // x_div; then bias and ReLU.
@@ -415,6 +426,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
         const int groups = kWarps / n_tiles > 1 ? kWarps / n_tiles : 1;
         const int n_steps = (K + 7) / 8;
         const int warp = tid >> 5, lane = tid & 31, g = lane >> 2, tq = lane & 3;
+        const bool float_x = a.xf != nullptr;
         if (warp < groups * n_tiles) {
             const int tile = warp / groups, kg = warp - tile * groups;
             const float* x_lo = xs + min(16 * tile + g, Bt - 1) * (K + 4);      // sample rows g and g + 8
@@ -424,13 +436,27 @@ __global__ void __launch_bounds__(kSmallThreads, 1) small_gen_kernel(const __gri
             for (int st = kg; st < n_steps; st += groups) {
                 const int k0 = 8 * st + tq, k1 = k0 + 4;
                 const bool in0 = k0 < K, in1 = k1 < K;
-                const uint32_t a[4] = { __float_as_uint(in0 ? x_lo[k0] : 0.0f), __float_as_uint(in0 ? x_hi[k0] : 0.0f),
-                                        __float_as_uint(in1 ? x_lo[k1] : 0.0f), __float_as_uint(in1 ? x_hi[k1] : 0.0f) };
+                const float xv[4] = { in0 ? x_lo[k0] : 0.0f, in0 ? x_hi[k0] : 0.0f, in1 ? x_lo[k1] : 0.0f,
+                                      in1 ? x_hi[k1] : 0.0f };
                 const float w0 = in0 ? wrow[k0] : 0.0f, w1 = in1 ? wrow[k1] : 0.0f;
                 const uint32_t h0 = to_tf32(w0), h1 = to_tf32(w1);
                 const uint32_t l0 = to_tf32(w0 - __uint_as_float(h0)), l1 = to_tf32(w1 - __uint_as_float(h1));
-                mma_tf32(d, a, h0, h1);
-                mma_tf32(d, a, l0, l1);
+                if (!float_x) {  // the levels are exact TF32 operands
+                    const uint32_t av[4] = { __float_as_uint(xv[0]), __float_as_uint(xv[1]), __float_as_uint(xv[2]),
+                                             __float_as_uint(xv[3]) };
+                    mma_tf32(d, av, h0, h1);
+                    mma_tf32(d, av, l0, l1);
+                } else {  // x_hi w_hi + x_hi w_lo + x_lo w_hi
+                    uint32_t ah[4], al[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        ah[e] = to_tf32(xv[e]);
+                        al[e] = to_tf32(xv[e] - __uint_as_float(ah[e]));
+                    }
+                    mma_tf32(d, ah, h0, h1);
+                    mma_tf32(d, ah, l0, l1);
+                    mma_tf32(d, al, h0, h1);
+                }
             }
             float* part = qs + (kg * T16 + 16 * tile) * kSlice;  // [16 samples][8 hidden units]
             part[g * kSlice + 2 * tq] = d[0];

@@ -200,16 +200,24 @@ def test_u8_host_entry_point_matches_device_entry_point(gpu):
 
 
 def test_profiling_counts_launches(gpu):
+    # The chain of kernels (here with the tensor-core evaluation): a selection,
+    # a breed and an evaluation stage per generation after the first, which
+    # evaluates only.  AUTO at this size: one launch per generation, counted
+    # as the breed stage (the first, evaluating, launch as the evaluation).
     dims, pop, batch = [784, 32, 10], 32, 16
-    st = gpu.LeeaState(pop, dims, gpu.Params(), 2)
-    st.leea_profile_enable(True)
     x, y = _dev_batch(*synthetic.make_split(batch, seed=3))
-    for _ in range(5):
-        st.leea_generation(x, y)
-    prof = st.leea_profile_read()
-    assert prof["evaluate"][1] == 5 and prof["breed"][1] == 4 and prof["select"][1] == 4
-    assert all(ms >= 0 for ms, _ in prof.values())
-    assert st.leea_profile_read()["evaluate"] == (0.0, 0)
+    for path, expect in ((gpu.EVAL_TENSOR, (4, 4, 5)), (gpu.EVAL_AUTO, (0, 4, 1))):
+        st = gpu.LeeaState(pop, dims, gpu.Params(eval_path=path), 2)
+        try:
+            st.leea_profile_enable(True)
+            for _ in range(5):
+                st.leea_generation(x, y)
+            prof = st.leea_profile_read()
+            assert (prof["select"][1], prof["breed"][1], prof["evaluate"][1]) == expect, (path, prof)
+            assert all(ms >= 0 for ms, _ in prof.values())
+            assert st.leea_profile_read()["evaluate"] == (0.0, 0)
+        finally:
+            st.close()
 
 
 def test_state_errors(gpu):

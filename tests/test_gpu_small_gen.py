@@ -186,11 +186,12 @@ def test_small_generation_limits(gpu):
         finally:
             st.close()
     st = gpu.LeeaState(8, [784, 32, 10], gpu.Params(eval_path=leea.EVAL_SMALL), 1)
-    try:  # 8-bit inputs only
-        xf = torch.zeros((8, 784), dtype=torch.float32, device="cuda")
+    try:  # FP32 batches 16-byte aligned (this one is 4 bytes off)
+        xf = torch.zeros(8 * 784 + 1, dtype=torch.float32, device="cuda")[1:].view(8, 784)
         y = torch.zeros(8, dtype=torch.int32, device="cuda")
-        with pytest.raises(gpu.LeeaError):
+        with pytest.raises(gpu.LeeaError) as e:
             st.leea_generation(xf, y)
+        assert e.value.status == gpu.EINVAL
     finally:
         st.close()
 
@@ -227,3 +228,53 @@ def test_auto_switches_between_the_paths_with_the_batch(gpu, oracle_mod):
     finally:
         ref.close()
         auto.close()
+
+
+def _batch_f32(dims, batch, seed):
+    torch = _torch()
+    if dims[0] == 784:
+        x, y = synthetic.make_split(batch, seed=seed)
+    else:
+        x, y = synthetic.tiny_problem(dims[0], dims[-1], batch, seed=seed)
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda(), torch.from_numpy(np.ascontiguousarray(y)).cuda()
+
+
+@pytest.mark.parametrize("case", [
+    dict(dims=[784, 32, 10], pop=32, batches=[16, 16, 5], prm=dict(sel_op=1, tour_k=3, sigma=0.01, alpha=0.2)),
+    dict(dims=[100, 24, 3], pop=9, batches=[33, 100], prm=dict(n_elite=2, xo_op=1, sigma=0.1)),
+    dict(dims=[64, 72, 10], pop=5, batches=[8, 20], prm=dict(sigma=0.05)),
+], ids=lambda c: f"{c['dims']}-P{c['pop']}")
+def test_small_generation_fp32_inputs_match_the_cuda_core_path(gpu, oracle_mod, case):
+    # FP32 batches (x_hi w_hi + x_hi w_lo + x_lo w_hi on the tensor cores):
+    # children bit-identical, fitness within the evaluation tolerance of the
+    # two-kernel CUDA-core path and of the FP64 oracle's evaluation of the same children.
+    from paper_1806_09819_gb300 import leea
+    dims, pop, prm = case["dims"], case["pop"], case["prm"]
+    ref = gpu.LeeaState(pop, dims, gpu.Params(**prm, eval_path=leea.EVAL_SIMT), seed=31)
+    sgl = gpu.LeeaState(pop, dims, gpu.Params(**prm, eval_path=leea.EVAL_SMALL), seed=31)
+    try:
+        for g, b in enumerate(case["batches"]):
+            xd, yd = _batch_f32(dims, b, seed=700 + g)
+            for st in (ref, sgl):
+                st.leea_generation(xd, yd)
+            kids = ref.leea_get_population()
+            np.testing.assert_array_equal(_bits(sgl.leea_get_population()), _bits(kids))
+            f_ref, cor_ref = ref.leea_fitness(with_correct=True)
+            f_sgl, cor_sgl = sgl.leea_fitness(with_correct=True)
+            assert_fitness_close(f_sgl, f_ref, f"generation {g}: f_adj")
+            o_f, _, logits = oracle_mod.evaluate(kids.astype(np.float64), dims, xd.cpu().numpy().astype(np.float64),
+                                                 yd.cpu().numpy(), want_logits=True)
+            assert_fitness_close(sgl.leea_raw_fitness(), o_f, f"generation {g}: f_raw vs the oracle")
+            assert_correct_close(cor_sgl, cor_ref, logits)
+            sgl.leea_set_fitness(f_ref)
+    finally:
+        ref.close()
+        sgl.close()
+
+
+def test_small_generation_fp32_lockstep_with_oracle(gpu, oracle_mod):
+    from test_gpu_generation import CONFIG_SMALL, _lockstep
+    from paper_1806_09819_gb300 import leea
+    prm = dict(CONFIG_SMALL["prm"], eval_path=leea.EVAL_SMALL)
+    _lockstep(gpu, oracle_mod, CONFIG_SMALL["dims"], CONFIG_SMALL["pop"], CONFIG_SMALL["batch"], prm, u8=False)
+    _lockstep(gpu, oracle_mod, [784, 16, 10], 5, 3, dict(sigma=0.05, xo_op=1, eval_path=leea.EVAL_SMALL), u8=False)
