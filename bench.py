@@ -836,7 +836,9 @@ def run_small(args, rank: int, world: int, local_rank: int):
                 pop, batch, 0, x16=args.eval_path in (0, 2)).values()))),
             "roofline": roofline, "clocks": clk}
     line["config"]["generation"] = ("one kernel: ranking, selection, breeding and evaluation (one CTA per child "
-                                    "and 8 hidden units)" if single_launch else "a chain of kernels")
+                                    "and 8 hidden units; layer 1 on m16n8k8 TF32 tiles, the levels exact, each "
+                                    "weight as two TF32 pieces: 22-bit significands, exact products, FP32 "
+                                    "accumulation)" if single_launch else "a chain of kernels")
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         x64 = xtr[idx[warmup + steps]].astype(np.float64) / 255.0
         line["cpu_baseline"] = small_cpu_baseline(st.leea_get_population(), st.leea_fitness(), x64,
